@@ -1,0 +1,231 @@
+/*
+ * psdproj.h -- C ABI of the GB300 (sm_103a) randomized PSD-projection library.
+ *
+ * Method: Jones & Anderson, "Approximate Projection onto the Positive
+ * Semidefinite Cone Using Randomization" (arXiv 2410.19208).
+ *   psdproj_alg1  = the paper's Alg. 2 (randomized PSD projection) with the
+ *                   randomized range finder of Alg. 1 inside;
+ *   psdproj_alg2  = the paper's Alg. 3 (scaled randomized PSD projection) with
+ *                   alpha from Alg. 5 (min_eig, built on Alg. 4) unless given.
+ * Naming: k is the target rank, p the oversampling (the paper's letter l),
+ * l = k + p the sketch width, q the power-iteration exponent of Alg. 1.
+ *
+ * Memory conventions (all pointers prefixed d are DEVICE pointers on the
+ * context's device; h are HOST pointers):
+ *   A   n x n symmetric, FP32, row-major with leading dimension lda >= n.
+ *       Only the upper triangle A[i*lda + j], j >= i, is ever read (BLAS
+ *       uplo='U' in row-major terms); the strict lower triangle may hold
+ *       anything, including NaN.
+ *   P   n x n FP32 output, row-major, ldp >= n.
+ *   tall matrices (Omega, Y, Q, W) are column-major n x c with leading
+ *       dimension ld >= n: element (i, c) at X[c*ld + i].
+ *   small matrices (Gram, R, core C, V) are column-major m x m, ld = m.
+ * Ownership: the caller owns every pointer it passes; the context owns its
+ * workspaces (allocated lazily, grown on demand, freed by psdproj_destroy).
+ * Asynchrony: every compute call is enqueued on the context's stream and
+ * returns without synchronising.  The return code reports argument, resource
+ * and launch errors; errors found on the device (non-finite data, eigensolver
+ * non-convergence) set a device status word read by psdproj_sync_status.
+ * Thread safety: a context may be used by one host thread at a time.
+ */
+#ifndef PSDPROJ_H
+#define PSDPROJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define PSDPROJ_OK          0
+#define PSDPROJ_EINVAL      1  /* bad argument (sizes, leading dims, NULL)     */
+#define PSDPROJ_ENOMEM      2  /* device allocation failed                      */
+#define PSDPROJ_ENOTFINITE  3  /* non-finite value met on the device            */
+#define PSDPROJ_ENOCONV     4  /* the l x l eigensolver hit its sweep limit     */
+#define PSDPROJ_ETIMEOUT    5  /* a bounded device wait gave up                 */
+#define PSDPROJ_ECUDA       6  /* a CUDA runtime / launch error                 */
+#define PSDPROJ_ENOTSUP     7  /* option not supported for these sizes         */
+
+/* ---- precision of the A-passes (sketch, power and core products) -------- */
+#define PSDPROJ_PREC_FP32    0 /* FP32 FMA on the CUDA cores (plain FP32)      */
+#define PSDPROJ_PREC_TF32    1 /* tcgen05 kind::tf32, FP32 accumulation        */
+#define PSDPROJ_PREC_BF16    2 /* tcgen05 kind::f16 (bf16 hi only)             */
+#define PSDPROJ_PREC_BF16X3  3 /* split-BF16: hi*hi + hi*lo + lo*hi            */
+
+/* ---- output modes -------------------------------------------------------- */
+#define PSDPROJ_OUT_FULL    0  /* P written in full (upper tiles mirrored)     */
+#define PSDPROJ_OUT_UPPER   1  /* only P[i*ldp + j], j >= i, written           */
+#define PSDPROJ_OUT_FACTOR  2  /* P not written; W = Q V sqrt(max(D,0)) only   */
+
+typedef struct psdproj_ctx psdproj_ctx;
+
+typedef struct psdproj_opts {
+    int prec;        /* PSDPROJ_PREC_* for the A-passes (default FP32)          */
+    int syrk_prec;   /* PSDPROJ_PREC_FP32 or _BF16X3 for P = W W^T (default FP32)*/
+    int N;           /* iterations of Alg. 4 inside Alg. 5 (default 10)          */
+    int out_mode;    /* PSDPROJ_OUT_* (default FULL)                             */
+    int reserved[4]; /* must be zero                                             */
+} psdproj_opts;
+
+/* Fill *o with the defaults listed above. */
+void psdproj_default_opts(psdproj_opts *o);
+
+/* Create a context bound to CUDA device `device` and CUDA stream `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Returns a status. */
+int psdproj_create(psdproj_ctx **ctx, int device, void *stream);
+/* Re-bind the context to another stream of the same device. */
+int psdproj_set_stream(psdproj_ctx *ctx, void *stream);
+/* Free the context and its workspaces (synchronises its stream first). */
+int psdproj_destroy(psdproj_ctx *ctx);
+/* Synchronise the context's stream; return the first device-side status
+ * recorded since the last call (then clear it), or a CUDA error. */
+int psdproj_sync_status(psdproj_ctx *ctx);
+/* Human-readable name of a status code (static storage). */
+const char *psdproj_status_string(int status);
+/* Bytes of device workspace the context holds now. */
+size_t psdproj_workspace_bytes(const psdproj_ctx *ctx);
+
+/* ---- diagnostics --------------------------------------------------------- */
+/* Stage classes timed by the context when timing is on. */
+#define PSDPROJ_STAGE_APASS   0  /* symmetric passes Y = (A + s I) X           */
+#define PSDPROJ_STAGE_GEMV    1  /* power-iteration products of Alg. 4          */
+#define PSDPROJ_STAGE_ORTH    2  /* CholeskyQR2                                 */
+#define PSDPROJ_STAGE_CORE    3  /* Q^T Z                                       */
+#define PSDPROJ_STAGE_EIG     4  /* l x l eigensolver                           */
+#define PSDPROJ_STAGE_FACTOR  5  /* W = Q V sqrt(D+)                            */
+#define PSDPROJ_STAGE_SYRK    6  /* P = W W^T                                   */
+#define PSDPROJ_STAGE_OTHER   7  /* Omega, alpha, copies                        */
+#define PSDPROJ_NSTAGES       8
+
+/* Turn per-stage CUDA-event timing on (1) or off (0).  When on, every stage
+ * launched on the context's stream is bracketed by two events (at most 4096
+ * stages between reads; later ones are not timed). */
+int psdproj_timing_enable(psdproj_ctx *ctx, int on);
+/* Synchronise the stream, add the elapsed milliseconds of every stage timed
+ * since the last read into ms[kind] and their number into count[kind]
+ * (arrays of nkinds entries, nkinds <= PSDPROJ_NSTAGES), then forget them. */
+int psdproj_timing_read(psdproj_ctx *ctx, double *ms, int *count, int nkinds);
+/* Number of kernels this library has launched in this process. */
+uint64_t psdproj_kernel_launches(void);
+
+/* ======================================================================== */
+/* Whole projections                                                         */
+/* ======================================================================== */
+
+/* Randomized PSD projection (Alg. 2 with the range finder of Alg. 1):
+ *   Omega = randn(n, k+p) (Philox4x32-10 stream 0 of `seed`),
+ *   Q = orth(A^(2q+1) Omega), orthonormalised after every product,
+ *   Q^T A Q = V D V^T,  W = Q V sqrt(max(D,0)),  P = W W^T.
+ * Requires n >= 1, k >= 1, p >= 0, 1 <= k+p <= min(n, 256), 0 <= q <= 16,
+ * lda >= n, ldp >= n (when P is written), ldw >= n (when dW != NULL).
+ * dP may be NULL only with out_mode FACTOR.  dW (n x (k+p), column-major)
+ * may be NULL; its columns beyond r+ are zero.  d_rank (device int, may be
+ * NULL) receives r+, the number of positive eigenvalues of Q^T A Q.
+ * opts may be NULL (defaults). */
+int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
+                 int k, int p, int q, uint64_t seed,
+                 float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
+                 const psdproj_opts *opts);
+
+/* Scaled randomized PSD projection (Alg. 3):
+ *   alpha = alpha_in if alpha_in > 0, else min_eig(A, N) (Alg. 5, start
+ *   vectors from Philox streams 3 and 4 of `seed`);
+ *   Q = orth((A + alpha I)^(2q+1) Omega)  -- the range of B = (A+alpha I)/alpha,
+ *   output Q (Q^T A Q)_+ Q^T, which equals the literal
+ *   alpha Q V (max(D,1) - I) V^T Q^T with V D V^T = Q^T B Q (Lemma 4).
+ * If alpha is not finite or alpha <= 1e-300 (A PSD and singular, or A = 0),
+ * the call computes psdproj_alg1's output instead and sets bit 0 of
+ * *d_info (device int, may be NULL).  d_alpha_out (device double, may be
+ * NULL) receives the alpha used.  Other arguments as for psdproj_alg1. */
+int psdproj_alg2(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
+                 int k, int p, int q, uint64_t seed, double alpha_in,
+                 double *d_alpha_out, int *d_info,
+                 float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
+                 const psdproj_opts *opts);
+
+/* Host-buffer forms of the two calls: hA, hP, hW, h_rank are HOST pointers
+ * (pinned memory recommended).  The call copies A to a context-owned device
+ * buffer, runs the projection, copies P (and W, r+) back, and synchronises
+ * the stream before returning.  Returns the first error, device-side status
+ * included. */
+int psdproj_alg1_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda,
+                      int k, int p, int q, uint64_t seed,
+                      float *hP, int64_t ldp, float *hW, int64_t ldw, int *h_rank,
+                      const psdproj_opts *opts);
+int psdproj_alg2_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda,
+                      int k, int p, int q, uint64_t seed, double alpha_in,
+                      double *h_alpha_out,
+                      float *hP, int64_t ldp, float *hW, int64_t ldw, int *h_rank,
+                      const psdproj_opts *opts);
+
+/* ======================================================================== */
+/* Steps of the path (each one kernel or a short chain of kernels)           */
+/* ======================================================================== */
+
+/* Test matrix of Alg. 1 ("Omega = randn"): dX[c*ldx + i] = N(0,1) sample keyed
+ * by Philox4x32-10 counter (i, c, stream, 0) and key (seed lo, seed hi), by
+ * Box-Muller (cosine branch) on output words 0 and 1, for i < n, c < m.
+ * Requires n >= 1, 1 <= m, ldx >= n. */
+int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream,
+                     int64_t n, int m, float *dX, int64_t ldx);
+
+/* Symmetric pass over A (Alg. 1 products, and Z = A Q of Alg. 2 line 2):
+ *   dY = A dX + shift dX,   shift = (d_shift ? *d_shift : 0),
+ * reading only the upper triangle of A, once.  dX, dY are n x m column-major
+ * (ldx, ldy >= n); dY is overwritten.  prec is PSDPROJ_PREC_*; the
+ * tensor-core forms need m <= 256 and return ENOTSUP otherwise. */
+int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
+                     const float *dX, int64_t ldx, int m, const double *d_shift,
+                     float *dY, int64_t ldy, int prec);
+
+/* Orthonormalisation of Alg. 1 (QR 'econ') by CholeskyQR2: G = Y^T Y with
+ * FP32 products accumulated in FP64, R = chol(G) in FP64, Q = Y R^-1, done
+ * twice.  A column whose pivot R_jj^2 <= 1e-10 * max_i G_ii is dependent: its
+ * Q column is set to zero.  dY (input) and dQ (output) are n x m column-major;
+ * they may alias.  d_qrank (device int, may be NULL) receives the number of
+ * independent columns.  Requires 1 <= m <= 256. */
+int psdproj_cholqr2(psdproj_ctx *ctx, const float *dY, int64_t n, int64_t ldy,
+                    int m, float *dQ, int64_t ldq, int *d_qrank);
+
+/* Projected core of Alg. 2 line 2: dC = (X^T Z + Z^T X) / 2 (m x m FP64,
+ * column-major), with FP32 products accumulated in FP64. */
+int psdproj_core(psdproj_ctx *ctx, const float *dX, int64_t ldx, const float *dZ,
+                 int64_t ldz, int64_t n, int m, double *dC);
+
+/* Small symmetric eigensolver of Alg. 2 line 2 ("eig(Q^T X Q)"): parallel
+ * cyclic Jacobi in one thread block on dC (m x m FP64 in, read only).
+ * dV (m x m column-major FP32) receives orthonormal eigenvectors, dd (m
+ * doubles) the eigenvalues; eigenpairs are sorted by decreasing eigenvalue.
+ * Requires 1 <= m <= 256.  Non-convergence sets PSDPROJ_ENOCONV in the
+ * device status. */
+int psdproj_eig(psdproj_ctx *ctx, const double *dC, int m, float *dV, double *dd);
+
+/* Factor of Alg. 2 line 3: dW = Q V diag(sqrt(max(d, 0))) (n x m, column-
+ * major; the r+ columns with d > 0 first, zero columns after), and *d_rank =
+ * r+.  dV, dd as produced by psdproj_eig (sorted decreasingly). */
+int psdproj_factor(psdproj_ctx *ctx, const float *dQ, int64_t ldq, int64_t n,
+                   int m, const float *dV, const double *dd, float *dW,
+                   int64_t ldw, int *d_rank);
+
+/* Reconstruction P = W W^T (Alg. 2 line 3) over the first *d_rank columns of
+ * dW (device int; NULL = all m).  out_mode FULL writes all of P, UPPER only
+ * j >= i.  prec: PSDPROJ_PREC_FP32 or PSDPROJ_PREC_BF16X3. */
+int psdproj_syrk(psdproj_ctx *ctx, const float *dW, int64_t ldw, int64_t n,
+                 int m, const int *d_rank, float *dP, int64_t ldp,
+                 int out_mode, int prec);
+
+/* min_eig of Alg. 5 on the device: sigma1 = power_iteration(A, N) (Alg. 4,
+ * start vector stream 3), sigma2 = power_iteration(A - sigma1 I, N) (stream
+ * 4), alpha = |sigma1 - sigma2|.  Each power iteration makes N + 1 symmetric
+ * matrix-vector passes over the upper triangle with FP64 norms.  Outputs are
+ * device doubles; d_sigma1 and d_sigma2 may be NULL. */
+int psdproj_min_eig(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
+                    int N, uint64_t seed, double *d_alpha, double *d_sigma1,
+                    double *d_sigma2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSDPROJ_H */

@@ -1,0 +1,246 @@
+"""Python binding of libpsdproj (include/psdproj.h): randomized PSD-cone
+projections (arXiv 2410.19208, Algs. 1-5) on one GB300 GPU.
+
+This module only marshals arguments: every step runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU path:
+if the compiled library is missing, importing the binding raises.
+
+Layouts (same as the C ABI):
+* A, P: square FP32 tensors, row-major (stride(1) == 1), only the upper
+  triangle of A is read.
+* tall matrices (Omega, Y, Q, W): shape (n, m) COLUMN-major, i.e. stride(0)
+  == 1 and stride(1) = ld >= n.  ``tall_empty(n, m)`` makes one.
+* small matrices (core C, V): shape (m, m) column-major (use ``.t()`` of a
+  row-major tensor).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpsdproj.so")
+
+PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
+OUT_FULL, OUT_UPPER, OUT_FACTOR = 0, 1, 2
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTFINITE", 4: "ENOCONV", 5: "ETIMEOUT",
+          6: "ECUDA", 7: "ENOTSUP"}
+
+
+class PsdprojError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("syrk_prec", ctypes.c_int), ("N", ctypes.c_int),
+                ("out_mode", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_u64 = ctypes.c_uint64
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpsdproj.so not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "psdproj_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "psdproj_create": (_int, [ctypes.POINTER(_P), _int, _P]),
+        "psdproj_set_stream": (_int, [_P, _P]),
+        "psdproj_destroy": (_int, [_P]),
+        "psdproj_sync_status": (_int, [_P]),
+        "psdproj_status_string": (ctypes.c_char_p, [_int]),
+        "psdproj_workspace_bytes": (ctypes.c_size_t, [_P]),
+        "psdproj_alg1": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, _P, _i64, _P, _i64,
+                                _P, ctypes.POINTER(Opts)]),
+        "psdproj_alg2": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, ctypes.c_double,
+                                _P, _P, _P, _i64, _P, _i64, _P, ctypes.POINTER(Opts)]),
+        "psdproj_alg1_host": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, _P, _i64, _P,
+                                     _i64, _P, ctypes.POINTER(Opts)]),
+        "psdproj_alg2_host": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64,
+                                     ctypes.c_double, _P, _P, _i64, _P, _i64, _P,
+                                     ctypes.POINTER(Opts)]),
+        "psdproj_gaussian": (_int, [_P, _u64, ctypes.c_uint32, _i64, _int, _P, _i64]),
+        "psdproj_sym_pass": (_int, [_P, _P, _i64, _i64, _P, _i64, _int, _P, _P, _i64, _int]),
+        "psdproj_cholqr2": (_int, [_P, _P, _i64, _i64, _int, _P, _i64, _P]),
+        "psdproj_core": (_int, [_P, _P, _i64, _P, _i64, _i64, _int, _P]),
+        "psdproj_eig": (_int, [_P, _P, _int, _P, _P]),
+        "psdproj_factor": (_int, [_P, _P, _i64, _i64, _int, _P, _P, _P, _i64, _P]),
+        "psdproj_syrk": (_int, [_P, _P, _i64, _i64, _int, _P, _P, _i64, _int, _int]),
+        "psdproj_min_eig": (_int, [_P, _P, _i64, _i64, _int, _u64, _P, _P, _P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def lib():
+    return _load()
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise PsdprojError(code, what)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _sq(A, name="A"):
+    assert A.is_cuda and A.dtype == torch.float32 and A.dim() == 2, name
+    assert A.shape[0] == A.shape[1] and A.stride(1) == 1, f"{name}: row-major square FP32"
+    return A.shape[0], A.stride(0)
+
+
+def _tall(X, name="X"):
+    assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2, name
+    assert X.stride(0) == 1 or X.shape[1] == 1, f"{name}: column-major (stride(0) == 1)"
+    ld = X.stride(1) if X.shape[1] > 1 else max(X.shape[0], X.stride(1))
+    return X.shape[0], X.shape[1], ld
+
+
+def tall_empty(n: int, m: int, device="cuda", ld: int | None = None):
+    """Column-major n x m FP32 device tensor (shape (n, m), stride (1, ld))."""
+    ld = ld or n
+    return torch.empty(m, ld, dtype=torch.float32, device=device).t()[:n]
+
+
+def make_opts(prec=PREC_FP32, syrk_prec=PREC_FP32, N=10, out_mode=OUT_FULL) -> Opts:
+    o = Opts()
+    _load().psdproj_default_opts(ctypes.byref(o))
+    o.prec, o.syrk_prec, o.N, o.out_mode = prec, syrk_prec, N, out_mode
+    return o
+
+
+class Context:
+    """A psdproj context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        lib = _load()
+        self.device = device
+        self.stream = stream or torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        _check(lib.psdproj_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream)),
+               "psdproj_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _load().psdproj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        _check(_load().psdproj_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "set_stream")
+
+    def sync_status(self) -> int:
+        return _load().psdproj_sync_status(self.h)
+
+    def workspace_bytes(self) -> int:
+        return int(_load().psdproj_workspace_bytes(self.h))
+
+    # ---- whole projections ------------------------------------------------
+    def alg1(self, A, k, p, q, seed, P=None, W=None, rank=None, opts: Opts | None = None):
+        n, lda = _sq(A)
+        ldp = P.stride(0) if P is not None else n
+        ldw = _tall(W, "W")[2] if W is not None else n
+        _check(_load().psdproj_alg1(self.h, _ptr(A), n, lda, k, p, q, seed, _ptr(P), ldp, _ptr(W),
+                                    ldw, _ptr(rank), ctypes.byref(opts) if opts else None),
+               "psdproj_alg1")
+
+    def alg2(self, A, k, p, q, seed, alpha_in=0.0, alpha_out=None, info=None, P=None, W=None,
+             rank=None, opts: Opts | None = None):
+        n, lda = _sq(A)
+        ldp = P.stride(0) if P is not None else n
+        ldw = _tall(W, "W")[2] if W is not None else n
+        _check(_load().psdproj_alg2(self.h, _ptr(A), n, lda, k, p, q, seed, float(alpha_in),
+                                    _ptr(alpha_out), _ptr(info), _ptr(P), ldp, _ptr(W), ldw,
+                                    _ptr(rank), ctypes.byref(opts) if opts else None),
+               "psdproj_alg2")
+
+    def alg1_host(self, A, k, p, q, seed, P=None, W=None, opts: Opts | None = None):
+        """Host tensors (CPU, pinned recommended); returns r+."""
+        n = A.shape[0]
+        rk = ctypes.c_int(0)
+        _check(_load().psdproj_alg1_host(
+            self.h, ctypes.c_void_p(A.data_ptr()), n, A.stride(0), k, p, q, seed,
+            _ptr(P), P.stride(0) if P is not None else n, _ptr(W),
+            W.stride(1) if W is not None else n, ctypes.byref(rk),
+            ctypes.byref(opts) if opts else None), "psdproj_alg1_host")
+        return rk.value
+
+    def alg2_host(self, A, k, p, q, seed, alpha_in=0.0, P=None, W=None, opts: Opts | None = None):
+        n = A.shape[0]
+        rk = ctypes.c_int(0)
+        al = ctypes.c_double(0)
+        _check(_load().psdproj_alg2_host(
+            self.h, ctypes.c_void_p(A.data_ptr()), n, A.stride(0), k, p, q, seed,
+            float(alpha_in), ctypes.byref(al), _ptr(P), P.stride(0) if P is not None else n,
+            _ptr(W), W.stride(1) if W is not None else n, ctypes.byref(rk),
+            ctypes.byref(opts) if opts else None), "psdproj_alg2_host")
+        return rk.value, al.value
+
+    # ---- steps of the path -----------------------------------------------
+    def gaussian(self, seed, stream_id, X):
+        n, m, ld = _tall(X)
+        _check(_load().psdproj_gaussian(self.h, seed, stream_id, n, m, _ptr(X), ld), "gaussian")
+
+    def sym_pass(self, A, X, Y, shift=None, prec=PREC_FP32):
+        n, lda = _sq(A)
+        _, m, ldx = _tall(X)
+        _, _, ldy = _tall(Y, "Y")
+        _check(_load().psdproj_sym_pass(self.h, _ptr(A), n, lda, _ptr(X), ldx, m, _ptr(shift),
+                                        _ptr(Y), ldy, prec), "sym_pass")
+
+    def cholqr2(self, Y, Q, qrank=None):
+        n, m, ldy = _tall(Y, "Y")
+        _, _, ldq = _tall(Q, "Q")
+        _check(_load().psdproj_cholqr2(self.h, _ptr(Y), n, ldy, m, _ptr(Q), ldq, _ptr(qrank)),
+               "cholqr2")
+
+    def core(self, X, Z, C):
+        n, m, ldx = _tall(X)
+        _, _, ldz = _tall(Z, "Z")
+        _check(_load().psdproj_core(self.h, _ptr(X), ldx, _ptr(Z), ldz, n, m, _ptr(C)), "core")
+
+    def eig(self, C, V, d):
+        m = C.shape[0]
+        _check(_load().psdproj_eig(self.h, _ptr(C), m, _ptr(V), _ptr(d)), "eig")
+
+    def factor(self, Q, V, d, W, rank=None):
+        n, m, ldq = _tall(Q, "Q")
+        _, _, ldw = _tall(W, "W")
+        _check(_load().psdproj_factor(self.h, _ptr(Q), ldq, n, m, _ptr(V), _ptr(d), _ptr(W), ldw,
+                                      _ptr(rank)), "factor")
+
+    def syrk(self, W, P, rank=None, out_mode=OUT_FULL, prec=PREC_FP32):
+        n, m, ldw = _tall(W, "W")
+        _check(_load().psdproj_syrk(self.h, _ptr(W), ldw, n, m, _ptr(rank), _ptr(P), P.stride(0),
+                                    out_mode, prec), "syrk")
+
+    def min_eig(self, A, N, seed, alpha, sigma1=None, sigma2=None):
+        n, lda = _sq(A)
+        _check(_load().psdproj_min_eig(self.h, _ptr(A), n, lda, N, seed, _ptr(alpha),
+                                       _ptr(sigma1), _ptr(sigma2)), "min_eig")

@@ -1,0 +1,616 @@
+// C ABI of the psdproj library: context, workspace and the two pipelines.
+//
+//   psdproj_alg1: Alg. 2 (randomized PSD projection) with the range finder of
+//                 Alg. 1, orthonormalising after every product.
+//   psdproj_alg2: Alg. 3 (scaled randomized PSD projection) with alpha from
+//                 Alg. 5 unless given; the core and last step use the reduced
+//                 form Q (Q^T A Q)_+ Q^T of Lemma 4.
+// Every step is a kernel of this library; nothing runs on the host but
+// argument checks, workspace management and launches.
+#include <cstdio>
+#include <cstdlib>
+#include <atomic>
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+
+namespace {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return PSDPROJ_OK;
+    if (e == cudaErrorMemoryAllocation) return PSDPROJ_ENOMEM;
+    if (e == cudaErrorNotSupported) return PSDPROJ_ENOTSUP;
+    return PSDPROJ_ECUDA;
+}
+
+#define PSD_CK(expr)                              \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess) return cuda_status(_e); \
+    } while (0)
+
+#define PSD_TRY(expr)                 \
+    do {                              \
+        int _s = (expr);              \
+        if (_s != PSDPROJ_OK) return _s; \
+    } while (0)
+
+struct device_guard {
+    int prev = -1;
+    explicit device_guard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~device_guard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+std::atomic<uint64_t> g_launches{0};
+
+// counts the kernels a launcher started, then checks its status
+#define PSD_KL(expr, nk)                                   \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return cuda_status(_e);     \
+        g_launches.fetch_add((uint64_t)(nk));              \
+    } while (0)
+
+// brackets one stage with two events when timing is on
+struct stage_scope {
+    psdproj_ctx *c;
+    bool rec = false;
+    stage_scope(psdproj_ctx *ctx, int kind) : c(ctx)
+    {
+        psd_timing &t = c->timing;
+        if (t.on && t.created && t.n < PSD_MAX_TIMED) {
+            cudaEventRecord(t.ev[2 * t.n], c->stream);
+            t.kind[t.n] = kind;
+            rec = true;
+        }
+    }
+    ~stage_scope()
+    {
+        if (rec) {
+            psd_timing &t = c->timing;
+            cudaEventRecord(t.ev[2 * t.n + 1], c->stream);
+            ++t.n;
+        }
+    }
+};
+
+void free_workspace(psd_workspace &ws)
+{
+    if (ws.base) cudaFree(ws.base);
+    ws = psd_workspace();
+}
+
+}  // namespace
+
+int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
+{
+    psd_workspace &ws = ctx->ws;
+    const int lpad = psd_lpad(m);
+    if (ws.base && ws.n >= n && ws.lpad >= lpad) return PSDPROJ_OK;
+    const int64_t nn = ws.base ? (n > ws.n ? n : ws.n) : n;
+    const int lp = ws.base ? (lpad > ws.lpad ? lpad : ws.lpad) : lpad;
+    const int64_t ld = psd_ld(nn);
+    const int64_t nchunk = (nn + PSD_GRAM_CHUNK - 1) / PSD_GRAM_CHUNK;
+    const size_t tall = align256(sizeof(float) * (size_t)ld * lp);
+    const size_t half_tall = align256(sizeof(uint16_t) * (size_t)ld * lp);
+    const size_t small_d = align256(sizeof(double) * (size_t)lp * lp);
+    const size_t small_f = align256(sizeof(float) * (size_t)lp * lp);
+    size_t total = 5 * tall + 2 * half_tall + align256(sizeof(float) * nchunk * lp * lp) +
+                   3 * small_d + align256(sizeof(double) * lp) + 3 * small_f +
+                   align256(sizeof(float) * 2 * (size_t)(lp + 2) * (lp + 2)) +
+                   align256(sizeof(int) * lp) + 2 * align256(sizeof(float) * ld) +
+                   align256(sizeof(double) * 16) + align256(sizeof(unsigned) * 16) +
+                   align256(sizeof(int) * 16);
+    if (ws.base) {
+        cudaStreamSynchronize(ctx->stream);
+        free_workspace(ws);
+    }
+    void *base = nullptr;
+    cudaError_t e = cudaMalloc(&base, total);
+    if (e != cudaSuccess) return cuda_status(e);
+    ws.base = base;
+    ws.bytes = total;
+    ws.n = nn;
+    ws.lpad = lp;
+    ws.ld = ld;
+    char *p = static_cast<char *>(base);
+    auto take = [&](size_t b) { char *q = p; p += b; return q; };
+    ws.Om = reinterpret_cast<float *>(take(tall));
+    ws.Y = reinterpret_cast<float *>(take(tall));
+    ws.Q = reinterpret_cast<float *>(take(tall));
+    ws.T = reinterpret_cast<float *>(take(tall));
+    ws.W = reinterpret_cast<float *>(take(tall));
+    ws.Xhi = reinterpret_cast<uint16_t *>(take(half_tall));
+    ws.Xlo = reinterpret_cast<uint16_t *>(take(half_tall));
+    ws.gpart = reinterpret_cast<float *>(take(align256(sizeof(float) * nchunk * lp * lp)));
+    ws.G = reinterpret_cast<double *>(take(small_d));
+    ws.R = reinterpret_cast<double *>(take(small_d));
+    ws.C = reinterpret_cast<double *>(take(small_d));
+    ws.d = reinterpret_cast<double *>(take(align256(sizeof(double) * lp)));
+    ws.Rinv = reinterpret_cast<float *>(take(small_f));
+    ws.V = reinterpret_cast<float *>(take(small_f));
+    ws.M = reinterpret_cast<float *>(take(small_f));
+    ws.eigscr = reinterpret_cast<float *>(take(align256(sizeof(float) * 2 * (size_t)(lp + 2) * (lp + 2))));
+    ws.dead = reinterpret_cast<int *>(take(align256(sizeof(int) * lp)));
+    ws.pv0 = reinterpret_cast<float *>(take(align256(sizeof(float) * ld)));
+    ws.pv1 = reinterpret_cast<float *>(take(align256(sizeof(float) * ld)));
+    ws.scal = reinterpret_cast<double *>(take(align256(sizeof(double) * 16)));
+    ws.counter = reinterpret_cast<unsigned *>(take(align256(sizeof(unsigned) * 16)));
+    ws.ints = reinterpret_cast<int *>(take(align256(sizeof(int) * 16)));
+    // zero everything once: padded rows / columns of the tall buffers stay 0
+    e = cudaMemsetAsync(base, 0, total, ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return PSDPROJ_OK;
+}
+
+namespace {
+
+// scalar slots in ws.scal
+enum { SC_SHIFT = 4, SC_SIGMA1 = 5, SC_SIGMA2 = 6, SC_ALPHA = 7 };
+// int slots in ws.ints
+enum { IN_RANK = 0, IN_INFO = 1, IN_QRANK = 2 };
+
+int check_opts(const psdproj_opts *o)
+{
+    if (o->prec < PSDPROJ_PREC_FP32 || o->prec > PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
+    if (o->syrk_prec != PSDPROJ_PREC_FP32 && o->syrk_prec != PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
+    if (o->out_mode < PSDPROJ_OUT_FULL || o->out_mode > PSDPROJ_OUT_FACTOR) return PSDPROJ_EINVAL;
+    if (o->N < 0 || o->N > 10000) return PSDPROJ_EINVAL;
+    return PSDPROJ_OK;
+}
+
+// Y = A X + shift X in the requested precision
+int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const float *X,
+             int64_t ldx, int m, const double *d_shift, float *Y, int64_t ldy, int prec)
+{
+    stage_scope st(ctx, PSDPROJ_STAGE_APASS);
+    if (prec == PSDPROJ_PREC_FP32) {
+        PSD_KL(launch_sym_pass_simt(ctx->stream, A, n, lda, X, ldx, m, d_shift, Y, ldy), 1);
+        return PSDPROJ_OK;
+    }
+    psd_workspace &ws = ctx->ws;
+    PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->sm_count, A, n, lda, X, ldx, m, d_shift, Y, ldy,
+                              prec, ws.Xhi, ws.Xlo, ws.ld, ctx->d_status), 2);
+    return PSDPROJ_OK;
+}
+
+// CholeskyQR2: Q = orth(Y); Y is read only in the first half.
+int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, float *Q,
+            int64_t ldq, int *d_qrank)
+{
+    psd_workspace &ws = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    const double tau = 1e-10;
+    stage_scope st(ctx, PSDPROJ_STAGE_ORTH);
+    PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1), 2);
+    PSD_KL(launch_cholesky(s, ws.G, m, ws.R, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status), 1);
+    PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, ws.T, ws.ld), 1);
+    PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1), 2);
+    PSD_KL(launch_cholesky(s, ws.G, m, ws.R, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status), 1);
+    PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq), 1);
+    return PSDPROJ_OK;
+}
+
+int validate(int64_t n, int64_t lda, int k, int p, int q, const void *A)
+{
+    if (!A || n < 1 || k < 1 || p < 0 || q < 0 || q > 16 || lda < n) return PSDPROJ_EINVAL;
+    const int64_t m = (int64_t)k + p;
+    if (m < 1 || m > n || m > PSD_MAX_M) return PSDPROJ_EINVAL;
+    return PSDPROJ_OK;
+}
+
+int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int k, int p,
+                   int q, uint64_t seed, bool scaled, double alpha_in, double *d_alpha_out,
+                   int *d_info, float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
+                   const psdproj_opts *opts_in)
+{
+    if (!ctx) return PSDPROJ_EINVAL;
+    psdproj_opts opts;
+    if (opts_in) opts = *opts_in; else psdproj_default_opts(&opts);
+    PSD_TRY(check_opts(&opts));
+    PSD_TRY(validate(n, lda, k, p, q, dA));
+    if (opts.out_mode != PSDPROJ_OUT_FACTOR && (!dP || ldp < n)) return PSDPROJ_EINVAL;
+    if (dW && ldw < n) return PSDPROJ_EINVAL;
+    const int m = k + p;
+    device_guard g(ctx->device);
+    PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    psd_workspace &ws = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    const double *shift = nullptr;
+    if (scaled) {
+        double *sc = ws.scal;
+        if (!(alpha_in > 0.0)) {
+            stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
+            PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
+                                          sc, ws.counter, sc + SC_SIGMA1), opts.N + 3);
+            PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0,
+                                          ws.pv1, sc, ws.counter, sc + SC_SIGMA2), opts.N + 3);
+        }
+        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
+        PSD_KL(launch_alpha_finish(s, sc + SC_SIGMA1, sc + SC_SIGMA2, alpha_in,
+                                   d_alpha_out ? d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
+                                   d_info ? d_info : ws.ints + IN_INFO), 1);
+        shift = sc + SC_SHIFT;
+    }
+    const int lpad = psd_lpad(m);
+    // Omega (Alg. 1), then Y = (A + shift I) Omega
+    {
+        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
+        PSD_KL(launch_gaussian(s, seed, 0u, n, m, lpad, ws.ld, ws.Om, ws.ld), 1);
+    }
+    PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, shift, ws.Y, ws.ld, opts.prec));
+    PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
+    for (int t = 0; t < 2 * q; ++t) {
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, shift, ws.Y, ws.ld, opts.prec));
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
+    }
+    // core C = Q^T A Q (Lemma 4: the unshifted A in both algorithms)
+    PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec));
+    {
+        stage_scope st(ctx, PSDPROJ_STAGE_CORE);
+        PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.Y, ws.ld, n, m, ws.gpart, ws.C, 2), 2);
+    }
+    {
+        stage_scope st(ctx, PSDPROJ_STAGE_EIG);
+        PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status), 1);
+    }
+    int *rk = ws.ints + IN_RANK;
+    float *Wd = dW ? dW : ws.W;
+    const int64_t ldwd = dW ? ldw : ws.ld;
+    {
+        stage_scope st(ctx, PSDPROJ_STAGE_FACTOR);
+        PSD_KL(launch_factor_prep(s, ws.V, ws.d, m, ws.M, rk), 1);
+        PSD_KL(launch_tall_small(s, ws.Q, ws.ld, n, m, ws.M, m, nullptr, rk, Wd, ldwd), 1);
+    }
+    if (opts.out_mode != PSDPROJ_OUT_FACTOR) {
+        stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
+        const int upper = opts.out_mode == PSDPROJ_OUT_UPPER;
+        if (opts.syrk_prec == PSDPROJ_PREC_FP32)
+            PSD_KL(launch_syrk_simt(s, Wd, ldwd, n, m, rk, dP, ldp, upper), 1);
+        else
+            PSD_KL(launch_syrk_tc(s, ctx->sm_count, Wd, ldwd, n, m, rk, dP, ldp, upper, ws.Xhi,
+                                  ws.Xlo, ws.ld, ctx->d_status), 2);
+    }
+    if (d_rank) PSD_CK(cudaMemcpyAsync(d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    return PSDPROJ_OK;
+}
+
+int ensure_stage(float **buf, size_t *cap, size_t bytes, cudaStream_t s)
+{
+    if (*cap >= bytes) return PSDPROJ_OK;
+    if (*buf) {
+        cudaStreamSynchronize(s);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMalloc(buf, bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    *cap = bytes;
+    return PSDPROJ_OK;
+}
+
+int run_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda, int k, int p, int q,
+             uint64_t seed, bool scaled, double alpha_in, double *h_alpha, float *hP,
+             int64_t ldp, float *hW, int64_t ldw, int *h_rank, const psdproj_opts *opts_in)
+{
+    if (!ctx) return PSDPROJ_EINVAL;
+    psdproj_opts opts;
+    if (opts_in) opts = *opts_in; else psdproj_default_opts(&opts);
+    PSD_TRY(check_opts(&opts));
+    PSD_TRY(validate(n, lda, k, p, q, hA));
+    const bool wantP = opts.out_mode != PSDPROJ_OUT_FACTOR;
+    if (wantP && (!hP || ldp < n)) return PSDPROJ_EINVAL;
+    if (hW && ldw < n) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    cudaStream_t s = ctx->stream;
+    const int m = k + p;
+    PSD_TRY(ensure_stage(&ctx->dA_stage, &ctx->dA_stage_bytes, sizeof(float) * n * n, s));
+    if (wantP) PSD_TRY(ensure_stage(&ctx->dP_stage, &ctx->dP_stage_bytes, sizeof(float) * n * n, s));
+    if (hW) PSD_TRY(ensure_stage(&ctx->dW_stage, &ctx->dW_stage_bytes, sizeof(float) * n * m, s));
+    PSD_CK(cudaMemcpy2DAsync(ctx->dA_stage, sizeof(float) * n, hA, sizeof(float) * lda,
+                             sizeof(float) * n, n, cudaMemcpyHostToDevice, s));
+    PSD_TRY(run_projection(ctx, ctx->dA_stage, n, n, k, p, q, seed, scaled, alpha_in,
+                           ctx->d_misc_f, ctx->d_misc + 1, wantP ? ctx->dP_stage : nullptr, n,
+                           hW ? ctx->dW_stage : nullptr, n, ctx->d_misc, &opts));
+    if (wantP)
+        PSD_CK(cudaMemcpy2DAsync(hP, sizeof(float) * ldp, ctx->dP_stage, sizeof(float) * n,
+                                 sizeof(float) * n, n, cudaMemcpyDeviceToHost, s));
+    if (hW)
+        PSD_CK(cudaMemcpy2DAsync(hW, sizeof(float) * ldw, ctx->dW_stage, sizeof(float) * n,
+                                 sizeof(float) * n, m, cudaMemcpyDeviceToHost, s));
+    if (h_rank) PSD_CK(cudaMemcpyAsync(h_rank, ctx->d_misc, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (h_alpha && scaled)
+        PSD_CK(cudaMemcpyAsync(h_alpha, ctx->d_misc_f, sizeof(double), cudaMemcpyDeviceToHost, s));
+    return psdproj_sync_status(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+void psdproj_default_opts(psdproj_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->prec = PSDPROJ_PREC_FP32;
+    o->syrk_prec = PSDPROJ_PREC_FP32;
+    o->N = 10;
+    o->out_mode = PSDPROJ_OUT_FULL;
+}
+
+int psdproj_create(psdproj_ctx **out, int device, void *stream)
+{
+    if (!out) return PSDPROJ_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return PSDPROJ_EINVAL;
+    device_guard g(device);
+    psdproj_ctx *c = new (std::nothrow) psdproj_ctx();
+    if (!c) return PSDPROJ_ENOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = cudaMalloc(&c->d_status, 64);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_misc, 64);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_misc_f, 64);
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 64);
+    if (e == cudaSuccess) e = cudaMemset(c->d_misc, 0, 64);
+    if (e != cudaSuccess) {
+        psdproj_destroy(c);
+        return cuda_status(e);
+    }
+    *out = c;
+    return PSDPROJ_OK;
+}
+
+int psdproj_set_stream(psdproj_ctx *ctx, void *stream)
+{
+    if (!ctx) return PSDPROJ_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return PSDPROJ_OK;
+}
+
+int psdproj_destroy(psdproj_ctx *ctx)
+{
+    if (!ctx) return PSDPROJ_OK;
+    device_guard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_workspace(ctx->ws);
+    if (ctx->timing.created)
+        for (int i = 0; i < 2 * PSD_MAX_TIMED; ++i) cudaEventDestroy(ctx->timing.ev[i]);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_misc) cudaFree(ctx->d_misc);
+    if (ctx->d_misc_f) cudaFree(ctx->d_misc_f);
+    if (ctx->dA_stage) cudaFree(ctx->dA_stage);
+    if (ctx->dP_stage) cudaFree(ctx->dP_stage);
+    if (ctx->dW_stage) cudaFree(ctx->dW_stage);
+    delete ctx;
+    return PSDPROJ_OK;
+}
+
+int psdproj_sync_status(psdproj_ctx *ctx)
+{
+    if (!ctx) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int st = 0;
+    e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (st) cudaMemset(ctx->d_status, 0, sizeof(int));
+    return st;
+}
+
+const char *psdproj_status_string(int s)
+{
+    switch (s) {
+    case PSDPROJ_OK: return "PSDPROJ_OK";
+    case PSDPROJ_EINVAL: return "PSDPROJ_EINVAL: invalid argument";
+    case PSDPROJ_ENOMEM: return "PSDPROJ_ENOMEM: device allocation failed";
+    case PSDPROJ_ENOTFINITE: return "PSDPROJ_ENOTFINITE: non-finite value";
+    case PSDPROJ_ENOCONV: return "PSDPROJ_ENOCONV: eigensolver did not converge";
+    case PSDPROJ_ETIMEOUT: return "PSDPROJ_ETIMEOUT: device wait gave up";
+    case PSDPROJ_ECUDA: return "PSDPROJ_ECUDA: CUDA error";
+    case PSDPROJ_ENOTSUP: return "PSDPROJ_ENOTSUP: unsupported option";
+    default: return "PSDPROJ: unknown status";
+    }
+}
+
+size_t psdproj_workspace_bytes(const psdproj_ctx *ctx) { return ctx ? ctx->ws.bytes : 0; }
+
+int psdproj_timing_enable(psdproj_ctx *ctx, int on)
+{
+    if (!ctx) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    psd_timing &t = ctx->timing;
+    if (on && !t.created) {
+        for (int i = 0; i < 2 * PSD_MAX_TIMED; ++i) PSD_CK(cudaEventCreate(&t.ev[i]));
+        t.created = true;
+    }
+    t.on = on ? 1 : 0;
+    return PSDPROJ_OK;
+}
+
+int psdproj_timing_read(psdproj_ctx *ctx, double *ms, int *count, int nkinds)
+{
+    if (!ctx || nkinds < 0 || nkinds > PSDPROJ_NSTAGES) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    PSD_CK(cudaStreamSynchronize(ctx->stream));
+    psd_timing &t = ctx->timing;
+    for (int i = 0; i < t.n; ++i) {
+        float e = 0.0f;
+        PSD_CK(cudaEventElapsedTime(&e, t.ev[2 * i], t.ev[2 * i + 1]));
+        const int k = t.kind[i];
+        if (k < nkinds) {
+            if (ms) ms[k] += e;
+            if (count) count[k] += 1;
+        }
+    }
+    t.n = 0;
+    return PSDPROJ_OK;
+}
+
+uint64_t psdproj_kernel_launches(void) { return g_launches.load(); }
+
+int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int k, int p, int q,
+                 uint64_t seed, float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
+                 const psdproj_opts *opts)
+{
+    return run_projection(ctx, dA, n, lda, k, p, q, seed, false, 0.0, nullptr, nullptr, dP, ldp, dW,
+                          ldw, d_rank, opts);
+}
+
+int psdproj_alg2(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int k, int p, int q,
+                 uint64_t seed, double alpha_in, double *d_alpha_out, int *d_info, float *dP,
+                 int64_t ldp, float *dW, int64_t ldw, int *d_rank, const psdproj_opts *opts)
+{
+    return run_projection(ctx, dA, n, lda, k, p, q, seed, true, alpha_in, d_alpha_out, d_info, dP,
+                          ldp, dW, ldw, d_rank, opts);
+}
+
+int psdproj_alg1_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda, int k, int p,
+                      int q, uint64_t seed, float *hP, int64_t ldp, float *hW, int64_t ldw,
+                      int *h_rank, const psdproj_opts *opts)
+{
+    return run_host(ctx, hA, n, lda, k, p, q, seed, false, 0.0, nullptr, hP, ldp, hW, ldw, h_rank,
+                    opts);
+}
+
+int psdproj_alg2_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda, int k, int p,
+                      int q, uint64_t seed, double alpha_in, double *h_alpha_out, float *hP,
+                      int64_t ldp, float *hW, int64_t ldw, int *h_rank, const psdproj_opts *opts)
+{
+    return run_host(ctx, hA, n, lda, k, p, q, seed, true, alpha_in, h_alpha_out, hP, ldp, hW, ldw,
+                    h_rank, opts);
+}
+
+int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream, int64_t n, int m,
+                     float *dX, int64_t ldx)
+{
+    if (!ctx || !dX || n < 1 || m < 1 || ldx < n) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    PSD_KL(launch_gaussian(ctx->stream, seed, stream, n, m, m, n, dX, ldx), 1);
+    return PSDPROJ_OK;
+}
+
+int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, const float *dX,
+                     int64_t ldx, int m, const double *d_shift, float *dY, int64_t ldy, int prec)
+{
+    if (!ctx || !dA || !dX || !dY || n < 1 || m < 1 || lda < n || ldx < n || ldy < n)
+        return PSDPROJ_EINVAL;
+    if (prec < PSDPROJ_PREC_FP32 || prec > PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
+    if (prec != PSDPROJ_PREC_FP32 && m > PSD_MAX_M) return PSDPROJ_ENOTSUP;
+    device_guard g(ctx->device);
+    if (prec != PSDPROJ_PREC_FP32) PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    return sym_pass(ctx, dA, n, lda, dX, ldx, m, d_shift, dY, ldy, prec);
+}
+
+int psdproj_cholqr2(psdproj_ctx *ctx, const float *dY, int64_t n, int64_t ldy, int m, float *dQ,
+                    int64_t ldq, int *d_qrank)
+{
+    if (!ctx || !dY || !dQ || n < 1 || m < 1 || m > PSD_MAX_M || ldy < n || ldq < n)
+        return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    return cholqr2(ctx, dY, ldy, n, m, dQ, ldq, d_qrank);
+}
+
+int psdproj_core(psdproj_ctx *ctx, const float *dX, int64_t ldx, const float *dZ, int64_t ldz,
+                 int64_t n, int m, double *dC)
+{
+    if (!ctx || !dX || !dZ || !dC || n < 1 || m < 1 || m > PSD_MAX_M || ldx < n || ldz < n)
+        return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    stage_scope st(ctx, PSDPROJ_STAGE_CORE);
+    PSD_KL(launch_gram(ctx->stream, dX, ldx, dZ, ldz, n, m, ctx->ws.gpart, dC, 2), 2);
+    return PSDPROJ_OK;
+}
+
+int psdproj_eig(psdproj_ctx *ctx, const double *dC, int m, float *dV, double *dd)
+{
+    if (!ctx || !dC || !dV || !dd || m < 1 || m > PSD_MAX_M) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    PSD_TRY(psd_ensure_workspace(ctx, 1, m));
+    stage_scope st(ctx, PSDPROJ_STAGE_EIG);
+    PSD_KL(launch_eig(ctx->stream, dC, m, dV, dd, ctx->ws.eigscr, ctx->d_status), 1);
+    return PSDPROJ_OK;
+}
+
+int psdproj_factor(psdproj_ctx *ctx, const float *dQ, int64_t ldq, int64_t n, int m,
+                   const float *dV, const double *dd, float *dW, int64_t ldw, int *d_rank)
+{
+    if (!ctx || !dQ || !dV || !dd || !dW || n < 1 || m < 1 || m > PSD_MAX_M || ldq < n || ldw < n)
+        return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    psd_workspace &ws = ctx->ws;
+    int *rk = ws.ints + IN_RANK;
+    stage_scope st(ctx, PSDPROJ_STAGE_FACTOR);
+    PSD_KL(launch_factor_prep(ctx->stream, dV, dd, m, ws.M, rk), 1);
+    PSD_KL(launch_tall_small(ctx->stream, dQ, ldq, n, m, ws.M, m, nullptr, rk, dW, ldw), 1);
+    if (d_rank)
+        PSD_CK(cudaMemcpyAsync(d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
+    return PSDPROJ_OK;
+}
+
+int psdproj_syrk(psdproj_ctx *ctx, const float *dW, int64_t ldw, int64_t n, int m,
+                 const int *d_rank, float *dP, int64_t ldp, int out_mode, int prec)
+{
+    if (!ctx || !dW || !dP || n < 1 || m < 1 || ldw < n || ldp < n) return PSDPROJ_EINVAL;
+    if (out_mode != PSDPROJ_OUT_FULL && out_mode != PSDPROJ_OUT_UPPER) return PSDPROJ_EINVAL;
+    if (prec != PSDPROJ_PREC_FP32 && prec != PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    const int upper = out_mode == PSDPROJ_OUT_UPPER;
+    if (prec == PSDPROJ_PREC_FP32) {
+        stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
+        PSD_KL(launch_syrk_simt(ctx->stream, dW, ldw, n, m, d_rank, dP, ldp, upper), 1);
+        return PSDPROJ_OK;
+    }
+    if (m > PSD_MAX_M) return PSDPROJ_ENOTSUP;
+    PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
+    PSD_KL(launch_syrk_tc(ctx->stream, ctx->sm_count, dW, ldw, n, m, d_rank, dP, ldp, upper,
+                          ctx->ws.Xhi, ctx->ws.Xlo, ctx->ws.ld, ctx->d_status), 2);
+    return PSDPROJ_OK;
+}
+
+int psdproj_min_eig(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int N,
+                    uint64_t seed, double *d_alpha, double *d_sigma1, double *d_sigma2)
+{
+    if (!ctx || !dA || !d_alpha || n < 1 || lda < n || N < 0) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    PSD_TRY(psd_ensure_workspace(ctx, n, 1));
+    psd_workspace &ws = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    double *sc = ws.scal;
+    stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
+    PSD_KL(launch_power_iteration(s, dA, n, lda, N, seed, 3u, nullptr, ws.pv0, ws.pv1, sc,
+                                  ws.counter, sc + SC_SIGMA1), N + 3);
+    PSD_KL(launch_power_iteration(s, dA, n, lda, N, seed, 4u, sc + SC_SIGMA1, ws.pv0, ws.pv1, sc,
+                                  ws.counter, sc + SC_SIGMA2), N + 3);
+    PSD_KL(launch_alpha_finish(s, sc + SC_SIGMA1, sc + SC_SIGMA2, 0.0, d_alpha, sc + SC_SHIFT,
+                               ws.ints + IN_INFO), 1);
+    if (d_sigma1)
+        PSD_CK(cudaMemcpyAsync(d_sigma1, sc + SC_SIGMA1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (d_sigma2)
+        PSD_CK(cudaMemcpyAsync(d_sigma2, sc + SC_SIGMA2, sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return PSDPROJ_OK;
+}
+
+}  // extern "C"

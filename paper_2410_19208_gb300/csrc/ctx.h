@@ -1,0 +1,140 @@
+// Internal declarations of the psdproj CUDA library (sm_103a).
+// The context, its workspace layout and the kernel launchers used by capi.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/psdproj.h"
+
+// Device status word: the first error code recorded wins.
+__device__ __forceinline__ void psd_set_status(int *st, int code)
+{
+    if (st) atomicCAS(st, 0, code);
+}
+
+static inline int64_t psd_round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// Tall-matrix leading dimension used for context-owned buffers: rows padded
+// to a multiple of 128 (TMA strides stay 16-byte aligned, tiles never read
+// past the allocation).
+static inline int64_t psd_ld(int64_t n) { return psd_round_up(n, 128); }
+// Sketch width padded to a multiple of 16 (UMMA N granularity at M = 128).
+static inline int psd_lpad(int m) { return (int)psd_round_up(m, 16); }
+
+constexpr int PSD_GRAM_CHUNK = 64;    // rows per Gram partial
+constexpr int PSD_MAX_M = 256;        // largest sketch width
+
+struct psd_workspace {
+    int64_t n = 0;      // rows the tall buffers hold
+    int lpad = 0;       // columns they hold
+    int64_t ld = 0;     // their leading dimension
+    void *base = nullptr;
+    size_t bytes = 0;
+    // tall FP32 buffers, ld x lpad each
+    float *Om = nullptr, *Y = nullptr, *Q = nullptr, *T = nullptr, *W = nullptr;
+    // bf16 hi / lo images of a tall buffer (tensor-core passes)
+    uint16_t *Xhi = nullptr, *Xlo = nullptr;
+    // Gram partials: nchunk x lpad x lpad floats
+    float *gpart = nullptr;
+    // small matrices
+    double *G = nullptr, *R = nullptr, *C = nullptr, *d = nullptr;
+    float *Rinv = nullptr, *V = nullptr, *M = nullptr, *eigscr = nullptr;
+    int *dead = nullptr;
+    // power iteration: two n-vectors (ld floats) and scalars
+    float *pv0 = nullptr, *pv1 = nullptr;
+    double *scal = nullptr;     // 16 doubles
+    unsigned *counter = nullptr; // 16 counters
+    int *ints = nullptr;         // 16 ints (ranks, info)
+};
+
+constexpr int PSD_MAX_TIMED = 4096;
+
+struct psd_timing {
+    int on = 0;
+    int n = 0;                       // stages recorded since the last read
+    bool created = false;
+    cudaEvent_t ev[2 * PSD_MAX_TIMED];
+    int kind[PSD_MAX_TIMED];
+};
+
+struct psdproj_ctx {
+    int device = 0;
+    psd_timing timing;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int *d_status = nullptr;     // device status word
+    psd_workspace ws;
+    // host-API staging buffers
+    float *dA_stage = nullptr;  size_t dA_stage_bytes = 0;
+    float *dP_stage = nullptr;  size_t dP_stage_bytes = 0;
+    float *dW_stage = nullptr;  size_t dW_stage_bytes = 0;
+    int *d_misc = nullptr;       // rank / info for host calls
+    double *d_misc_f = nullptr;  // alpha for host calls
+};
+
+// Make sure the workspace holds n rows x m columns; may synchronise the
+// stream and reallocate.  Returns a PSDPROJ_* status.
+int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m);
+
+// ---- launchers (all asynchronous on `s`; return cudaGetLastError) -------
+cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, uint32_t stream_id,
+                            int64_t n, int m, int mpad, int64_t rows_pad,
+                            float *X, int64_t ldx);
+
+cudaError_t launch_sym_pass_simt(cudaStream_t s, const float *A, int64_t n, int64_t lda,
+                                 const float *X, int64_t ldx, int m, const double *d_shift,
+                                 float *Y, int64_t ldy);
+
+// Tensor-core symmetric pass; returns cudaErrorNotSupported when the
+// configuration is outside what the kernel handles.
+cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const float *A, int64_t n,
+                               int64_t lda, const float *X, int64_t ldx, int m,
+                               const double *d_shift, float *Y, int64_t ldy, int prec,
+                               uint16_t *Xhi, uint16_t *Xlo, int64_t ldh, int *d_status);
+
+// Gram partials + FP64 reduction: G = X^T Z (sym = 1: X == Z, symmetric).
+cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
+                        int64_t ldz, int64_t n, int m, float *gpart, double *G,
+                        int symmetrize);
+
+cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, double *R, float *Rinv,
+                            int *dead, int *d_qrank, double tau, int *d_status);
+
+// Y (n x m) times a small m x c matrix B (column-major, ld = m) -> Z (n x c).
+// colmask (may be NULL): columns j with colmask[j] != 0 are written as zero.
+// d_cols (may be NULL): device int; only the first *d_cols columns of B are
+// used and the rest of Z is written as zero.
+cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64_t n, int m,
+                              const float *B, int c, const int *colmask, const int *d_cols,
+                              float *Z, int64_t ldz);
+
+// scratch: 2 (m+2)^2 floats of device memory (used when m is too large for
+// shared memory)
+cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double *d,
+                       float *scratch, int *d_status);
+
+cudaError_t launch_factor_prep(cudaStream_t s, const float *V, const double *d, int m,
+                               float *M, int *d_rank);
+
+cudaError_t launch_syrk_simt(cudaStream_t s, const float *W, int64_t ldw, int64_t n, int m,
+                             const int *d_rank, float *P, int64_t ldp, int upper_only);
+
+cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t ldw,
+                           int64_t n, int m, const int *d_rank, float *P, int64_t ldp,
+                           int upper_only, uint16_t *Whi, uint16_t *Wlo, int64_t ldh,
+                           int *d_status);
+
+// Power iteration (Alg. 4) with optional shift taken from *d_shift_in
+// (negated sigma); writes sigma to *d_sigma.
+cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, int64_t lda,
+                                   int N, uint64_t seed, uint32_t stream_id,
+                                   const double *d_shift_neg, float *v0, float *v1,
+                                   double *scal, unsigned *counter, double *d_sigma);
+
+cudaError_t launch_alpha_finish(cudaStream_t s, const double *d_s1, const double *d_s2,
+                                double alpha_in, double *d_alpha, double *d_shift,
+                                int *d_info);
+
+cudaError_t launch_copy_tall(cudaStream_t s, const float *X, int64_t ldx, int64_t n, int m,
+                             float *Y, int64_t ldy);

@@ -1,0 +1,127 @@
+// Gram products of the small-matrix steps:
+//   G = Y^T Y           (CholeskyQR2, the QR 'econ' of Alg. 1)
+//   C = (Q^T Z + Z^T Q)/2 with Z = A Q  (the projected core Q^T A Q of Alg. 2)
+// Each thread block forms the FP32 partial product of one chunk of 64 rows
+// (8 x 8 register micro-tiles); a second kernel sums the chunk partials in
+// FP64 in a fixed order (deterministic, no atomics).
+#include "ctx.h"
+
+namespace {
+
+constexpr int CH = 64;    // rows per chunk (PSD_GRAM_CHUNK)
+constexpr int RS = 32;    // rows staged in shared memory at a time
+constexpr int NT = 256;
+
+__global__ void __launch_bounds__(NT)
+gram_partial_kernel(const float *__restrict__ X, int64_t ldx, const float *__restrict__ Z,
+                    int64_t ldz, int64_t n, int m, int mp, int upper_only,
+                    float *__restrict__ gpart)
+{
+    extern __shared__ float sm[];
+    float *Xs = sm;              // RS x mp
+    float *Zs = sm + RS * mp;    // RS x mp
+    const int64_t row0 = (int64_t)blockIdx.x * CH;
+    const int nbt = mp / 8;      // micro-tiles per side
+    const int ntiles = upper_only ? nbt * (nbt + 1) / 2 : nbt * nbt;
+    float *out = gpart + (int64_t)blockIdx.x * mp * mp;
+    const bool same = (X == Z) && (ldx == ldz);
+
+    for (int pass = 0; pass * NT < ntiles; ++pass) {
+        const int tile = pass * NT + threadIdx.x;
+        int bi = 0, bj = 0;
+        const bool active = tile < ntiles;
+        if (active) {
+            if (upper_only) {
+                // tile -> (bi <= bj), row-major over the upper triangle
+                int t = tile;
+                bi = 0;
+                while (t >= nbt - bi) { t -= nbt - bi; ++bi; }
+                bj = bi + t;
+            } else {
+                bi = tile / nbt;
+                bj = tile % nbt;
+            }
+        }
+        float acc[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+        for (int rs = 0; rs < CH; rs += RS) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < RS * mp; e += NT) {
+                const int a = e / RS, k = e % RS;
+                const int64_t r = row0 + rs + k;
+                const bool ok = r < n && a < m;
+                Xs[k * mp + a] = ok ? X[(int64_t)a * ldx + r] : 0.0f;
+                if (!same) Zs[k * mp + a] = ok ? Z[(int64_t)a * ldz + r] : 0.0f;
+            }
+            __syncthreads();
+            const float *Zsrc = same ? Xs : Zs;
+            if (active) {
+#pragma unroll 2
+                for (int k = 0; k < RS; ++k) {
+                    float x[8], z[8];
+                    const float4 *xp = reinterpret_cast<const float4 *>(Xs + k * mp + 8 * bi);
+                    const float4 *zp = reinterpret_cast<const float4 *>(Zsrc + k * mp + 8 * bj);
+                    float4 x0 = xp[0], x1 = xp[1], z0 = zp[0], z1 = zp[1];
+                    x[0] = x0.x; x[1] = x0.y; x[2] = x0.z; x[3] = x0.w;
+                    x[4] = x1.x; x[5] = x1.y; x[6] = x1.z; x[7] = x1.w;
+                    z[0] = z0.x; z[1] = z0.y; z[2] = z0.z; z[3] = z0.w;
+                    z[4] = z1.x; z[5] = z1.y; z[6] = z1.z; z[7] = z1.w;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(x[i], z[j], acc[i][j]);
+                }
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) out[(8 * bi + i) * mp + 8 * bj + j] = acc[i][j];
+        }
+    }
+}
+
+// G[a + b*m] = sum over chunks of gpart (FP64); mode 0: full product,
+// mode 1: upper-only symmetric Gram (mirror), mode 2: symmetrise (S+S^T)/2.
+__global__ void gram_reduce_kernel(const float *__restrict__ gpart, int nchunk, int m, int mp,
+                                   int mode, double *__restrict__ G)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int a = e % m, b = e / m;
+    int ia = a, ib = b;
+    if (mode == 1 && ia > ib) { ia = b; ib = a; }
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += (double)gpart[(int64_t)c * mp * mp + ia * mp + ib];
+    if (mode == 2) {
+        double t = 0.0;
+        for (int c = 0; c < nchunk; ++c) t += (double)gpart[(int64_t)c * mp * mp + ib * mp + ia];
+        s = 0.5 * (s + t);
+    }
+    G[(int64_t)b * m + a] = s;
+}
+
+}  // namespace
+
+// symmetrize: 0 = G = X^T Z as is; 1 = X == Z (upper computed, mirrored);
+// 2 = (X^T Z + Z^T X)/2.
+cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
+                        int64_t ldz, int64_t n, int m, float *gpart, double *G, int symmetrize)
+{
+    const int mp = (int)psd_round_up(m, 8);
+    const int nchunk = (int)((n + CH - 1) / CH);
+    const size_t smem = sizeof(float) * 2 * RS * (size_t)mp;
+    cudaError_t e = cudaFuncSetAttribute(gram_partial_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    gram_partial_kernel<<<nchunk, NT, smem, s>>>(X, ldx, Z, ldz, n, m, mp, symmetrize == 1,
+                                                 gpart);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, s>>>(gpart, nchunk, m, mp, symmetrize, G);
+    return cudaGetLastError();
+}

@@ -1,0 +1,63 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports
+every entry point include/psdproj.h declares; host-side behaviour that needs
+no GPU (defaults, status strings, argument rejection before any launch)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2410_19208_gb300 import build as b
+    b.build()
+    import paper_2410_19208_gb300 as ps
+    return ps.lib()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(psdproj_\w+)\s*\(", txt))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 19
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_defaults_and_status_strings(lib):
+    import paper_2410_19208_gb300 as ps
+    o = ps.Opts()
+    lib.psdproj_default_opts(ctypes.byref(o))
+    assert (o.prec, o.syrk_prec, o.N, o.out_mode) == (0, 0, 10, 0)
+    for code in range(8):
+        s = lib.psdproj_status_string(code)
+        assert s.startswith(b"PSDPROJ")
+    assert b"unknown" in lib.psdproj_status_string(99)
+
+
+def test_rejects_bad_arguments_without_a_gpu(lib):
+    # NULL contexts and out-of-range sizes fail in the argument checks,
+    # before any CUDA call
+    assert lib.psdproj_alg1(None, None, 10, 10, 2, 2, 0, 1, None, 10, None, 10, None, None) == 1
+    assert lib.psdproj_destroy(None) == 0
+    assert lib.psdproj_sync_status(None) == 1
+    assert lib.psdproj_create(None, 0, None) == 1
+    h = ctypes.c_void_p()
+    # device index out of range (no device here, or index too large)
+    assert lib.psdproj_create(ctypes.byref(h), 1 << 20, None) != 0
+
+
+def test_built_for_sm_103a_only():
+    src = open(os.path.join(ROOT, "paper_2410_19208_gb300", "build.py")).read()
+    assert "arch=compute_103a,code=sm_103a" in src

@@ -1,0 +1,223 @@
+"""End-to-end parity of psdproj_alg1 / psdproj_alg2 (C ABI) against the oracle.
+
+The FP32 form must match the oracle's randomized output to a relative
+Frobenius error <= 1e-4 (the bound the build targets for the plain FP32
+form).  Inputs: synth_inputs recipes; expected values: oracle/ only.
+"""
+import numpy as np
+import pytest
+
+import synth_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2410_19208_gb300 as ps  # noqa: E402
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ps.Context(0)
+    yield c
+    c.close()
+
+
+def _A(kind, n, **kw):
+    Vr, lam = si.make_problem(kind, n, **kw)
+    return Vr, lam, si.form_A_numpy(Vr, lam).astype(np.float32)
+
+
+def _run(ctx, A32, k, p, q, seed, alg=1, opts=None, alpha_in=0.0, poison=False):
+    n = A32.shape[0]
+    A = A32.copy()
+    if poison:
+        A[np.tril_indices(n, -1)] = np.nan
+    Ad = torch.from_numpy(A).cuda()
+    P = torch.full((n, n), float("nan"), device="cuda")
+    W = ps.tall_empty(n, k + p)
+    rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+    if alg == 1:
+        ctx.alg1(Ad, k, p, q, seed, P=P, W=W, rank=rank, opts=opts)
+    else:
+        alpha = torch.zeros(1, dtype=torch.float64, device="cuda")
+        info = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        ctx.alg2(Ad, k, p, q, seed, alpha_in=alpha_in, alpha_out=alpha, info=info, P=P, W=W,
+                 rank=rank, opts=opts)
+    st = ctx.sync_status()
+    assert st == 0, ps.STATUS.get(st)
+    out = dict(P=P.cpu().numpy().astype(np.float64), W=W.cpu().numpy().astype(np.float64),
+               rank=int(rank.item()))
+    if alg == 2:
+        out["alpha"] = alpha.item()
+        out["info"] = int(info.item())
+    return out
+
+
+def _rel(P, Pref):
+    return np.linalg.norm(P - Pref) / max(np.linalg.norm(Pref), 1e-300)
+
+
+CASES = [
+    ("small", 1000, 40, 10, 0, 1),     # the n = 1000 recipe, Omega from seed 1
+    ("small", 257, 20, 6, 1, 2),
+    ("small", 300, 30, 5, 2, 3),
+    ("decay", 4099, 100, 10, 1, 1),
+    ("decay", 1500, 50, 10, 0, 4),
+]
+
+
+@pytest.mark.parametrize("kind,n,k,p,q,seed", CASES)
+def test_alg1_matches_oracle(ctx, oracle_lib, kind, n, k, p, q, seed):
+    Vr, lam, A32 = _A(kind, n)
+    got = _run(ctx, A32, k, p, q, seed, alg=1)
+    ref = oracle_lib.alg1(A32.astype(np.float64), k, p, q, seed)
+    Pref = ref["W"] @ ref["W"].T
+    assert _rel(got["P"], Pref) <= TOL
+    assert got["rank"] == ref["rplus"]
+    # the returned factor reproduces P
+    assert _rel(got["W"] @ got["W"].T, got["P"]) <= 1e-5
+
+
+@pytest.mark.parametrize("kind,n,k,p,q,seed", CASES)
+def test_alg2_matches_oracle(ctx, oracle_lib, kind, n, k, p, q, seed):
+    Vr, lam, A32 = _A(kind, n)
+    got = _run(ctx, A32, k, p, q, seed, alg=2)
+    ref = oracle_lib.alg2(A32.astype(np.float64), k, p, q, seed, N=10)
+    assert got["info"] == 0 and ref["degraded"] == 0
+    assert abs(got["alpha"] - ref["alpha"]) <= 1e-5 * abs(ref["alpha"]) + 1e-6
+    Pref = ref["W_red"] @ ref["W_red"].T
+    assert _rel(got["P"], Pref) <= TOL
+    # Lemma 4: the oracle's literal last step gives the same projection
+    Plit = ref["W_lit"] @ ref["W_lit"].T
+    assert _rel(got["P"], Plit) <= TOL
+
+
+def test_alg2_with_given_alpha(ctx, oracle_lib):
+    Vr, lam, A32 = _A("decay", 800)
+    alpha = float(-lam.min())
+    got = _run(ctx, A32, 40, 10, 1, 5, alg=2, alpha_in=alpha)
+    ref = oracle_lib.alg2(A32.astype(np.float64), 40, 10, 1, 5, alpha=alpha)
+    assert got["alpha"] == alpha
+    assert _rel(got["P"], ref["W_red"] @ ref["W_red"].T) <= TOL
+
+
+def test_exact_recovery_low_rank(ctx, oracle_lib):
+    n, k, p = 2000, 12, 6
+    Vr, lam = si.lowrank_problem(n, [9.0, 7.0, 5.0, -3.0, 2.0, -6.0, 1.0, 0.5, -0.25, 4.0], seed=4)
+    A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
+    Xp = oracle_lib.closed_form_proj(Vr, lam)
+    for alg in (1, 2):
+        got = _run(ctx, A32, k, p, 1, 7, alg=alg)
+        assert _rel(got["P"], Xp) <= 2e-5
+        assert got["rank"] == int((lam > 0).sum()) == 7
+
+
+def test_lower_triangle_is_never_read(ctx):
+    Vr, lam, A32 = _A("small", 700)
+    a = _run(ctx, A32, 30, 8, 1, 3, alg=1)
+    b = _run(ctx, A32, 30, 8, 1, 3, alg=1, poison=True)
+    assert np.all(np.isfinite(b["P"]))
+    assert _rel(b["P"], a["P"]) <= 1e-5
+    a2 = _run(ctx, A32, 30, 8, 1, 3, alg=2)
+    b2 = _run(ctx, A32, 30, 8, 1, 3, alg=2, poison=True)
+    assert np.all(np.isfinite(b2["P"]))
+    assert _rel(b2["P"], a2["P"]) <= 1e-5
+
+
+def test_output_modes_and_host_api(ctx):
+    Vr, lam, A32 = _A("small", 500)
+    k, p, q, seed = 25, 5, 1, 2
+    full = _run(ctx, A32, k, p, q, seed)
+    up = _run(ctx, A32, k, p, q, seed, opts=ps.make_opts(out_mode=ps.OUT_UPPER))
+    iu = np.triu_indices(500)
+    assert _rel(up["P"][iu], full["P"][iu]) <= 1e-5
+    assert np.all(np.isnan(up["P"][np.tril_indices(500, -1)]))
+    fac = _run(ctx, A32, k, p, q, seed, opts=ps.make_opts(out_mode=ps.OUT_FACTOR))
+    assert np.all(np.isnan(fac["P"]))
+    assert _rel(fac["W"] @ fac["W"].T, full["P"]) <= 1e-5
+    # host buffers
+    Ah = torch.from_numpy(A32).pin_memory()
+    Ph = torch.empty(500, 500).pin_memory()
+    rk = ctx.alg1_host(Ah, k, p, q, seed, P=Ph)
+    assert rk == full["rank"]
+    assert _rel(Ph.numpy().astype(np.float64), full["P"]) <= 1e-5
+    rk2, al = ctx.alg2_host(Ah, k, p, q, seed, P=Ph)
+    assert al > 0
+
+
+def test_edge_cases(ctx, oracle_lib):
+    # n = 1
+    A = np.array([[-2.0]], dtype=np.float32)
+    assert np.all(_run(ctx, A, 1, 0, 0, 1)["P"] == 0)
+    A = np.array([[3.0]], dtype=np.float32)
+    assert abs(_run(ctx, A, 1, 0, 0, 1)["P"][0, 0] - 3.0) < 1e-6
+    # sketch as wide as the matrix: exact projection
+    n = 48
+    Vr, lam = si.householder_vectors(n, 2, 1), np.linspace(-3, 4, n)
+    A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
+    got = _run(ctx, A32, 40, 8, 0, 1)
+    Xp = oracle_lib.closed_form_proj(Vr, lam)
+    assert _rel(got["P"], Xp) <= 2e-5
+    # A = 0: P = 0; Alg. 2 reports the degraded alpha
+    Z = np.zeros((200, 200), dtype=np.float32)
+    g1 = _run(ctx, Z, 10, 4, 1, 1)
+    assert np.all(g1["P"] == 0) and g1["rank"] == 0
+    g2 = _run(ctx, Z, 10, 4, 1, 1, alg=2)
+    assert np.all(g2["P"] == 0) and g2["info"] == 1
+    # negative definite: P = 0
+    N = -np.eye(100, dtype=np.float32)
+    assert np.abs(_run(ctx, N, 10, 5, 1, 1)["P"]).max() == 0
+
+
+def test_invalid_arguments(ctx):
+    A = torch.zeros(10, 10, device="cuda")
+    P = torch.zeros(10, 10, device="cuda")
+    for (k, p, q) in [(0, 2, 0), (8, 3, 0), (2, 1, -1), (2, 1, 17)]:
+        with pytest.raises(ps.PsdprojError) as ei:
+            ctx.alg1(A, k, p, q, 1, P=P)
+        assert ei.value.code == 1
+    with pytest.raises(ps.PsdprojError):
+        ctx.alg1(A, 2, 1, 0, 1, P=None)  # P required unless factor mode
+    with pytest.raises(ps.PsdprojError):
+        ctx.alg1(A, 2, 1, 0, 1, P=P, opts=ps.make_opts(prec=9))
+
+
+@pytest.mark.parametrize("alg", [1, 2])
+def test_full_size_n20000_against_oracle(ctx, oracle_lib, alg):
+    """n = 20000, k = 100, p = 10, q = 1 (the benchmark workload): the whole
+    factor is compared in Gram form, plus sampled entries of the returned P."""
+    n, k, p, q, seed = 20000, 100, 10, 1, 1
+    Vr, lam = si.make_problem("decay", n)
+    A = si.form_A_torch(Vr, lam, "cuda")
+    Pd = torch.empty(n, n, device="cuda")
+    Wd = ps.tall_empty(n, k + p)
+    rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+    if alg == 1:
+        ctx.alg1(A, k, p, q, seed, P=Pd, W=Wd, rank=rank)
+    else:
+        ctx.alg2(A, k, p, q, seed, P=Pd, W=Wd, rank=rank)
+    assert ctx.sync_status() == 0
+    W = Wd.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(0)
+    ii = rng.integers(0, n, 4000)
+    jj = rng.integers(0, n, 4000)
+    Ps = Pd[torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].cpu().numpy().astype(np.float64)
+    A64 = A.cpu().numpy().astype(np.float64)
+    del Pd, A
+    if alg == 1:
+        Wr = oracle_lib.alg1(A64, k, p, q, seed)["W"]
+    else:
+        Wr = oracle_lib.alg2(A64, k, p, q, seed, N=10)["W_red"]
+    del A64
+    rel = np.sqrt(max(oracle_lib.factor_dist2(W, Wr), 0.0) / oracle_lib.factor_norm2(Wr))
+    assert rel <= TOL
+    Pr = np.einsum("ij,ij->i", Wr[ii], Wr[jj])
+    scale = np.sqrt(np.einsum("ij,ij->i", Wr[ii], Wr[ii]) * np.einsum("ij,ij->i", Wr[jj], Wr[jj]))
+    assert np.all(np.abs(Ps - Pr) <= TOL * scale + 1e-7)
+    # the returned P matches the returned factor on the samples
+    assert np.all(np.abs(Ps - np.einsum("ij,ij->i", W[ii], W[jj])) <= 1e-5 * scale + 1e-7)

@@ -1,0 +1,246 @@
+"""Per-step parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Every input comes from synth_inputs / numpy generators; every expected value
+from oracle/ (or, for library-pinned pieces, numpy / LAPACK).  Tolerances are
+derived from FP32 arithmetic: an FP32 dot product of length n with FMA has
+error <= gamma_n sum |a_i x_i|; the tests allow c * sqrt(n) * 2^-24 of that
+bound (typical, not worst-case, rounding growth) with a margin.
+"""
+import numpy as np
+import pytest
+
+import synth_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2410_19208_gb300 as ps  # noqa: E402
+
+EPS32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ps.Context(0)
+    yield c
+    c.close()
+
+
+def _tall_from_np(X, ld=None):
+    n, m = X.shape
+    T = ps.tall_empty(n, m, "cuda", ld=ld)
+    T.copy_(torch.from_numpy(np.asarray(X, dtype=np.float32)))
+    return T
+
+
+def _np(T):
+    return T.detach().cpu().numpy().astype(np.float64)
+
+
+def _sym_A(n, seed, poison=False):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, n)).astype(np.float32)
+    A = np.triu(X) + np.triu(X, 1).T
+    if poison:
+        A = A.copy()
+        A[np.tril_indices(n, -1)] = np.nan
+    return A
+
+
+@pytest.mark.parametrize("n,m,stream", [(1000, 50, 0), (4099, 112, 0), (777, 1, 3), (5, 3, 4)])
+def test_gaussian_matches_oracle(ctx, oracle_lib, n, m, stream):
+    X = ps.tall_empty(n, m, "cuda", ld=n + 3)
+    ctx.gaussian(7, stream, X)
+    assert ctx.sync_status() == 0
+    ref = oracle_lib.omega(7, n, m, stream)
+    got = _np(X)
+    assert np.all(np.abs(got - ref) <= 1e-6 * np.maximum(1.0, np.abs(ref)))
+
+
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 127, 257, 1000, 4099])
+@pytest.mark.parametrize("m", [1, 7, 50, 112])
+def test_sym_pass_fp32(ctx, oracle_lib, n, m):
+    if m > 50 and n in (1, 2):
+        return
+    A = _sym_A(n, seed=n * 7 + m)
+    rng = np.random.default_rng(m)
+    X = rng.standard_normal((n, m)).astype(np.float32)
+    Xd = _tall_from_np(X, ld=n + 5)
+    Y = ps.tall_empty(n, m, "cuda", ld=n + 1)
+    Ad = torch.from_numpy(A).cuda()
+    ctx.sym_pass(Ad, Xd, Y)
+    assert ctx.sync_status() == 0
+    A64 = A.astype(np.float64)
+    ref = oracle_lib.sym_mul(A64, X.astype(np.float64))
+    bound = np.abs(A64) @ np.abs(X.astype(np.float64))
+    tol = 8.0 * np.sqrt(n) * EPS32 * bound + 1e-30
+    assert np.all(np.abs(_np(Y) - ref) <= tol)
+
+
+def test_sym_pass_reads_upper_only_and_shift(ctx, oracle_lib):
+    n, m = 1000, 40
+    A = _sym_A(n, seed=3)
+    Ap = _sym_A(n, seed=3, poison=True)
+    X = np.random.default_rng(4).standard_normal((n, m)).astype(np.float32)
+    Xd = _tall_from_np(X)
+    Y1 = ps.tall_empty(n, m)
+    Y2 = ps.tall_empty(n, m)
+    shift = torch.tensor([2.5], dtype=torch.float64, device="cuda")
+    ctx.sym_pass(torch.from_numpy(A).cuda(), Xd, Y1, shift=shift)
+    ctx.sym_pass(torch.from_numpy(Ap).cuda(), Xd, Y2, shift=shift)
+    assert ctx.sync_status() == 0
+    y1, y2 = _np(Y1), _np(Y2)
+    assert np.all(np.isfinite(y2))
+    ref = oracle_lib.sym_mul(A.astype(np.float64), X.astype(np.float64), shift=2.5)
+    bound = np.abs(A.astype(np.float64)) @ np.abs(X.astype(np.float64)) + 2.5 * np.abs(X)
+    assert np.all(np.abs(y1 - ref) <= 8 * np.sqrt(n) * EPS32 * bound)
+    assert np.all(np.abs(y2 - ref) <= 8 * np.sqrt(n) * EPS32 * bound)
+
+
+def _cond_tall(n, m, cond, seed):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    Vt, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    s = np.logspace(0, -np.log10(cond), m)
+    return ((U * s) @ Vt).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,m,cond", [(1000, 50, 10.0), (4099, 112, 100.0), (300, 7, 1e3),
+                                      (129, 128, 10.0), (600, 200, 10.0)])
+def test_cholqr2_orthonormal_same_range(ctx, oracle_lib, n, m, cond):
+    Y = _cond_tall(n, m, cond, seed=m)
+    Yd = _tall_from_np(Y)
+    Q = ps.tall_empty(n, m)
+    qr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.cholqr2(Yd, Q, qrank=qr)
+    assert ctx.sync_status() == 0
+    q = _np(Q)
+    assert int(qr.item()) == m
+    assert np.abs(q.T @ q - np.eye(m)).max() < 2e-5
+    Qo, r = oracle_lib.orth(Y.astype(np.float64))
+    assert r == m
+    # projector distance: same range (an FP32 Y of condition cond)
+    d = np.linalg.norm(q @ (q.T @ Qo) - Qo) / np.sqrt(m)
+    assert d < 50 * cond * EPS32 * np.sqrt(m)
+
+
+def test_cholqr2_dependent_columns(ctx, oracle_lib):
+    n, m = 500, 12
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((n, 8))
+    Y = np.concatenate([B, B[:, :4] @ rng.standard_normal((4, 4))], axis=1).astype(np.float32)
+    Yd = _tall_from_np(Y)
+    Q = ps.tall_empty(n, m)
+    qr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.cholqr2(Yd, Q, qrank=qr)
+    assert ctx.sync_status() == 0
+    q = _np(Q)
+    Qo, r = oracle_lib.orth(Y.astype(np.float64))
+    assert int(qr.item()) == r == 8
+    assert np.all(q[:, 8:] == 0)
+    live = q[:, :8]
+    assert np.abs(live.T @ live - np.eye(8)).max() < 2e-5
+    assert np.linalg.norm(live @ (live.T @ Qo[:, :8]) - Qo[:, :8]) < 1e-4
+
+
+def test_core_matches_oracle(ctx, oracle_lib):
+    n, m = 2000, 60
+    A = _sym_A(n, 5)
+    Q, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((n, m)))
+    Q = Q.astype(np.float32)
+    A64, Q64 = A.astype(np.float64), Q.astype(np.float64)
+    Z = oracle_lib.sym_mul(A64, Q64).astype(np.float32)   # Z from the oracle
+    C = torch.zeros(m, m, dtype=torch.float64, device="cuda")
+    ctx.core(_tall_from_np(Q), _tall_from_np(Z), C)
+    assert ctx.sync_status() == 0
+    ref = Q64.T @ Z.astype(np.float64)
+    ref = 0.5 * (ref + ref.T)
+    got = C.cpu().numpy().T  # column-major
+    bound = np.abs(Q64).T @ np.abs(Z.astype(np.float64))
+    assert np.all(np.abs(got - ref) <= 8 * np.sqrt(n) * EPS32 * bound)
+    assert np.array_equal(got, got.T)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 17, 60, 110, 112, 161, 210, 256])
+def test_eig_matches_lapack(ctx, m):
+    rng = np.random.default_rng(m)
+    X = rng.standard_normal((m, m))
+    C = (X + X.T) / 2
+    C[: m // 3, : m // 3] *= 10.0
+    Cd = torch.from_numpy(np.ascontiguousarray(C.T)).cuda()  # column-major
+    V = torch.zeros(m, m, dtype=torch.float32, device="cuda")
+    d = torch.zeros(m, dtype=torch.float64, device="cuda")
+    ctx.eig(Cd, V, d)
+    assert ctx.sync_status() == 0
+    dv = d.cpu().numpy()
+    Vv = V.cpu().numpy().T.astype(np.float64)  # column-major -> (row, col)
+    ref = np.linalg.eigvalsh(C)[::-1]
+    nrm = np.linalg.norm(C)
+    assert np.all(np.diff(dv) <= 0)
+    assert np.abs(dv - ref).max() <= 2e-6 * nrm
+    assert np.abs(Vv.T @ Vv - np.eye(m)).max() <= 2e-5
+    assert np.linalg.norm(Vv @ np.diag(dv) @ Vv.T - C) <= 5e-6 * nrm * np.sqrt(m)
+
+
+def test_eig_degenerate_inputs(ctx):
+    for C in [np.zeros((5, 5)), np.diag([3.0, 3.0, -1.0, 0.0]), np.eye(6) * 2.0]:
+        m = C.shape[0]
+        V = torch.zeros(m, m, dtype=torch.float32, device="cuda")
+        d = torch.zeros(m, dtype=torch.float64, device="cuda")
+        ctx.eig(torch.from_numpy(np.ascontiguousarray(C.T)).cuda(), V, d)
+        assert ctx.sync_status() == 0
+        assert np.allclose(d.cpu().numpy(), np.sort(np.diag(C))[::-1])
+        Vv = V.cpu().numpy().T
+        assert np.allclose(Vv.T @ Vv, np.eye(m), atol=1e-6)
+
+
+def test_factor_and_syrk(ctx):
+    n, m = 1500, 40
+    rng = np.random.default_rng(9)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, m)))
+    V, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    d = np.sort(rng.standard_normal(m))[::-1].copy()
+    d[5] = 0.0
+    Qd = _tall_from_np(Q)
+    Vd = torch.from_numpy(np.ascontiguousarray(V.T).astype(np.float32)).cuda()
+    dd = torch.from_numpy(d).cuda()
+    W = ps.tall_empty(n, m)
+    rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.factor(Qd, Vd, dd, W, rank=rank)
+    P = torch.full((n, n), float("nan"), device="cuda")
+    ctx.syrk(W, P, rank=rank)
+    Pu = torch.full((n, n), float("nan"), device="cuda")
+    ctx.syrk(W, Pu, rank=rank, out_mode=ps.OUT_UPPER)
+    assert ctx.sync_status() == 0
+    rp = int((d > 0).sum())
+    assert int(rank.item()) == rp
+    Q32, V32 = Q.astype(np.float32).astype(np.float64), V.astype(np.float32).astype(np.float64)
+    Wref = Q32 @ V32[:, :rp] * np.sqrt(d[:rp])
+    w = _np(W)
+    assert np.abs(w[:, :rp] - Wref).max() < 1e-5 * np.abs(Wref).max()
+    assert np.all(w[:, rp:] == 0)
+    Pref = w @ w.T
+    p = _np(P)
+    assert np.abs(p - Pref).max() <= 8 * np.sqrt(m) * EPS32 * (np.abs(w) @ np.abs(w).T).max()
+    pu = _np(Pu)
+    iu = np.triu_indices(n)
+    assert np.array_equal(pu[iu], p[iu])
+    assert np.all(np.isnan(pu[np.tril_indices(n, -1)]))
+
+
+@pytest.mark.parametrize("n,N", [(500, 10), (2051, 10), (64, 0)])
+def test_min_eig_matches_oracle(ctx, oracle_lib, n, N):
+    Vr, lam = si.make_problem("small", n) if n >= 40 else (None, None)
+    A = si.form_A_numpy(Vr, lam).astype(np.float32)
+    alpha = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s1 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    s2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.min_eig(torch.from_numpy(A).cuda(), N, 3, alpha, s1, s2)
+    assert ctx.sync_status() == 0
+    a_o, s1_o, s2_o = oracle_lib.min_eig(A.astype(np.float64), N, 3)
+    assert abs(s1.item() - s1_o) <= 1e-5 * s1_o
+    assert abs(s2.item() - s2_o) <= 1e-5 * s2_o
+    assert abs(alpha.item() - a_o) <= 1e-5 * s2_o
