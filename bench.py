@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark: randomized PSD projections per second at n = 20000.
+
+Workload (one "step"): one Algorithm 1 projection (the paper's Alg. 2 with the
+range finder of Alg. 1) and one Algorithm 2 projection (the paper's Alg. 3
+with alpha from Alg. 5, N = 10) of the same synthetic FP32 symmetric matrix,
+n = 20000, k = 100, p = 10 (sketch width 110), q = 1, full P = W W^T written.
+A step therefore runs every step of the path: Omega, the sketch and power
+passes, CholeskyQR2, the core pass, the l x l eigensolve, the factor, the
+reconstruction and the alpha estimate.
+
+Matrix recipe: A = U diag(lam) U^T, U = 4 Householder reflectors, 200
+eigenvalues decaying geometrically 100 -> 0.1, 300 uniform in [-5, -0.1], the
+rest N(0, 0.01^2), formed in FP64 and rounded to FP32 (synth_inputs.py).
+A (1.6 GB) is larger than L2, so no flush is needed between steps.
+
+`value` = projections / s over all ranks (N > 1: independent replicas, one
+per GPU, no collective on the data path).  Extra keys: roofline of the
+dominant kernel, cpu_baseline (the FP64 oracle on host cores), e2e (the
+host-buffer C-ABI call with copies inside the timed region), clocks, kernel
+launches, per-algorithm latency p50/p99, per-stage times and accuracy against
+the oracle and the exact projection.
+
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT, K_DEFAULT, P_DEFAULT, Q_DEFAULT, SEED = 20000, 100, 10, 1, 1
+STAGES = ["apass", "gemv", "orth", "core", "eig", "factor", "syrk", "other"]
+PREC_NAMES = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
+DTYPE_NAMES = {"fp32": "f32", "tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--k", type=int, default=K_DEFAULT)
+    ap.add_argument("--p", type=int, default=P_DEFAULT)
+    ap.add_argument("--q", type=int, default=Q_DEFAULT)
+    ap.add_argument("--prec", default="auto", choices=["auto", *PREC_NAMES])
+    ap.add_argument("--syrk-prec", default="auto", choices=["auto", "fp32", "bf16x3"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks sampled with nvidia-smi during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# the oracle baseline (host cores)
+# --------------------------------------------------------------------------
+def oracle_sample(A64_or_none, n, k, p, q, Vr=None, lam=None):
+    """One FP64 oracle Algorithm 1 projection; returns (seconds, W)."""
+    import numpy as np
+    import oracle
+    import synth_inputs as si
+    if A64_or_none is None:
+        A64_or_none = si.form_A_numpy(Vr, lam).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    out = oracle.alg1(A64_or_none, k, p, q, SEED)
+    return time.perf_counter() - t0, out["W"]
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, rank 0 only.
+    Each step is a bounded sample: one Algorithm-1 projection at n_s = n/4
+    with the same recipe and (k, p, q); its time is scaled to n by the
+    O(k n^2) cost of the passes, (n / n_s)^2."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import synth_inputs as si
+    n_s = max(args.k + args.p + 1, args.n // 4)
+    Vr, lam = si.make_problem("decay", n_s)
+    A64 = si.form_A_numpy(Vr, lam).astype(np.float32).astype(np.float64)
+    for _ in range(args.warmup):
+        oracle_sample(A64, n_s, args.k, args.p, args.q)
+    times = []
+    for _ in range(args.steps):
+        t, _ = oracle_sample(A64, n_s, args.k, args.p, args.q)
+        times.append(t)
+    scale = (args.n / n_s) ** 2
+    per_proj = statistics.mean(times) * scale
+    value = 1.0 / per_proj
+    sample = (f"one FP64 oracle Algorithm-1 projection per step at n={n_s} (k={args.k}, "
+              f"p={args.p}, q={args.q}), time scaled by (n/{n_s})^2 to n={args.n}")
+    line = {
+        "metric": f"PSD projections/s at n={args.n}", "value": value, "unit": "projections/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_proj * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": workload_config(args, "fp64-oracle", "n/a"),
+        "cpu_baseline": {"value": value, "unit": "projections/s", "cores": cores_used(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "projections/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, prec, syrk_prec):
+    return {"workload": (f"randomized PSD projection, Alg. 1 + Alg. 2 per step, n={args.n}, "
+                         f"k={args.k}, p={args.p}, q={args.q}, N=10, full P"),
+            "n": args.n, "k": args.k, "p": args.p, "q": args.q, "N": 10,
+            "prec": prec, "syrk_prec": syrk_prec,
+            "l2": "inputs larger than L2 (A = %.2f GB)" % (4.0 * args.n * args.n / 1e9),
+            "parallelism": f"replicas{args.gpus}"}
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for pth in paths:
+        with open(os.path.join(ROOT, pth), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel_file: str, n: int):
+    """traffic per launch recorded by the committed ncu summary, if it was
+    taken on the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = source_sha([kernel_file])
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 4 and parts[0] == kernel_file and parts[1] == sha and int(parts[2]) == n:
+            return float(parts[3])
+    return None
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2410_19208_gb300 as ps
+    import synth_inputs as si
+
+    prec = args.prec if args.prec != "auto" else "fp32"
+    syrk_prec = args.syrk_prec if args.syrk_prec != "auto" else "fp32"
+    n, k, p, q = args.n, args.k, args.p, args.q
+    m = k + p
+    Vr, lam = si.make_problem("decay", n)
+    A = si.form_A_torch(Vr, lam, dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = ps.Context(local, stream)
+    P = torch.empty(n, n, device=dev)
+    W = ps.tall_empty(n, m, dev)
+    rank_t = torch.zeros(1, dtype=torch.int32, device=dev)
+    alpha_t = torch.zeros(1, dtype=torch.float64, device=dev)
+    opts = ps.make_opts(prec=PREC_NAMES[prec], syrk_prec=PREC_NAMES[syrk_prec])
+
+    def step(lat=None):
+        if lat is not None:
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+        ctx.alg1(A, k, p, q, SEED, P=P, W=W, rank=rank_t, opts=opts)
+        if lat is not None:
+            e1.record(stream)
+        ctx.alg2(A, k, p, q, SEED, alpha_out=alpha_t, P=P, W=W, rank=rank_t, opts=opts)
+        if lat is not None:
+            e2.record(stream)
+            lat.append((e0, e1, e2))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    st = ctx.sync_status()
+    if st != 0:
+        raise SystemExit(f"device status {ps.STATUS.get(st)} during warm-up")
+
+    # ---- timed region ---------------------------------------------------
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    ctx_launch0 = ps.lib().psdproj_kernel_launches()
+    ps.lib().psdproj_timing_enable(ctx.h, 1)
+    lat = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(lat)
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = int(ps.lib().psdproj_kernel_launches() - ctx_launch0)
+    import ctypes
+    ms_k = (ctypes.c_double * 8)()
+    cnt_k = (ctypes.c_int * 8)()
+    ps.lib().psdproj_timing_read(ctx.h, ms_k, cnt_k, 8)
+    ps.lib().psdproj_timing_enable(ctx.h, 0)
+    st = ctx.sync_status()
+    if st != 0:
+        raise SystemExit(f"device status {ps.STATUS.get(st)} in the timed region")
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_proj = 2 * args.steps * world
+    value = total_proj / (elapsed_ms / 1e3)
+    a1 = [x[0].elapsed_time(x[1]) for x in lat]
+    a2 = [x[1].elapsed_time(x[2]) for x in lat]
+
+    def pct(v, q_):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(q_ * (len(v) - 1))))]
+
+    stages = {STAGES[i]: {"ms_total": ms_k[i], "launches": cnt_k[i],
+                          "ms_avg": (ms_k[i] / cnt_k[i]) if cnt_k[i] else None} for i in range(8)}
+
+    # ---- roofline of the dominant kernel: the symmetric A-pass ------------
+    peaks, peak_kind = measured_peaks()
+    apass_ms = stages["apass"]["ms_avg"]
+    upper_elems = n * (n + 1) // 2
+    if prec == "fp32":
+        # FP32 FMA on the CUDA cores: 2 n^2 m algorithmic FLOPs per pass,
+        # peak = 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock
+        flops = 2.0 * n * n * m
+        achieved = flops / (apass_ms / 1e3) / 1e12
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "kernel": "sym_pass_simt",
+                "peak_source": f"derived: 152 SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
+                "hbm_frac_of_" + peak_kind: (upper_elems * 4 / (apass_ms / 1e3) / 1e9) / peaks["hbm_gbs"],
+                "traffic": traffic_from_profile("paper_2410_19208_gb300/csrc/sympass_simt.cu", n)}
+    else:
+        bytes_alg = upper_elems * 4.0
+        achieved = bytes_alg / (apass_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "kernel": "sym_pass_tc",
+                "peak_source": peak_kind,
+                "traffic": traffic_from_profile("paper_2410_19208_gb300/csrc/sympass_tc.cu", n)}
+    roof["per_launch_ms"] = apass_ms
+    roof["algorithmic_bytes_per_launch"] = upper_elems * 4.0
+    roof["algorithmic_flops_per_launch"] = 2.0 * n * n * m
+
+    line = {
+        "metric": f"PSD projections/s at n={n}", "value": value, "unit": "projections/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE_NAMES[prec], "data": "synthetic",
+        "config": workload_config(args, prec, syrk_prec),
+        "roofline": roof,
+        "latency_ms": {"alg1_p50": pct(a1, 0.5), "alg1_p99": pct(a1, 0.99),
+                       "alg2_p50": pct(a2, 0.5), "alg2_p99": pct(a2, 0.99)},
+        "stages": stages, "gpu_launches": launches, "clocks": clocks,
+    }
+
+    # ---- end to end through the host-buffer C-ABI call --------------------
+    if not args.no_e2e:
+        Ah = A.cpu().pin_memory()
+        Ph = torch.empty(n, n, dtype=torch.float32).pin_memory()
+        ctx.alg1_host(Ah, k, p, q, SEED, P=Ph, opts=opts)
+        ctx.alg2_host(Ah, k, p, q, SEED, P=Ph, opts=opts)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ctx.alg1_host(Ah, k, p, q, SEED, P=Ph, opts=opts)
+            ctx.alg2_host(Ah, k, p, q, SEED, P=Ph, opts=opts)
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        line["e2e"] = {"value": 2 * args.e2e_steps * world / dt, "unit": "projections/s",
+                       "h2d_bytes_per_step": 2 * 4 * n * n, "d2h_bytes_per_step": 2 * (4 * n * n + 4 + 8),
+                       "api": "psdproj_alg1_host + psdproj_alg2_host, pinned host buffers"}
+        del Ah, Ph
+
+    # ---- accuracy and the oracle baseline (rank 0, N = 1 only) -------------
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        ctx.alg1(A, k, p, q, SEED, P=P, W=W, rank=rank_t, opts=opts)
+        Wg = W.cpu().numpy().astype(np.float64)
+        A64 = A.cpu().numpy().astype(np.float64)
+        del P
+        torch.cuda.empty_cache()
+        t_or, Wo = oracle_sample(A64, n, k, p, q)
+        del A64
+        rel_or = np.sqrt(max(oracle.factor_dist2(Wg, Wo), 0.0) / oracle.factor_norm2(Wo))
+        xp2 = float(np.sum(np.maximum(lam, 0.0) ** 2))
+        err_g = np.sqrt(max(oracle.exact_dist2(Vr, lam, Wg), 0.0) / xp2)
+        err_o = np.sqrt(max(oracle.exact_dist2(Vr, lam, Wo), 0.0) / xp2)
+        line["accuracy_alg1"] = {"rel_fro_vs_oracle": rel_or, "rel_fro_vs_exact": err_g,
+                                 "oracle_rel_fro_vs_exact": err_o, "ratio_to_oracle_error": err_g / err_o}
+        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "projections/s", "cores": cores_used(),
+                                "kind": "oracle",
+                                "sample": f"one FP64 oracle Algorithm-1 projection at n={n} "
+                                          f"(k={k}, p={p}, q={q}), {t_or:.1f} s"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -113,7 +113,7 @@ static int sym_mul(const double *A, int64_t n, int64_t lda, const double *X,
         t = omp_get_thread_num();
 #endif
         double *Yt = acc + (size_t)t * (size_t)n * (size_t)m;
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(static, 16)
         for (int64_t i = 0; i < n; ++i) {
             const double *Ai = A + i * lda;
             double *yi = Yt + i * m;
