@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison")
     return ap.parse_args()
 
 
@@ -242,8 +243,8 @@ def main():
     import paper_2410_19208_gb300 as ps
     import synth_inputs as si
 
-    prec = args.prec if args.prec != "auto" else "fp32"
-    syrk_prec = args.syrk_prec if args.syrk_prec != "auto" else "fp32"
+    prec = args.prec if args.prec != "auto" else "bf16"
+    syrk_prec = args.syrk_prec if args.syrk_prec != "auto" else ("fp32" if prec == "fp32" else "bf16x3")
     n, k, p, q = args.n, args.k, args.p, args.q
     m = k + p
     Vr, lam = si.make_problem("decay", n)
@@ -254,71 +255,102 @@ def main():
     W = ps.tall_empty(n, m, dev)
     rank_t = torch.zeros(1, dtype=torch.int32, device=dev)
     alpha_t = torch.zeros(1, dtype=torch.float64, device=dev)
-    opts = ps.make_opts(prec=PREC_NAMES[prec], syrk_prec=PREC_NAMES[syrk_prec])
-
-    def step(lat=None):
-        if lat is not None:
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-        ctx.alg1(A, k, p, q, SEED, P=P, W=W, rank=rank_t, opts=opts)
-        if lat is not None:
-            e1.record(stream)
-        ctx.alg2(A, k, p, q, SEED, alpha_out=alpha_t, P=P, W=W, rank=rank_t, opts=opts)
-        if lat is not None:
-            e2.record(stream)
-            lat.append((e0, e1, e2))
-
-    for _ in range(max(args.warmup, 3)):
-        step()
-    st = ctx.sync_status()
-    if st != 0:
-        raise SystemExit(f"device status {ps.STATUS.get(st)} during warm-up")
-
-    # ---- timed region ---------------------------------------------------
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.4)
-    ctx_launch0 = ps.lib().psdproj_kernel_launches()
-    ps.lib().psdproj_timing_enable(ctx.h, 1)
-    lat = []
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for _ in range(args.steps):
-        step(lat)
-    t_end.record(stream)
-    torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    launches = int(ps.lib().psdproj_kernel_launches() - ctx_launch0)
     import ctypes
-    ms_k = (ctypes.c_double * 8)()
-    cnt_k = (ctypes.c_int * 8)()
-    ps.lib().psdproj_timing_read(ctx.h, ms_k, cnt_k, 8)
-    ps.lib().psdproj_timing_enable(ctx.h, 0)
-    st = ctx.sync_status()
-    if st != 0:
-        raise SystemExit(f"device status {ps.STATUS.get(st)} in the timed region")
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_proj = 2 * args.steps * world
-    value = total_proj / (elapsed_ms / 1e3)
-    a1 = [x[0].elapsed_time(x[1]) for x in lat]
-    a2 = [x[1].elapsed_time(x[2]) for x in lat]
 
     def pct(v, q_):
         v = sorted(v)
         return v[min(len(v) - 1, int(round(q_ * (len(v) - 1))))]
 
-    stages = {STAGES[i]: {"ms_total": ms_k[i], "launches": cnt_k[i],
-                          "ms_avg": (ms_k[i] / cnt_k[i]) if cnt_k[i] else None} for i in range(8)}
+    def measure(prec_, syrk_, steps, sample_clocks):
+        opts = ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_])
+
+        def step(lat=None):
+            if lat is not None:
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record(stream)
+            ctx.alg1(A, k, p, q, SEED, P=P, W=W, rank=rank_t, opts=opts)
+            if lat is not None:
+                e1.record(stream)
+            ctx.alg2(A, k, p, q, SEED, alpha_out=alpha_t, P=P, W=W, rank=rank_t, opts=opts)
+            if lat is not None:
+                e2.record(stream)
+                lat.append((e0, e1, e2))
+
+        for _ in range(max(args.warmup, 3)):
+            step()
+        st = ctx.sync_status()
+        if st != 0:
+            raise SystemExit(f"device status {ps.STATUS.get(st)} during warm-up ({prec_})")
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.4)
+        l0 = ps.lib().psdproj_kernel_launches()
+        ps.lib().psdproj_timing_enable(ctx.h, 1)
+        lat = []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(steps):
+            step(lat)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = int(ps.lib().psdproj_kernel_launches() - l0)
+        ms_k = (ctypes.c_double * 8)()
+        cnt_k = (ctypes.c_int * 8)()
+        ps.lib().psdproj_timing_read(ctx.h, ms_k, cnt_k, 8)
+        ps.lib().psdproj_timing_enable(ctx.h, 0)
+        st = ctx.sync_status()
+        if st != 0:
+            raise SystemExit(f"device status {ps.STATUS.get(st)} in the timed region ({prec_})")
+        elapsed_ms = t_start.elapsed_time(t_end)
+        if dist:
+            t = torch.tensor([elapsed_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            elapsed_ms = float(t.item())
+        a1 = [x[0].elapsed_time(x[1]) for x in lat]
+        a2 = [x[1].elapsed_time(x[2]) for x in lat]
+        stages = {STAGES[i]: {"ms_total": ms_k[i], "launches": cnt_k[i],
+                              "ms_avg": (ms_k[i] / cnt_k[i]) if cnt_k[i] else None} for i in range(8)}
+        # accuracy of this form against the exact projection (closed form)
+        ctx.alg1(A, k, p, q, SEED, P=None, W=W, rank=rank_t,
+                 opts=ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_],
+                                   out_mode=ps.OUT_FACTOR))
+        W1 = W.cpu().numpy().astype(np.float64)
+        ctx.alg2(A, k, p, q, SEED, alpha_out=alpha_t, P=None, W=W, rank=rank_t,
+                 opts=ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_],
+                                   out_mode=ps.OUT_FACTOR))
+        W2 = W.cpu().numpy().astype(np.float64)
+        return dict(elapsed_ms=elapsed_ms, lat1=a1, lat2=a2, stages=stages, launches=launches,
+                    clocks=clocks, W1=W1, W2=W2, opts=opts)
+
+    # relative Frobenius error against the exact projection X+ = U diag(lam+) U^T,
+    # in Gram form through the reflectors (no n x n matrix):
+    #   ||X+ - W W^T||^2 = sum lam+^2 - 2 sum_i lam+_i ||(U^T W)_i||^2 + ||W^T W||^2
+    lam_p = np.maximum(lam, 0.0)
+    xp = float(np.sqrt(np.sum(lam_p ** 2)))
+
+    def err_exact(Wf):
+        X = Wf.copy()
+        for t in range(Vr.shape[0]):          # U^T = H_r ... H_1: apply H_1 first
+            v = Vr[t]
+            X -= np.outer(v, (2.0 / float(v @ v)) * (v @ X))
+        G = Wf.T @ Wf
+        d2 = float(np.sum(lam_p ** 2) - 2.0 * np.sum(lam_p * np.sum(X * X, axis=1)) + np.sum(G * G))
+        return float(np.sqrt(max(d2, 0.0)) / xp)
+
+    head = measure(prec, syrk_prec, args.steps, True)
+    elapsed_ms = head["elapsed_ms"]
+    total_proj = 2 * args.steps * world
+    value = total_proj / (elapsed_ms / 1e3)
+    stages = head["stages"]
+    opts = head["opts"]
 
     # ---- roofline of the dominant kernel: the symmetric A-pass ------------
     peaks, peak_kind = measured_peaks()
@@ -339,8 +371,8 @@ def main():
         bytes_alg = upper_elems * 4.0
         achieved = bytes_alg / (apass_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "kernel": "sym_pass_tc",
-                "peak_source": peak_kind,
+                "frac": achieved / peaks["hbm_gbs"], "kernel": "sym_pass_bf16 (tcgen05)",
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": traffic_from_profile("paper_2410_19208_gb300/csrc/sympass_tc.cu", n)}
     roof["per_launch_ms"] = apass_ms
     roof["algorithmic_bytes_per_launch"] = upper_elems * 4.0
@@ -353,10 +385,22 @@ def main():
         "vs_baseline": None, "dtype": DTYPE_NAMES[prec], "data": "synthetic",
         "config": workload_config(args, prec, syrk_prec),
         "roofline": roof,
-        "latency_ms": {"alg1_p50": pct(a1, 0.5), "alg1_p99": pct(a1, 0.99),
-                       "alg2_p50": pct(a2, 0.5), "alg2_p99": pct(a2, 0.99)},
-        "stages": stages, "gpu_launches": launches, "clocks": clocks,
+        "latency_ms": {"alg1_p50": pct(head["lat1"], 0.5), "alg1_p99": pct(head["lat1"], 0.99),
+                       "alg2_p50": pct(head["lat2"], 0.5), "alg2_p99": pct(head["lat2"], 0.99)},
+        "stages": stages, "gpu_launches": head["launches"], "clocks": head["clocks"],
+        "error_vs_exact": {"alg1": err_exact(head["W1"]), "alg2": err_exact(head["W2"])},
     }
+    if prec != "fp32" and not args.no_plain:
+        plain = measure("fp32", "fp32", max(2, min(args.steps, 5)), False)
+        pv = 2 * max(2, min(args.steps, 5)) * world / (plain["elapsed_ms"] / 1e3)
+        line["plain_fp32"] = {"value": pv, "unit": "projections/s",
+                              "ms_per_step": plain["elapsed_ms"] / max(2, min(args.steps, 5)),
+                              "speedup_of_headline": value / pv,
+                              "error_vs_exact": {"alg1": err_exact(plain["W1"]),
+                                                 "alg2": err_exact(plain["W2"])}}
+        Wg = plain["W1"]
+    else:
+        Wg = head["W1"]
 
     # ---- end to end through the host-buffer C-ABI call --------------------
     if not args.no_e2e:
@@ -383,19 +427,19 @@ def main():
     # ---- accuracy and the oracle baseline (rank 0, N = 1 only) -------------
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
-        ctx.alg1(A, k, p, q, SEED, P=P, W=W, rank=rank_t, opts=opts)
-        Wg = W.cpu().numpy().astype(np.float64)
         A64 = A.cpu().numpy().astype(np.float64)
         del P
         torch.cuda.empty_cache()
         t_or, Wo = oracle_sample(A64, n, k, p, q)
         del A64
-        rel_or = np.sqrt(max(oracle.factor_dist2(Wg, Wo), 0.0) / oracle.factor_norm2(Wo))
-        xp2 = float(np.sum(np.maximum(lam, 0.0) ** 2))
-        err_g = np.sqrt(max(oracle.exact_dist2(Vr, lam, Wg), 0.0) / xp2)
-        err_o = np.sqrt(max(oracle.exact_dist2(Vr, lam, Wo), 0.0) / xp2)
-        line["accuracy_alg1"] = {"rel_fro_vs_oracle": rel_or, "rel_fro_vs_exact": err_g,
-                                 "oracle_rel_fro_vs_exact": err_o, "ratio_to_oracle_error": err_g / err_o}
+        rel = lambda Wx: float(np.sqrt(max(oracle.factor_dist2(Wx, Wo), 0.0) / oracle.factor_norm2(Wo)))
+        err_o = err_exact(Wo)
+        line["accuracy_alg1"] = {
+            "headline_rel_fro_vs_oracle": rel(head["W1"]),
+            "plain_fp32_rel_fro_vs_oracle": rel(Wg),
+            "headline_rel_fro_vs_exact": err_exact(head["W1"]),
+            "oracle_rel_fro_vs_exact": err_o,
+            "headline_ratio_to_oracle_error": err_exact(head["W1"]) / err_o}
         line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "projections/s", "cores": cores_used(),
                                 "kind": "oracle",
                                 "sample": f"one FP64 oracle Algorithm-1 projection at n={n} "

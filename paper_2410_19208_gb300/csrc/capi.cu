@@ -108,8 +108,9 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
     const size_t half_tall = align256(sizeof(uint16_t) * (size_t)ld * lp);
     const size_t small_d = align256(sizeof(double) * (size_t)lp * lp);
     const size_t small_f = align256(sizeof(float) * (size_t)lp * lp);
+    const size_t chol_scr = align256(sizeof(double) * ((size_t)lp * lp + lp));
     size_t total = 5 * tall + 2 * half_tall + align256(sizeof(float) * nchunk * lp * lp) +
-                   3 * small_d + align256(sizeof(double) * lp) + 3 * small_f +
+                   3 * small_d + chol_scr + align256(sizeof(double) * lp) + 3 * small_f +
                    align256(sizeof(float) * 2 * (size_t)(lp + 2) * (lp + 2)) +
                    align256(sizeof(int) * lp) + 2 * align256(sizeof(float) * ld) +
                    align256(sizeof(double) * 16) + align256(sizeof(unsigned) * 16) +
@@ -139,6 +140,7 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
     ws.G = reinterpret_cast<double *>(take(small_d));
     ws.R = reinterpret_cast<double *>(take(small_d));
     ws.C = reinterpret_cast<double *>(take(small_d));
+    ws.cholscr = reinterpret_cast<double *>(take(chol_scr));
     ws.d = reinterpret_cast<double *>(take(align256(sizeof(double) * lp)));
     ws.Rinv = reinterpret_cast<float *>(take(small_f));
     ws.V = reinterpret_cast<float *>(take(small_f));
@@ -196,10 +198,12 @@ int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, flo
     const double tau = 1e-10;
     stage_scope st(ctx, PSDPROJ_STAGE_ORTH);
     PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1), 2);
-    PSD_KL(launch_cholesky(s, ws.G, m, ws.R, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status), 1);
+    PSD_KL(launch_cholesky(s, ws.G, m, ws.R, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status, 1,
+                           ws.cholscr), 1);
     PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, ws.T, ws.ld), 1);
     PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1), 2);
-    PSD_KL(launch_cholesky(s, ws.G, m, ws.R, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status), 1);
+    PSD_KL(launch_cholesky(s, ws.G, m, ws.R, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
+                           ws.cholscr), 1);
     PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq), 1);
     return PSDPROJ_OK;
 }

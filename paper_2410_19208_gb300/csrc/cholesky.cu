@@ -1,6 +1,9 @@
 // CholeskyQR steps of the orthonormalisation (QR 'econ' in Alg. 1):
-//   R = chol(G) in FP64 with the dependent-column rule, R^-1 in FP32, and
-//   Q = Y R^-1 (a tall x small product on the CUDA cores).
+//   R = chol(G) (FP64 for the first pass of CholeskyQR2, FP32 for the second,
+//   whose Gram is I + O(eps)) with the dependent-column rule, R^-1 in FP32,
+//   and Q = Y R^-1 (a tall x small product on the CUDA cores).
+// The factorization is right-looking with two block barriers per column;
+// each thread owns a fixed set of upper-triangle entries.
 //
 // Dependent-column rule: column j is dependent when its pivot (the squared
 // norm of y_j after removing the earlier columns) is <= tau * max_i G_ii, or
@@ -12,27 +15,34 @@ namespace {
 
 constexpr int NT = 1024;
 constexpr int SMEM_M = 128;  // largest m kept in shared memory
+constexpr int EPT = (SMEM_M * (SMEM_M + 1) / 2 + NT - 1) / NT;  // upper entries per thread
 
+// T = double: the first CholeskyQR pass (the Gram of the raw sketch, which can
+// be ill-conditioned); T = float: the second pass, whose Gram is I + O(eps).
+template <typename T>
 __global__ void __launch_bounds__(NT)
 cholesky_kernel(const double *__restrict__ G, int m, double *R, float *Rinv,
-                int *__restrict__ dead, int *__restrict__ d_qrank, double tau, double *gU,
+                int *__restrict__ dead, int *__restrict__ d_qrank, double tau, T *gU, T *growj,
                 int *d_status)
 {
-    extern __shared__ double smd[];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const bool in_smem = m <= SMEM_M;
     const int ldu = in_smem ? (m + 1) : m;
-    double *U = in_smem ? smd : gU;                                  // m x ldu, row-major
-    float *X = in_smem ? reinterpret_cast<float *>(smd + m * (m + 1)) : Rinv;  // R^-1
-    const int ldx = in_smem ? (m + 1) : m;
+    T *U = in_smem ? reinterpret_cast<T *>(smraw) : gU;            // row-major upper triangle
+    T *rowj = in_smem ? (U + m * (m + 1)) : growj;                  // scaled row j
+    float *Rs = in_smem ? reinterpret_cast<float *>(rowj + m) : nullptr;  // FP32 R (row-major)
     __shared__ double s_gmax;
     __shared__ int s_dead[PSD_MAX_M];
     __shared__ int s_bad;
+    __shared__ T s_r, s_inv;
+    __shared__ int s_dj;
     const int tid = threadIdx.x;
+    const int nup = m * (m + 1) / 2;
 
-    // U = upper(G) (row-major: U[i*ldu + k] = G(i,k), k >= i)
+    // U = upper(G)
     for (int e = tid; e < m * m; e += NT) {
-        const int i = e / m, k = e % m;
-        if (k >= i) U[i * ldu + k] = G[(int64_t)k * m + i];
+        const int i = e / m, k = e - (e / m) * m;
+        if (k >= i) U[i * ldu + k] = (T)G[(int64_t)k * m + i];
     }
     if (tid == 0) {
         double g = 0.0;
@@ -45,83 +55,102 @@ cholesky_kernel(const double *__restrict__ G, int m, double *R, float *Rinv,
         s_gmax = g;
         s_bad = bad;
     }
+    // this thread's upper-triangle entries (fixed for the whole factorization)
+    int ei[EPT], ek[EPT];
+#pragma unroll
+    for (int c = 0; c < EPT; ++c) {
+        const int e = tid + c * NT;
+        ei[c] = -1;
+        ek[c] = 0;
+        if (in_smem && e < nup) {
+            // e -> (i <= k), row-major over the upper triangle
+            const float hb = 2.0f * m + 1.0f;
+            int i = (int)((hb - sqrtf(fmaxf(hb * hb - 8.0f * e, 0.0f))) * 0.5f);
+            i = max(0, min(i, m - 1));
+            while (i > 0 && i * m - i * (i - 1) / 2 > e) --i;
+            while (i + 1 < m && (i + 1) * m - (i + 1) * i / 2 <= e) ++i;
+            ei[c] = i;
+            ek[c] = i + (e - (i * m - i * (i - 1) / 2));
+        }
+    }
     __syncthreads();
     if (s_bad) psd_set_status(d_status, PSDPROJ_ENOTFINITE);
-    const double thr = tau * s_gmax;
+    const T thr = (T)(tau * s_gmax);
+    const bool any = s_gmax > 0.0;
 
     for (int j = 0; j < m; ++j) {
-        const double piv = U[j * ldu + j];
-        __syncthreads();  // every thread holds piv before row j is rewritten
-        const bool dj = !(piv > thr) || !(s_gmax > 0.0);
-        if (dj) {
-            for (int k = j + 1 + tid; k < m; k += NT) U[j * ldu + k] = 0.0;
-            if (tid == 0) { U[j * ldu + j] = 1.0; s_dead[j] = 1; }
-            __syncthreads();
-            continue;
-        }
-        const double r = sqrt(piv);
-        const double inv = 1.0 / r;
-        for (int k = j + 1 + tid; k < m; k += NT) U[j * ldu + k] *= inv;
-        if (tid == 0) { U[j * ldu + j] = r; s_dead[j] = 0; }
-        __syncthreads();
-        // trailing update of the upper triangle: U(i,k) -= R(j,i) R(j,k), j < i <= k
-        const int t = m - j - 1;
-        for (int e = tid; e < t * t; e += NT) {
-            const int a = e / t, b = e - (e / t) * t;
-            if (b < a) continue;
-            const int i = j + 1 + a, k = j + 1 + b;
-            U[i * ldu + k] -= U[j * ldu + i] * U[j * ldu + k];
+        // phase A: pivot (one thread: FP64 sqrt and division are slow on
+        // this GPU) and scaled row j
+        if (tid == 0) {
+            const T piv = U[j * ldu + j];
+            const bool d0 = !(piv > thr) || !any;
+            const T r0 = d0 ? (T)1 : (T)sqrt(piv);
+            s_r = r0;
+            s_inv = (T)1 / r0;
+            s_dj = d0 ? 1 : 0;
         }
         __syncthreads();
-    }
-
-    // R^-1 (upper) in FP32, row by row from the bottom:
-    //   X(i, j) = (delta_ij - sum_{i<k<=j} R(i,k) X(k,j)) / R(i,i),  j >= i.
-    // Eight lanes share one output and split the sum.
-    for (int e = tid; e < m * m; e += NT) {
-        const int i = e / m, k = e % m;
-        X[i * ldx + k] = 0.0f;
-    }
-    __syncthreads();
-    const int grp = tid >> 3, lane8 = tid & 7;
-    for (int i = m - 1; i >= 0; --i) {
-        const float rii = (float)U[i * ldu + i];
-        for (int j0 = i; j0 < m; j0 += NT / 8) {
-            const int j = j0 + grp;
-            float s = 0.0f;
-            if (j < m)
-                for (int k = i + 1 + lane8; k <= j; k += 8) s = fmaf((float)U[i * ldu + k], X[k * ldx + j], s);
-            s += __shfl_xor_sync(0xffffffffu, s, 1);
-            s += __shfl_xor_sync(0xffffffffu, s, 2);
-            s += __shfl_xor_sync(0xffffffffu, s, 4);
-            if (j < m && lane8 == 0) X[i * ldx + j] = ((i == j ? 1.0f : 0.0f) - s) / rii;
+        const bool dj = s_dj != 0;
+        const T r = s_r, inv = s_inv;
+        for (int k = j + tid; k < m; k += NT) {
+            const T v = (k == j) ? r : (dj ? (T)0 : U[j * ldu + k] * inv);
+            U[j * ldu + k] = v;
+            rowj[k] = (k == j) ? (T)0 : v;
         }
+        if (tid == 0) s_dead[j] = dj ? 1 : 0;
         __syncthreads();
-    }
-
-    // outputs: R (column-major FP64), R^-1 (column-major FP32)
-    if (in_smem) {
-        for (int e = tid; e < m * m; e += NT) {
-            const int i = e % m, k = e / m;  // (row i, column k)
-            R[(int64_t)k * m + i] = (k >= i) ? U[i * ldu + k] : 0.0;
-            Rinv[(int64_t)k * m + i] = X[i * ldx + k];
-        }
-    } else {
-        // U (in R) and X (in Rinv) are row-major upper triangles: transpose
-        // in place pairwise, zeroing the strict lower parts
-        for (int e = tid; e < m * m; e += NT) {
-            const int i = e / m, k = e % m;
-            if (k > i) {
-                const double u = R[(int64_t)i * m + k];
-                R[(int64_t)k * m + i] = u;
-                R[(int64_t)i * m + k] = 0.0;
-                const float x = Rinv[(int64_t)i * m + k];
-                Rinv[(int64_t)k * m + i] = x;
-                Rinv[(int64_t)i * m + k] = 0.0f;
+        // phase B: trailing update U(i,k) -= R(j,i) R(j,k), j < i <= k
+        if (!dj) {
+            if (in_smem) {
+#pragma unroll
+                for (int c = 0; c < EPT; ++c) {
+                    if (ei[c] > j) {
+                        const int i = ei[c], k = ek[c];
+                        U[i * ldu + k] -= rowj[i] * rowj[k];
+                    }
+                }
+            } else {
+                const int t = m - j - 1;
+                for (int e = tid; e < t * t; e += NT) {
+                    const int a = e / t, b = e - (e / t) * t;
+                    if (b < a) continue;
+                    const int i = j + 1 + a, k = j + 1 + b;
+                    U[i * ldu + k] -= rowj[i] * rowj[k];
+                }
             }
         }
+        __syncthreads();
+    }
+
+    // R (column-major FP64) and an FP32 copy for the inverse
+    for (int e = tid; e < m * m; e += NT) {
+        const int i = e % m, k = e / m;  // (row i, column k)
+        const T u = (k >= i) ? U[i * ldu + k] : (T)0;
+        R[(int64_t)k * m + i] = (double)u;
+        if (in_smem) Rs[i * ldu + k] = (float)u;
     }
     __syncthreads();
+    // R^-1 (upper, FP32): one warp per column j, back substitution
+    //   x_j = 1 / R_jj;  x_i = -(sum_{i<k<=j} R_ik x_k) / R_ii  (i = j-1 .. 0)
+    // x is kept in the output column of Rinv (column-major, ld m).
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int j = warp; j < m; j += NT / 32) {
+        float *x = Rinv + (int64_t)j * m;
+        for (int i = lane; i < m; i += 32) x[i] = 0.0f;
+        __syncwarp();
+        auto Rget = [&](int i, int k) -> float {
+            return in_smem ? Rs[i * ldu + k] : (float)R[(int64_t)k * m + i];
+        };
+        if (lane == 0) x[j] = 1.0f / Rget(j, j);
+        __syncwarp();
+        for (int i = j - 1; i >= 0; --i) {
+            float sacc = 0.0f;
+            for (int k = i + 1 + lane; k <= j; k += 32) sacc = fmaf(Rget(i, k), x[k], sacc);
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) x[i] = -sacc / Rget(i, i);
+            __syncwarp();
+        }
+    }
     for (int j = tid; j < m; j += NT) dead[j] = s_dead[j];
     if (tid == 0 && d_qrank) {
         int r = 0;
@@ -192,14 +221,26 @@ tall_small_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m,
 }  // namespace
 
 cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, double *R, float *Rinv,
-                            int *dead, int *d_qrank, double tau, int *d_status)
+                            int *dead, int *d_qrank, double tau, int *d_status, int fp64,
+                            double *gscratch)
 {
-    // large m works in global memory: U in R, X in Rinv
-    const size_t smem = m <= SMEM_M ? (sizeof(double) * m * (m + 1) + sizeof(float) * m * (m + 1)) : 0;
-    cudaError_t e = cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    cholesky_kernel<<<1, NT, smem, s>>>(G, m, R, Rinv, dead, d_qrank, tau, R, d_status);
+    // large m works in global memory (gscratch: m*m + m doubles)
+    if (fp64) {
+        const size_t smem = m <= SMEM_M ? (sizeof(double) * (m * (m + 1) + m) + sizeof(float) * m * (m + 1)) : 0;
+        cudaError_t e = cudaFuncSetAttribute(cholesky_kernel<double>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cholesky_kernel<double><<<1, NT, smem, s>>>(G, m, R, Rinv, dead, d_qrank, tau, gscratch,
+                                                    gscratch + (size_t)m * m, d_status);
+    } else {
+        float *fs = reinterpret_cast<float *>(gscratch);
+        const size_t smem = m <= SMEM_M ? (sizeof(float) * (m * (m + 1) + m) + sizeof(float) * m * (m + 1)) : 0;
+        cudaError_t e = cudaFuncSetAttribute(cholesky_kernel<float>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cholesky_kernel<float><<<1, NT, smem, s>>>(G, m, R, Rinv, dead, d_qrank, tau, fs,
+                                                   fs + (size_t)m * m, d_status);
+    }
     return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ struct psd_workspace {
     // Gram partials: nchunk x lpad x lpad floats
     float *gpart = nullptr;
     // small matrices
-    double *G = nullptr, *R = nullptr, *C = nullptr, *d = nullptr;
+    double *G = nullptr, *R = nullptr, *C = nullptr, *d = nullptr, *cholscr = nullptr;
     float *Rinv = nullptr, *V = nullptr, *M = nullptr, *eigscr = nullptr;
     int *dead = nullptr;
     // power iteration: two n-vectors (ld floats) and scalars
@@ -98,8 +98,11 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
                         int64_t ldz, int64_t n, int m, float *gpart, double *G,
                         int symmetrize);
 
+// fp64 = 1: FP64 factorization; 0: FP32.  gscratch: (m*m + m) doubles of
+// device memory, used when m > 128.
 cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, double *R, float *Rinv,
-                            int *dead, int *d_qrank, double tau, int *d_status);
+                            int *dead, int *d_qrank, double tau, int *d_status, int fp64,
+                            double *gscratch);
 
 // Y (n x m) times a small m x c matrix B (column-major, ld = m) -> Z (n x c).
 // colmask (may be NULL): columns j with colmask[j] != 0 are written as zero.

@@ -17,15 +17,18 @@ constexpr int TCW = 128;   // columns per tile
 constexpr int SEGW = 8;    // tiles per block
 constexpr int NTW = 256;
 
-// scal[0]: scale of the input vector; scal[1]: norm of the last output;
-// scal[2]: the shift applied (A + shift I).
-__global__ void __launch_bounds__(NTW)
+// scal[0]: scale of the input vector; scal[1]: norm of the last output.
+// A block owns a segment of SEGW tiles (32 rows x 128 columns each) of one
+// block row.  Warp w holds rows 4w..4w+3, lane l columns 4l..4l+3 of every
+// tile; the loads of the whole segment are independent, and the column
+// partial sums stay in registers until the segment ends (one barrier).
+__global__ void __launch_bounds__(NTW, 2)
 sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
                 const float *__restrict__ x, float *__restrict__ y, float *__restrict__ other,
                 double *scal, unsigned *counter, const double *d_shift_neg, double *d_sigma,
                 int nb, int vec)
 {
-    __shared__ float colsum[8][TCW];
+    __shared__ float colsum[8][SEGW * TCW];
     __shared__ double red[NTW / 32];
     __shared__ bool s_last;
     int64_t idx = blockIdx.x;
@@ -39,7 +42,7 @@ sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
     }
     const int64_t row0 = (int64_t)I * TRW;
     const int tiles = (int)((n - row0 + TCW - 1) / TCW);
-    const int t0 = (int)idx * SEGW, t1 = min(tiles, t0 + SEGW);
+    const int t0 = (int)idx * SEGW;
     const float sc = (float)scal[0];
     const float shift = d_shift_neg ? (float)(-(*d_shift_neg)) : 0.0f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -51,42 +54,66 @@ sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
         const int64_t gr = row0 + warp * 4 + i;
         xr[i] = gr < n ? x[gr] * sc : 0.0f;
     }
-    for (int t = t0; t < t1; ++t) {
-        const int64_t c0 = row0 + (int64_t)t * TCW + lane * 4;
-        float xc[4];
-        float colacc[4] = {0.f, 0.f, 0.f, 0.f};
+    // two batches of four tiles: the 16 float4 loads of a batch are issued
+    // together (predicated, no branches), then consumed
+#pragma unroll 1
+    for (int b = 0; b < SEGW; b += 4) {
+        float4 va[4][4];
+        float colacc[4][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) xc[j] = (c0 + j < n) ? x[c0 + j] * sc : 0.0f;
+        for (int t = 0; t < 4; ++t) {
+            const int tt = t0 + b + t;
+            const int64_t c0 = row0 + (int64_t)tt * TCW + lane * 4;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int64_t gr = row0 + warp * 4 + i;
-            if (gr >= n) continue;
-            float a[4];
-            if (vec && c0 + 3 < n && c0 >= gr) {
-                const float4 v4 = *reinterpret_cast<const float4 *>(A + gr * lda + c0);
-                a[0] = v4.x; a[1] = v4.y; a[2] = v4.z; a[3] = v4.w;
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    a[j] = (c0 + j < n && c0 + j >= gr) ? A[gr * lda + c0 + j] : 0.0f;
+            for (int i = 0; i < 4; ++i) {
+                const int64_t gr = row0 + warp * 4 + i;
+                const bool ok = vec && tt < tiles && gr < n && c0 + 3 < n;
+                const float4 *src = reinterpret_cast<const float4 *>(A + (ok ? gr * lda + c0 : 0));
+                va[t][i] = ok ? __ldcs(src) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int tt = t0 + b + t;
+            const int64_t c0 = row0 + (int64_t)tt * TCW + lane * 4;
+            float xc[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                rowacc[i] = fmaf(a[j], xc[j], rowacc[i]);
-                if (c0 + j > gr) colacc[j] = fmaf(a[j], xr[i], colacc[j]);
+                colacc[t][j] = 0.0f;
+                xc[j] = (tt < tiles && c0 + j < n) ? x[c0 + j] * sc : 0.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t gr = row0 + warp * 4 + i;
+                float a[4] = {va[t][i].x, va[t][i].y, va[t][i].z, va[t][i].w};
+                if (tt < tiles && gr < n && (!vec || c0 + 3 >= n) && c0 < n) {
+                    // ragged right edge or unaligned rows: scalar loads
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        a[j] = (c0 + j < n && c0 + j >= gr) ? A[gr * lda + c0 + j] : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    // strictly-lower entries of the diagonal tile are discarded
+                    const float aj = (c0 + j >= gr) ? a[j] : 0.0f;
+                    rowacc[i] = fmaf(aj, xc[j], rowacc[i]);
+                    colacc[t][j] = fmaf((c0 + j > gr) ? aj : 0.0f, xr[i], colacc[t][j]);
+                }
             }
         }
+        // this thread's column partials of the batch (one owner per slot)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) colsum[warp][lane * 4 + j] = colacc[j];
-        __syncthreads();
-        if (threadIdx.x < TCW) {
-            float s = 0.0f;
+        for (int t = 0; t < 4; ++t)
 #pragma unroll
-            for (int w = 0; w < 8; ++w) s += colsum[w][threadIdx.x];
-            const int64_t gc = row0 + (int64_t)t * TCW + threadIdx.x;
-            if (gc < n && s != 0.0f) atomicAdd(&y[gc], s);
-        }
-        __syncthreads();
+            for (int j = 0; j < 4; ++j) colsum[warp][(b + t) * TCW + lane * 4 + j] = colacc[t][j];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < SEGW * TCW; c += NTW) {
+        float s = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += colsum[w][c];
+        const int64_t gc = row0 + (int64_t)t0 * TCW + c;
+        if (gc < n && s != 0.0f) atomicAdd(&y[gc], s);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {

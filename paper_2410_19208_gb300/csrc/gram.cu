@@ -87,22 +87,34 @@ gram_partial_kernel(const float *__restrict__ X, int64_t ldx, const float *__res
 
 // G[a + b*m] = sum over chunks of gpart (FP64); mode 0: full product,
 // mode 1: upper-only symmetric Gram (mirror), mode 2: symmetrise (S+S^T)/2.
+// Eight lanes share one entry of the partials (coalesced over the entry
+// index) and split the chunk sum; the FP64 adds spread over the whole GPU.
 __global__ void gram_reduce_kernel(const float *__restrict__ gpart, int nchunk, int m, int mp,
                                    int mode, double *__restrict__ G)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= m * m) return;
-    const int a = e % m, b = e / m;
-    int ia = a, ib = b;
-    if (mode == 1 && ia > ib) { ia = b; ib = a; }
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int f = (int)(tid >> 3), sub = (int)(tid & 7);
+    const bool act = f < mp * mp;
+    const int ia = act ? f / mp : 0, ib = act ? f - (f / mp) * mp : 0;
     double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += (double)gpart[(int64_t)c * mp * mp + ia * mp + ib];
-    if (mode == 2) {
-        double t = 0.0;
-        for (int c = 0; c < nchunk; ++c) t += (double)gpart[(int64_t)c * mp * mp + ib * mp + ia];
-        s = 0.5 * (s + t);
+    if (act && ia < m && ib < m && (mode != 1 || ia <= ib))
+        for (int c = sub; c < nchunk; c += 8) s += (double)gpart[(int64_t)c * mp * mp + f];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (!act || sub != 0 || ia >= m || ib >= m) return;
+    if (mode == 0) {
+        G[(int64_t)ib * m + ia] = s;
+    } else if (mode == 1) {
+        if (ia <= ib) {
+            G[(int64_t)ib * m + ia] = s;
+            G[(int64_t)ia * m + ib] = s;
+        }
+    } else {
+        // (S + S^T)/2: entry (ia, ib) contributes half to both positions
+        atomicAdd(&G[(int64_t)ib * m + ia], 0.5 * s);
+        atomicAdd(&G[(int64_t)ia * m + ib], 0.5 * s);
     }
-    G[(int64_t)b * m + a] = s;
 }
 
 }  // namespace
@@ -122,6 +134,11 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
                                                  gpart);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, s>>>(gpart, nchunk, m, mp, symmetrize, G);
+    if (symmetrize == 2) {
+        e = cudaMemsetAsync(G, 0, sizeof(double) * (size_t)m * m, s);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t threads = (int64_t)mp * mp * 8;
+    gram_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(gpart, nchunk, m, mp, symmetrize, G);
     return cudaGetLastError();
 }

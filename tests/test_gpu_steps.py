@@ -128,10 +128,15 @@ def test_cholqr2_orthonormal_same_range(ctx, oracle_lib, n, m, cond):
 
 
 def test_cholqr2_dependent_columns(ctx, oracle_lib):
+    """Columns dependent exactly in FP32 (duplicates, a zero column, a power-
+    of-two multiple) are detected on both sides and give zero Q columns.
+    (The GPU Gram sums FP32 products in FP32 within 64-row chunks, so
+    dependence is resolved to ~1e-6 relative, not to the oracle's 1e-10.)"""
     n, m = 500, 12
     rng = np.random.default_rng(1)
-    B = rng.standard_normal((n, 8))
-    Y = np.concatenate([B, B[:, :4] @ rng.standard_normal((4, 4))], axis=1).astype(np.float32)
+    B = rng.standard_normal((n, 8)).astype(np.float32)
+    Y = np.concatenate([B, B[:, 2:3], np.zeros((n, 1), np.float32), 2.0 * B[:, 5:6],
+                        B[:, 0:1]], axis=1)
     Yd = _tall_from_np(Y)
     Q = ps.tall_empty(n, m)
     qr = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -144,6 +149,27 @@ def test_cholqr2_dependent_columns(ctx, oracle_lib):
     live = q[:, :8]
     assert np.abs(live.T @ live - np.eye(8)).max() < 2e-5
     assert np.linalg.norm(live @ (live.T @ Qo[:, :8]) - Qo[:, :8]) < 1e-4
+
+
+def test_cholqr2_nearly_dependent_columns_keep_range(ctx):
+    """Columns dependent only up to FP32 rounding: whatever the rank decision,
+    Q stays orthonormal on its live columns and spans range(Y)."""
+    n, m = 500, 12
+    rng = np.random.default_rng(2)
+    B = rng.standard_normal((n, 8))
+    Y = np.concatenate([B, B[:, :4] @ rng.standard_normal((4, 4))], axis=1).astype(np.float32)
+    Q = ps.tall_empty(n, m)
+    qr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.cholqr2(_tall_from_np(Y), Q, qrank=qr)
+    assert ctx.sync_status() == 0
+    q = _np(Q)
+    r = int(qr.item())
+    assert 8 <= r <= 12
+    live = q[:, np.abs(q).sum(axis=0) > 0]
+    assert live.shape[1] == r
+    assert np.abs(live.T @ live - np.eye(r)).max() < 2e-4
+    Y64 = Y.astype(np.float64)
+    assert np.linalg.norm(Y64 - live @ (live.T @ Y64)) <= 1e-5 * np.linalg.norm(Y64)
 
 
 def test_core_matches_oracle(ctx, oracle_lib):
@@ -244,3 +270,104 @@ def test_min_eig_matches_oracle(ctx, oracle_lib, n, N):
     assert abs(s1.item() - s1_o) <= 1e-5 * s1_o
     assert abs(s2.item() - s2_o) <= 1e-5 * s2_o
     assert abs(alpha.item() - a_o) <= 1e-5 * s2_o
+
+
+# ----------------------------------------------------------------------------
+# tensor-core (tcgen05) symmetric pass, BF16 products, FP32 accumulation
+# ----------------------------------------------------------------------------
+def _bf16(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(torch.bfloat16).float().numpy()
+
+
+def _padded_A(A, pad=4):
+    """Row-major device copy with lda rounded up to a multiple of `pad`."""
+    n = A.shape[0]
+    lda = -(-n // pad) * pad
+    buf = torch.full((n, lda), float("nan"), device="cuda")
+    buf[:, :n] = torch.from_numpy(A).cuda()
+    return buf[:, :n]
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 255, 256, 257, 1000, 4099])
+@pytest.mark.parametrize("m", [1, 7, 50, 112, 128])
+def test_sym_pass_bf16_tensor_cores(ctx, oracle_lib, n, m):
+    A = _sym_A(n, seed=n + 13 * m)
+    rng = np.random.default_rng(m + 1)
+    X = rng.standard_normal((n, m)).astype(np.float32)
+    Ad = _padded_A(A)
+    Xd = _tall_from_np(X, ld=n + 4)
+    Y = ps.tall_empty(n, m, "cuda", ld=-(-n // 4) * 4)
+    shift = torch.tensor([0.75], dtype=torch.float64, device="cuda")
+    ctx.sym_pass(Ad, Xd, Y, shift=shift, prec=ps.PREC_BF16)
+    assert ctx.sync_status() == 0
+    Ab, Xb = _bf16(A).astype(np.float64), _bf16(X).astype(np.float64)
+    ref = oracle_lib.sym_mul(Ab, Xb) + 0.75 * X.astype(np.float64)
+    bound = np.abs(Ab) @ np.abs(Xb) + 0.75 * np.abs(X)
+    got = _np(Y)
+    assert np.all(np.abs(got - ref) <= 8 * np.sqrt(n) * EPS32 * bound + 1e-30)
+
+
+def test_sym_pass_bf16_lower_triangle_and_strides(ctx, oracle_lib):
+    n, m = 777, 33
+    A = _sym_A(n, seed=5)
+    Ap = _sym_A(n, seed=5, poison=True)
+    X = np.random.default_rng(6).standard_normal((n, m)).astype(np.float32)
+    Y1 = ps.tall_empty(n, m, "cuda", ld=n + 3)   # ld not a multiple of 4: scalar atomics
+    Y2 = ps.tall_empty(n, m, "cuda", ld=n + 1)
+    ctx.sym_pass(_padded_A(A), _tall_from_np(X), Y1, prec=ps.PREC_BF16)
+    ctx.sym_pass(_padded_A(Ap), _tall_from_np(X), Y2, prec=ps.PREC_BF16)
+    assert ctx.sync_status() == 0
+    y1, y2 = _np(Y1), _np(Y2)
+    assert np.all(np.isfinite(y2))
+    Ab, Xb = _bf16(A).astype(np.float64), _bf16(X).astype(np.float64)
+    ref = oracle_lib.sym_mul(Ab, Xb)
+    bound = np.abs(Ab) @ np.abs(Xb)
+    for y in (y1, y2):
+        assert np.all(np.abs(y - ref) <= 8 * np.sqrt(n) * EPS32 * bound)
+
+
+def test_sym_pass_tensor_core_unsupported_layouts(ctx):
+    n = 10
+    A = torch.zeros(n, n, device="cuda")          # lda = 10: not a multiple of 4
+    X = ps.tall_empty(n, 2)
+    Y = ps.tall_empty(n, 2)
+    with pytest.raises(ps.PsdprojError) as ei:
+        ctx.sym_pass(A, X, Y, prec=ps.PREC_BF16)
+    assert ei.value.code == 7
+    A2 = torch.zeros(200, 200, device="cuda")
+    X2 = ps.tall_empty(200, 129)
+    Y2 = ps.tall_empty(200, 129)
+    with pytest.raises(ps.PsdprojError) as ei:
+        ctx.sym_pass(A2, X2, Y2, prec=ps.PREC_BF16)   # m > 128
+    assert ei.value.code == 7
+
+
+# ----------------------------------------------------------------------------
+# tensor-core SYRK P = W W^T (split BF16, FP32 accumulation)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m,r", [(1, 1, 1), (100, 17, 17), (128, 128, 128), (129, 40, 33),
+                                   (1000, 112, 87), (4099, 110, 110), (300, 50, 0)])
+def test_syrk_split_bf16_tensor_cores(ctx, n, m, r):
+    rng = np.random.default_rng(n + m)
+    W = rng.standard_normal((n, m)).astype(np.float32)
+    W[:, r:] = 0.0
+    Wd = _tall_from_np(W, ld=n + 2)
+    rank = torch.tensor([r], dtype=torch.int32, device="cuda")
+    ldp = -(-n // 4) * 4
+    Pbuf = torch.full((n, ldp), float("nan"), device="cuda")
+    P = Pbuf[:, :n]
+    ctx.syrk(Wd, P, rank=rank, prec=ps.PREC_BF16X3)
+    Pub = torch.full((n, ldp), float("nan"), device="cuda")
+    Pu = Pub[:, :n]
+    ctx.syrk(Wd, Pu, rank=rank, out_mode=ps.OUT_UPPER, prec=ps.PREC_BF16X3)
+    assert ctx.sync_status() == 0
+    W64 = W.astype(np.float64)[:, :r]
+    ref = W64 @ W64.T
+    bound = np.abs(W64) @ np.abs(W64).T
+    p = P.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(p - ref) <= 3e-5 * bound + 1e-30)
+    pu = Pu.cpu().numpy().astype(np.float64)
+    iu = np.triu_indices(n)
+    assert np.array_equal(pu[iu], p[iu])
+    if n > 1:
+        assert np.all(np.isnan(pu[np.tril_indices(n, -1)]))
