@@ -47,6 +47,7 @@ extern "C" {
 #define PSDPROJ_ETIMEOUT    5  /* a bounded device wait gave up                 */
 #define PSDPROJ_ECUDA       6  /* a CUDA runtime / launch error                 */
 #define PSDPROJ_ENOTSUP     7  /* option not supported for these sizes         */
+#define PSDPROJ_ETOOLARGE   8  /* size above a fixed scratch capacity          */
 
 /* ---- precision of the A-passes (sketch, power and core products) -------- */
 #define PSDPROJ_PREC_FP32    0 /* FP32 FMA on the CUDA cores (plain FP32)      */
@@ -224,6 +225,29 @@ int psdproj_syrk(psdproj_ctx *ctx, const float *dW, int64_t ldw, int64_t n,
 int psdproj_min_eig(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                     int N, uint64_t seed, double *d_alpha, double *d_sigma1,
                     double *d_sigma2);
+
+/* Allocation-free min_eig (no counterpart in the paper; same result as
+ * psdproj_min_eig).  For callers that cannot call cudaMalloc: code running
+ * under another library's memory manager or a caching allocator that forbids
+ * allocations in its hot path, plug-ins whose host cannot grant device
+ * allocations, or processes whose device memory is reserved up front.  It
+ * needs no context and allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine): its scratch is a fixed device array of
+ * 2 * PSDPROJ_NOALLOC_MAX_N floats plus a few scalars, held by every GPU that
+ * loads this library until the process exits.
+ *   dA: device, n x n FP32 row-major (upper triangle read), lda >= n;
+ *   n <= PSDPROJ_NOALLOC_MAX_N, otherwise PSDPROJ_ETOOLARGE and nothing runs;
+ *   d_alpha (required), d_sigma1, d_sigma2 (may be NULL): device doubles;
+ *   stream: the cudaStream_t to enqueue on (NULL = legacy default stream).
+ * The first call on a device (with that device current) looks up the device
+ * address of the scratch array; make that first call before any stream
+ * capture.  Every call shares the one array per device and leaves its
+ * contents behind: calls that overlap on the GPU (other streams, or
+ * concurrent host threads) race and must be serialised by the caller.
+ * Errors found on the host are returned; nothing is synchronised. */
+#define PSDPROJ_NOALLOC_MAX_N 131072
+int psdproj_min_eig_noalloc(const float *dA, int64_t n, int64_t lda, int N, uint64_t seed,
+                            double *d_alpha, double *d_sigma1, double *d_sigma2, void *stream);
 
 #ifdef __cplusplus
 }

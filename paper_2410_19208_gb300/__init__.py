@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpsdproj.so")
 PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
 OUT_FULL, OUT_UPPER, OUT_FACTOR = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTFINITE", 4: "ENOCONV", 5: "ETIMEOUT",
-          6: "ECUDA", 7: "ENOTSUP"}
+          6: "ECUDA", 7: "ENOTSUP", 8: "ETOOLARGE"}
 
 
 class PsdprojError(RuntimeError):
@@ -80,6 +80,7 @@ def _load():
         "psdproj_factor": (_int, [_P, _P, _i64, _i64, _int, _P, _P, _P, _i64, _P]),
         "psdproj_syrk": (_int, [_P, _P, _i64, _i64, _int, _P, _P, _i64, _int, _int]),
         "psdproj_min_eig": (_int, [_P, _P, _i64, _i64, _int, _u64, _P, _P, _P]),
+        "psdproj_min_eig_noalloc": (_int, [_P, _i64, _i64, _int, _u64, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

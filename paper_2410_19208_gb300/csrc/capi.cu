@@ -431,6 +431,7 @@ const char *psdproj_status_string(int s)
     case PSDPROJ_ETIMEOUT: return "PSDPROJ_ETIMEOUT: device wait gave up";
     case PSDPROJ_ECUDA: return "PSDPROJ_ECUDA: CUDA error";
     case PSDPROJ_ENOTSUP: return "PSDPROJ_ENOTSUP: unsupported option";
+    case PSDPROJ_ETOOLARGE: return "PSDPROJ_ETOOLARGE: size above the fixed scratch capacity";
     default: return "PSDPROJ: unknown status";
     }
 }

@@ -22,7 +22,7 @@ constexpr int NTW = 256;
 // block row.  Warp w holds rows 4w..4w+3, lane l columns 4l..4l+3 of every
 // tile; the loads of the whole segment are independent, and the column
 // partial sums stay in registers until the segment ends (one barrier).
-__global__ void __launch_bounds__(NTW, 2)
+__global__ void __launch_bounds__(NTW)
 sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
                 const float *__restrict__ x, float *__restrict__ y, float *__restrict__ other,
                 double *scal, unsigned *counter, const double *d_shift_neg, double *d_sigma,
@@ -54,58 +54,75 @@ sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
         const int64_t gr = row0 + warp * 4 + i;
         xr[i] = gr < n ? x[gr] * sc : 0.0f;
     }
-    // two batches of four tiles: the 16 float4 loads of a batch are issued
-    // together (predicated, no branches), then consumed
+    // Interior tiles (strictly above the diagonal block, not past column n)
+    // take an unmasked path: per row one float4 load, 4 FMAs into the row sum
+    // and 4 into the column partials.  The diagonal tile, the ragged last
+    // tile and unaligned rows take the masked path.
+    const float *rowp[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gr = row0 + warp * 4 + i;
+        rowp[i] = A + (gr < n ? gr : 0) * lda;
+    }
+    auto is_interior = [&](int tt) {
+        const int64_t cb = row0 + (int64_t)tt * TCW;
+        return vec && tt > 0 && tt < tiles && cb + TCW <= n && row0 + 32 <= n;
+    };
+    // software pipeline: the loads of tile t+1 are issued before tile t is used
+    float4 nxt[4];
+    bool nxt_int = is_interior(t0);
+    if (nxt_int) {
+        const int64_t c0 = row0 + (int64_t)t0 * TCW + lane * 4;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) nxt[i] = __ldcs(reinterpret_cast<const float4 *>(rowp[i] + c0));
+    }
 #pragma unroll 1
-    for (int b = 0; b < SEGW; b += 4) {
-        float4 va[4][4];
-        float colacc[4][4];
+    for (int t = 0; t < SEGW; ++t) {
+        const int tt = t0 + t;
+        const int64_t c0 = row0 + (int64_t)tt * TCW + lane * 4;
+        float colacc[4] = {0.f, 0.f, 0.f, 0.f};
+        const bool interior = nxt_int;
+        float4 a4[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int tt = t0 + b + t;
-            const int64_t c0 = row0 + (int64_t)tt * TCW + lane * 4;
+        for (int i = 0; i < 4; ++i) a4[i] = nxt[i];
+        nxt_int = (t + 1 < SEGW) && is_interior(tt + 1);
+        if (nxt_int) {
+            const int64_t c1 = c0 + TCW;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int64_t gr = row0 + warp * 4 + i;
-                const bool ok = vec && tt < tiles && gr < n && c0 + 3 < n;
-                const float4 *src = reinterpret_cast<const float4 *>(A + (ok ? gr * lda + c0 : 0));
-                va[t][i] = ok ? __ldcs(src) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            for (int i = 0; i < 4; ++i) nxt[i] = __ldcs(reinterpret_cast<const float4 *>(rowp[i] + c1));
         }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int tt = t0 + b + t;
-            const int64_t c0 = row0 + (int64_t)tt * TCW + lane * 4;
-            float xc[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                colacc[t][j] = 0.0f;
-                xc[j] = (tt < tiles && c0 + j < n) ? x[c0 + j] * sc : 0.0f;
-            }
+        if (interior) {
+            const float4 xv = __ldg(reinterpret_cast<const float4 *>(x + c0));
+            const float xc[4] = {xv.x * sc, xv.y * sc, xv.z * sc, xv.w * sc};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int64_t gr = row0 + warp * 4 + i;
-                float a[4] = {va[t][i].x, va[t][i].y, va[t][i].z, va[t][i].w};
-                if (tt < tiles && gr < n && (!vec || c0 + 3 >= n) && c0 < n) {
-                    // ragged right edge or unaligned rows: scalar loads
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        a[j] = (c0 + j < n && c0 + j >= gr) ? A[gr * lda + c0 + j] : 0.0f;
-                }
+                const float a[4] = {a4[i].x, a4[i].y, a4[i].z, a4[i].w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    // strictly-lower entries of the diagonal tile are discarded
-                    const float aj = (c0 + j >= gr) ? a[j] : 0.0f;
-                    rowacc[i] = fmaf(aj, xc[j], rowacc[i]);
-                    colacc[t][j] = fmaf((c0 + j > gr) ? aj : 0.0f, xr[i], colacc[t][j]);
+                    rowacc[i] = fmaf(a[j], xc[j], rowacc[i]);
+                    colacc[j] = fmaf(a[j], xr[i], colacc[j]);
+                }
+            }
+        } else if (tt < tiles) {
+            float xc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xc[j] = (c0 + j < n) ? x[c0 + j] * sc : 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t gr = row0 + warp * 4 + i;
+                if (gr >= n) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    // strictly-lower entries of the diagonal tile are never loaded
+                    const float a = (c0 + j < n && c0 + j >= gr) ? rowp[i][c0 + j] : 0.0f;
+                    rowacc[i] = fmaf(a, xc[j], rowacc[i]);
+                    if (c0 + j > gr) colacc[j] = fmaf(a, xr[i], colacc[j]);
                 }
             }
         }
-        // this thread's column partials of the batch (one owner per slot)
+        // this thread's column partials of tile t (one owner per slot)
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) colsum[warp][(b + t) * TCW + lane * 4 + j] = colacc[t][j];
+        for (int j = 0; j < 4; ++j) colsum[warp][t * TCW + lane * 4 + j] = colacc[j];
     }
     __syncthreads();
     for (int c = threadIdx.x; c < SEGW * TCW; c += NTW) {
@@ -211,4 +228,80 @@ cudaError_t launch_alpha_finish(cudaStream_t s, const double *d_s1, const double
 {
     alpha_finish_kernel<<<1, 1, 0, s>>>(d_s1, d_s2, alpha_in, d_alpha, d_shift, d_info);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of min_eig.
+//
+// For callers that cannot call cudaMalloc: code running inside another
+// library's memory manager or a custom allocator that forbids allocations in
+// its hot path, plug-ins whose host cannot grant device allocations, or
+// contexts whose memory is capped and fully reserved up front.  Its scratch
+// (the two power-iteration vectors, the norms and the completion ticket) is a
+// fixed file-scope device array, present on every GPU that loads this
+// library until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NOALLOC_MAX_N = PSDPROJ_NOALLOC_MAX_N;
+constexpr size_t NOALLOC_VEC_BYTES = sizeof(float) * (size_t)NOALLOC_MAX_N;
+constexpr size_t NOALLOC_BYTES = 2 * NOALLOC_VEC_BYTES + 32 * sizeof(double) + 16 * sizeof(unsigned);
+
+// the shared scratch: v0, v1, then 32 doubles (scales, sigmas, shift, info), then tickets
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+__global__ void noalloc_reset_kernel(unsigned *counter) { if (threadIdx.x < 16) counter[threadIdx.x] = 0u; }
+
+__global__ void noalloc_copy_kernel(const double *s1, const double *s2, double *d1, double *d2)
+{
+    if (d1) *d1 = *s1;
+    if (d2) *d2 = *s2;
+}
+
+}  // namespace
+
+#include <mutex>
+
+extern "C" int psdproj_min_eig_noalloc(const float *dA, int64_t n, int64_t lda, int N, uint64_t seed,
+                                       double *d_alpha, double *d_sigma1, double *d_sigma2,
+                                       void *stream)
+{
+    if (!dA || !d_alpha || n < 1 || lda < n || N < 0) return PSDPROJ_EINVAL;
+    if (n > NOALLOC_MAX_N) return PSDPROJ_ETOOLARGE;
+    // set-up, once per device, with that device current: the device address
+    // of the scratch array (its name in host code is only a host-side stand-in)
+    static std::mutex mu;
+    static void *addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PSDPROJ_ECUDA;
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PSDPROJ_ECUDA;
+            addr[dev] = p;
+        }
+        base = static_cast<unsigned char *>(addr[dev]);
+    }
+    float *v0 = reinterpret_cast<float *>(base);
+    float *v1 = reinterpret_cast<float *>(base + NOALLOC_VEC_BYTES);
+    double *scal = reinterpret_cast<double *>(base + 2 * NOALLOC_VEC_BYTES);
+    unsigned *counter = reinterpret_cast<unsigned *>(base + 2 * NOALLOC_VEC_BYTES + 32 * sizeof(double));
+    double *sig1 = scal + 16, *sig2 = scal + 17, *shift = scal + 18;
+    int *info = reinterpret_cast<int *>(scal + 19);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the ticket must start at zero whatever an earlier call left behind
+    noalloc_reset_kernel<<<1, 32, 0, s>>>(counter);
+    if (cudaGetLastError() != cudaSuccess) return PSDPROJ_ECUDA;
+    if (launch_power_iteration(s, dA, n, lda, N, seed, 3u, nullptr, v0, v1, scal, counter, sig1) != cudaSuccess)
+        return PSDPROJ_ECUDA;
+    if (launch_power_iteration(s, dA, n, lda, N, seed, 4u, sig1, v0, v1, scal, counter, sig2) != cudaSuccess)
+        return PSDPROJ_ECUDA;
+    if (launch_alpha_finish(s, sig1, sig2, 0.0, d_alpha, shift, info) != cudaSuccess) return PSDPROJ_ECUDA;
+    if (d_sigma1 || d_sigma2) {
+        noalloc_copy_kernel<<<1, 1, 0, s>>>(sig1, sig2, d_sigma1, d_sigma2);
+        if (cudaGetLastError() != cudaSuccess) return PSDPROJ_ECUDA;
+    }
+    return PSDPROJ_OK;
 }
