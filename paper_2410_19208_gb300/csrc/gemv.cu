@@ -26,23 +26,18 @@ __global__ void __launch_bounds__(NTW)
 sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
                 const float *__restrict__ x, float *__restrict__ y, float *__restrict__ other,
                 double *scal, unsigned *counter, const double *d_shift_neg, double *d_sigma,
-                int nb, int vec)
+                unsigned nactive, int vec)
 {
     __shared__ float colsum[8][SEGW * TCW];
     __shared__ double red[NTW / 32];
     __shared__ bool s_last;
-    int64_t idx = blockIdx.x;
-    int I = 0;
-    for (; I < nb; ++I) {
-        const int64_t row0 = (int64_t)I * TRW;
-        const int tiles = (int)((n - row0 + TCW - 1) / TCW);
-        const int cnt = (tiles + SEGW - 1) / SEGW;
-        if (idx < cnt) break;
-        idx -= cnt;
-    }
+    // grid: x = segment within the block row, y = block row; segments past
+    // the end of a row exit at once (and take no completion ticket)
+    const int I = blockIdx.y;
     const int64_t row0 = (int64_t)I * TRW;
     const int tiles = (int)((n - row0 + TCW - 1) / TCW);
-    const int t0 = (int)idx * SEGW;
+    const int t0 = (int)blockIdx.x * SEGW;
+    if (t0 >= tiles) return;
     const float sc = (float)scal[0];
     const float shift = d_shift_neg ? (float)(-(*d_shift_neg)) : 0.0f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -146,7 +141,7 @@ sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
     // ticket: the last block finishes the product
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == nactive - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
@@ -210,12 +205,13 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
         const int tiles = (int)((n - (int64_t)I * TRW + TCW - 1) / TCW);
         blocks += (tiles + SEGW - 1) / SEGW;
     }
+    const int maxseg = (int)(((n + TCW - 1) / TCW + SEGW - 1) / SEGW);  // row 0 has the most
+    const dim3 grid((unsigned)maxseg, (unsigned)nb);
     const int vec = ((lda % 4) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     float *in = v0, *out = v1;
     for (int it = 0; it <= N; ++it) {
-        sym_gemv_kernel<<<(unsigned)blocks, NTW, 0, s>>>(A, n, lda, in, out, in, scal, counter,
-                                                         d_shift_neg, it == N ? d_sigma : nullptr,
-                                                         nb, vec);
+        sym_gemv_kernel<<<grid, NTW, 0, s>>>(A, n, lda, in, out, in, scal, counter, d_shift_neg,
+                                             it == N ? d_sigma : nullptr, (unsigned)blocks, vec);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         float *t = in; in = out; out = t;
