@@ -60,6 +60,11 @@ extern "C" {
 #define PSDPROJ_OUT_UPPER   1  /* only P[i*ldp + j], j >= i, written           */
 #define PSDPROJ_OUT_FACTOR  2  /* P not written; W = Q V sqrt(max(D,0)) only   */
 
+/* Small eigensolver used for eig(Q^T X Q) (Alg. 2 line 2, Alg. 3 line 3) */
+#define PSDPROJ_EIG_AUTO     0 /* tridiagonal solver, Jacobi when it flags a failure */
+#define PSDPROJ_EIG_JACOBI   1 /* parallel cyclic Jacobi only                     */
+#define PSDPROJ_EIG_TRIDIAG  2 /* tridiagonal solver only (failure: ENOCONV)      */
+
 typedef struct psdproj_ctx psdproj_ctx;
 
 typedef struct psdproj_opts {
@@ -67,7 +72,8 @@ typedef struct psdproj_opts {
     int syrk_prec;   /* PSDPROJ_PREC_FP32 or _BF16X3 for P = W W^T (default FP32)*/
     int N;           /* iterations of Alg. 4 inside Alg. 5 (default 10)          */
     int out_mode;    /* PSDPROJ_OUT_* (default FULL)                             */
-    int reserved[4]; /* must be zero                                             */
+    int eig;         /* PSDPROJ_EIG_* (default AUTO)                             */
+    int reserved[3]; /* must be zero                                             */
 } psdproj_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -195,13 +201,21 @@ int psdproj_cholqr2(psdproj_ctx *ctx, const float *dY, int64_t n, int64_t ldy,
 int psdproj_core(psdproj_ctx *ctx, const float *dX, int64_t ldx, const float *dZ,
                  int64_t ldz, int64_t n, int m, double *dC);
 
-/* Small symmetric eigensolver of Alg. 2 line 2 ("eig(Q^T X Q)"): parallel
- * cyclic Jacobi in one thread block on dC (m x m FP64 in, read only).
- * dV (m x m column-major FP32) receives orthonormal eigenvectors, dd (m
- * doubles) the eigenvalues; eigenpairs are sorted by decreasing eigenvalue.
- * Requires 1 <= m <= 256.  Non-convergence sets PSDPROJ_ENOCONV in the
+/* Small symmetric eigensolver of Alg. 2 line 2 ("eig(Q^T X Q)") on dC (m x m
+ * FP64 in, read only), in FP32 in one thread block.  dV (m x m column-major
+ * FP32) receives orthonormal eigenvectors, dd (m doubles) the eigenvalues;
+ * eigenpairs are sorted by decreasing eigenvalue.  Requires 1 <= m <= 256.
+ * psdproj_eig uses PSDPROJ_EIG_AUTO: Householder tridiagonalization,
+ * bisection, twisted-factorization eigenvectors and one Newton-Schulz
+ * orthogonalization step; when that solver flags a failure (a non-finite or
+ * inaccurate vector, V^T V far from I) the Jacobi solver recomputes the
+ * result on the device.  Jacobi non-convergence, or a failure of the
+ * tridiagonal solver under PSDPROJ_EIG_TRIDIAG, sets PSDPROJ_ENOCONV in the
  * device status. */
 int psdproj_eig(psdproj_ctx *ctx, const double *dC, int m, float *dV, double *dd);
+/* As psdproj_eig with the solver chosen by `method` (PSDPROJ_EIG_*). */
+int psdproj_eig_method(psdproj_ctx *ctx, const double *dC, int m, float *dV, double *dd,
+                       int method);
 
 /* Factor of Alg. 2 line 3: dW = Q V diag(sqrt(max(d, 0))) (n x m, column-
  * major; the r+ columns with d > 0 first, zero columns after), and *d_rank =

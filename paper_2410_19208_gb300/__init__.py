@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpsdproj.so")
 
 PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
 OUT_FULL, OUT_UPPER, OUT_FACTOR = 0, 1, 2
+EIG_AUTO, EIG_JACOBI, EIG_TRIDIAG = 0, 1, 2
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTFINITE", 4: "ENOCONV", 5: "ETIMEOUT",
           6: "ECUDA", 7: "ENOTSUP", 8: "ETOOLARGE"}
 
@@ -37,7 +38,7 @@ class PsdprojError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("syrk_prec", ctypes.c_int), ("N", ctypes.c_int),
-                ("out_mode", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("out_mode", ctypes.c_int), ("eig", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -77,6 +78,7 @@ def _load():
         "psdproj_cholqr2": (_int, [_P, _P, _i64, _i64, _int, _P, _i64, _P]),
         "psdproj_core": (_int, [_P, _P, _i64, _P, _i64, _i64, _int, _P]),
         "psdproj_eig": (_int, [_P, _P, _int, _P, _P]),
+        "psdproj_eig_method": (_int, [_P, _P, _int, _P, _P, _int]),
         "psdproj_factor": (_int, [_P, _P, _i64, _i64, _int, _P, _P, _P, _i64, _P]),
         "psdproj_syrk": (_int, [_P, _P, _i64, _i64, _int, _P, _P, _i64, _int, _int]),
         "psdproj_min_eig": (_int, [_P, _P, _i64, _i64, _int, _u64, _P, _P, _P]),
@@ -122,10 +124,11 @@ def tall_empty(n: int, m: int, device="cuda", ld: int | None = None):
     return torch.empty(m, ld, dtype=torch.float32, device=device).t()[:n]
 
 
-def make_opts(prec=PREC_FP32, syrk_prec=PREC_FP32, N=10, out_mode=OUT_FULL) -> Opts:
+def make_opts(prec=PREC_FP32, syrk_prec=PREC_FP32, N=10, out_mode=OUT_FULL,
+              eig=EIG_AUTO) -> Opts:
     o = Opts()
     _load().psdproj_default_opts(ctypes.byref(o))
-    o.prec, o.syrk_prec, o.N, o.out_mode = prec, syrk_prec, N, out_mode
+    o.prec, o.syrk_prec, o.N, o.out_mode, o.eig = prec, syrk_prec, N, out_mode, eig
     return o
 
 
@@ -226,9 +229,9 @@ class Context:
         _, _, ldz = _tall(Z, "Z")
         _check(_load().psdproj_core(self.h, _ptr(X), ldx, _ptr(Z), ldz, n, m, _ptr(C)), "core")
 
-    def eig(self, C, V, d):
+    def eig(self, C, V, d, method=EIG_AUTO):
         m = C.shape[0]
-        _check(_load().psdproj_eig(self.h, _ptr(C), m, _ptr(V), _ptr(d)), "eig")
+        _check(_load().psdproj_eig_method(self.h, _ptr(C), m, _ptr(V), _ptr(d), method), "eig")
 
     def factor(self, Q, V, d, W, rank=None):
         n, m, ldq = _tall(Q, "Q")

@@ -108,13 +108,39 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
     const size_t half_tall = align256(sizeof(uint16_t) * (size_t)ld * lp);
     const size_t small_d = align256(sizeof(double) * (size_t)lp * lp);
     const size_t small_f = align256(sizeof(float) * (size_t)lp * lp);
-    const size_t chol_scr = align256(sizeof(double) * ((size_t)lp * lp + lp));
-    size_t total = 5 * tall + 2 * half_tall + align256(sizeof(float) * nchunk * lp * lp) +
-                   3 * small_d + chol_scr + align256(sizeof(double) * lp) + 3 * small_f +
-                   align256(sizeof(float) * 2 * (size_t)(lp + 2) * (lp + 2)) +
-                   align256(sizeof(int) * lp) + 2 * align256(sizeof(float) * ld) +
-                   align256(sizeof(double) * 16) + align256(sizeof(unsigned) * 16) +
-                   align256(sizeof(int) * 16);
+    const size_t chol_scr = align256(sizeof(double) * ((size_t)lp * lp + lp) + sizeof(float) * (size_t)lp * lp);
+    // One carve-up serves both the size (base == nullptr: offsets only) and
+    // the pointers, so the two cannot disagree.
+    psd_workspace lay;
+    auto carve = [&](char *base) -> size_t {
+        size_t off = 0;
+        auto take = [&](size_t b) { char *q = base ? base + off : nullptr; off += align256(b); return q; };
+        lay.Om = reinterpret_cast<float *>(take(tall));
+        lay.Y = reinterpret_cast<float *>(take(tall));
+        lay.Q = reinterpret_cast<float *>(take(tall));
+        lay.T = reinterpret_cast<float *>(take(tall));
+        lay.W = reinterpret_cast<float *>(take(tall));
+        lay.Xhi = reinterpret_cast<uint16_t *>(take(half_tall));
+        lay.Xlo = reinterpret_cast<uint16_t *>(take(half_tall));
+        lay.gpart = reinterpret_cast<float *>(take(sizeof(float) * nchunk * lp * lp));
+        lay.G = reinterpret_cast<double *>(take(small_d));
+        lay.R = reinterpret_cast<double *>(take(small_d));
+        lay.C = reinterpret_cast<double *>(take(small_d));
+        lay.cholscr = reinterpret_cast<double *>(take(chol_scr));
+        lay.d = reinterpret_cast<double *>(take(sizeof(double) * lp));
+        lay.Rinv = reinterpret_cast<float *>(take(small_f));
+        lay.V = reinterpret_cast<float *>(take(small_f));
+        lay.M = reinterpret_cast<float *>(take(small_f));
+        lay.eigscr = reinterpret_cast<float *>(take(sizeof(float) * 3 * (size_t)(lp + 2) * (lp + 2)));
+        lay.dead = reinterpret_cast<int *>(take(sizeof(int) * lp));
+        lay.pv0 = reinterpret_cast<float *>(take(sizeof(float) * ld));
+        lay.pv1 = reinterpret_cast<float *>(take(sizeof(float) * ld));
+        lay.scal = reinterpret_cast<double *>(take(sizeof(double) * 16));
+        lay.counter = reinterpret_cast<unsigned *>(take(sizeof(unsigned) * 16));
+        lay.ints = reinterpret_cast<int *>(take(sizeof(int) * 16));
+        return off;
+    };
+    const size_t total = carve(nullptr);
     if (ws.base) {
         cudaStreamSynchronize(ctx->stream);
         free_workspace(ws);
@@ -122,36 +148,13 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
     void *base = nullptr;
     cudaError_t e = cudaMalloc(&base, total);
     if (e != cudaSuccess) return cuda_status(e);
+    carve(static_cast<char *>(base));
+    ws = lay;
     ws.base = base;
     ws.bytes = total;
     ws.n = nn;
     ws.lpad = lp;
     ws.ld = ld;
-    char *p = static_cast<char *>(base);
-    auto take = [&](size_t b) { char *q = p; p += b; return q; };
-    ws.Om = reinterpret_cast<float *>(take(tall));
-    ws.Y = reinterpret_cast<float *>(take(tall));
-    ws.Q = reinterpret_cast<float *>(take(tall));
-    ws.T = reinterpret_cast<float *>(take(tall));
-    ws.W = reinterpret_cast<float *>(take(tall));
-    ws.Xhi = reinterpret_cast<uint16_t *>(take(half_tall));
-    ws.Xlo = reinterpret_cast<uint16_t *>(take(half_tall));
-    ws.gpart = reinterpret_cast<float *>(take(align256(sizeof(float) * nchunk * lp * lp)));
-    ws.G = reinterpret_cast<double *>(take(small_d));
-    ws.R = reinterpret_cast<double *>(take(small_d));
-    ws.C = reinterpret_cast<double *>(take(small_d));
-    ws.cholscr = reinterpret_cast<double *>(take(chol_scr));
-    ws.d = reinterpret_cast<double *>(take(align256(sizeof(double) * lp)));
-    ws.Rinv = reinterpret_cast<float *>(take(small_f));
-    ws.V = reinterpret_cast<float *>(take(small_f));
-    ws.M = reinterpret_cast<float *>(take(small_f));
-    ws.eigscr = reinterpret_cast<float *>(take(align256(sizeof(float) * 2 * (size_t)(lp + 2) * (lp + 2))));
-    ws.dead = reinterpret_cast<int *>(take(align256(sizeof(int) * lp)));
-    ws.pv0 = reinterpret_cast<float *>(take(align256(sizeof(float) * ld)));
-    ws.pv1 = reinterpret_cast<float *>(take(align256(sizeof(float) * ld)));
-    ws.scal = reinterpret_cast<double *>(take(align256(sizeof(double) * 16)));
-    ws.counter = reinterpret_cast<unsigned *>(take(align256(sizeof(unsigned) * 16)));
-    ws.ints = reinterpret_cast<int *>(take(align256(sizeof(int) * 16)));
     // zero everything once: padded rows / columns of the tall buffers stay 0
     e = cudaMemsetAsync(base, 0, total, ctx->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -163,7 +166,7 @@ namespace {
 // scalar slots in ws.scal
 enum { SC_SHIFT = 4, SC_SIGMA1 = 5, SC_SIGMA2 = 6, SC_ALPHA = 7 };
 // int slots in ws.ints
-enum { IN_RANK = 0, IN_INFO = 1, IN_QRANK = 2 };
+enum { IN_RANK = 0, IN_INFO = 1, IN_QRANK = 2, IN_EIGFAIL = 3 };
 
 int check_opts(const psdproj_opts *o)
 {
@@ -171,6 +174,7 @@ int check_opts(const psdproj_opts *o)
     if (o->syrk_prec != PSDPROJ_PREC_FP32 && o->syrk_prec != PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
     if (o->out_mode < PSDPROJ_OUT_FULL || o->out_mode > PSDPROJ_OUT_FACTOR) return PSDPROJ_EINVAL;
     if (o->N < 0 || o->N > 10000) return PSDPROJ_EINVAL;
+    if (o->eig < PSDPROJ_EIG_AUTO || o->eig > PSDPROJ_EIG_TRIDIAG) return PSDPROJ_EINVAL;
     return PSDPROJ_OK;
 }
 
@@ -198,11 +202,11 @@ int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, flo
     const double tau = 1e-10;
     stage_scope st(ctx, PSDPROJ_STAGE_ORTH);
     PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1), 2);
-    PSD_KL(launch_cholesky(s, ws.G, m, ws.R, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status, 1,
+    PSD_KL(launch_cholesky(s, ws.G, m, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status, 1,
                            ws.cholscr), 1);
     PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, ws.T, ws.ld), 1);
     PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1), 2);
-    PSD_KL(launch_cholesky(s, ws.G, m, ws.R, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
+    PSD_KL(launch_cholesky(s, ws.G, m, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
                            ws.cholscr), 1);
     PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq), 1);
     return PSDPROJ_OK;
@@ -269,7 +273,8 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     }
     {
         stage_scope st(ctx, PSDPROJ_STAGE_EIG);
-        PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status), 1);
+        PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, opts.eig,
+                          ws.ints + IN_EIGFAIL), opts.eig == PSDPROJ_EIG_AUTO ? 2 : 1);
     }
     int *rk = ws.ints + IN_RANK;
     float *Wd = dW ? dW : ws.W;
@@ -547,14 +552,22 @@ int psdproj_core(psdproj_ctx *ctx, const float *dX, int64_t ldx, const float *dZ
     return PSDPROJ_OK;
 }
 
-int psdproj_eig(psdproj_ctx *ctx, const double *dC, int m, float *dV, double *dd)
+int psdproj_eig_method(psdproj_ctx *ctx, const double *dC, int m, float *dV, double *dd,
+                       int method)
 {
     if (!ctx || !dC || !dV || !dd || m < 1 || m > PSD_MAX_M) return PSDPROJ_EINVAL;
+    if (method < PSDPROJ_EIG_AUTO || method > PSDPROJ_EIG_TRIDIAG) return PSDPROJ_EINVAL;
     device_guard g(ctx->device);
     PSD_TRY(psd_ensure_workspace(ctx, 1, m));
     stage_scope st(ctx, PSDPROJ_STAGE_EIG);
-    PSD_KL(launch_eig(ctx->stream, dC, m, dV, dd, ctx->ws.eigscr, ctx->d_status), 1);
+    PSD_KL(launch_eig(ctx->stream, dC, m, dV, dd, ctx->ws.eigscr, ctx->d_status, method,
+                      ctx->ws.ints + IN_EIGFAIL), method == PSDPROJ_EIG_AUTO ? 2 : 1);
     return PSDPROJ_OK;
+}
+
+int psdproj_eig(psdproj_ctx *ctx, const double *dC, int m, float *dV, double *dd)
+{
+    return psdproj_eig_method(ctx, dC, m, dV, dd, PSDPROJ_EIG_AUTO);
 }
 
 int psdproj_factor(psdproj_ctx *ctx, const float *dQ, int64_t ldq, int64_t n, int m,

@@ -1,9 +1,15 @@
 // CholeskyQR steps of the orthonormalisation (QR 'econ' in Alg. 1):
-//   R = chol(G) (FP64 for the first pass of CholeskyQR2, FP32 for the second,
-//   whose Gram is I + O(eps)) with the dependent-column rule, R^-1 in FP32,
-//   and Q = Y R^-1 (a tall x small product on the CUDA cores).
-// The factorization is right-looking with two block barriers per column;
-// each thread owns a fixed set of upper-triangle entries.
+//   R = chol(G) (double-float for the first pass of CholeskyQR2, whose Gram
+//   of the raw product can be ill-conditioned; FP32 for the second, whose
+//   Gram is I + O(eps)), with the dependent-column rule; R^-1 in FP32; and
+//   Q = Y R^-1 (a tall x small product on the CUDA cores).
+// The factorization is right-looking in one thread block with two block
+// barriers per column; each thread owns a fixed set of upper-triangle
+// entries and every thread computes the pivot itself.  Double-float numbers
+// are unevaluated sums hi + lo of two FP32 values (about 48 significant
+// bits; Dekker's two-product by FMA and Knuth's two-sum), which keeps the
+// O(m^3) update off the FP64 pipe (about 2 FMA/clk/SM on this GPU).  Sizes
+// above 128 work in global memory with FP64 for the first pass.
 //
 // Dependent-column rule: column j is dependent when its pivot (the squared
 // norm of y_j after removing the earlier columns) is <= tau * max_i G_ii, or
@@ -16,44 +22,144 @@ namespace {
 constexpr int NT = 1024;
 constexpr int SMEM_M = 128;  // largest m kept in shared memory
 constexpr int EPT = (SMEM_M * (SMEM_M + 1) / 2 + NT - 1) / NT;  // upper entries per thread
+constexpr int CPL = PSD_MAX_M / 32;  // entries of an R^-1 column per lane
 
-// T = double: the first CholeskyQR pass (the Gram of the raw sketch, which can
-// be ill-conditioned); T = float: the second pass, whose Gram is I + O(eps).
+// ---- double-float arithmetic ------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df quick_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ df two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ df df_mul(df x, df y)
+{
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_sub(df x, df y)
+{
+    df s = two_sum(x.hi, -y.hi);
+    s.lo += x.lo - y.lo;
+    return quick_two_sum(s.hi, s.lo);
+}
+
+// ---- the three number types behind one interface ------------------------
+template <typename T> struct num;
+
+template <> struct num<float> {
+    __device__ static float from(double v) { return (float)v; }
+    __device__ static float hi(float v) { return v; }
+    __device__ static float zero() { return 0.0f; }
+    __device__ static float mul(float a, float b) { return a * b; }
+    __device__ static float fms(float u, float a, float b) { return fmaf(-a, b, u); }
+    // r = sqrt(p), inv = 1 / r
+    __device__ static void root(float p, float &r, float &inv)
+    {
+        r = sqrtf(p);
+        inv = 1.0f / r;
+    }
+    __device__ static float one() { return 1.0f; }
+};
+
+template <> struct num<double> {
+    __device__ static double from(double v) { return v; }
+    __device__ static float hi(double v) { return (float)v; }
+    __device__ static double zero() { return 0.0; }
+    __device__ static double mul(double a, double b) { return a * b; }
+    __device__ static double fms(double u, double a, double b) { return fma(-a, b, u); }
+    __device__ static void root(double p, double &r, double &inv)
+    {
+        r = sqrt(p);
+        inv = 1.0 / r;
+    }
+    __device__ static double one() { return 1.0; }
+};
+
+template <> struct num<df> {
+    __device__ static df from(double v)
+    {
+        const float h = (float)v;
+        return {h, (float)(v - (double)h)};
+    }
+    __device__ static float hi(df v) { return v.hi; }
+    __device__ static df zero() { return {0.0f, 0.0f}; }
+    __device__ static df mul(df a, df b) { return df_mul(a, b); }
+    __device__ static df fms(df u, df a, df b) { return df_sub(u, df_mul(a, b)); }
+    // one Newton step from the FP32 root: r = x + (p - x^2) / (2x); then
+    // inv = q + q (1 - q r) from q = 1 / r.hi
+    __device__ static void root(df p, df &r, df &inv)
+    {
+        const float x = sqrtf(p.hi);
+        const float x2 = x * x;
+        const df sq = {x2, fmaf(x, x, -x2)};
+        const df dlt = df_sub(p, sq);
+        r = quick_two_sum(x, dlt.hi / (2.0f * x));
+        const float q = 1.0f / r.hi;
+        const df qr = df_mul({q, 0.0f}, r);
+        const df res = df_sub({1.0f, 0.0f}, qr);
+        inv = quick_two_sum(q, res.hi * q);
+    }
+    __device__ static df one() { return {1.0f, 0.0f}; }
+};
+
+// T: df (first pass, m <= 128), double (first pass, m > 128) or float (second pass).
 template <typename T>
 __global__ void __launch_bounds__(NT)
-cholesky_kernel(const double *__restrict__ G, int m, double *R, float *Rinv,
-                int *__restrict__ dead, int *__restrict__ d_qrank, double tau, T *gU, T *growj,
+cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restrict__ dead,
+                int *__restrict__ d_qrank, double tau, T *gU, T *growj, float *gRf,
                 int *d_status)
 {
+    using N = num<T>;
     extern __shared__ __align__(16) unsigned char smraw[];
     const bool in_smem = m <= SMEM_M;
     const int ldu = in_smem ? (m + 1) : m;
-    T *U = in_smem ? reinterpret_cast<T *>(smraw) : gU;            // row-major upper triangle
+    T *U = in_smem ? reinterpret_cast<T *>(smraw) : gU;             // row-major upper triangle
     T *rowj = in_smem ? (U + m * (m + 1)) : growj;                  // scaled row j
-    float *Rs = in_smem ? reinterpret_cast<float *>(rowj + m) : nullptr;  // FP32 R (row-major)
+    float *Rf = in_smem ? reinterpret_cast<float *>(rowj + m) : gRf; // FP32 R (row-major, ldu)
     __shared__ double s_gmax;
     __shared__ int s_dead[PSD_MAX_M];
+    __shared__ float s_rdinv[PSD_MAX_M];
     __shared__ int s_bad;
-    __shared__ T s_r, s_inv;
-    __shared__ int s_dj;
     const int tid = threadIdx.x;
     const int nup = m * (m + 1) / 2;
 
     // U = upper(G)
     for (int e = tid; e < m * m; e += NT) {
         const int i = e / m, k = e - (e / m) * m;
-        if (k >= i) U[i * ldu + k] = (T)G[(int64_t)k * m + i];
+        if (k >= i) U[i * ldu + k] = N::from(G[(int64_t)k * m + i]);
     }
-    if (tid == 0) {
+    if (tid < 32) {
         double g = 0.0;
         int bad = 0;
-        for (int i = 0; i < m; ++i) {
+        for (int i = tid; i < m; i += 32) {
             const double v = G[(int64_t)i * m + i];
             if (!isfinite(v)) bad = 1;
             else if (v > g) g = v;
         }
-        s_gmax = g;
-        s_bad = bad;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+            bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        }
+        if (tid == 0) {
+            s_gmax = g;
+            s_bad = bad;
+        }
     }
     // this thread's upper-triangle entries (fixed for the whole factorization)
     int ei[EPT], ek[EPT];
@@ -75,29 +181,24 @@ cholesky_kernel(const double *__restrict__ G, int m, double *R, float *Rinv,
     }
     __syncthreads();
     if (s_bad) psd_set_status(d_status, PSDPROJ_ENOTFINITE);
-    const T thr = (T)(tau * s_gmax);
+    const float thr = (float)(tau * s_gmax);
     const bool any = s_gmax > 0.0;
 
     for (int j = 0; j < m; ++j) {
-        // phase A: pivot (one thread: FP64 sqrt and division are slow on
-        // this GPU) and scaled row j
-        if (tid == 0) {
-            const T piv = U[j * ldu + j];
-            const bool d0 = !(piv > thr) || !any;
-            const T r0 = d0 ? (T)1 : (T)sqrt(piv);
-            s_r = r0;
-            s_inv = (T)1 / r0;
-            s_dj = d0 ? 1 : 0;
-        }
-        __syncthreads();
-        const bool dj = s_dj != 0;
-        const T r = s_r, inv = s_inv;
+        // phase A: every thread forms the pivot; row j of R into rowj and Rf
+        const T piv = U[j * ldu + j];
+        const bool dj = !(N::hi(piv) > thr) || !any;
+        T r = N::one(), inv = N::one();
+        if (!dj) N::root(piv, r, inv);
         for (int k = j + tid; k < m; k += NT) {
-            const T v = (k == j) ? r : (dj ? (T)0 : U[j * ldu + k] * inv);
-            U[j * ldu + k] = v;
-            rowj[k] = (k == j) ? (T)0 : v;
+            const T v = (k == j) ? r : (dj ? N::zero() : N::mul(U[j * ldu + k], inv));
+            rowj[k] = (k == j) ? N::zero() : v;
+            Rf[j * ldu + k] = N::hi(v);
         }
-        if (tid == 0) s_dead[j] = dj ? 1 : 0;
+        if (tid == 0) {
+            s_dead[j] = dj ? 1 : 0;
+            s_rdinv[j] = 1.0f / N::hi(r);
+        }
         __syncthreads();
         // phase B: trailing update U(i,k) -= R(j,i) R(j,k), j < i <= k
         if (!dj) {
@@ -106,7 +207,7 @@ cholesky_kernel(const double *__restrict__ G, int m, double *R, float *Rinv,
                 for (int c = 0; c < EPT; ++c) {
                     if (ei[c] > j) {
                         const int i = ei[c], k = ek[c];
-                        U[i * ldu + k] -= rowj[i] * rowj[k];
+                        U[i * ldu + k] = N::fms(U[i * ldu + k], rowj[i], rowj[k]);
                     }
                 }
             } else {
@@ -115,40 +216,39 @@ cholesky_kernel(const double *__restrict__ G, int m, double *R, float *Rinv,
                     const int a = e / t, b = e - (e / t) * t;
                     if (b < a) continue;
                     const int i = j + 1 + a, k = j + 1 + b;
-                    U[i * ldu + k] -= rowj[i] * rowj[k];
+                    U[i * ldu + k] = N::fms(U[i * ldu + k], rowj[i], rowj[k]);
                 }
             }
         }
         __syncthreads();
     }
 
-    // R (column-major FP64) and an FP32 copy for the inverse
-    for (int e = tid; e < m * m; e += NT) {
-        const int i = e % m, k = e / m;  // (row i, column k)
-        const T u = (k >= i) ? U[i * ldu + k] : (T)0;
-        R[(int64_t)k * m + i] = (double)u;
-        if (in_smem) Rs[i * ldu + k] = (float)u;
-    }
-    __syncthreads();
-    // R^-1 (upper, FP32): one warp per column j, back substitution
-    //   x_j = 1 / R_jj;  x_i = -(sum_{i<k<=j} R_ik x_k) / R_ii  (i = j-1 .. 0)
-    // x is kept in the output column of Rinv (column-major, ld m).
+    // R^-1 (upper, FP32), one warp per column j: back substitution in axpy
+    // form with the column held in registers (lane l owns rows l + 32 c):
+    //   for i = j .. 0:  x_i = b_i / R_ii;  b_r -= x_i R_ri  (r < i),  b = e_j
     const int warp = tid >> 5, lane = tid & 31;
     for (int j = warp; j < m; j += NT / 32) {
-        float *x = Rinv + (int64_t)j * m;
-        for (int i = lane; i < m; i += 32) x[i] = 0.0f;
-        __syncwarp();
-        auto Rget = [&](int i, int k) -> float {
-            return in_smem ? Rs[i * ldu + k] : (float)R[(int64_t)k * m + i];
-        };
-        if (lane == 0) x[j] = 1.0f / Rget(j, j);
-        __syncwarp();
-        for (int i = j - 1; i >= 0; --i) {
-            float sacc = 0.0f;
-            for (int k = i + 1 + lane; k <= j; k += 32) sacc = fmaf(Rget(i, k), x[k], sacc);
-            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-            if (lane == 0) x[i] = -sacc / Rget(i, i);
-            __syncwarp();
+        float b[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) b[c] = (lane + 32 * c == j) ? 1.0f : 0.0f;
+        for (int i = j; i >= 0; --i) {
+            const int ci = i >> 5;
+            float v = 0.0f;
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) v = (c == ci) ? b[c] : v;
+            v = __shfl_sync(0xffffffffu, v, i & 31);
+            const float xi = v * s_rdinv[i];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+                const int r = lane + 32 * c;
+                if (r == i) b[c] = xi;
+                else if (r < i) b[c] = fmaf(-xi, Rf[r * ldu + i], b[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int r = lane + 32 * c;
+            if (r < m) Rinv[(int64_t)j * m + r] = b[c];
         }
     }
     for (int j = tid; j < m; j += NT) dead[j] = s_dead[j];
@@ -220,26 +320,31 @@ tall_small_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m,
 
 }  // namespace
 
-cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, double *R, float *Rinv,
-                            int *dead, int *d_qrank, double tau, int *d_status, int fp64,
+cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv, int *dead,
+                            int *d_qrank, double tau, int *d_status, int first_pass,
                             double *gscratch)
 {
-    // large m works in global memory (gscratch: m*m + m doubles)
-    if (fp64) {
-        const size_t smem = m <= SMEM_M ? (sizeof(double) * (m * (m + 1) + m) + sizeof(float) * m * (m + 1)) : 0;
-        cudaError_t e = cudaFuncSetAttribute(cholesky_kernel<double>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // large m works in global memory: gscratch holds U (m*m), rowj (m) in
+    // the factorization type and the FP32 copy of R (m*m floats)
+    const bool sm_path = m <= SMEM_M;
+    float *gRf = reinterpret_cast<float *>(gscratch + (size_t)m * m + m);
+    cudaError_t e;
+    if (first_pass && sm_path) {
+        const size_t smem = sizeof(df) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1);
+        e = cudaFuncSetAttribute(cholesky_kernel<df>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        cholesky_kernel<double><<<1, NT, smem, s>>>(G, m, R, Rinv, dead, d_qrank, tau, gscratch,
-                                                    gscratch + (size_t)m * m, d_status);
+        cholesky_kernel<df><<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, nullptr, nullptr,
+                                                nullptr, d_status);
+    } else if (first_pass) {
+        cholesky_kernel<double><<<1, NT, 0, s>>>(G, m, Rinv, dead, d_qrank, tau, gscratch,
+                                                 gscratch + (size_t)m * m, gRf, d_status);
     } else {
         float *fs = reinterpret_cast<float *>(gscratch);
-        const size_t smem = m <= SMEM_M ? (sizeof(float) * (m * (m + 1) + m) + sizeof(float) * m * (m + 1)) : 0;
-        cudaError_t e = cudaFuncSetAttribute(cholesky_kernel<float>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t smem = sm_path ? sizeof(float) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1) : 0;
+        e = cudaFuncSetAttribute(cholesky_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        cholesky_kernel<float><<<1, NT, smem, s>>>(G, m, R, Rinv, dead, d_qrank, tau, fs,
-                                                   fs + (size_t)m * m, d_status);
+        cholesky_kernel<float><<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, fs, fs + (size_t)m * m,
+                                                   gRf, d_status);
     }
     return cudaGetLastError();
 }

@@ -98,10 +98,12 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
                         int64_t ldz, int64_t n, int m, float *gpart, double *G,
                         int symmetrize);
 
-// fp64 = 1: FP64 factorization; 0: FP32.  gscratch: (m*m + m) doubles of
-// device memory, used when m > 128.
-cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, double *R, float *Rinv,
-                            int *dead, int *d_qrank, double tau, int *d_status, int fp64,
+// first_pass = 1: double-float factorization (FP64 when m > 128); 0: FP32.
+// Writes R^-1 (m x m column-major FP32), the dependent-column flags and
+// (d_qrank, may be NULL) the number of independent columns.  gscratch:
+// (m*m + m) doubles + m*m floats of device memory, used when m > 128.
+cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv, int *dead,
+                            int *d_qrank, double tau, int *d_status, int first_pass,
                             double *gscratch);
 
 // Y (n x m) times a small m x c matrix B (column-major, ld = m) -> Z (n x c).
@@ -112,10 +114,13 @@ cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64
                               const float *B, int c, const int *colmask, const int *d_cols,
                               float *Z, int64_t ldz);
 
-// scratch: 2 (m+2)^2 floats of device memory (used when m is too large for
-// shared memory)
+// scratch: 3 (m+2)^2 floats of device memory (used when m is too large for
+// shared memory); d_flag: one device int (the tridiagonal solver's failure
+// flag); method: PSDPROJ_EIG_*.
 cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double *d,
-                       float *scratch, int *d_status);
+                       float *scratch, int *d_status, int method, int *d_flag);
+cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V, double *d,
+                               float *scratch, int *d_fail, int *d_status_on_fail);
 
 cudaError_t launch_factor_prep(cudaStream_t s, const float *V, const double *d, int m,
                                float *M, int *d_rank);

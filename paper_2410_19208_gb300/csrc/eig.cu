@@ -1,5 +1,8 @@
 // Small symmetric eigensolver of Alg. 2 line 2 / Alg. 3 line 3 ("eig(Q^T X Q)"):
-// parallel cyclic Jacobi in one thread block.
+// parallel cyclic Jacobi in one thread block.  Used on its own
+// (PSDPROJ_EIG_JACOBI) or as the fallback of the tridiagonal solver
+// (eig_tridiag.cu), in which case it runs only when that solver's failure
+// flag is set.
 //
 // The m x m core is held in shared memory in FP32 (GB300's FP64 pipe runs at
 // about 2 FMA/clk/SM, so an FP64 Jacobi on 112 x 112 would take ~17 ms; the
@@ -29,8 +32,10 @@ constexpr int MAXH = PSD_MAX_M / 2;
 __global__ void __launch_bounds__(NT, 1)
 eig_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
            double *__restrict__ dout, float *gA, float *gV, int smem_A, int smem_V,
-           int *d_status)
+           int *d_status, const int *only_if)
 {
+    // fallback use: run only when the tridiagonal solver flagged a failure
+    if (only_if && *only_if == 0) return;
     extern __shared__ float sm[];
     const int mm = m + (m & 1);           // even size (ghost index when m is odd)
     const int ld = mm + 1;
@@ -38,7 +43,7 @@ eig_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
     float *A = smem_A ? sm : gA;
     float *Vt = smem_V ? (sm + (smem_A ? ((mm * ld + 3) & ~3) : 0)) : gV;
     __shared__ int rp[MAXH], rq[MAXH];
-    __shared__ float rc[MAXH], rs[MAXH], rt[MAXH], rtau[MAXH];
+    __shared__ float rs[MAXH], rt[MAXH], rtau[MAXH];
     __shared__ int s_rot;
     __shared__ float s_fro;
     __shared__ float red[2][NT / 32];
@@ -113,7 +118,7 @@ eig_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
                     s = t * c;
                     s_rot = 1;  // any rotation in this sweep (plain store: same value)
                 }
-                rp[tid] = p; rq[tid] = q; rc[tid] = c; rs[tid] = s; rt[tid] = t;
+                rp[tid] = p; rq[tid] = q; rs[tid] = s; rt[tid] = t;
                 rtau[tid] = s / (1.0f + c);
             }
             __syncthreads();
@@ -207,8 +212,15 @@ eig_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
 }  // namespace
 
 cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double *d,
-                       float *scratch, int *d_status)
+                       float *scratch, int *d_status, int method, int *d_flag)
 {
+    const int *only_if = nullptr;
+    if (method != PSDPROJ_EIG_JACOBI) {
+        cudaError_t e = launch_eig_tridiag(s, C, m, V, d, scratch, d_flag,
+                                           method == PSDPROJ_EIG_TRIDIAG ? d_status : nullptr);
+        if (e != cudaSuccess || method == PSDPROJ_EIG_TRIDIAG) return e;
+        only_if = d_flag;
+    }
     const int mm = m + (m & 1);
     const size_t matA = sizeof(float) * (((size_t)mm * (mm + 1) + 3) & ~(size_t)3);
     const size_t matV = sizeof(float) * (size_t)mm * (mm + 4);
@@ -221,6 +233,6 @@ cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double 
     cudaError_t e = cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    eig_kernel<<<1, NT, smem, s>>>(C, m, V, d, gA, gV, smem_A, smem_V, d_status);
+    eig_kernel<<<1, NT, smem, s>>>(C, m, V, d, gA, gV, smem_A, smem_V, d_status, only_if);
     return cudaGetLastError();
 }

@@ -1,0 +1,483 @@
+// Small symmetric eigensolver of Alg. 2 line 2 / Alg. 3 line 3 ("eig(Q^T X Q)")
+// by tridiagonalization, in one thread block, FP32:
+//
+//   1. Householder reduction C = H T H^T (H = H_0 ... H_{m-3}), column by
+//      column on the full matrix in shared memory; the reflector vectors are
+//      kept below the subdiagonal.
+//   2. Eigenvalues of T by bisection on Sturm counts (the number of negative
+//      pivots of the LDL^T factorization of T - x I), four lanes per
+//      eigenvalue evaluating four points per step (5-way multisection).
+//   3. Eigenvectors of T from the twisted factorization of T - lambda I
+//      (forward pivots d+, backward pivots d-, twist index r = argmin
+//      |d+_r + d-_r - (d_r - lambda)|, then the two recurrences from r).
+//      Eigenvalues closer than 1e-4 ||T|| form a cluster; its members take
+//      distinct twist indices and are re-orthogonalised (modified
+//      Gram-Schmidt) against the earlier members.
+//   4. Back-transformation V = H Z.
+//   5. One Newton-Schulz step towards the orthogonal polar factor,
+//      V <- V (3I - V^T V)/2: the twisted vectors of neighbouring eigenvalues
+//      are orthogonal only to ~eps ||T|| / gap (~1e-5 here); the step makes
+//      the error quadratic (~1e-10) and mixes each pair symmetrically, which
+//      moves V Lambda_+ V^T by O(eps ||T||) only.
+// Output as the Jacobi solver: V (m x m column-major, orthonormal columns)
+// and the eigenvalues, sorted by decreasing eigenvalue.  *d_fail is set to
+// 1 when a vector is not finite, a twisted residual is large, or V^T V is
+// far from I; the caller then runs the Jacobi solver, which reads the flag.
+// Cost is O(m^3) work with O(m) block barriers, against O(m^3) work with
+// O(m^2) barriers for cyclic Jacobi.
+#include "ctx.h"
+
+namespace {
+
+constexpr int NT = 512;
+constexpr int SMEM_M = 128;   // largest m kept in shared memory
+constexpr int NBIS = 16;      // multisection steps: 5^16 > 2^37
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// number of eigenvalues of tridiag(d, e) below x (ee = e^2)
+__device__ __forceinline__ int sturm(const float *d, const float *ee, int m, float x, float pivmin)
+{
+    float q = d[0] - x;
+    int c = q < 0.0f;
+    for (int i = 1; i < m; ++i) {
+        if (fabsf(q) < pivmin) q = -pivmin;
+        q = (d[i] - x) - ee[i - 1] / q;
+        c += q < 0.0f;
+    }
+    return c;
+}
+
+// twisted eigenvector of T for lambda into z (column stride ldz), using t
+// (same stride) as scratch; *gamma_out = |gamma_r| at the twist index r,
+// which is returned.
+__device__ int twisted_vector(const float *d, const float *e, int m, float lambda, float pivmin,
+                              float *z, float *t, int ldz, float *gamma_out)
+{
+    // forward pivots d+ kept in z
+    float dp = d[0] - lambda;
+    for (int i = 0; i < m; ++i) {
+        if (fabsf(dp) < pivmin) dp = -pivmin;
+        z[i * ldz] = dp;
+        if (i + 1 < m) dp = (d[i + 1] - lambda) - e[i] * e[i] / dp;
+    }
+    // backward pivots d-, ratios u- kept in t, twist by the smallest |gamma|
+    float dm = d[m - 1] - lambda;
+    int r = -1;
+    float best = 0.0f;
+    for (int i = m - 1; i >= 0; --i) {
+        if (fabsf(dm) < pivmin) dm = -pivmin;
+        const float g = z[i * ldz] + dm - (d[i] - lambda);
+        if (r < 0 || fabsf(g) < best) {
+            best = fabsf(g);
+            r = i;
+        }
+        if (i > 0) {
+            const float u = e[i - 1] / dm;   // u-_{i-1}
+            t[(i - 1) * ldz] = u;
+            dm = (d[i - 1] - lambda) - u * e[i - 1];
+        }
+    }
+    if (r < 0) r = 0;
+    *gamma_out = best;
+    // z_r = 1; downward z_i = -(e_i / d+_i) z_{i+1}; upward z_i = -u-_{i-1} z_{i-1}
+    float zi = 1.0f;
+    for (int i = r - 1; i >= 0; --i) {
+        zi = -(e[i] / z[i * ldz]) * zi;
+        z[i * ldz] = zi;
+    }
+    zi = 1.0f;
+    for (int i = r + 1; i < m; ++i) {
+        zi = -t[(i - 1) * ldz] * zi;
+        z[i * ldz] = zi;
+    }
+    z[r * ldz] = 1.0f;
+    return r;
+}
+
+// pseudo-random value in [-1, 1) for entry i of start vector k (integer hash)
+__device__ __forceinline__ float hash_uniform(int i, int k)
+{
+    uint32_t x = (uint32_t)i * 0x9E3779B1u + (uint32_t)k * 0x85EBCA77u + 0x165667B1u;
+    x ^= x >> 15;
+    x *= 0x2C1B3C6Du;
+    x ^= x >> 12;
+    x *= 0x297A2D39u;
+    x ^= x >> 15;
+    return (float)x * 4.656612873e-10f - 1.0f;
+}
+
+// One step of inverse iteration x <- (T - lambda I)^{-1} x through
+// T - lambda I = L D L^T (pivots below piv in magnitude are replaced by
+// -piv), then x scaled to unit 2-norm.  dp (stride ld) holds the pivots.
+// The vector is rescaled by 1e-20 whenever an entry passes 1e20, which
+// keeps the solve finite for any shift.
+__device__ void inverse_step(const float *d, const float *e, int m, float lambda, float piv,
+                             float *x, float *dp, int ld)
+{
+    constexpr float BIG = 1e20f, SMALL = 1e-20f;
+    float q = d[0] - lambda;
+    for (int i = 0; i < m; ++i) {
+        if (fabsf(q) < piv) q = -piv;
+        dp[i * ld] = q;
+        if (i + 1 < m) q = (d[i + 1] - lambda) - e[i] * e[i] / q;
+    }
+    // L y = x
+    float yp = x[0];
+    for (int i = 1; i < m; ++i) {
+        float y = x[i * ld] - (e[i - 1] / dp[(i - 1) * ld]) * yp;
+        if (fabsf(y) > BIG) {
+            for (int j = 0; j < i; ++j) x[j * ld] *= SMALL;
+            y *= SMALL;
+        }
+        x[i * ld] = y;
+        yp = y;
+    }
+    // D L^T x = y
+    float xn = x[(m - 1) * ld] / dp[(m - 1) * ld];
+    if (fabsf(xn) > BIG) {
+        for (int j = 0; j < m - 1; ++j) x[j * ld] *= SMALL;
+        xn *= SMALL;
+    }
+    x[(m - 1) * ld] = xn;
+    for (int i = m - 2; i >= 0; --i) {
+        float xi = x[i * ld] / dp[i * ld] - (e[i] / dp[i * ld]) * xn;
+        if (fabsf(xi) > BIG) {
+            for (int j = 0; j < m; ++j) x[j * ld] *= SMALL;
+            xi *= SMALL;
+        }
+        x[i * ld] = xi;
+        xn = xi;
+    }
+    float mx = 0.0f;
+    for (int i = 0; i < m; ++i) mx = fmaxf(mx, fabsf(x[i * ld]));
+    const float sc = mx > 0.0f ? 1.0f / mx : 1.0f;
+    float nrm = 0.0f;
+    for (int i = 0; i < m; ++i) {
+        const float v = x[i * ld] * sc;
+        nrm = fmaf(v, v, nrm);
+    }
+    const float inv = sc / sqrtf(nrm);
+    for (int i = 0; i < m; ++i) x[i * ld] *= inv;
+}
+
+__global__ void __launch_bounds__(NT, 1)
+eig_tridiag_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
+                   double *__restrict__ dout, float *gscr, int *__restrict__ d_fail,
+                   int *d_status_on_fail)
+{
+    extern __shared__ float sm[];
+    const bool in_smem = m <= SMEM_M;
+    const int ld = m + 1;
+    float *A = in_smem ? sm : gscr;                 // m x ld, row-major
+    float *Z = A + m * ld;                          // eigenvectors of T (row i, column k)
+    float *T = Z + m * ld;                          // scratch of the twisted factorization
+    __shared__ float d[PSD_MAX_M], e[PSD_MAX_M], ee[PSD_MAX_M], beta[PSD_MAX_M];
+    __shared__ float vv[PSD_MAX_M], pp[PSD_MAX_M], lam[PSD_MAX_M];
+    __shared__ float red[NT / 32];
+    __shared__ int cl_start[PSD_MAX_M];
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_fail = 0;
+
+    for (int e0 = tid; e0 < m * m; e0 += NT) {
+        const int i = e0 / m, j = e0 - (e0 / m) * m;
+        A[i * ld + j] = (float)C[(int64_t)j * m + i];
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- 1
+    for (int j = 0; j + 2 < m; ++j) {
+        const int r0 = j + 1;                       // first row of the trailing block
+        // squared norm of x = A[r0.., j] below its first entry
+        float part = 0.0f;
+        for (int i = r0 + 1 + tid; i < m; i += NT) part = fmaf(A[i * ld + j], A[i * ld + j], part);
+        part = warp_sum(part);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
+        float tail = 0.0f;
+        for (int w = 0; w < NT / 32; ++w) tail += red[w];
+        const float x0 = A[r0 * ld + j];
+        const bool skip = !(tail > 0.0f);           // column already tridiagonal
+        const float sigma = sqrtf(fmaf(x0, x0, tail));
+        const float alpha = -copysignf(sigma, x0);
+        const float bt = skip ? 0.0f : 1.0f / (sigma * sigma - alpha * x0);
+        for (int i = r0 + tid; i < m; i += NT) vv[i] = (i == r0) ? (x0 - alpha) : A[i * ld + j];
+        if (tid == 0) {
+            d[j] = A[j * ld + j];
+            e[j] = skip ? x0 : alpha;
+            beta[j] = bt;
+        }
+        __syncthreads();                            // vv ready; red reusable
+        if (skip) {
+            // keep a zero reflector below the subdiagonal
+            for (int i = r0 + tid; i < m; i += NT) A[i * ld + j] = 0.0f;
+            __syncthreads();
+            continue;
+        }
+        // p = bt A22 v (thread per row) and v^T p
+        float pv = 0.0f;
+        for (int i = r0 + tid; i < m; i += NT) {
+            const float *row = A + i * ld;
+            float s0 = 0.0f, s1 = 0.0f;
+            int k = r0;
+            for (; k + 1 < m; k += 2) {
+                s0 = fmaf(row[k], vv[k], s0);
+                s1 = fmaf(row[k + 1], vv[k + 1], s1);
+            }
+            if (k < m) s0 = fmaf(row[k], vv[k], s0);
+            const float p = bt * (s0 + s1);
+            pp[i] = p;
+            pv = fmaf(p, vv[i], pv);
+        }
+        pv = warp_sum(pv);
+        if (lane == 0) red[warp] = pv;
+        __syncthreads();
+        float vtp = 0.0f;
+        for (int w = 0; w < NT / 32; ++w) vtp += red[w];
+        const float K = 0.5f * bt * vtp;
+        // A22 -= v w^T + w v^T with w = p - K v; the reflector goes below the subdiagonal
+        const int L = m - r0;
+        for (int q = tid; q < L * L; q += NT) {
+            const int a = q / L, b = q - (q / L) * L;
+            const int i = r0 + a, k = r0 + b;
+            const float wi = pp[i] - K * vv[i], wk = pp[k] - K * vv[k];
+            A[i * ld + k] -= vv[i] * wk + wi * vv[k];
+        }
+        for (int i = r0 + tid; i < m; i += NT) A[i * ld + j] = vv[i];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (m >= 2) {
+            d[m - 2] = A[(m - 2) * ld + (m - 2)];
+            e[m - 2] = A[(m - 1) * ld + (m - 2)];
+            beta[m - 2] = 0.0f;
+        }
+        d[m - 1] = A[(m - 1) * ld + (m - 1)];
+        e[m - 1] = 0.0f;
+        beta[m - 1] = 0.0f;
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- 2
+    __shared__ float s_gl, s_gu, s_pivmin, s_tnorm;
+    if (tid == 0) {
+        float gl = 3.0e38f, gu = -3.0e38f, emax = 0.0f;
+        for (int i = 0; i < m; ++i) {
+            const float r = (i > 0 ? fabsf(e[i - 1]) : 0.0f) + (i + 1 < m ? fabsf(e[i]) : 0.0f);
+            gl = fminf(gl, d[i] - r);
+            gu = fmaxf(gu, d[i] + r);
+            if (i + 1 < m) emax = fmaxf(emax, e[i] * e[i]);
+        }
+        const float tn = fmaxf(fabsf(gl), fabsf(gu));
+        const float pad = 2.0f * 1.2e-7f * tn + 1e-30f;
+        s_gl = gl - pad;
+        s_gu = gu + pad;
+        s_tnorm = tn;
+        s_pivmin = fmaxf(1e-30f, 1e-30f * emax);
+    }
+    for (int i = tid; i < m; i += NT) ee[i] = (i + 1 < m) ? e[i] * e[i] : 0.0f;
+    __syncthreads();
+    const float pivmin = s_pivmin;
+    for (int base = 0; base < m; base += NT / 4) {
+        const int k = base + (tid >> 2);            // eigenvalue index (ascending)
+        const int sub = tid & 3;
+        float lo = s_gl, hi = s_gu;
+        for (int it = 0; it < NBIS; ++it) {
+            const float x = lo + (hi - lo) * (float)(sub + 1) * 0.2f;
+            const int c = (k < m) ? sturm(d, ee, m, x, pivmin) : 0;
+            // new interval: [largest x with count <= k, smallest x with count > k]
+            const unsigned lmask = 0xFu << (lane & ~3);
+            const unsigned below = __ballot_sync(0xffffffffu, c <= k) & lmask;
+            const int nb = __popc(below);           // points at or below lambda_k
+            const float nlo = nb > 0 ? lo + (hi - lo) * (float)nb * 0.2f : lo;
+            const float nhi = nb < 4 ? lo + (hi - lo) * (float)(nb + 1) * 0.2f : hi;
+            lo = nlo;
+            hi = nhi;
+        }
+        if (k < m && sub == 0) lam[k] = 0.5f * (lo + hi);
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- 3
+    // clusters: runs of eigenvalues closer than 1e-4 ||T||
+    const float ctol = 1e-4f * s_tnorm + 1e-30f;
+    const float pivsolve = fmaxf(1.2e-7f * s_tnorm, 1e-30f);
+    for (int k = tid; k < m; k += NT) {
+        int s = k;
+        while (s > 0 && lam[s] - lam[s - 1] <= ctol) --s;
+        cl_start[k] = s;
+    }
+    __syncthreads();
+    // isolated eigenvalues: twisted factorization, one thread each;
+    // cluster members: pseudo-random start vectors
+    for (int k = tid; k < m; k += NT) {
+        float *z = Z + k, *t = T + k;
+        const bool single = cl_start[k] == k && !(k + 1 < m && cl_start[k + 1] == k);
+        if (!single) {
+            for (int i = 0; i < m; ++i) z[i * ld] = hash_uniform(i, k);
+            continue;
+        }
+        float gam;
+        twisted_vector(d, e, m, lam[k], pivmin, z, t, ld, &gam);
+        float nrm = 0.0f;
+        for (int i = 0; i < m; ++i) nrm = fmaf(z[i * ld], z[i * ld], nrm);
+        const float inv = 1.0f / sqrtf(nrm);
+        for (int i = 0; i < m; ++i) z[i * ld] *= inv;
+        // ||(T - lambda I) z|| = |gamma_r| / ||z|| for the twisted solution
+        if (!(nrm >= 1.0f && isfinite(nrm)) || !(gam * inv <= 1e-3f * s_tnorm + 1e-20f)) s_fail = 1;
+    }
+    __syncthreads();
+    // clusters, one warp each: two steps of inverse iteration, each member
+    // with its own shift (lanes in parallel), then modified Gram-Schmidt
+    // over the members in order (the warp together): subspace iteration
+    // onto the cluster's invariant subspace
+    {
+        int cid = 0;
+        for (int s = 0; s < m; ++s) {
+            if (cl_start[s] != s) continue;
+            int g = 1;
+            while (s + g < m && cl_start[s + g] == s) ++g;
+            if (g == 1) continue;
+            if ((cid++ % (NT / 32)) != warp) continue;
+            for (int it = 0; it < 2; ++it) {
+                for (int k = s + lane; k < s + g; k += 32)
+                    inverse_step(d, e, m, lam[k], pivsolve, Z + k, T + k, ld);
+                __syncwarp();
+                for (int k = s; k < s + g; ++k) {
+                    float *z = Z + k;
+                    for (int pass = 0; pass < 2; ++pass) {
+                        for (int o = s; o < k; ++o) {
+                            float dot = 0.0f;
+                            for (int i = lane; i < m; i += 32) dot = fmaf(Z[i * ld + o], z[i * ld], dot);
+                            dot = warp_sum(dot);
+                            for (int i = lane; i < m; i += 32) z[i * ld] = fmaf(-dot, Z[i * ld + o], z[i * ld]);
+                            __syncwarp();
+                        }
+                    }
+                    float nrm = 0.0f;
+                    for (int i = lane; i < m; i += 32) nrm = fmaf(z[i * ld], z[i * ld], nrm);
+                    nrm = warp_sum(nrm);
+                    const float inv = 1.0f / sqrtf(nrm);
+                    for (int i = lane; i < m; i += 32) z[i * ld] *= inv;
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- 4
+    // Z <- H_j Z for j = m-3 .. 0, H_j = I - beta_j v_j v_j^T, v_j = A[j+1.., j]
+    for (int j = m - 3; j >= 0; --j) {
+        const float bt = beta[j];
+        if (bt == 0.0f) continue;                   // uniform across the block
+        const int r0 = j + 1;
+        // pp[c] = bt v^T Z[:, c]
+        for (int c = tid; c < m; c += NT) {
+            float s0 = 0.0f;
+            for (int i = r0; i < m; ++i) s0 = fmaf(A[i * ld + j], Z[i * ld + c], s0);
+            pp[c] = bt * s0;
+        }
+        __syncthreads();
+        const int L = m - r0;
+        for (int q = tid; q < L * m; q += NT) {
+            const int a = q / m, c = q - (q / m) * m;
+            const int i = r0 + a;
+            Z[i * ld + c] -= A[i * ld + j] * pp[c];
+        }
+        __syncthreads();
+    }
+
+    // ---------------------------------------------------------------- 5
+    // S = (3I - Z^T Z)/2 into T, then Z S into A (4 x 4 register tiles)
+    __shared__ unsigned s_dev;
+    if (tid == 0) s_dev = 0u;
+    __syncthreads();
+    const int nt4 = (m + 3) >> 2;
+    for (int q = tid; q < nt4 * nt4; q += NT) {
+        const int a0 = (q / nt4) * 4, b0 = (q - (q / nt4) * nt4) * 4;
+        float acc[4][4] = {};
+        for (int i = 0; i < m; ++i) {
+            const float *zr = Z + i * ld;
+            float x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[u] = (a0 + u < m) ? zr[a0 + u] : 0.0f;
+                y[u] = (b0 + u < m) ? zr[b0 + u] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+        }
+        float dev = 0.0f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int a = a0 + u, b = b0 + v;
+                if (a < m && b < m) {
+                    const float g = acc[u][v] - (a == b ? 1.0f : 0.0f);
+                    dev = fmaxf(dev, isfinite(g) ? fabsf(g) : 3.0e38f);
+                    T[a * ld + b] = -0.5f * g + (a == b ? 1.0f : 0.0f);
+                }
+            }
+        atomicMax(&s_dev, __float_as_uint(dev));
+    }
+    __syncthreads();
+    for (int q = tid; q < nt4 * nt4; q += NT) {
+        const int i0 = (q / nt4) * 4, b0 = (q - (q / nt4) * nt4) * 4;
+        float acc[4][4] = {};
+        for (int a = 0; a < m; ++a) {
+            const float *sr = T + a * ld;
+            float x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                x[u] = (i0 + u < m) ? Z[(i0 + u) * ld + a] : 0.0f;
+                y[u] = (b0 + u < m) ? sr[b0 + u] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                if (i0 + u < m && b0 + v < m) A[(i0 + u) * ld + b0 + v] = acc[u][v];
+    }
+    __syncthreads();
+
+    if (tid == 0) {
+        int bad = s_fail || !(__uint_as_float(s_dev) <= 1e-2f);
+        for (int k = 0; k < m; ++k) bad |= !isfinite(lam[k]);
+        *d_fail = bad;
+        if (bad && d_status_on_fail) psd_set_status(d_status_on_fail, PSDPROJ_ENOCONV);
+    }
+    // descending order: ascending index k goes to position m-1-k
+    for (int e0 = tid; e0 < m * m; e0 += NT) {
+        const int row = e0 % m, col = e0 / m;
+        Vout[(int64_t)(m - 1 - col) * m + row] = A[row * ld + col];
+    }
+    for (int k = tid; k < m; k += NT) dout[m - 1 - k] = (double)lam[k];
+}
+
+}  // namespace
+
+cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V, double *d,
+                               float *scratch, int *d_fail, int *d_status_on_fail)
+{
+    const size_t smem = m <= SMEM_M ? sizeof(float) * 3 * (size_t)m * (m + 1) : 0;
+    cudaError_t e = cudaFuncSetAttribute(eig_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    eig_tridiag_kernel<<<1, NT, smem, s>>>(C, m, V, d, scratch, d_fail, d_status_on_fail);
+    return cudaGetLastError();
+}

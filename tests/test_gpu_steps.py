@@ -191,7 +191,8 @@ def test_core_matches_oracle(ctx, oracle_lib):
 
 
 @pytest.mark.parametrize("m", [1, 2, 3, 17, 60, 110, 112, 161, 210, 256])
-def test_eig_matches_lapack(ctx, m):
+@pytest.mark.parametrize("method", [ps.EIG_AUTO, ps.EIG_JACOBI, ps.EIG_TRIDIAG])
+def test_eig_matches_lapack(ctx, m, method):
     rng = np.random.default_rng(m)
     X = rng.standard_normal((m, m))
     C = (X + X.T) / 2
@@ -199,7 +200,7 @@ def test_eig_matches_lapack(ctx, m):
     Cd = torch.from_numpy(np.ascontiguousarray(C.T)).cuda()  # column-major
     V = torch.zeros(m, m, dtype=torch.float32, device="cuda")
     d = torch.zeros(m, dtype=torch.float64, device="cuda")
-    ctx.eig(Cd, V, d)
+    ctx.eig(Cd, V, d, method=method)
     assert ctx.sync_status() == 0
     dv = d.cpu().numpy()
     Vv = V.cpu().numpy().T.astype(np.float64)  # column-major -> (row, col)
@@ -211,16 +212,60 @@ def test_eig_matches_lapack(ctx, m):
     assert np.linalg.norm(Vv @ np.diag(dv) @ Vv.T - C) <= 5e-6 * nrm * np.sqrt(m)
 
 
-def test_eig_degenerate_inputs(ctx):
-    for C in [np.zeros((5, 5)), np.diag([3.0, 3.0, -1.0, 0.0]), np.eye(6) * 2.0]:
+@pytest.mark.parametrize("method", [ps.EIG_AUTO, ps.EIG_JACOBI, ps.EIG_TRIDIAG])
+def test_eig_degenerate_inputs(ctx, method):
+    for C in [np.zeros((5, 5)), np.diag([3.0, 3.0, -1.0, 0.0]), np.eye(6) * 2.0,
+              np.ones((1, 1)) * -2.0]:
         m = C.shape[0]
         V = torch.zeros(m, m, dtype=torch.float32, device="cuda")
         d = torch.zeros(m, dtype=torch.float64, device="cuda")
-        ctx.eig(torch.from_numpy(np.ascontiguousarray(C.T)).cuda(), V, d)
+        ctx.eig(torch.from_numpy(np.ascontiguousarray(C.T)).cuda(), V, d, method=method)
         assert ctx.sync_status() == 0
         assert np.allclose(d.cpu().numpy(), np.sort(np.diag(C))[::-1])
         Vv = V.cpu().numpy().T
         assert np.allclose(Vv.T @ Vv, np.eye(m), atol=1e-6)
+
+
+@pytest.mark.parametrize("method", [ps.EIG_AUTO, ps.EIG_TRIDIAG])
+@pytest.mark.parametrize("m", [30, 110, 200])
+def test_eig_clusters_in_random_basis(ctx, m, method):
+    # exact multiplicities plus near-multiplicities (1e-7 apart) in a random
+    # basis: the tridiagonal solver's cluster path; P = V max(D,0) V^T is
+    # unique even where V is not
+    rng = np.random.default_rng(100 + m)
+    q = m // 3
+    lam = np.concatenate([np.full(q, 3.0), np.full(q, -1.0), 1e-7 * np.arange(m - 2 * q)])
+    U, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    C = (U * lam) @ U.T
+    C = (C + C.T) / 2
+    V = torch.zeros(m, m, dtype=torch.float32, device="cuda")
+    d = torch.zeros(m, dtype=torch.float64, device="cuda")
+    ctx.eig(torch.from_numpy(np.ascontiguousarray(C.T)).cuda(), V, d, method=method)
+    assert ctx.sync_status() == 0
+    dv = d.cpu().numpy()
+    Vv = V.cpu().numpy().T.astype(np.float64)
+    nrm = np.linalg.norm(C)
+    assert np.abs(dv - np.sort(lam)[::-1]).max() <= 2e-6 * nrm
+    assert np.abs(Vv.T @ Vv - np.eye(m)).max() <= 2e-5
+    P = (Vv * np.maximum(dv, 0)) @ Vv.T
+    Pe = (U * np.maximum(lam, 0)) @ U.T
+    assert np.linalg.norm(P - Pe) <= 5e-6 * nrm
+
+
+def test_eig_auto_skips_jacobi_when_tridiagonal_succeeds(ctx):
+    # AUTO = the tridiagonal result bit for bit when no failure is flagged
+    m = 110
+    rng = np.random.default_rng(7)
+    X = rng.standard_normal((m, m))
+    Cd = torch.from_numpy(np.ascontiguousarray(((X + X.T) / 2).T)).cuda()
+    out = []
+    for method in (ps.EIG_AUTO, ps.EIG_TRIDIAG):
+        V = torch.zeros(m, m, dtype=torch.float32, device="cuda")
+        d = torch.zeros(m, dtype=torch.float64, device="cuda")
+        ctx.eig(Cd, V, d, method=method)
+        assert ctx.sync_status() == 0
+        out.append((V.cpu(), d.cpu()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
 
 
 def test_factor_and_syrk(ctx):
