@@ -51,9 +51,11 @@ extern "C" {
 
 /* ---- precision of the A-passes (sketch, power and core products) -------- */
 #define PSDPROJ_PREC_FP32    0 /* FP32 FMA on the CUDA cores (plain FP32)      */
-#define PSDPROJ_PREC_TF32    1 /* tcgen05 kind::tf32, FP32 accumulation        */
-#define PSDPROJ_PREC_BF16    2 /* tcgen05 kind::f16 (bf16 hi only)             */
-#define PSDPROJ_PREC_BF16X3  3 /* split-BF16: hi*hi + hi*lo + lo*hi            */
+#define PSDPROJ_PREC_TF32    1 /* reserved (A-passes: ENOTSUP)                  */
+#define PSDPROJ_PREC_BF16    2 /* tcgen05 kind::f16 on a BF16 image of A, FP32
+                                  accumulation (see psdproj_alg1)              */
+#define PSDPROJ_PREC_BF16X3  3 /* split-BF16: hi*hi + hi*lo + lo*hi (SYRK only;
+                                  A-passes: ENOTSUP)                          */
 
 /* ---- output modes -------------------------------------------------------- */
 #define PSDPROJ_OUT_FULL    0  /* P written in full (upper tiles mirrored)     */
@@ -91,7 +93,8 @@ int psdproj_destroy(psdproj_ctx *ctx);
 int psdproj_sync_status(psdproj_ctx *ctx);
 /* Human-readable name of a status code (static storage). */
 const char *psdproj_status_string(int status);
-/* Bytes of device workspace the context holds now. */
+/* Bytes of device workspace the context holds now (the BF16 image of A
+ * included). */
 size_t psdproj_workspace_bytes(const psdproj_ctx *ctx);
 
 /* ---- diagnostics --------------------------------------------------------- */
@@ -130,7 +133,12 @@ uint64_t psdproj_kernel_launches(void);
  * dP may be NULL only with out_mode FACTOR.  dW (n x (k+p), column-major)
  * may be NULL; its columns beyond r+ are zero.  d_rank (device int, may be
  * NULL) receives r+, the number of positive eigenvalues of Q^T A Q.
- * opts may be NULL (defaults). */
+ * opts may be NULL (defaults).  With opts->prec = PSDPROJ_PREC_BF16 (needs
+ * k+p <= 128) the call first packs A's block upper triangle into the
+ * context's BF16 image (npad x npad, npad = n rounded up to 256; kept for
+ * later calls) and every product with A, the power iterations of
+ * psdproj_alg2 included, reads that image on the tensor cores or CUDA cores
+ * with FP32 accumulation. */
 int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                  int k, int p, int q, uint64_t seed,
                  float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
@@ -180,9 +188,12 @@ int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream,
 
 /* Symmetric pass over A (Alg. 1 products, and Z = A Q of Alg. 2 line 2):
  *   dY = A dX + shift dX,   shift = (d_shift ? *d_shift : 0),
- * reading only the upper triangle of A, once.  dX, dY are n x m column-major
- * (ldx, ldy >= n); dY is overwritten.  prec is PSDPROJ_PREC_*; the
- * tensor-core forms need m <= 256 and return ENOTSUP otherwise. */
+ * reading only the upper triangle of A.  dX, dY are n x m column-major
+ * (ldx, ldy >= n); dY is overwritten.  prec PSDPROJ_PREC_FP32: CUDA cores,
+ * A read once.  PSDPROJ_PREC_BF16: A's block upper triangle is first packed
+ * into the context's BF16 image (4 bytes read, 2 written per entry), which
+ * the tensor-core pass then reads; requires m <= 128.  Other precisions and
+ * m > 128 in BF16 return ENOTSUP. */
 int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                      const float *dX, int64_t ldx, int m, const double *d_shift,
                      float *dY, int64_t ldy, int prec);

@@ -178,7 +178,31 @@ int check_opts(const psdproj_opts *o)
     return PSDPROJ_OK;
 }
 
-// Y = A X + shift X in the requested precision
+// The BF16 image of A used by the tensor-core passes: allocated on first
+// use (npad x npad BF16, kept for later calls) and written from A.
+int pack_bf16_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda)
+{
+    const int64_t npad = psd_bf16_image_pad(n);
+    const size_t bytes = sizeof(uint16_t) * (size_t)npad * (size_t)npad;
+    if (ctx->Ab_bytes < bytes || ctx->Ab_ld < npad) {
+        if (ctx->Ab) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->Ab);
+            ctx->Ab = nullptr;
+            ctx->Ab_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&ctx->Ab, bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        ctx->Ab_bytes = bytes;
+    }
+    ctx->Ab_ld = npad;
+    stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
+    PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab, ctx->Ab_ld), 1);
+    return PSDPROJ_OK;
+}
+
+// Y = A X + shift X in the requested precision (BF16: from the image that
+// pack_bf16_image wrote last)
 int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const float *X,
              int64_t ldx, int m, const double *d_shift, float *Y, int64_t ldy, int prec)
 {
@@ -187,9 +211,10 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
         PSD_KL(launch_sym_pass_simt(ctx->stream, A, n, lda, X, ldx, m, d_shift, Y, ldy), 1);
         return PSDPROJ_OK;
     }
+    if (prec != PSDPROJ_PREC_BF16) return PSDPROJ_ENOTSUP;
     psd_workspace &ws = ctx->ws;
-    PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->sm_count, A, n, lda, X, ldx, m, d_shift, Y, ldy,
-                              prec, ws.Xhi, ws.Xlo, ws.ld, ctx->d_status), 2);
+    PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->sm_count, ctx->Ab, ctx->Ab_ld, n, X, ldx, m,
+                              d_shift, Y, ldy, ws.Xhi, ws.ld, ctx->d_status), 2);
     return PSDPROJ_OK;
 }
 
@@ -238,14 +263,29 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     psd_workspace &ws = ctx->ws;
     cudaStream_t s = ctx->stream;
     const double *shift = nullptr;
+    const bool tc = opts.prec == PSDPROJ_PREC_BF16;
+    if (opts.prec != PSDPROJ_PREC_FP32 && !tc) return PSDPROJ_ENOTSUP;
+    if (tc && m > 128) return PSDPROJ_ENOTSUP;
+    // the BF16 form reads A once here and its 2-byte image in every later pass
+    if (tc) PSD_TRY(pack_bf16_image(ctx, dA, n, lda));
     if (scaled) {
         double *sc = ws.scal;
         if (!(alpha_in > 0.0)) {
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
-            PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
-                                          sc, ws.counter, sc + SC_SIGMA1), opts.N + 3);
-            PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0,
-                                          ws.pv1, sc, ws.counter, sc + SC_SIGMA2), opts.N + 3);
+            if (tc) {
+                PSD_KL(launch_power_iteration_bf16(s, ctx->Ab, ctx->Ab_ld, n, opts.N, seed, 3u, nullptr,
+                                                   ws.pv0, ws.pv1, sc, ws.counter, sc + SC_SIGMA1),
+                       opts.N + 3);
+                PSD_KL(launch_power_iteration_bf16(s, ctx->Ab, ctx->Ab_ld, n, opts.N, seed, 4u,
+                                                   sc + SC_SIGMA1, ws.pv0, ws.pv1, sc, ws.counter,
+                                                   sc + SC_SIGMA2),
+                       opts.N + 3);
+            } else {
+                PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
+                                              sc, ws.counter, sc + SC_SIGMA1), opts.N + 3);
+                PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0,
+                                              ws.pv1, sc, ws.counter, sc + SC_SIGMA2), opts.N + 3);
+            }
         }
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
         PSD_KL(launch_alpha_finish(s, sc + SC_SIGMA1, sc + SC_SIGMA2, alpha_in,
@@ -408,6 +448,7 @@ int psdproj_destroy(psdproj_ctx *ctx)
     if (ctx->dA_stage) cudaFree(ctx->dA_stage);
     if (ctx->dP_stage) cudaFree(ctx->dP_stage);
     if (ctx->dW_stage) cudaFree(ctx->dW_stage);
+    if (ctx->Ab) cudaFree(ctx->Ab);
     delete ctx;
     return PSDPROJ_OK;
 }
@@ -441,7 +482,7 @@ const char *psdproj_status_string(int s)
     }
 }
 
-size_t psdproj_workspace_bytes(const psdproj_ctx *ctx) { return ctx ? ctx->ws.bytes : 0; }
+size_t psdproj_workspace_bytes(const psdproj_ctx *ctx) { return ctx ? ctx->ws.bytes + ctx->Ab_bytes : 0; }
 
 int psdproj_timing_enable(psdproj_ctx *ctx, int on)
 {
@@ -524,9 +565,12 @@ int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, 
     if (!ctx || !dA || !dX || !dY || n < 1 || m < 1 || lda < n || ldx < n || ldy < n)
         return PSDPROJ_EINVAL;
     if (prec < PSDPROJ_PREC_FP32 || prec > PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
-    if (prec != PSDPROJ_PREC_FP32 && m > PSD_MAX_M) return PSDPROJ_ENOTSUP;
+    if (prec != PSDPROJ_PREC_FP32 && prec != PSDPROJ_PREC_BF16) return PSDPROJ_ENOTSUP;
+    if (prec == PSDPROJ_PREC_BF16 && m > 128) return PSDPROJ_ENOTSUP;
     device_guard g(ctx->device);
-    if (prec != PSDPROJ_PREC_FP32) PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    if (prec == PSDPROJ_PREC_FP32) return sym_pass(ctx, dA, n, lda, dX, ldx, m, d_shift, dY, ldy, prec);
+    PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    PSD_TRY(pack_bf16_image(ctx, dA, n, lda));
     return sym_pass(ctx, dA, n, lda, dX, ldx, m, d_shift, dY, ldy, prec);
 }
 

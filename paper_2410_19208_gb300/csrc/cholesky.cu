@@ -22,7 +22,6 @@ namespace {
 constexpr int NT = 1024;
 constexpr int SMEM_M = 128;  // largest m kept in shared memory
 constexpr int EPT = (SMEM_M * (SMEM_M + 1) / 2 + NT - 1) / NT;  // upper entries per thread
-constexpr int CPL = PSD_MAX_M / 32;  // entries of an R^-1 column per lane
 
 // ---- double-float arithmetic ------------------------------------------
 struct df {
@@ -117,8 +116,9 @@ template <> struct num<df> {
     __device__ static df one() { return {1.0f, 0.0f}; }
 };
 
-// T: df (first pass, m <= 128), double (first pass, m > 128) or float (second pass).
-template <typename T>
+// T: df (first pass, m <= 128), double (first pass, m > 128) or float (second
+// pass).  CPL: entries of an R^-1 column per lane (m <= 32 CPL).
+template <typename T, int CPL>
 __global__ void __launch_bounds__(NT)
 cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restrict__ dead,
                 int *__restrict__ d_qrank, double tau, T *gU, T *growj, float *gRf,
@@ -134,6 +134,7 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
     __shared__ double s_gmax;
     __shared__ int s_dead[PSD_MAX_M];
     __shared__ float s_rdinv[PSD_MAX_M];
+    __shared__ T s_r[PSD_MAX_M], s_inv[PSD_MAX_M];
     __shared__ int s_bad;
     const int tid = threadIdx.x;
     const int nup = m * (m + 1) / 2;
@@ -183,35 +184,45 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
     if (s_bad) psd_set_status(d_status, PSDPROJ_ENOTFINITE);
     const float thr = (float)(tau * s_gmax);
     const bool any = s_gmax > 0.0;
-
-    for (int j = 0; j < m; ++j) {
-        // phase A: every thread forms the pivot; row j of R into rowj and Rf
-        const T piv = U[j * ldu + j];
+    // pivot j -> R_jj, 1 / R_jj and the dependence flag, by one thread
+    auto pivot = [&](int j, T piv) {
         const bool dj = !(N::hi(piv) > thr) || !any;
         T r = N::one(), inv = N::one();
         if (!dj) N::root(piv, r, inv);
+        s_r[j] = r;
+        s_inv[j] = inv;
+        s_dead[j] = dj ? 1 : 0;
+        s_rdinv[j] = 1.0f / N::hi(r);
+    };
+    if (tid == 0) pivot(0, U[0]);
+    __syncthreads();
+
+    for (int j = 0; j < m; ++j) {
+        // phase A: row j of R into rowj (the update's operand) and Rf
+        const bool dj = s_dead[j] != 0;
+        const T inv = s_inv[j];
         for (int k = j + tid; k < m; k += NT) {
-            const T v = (k == j) ? r : (dj ? N::zero() : N::mul(U[j * ldu + k], inv));
+            const T v = (k == j) ? s_r[j] : (dj ? N::zero() : N::mul(U[j * ldu + k], inv));
             rowj[k] = (k == j) ? N::zero() : v;
             Rf[j * ldu + k] = N::hi(v);
         }
-        if (tid == 0) {
-            s_dead[j] = dj ? 1 : 0;
-            s_rdinv[j] = 1.0f / N::hi(r);
-        }
         __syncthreads();
-        // phase B: trailing update U(i,k) -= R(j,i) R(j,k), j < i <= k
-        if (!dj) {
-            if (in_smem) {
+        // phase B: trailing update U(i,k) -= R(j,i) R(j,k), j < i <= k; the
+        // thread that updates U(j+1, j+1) also forms the next pivot
+        if (in_smem) {
 #pragma unroll
-                for (int c = 0; c < EPT; ++c) {
-                    if (ei[c] > j) {
-                        const int i = ei[c], k = ek[c];
-                        U[i * ldu + k] = N::fms(U[i * ldu + k], rowj[i], rowj[k]);
-                    }
+            for (int c = 0; c < EPT; ++c) {
+                if (ei[c] > j) {
+                    const int i = ei[c], k = ek[c];
+                    T u = U[i * ldu + k];
+                    if (!dj) u = N::fms(u, rowj[i], rowj[k]);
+                    U[i * ldu + k] = u;
+                    if (i == j + 1 && k == j + 1) pivot(j + 1, u);
                 }
-            } else {
-                const int t = m - j - 1;
+            }
+        } else {
+            const int t = m - j - 1;
+            if (!dj) {
                 for (int e = tid; e < t * t; e += NT) {
                     const int a = e / t, b = e - (e / t) * t;
                     if (b < a) continue;
@@ -219,6 +230,8 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
                     U[i * ldu + k] = N::fms(U[i * ldu + k], rowj[i], rowj[k]);
                 }
             }
+            // e = 0 is entry (j+1, j+1), updated by thread 0 above
+            if (tid == 0 && t > 0) pivot(j + 1, U[(j + 1) * ldu + (j + 1)]);
         }
         __syncthreads();
     }
@@ -226,6 +239,8 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
     // R^-1 (upper, FP32), one warp per column j: back substitution in axpy
     // form with the column held in registers (lane l owns rows l + 32 c):
     //   for i = j .. 0:  x_i = b_i / R_ii;  b_r -= x_i R_ri  (r < i),  b = e_j
+    // Slots c above the one holding row i hold rows > i and are skipped
+    // (a warp-uniform branch).
     const int warp = tid >> 5, lane = tid & 31;
     for (int j = warp; j < m; j += NT / 32) {
         float b[CPL];
@@ -233,16 +248,18 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
         for (int c = 0; c < CPL; ++c) b[c] = (lane + 32 * c == j) ? 1.0f : 0.0f;
         for (int i = j; i >= 0; --i) {
             const int ci = i >> 5;
-            float v = 0.0f;
+            float v = b[0];
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) v = (c == ci) ? b[c] : v;
+            for (int c = 1; c < CPL; ++c)
+                if (c == ci) v = b[c];
             v = __shfl_sync(0xffffffffu, v, i & 31);
             const float xi = v * s_rdinv[i];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
+                if (c > ci) break;
                 const int r = lane + 32 * c;
-                if (r == i) b[c] = xi;
-                else if (r < i) b[c] = fmaf(-xi, Rf[r * ldu + i], b[c]);
+                if (r < i) b[c] = fmaf(-xi, Rf[r * ldu + i], b[c]);
+                else if (r == i) b[c] = xi;
             }
         }
 #pragma unroll
@@ -331,20 +348,25 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv,
     cudaError_t e;
     if (first_pass && sm_path) {
         const size_t smem = sizeof(df) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1);
-        e = cudaFuncSetAttribute(cholesky_kernel<df>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto kern = cholesky_kernel<df, SMEM_M / 32>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        cholesky_kernel<df><<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, nullptr, nullptr,
-                                                nullptr, d_status);
+        kern<<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, nullptr, nullptr, nullptr, d_status);
     } else if (first_pass) {
-        cholesky_kernel<double><<<1, NT, 0, s>>>(G, m, Rinv, dead, d_qrank, tau, gscratch,
-                                                 gscratch + (size_t)m * m, gRf, d_status);
+        cholesky_kernel<double, PSD_MAX_M / 32><<<1, NT, 0, s>>>(G, m, Rinv, dead, d_qrank, tau, gscratch,
+                                                                 gscratch + (size_t)m * m, gRf, d_status);
     } else {
         float *fs = reinterpret_cast<float *>(gscratch);
-        const size_t smem = sm_path ? sizeof(float) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1) : 0;
-        e = cudaFuncSetAttribute(cholesky_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        cholesky_kernel<float><<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, fs, fs + (size_t)m * m,
-                                                   gRf, d_status);
+        if (sm_path) {
+            const size_t smem = sizeof(float) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1);
+            auto kern = cholesky_kernel<float, SMEM_M / 32>;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            kern<<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, fs, fs + (size_t)m * m, gRf, d_status);
+        } else {
+            cholesky_kernel<float, PSD_MAX_M / 32><<<1, NT, 0, s>>>(G, m, Rinv, dead, d_qrank, tau, fs,
+                                                                   fs + (size_t)m * m, gRf, d_status);
+        }
     }
     return cudaGetLastError();
 }

@@ -71,6 +71,10 @@ struct psdproj_ctx {
     float *dW_stage = nullptr;  size_t dW_stage_bytes = 0;
     int *d_misc = nullptr;       // rank / info for host calls
     double *d_misc_f = nullptr;  // alpha for host calls
+    // BF16 image of the block upper triangle of A (tensor-core passes)
+    uint16_t *Ab = nullptr;
+    size_t Ab_bytes = 0;
+    int64_t Ab_ld = 0;
 };
 
 // Make sure the workspace holds n rows x m columns; may synchronise the
@@ -86,12 +90,24 @@ cudaError_t launch_sym_pass_simt(cudaStream_t s, const float *A, int64_t n, int6
                                  const float *X, int64_t ldx, int m, const double *d_shift,
                                  float *Y, int64_t ldy);
 
-// Tensor-core symmetric pass; returns cudaErrorNotSupported when the
-// configuration is outside what the kernel handles.
-cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const float *A, int64_t n,
-                               int64_t lda, const float *X, int64_t ldx, int m,
-                               const double *d_shift, float *Y, int64_t ldy, int prec,
-                               uint16_t *Xhi, uint16_t *Xlo, int64_t ldh, int *d_status);
+// Rows and columns of the BF16 image of an n x n matrix (n rounded up to the
+// 256-row tiles of the tensor-core pass).
+int64_t psd_bf16_image_pad(int64_t n);
+
+// BF16 image A' of the block upper triangle of A (256 x 256 diagonal blocks
+// strictly upper, diagonal halved, zero below; A = A' + A'^T), npad x npad
+// with leading dimension ldb (>= npad, multiple of 8), zero padded.
+cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab,
+                             int64_t ldb);
+
+// Tensor-core symmetric pass Y = (A' + A'^T) X + shift X on the BF16 image;
+// Xh (ldh >= n, multiple of 8) receives the BF16 image of X.  Returns
+// cudaErrorNotSupported when the configuration is outside what the kernel
+// handles (m > 128, misaligned buffers).
+cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t ldb,
+                               int64_t n, const float *X, int64_t ldx, int m,
+                               const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
+                               int64_t ldh, int *d_status);
 
 // Gram partials + FP64 reduction: G = X^T Z (sym = 1: X == Z, symmetric).
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
@@ -139,6 +155,12 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
                                    int N, uint64_t seed, uint32_t stream_id,
                                    const double *d_shift_neg, float *v0, float *v1,
                                    double *scal, unsigned *counter, double *d_sigma);
+
+// The same on the BF16 image (launch_pack_bf16); v0, v1 16-byte aligned.
+cudaError_t launch_power_iteration_bf16(cudaStream_t s, const uint16_t *Ab, int64_t ldb, int64_t n,
+                                        int N, uint64_t seed, uint32_t stream_id,
+                                        const double *d_shift_neg, float *v0, float *v1, double *scal,
+                                        unsigned *counter, double *d_sigma);
 
 cudaError_t launch_alpha_finish(cudaStream_t s, const double *d_s1, const double *d_s2,
                                 double alpha_in, double *d_alpha, double *d_shift,

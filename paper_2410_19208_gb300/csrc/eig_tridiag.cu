@@ -31,7 +31,7 @@ namespace {
 
 constexpr int NT = 512;
 constexpr int SMEM_M = 128;   // largest m kept in shared memory
-constexpr int NBIS = 16;      // multisection steps: 5^16 > 2^37
+constexpr int NBIS = 12;      // 5-way multisection steps: width 2.4e-9 of the start interval
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -40,14 +40,16 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// number of eigenvalues of tridiag(d, e) below x (ee = e^2)
+// number of eigenvalues of tridiag(d, e) below x (ee = e^2); pivots below
+// pivmin (>= 1e-30) in magnitude are replaced by -pivmin, so the fast
+// division sees |q| in its accurate range
 __device__ __forceinline__ int sturm(const float *d, const float *ee, int m, float x, float pivmin)
 {
     float q = d[0] - x;
     int c = q < 0.0f;
     for (int i = 1; i < m; ++i) {
         if (fabsf(q) < pivmin) q = -pivmin;
-        q = (d[i] - x) - ee[i - 1] / q;
+        q = (d[i] - x) - __fdividef(ee[i - 1], q);
         c += q < 0.0f;
     }
     return c;
@@ -167,30 +169,66 @@ __device__ void inverse_step(const float *d, const float *e, int m, float lambda
 }
 
 __global__ void __launch_bounds__(NT, 1)
-eig_tridiag_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
+eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ Vout,
                    double *__restrict__ dout, float *gscr, int *__restrict__ d_fail,
                    int *d_status_on_fail)
 {
     extern __shared__ float sm[];
-    const bool in_smem = m <= SMEM_M;
-    const int ld = m + 1;
+    const bool in_smem = mfull <= SMEM_M;
+    const int ld = mfull + 1;
     float *A = in_smem ? sm : gscr;                 // m x ld, row-major
-    float *Z = A + m * ld;                          // eigenvectors of T (row i, column k)
-    float *T = Z + m * ld;                          // scratch of the twisted factorization
+    float *Z = A + mfull * ld;                      // eigenvectors of T (row i, column k)
+    float *T = Z + mfull * ld;                      // scratch of the twisted factorization
     __shared__ float d[PSD_MAX_M], e[PSD_MAX_M], ee[PSD_MAX_M], beta[PSD_MAX_M];
     __shared__ float vv[PSD_MAX_M], pp[PSD_MAX_M], lam[PSD_MAX_M];
     __shared__ float red[NT / 32];
     __shared__ int cl_start[PSD_MAX_M];
-    __shared__ int s_fail;
+    __shared__ int s_pos[PSD_MAX_M], s_src[PSD_MAX_M];
+    __shared__ int s_fail, s_mc;
+    __shared__ unsigned s_dev;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_fail = 0;
+    if (tid == 0) {
+        s_fail = 0;
+        s_dev = 0u;
+    }
 
-    for (int e0 = tid; e0 < m * m; e0 += NT) {
-        const int i = e0 / m, j = e0 - (e0 / m) * m;
-        A[i * ld + j] = (float)C[(int64_t)j * m + i];
+    for (int e0 = tid; e0 < mfull * mfull; e0 += NT) {
+        const int i = e0 / mfull, j = e0 - (e0 / mfull) * mfull;
+        A[i * ld + j] = (float)C[(int64_t)j * mfull + i];
     }
     __syncthreads();
 
+    // Rows that are exactly zero (the zeroed dependent columns of Q) carry
+    // the eigenvalue 0 with a unit eigenvector; they are taken out and the
+    // solver runs on the remaining m x m block, so that these eigenvalues stay
+    // exactly 0 and never count as positive.
+    for (int i = tid; i < mfull; i += NT) {
+        int nz = 0;
+        for (int k = 0; k < mfull; ++k) nz |= (A[i * ld + k] != 0.0f);   // NaN counts as nonzero
+        s_pos[i] = nz;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int c = 0;
+        for (int i = 0; i < mfull; ++i) s_pos[i] = s_pos[i] ? c++ : -1;
+        s_mc = c;
+    }
+    __syncthreads();
+    const int m = s_mc;
+    if (m < mfull && m > 0) {
+        for (int e0 = tid; e0 < mfull * mfull; e0 += NT) {
+            const int i = e0 / mfull, k = e0 - (e0 / mfull) * mfull;
+            const int pi = s_pos[i], pk = s_pos[k];
+            if (pi >= 0 && pk >= 0) Z[pi * ld + pk] = A[i * ld + k];
+        }
+        __syncthreads();
+        for (int e0 = tid; e0 < m * m; e0 += NT) {
+            const int i = e0 / m, k = e0 - (e0 / m) * m;
+            A[i * ld + k] = Z[i * ld + k];
+        }
+        __syncthreads();
+    }
+    if (m > 0) {
     // ---------------------------------------------------------------- 1
     for (int j = 0; j + 2 < m; ++j) {
         const int r0 = j + 1;                       // first row of the trailing block
@@ -220,34 +258,31 @@ eig_tridiag_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout
             __syncthreads();
             continue;
         }
-        // p = bt A22 v (thread per row) and v^T p
+        // p = bt A22 v (a warp per row, lanes split the row) and v^T p
         float pv = 0.0f;
-        for (int i = r0 + tid; i < m; i += NT) {
+        for (int i = r0 + warp; i < m; i += NT / 32) {
             const float *row = A + i * ld;
-            float s0 = 0.0f, s1 = 0.0f;
-            int k = r0;
-            for (; k + 1 < m; k += 2) {
-                s0 = fmaf(row[k], vv[k], s0);
-                s1 = fmaf(row[k + 1], vv[k + 1], s1);
-            }
-            if (k < m) s0 = fmaf(row[k], vv[k], s0);
-            const float p = bt * (s0 + s1);
-            pp[i] = p;
+            float s0 = 0.0f;
+            for (int k = r0 + lane; k < m; k += 32) s0 = fmaf(row[k], vv[k], s0);
+            s0 = warp_sum(s0);
+            const float p = bt * s0;
+            if (lane == 0) pp[i] = p;
             pv = fmaf(p, vv[i], pv);
         }
-        pv = warp_sum(pv);
         if (lane == 0) red[warp] = pv;
         __syncthreads();
         float vtp = 0.0f;
         for (int w = 0; w < NT / 32; ++w) vtp += red[w];
         const float K = 0.5f * bt * vtp;
-        // A22 -= v w^T + w v^T with w = p - K v; the reflector goes below the subdiagonal
-        const int L = m - r0;
-        for (int q = tid; q < L * L; q += NT) {
-            const int a = q / L, b = q - (q / L) * L;
-            const int i = r0 + a, k = r0 + b;
-            const float wi = pp[i] - K * vv[i], wk = pp[k] - K * vv[k];
-            A[i * ld + k] -= vv[i] * wk + wi * vv[k];
+        // A22 -= v w^T + w v^T with w = p - K v (rows by warp, columns by
+        // lane); the reflector goes below the subdiagonal
+        for (int i = r0 + warp; i < m; i += NT / 32) {
+            const float vi = vv[i], wi = pp[i] - K * vv[i];
+            float *row = A + i * ld;
+            for (int k = r0 + lane; k < m; k += 32) {
+                const float wk = pp[k] - K * vv[k];
+                row[k] -= vi * wk + wi * vv[k];
+            }
         }
         for (int i = r0 + tid; i < m; i += NT) A[i * ld + j] = vv[i];
         __syncthreads();
@@ -374,53 +409,56 @@ eig_tridiag_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout
 
     // ---------------------------------------------------------------- 4
     // Z <- H_j Z for j = m-3 .. 0, H_j = I - beta_j v_j v_j^T, v_j = A[j+1.., j]
+    // (the four quarters of the block form partial dot products over rows
+    // i = quarter mod 4; T holds them, 4 x m)
     for (int j = m - 3; j >= 0; --j) {
         const float bt = beta[j];
         if (bt == 0.0f) continue;                   // uniform across the block
         const int r0 = j + 1;
-        // pp[c] = bt v^T Z[:, c]
-        for (int c = tid; c < m; c += NT) {
+        const int qtr = tid >> 7, cl = tid & 127;
+        for (int c = cl; c < m; c += 128) {
             float s0 = 0.0f;
-            for (int i = r0; i < m; ++i) s0 = fmaf(A[i * ld + j], Z[i * ld + c], s0);
-            pp[c] = bt * s0;
+            for (int i = r0 + qtr; i < m; i += 4) s0 = fmaf(A[i * ld + j], Z[i * ld + c], s0);
+            T[qtr * ld + c] = s0;
         }
         __syncthreads();
-        const int L = m - r0;
-        for (int q = tid; q < L * m; q += NT) {
-            const int a = q / m, c = q - (q / m) * m;
-            const int i = r0 + a;
-            Z[i * ld + c] -= A[i * ld + j] * pp[c];
+        for (int c = tid; c < m; c += NT) pp[c] = bt * ((T[c] + T[ld + c]) + (T[2 * ld + c] + T[3 * ld + c]));
+        __syncthreads();
+        for (int i = r0 + warp; i < m; i += NT / 32) {
+            const float vi = A[i * ld + j];
+            float *zr = Z + i * ld;
+            for (int c = lane; c < m; c += 32) zr[c] = fmaf(-vi, pp[c], zr[c]);
         }
         __syncthreads();
     }
 
     // ---------------------------------------------------------------- 5
-    // S = (3I - Z^T Z)/2 into T, then Z S into A (4 x 4 register tiles)
-    __shared__ unsigned s_dev;
-    if (tid == 0) s_dev = 0u;
-    __syncthreads();
-    const int nt4 = (m + 3) >> 2;
-    for (int q = tid; q < nt4 * nt4; q += NT) {
-        const int a0 = (q / nt4) * 4, b0 = (q - (q / nt4) * nt4) * 4;
-        float acc[4][4] = {};
+    // S = (3I - Z^T Z)/2 into T, then Z S into A
+    // 8 x 8 register tiles; loads past column m - 1 or row m - 1 read the
+    // next row or the slack after the buffers and only feed entries that are
+    // not stored
+    const int nt8 = (m + 7) >> 3;
+    for (int q = tid; q < nt8 * nt8; q += NT) {
+        const int a0 = (q / nt8) * 8, b0 = (q - (q / nt8) * nt8) * 8;
+        float acc[8][8] = {};
         for (int i = 0; i < m; ++i) {
             const float *zr = Z + i * ld;
-            float x[4], y[4];
+            float x[8], y[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                x[u] = (a0 + u < m) ? zr[a0 + u] : 0.0f;
-                y[u] = (b0 + u < m) ? zr[b0 + u] : 0.0f;
+            for (int u = 0; u < 8; ++u) {
+                x[u] = zr[a0 + u];
+                y[u] = zr[b0 + u];
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
         }
         float dev = 0.0f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
+            for (int v = 0; v < 8; ++v) {
                 const int a = a0 + u, b = b0 + v;
                 if (a < m && b < m) {
                     const float g = acc[u][v] - (a == b ? 1.0f : 0.0f);
@@ -431,42 +469,63 @@ eig_tridiag_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout
         atomicMax(&s_dev, __float_as_uint(dev));
     }
     __syncthreads();
-    for (int q = tid; q < nt4 * nt4; q += NT) {
-        const int i0 = (q / nt4) * 4, b0 = (q - (q / nt4) * nt4) * 4;
-        float acc[4][4] = {};
+    for (int q = tid; q < nt8 * nt8; q += NT) {
+        const int i0 = (q / nt8) * 8, b0 = (q - (q / nt8) * nt8) * 8;
+        float acc[8][8] = {};
         for (int a = 0; a < m; ++a) {
             const float *sr = T + a * ld;
-            float x[4], y[4];
+            float x[8], y[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                x[u] = (i0 + u < m) ? Z[(i0 + u) * ld + a] : 0.0f;
-                y[u] = (b0 + u < m) ? sr[b0 + u] : 0.0f;
+            for (int u = 0; u < 8; ++u) {
+                x[u] = Z[(i0 + u) * ld + a];
+                y[u] = sr[b0 + u];
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
+            for (int v = 0; v < 8; ++v)
                 if (i0 + u < m && b0 + v < m) A[(i0 + u) * ld + b0 + v] = acc[u][v];
     }
     __syncthreads();
 
+    }  // m > 0
+
+    // Output in decreasing order: the positive eigenvalues of the block, the
+    // exact zeros of the removed rows, then the rest of the block (lam is
+    // ascending).  s_src[position] = block index k, or -(i+1) for removed row i.
     if (tid == 0) {
         int bad = s_fail || !(__uint_as_float(s_dev) <= 1e-2f);
-        for (int k = 0; k < m; ++k) bad |= !isfinite(lam[k]);
+        int npos = 0;
+        for (int k = 0; k < m; ++k) {
+            bad |= !isfinite(lam[k]);
+            npos += lam[k] > 0.0f;
+        }
         *d_fail = bad;
         if (bad && d_status_on_fail) psd_set_status(d_status_on_fail, PSDPROJ_ENOCONV);
+        const int ndead = mfull - m;
+        for (int k = 0; k < m; ++k) s_src[lam[k] > 0.0f ? (m - 1 - k) : (m - 1 - k + ndead)] = k;
+        int t = 0;
+        for (int i = 0; i < mfull; ++i)
+            if (s_pos[i] < 0) s_src[npos + t++] = -(i + 1);
     }
-    // descending order: ascending index k goes to position m-1-k
-    for (int e0 = tid; e0 < m * m; e0 += NT) {
-        const int row = e0 % m, col = e0 / m;
-        Vout[(int64_t)(m - 1 - col) * m + row] = A[row * ld + col];
+    __syncthreads();
+    for (int e0 = tid; e0 < mfull * mfull; e0 += NT) {
+        const int row = e0 % mfull, col = e0 / mfull;
+        const int src = s_src[col];
+        float v;
+        if (src >= 0) v = s_pos[row] >= 0 ? A[s_pos[row] * ld + src] : 0.0f;
+        else v = (row == -src - 1) ? 1.0f : 0.0f;
+        Vout[(int64_t)col * mfull + row] = v;
     }
-    for (int k = tid; k < m; k += NT) dout[m - 1 - k] = (double)lam[k];
+    for (int col = tid; col < mfull; col += NT) {
+        const int src = s_src[col];
+        dout[col] = src >= 0 ? (double)lam[src] : 0.0;
+    }
 }
 
 }  // namespace
@@ -474,7 +533,9 @@ eig_tridiag_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout
 cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V, double *d,
                                float *scratch, int *d_fail, int *d_status_on_fail)
 {
-    const size_t smem = m <= SMEM_M ? sizeof(float) * 3 * (size_t)m * (m + 1) : 0;
+    // three m x (m+1) buffers plus 8 slack rows read (never used) by the
+    // edge tiles of the Newton-Schulz products
+    const size_t smem = m <= SMEM_M ? sizeof(float) * (3 * (size_t)m + 8) * (m + 1) : 0;
     cudaError_t e = cudaFuncSetAttribute(eig_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;

@@ -165,6 +165,140 @@ sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
     for (int64_t i = threadIdx.x; i < n; i += NTW) other[i] = 0.0f;
 }
 
+// The same product on the BF16 image A' of the block upper triangle
+// (A = A' + A'^T; written by the tensor-core pass's pack kernel, zero padded
+// to npad = a multiple of 256).  Block row of 32 rows from row0: its tiles
+// start at the first column of its 256 x 256 diagonal block and are 256
+// columns wide (lane l: columns 8l..8l+7, one 16-byte load per row); no
+// entry needs masking, and the diagonal block's halved diagonal enters once
+// through the row sums and once through the column sums.
+constexpr int TCB = 256;   // columns per BF16 tile
+constexpr int SEGB = 4;    // tiles per block
+
+__device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
+{
+    a[0] = __uint_as_float(u.x << 16); a[1] = __uint_as_float(u.x & 0xFFFF0000u);
+    a[2] = __uint_as_float(u.y << 16); a[3] = __uint_as_float(u.y & 0xFFFF0000u);
+    a[4] = __uint_as_float(u.z << 16); a[5] = __uint_as_float(u.z & 0xFFFF0000u);
+    a[6] = __uint_as_float(u.w << 16); a[7] = __uint_as_float(u.w & 0xFFFF0000u);
+}
+
+__global__ void __launch_bounds__(NTW)
+sym_gemv_bf16_kernel(const uint16_t *__restrict__ Ab, int64_t ldb, int64_t n, int64_t npad,
+                     const float *__restrict__ x, float *__restrict__ y, float *__restrict__ other,
+                     double *scal, unsigned *counter, const double *d_shift_neg, double *d_sigma,
+                     unsigned nactive)
+{
+    __shared__ float colsum[8][SEGB * TCB];
+    __shared__ double red[NTW / 32];
+    __shared__ bool s_last;
+    const int64_t row0 = (int64_t)blockIdx.y * TRW;
+    const int64_t cs = (row0 / 256) * 256;
+    const int tiles = (int)((npad - cs) / TCB);
+    const int t0 = (int)blockIdx.x * SEGB;
+    if (t0 >= tiles) return;
+    const float sc = (float)scal[0];
+    const float shift = d_shift_neg ? (float)(-(*d_shift_neg)) : 0.0f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    float rowacc[4] = {0.f, 0.f, 0.f, 0.f};
+    float xr[4];
+    const uint16_t *rowp[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gr = row0 + warp * 4 + i;      // < npad
+        xr[i] = gr < n ? x[gr] * sc : 0.0f;
+        rowp[i] = Ab + gr * ldb;
+    }
+    const int nt = min(SEGB, tiles - t0);
+    uint4 nxt[4];
+    {
+        const int64_t c0 = cs + (int64_t)t0 * TCB + lane * 8;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) nxt[i] = __ldcs(reinterpret_cast<const uint4 *>(rowp[i] + c0));
+    }
+#pragma unroll 1
+    for (int t = 0; t < nt; ++t) {
+        const int64_t c0 = cs + (int64_t)(t0 + t) * TCB + lane * 8;
+        uint4 cur[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
+        if (t + 1 < nt) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                nxt[i] = __ldcs(reinterpret_cast<const uint4 *>(rowp[i] + c0 + TCB));
+        }
+        float xc[8];
+        if (c0 + 8 <= n) {
+            const float4 x0 = __ldg(reinterpret_cast<const float4 *>(x + c0));
+            const float4 x1 = __ldg(reinterpret_cast<const float4 *>(x + c0 + 4));
+            xc[0] = x0.x * sc; xc[1] = x0.y * sc; xc[2] = x0.z * sc; xc[3] = x0.w * sc;
+            xc[4] = x1.x * sc; xc[5] = x1.y * sc; xc[6] = x1.z * sc; xc[7] = x1.w * sc;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) xc[j] = (c0 + j < n) ? x[c0 + j] * sc : 0.0f;
+        }
+        float colacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float a[8];
+            bf16x8_to_f32(cur[i], a);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                rowacc[i] = fmaf(a[j], xc[j], rowacc[i]);
+                colacc[j] = fmaf(a[j], xr[i], colacc[j]);
+            }
+        }
+        float4 *dst = reinterpret_cast<float4 *>(&colsum[warp][t * TCB + lane * 8]);
+        dst[0] = make_float4(colacc[0], colacc[1], colacc[2], colacc[3]);
+        dst[1] = make_float4(colacc[4], colacc[5], colacc[6], colacc[7]);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nt * TCB; c += NTW) {
+        float sacc = 0.0f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sacc += colsum[w][c];
+        const int64_t gc = cs + (int64_t)t0 * TCB + c;
+        if (gc < n && sacc != 0.0f) atomicAdd(&y[gc], sacc);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float sacc = rowacc[i];
+        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+        const int64_t gr = row0 + warp * 4 + i;
+        if (lane == 0 && gr < n) {
+            if (t0 == 0) sacc = fmaf(shift, xr[i], sacc);  // the segment holding the diagonal
+            atomicAdd(&y[gr], sacc);
+        }
+    }
+
+    // ticket: the last block finishes the product
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == nactive - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += NTW) {
+        const double v = (double)__ldcg(&y[i]);
+        acc += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sacc = 0.0;
+        for (int w = 0; w < NTW / 32; ++w) sacc += red[w];
+        const double nrm = sqrt(sacc);
+        scal[1] = nrm;
+        scal[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+        if (d_sigma) *d_sigma = nrm;
+        *counter = 0u;
+    }
+    for (int64_t i = threadIdx.x; i < n; i += NTW) other[i] = 0.0f;
+}
+
 __global__ void pi_init_kernel(double *scal, float *v1, int64_t n)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0) { scal[0] = 1.0; scal[1] = 0.0; }
@@ -212,6 +346,41 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
     for (int it = 0; it <= N; ++it) {
         sym_gemv_kernel<<<grid, NTW, 0, s>>>(A, n, lda, in, out, in, scal, counter, d_shift_neg,
                                              it == N ? d_sigma : nullptr, (unsigned)blocks, vec);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        float *t = in; in = out; out = t;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_power_iteration_bf16(cudaStream_t s, const uint16_t *Ab, int64_t ldb, int64_t n,
+                                        int N, uint64_t seed, uint32_t stream_id,
+                                        const double *d_shift_neg, float *v0, float *v1, double *scal,
+                                        unsigned *counter, double *d_sigma)
+{
+    const int64_t npad = psd_round_up(n, 256);
+    if (ldb < npad || (ldb % 8) != 0 || (reinterpret_cast<uintptr_t>(Ab) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(v0) & 15) != 0 || (reinterpret_cast<uintptr_t>(v1) & 15) != 0)
+        return cudaErrorInvalidValue;
+    cudaError_t e = launch_gaussian(s, seed, stream_id, n, 1, 1, n, v0, n);
+    if (e != cudaSuccess) return e;
+    pi_init_kernel<<<64, 256, 0, s>>>(scal, v1, n);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nb = (int)((n + TRW - 1) / TRW);   // block rows holding rows < n
+    int64_t blocks = 0;
+    for (int I = 0; I < nb; ++I) {
+        const int64_t cs = ((int64_t)I * TRW / 256) * 256;
+        const int tiles = (int)((npad - cs) / TCB);
+        blocks += (tiles + SEGB - 1) / SEGB;
+    }
+    const int maxseg = (int)((npad / TCB + SEGB - 1) / SEGB);
+    const dim3 grid((unsigned)maxseg, (unsigned)nb);
+    float *in = v0, *out = v1;
+    for (int it = 0; it <= N; ++it) {
+        sym_gemv_bf16_kernel<<<grid, NTW, 0, s>>>(Ab, ldb, n, npad, in, out, in, scal, counter,
+                                                  d_shift_neg, it == N ? d_sigma : nullptr,
+                                                  (unsigned)blocks);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         float *t = in; in = out; out = t;

@@ -3,28 +3,29 @@
 // (Alg. 1) and the core product Z = A Q of Alg. 2, in BF16 with FP32
 // accumulation.
 //
-// A (FP32, row-major) is streamed from HBM once, upper triangle only, in
-// tiles of BM rows x 64 columns (BM = 256, two stages in flight) loaded by
-// TMA (128-byte swizzle).  Tiles (I, J) with J >= (BM/64) I cover the upper
-// triangle; the BM/64 tiles of a block row that meet the diagonal also carry
-// strictly-lower entries, which are discarded by selection before any
-// arithmetic.
+// The pass reads a BF16 image A' of A written once per projection by
+// pack_upper_bf16_kernel: the tiles (I, J) of BM = 256 rows x 64 columns with
+// J >= 4 I (the block upper triangle), where the 256 x 256 blocks on the
+// diagonal hold a_ij for j > i, a_ii / 2 on the diagonal and 0 below it, so
+// that A = A' + A'^T exactly.  The image is padded with zeros to a multiple
+// of 256 in both directions.  Every later pass over A then streams 2 bytes
+// per upper-triangle entry instead of 4, and needs no masking.
 //
-// Both products of a tile read the same converted BF16 tile:
-//   P1  D1^T (m x BM) += X_J^T (m x 64) . A_IJ^T    (B operand K-major)
-//   P2  D2^T (m x 64)   = X_I^T (m x BM) . A_IJ     (B operand MN-major)
-// with M = 128 rows of X^T (m <= 128; rows m..127 are zero).  Inside diagonal
-// tiles the converter writes 0 below the diagonal and a_ii / 2 on it, so
-// P1 + P2 count every upper entry once in each direction and a_ii once.
-// D1^T accumulates over the run of tiles a CTA owns in one block row and is
-// flushed once; D2^T is double-buffered in TMEM and added to Y with
-// red.global.add.v4.f32 after every tile.
+// Each tile is loaded by TMA (128-byte swizzle, four stages in flight) and
+// feeds two products straight from shared memory:
+//   P1  D1^T (m x BM) += X_J^T (m x 64) . A'_IJ^T   (B operand K-major)
+//   P2  D2^T (m x 64)   = X_I^T (m x BM) . A'_IJ    (B operand MN-major)
+// with M = 128 rows of X^T (m <= 128; rows m..127 are zero).  D1^T
+// accumulates over the run of tiles a CTA owns in one block row and is
+// flushed once (with the shift term when the run holds the diagonal block);
+// D2^T is double-buffered in TMEM and added to Y with red.global.add.v4.f32
+// after every tile.
 //
-// Warp roles (384 threads, one CTA per SM, persistent over an equal share of
+// Warp roles (256 threads, one CTA per SM, persistent over an equal share of
 // the tiles in row-major order): warp 0 issues TMA, warp 1 owns TMEM and
-// issues tcgen05.mma from one thread, warps 4-7 convert FP32 -> BF16 in place,
-// warps 8-11 drain TMEM.  Every mbarrier wait is bounded; on a timeout the
-// CTA records PSDPROJ_ETIMEOUT, unwinds and frees its TMEM.
+// issues tcgen05.mma from one thread, warps 4-7 drain TMEM.  Every mbarrier
+// wait is bounded; on a timeout the CTA records PSDPROJ_ETIMEOUT, unwinds and
+// frees its TMEM.
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -36,30 +37,25 @@ namespace {
 using namespace tc;
 
 constexpr int BN = 64;
-constexpr int MAXSTAGE = 4;
+constexpr int BM = 256;
+constexpr int R = BM / BN;                       // column tiles per block-row step
+constexpr int NSTAGE = 4;
+constexpr uint32_t A_STAGE = BM * BN * 2;        // BF16 tile
 constexpr uint32_t XJ_BYTES = 128 * BN * 2;      // 16 KB
-constexpr int NT = 384;
+constexpr uint32_t XI_BYTES = 128 * BM * 2;      // 64 KB
+constexpr uint32_t OFF_A = 0;
+constexpr uint32_t OFF_XJ = NSTAGE * A_STAGE;
+constexpr uint32_t OFF_XI = OFF_XJ + 2 * XJ_BYTES;
+constexpr uint32_t OFF_BAR = OFF_XI + XI_BYTES;
+constexpr uint32_t SMEM_BYTES = OFF_BAR + 256;
+constexpr uint32_t D1_COL = 0, D2_COL = BM;      // TMEM columns: D1 256, D2 2 x 64
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int NT = 256;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s at 2 GHz
-
-// Tile height BM (128 or 256) and number of A stages: the layout of the
-// dynamic shared memory and the TMEM columns follow from them.
-template <int BM, int NSTAGE>
-struct Cfg {
-    static constexpr int R = BM / BN;                        // column tiles per block row step
-    static constexpr uint32_t A_STAGE = BM * BN * 4;         // FP32 tile (BF16 image in place)
-    static constexpr uint32_t XI_BYTES = 128 * BM * 2;
-    static constexpr uint32_t OFF_A = 0;
-    static constexpr uint32_t OFF_XJ = NSTAGE * A_STAGE;
-    static constexpr uint32_t OFF_XI = OFF_XJ + 2 * XJ_BYTES;
-    static constexpr uint32_t OFF_BAR = OFF_XI + XI_BYTES;
-    static constexpr uint32_t SMEM_BYTES = OFF_BAR + 256;
-    static constexpr uint32_t D1_COL = 0, D2_COL = BM;
-    static constexpr uint32_t TMEM_COLS = (BM + 2 * BN) <= 256 ? 256 : 512;
-    static_assert(SMEM_BYTES <= 232448, "shared memory");
-};
+static_assert(SMEM_BYTES <= 232448, "shared memory");
 
 struct Bars {
-    uint64_t fullA[MAXSTAGE], convA[MAXSTAGE], emptyA[MAXSTAGE];
+    uint64_t fullA[NSTAGE], emptyA[NSTAGE];
     uint64_t fullXJ[2], emptyXJ[2];
     uint64_t fullXI, emptyXI;
     uint64_t d2full[2], d2empty[2];
@@ -67,7 +63,6 @@ struct Bars {
     uint64_t mmadone;
     uint32_t tmem_base;
     int abort;
-    int conv_ok;
 };
 static_assert(sizeof(Bars) <= 256, "barrier block");
 
@@ -87,29 +82,26 @@ struct Params {
 
 // tiles of block row I are J = R I .. nbc - 1; rows 0..I-1 hold
 // sum_i (nbc - R i) = I nbc - R I (I - 1) / 2 of them
-template <int R>
 __device__ __forceinline__ int64_t row_start(int I, int nbc)
 {
     return (int64_t)I * nbc - (int64_t)R * I * (I - 1) / 2;
 }
 
-template <int R>
 __device__ __forceinline__ void tile_of(int64_t t, int nbc, int nbr, int &I, int &J)
 {
     int lo = 0, hi = nbr - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (row_start<R>(mid, nbc) <= t) lo = mid; else hi = mid - 1;
+        if (row_start(mid, nbc) <= t) lo = mid; else hi = mid - 1;
     }
     I = lo;
-    J = R * lo + (int)(t - row_start<R>(lo, nbc));
+    J = R * lo + (int)(t - row_start(lo, nbc));
 }
 
 // last tile of a run inside one block row
-template <int R>
 __device__ __forceinline__ bool last_in_row_run(int64_t t, int64_t t1, int I, const Params &P)
 {
-    return (t + 1 == t1) || (I + 1 < P.nbr && t + 1 == row_start<R>(I + 1, P.nbc));
+    return (t + 1 == t1) || (I + 1 < P.nbr && t + 1 == row_start(I + 1, P.nbc));
 }
 
 __device__ __forceinline__ void fail(Bars &B, int *st)
@@ -124,16 +116,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-template <int BM, int NSTAGE>
 __global__ void __launch_bounds__(NT, 1)
 sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                      const Params P)
 {
-    using C = Cfg<BM, NSTAGE>;
-    constexpr int R = C::R;
-    constexpr uint32_t A_STAGE = C::A_STAGE, XI_BYTES = C::XI_BYTES;
-    constexpr uint32_t OFF_A = C::OFF_A, OFF_XJ = C::OFF_XJ, OFF_XI = C::OFF_XI, OFF_BAR = C::OFF_BAR;
-    constexpr uint32_t D1_COL = C::D1_COL, D2_COL = C::D2_COL, TMEM_COLS = C::TMEM_COLS;
     extern __shared__ __align__(1024) uint8_t sm[];
     Bars &B = *reinterpret_cast<Bars *>(sm + OFF_BAR);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -146,7 +132,6 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(&B.fullA[s], 1);
-            mbar_init(&B.convA[s], 4);
             mbar_init(&B.emptyA[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -182,7 +167,7 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             int64_t it = 0;
             for (int64_t t = t0; t < t1; ++t, ++it) {
                 int I, J;
-                tile_of<R>(t, P.nbc, P.nbr, I, J);
+                tile_of(t, P.nbc, P.nbr, I, J);
                 if (I != curI) {
                     if (!mbar_wait(&B.emptyXI, (xi_uses & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                     mbar_arrive_expect_tx(&B.fullXI, XI_BYTES);
@@ -196,7 +181,6 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 if (!mbar_wait(&B.emptyA[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                 mbar_arrive_expect_tx(&B.fullA[s], A_STAGE);
                 tma_load_2d(sm + OFF_A + s * A_STAGE, &tmA, BN * J, BM * I, &B.fullA[s]);
-                tma_load_2d(sm + OFF_A + s * A_STAGE + A_STAGE / 2, &tmA, BN * J + 32, BM * I, &B.fullA[s]);
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
                 if (!mbar_wait(&B.emptyXJ[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
@@ -221,9 +205,9 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             bool issued = false;
             for (int64_t t = t0; t < t1; ++t, ++it) {
                 int I, J;
-                tile_of<R>(t, P.nbc, P.nbr, I, J);
+                tile_of(t, P.nbc, P.nbr, I, J);
                 const bool first = (I != curI);
-                const bool last = last_in_row_run<R>(t, t1, I, P);
+                const bool last = last_in_row_run(t, t1, I, P);
                 if (first) {
                     if (!mbar_wait(&B.fullXI, seg & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                     if (!mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
@@ -233,7 +217,7 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 const uint32_t us = (uint32_t)(it / NSTAGE);
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
-                if (!mbar_wait(&B.convA[s], us & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                if (!mbar_wait(&B.fullA[s], us & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                 if (!mbar_wait(&B.fullXJ[b], ub & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                 if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                 tc_fence_after();
@@ -251,7 +235,7 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
 #pragma unroll
                 for (int kk = 0; kk < BM / 16; ++kk) {
                     const uint64_t ad = sdesc_sw128(xi + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
-                    const uint64_t bd = sdesc_sw128(a_tile + kk * 2048, A_STAGE / 2, 1024);
+                    const uint64_t bd = sdesc_sw128(a_tile + kk * 2048, 16384, 1024);
                     mma_bf16_ss(tmem + D2_COL + BN * b, ad, bd, id2, kk > 0 ? 1u : 0u);
                 }
                 issued = true;
@@ -270,65 +254,7 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 mbar_wait(&B.mmadone, 0, abort, WAIT_LIMIT);
             }
         }
-    } else if (warp >= 4 && warp < 8) {
-        // ------------------------------------------------------ converter
-        const int ct = threadIdx.x - 128;
-        int64_t it = 0;
-        for (int64_t t = t0; t < t1; ++t, ++it) {
-            int I, J;
-            tile_of<R>(t, P.nbc, P.nbr, I, J);
-            const int s = (int)(it % NSTAGE);
-            const uint32_t us = (uint32_t)(it / NSTAGE);
-            // one thread waits (bounded) and the group leaves together
-            if (ct == 0) {
-                const bool ok = mbar_wait(&B.fullA[s], us & 1, abort, WAIT_LIMIT);
-                if (!ok) fail(B, P.d_status);
-                B.conv_ok = ok ? 1 : 0;
-            }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            if (!B.conv_ok) break;
-            const bool diag = J < R * I + R;
-            const int64_t gi0 = (int64_t)BM * I, gj0 = (int64_t)BN * J;
-            uint8_t *base = sm + OFF_A + s * A_STAGE;
-#pragma unroll 1
-            for (int half = 0; half < BM / 128; ++half) {
-                float4 va[8], vb[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int g = i * 128 + ct;
-                    const int r = 128 * half + (g >> 3), cc = g & 7;
-                    const int box = cc >> 2, ch0 = 2 * (cc & 3);
-                    const uint8_t *row = base + box * (A_STAGE / 2) + r * 128;
-                    va[i] = *reinterpret_cast<const float4 *>(row + ((ch0 ^ (r & 7)) << 4));
-                    vb[i] = *reinterpret_cast<const float4 *>(row + (((ch0 + 1) ^ (r & 7)) << 4));
-                }
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int g = i * 128 + ct;
-                    const int r = 128 * half + (g >> 3), cc = g & 7;
-                    float e[8] = {va[i].x, va[i].y, va[i].z, va[i].w, vb[i].x, vb[i].y, vb[i].z, vb[i].w};
-                    if (diag) {
-                        const int64_t gi = gi0 + r;
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int64_t gj = gj0 + 8 * cc + q;
-                            e[q] = gj > gi ? e[q] : (gj == gi ? 0.5f * e[q] : 0.0f);
-                        }
-                    }
-                    uint4 o;
-                    o.x = pack_bf16(e[0], e[1]);
-                    o.y = pack_bf16(e[2], e[3]);
-                    o.z = pack_bf16(e[4], e[5]);
-                    o.w = pack_bf16(e[6], e[7]);
-                    *reinterpret_cast<uint4 *>(base + r * 128 + ((cc ^ (r & 7)) << 4)) = o;
-                }
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&B.convA[s]);
-        }
-    } else if (warp >= 8) {
+    } else if (warp >= 4) {
         // ------------------------------------------------------- epilogue
         const int q = warp & 3;                // TMEM lane quarter of this warp
         const int c = 32 * q + lane;           // column of X / Y held by this thread
@@ -340,12 +266,12 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         float *ycol = P.Y + (int64_t)c * P.ldy;
         for (int64_t t = t0; t < t1; ++t, ++it) {
             int I, J;
-            tile_of<R>(t, P.nbc, P.nbr, I, J);
+            tile_of(t, P.nbc, P.nbr, I, J);
             if (I != curI) {
                 curI = I;
                 has_diag = (J == R * I);
             }
-            const bool last = last_in_row_run<R>(t, t1, I, P);
+            const bool last = last_in_row_run(t, t1, I, P);
             const int b = (int)(it & 1);
             const uint32_t ub = (uint32_t)(it >> 1);
             {
@@ -436,9 +362,40 @@ __global__ void to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t
     }
 }
 
-// the configuration used by the pass: 256-row tiles, two A stages (128-row
-// tiles with four stages measured slower: twice the reductions of D2)
-constexpr int TILE_BM = 256, TILE_STAGES = 2;
+// BF16 image A' of the block upper triangle of A (see the top of this file).
+// Block: 16 rows x 64 columns, 16 threads per row, one float4 of A and one
+// 8-byte store of A' per thread.  grid.x: 64-column tiles, grid.y: 16-row
+// chunks; tiles left of the diagonal 256 x 256 block exit at once.
+__global__ void __launch_bounds__(256)
+pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
+                       uint16_t *__restrict__ Ab, int64_t ldb, int vec)
+{
+    const int64_t r = (int64_t)blockIdx.y * 16 + (threadIdx.x >> 4);
+    const int64_t cbase = (int64_t)blockIdx.x * BN;
+    const int64_t blk0 = (r / BM) * BM;               // first column of the diagonal block
+    if (cbase + BN <= blk0) return;                   // uniform across the block
+    const int64_t c0 = cbase + 4 * (threadIdx.x & 15);
+    float v[4];
+    if (r < n && vec && c0 + 4 <= n) {
+        const float4 a = __ldcs(reinterpret_cast<const float4 *>(A + r * lda + c0));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (r < n && c0 + q < n) ? A[r * lda + c0 + q] : 0.0f;
+    }
+    if (cbase < blk0 + BM) {
+        // diagonal block: keep the strict upper part, halve the diagonal
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t c = c0 + q;
+            v[q] = c > r ? v[q] : (c == r ? 0.5f * v[q] : 0.0f);
+        }
+    }
+    uint2 o;
+    o.x = pack_bf16(v[0], v[1]);
+    o.y = pack_bf16(v[2], v[3]);
+    *reinterpret_cast<uint2 *>(Ab + r * ldb + c0) = o;
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 {
@@ -457,16 +414,30 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 
 }  // namespace
 
-cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const float *A, int64_t n, int64_t lda,
-                               const float *X, int64_t ldx, int m, const double *d_shift, float *Y,
-                               int64_t ldy, int prec, uint16_t *Xhi, uint16_t *Xlo, int64_t ldh,
-                               int *d_status)
+int64_t psd_bf16_image_pad(int64_t n) { return psd_round_up(n, BM); }
+
+cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab,
+                             int64_t ldb)
 {
-    (void)Xlo;
-    if (prec != PSDPROJ_PREC_BF16) return cudaErrorNotSupported;
+    const int64_t npad = psd_bf16_image_pad(n);
+    if (ldb < npad || (ldb % 8) != 0 || (reinterpret_cast<uintptr_t>(Ab) & 15) != 0)
+        return cudaErrorInvalidValue;
+    const int vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+    dim3 grid((unsigned)(npad / BN), (unsigned)(npad / 16));
+    pack_upper_bf16_kernel<<<grid, 256, 0, s>>>(A, n, lda, Ab, ldb, vec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t ldb,
+                               int64_t n, const float *X, int64_t ldx, int m,
+                               const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
+                               int64_t ldh, int *d_status)
+{
+    const int64_t npad = psd_bf16_image_pad(n);
     if (m < 1 || m > 128) return cudaErrorNotSupported;
-    if ((lda % 4) != 0 || (reinterpret_cast<uintptr_t>(A) & 15) != 0) return cudaErrorNotSupported;
-    if ((ldh % 8) != 0 || (reinterpret_cast<uintptr_t>(Xhi) & 15) != 0 || ldh < n)
+    if (ldb < npad || (ldb % 8) != 0 || (reinterpret_cast<uintptr_t>(Ab) & 15) != 0)
+        return cudaErrorNotSupported;
+    if ((ldh % 8) != 0 || (reinterpret_cast<uintptr_t>(Xh) & 15) != 0 || ldh < n)
         return cudaErrorNotSupported;
     auto encode = get_encode();
     if (!encode) return cudaErrorNotSupported;
@@ -476,18 +447,18 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const float *A, int
         const int64_t total = n * (int64_t)m;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4096) blocks = 4096;
-        to_bf16_kernel<<<blocks, 256, 0, s>>>(X, ldx, n, m, reinterpret_cast<__nv_bfloat16 *>(Xhi), ldh);
+        to_bf16_kernel<<<blocks, 256, 0, s>>>(X, ldx, n, m, reinterpret_cast<__nv_bfloat16 *>(Xh), ldh);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     CUtensorMap tmA, tmX;
     {
-        cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
-        cuuint64_t strides[1] = {(cuuint64_t)lda * 4};
-        cuuint32_t box[2] = {32, (cuuint32_t)TILE_BM};
+        cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)npad};
+        cuuint64_t strides[1] = {(cuuint64_t)ldb * 2};
+        cuuint32_t box[2] = {(cuuint32_t)BN, (cuuint32_t)BM};
         cuuint32_t estr[2] = {1, 1};
-        if (encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(A), dims, strides, box,
-                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+        if (encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(Ab), dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
@@ -496,7 +467,7 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const float *A, int
         cuuint64_t strides[1] = {(cuuint64_t)ldh * 2};
         cuuint32_t box[2] = {64, 128};
         cuuint32_t estr[2] = {1, 1};
-        if (encode(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xhi, dims, strides, box, estr,
+        if (encode(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xh, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
@@ -504,9 +475,8 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const float *A, int
     Params P;
     P.n = n;
     P.m = m;
-    P.nbr = (int)((n + TILE_BM - 1) / TILE_BM);
-    P.nbc = (int)((n + BN - 1) / BN);
-    constexpr int R = TILE_BM / BN;
+    P.nbr = (int)(npad / BM);
+    P.nbc = (int)(npad / BN);
     P.tiles = (int64_t)P.nbr * P.nbc - (int64_t)R * P.nbr * (P.nbr - 1) / 2;
     P.X = X;
     P.ldx = ldx;
@@ -519,12 +489,11 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const float *A, int
     cudaError_t e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(float), 0, (size_t)n * sizeof(float),
                                       (size_t)m, s);
     if (e != cudaSuccess) return e;
-    auto kern = sym_pass_bf16_kernel<TILE_BM, TILE_STAGES>;
-    constexpr uint32_t smem = Cfg<TILE_BM, TILE_STAGES>::SMEM_BYTES;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(sym_pass_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
     int grid = sm_count > 0 ? sm_count : 148;
     if ((int64_t)grid > P.tiles) grid = (int)P.tiles;
-    kern<<<grid, NT, smem, s>>>(tmA, tmX, P);
+    sym_pass_bf16_kernel<<<grid, NT, SMEM_BYTES, s>>>(tmA, tmX, P);
     return cudaGetLastError();
 }

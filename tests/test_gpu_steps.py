@@ -252,6 +252,35 @@ def test_eig_clusters_in_random_basis(ctx, m, method):
     assert np.linalg.norm(P - Pe) <= 5e-6 * nrm
 
 
+@pytest.mark.parametrize("method", [ps.EIG_AUTO, ps.EIG_JACOBI, ps.EIG_TRIDIAG])
+@pytest.mark.parametrize("m", [20, 110, 150])
+def test_eig_zero_rows_give_exact_zero_eigenvalues(ctx, m, method):
+    # zeroed rows / columns (the dependent columns of Q) must come back as
+    # eigenvalue exactly 0 with a unit vector, never as a small positive
+    rng = np.random.default_rng(300 + m)
+    X = rng.standard_normal((m, m))
+    C = (X + X.T) / 2
+    dead = [1, 7, m // 2, m - 1]
+    C[dead, :] = 0.0
+    C[:, dead] = 0.0
+    V = torch.zeros(m, m, dtype=torch.float32, device="cuda")
+    d = torch.zeros(m, dtype=torch.float64, device="cuda")
+    ctx.eig(torch.from_numpy(np.ascontiguousarray(C.T)).cuda(), V, d, method=method)
+    assert ctx.sync_status() == 0
+    dv = d.cpu().numpy()
+    Vv = V.cpu().numpy().T.astype(np.float64)
+    ref = np.linalg.eigvalsh(C)[::-1]
+    assert np.all(np.diff(dv) <= 0)
+    assert np.abs(dv - ref).max() <= 2e-6 * np.linalg.norm(C)
+    assert int((dv == 0.0).sum()) >= len(dead)
+    live = np.ones(m, bool); live[dead] = False
+    assert int((dv > 0).sum()) == int((np.linalg.eigvalsh(C[np.ix_(live, live)]) > 0).sum())
+    for i in dead:
+        col = np.flatnonzero(np.abs(Vv[i, :]) == 1.0)
+        assert col.size == 1 and dv[col[0]] == 0.0
+    assert np.abs(Vv.T @ Vv - np.eye(m)).max() <= 2e-5
+
+
 def test_eig_auto_skips_jacobi_when_tridiagonal_succeeds(ctx):
     # AUTO = the tridiagonal result bit for bit when no failure is flagged
     m = 110
@@ -371,20 +400,33 @@ def test_sym_pass_bf16_lower_triangle_and_strides(ctx, oracle_lib):
         assert np.all(np.abs(y - ref) <= 8 * np.sqrt(n) * EPS32 * bound)
 
 
-def test_sym_pass_tensor_core_unsupported_layouts(ctx):
-    n = 10
-    A = torch.zeros(n, n, device="cuda")          # lda = 10: not a multiple of 4
-    X = ps.tall_empty(n, 2)
-    Y = ps.tall_empty(n, 2)
-    with pytest.raises(ps.PsdprojError) as ei:
-        ctx.sym_pass(A, X, Y, prec=ps.PREC_BF16)
-    assert ei.value.code == 7
+def test_sym_pass_bf16_any_lda(ctx, oracle_lib):
+    # lda = 10 (not a multiple of 4): the BF16 image is packed with scalar loads
+    n, m = 10, 2
+    A = _sym_A(n, seed=21)
+    X = np.random.default_rng(22).standard_normal((n, m)).astype(np.float32)
+    Y = ps.tall_empty(n, m)
+    ctx.sym_pass(torch.from_numpy(A).cuda(), _tall_from_np(X), Y, prec=ps.PREC_BF16)
+    assert ctx.sync_status() == 0
+    Ab, Xb = _bf16(A).astype(np.float64), _bf16(X).astype(np.float64)
+    ref = oracle_lib.sym_mul(Ab, Xb)
+    bound = np.abs(Ab) @ np.abs(Xb)
+    assert np.all(np.abs(_np(Y) - ref) <= 8 * np.sqrt(n) * EPS32 * bound + 1e-30)
+
+
+def test_sym_pass_tensor_core_unsupported(ctx):
     A2 = torch.zeros(200, 200, device="cuda")
     X2 = ps.tall_empty(200, 129)
     Y2 = ps.tall_empty(200, 129)
     with pytest.raises(ps.PsdprojError) as ei:
         ctx.sym_pass(A2, X2, Y2, prec=ps.PREC_BF16)   # m > 128
     assert ei.value.code == 7
+    X3 = ps.tall_empty(200, 8)
+    Y3 = ps.tall_empty(200, 8)
+    for prec in (ps.PREC_TF32, ps.PREC_BF16X3):        # A-pass forms not provided
+        with pytest.raises(ps.PsdprojError) as ei:
+            ctx.sym_pass(A2, X3, Y3, prec=prec)
+        assert ei.value.code == 7
 
 
 # ----------------------------------------------------------------------------
