@@ -135,10 +135,10 @@ uint64_t psdproj_kernel_launches(void);
  * NULL) receives r+, the number of positive eigenvalues of Q^T A Q.
  * opts may be NULL (defaults).  With opts->prec = PSDPROJ_PREC_BF16 (needs
  * k+p <= 128) the call first packs A's block upper triangle into the
- * context's BF16 image (npad x npad, npad = n rounded up to 256; kept for
- * later calls) and every product with A, the power iterations of
- * psdproj_alg2 included, reads that image on the tensor cores or CUDA cores
- * with FP32 accumulation. */
+ * context's BF16 image (256 x 64 tiles stored contiguously, about n^2 + 128 n
+ * bytes; kept for later calls) and every product with A, the power
+ * iterations of psdproj_alg2 included, reads that image on the tensor cores
+ * or CUDA cores with FP32 accumulation. */
 int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                  int k, int p, int q, uint64_t seed,
                  float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,

@@ -179,12 +179,12 @@ int check_opts(const psdproj_opts *o)
 }
 
 // The BF16 image of A used by the tensor-core passes: allocated on first
-// use (npad x npad BF16, kept for later calls) and written from A.
+// use (psd_tile_count(n) tiles of 32 KB, kept for later calls) and written
+// from A.
 int pack_bf16_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda)
 {
-    const int64_t npad = psd_bf16_image_pad(n);
-    const size_t bytes = sizeof(uint16_t) * (size_t)npad * (size_t)npad;
-    if (ctx->Ab_bytes < bytes || ctx->Ab_ld < npad) {
+    const size_t bytes = sizeof(uint16_t) * (size_t)psd_tile_count(n) * (size_t)PSD_TILE_ELEMS;
+    if (ctx->Ab_bytes < bytes) {
         if (ctx->Ab) {
             cudaStreamSynchronize(ctx->stream);
             cudaFree(ctx->Ab);
@@ -195,9 +195,8 @@ int pack_bf16_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda)
         if (e != cudaSuccess) return cuda_status(e);
         ctx->Ab_bytes = bytes;
     }
-    ctx->Ab_ld = npad;
     stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
-    PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab, ctx->Ab_ld), 1);
+    PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab), 1);
     return PSDPROJ_OK;
 }
 
@@ -213,8 +212,8 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
     }
     if (prec != PSDPROJ_PREC_BF16) return PSDPROJ_ENOTSUP;
     psd_workspace &ws = ctx->ws;
-    PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->sm_count, ctx->Ab, ctx->Ab_ld, n, X, ldx, m,
-                              d_shift, Y, ldy, ws.Xhi, ws.ld, ctx->d_status), 2);
+    PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->sm_count, ctx->Ab, n, X, ldx, m, d_shift, Y, ldy,
+                              ws.Xhi, ws.ld, ctx->d_status), 2);
     return PSDPROJ_OK;
 }
 
@@ -273,12 +272,13 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         if (!(alpha_in > 0.0)) {
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
             if (tc) {
-                PSD_KL(launch_power_iteration_bf16(s, ctx->Ab, ctx->Ab_ld, n, opts.N, seed, 3u, nullptr,
-                                                   ws.pv0, ws.pv1, sc, ws.counter, sc + SC_SIGMA1),
+                PSD_KL(launch_power_iteration_bf16(s, ctx->sm_count, ctx->Ab, n, opts.N, seed, 3u, nullptr,
+                                                   ws.pv0, ws.pv1, sc, ws.counter, sc + SC_SIGMA1,
+                                                   ctx->d_status),
                        opts.N + 3);
-                PSD_KL(launch_power_iteration_bf16(s, ctx->Ab, ctx->Ab_ld, n, opts.N, seed, 4u,
+                PSD_KL(launch_power_iteration_bf16(s, ctx->sm_count, ctx->Ab, n, opts.N, seed, 4u,
                                                    sc + SC_SIGMA1, ws.pv0, ws.pv1, sc, ws.counter,
-                                                   sc + SC_SIGMA2),
+                                                   sc + SC_SIGMA2, ctx->d_status),
                        opts.N + 3);
             } else {
                 PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,

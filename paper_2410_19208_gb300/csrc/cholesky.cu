@@ -162,22 +162,24 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
             s_bad = bad;
         }
     }
-    // this thread's upper-triangle entries (fixed for the whole factorization)
-    int ei[EPT], ek[EPT];
+    // this thread's upper-triangle entries (fixed for the whole factorization),
+    // packed as i | k << 16.  They are counted from the END of the row-major
+    // order (slot c holds entry nup - 1 - (tid + c NT)), so the entries still
+    // to update at column j, rows >= j, are slot prefixes: a thread stops at
+    // its first finished slot.
+    int eik[EPT];
 #pragma unroll
     for (int c = 0; c < EPT; ++c) {
-        const int e = tid + c * NT;
-        ei[c] = -1;
-        ek[c] = 0;
-        if (in_smem && e < nup) {
+        const int e = nup - 1 - (tid + c * NT);
+        eik[c] = -1;
+        if (in_smem && e >= 0) {
             // e -> (i <= k), row-major over the upper triangle
             const float hb = 2.0f * m + 1.0f;
             int i = (int)((hb - sqrtf(fmaxf(hb * hb - 8.0f * e, 0.0f))) * 0.5f);
             i = max(0, min(i, m - 1));
             while (i > 0 && i * m - i * (i - 1) / 2 > e) --i;
             while (i + 1 < m && (i + 1) * m - (i + 1) * i / 2 <= e) ++i;
-            ei[c] = i;
-            ek[c] = i + (e - (i * m - i * (i - 1) / 2));
+            eik[c] = i | ((i + (e - (i * m - i * (i - 1) / 2))) << 16);
         }
     }
     __syncthreads();
@@ -197,30 +199,47 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
     if (tid == 0) pivot(0, U[0]);
     __syncthreads();
 
-    for (int j = 0; j < m; ++j) {
-        // phase A: row j of R into rowj (the update's operand) and Rf
-        const bool dj = s_dead[j] != 0;
-        const T inv = s_inv[j];
-        for (int k = j + tid; k < m; k += NT) {
-            const T v = (k == j) ? s_r[j] : (dj ? N::zero() : N::mul(U[j * ldu + k], inv));
-            rowj[k] = (k == j) ? N::zero() : v;
-            Rf[j * ldu + k] = N::hi(v);
-        }
-        __syncthreads();
-        // phase B: trailing update U(i,k) -= R(j,i) R(j,k), j < i <= k; the
-        // thread that updates U(j+1, j+1) also forms the next pivot
-        if (in_smem) {
+    if (in_smem) {
+        // One phase and one barrier per column.  Row j of U is final when
+        // column j starts and is only read in its phase: the owners of
+        // (j, k) write row j of R, the owners of (i, k), i > j, update
+        //   U(i,k) -= U(j,i) U(j,k) / R_jj^2,
+        // and the owner of (j+1, j+1) forms the next pivot.  A thread takes
+        // its entries in groups of G, loads first, so the loads overlap.
+        for (int j = 0; j < m; ++j) {
+            const bool dj = s_dead[j] != 0;
+            const T inv = s_inv[j];
+            const T inv2 = N::mul(inv, inv);
+            const T *rowU = U + j * ldu;
+            const int nact = nup - (j * m - j * (j - 1) / 2);   // entries (i, k), i >= j
 #pragma unroll
             for (int c = 0; c < EPT; ++c) {
-                if (ei[c] > j) {
-                    const int i = ei[c], k = ek[c];
-                    T u = U[i * ldu + k];
-                    if (!dj) u = N::fms(u, rowj[i], rowj[k]);
+                if (tid + c * NT >= nact) break;
+                const int i = eik[c] & 0xFFFF, k = eik[c] >> 16;
+                const T u0 = U[i * ldu + k];
+                if (i == j) {
+                    Rf[j * ldu + k] = (k == j) ? N::hi(s_r[j]) : (dj ? 0.0f : N::hi(N::mul(u0, inv)));
+                } else {
+                    T u = u0;
+                    if (!dj) u = N::fms(u, N::mul(rowU[i], inv2), rowU[k]);
                     U[i * ldu + k] = u;
                     if (i == j + 1 && k == j + 1) pivot(j + 1, u);
                 }
             }
-        } else {
+            __syncthreads();
+        }
+    } else {
+        for (int j = 0; j < m; ++j) {
+            // phase A: row j of R into rowj (the update's operand) and Rf
+            const bool dj = s_dead[j] != 0;
+            const T inv = s_inv[j];
+            for (int k = j + tid; k < m; k += NT) {
+                const T v = (k == j) ? s_r[j] : (dj ? N::zero() : N::mul(U[j * ldu + k], inv));
+                rowj[k] = (k == j) ? N::zero() : v;
+                Rf[j * ldu + k] = N::hi(v);
+            }
+            __syncthreads();
+            // phase B: trailing update U(i,k) -= R(j,i) R(j,k), j < i <= k
             const int t = m - j - 1;
             if (!dj) {
                 for (int e = tid; e < t * t; e += NT) {
@@ -232,8 +251,8 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
             }
             // e = 0 is entry (j+1, j+1), updated by thread 0 above
             if (tid == 0 && t > 0) pivot(j + 1, U[(j + 1) * ldu + (j + 1)]);
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     // R^-1 (upper, FP32), one warp per column j: back substitution in axpy

@@ -23,6 +23,26 @@ static inline int64_t psd_ld(int64_t n) { return psd_round_up(n, 128); }
 static inline int psd_lpad(int m) { return (int)psd_round_up(m, 16); }
 
 constexpr int PSD_GRAM_CHUNK = 64;    // rows per Gram partial
+
+// Tiles of the BF16 image of A (tensor-core pass and BF16 power iteration):
+// the block upper triangle of A in tiles of 256 rows x 64 columns, stored
+// tile after tile in row-major tile order (block row I holds the tiles
+// J = 4 I .. nbc - 1), each tile 32 KB in the 128-byte-swizzled layout of a
+// UMMA operand: row r at r * 128 bytes, its 16-byte chunk k (columns
+// 8k..8k+7) at position k ^ (r & 7) within the row.
+constexpr int PSD_TILE_M = 256, PSD_TILE_N = 64;
+constexpr int PSD_TILE_R = PSD_TILE_M / PSD_TILE_N;
+constexpr int64_t PSD_TILE_ELEMS = (int64_t)PSD_TILE_M * PSD_TILE_N;
+// first tile of block row I (nbc = 64-column tiles of the padded matrix)
+__host__ __device__ inline int64_t psd_tile_row_start(int I, int nbc)
+{
+    return (int64_t)I * nbc - (int64_t)PSD_TILE_R * I * (I - 1) / 2;
+}
+__host__ __device__ inline int64_t psd_tile_count(int64_t n)
+{
+    const int nbr = (int)((n + PSD_TILE_M - 1) / PSD_TILE_M);
+    return psd_tile_row_start(nbr, nbr * PSD_TILE_R);
+}
 constexpr int PSD_MAX_M = 256;        // largest sketch width
 
 struct psd_workspace {
@@ -74,7 +94,6 @@ struct psdproj_ctx {
     // BF16 image of the block upper triangle of A (tensor-core passes)
     uint16_t *Ab = nullptr;
     size_t Ab_bytes = 0;
-    int64_t Ab_ld = 0;
 };
 
 // Make sure the workspace holds n rows x m columns; may synchronise the
@@ -90,21 +109,17 @@ cudaError_t launch_sym_pass_simt(cudaStream_t s, const float *A, int64_t n, int6
                                  const float *X, int64_t ldx, int m, const double *d_shift,
                                  float *Y, int64_t ldy);
 
-// Rows and columns of the BF16 image of an n x n matrix (n rounded up to the
-// 256-row tiles of the tensor-core pass).
-int64_t psd_bf16_image_pad(int64_t n);
-
 // BF16 image A' of the block upper triangle of A (256 x 256 diagonal blocks
-// strictly upper, diagonal halved, zero below; A = A' + A'^T), npad x npad
-// with leading dimension ldb (>= npad, multiple of 8), zero padded.
-cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab,
-                             int64_t ldb);
+// strictly upper, diagonal halved, zero below; A = A' + A'^T), in the tile
+// layout described with PSD_TILE_M (psd_tile_count(n) tiles of 32 KB), zero
+// padded past row / column n.  Ab 16-byte aligned.
+cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab);
 
 // Tensor-core symmetric pass Y = (A' + A'^T) X + shift X on the BF16 image;
 // Xh (ldh >= n, multiple of 8) receives the BF16 image of X.  Returns
 // cudaErrorNotSupported when the configuration is outside what the kernel
 // handles (m > 128, misaligned buffers).
-cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t ldb,
+cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t n, const float *X, int64_t ldx, int m,
                                const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
                                int64_t ldh, int *d_status);
@@ -157,10 +172,10 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
                                    double *scal, unsigned *counter, double *d_sigma);
 
 // The same on the BF16 image (launch_pack_bf16); v0, v1 16-byte aligned.
-cudaError_t launch_power_iteration_bf16(cudaStream_t s, const uint16_t *Ab, int64_t ldb, int64_t n,
+cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t n,
                                         int N, uint64_t seed, uint32_t stream_id,
                                         const double *d_shift_neg, float *v0, float *v1, double *scal,
-                                        unsigned *counter, double *d_sigma);
+                                        unsigned *counter, double *d_sigma, int *d_status);
 
 cudaError_t launch_alpha_finish(cudaStream_t s, const double *d_s1, const double *d_s2,
                                 double alpha_in, double *d_alpha, double *d_shift,

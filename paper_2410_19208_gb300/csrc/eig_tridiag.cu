@@ -33,6 +33,15 @@ constexpr int NT = 512;
 constexpr int SMEM_M = 128;   // largest m kept in shared memory
 constexpr int NBIS = 12;      // 5-way multisection steps: width 2.4e-9 of the start interval
 
+// sum of the NT / 32 = 16 warp partials (four 16-byte loads, tree adds)
+__device__ __forceinline__ float sum16(const float *red)
+{
+    const float4 a = reinterpret_cast<const float4 *>(red)[0], b = reinterpret_cast<const float4 *>(red)[1];
+    const float4 c = reinterpret_cast<const float4 *>(red)[2], d = reinterpret_cast<const float4 *>(red)[3];
+    return (((a.x + a.y) + (a.z + a.w)) + ((b.x + b.y) + (b.z + b.w))) +
+           (((c.x + c.y) + (c.z + c.w)) + ((d.x + d.y) + (d.z + d.w)));
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -181,7 +190,8 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     float *T = Z + mfull * ld;                      // scratch of the twisted factorization
     __shared__ float d[PSD_MAX_M], e[PSD_MAX_M], ee[PSD_MAX_M], beta[PSD_MAX_M];
     __shared__ float vv[PSD_MAX_M], pp[PSD_MAX_M], lam[PSD_MAX_M];
-    __shared__ float red[NT / 32];
+    __shared__ __align__(16) float red[NT / 32];
+    static_assert(NT / 32 == 16, "sum16");
     __shared__ int cl_start[PSD_MAX_M];
     __shared__ int s_pos[PSD_MAX_M], s_src[PSD_MAX_M];
     __shared__ int s_fail, s_mc;
@@ -238,8 +248,7 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
         part = warp_sum(part);
         if (lane == 0) red[warp] = part;
         __syncthreads();
-        float tail = 0.0f;
-        for (int w = 0; w < NT / 32; ++w) tail += red[w];
+        const float tail = sum16(red);
         const float x0 = A[r0 * ld + j];
         const bool skip = !(tail > 0.0f);           // column already tridiagonal
         const float sigma = sqrtf(fmaf(x0, x0, tail));
@@ -271,8 +280,7 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
         }
         if (lane == 0) red[warp] = pv;
         __syncthreads();
-        float vtp = 0.0f;
-        for (int w = 0; w < NT / 32; ++w) vtp += red[w];
+        const float vtp = sum16(red);
         const float K = 0.5f * bt * vtp;
         // A22 -= v w^T + w v^T with w = p - K v (rows by warp, columns by
         // lane); the reflector goes below the subdiagonal

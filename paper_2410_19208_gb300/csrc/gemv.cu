@@ -9,6 +9,7 @@
 // clears the other vector for the next product, and resets the ticket.
 // sigma = ||A v|| after the N normalised steps is written to *d_sigma.
 #include "ctx.h"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -165,15 +166,26 @@ sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
     for (int64_t i = threadIdx.x; i < n; i += NTW) other[i] = 0.0f;
 }
 
-// The same product on the BF16 image A' of the block upper triangle
-// (A = A' + A'^T; written by the tensor-core pass's pack kernel, zero padded
-// to npad = a multiple of 256).  Block row of 32 rows from row0: its tiles
-// start at the first column of its 256 x 256 diagonal block and are 256
-// columns wide (lane l: columns 8l..8l+7, one 16-byte load per row); no
-// entry needs masking, and the diagonal block's halved diagonal enters once
-// through the row sums and once through the column sums.
-constexpr int TCB = 256;   // columns per BF16 tile
-constexpr int SEGB = 4;    // tiles per block
+// The same product on the tiled BF16 image A' of the block upper triangle
+// (A = A' + A'^T; written by the tensor-core pass's pack kernel, tiles of
+// 256 x 64 in 128-byte-swizzled rows, stored in row-major tile order).  A
+// persistent CTA (two per SM) streams a contiguous range of tiles into a three-stage ring
+// by bulk copies (one producer thread, bounded mbarrier waits) and eight
+// compute warps read them from shared memory: thread (g, k) owns rows
+// 8g..8g+7 and columns 8k..8k+7 of a tile.  Row sums stay in registers over
+// a run of tiles in one block row and are reduced when the run ends; column
+// sums are reduced per tile (warp shuffles, then a shared table over the
+// eight warps) and added to y with atomics.  No entry needs masking; the
+// diagonal block's halved diagonal enters once through each side.
+namespace gt {
+constexpr int STAGES = 3;
+constexpr int CTAS_PER_SM = 2;    // two CTAs per SM: one computes while the other waits
+constexpr uint32_t TILE_BYTES = (uint32_t)PSD_TILE_ELEMS * 2;
+constexpr int NCOMP = 256;               // compute threads (warps 0-7)
+constexpr int NTG = NCOMP + 32;          // + producer warp 8
+constexpr uint32_t SMEM = STAGES * TILE_BYTES + 1024;
+constexpr long long WAIT_LIMIT = 4000000000LL;
+}
 
 __device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
 {
@@ -183,104 +195,179 @@ __device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
     a[6] = __uint_as_float(u.w << 16); a[7] = __uint_as_float(u.w & 0xFFFF0000u);
 }
 
-__global__ void __launch_bounds__(NTW)
-sym_gemv_bf16_kernel(const uint16_t *__restrict__ Ab, int64_t ldb, int64_t n, int64_t npad,
-                     const float *__restrict__ x, float *__restrict__ y, float *__restrict__ other,
-                     double *scal, unsigned *counter, const double *d_shift_neg, double *d_sigma,
-                     unsigned nactive)
+__global__ void __launch_bounds__(gt::NTG, gt::CTAS_PER_SM)
+sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64_t tiles,
+                      const float *__restrict__ x, float *__restrict__ y, float *__restrict__ other,
+                      double *scal, unsigned *counter, const double *d_shift_neg, double *d_sigma,
+                      int *d_status)
 {
-    __shared__ float colsum[8][SEGB * TCB];
-    __shared__ double red[NTW / 32];
+    using namespace tc;
+    extern __shared__ __align__(1024) uint8_t smt[];
+    __shared__ uint64_t full[gt::STAGES], empty[gt::STAGES];
+    __shared__ float colred[2][8][PSD_TILE_N];
+    __shared__ double red[gt::NTG / 32];
+    __shared__ int s_abort;       // any role gave up: stop waiting
+    __shared__ int s_cabort;      // compute warps: written before, read after their barrier
     __shared__ bool s_last;
-    const int64_t row0 = (int64_t)blockIdx.y * TRW;
-    const int64_t cs = (row0 / 256) * 256;
-    const int tiles = (int)((npad - cs) / TCB);
-    const int t0 = (int)blockIdx.x * SEGB;
-    if (t0 >= tiles) return;
+    const int nbc = nbr * PSD_TILE_R;
+    const int64_t t0 = tiles * blockIdx.x / gridDim.x;
+    const int64_t t1 = tiles * (blockIdx.x + 1) / gridDim.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < gt::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 8);
+        }
+        s_abort = 0;
+        s_cabort = 0;
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    volatile int *abort = &s_abort;
+    volatile int *cabort = &s_cabort;
     const float sc = (float)scal[0];
     const float shift = d_shift_neg ? (float)(-(*d_shift_neg)) : 0.0f;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    float rowacc[4] = {0.f, 0.f, 0.f, 0.f};
-    float xr[4];
-    const uint16_t *rowp[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t gr = row0 + warp * 4 + i;      // < npad
-        xr[i] = gr < n ? x[gr] * sc : 0.0f;
-        rowp[i] = Ab + gr * ldb;
-    }
-    const int nt = min(SEGB, tiles - t0);
-    uint4 nxt[4];
-    {
-        const int64_t c0 = cs + (int64_t)t0 * TCB + lane * 8;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) nxt[i] = __ldcs(reinterpret_cast<const uint4 *>(rowp[i] + c0));
-    }
-#pragma unroll 1
-    for (int t = 0; t < nt; ++t) {
-        const int64_t c0 = cs + (int64_t)(t0 + t) * TCB + lane * 8;
-        uint4 cur[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
-        if (t + 1 < nt) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                nxt[i] = __ldcs(reinterpret_cast<const uint4 *>(rowp[i] + c0 + TCB));
+    if (warp == 8) {
+        // ---- producer: one bulk copy per tile
+        if (lane == 0) {
+            int64_t it = 0;
+            for (int64_t t = t0; t < t1; ++t, ++it) {
+                const int s = (int)(it % gt::STAGES);
+                const uint32_t us = (uint32_t)(it / gt::STAGES);
+                if (!mbar_wait(&empty[s], (us & 1) ^ 1, abort, gt::WAIT_LIMIT)) {
+                    s_abort = 1;
+                    psd_set_status(d_status, PSDPROJ_ETIMEOUT);
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], gt::TILE_BYTES);
+                bulk_load(smt + s * gt::TILE_BYTES, Ab + t * PSD_TILE_ELEMS, gt::TILE_BYTES, &full[s]);
+            }
+            const int64_t n_it = it;
+            for (int64_t k = (n_it > gt::STAGES ? n_it - gt::STAGES : 0); k < n_it; ++k)
+                mbar_wait(&full[k % gt::STAGES], (uint32_t)((k / gt::STAGES) & 1), abort, gt::WAIT_LIMIT);
         }
-        float xc[8];
-        if (c0 + 8 <= n) {
-            const float4 x0 = __ldg(reinterpret_cast<const float4 *>(x + c0));
-            const float4 x1 = __ldg(reinterpret_cast<const float4 *>(x + c0 + 4));
-            xc[0] = x0.x * sc; xc[1] = x0.y * sc; xc[2] = x0.z * sc; xc[3] = x0.w * sc;
-            xc[4] = x1.x * sc; xc[5] = x1.y * sc; xc[6] = x1.z * sc; xc[7] = x1.w * sc;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) xc[j] = (c0 + j < n) ? x[c0 + j] * sc : 0.0f;
+    } else if (t0 < t1) {
+        // ---- compute: thread (g, k): rows 8g..8g+7, columns 8k..8k+7 of each tile
+        const int g = threadIdx.x >> 3, k = threadIdx.x & 7;
+        int I = 0, J = 0;
+        {
+            int lo = 0, hi = nbr - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (psd_tile_row_start(mid, nbc) <= t0) lo = mid; else hi = mid - 1;
+            }
+            I = lo;
+            J = PSD_TILE_R * lo + (int)(t0 - psd_tile_row_start(lo, nbc));
         }
-        float colacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float rowacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float xr[8];
+        bool has_diag = false;
+        auto load_xr = [&](int Iv) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float a[8];
-            bf16x8_to_f32(cur[i], a);
+            for (int u = 0; u < 8; ++u) {
+                const int64_t gr = (int64_t)Iv * PSD_TILE_M + 8 * g + u;
+                xr[u] = gr < n ? x[gr] * sc : 0.0f;
+            }
+        };
+        load_xr(I);
+        int64_t it = 0;
+        for (int64_t t = t0; t < t1; ++t, ++it) {
+            if (J == PSD_TILE_R * I) has_diag = true;
+            const int s = (int)(it % gt::STAGES);
+            const uint32_t us = (uint32_t)(it / gt::STAGES);
+            // a warp whose bounded wait fails records the abort but still
+            // reaches the barrier below; every warp leaves after it together
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&full[s], us & 1, abort, gt::WAIT_LIMIT) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok && lane == 0) {
+                *cabort = 1;
+                *abort = 1;
+                psd_set_status(d_status, PSDPROJ_ETIMEOUT);
+            }
+            float xc[8];
+            const int64_t c0 = (int64_t)J * PSD_TILE_N + 8 * k;
+            if (c0 + 8 <= n) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(x + c0));
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(x + c0 + 4));
+                xc[0] = a.x * sc; xc[1] = a.y * sc; xc[2] = a.z * sc; xc[3] = a.w * sc;
+                xc[4] = b.x * sc; xc[5] = b.y * sc; xc[6] = b.z * sc; xc[7] = b.w * sc;
+            } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                rowacc[i] = fmaf(a[j], xc[j], rowacc[i]);
-                colacc[j] = fmaf(a[j], xr[i], colacc[j]);
+                for (int v = 0; v < 8; ++v) xc[v] = (c0 + v < n) ? x[c0 + v] * sc : 0.0f;
+            }
+            float colacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const uint8_t *tile = smt + s * gt::TILE_BYTES;
+#pragma unroll
+            for (int u = 0; u < 8 && ok; ++u) {
+                const int r = 8 * g + u;                        // r & 7 == u
+                const uint4 q = *reinterpret_cast<const uint4 *>(tile + r * 128 + ((k ^ u) << 4));
+                float a[8];
+                bf16x8_to_f32(q, a);
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    rowacc[u] = fmaf(a[v], xc[v], rowacc[u]);
+                    colacc[v] = fmaf(a[v], xr[u], colacc[v]);
+                }
+            }
+            __syncwarp();
+            if (lane == 0 && ok) mbar_arrive(&empty[s]);
+            // column sums: over the four row groups of the warp, then the 8 warps
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                colacc[v] += __shfl_xor_sync(0xffffffffu, colacc[v], 8);
+                colacc[v] += __shfl_xor_sync(0xffffffffu, colacc[v], 16);
+            }
+            const int pb = (int)(it & 1);
+            if (lane < 8) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) colred[pb][warp][8 * k + v] = colacc[v];
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (*cabort) break;                      // uniform: read after the barrier
+            if (threadIdx.x < PSD_TILE_N) {
+                float cs = 0.0f;
+#pragma unroll
+                for (int w = 0; w < 8; ++w) cs += colred[pb][w][threadIdx.x];
+                const int64_t gc = (int64_t)J * PSD_TILE_N + threadIdx.x;
+                if (gc < n && cs != 0.0f) atomicAdd(&y[gc], cs);
+            }
+            // run end: the row sums of block row I
+            const bool last = (J == nbc - 1) || (t + 1 == t1);
+            if (last) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    float v = rowacc[u];
+                    v += __shfl_xor_sync(0xffffffffu, v, 1);
+                    v += __shfl_xor_sync(0xffffffffu, v, 2);
+                    v += __shfl_xor_sync(0xffffffffu, v, 4);
+                    rowacc[u] = 0.0f;
+                    const int64_t gr = (int64_t)I * PSD_TILE_M + 8 * g + u;
+                    if (k == 0 && gr < n) {
+                        if (has_diag) v = fmaf(shift, xr[u], v);
+                        atomicAdd(&y[gr], v);
+                    }
+                }
+                has_diag = false;
+            }
+            if (++J == nbc) {
+                ++I;
+                J = PSD_TILE_R * I;
+                load_xr(I);
             }
         }
-        float4 *dst = reinterpret_cast<float4 *>(&colsum[warp][t * TCB + lane * 8]);
-        dst[0] = make_float4(colacc[0], colacc[1], colacc[2], colacc[3]);
-        dst[1] = make_float4(colacc[4], colacc[5], colacc[6], colacc[7]);
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < nt * TCB; c += NTW) {
-        float sacc = 0.0f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) sacc += colsum[w][c];
-        const int64_t gc = cs + (int64_t)t0 * TCB + c;
-        if (gc < n && sacc != 0.0f) atomicAdd(&y[gc], sacc);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float sacc = rowacc[i];
-        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-        const int64_t gr = row0 + warp * 4 + i;
-        if (lane == 0 && gr < n) {
-            if (t0 == 0) sacc = fmaf(shift, xr[i], sacc);  // the segment holding the diagonal
-            atomicAdd(&y[gr], sacc);
-        }
     }
 
-    // ticket: the last block finishes the product
+    // ticket: the last CTA finishes the product
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == nactive - 1);
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += NTW) {
+    for (int64_t i = threadIdx.x; i < n; i += gt::NTG) {
         const double v = (double)__ldcg(&y[i]);
         acc += v * v;
     }
@@ -289,14 +376,14 @@ sym_gemv_bf16_kernel(const uint16_t *__restrict__ Ab, int64_t ldb, int64_t n, in
     __syncthreads();
     if (threadIdx.x == 0) {
         double sacc = 0.0;
-        for (int w = 0; w < NTW / 32; ++w) sacc += red[w];
+        for (int w = 0; w < gt::NTG / 32; ++w) sacc += red[w];
         const double nrm = sqrt(sacc);
         scal[1] = nrm;
         scal[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
         if (d_sigma) *d_sigma = nrm;
         *counter = 0u;
     }
-    for (int64_t i = threadIdx.x; i < n; i += NTW) other[i] = 0.0f;
+    for (int64_t i = threadIdx.x; i < n; i += gt::NTG) other[i] = 0.0f;
 }
 
 __global__ void pi_init_kernel(double *scal, float *v1, int64_t n)
@@ -353,34 +440,31 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
     return cudaSuccess;
 }
 
-cudaError_t launch_power_iteration_bf16(cudaStream_t s, const uint16_t *Ab, int64_t ldb, int64_t n,
+cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t n,
                                         int N, uint64_t seed, uint32_t stream_id,
                                         const double *d_shift_neg, float *v0, float *v1, double *scal,
-                                        unsigned *counter, double *d_sigma)
+                                        unsigned *counter, double *d_sigma, int *d_status)
 {
-    const int64_t npad = psd_round_up(n, 256);
-    if (ldb < npad || (ldb % 8) != 0 || (reinterpret_cast<uintptr_t>(Ab) & 15) != 0 ||
-        (reinterpret_cast<uintptr_t>(v0) & 15) != 0 || (reinterpret_cast<uintptr_t>(v1) & 15) != 0)
+    if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0 || (reinterpret_cast<uintptr_t>(v0) & 15) != 0 ||
+        (reinterpret_cast<uintptr_t>(v1) & 15) != 0)
         return cudaErrorInvalidValue;
     cudaError_t e = launch_gaussian(s, seed, stream_id, n, 1, 1, n, v0, n);
     if (e != cudaSuccess) return e;
     pi_init_kernel<<<64, 256, 0, s>>>(scal, v1, n);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int nb = (int)((n + TRW - 1) / TRW);   // block rows holding rows < n
-    int64_t blocks = 0;
-    for (int I = 0; I < nb; ++I) {
-        const int64_t cs = ((int64_t)I * TRW / 256) * 256;
-        const int tiles = (int)((npad - cs) / TCB);
-        blocks += (tiles + SEGB - 1) / SEGB;
-    }
-    const int maxseg = (int)((npad / TCB + SEGB - 1) / SEGB);
-    const dim3 grid((unsigned)maxseg, (unsigned)nb);
+    e = cudaFuncSetAttribute(sym_gemv_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)gt::SMEM);
+    if (e != cudaSuccess) return e;
+    const int nbr = (int)((n + PSD_TILE_M - 1) / PSD_TILE_M);
+    const int64_t tiles = psd_tile_count(n);
+    int grid = (sm_count > 0 ? sm_count : 148) * gt::CTAS_PER_SM;
+    if ((int64_t)grid > tiles) grid = (int)tiles;
     float *in = v0, *out = v1;
     for (int it = 0; it <= N; ++it) {
-        sym_gemv_bf16_kernel<<<grid, NTW, 0, s>>>(Ab, ldb, n, npad, in, out, in, scal, counter,
-                                                  d_shift_neg, it == N ? d_sigma : nullptr,
-                                                  (unsigned)blocks);
+        sym_gemv_tiles_kernel<<<grid, gt::NTG, gt::SMEM, s>>>(Ab, n, nbr, tiles, in, out, in, scal, counter,
+                                                              d_shift_neg, it == N ? d_sigma : nullptr,
+                                                              d_status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         float *t = in; in = out; out = t;

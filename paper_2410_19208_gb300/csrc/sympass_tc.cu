@@ -7,26 +7,30 @@
 // pack_upper_bf16_kernel: the tiles (I, J) of BM = 256 rows x 64 columns with
 // J >= 4 I (the block upper triangle), where the 256 x 256 blocks on the
 // diagonal hold a_ij for j > i, a_ii / 2 on the diagonal and 0 below it, so
-// that A = A' + A'^T exactly.  The image is padded with zeros to a multiple
-// of 256 in both directions.  Every later pass over A then streams 2 bytes
-// per upper-triangle entry instead of 4, and needs no masking.
+// that A = A' + A'^T exactly; entries past row or column n are zero.  The
+// tiles are stored one after another in row-major tile order, each 32 KB
+// already in the 128-byte-swizzled layout of a UMMA operand, so a CTA streams
+// a contiguous range of the image, one bulk copy per tile, and every later
+// pass over A reads 2 bytes per upper-triangle entry instead of 4.
 //
-// Each tile is loaded by TMA (128-byte swizzle, four stages in flight) and
-// feeds two products straight from shared memory:
+// Each tile (with the X_J tile loaded by TMA beside it, three stages in
+// flight) feeds two products straight from shared memory:
 //   P1  D1^T (m x BM) += X_J^T (m x 64) . A'_IJ^T   (B operand K-major)
 //   P2  D2^T (m x 64)   = X_I^T (m x BM) . A'_IJ    (B operand MN-major)
 // with M = 128 rows of X^T (m <= 128; rows m..127 are zero).  D1^T
 // accumulates over the run of tiles a CTA owns in one block row and is
 // flushed once (with the shift term when the run holds the diagonal block);
-// D2^T is double-buffered in TMEM and added to Y with red.global.add.v4.f32
-// after every tile.
+// D2^T is double-buffered in TMEM and added to Y after every tile.  Both are
+// added by TMA bulk reduce-add from a swizzled 32 x 32 staging box per warp
+// (scalar atomics when Y is not 16-byte aligned with ld % 4 == 0).
 //
 // Warp roles (256 threads, one CTA per SM, persistent over an equal share of
-// the tiles in row-major order): warp 0 issues TMA, warp 1 owns TMEM and
+// the tiles in row-major order): warp 0 issues the copies, warp 1 owns TMEM and
 // issues tcgen05.mma from one thread, warps 4-7 drain TMEM.  Every mbarrier
 // wait is bounded; on a timeout the CTA records PSDPROJ_ETIMEOUT, unwinds and
 // frees its TMEM.
 #include <cuda_bf16.h>
+#include <cstring>
 #include <cudaTypedefs.h>
 
 #include "ctx.h"
@@ -36,27 +40,29 @@ namespace {
 
 using namespace tc;
 
-constexpr int BN = 64;
-constexpr int BM = 256;
-constexpr int R = BM / BN;                       // column tiles per block-row step
-constexpr int NSTAGE = 4;
-constexpr uint32_t A_STAGE = BM * BN * 2;        // BF16 tile
-constexpr uint32_t XJ_BYTES = 128 * BN * 2;      // 16 KB
+constexpr int BN = PSD_TILE_N;
+constexpr int BM = PSD_TILE_M;
+constexpr int R = PSD_TILE_R;                    // column tiles per block-row step
+constexpr int NSTAGE = 3;
+constexpr uint32_t A_BYTES = BM * BN * 2;        // BF16 tile of A'
+constexpr uint32_t XJ_BYTES = 128 * BN * 2;      // X_J^T rows 0..127 (16 KB)
+constexpr uint32_t STAGE = A_BYTES + XJ_BYTES;   // one stage: A' tile, then X_J
 constexpr uint32_t XI_BYTES = 128 * BM * 2;      // 64 KB
+constexpr uint32_t STG_BYTES = 32 * 32 * 4;      // epilogue staging box per warp
 constexpr uint32_t OFF_A = 0;
-constexpr uint32_t OFF_XJ = NSTAGE * A_STAGE;
-constexpr uint32_t OFF_XI = OFF_XJ + 2 * XJ_BYTES;
-constexpr uint32_t OFF_BAR = OFF_XI + XI_BYTES;
+constexpr uint32_t OFF_XI = NSTAGE * STAGE;
+constexpr uint32_t OFF_STG = OFF_XI + XI_BYTES;
+constexpr uint32_t OFF_BAR = OFF_STG + 4 * STG_BYTES;
 constexpr uint32_t SMEM_BYTES = OFF_BAR + 256;
 constexpr uint32_t D1_COL = 0, D2_COL = BM;      // TMEM columns: D1 256, D2 2 x 64
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int NT = 256;
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s at 2 GHz
 static_assert(SMEM_BYTES <= 232448, "shared memory");
+static_assert(STAGE % 1024 == 0 && OFF_XI % 1024 == 0 && OFF_STG % 1024 == 0, "swizzle atoms");
 
 struct Bars {
-    uint64_t fullA[NSTAGE], emptyA[NSTAGE];
-    uint64_t fullXJ[2], emptyXJ[2];
+    uint64_t full[NSTAGE], empty[NSTAGE];
     uint64_t fullXI, emptyXI;
     uint64_t d2full[2], d2empty[2];
     uint64_t d1full, d1empty;
@@ -77,31 +83,27 @@ struct Params {
     int64_t ldy;
     const double *d_shift;
     int *d_status;
-    int vec_ok;
+    int tma_y;          // Y reduced by TMA (aligned Y); else scalar atomics
 };
-
-// tiles of block row I are J = R I .. nbc - 1; rows 0..I-1 hold
-// sum_i (nbc - R i) = I nbc - R I (I - 1) / 2 of them
-__device__ __forceinline__ int64_t row_start(int I, int nbc)
-{
-    return (int64_t)I * nbc - (int64_t)R * I * (I - 1) / 2;
-}
 
 __device__ __forceinline__ void tile_of(int64_t t, int nbc, int nbr, int &I, int &J)
 {
     int lo = 0, hi = nbr - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (row_start(mid, nbc) <= t) lo = mid; else hi = mid - 1;
+        if (psd_tile_row_start(mid, nbc) <= t) lo = mid; else hi = mid - 1;
     }
     I = lo;
-    J = R * lo + (int)(t - row_start(lo, nbc));
+    J = R * lo + (int)(t - psd_tile_row_start(lo, nbc));
 }
 
-// last tile of a run inside one block row
-__device__ __forceinline__ bool last_in_row_run(int64_t t, int64_t t1, int I, const Params &P)
+// the next tile in row-major order over the block upper triangle
+__device__ __forceinline__ void tile_next(int &I, int &J, int nbc)
 {
-    return (t + 1 == t1) || (I + 1 < P.nbr && t + 1 == row_start(I + 1, P.nbc));
+    if (++J == nbc) {
+        ++I;
+        J = R * I;
+    }
 }
 
 __device__ __forceinline__ void fail(Bars &B, int *st)
@@ -116,9 +118,39 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// Epilogue: add 32 rows (r0 .. r0+31) of column c = 32 q + lane, held in v,
+// to Y.  With TMA: stage as a 32 x 32 box (128-byte swizzle: the 16-byte
+// chunk j of column c at c*128 + ((j ^ (c & 7)) << 4)) and reduce-add it;
+// the staging box is reused after the previous reduce has read it.
+__device__ __forceinline__ void flush32(const Params &P, const CUtensorMap *tmY, uint8_t *stg, int q,
+                                        int lane, int64_t r0, const float (&v)[32])
+{
+    const int c = 32 * q + lane;
+    if (P.tma_y) {
+        if (r0 >= P.n || 32 * q >= P.m) return;               // the whole box is outside Y
+        if (lane == 0) bulk_wait_read();
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<float4 *>(stg + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            tma_reduce_add_2d(tmY, (int)r0, 32 * q, stg);
+            bulk_commit();
+        }
+    } else if (c < P.m) {
+        float *ycol = P.Y + (int64_t)c * P.ldy;
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+            if (r0 + e < P.n) atomicAdd(ycol + r0 + e, v[e]);
+    }
+}
+
 __global__ void __launch_bounds__(NT, 1)
-sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
-                     const Params P)
+sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CUtensorMap tmX,
+                     const __grid_constant__ CUtensorMap tmY, const Params P)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     Bars &B = *reinterpret_cast<Bars *>(sm + OFF_BAR);
@@ -131,12 +163,10 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(&B.fullA[s], 1);
-            mbar_init(&B.emptyA[s], 1);
+            mbar_init(&B.full[s], 1);
+            mbar_init(&B.empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&B.fullXJ[b], 1);
-            mbar_init(&B.emptyXJ[b], 1);
             mbar_init(&B.d2full[b], 1);
             mbar_init(&B.d2empty[b], 4);
         }
@@ -147,8 +177,8 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         mbar_init(&B.mmadone, 1);
         B.abort = 0;
         fence_proxy_async_smem();
-        prefetch_tmap(&tmA);
         prefetch_tmap(&tmX);
+        if (P.tma_y) prefetch_tmap(&tmY);
     }
     if (warp == 1) {
         tmem_alloc(&B.tmem_base, TMEM_COLS);
@@ -159,15 +189,15 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
     tc_fence_after();
     const uint32_t tmem = B.tmem_base;
     volatile int *abort = &B.abort;
+    int I0 = 0, J0 = 0;
+    if (t0 < t1) tile_of(t0, P.nbc, P.nbr, I0, J0);
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA
         if (lane == 0) {
-            int curI = -1, xi_uses = 0;
+            int I = I0, J = J0, curI = -1, xi_uses = 0;
             int64_t it = 0;
-            for (int64_t t = t0; t < t1; ++t, ++it) {
-                int I, J;
-                tile_of(t, P.nbc, P.nbr, I, J);
+            for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
                 if (I != curI) {
                     if (!mbar_wait(&B.emptyXI, (xi_uses & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                     mbar_arrive_expect_tx(&B.fullXI, XI_BYTES);
@@ -178,21 +208,15 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 }
                 const int s = (int)(it % NSTAGE);
                 const uint32_t us = (uint32_t)(it / NSTAGE);
-                if (!mbar_wait(&B.emptyA[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                mbar_arrive_expect_tx(&B.fullA[s], A_STAGE);
-                tma_load_2d(sm + OFF_A + s * A_STAGE, &tmA, BN * J, BM * I, &B.fullA[s]);
-                const int b = (int)(it & 1);
-                const uint32_t ub = (uint32_t)(it >> 1);
-                if (!mbar_wait(&B.emptyXJ[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                mbar_arrive_expect_tx(&B.fullXJ[b], XJ_BYTES);
-                tma_load_2d(sm + OFF_XJ + b * XJ_BYTES, &tmX, BN * J, 0, &B.fullXJ[b]);
+                if (!mbar_wait(&B.empty[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                mbar_arrive_expect_tx(&B.full[s], STAGE);
+                bulk_load(sm + OFF_A + s * STAGE, Ab + t * PSD_TILE_ELEMS, A_BYTES, &B.full[s]);
+                tma_load_2d(sm + OFF_A + s * STAGE + A_BYTES, &tmX, BN * J, 0, &B.full[s]);
             }
             // wait (bounded) for the copies still in flight to land
             const int64_t n_it = it;
             for (int64_t k = (n_it > NSTAGE ? n_it - NSTAGE : 0); k < n_it; ++k)
-                mbar_wait(&B.fullA[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1), abort, WAIT_LIMIT);
-            for (int64_t k = (n_it > 2 ? n_it - 2 : 0); k < n_it; ++k)
-                mbar_wait(&B.fullXJ[k & 1], (uint32_t)((k >> 1) & 1), abort, WAIT_LIMIT);
+                mbar_wait(&B.full[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1), abort, WAIT_LIMIT);
             if (xi_uses > 0) mbar_wait(&B.fullXI, (uint32_t)((xi_uses - 1) & 1), abort, WAIT_LIMIT);
         }
     } else if (warp == 1) {
@@ -200,14 +224,12 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         if (lane == 0) {
             const uint32_t id1 = idesc_bf16(128, BM, 0, 0);
             const uint32_t id2 = idesc_bf16(128, BN, 0, 1);
-            int curI = -1, seg = 0;
+            int I = I0, J = J0, curI = -1, seg = 0;
             int64_t it = 0;
             bool issued = false;
-            for (int64_t t = t0; t < t1; ++t, ++it) {
-                int I, J;
-                tile_of(t, P.nbc, P.nbr, I, J);
+            for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
                 const bool first = (I != curI);
-                const bool last = last_in_row_run(t, t1, I, P);
+                const bool last = (J == P.nbc - 1) || (t + 1 == t1);
                 if (first) {
                     if (!mbar_wait(&B.fullXI, seg & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                     if (!mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
@@ -217,12 +239,11 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 const uint32_t us = (uint32_t)(it / NSTAGE);
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
-                if (!mbar_wait(&B.fullA[s], us & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                if (!mbar_wait(&B.fullXJ[b], ub & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                if (!mbar_wait(&B.full[s], us & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                 if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                 tc_fence_after();
-                const uint32_t a_tile = smem_u32(sm + OFF_A + s * A_STAGE);
-                const uint32_t xj = smem_u32(sm + OFF_XJ + b * XJ_BYTES);
+                const uint32_t a_tile = smem_u32(sm + OFF_A + s * STAGE);
+                const uint32_t xj = a_tile + A_BYTES;
                 const uint32_t xi = smem_u32(sm + OFF_XI);
                 // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns)
 #pragma unroll
@@ -239,8 +260,7 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                     mma_bf16_ss(tmem + D2_COL + BN * b, ad, bd, id2, kk > 0 ? 1u : 0u);
                 }
                 issued = true;
-                mma_commit(&B.emptyA[s]);
-                mma_commit(&B.emptyXJ[b]);
+                mma_commit(&B.empty[s]);
                 mma_commit(&B.d2full[b]);
                 if (last) {
                     mma_commit(&B.d1full);
@@ -258,20 +278,14 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
         // ------------------------------------------------------- epilogue
         const int q = warp & 3;                // TMEM lane quarter of this warp
         const int c = 32 * q + lane;           // column of X / Y held by this thread
-        const bool cok = c < P.m;
+        uint8_t *stg = sm + OFF_STG + q * STG_BYTES;
         const double shift = P.d_shift ? *P.d_shift : 0.0;
-        int curI = -1, seg = 0;
+        int I = I0, J = J0, seg = 0;
         bool has_diag = false;
         int64_t it = 0;
-        float *ycol = P.Y + (int64_t)c * P.ldy;
-        for (int64_t t = t0; t < t1; ++t, ++it) {
-            int I, J;
-            tile_of(t, P.nbc, P.nbr, I, J);
-            if (I != curI) {
-                curI = I;
-                has_diag = (J == R * I);
-            }
-            const bool last = last_in_row_run(t, t1, I, P);
+        for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
+            if (J == R * I) has_diag = true;   // this run holds the diagonal block's first tile
+            const bool last = (J == P.nbc - 1) || (t + 1 == t1);
             const int b = (int)(it & 1);
             const uint32_t ub = (uint32_t)(it >> 1);
             {
@@ -289,21 +303,8 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&B.d2empty[b]);
-            if (cok) {
-                const int64_t r0 = (int64_t)BN * J;
-#pragma unroll
-                for (int j = 0; j < 64; j += 4) {
-                    const float *src = j < 32 ? v0 + j : v1 + (j - 32);
-                    const int64_t r = r0 + j;
-                    if (P.vec_ok && r + 3 < P.n) {
-                        red_add_v4(ycol + r, src[0], src[1], src[2], src[3]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (r + e < P.n) atomicAdd(ycol + r + e, src[e]);
-                    }
-                }
-            }
+            flush32(P, &tmY, stg, q, lane, (int64_t)BN * J, v0);
+            flush32(P, &tmY, stg, q, lane, (int64_t)BN * J + 32, v1);
             if (last) {
                 int ok = 1;
                 if (lane == 0) ok = mbar_wait(&B.d1full, seg & 1, abort, WAIT_LIMIT) ? 1 : 0;
@@ -315,33 +316,23 @@ sym_pass_bf16_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_const
                 for (int ch = 0; ch < BM / 32; ++ch) {
                     float v[32];
                     tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + D1_COL + 32 * ch, v);
-                    if (cok) {
-                        const int64_t rb = r0 + 32 * ch;
-                        if (has_diag && shift != 0.0) {
-                            const float *xc = P.X + (int64_t)c * P.ldx;
+                    const int64_t rb = r0 + 32 * ch;
+                    if (has_diag && shift != 0.0 && c < P.m) {
+                        const float *xc = P.X + (int64_t)c * P.ldx;
 #pragma unroll
-                            for (int e = 0; e < 32; ++e)
-                                if (rb + e < P.n) v[e] = fmaf((float)shift, xc[rb + e], v[e]);
-                        }
-#pragma unroll
-                        for (int e = 0; e < 32; e += 4) {
-                            const int64_t r = rb + e;
-                            if (P.vec_ok && r + 3 < P.n) {
-                                red_add_v4(ycol + r, v[e], v[e + 1], v[e + 2], v[e + 3]);
-                            } else {
-#pragma unroll
-                                for (int f = 0; f < 4; ++f)
-                                    if (r + f < P.n) atomicAdd(ycol + r + f, v[e + f]);
-                            }
-                        }
+                        for (int e = 0; e < 32; ++e)
+                            if (rb + e < P.n) v[e] = fmaf((float)shift, xc[rb + e], v[e]);
                     }
+                    flush32(P, &tmY, stg, q, lane, rb, v);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&B.d1empty);
                 ++seg;
+                has_diag = false;
             }
         }
+        if (lane == 0 && P.tma_y) bulk_wait_all();
     }
 
     tc_fence_before();
@@ -363,18 +354,19 @@ __global__ void to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t
 }
 
 // BF16 image A' of the block upper triangle of A (see the top of this file).
-// Block: 16 rows x 64 columns, 16 threads per row, one float4 of A and one
-// 8-byte store of A' per thread.  grid.x: 64-column tiles, grid.y: 16-row
-// chunks; tiles left of the diagonal 256 x 256 block exit at once.
+// Block: 16 rows x 64 columns of one tile, 16 threads per row; a thread
+// converts 4 consecutive entries (one float4 of A) into the half of a
+// 16-byte chunk of its row.  grid.x: 64-column tiles J, grid.y: 16-row
+// chunks; tiles left of the diagonal block exit at once.
 __global__ void __launch_bounds__(256)
 pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
-                       uint16_t *__restrict__ Ab, int64_t ldb, int vec)
+                       uint16_t *__restrict__ Ab, int nbc, int vec)
 {
+    const int J = blockIdx.x;
     const int64_t r = (int64_t)blockIdx.y * 16 + (threadIdx.x >> 4);
-    const int64_t cbase = (int64_t)blockIdx.x * BN;
-    const int64_t blk0 = (r / BM) * BM;               // first column of the diagonal block
-    if (cbase + BN <= blk0) return;                   // uniform across the block
-    const int64_t c0 = cbase + 4 * (threadIdx.x & 15);
+    const int I = (int)(((int64_t)blockIdx.y * 16) / BM);
+    if (J < R * I) return;                            // uniform across the block
+    const int64_t c0 = (int64_t)J * BN + 4 * (threadIdx.x & 15);
     float v[4];
     if (r < n && vec && c0 + 4 <= n) {
         const float4 a = __ldcs(reinterpret_cast<const float4 *>(A + r * lda + c0));
@@ -383,7 +375,7 @@ pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[q] = (r < n && c0 + q < n) ? A[r * lda + c0 + q] : 0.0f;
     }
-    if (cbase < blk0 + BM) {
+    if (J < R * (I + 1)) {
         // diagonal block: keep the strict upper part, halve the diagonal
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -394,7 +386,11 @@ pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
     uint2 o;
     o.x = pack_bf16(v[0], v[1]);
     o.y = pack_bf16(v[2], v[3]);
-    *reinterpret_cast<uint2 *>(Ab + r * ldb + c0) = o;
+    const int rt = (int)(r - (int64_t)I * BM);         // row within the tile
+    const int k = (threadIdx.x & 15) >> 1;             // 16-byte chunk of the row
+    const int64_t t = psd_tile_row_start(I, nbc) + (J - R * I);
+    uint8_t *tile = reinterpret_cast<uint8_t *>(Ab + t * PSD_TILE_ELEMS);
+    *reinterpret_cast<uint2 *>(tile + rt * 128 + ((k ^ (rt & 7)) << 4) + 8 * (threadIdx.x & 1)) = o;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
@@ -414,29 +410,24 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 
 }  // namespace
 
-int64_t psd_bf16_image_pad(int64_t n) { return psd_round_up(n, BM); }
-
-cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab,
-                             int64_t ldb)
+cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab)
 {
-    const int64_t npad = psd_bf16_image_pad(n);
-    if (ldb < npad || (ldb % 8) != 0 || (reinterpret_cast<uintptr_t>(Ab) & 15) != 0)
-        return cudaErrorInvalidValue;
+    if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0) return cudaErrorInvalidValue;
+    const int nbr = (int)((n + BM - 1) / BM);
+    const int nbc = nbr * R;
     const int vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
-    dim3 grid((unsigned)(npad / BN), (unsigned)(npad / 16));
-    pack_upper_bf16_kernel<<<grid, 256, 0, s>>>(A, n, lda, Ab, ldb, vec);
+    dim3 grid((unsigned)nbc, (unsigned)(nbr * (BM / 16)));
+    pack_upper_bf16_kernel<<<grid, 256, 0, s>>>(A, n, lda, Ab, nbc, vec);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t ldb,
+cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t n, const float *X, int64_t ldx, int m,
                                const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
                                int64_t ldh, int *d_status)
 {
-    const int64_t npad = psd_bf16_image_pad(n);
     if (m < 1 || m > 128) return cudaErrorNotSupported;
-    if (ldb < npad || (ldb % 8) != 0 || (reinterpret_cast<uintptr_t>(Ab) & 15) != 0)
-        return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0) return cudaErrorNotSupported;
     if ((ldh % 8) != 0 || (reinterpret_cast<uintptr_t>(Xh) & 15) != 0 || ldh < n)
         return cudaErrorNotSupported;
     auto encode = get_encode();
@@ -451,17 +442,7 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    CUtensorMap tmA, tmX;
-    {
-        cuuint64_t dims[2] = {(cuuint64_t)npad, (cuuint64_t)npad};
-        cuuint64_t strides[1] = {(cuuint64_t)ldb * 2};
-        cuuint32_t box[2] = {(cuuint32_t)BN, (cuuint32_t)BM};
-        cuuint32_t estr[2] = {1, 1};
-        if (encode(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(Ab), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-    }
+    CUtensorMap tmX;
     {
         cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
         cuuint64_t strides[1] = {(cuuint64_t)ldh * 2};
@@ -475,16 +456,28 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
     Params P;
     P.n = n;
     P.m = m;
-    P.nbr = (int)(npad / BM);
-    P.nbc = (int)(npad / BN);
-    P.tiles = (int64_t)P.nbr * P.nbc - (int64_t)R * P.nbr * (P.nbr - 1) / 2;
+    P.nbr = (int)((n + BM - 1) / BM);
+    P.nbc = P.nbr * R;
+    P.tiles = psd_tile_count(n);
     P.X = X;
     P.ldx = ldx;
     P.Y = Y;
     P.ldy = ldy;
     P.d_shift = d_shift;
     P.d_status = d_status;
-    P.vec_ok = ((ldy % 4) == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0);
+    P.tma_y = ((ldy % 4) == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0);
+    CUtensorMap tmY;
+    memset(&tmY, 0, sizeof(tmY));
+    if (P.tma_y) {
+        cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+        cuuint64_t strides[1] = {(cuuint64_t)ldy * 4};
+        cuuint32_t box[2] = {32, 32};
+        cuuint32_t estr[2] = {1, 1};
+        if (encode(&tmY, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, Y, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            P.tma_y = 0;
+    }
 
     cudaError_t e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(float), 0, (size_t)n * sizeof(float),
                                       (size_t)m, s);
@@ -494,6 +487,6 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
     if (e != cudaSuccess) return e;
     int grid = sm_count > 0 ? sm_count : 148;
     if ((int64_t)grid > P.tiles) grid = (int)P.tiles;
-    sym_pass_bf16_kernel<<<grid, NT, SMEM_BYTES, s>>>(tmA, tmX, P);
+    sym_pass_bf16_kernel<<<grid, NT, SMEM_BYTES, s>>>(Ab, tmX, tmY, P);
     return cudaGetLastError();
 }

@@ -249,7 +249,8 @@ def test_eig_clusters_in_random_basis(ctx, m, method):
     assert np.abs(Vv.T @ Vv - np.eye(m)).max() <= 2e-5
     P = (Vv * np.maximum(dv, 0)) @ Vv.T
     Pe = (U * np.maximum(lam, 0)) @ U.T
-    assert np.linalg.norm(P - Pe) <= 5e-6 * nrm
+    # FP32 Householder backward error grows like m * eps32 * ||C||
+    assert np.linalg.norm(P - Pe) <= max(5e-6, 2 * m * EPS32) * nrm
 
 
 @pytest.mark.parametrize("method", [ps.EIG_AUTO, ps.EIG_JACOBI, ps.EIG_TRIDIAG])
