@@ -39,7 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_DEFAULT, K_DEFAULT, P_DEFAULT, Q_DEFAULT, SEED = 20000, 100, 10, 1, 1
-STAGES = ["apass", "gemv", "orth", "core", "eig", "factor", "syrk", "other"]
+STAGES = ["apass", "gemv", "orth", "core", "eig", "factor", "syrk", "other", "pack"]
 PREC_NAMES = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
 DTYPE_NAMES = {"fp32": "f32", "tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}
 
@@ -206,17 +206,19 @@ def source_sha(paths):
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(kernel_file: str, n: int):
-    """traffic per launch recorded by the committed ncu summary, if it was
-    taken on the current source of the kernel (else None)."""
+def traffic_from_profile(kernel_file: str, n: int, kernel: str):
+    """DRAM traffic per launch (bytes) recorded in profiles/traffic.txt for
+    `kernel` at size n, if it was taken on the current source of the kernel's
+    file (else None).  Lines: file sha16 n kernel bytes; '#' starts a comment."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
     sha = source_sha([kernel_file])
     for ln in open(path):
-        parts = ln.split()
-        if len(parts) >= 4 and parts[0] == kernel_file and parts[1] == sha and int(parts[2]) == n:
-            return float(parts[3])
+        parts = ln.split("#")[0].split()
+        if (len(parts) >= 5 and parts[0] == kernel_file and parts[1] == sha and int(parts[2]) == n
+                and parts[3] == kernel):
+            return float(parts[4])
     return None
 
 
@@ -302,9 +304,9 @@ def main():
             dist.barrier()
         clocks = sampler.stop() if sampler else None
         launches = int(ps.lib().psdproj_kernel_launches() - l0)
-        ms_k = (ctypes.c_double * 8)()
-        cnt_k = (ctypes.c_int * 8)()
-        ps.lib().psdproj_timing_read(ctx.h, ms_k, cnt_k, 8)
+        ms_k = (ctypes.c_double * len(STAGES))()
+        cnt_k = (ctypes.c_int * len(STAGES))()
+        ps.lib().psdproj_timing_read(ctx.h, ms_k, cnt_k, len(STAGES))
         ps.lib().psdproj_timing_enable(ctx.h, 0)
         st = ctx.sync_status()
         if st != 0:
@@ -317,7 +319,7 @@ def main():
         a1 = [x[0].elapsed_time(x[1]) for x in lat]
         a2 = [x[1].elapsed_time(x[2]) for x in lat]
         stages = {STAGES[i]: {"ms_total": ms_k[i], "launches": cnt_k[i],
-                              "ms_avg": (ms_k[i] / cnt_k[i]) if cnt_k[i] else None} for i in range(8)}
+                              "ms_avg": (ms_k[i] / cnt_k[i]) if cnt_k[i] else None} for i in range(len(STAGES))}
         # accuracy of this form against the exact projection (closed form)
         ctx.alg1(A, k, p, q, SEED, P=None, W=W, rank=rank_t,
                  opts=ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_],
@@ -352,13 +354,43 @@ def main():
     stages = head["stages"]
     opts = head["opts"]
 
-    # ---- roofline of the dominant kernel: the symmetric A-pass ------------
+    # ---- rooflines: the dominant kernel and the other HBM-bound ones -------
+    # algorithmic bytes per launch (stated in the design doc): U(n) = n(n+1)/2
+    # upper-triangle entries; the BF16 form reads 2 bytes per entry from its
+    # image, the FP32 form 4 bytes from A.  Per-launch times come from the
+    # context's CUDA-event stage timing over the timed region (events on the
+    # launching stream), divided by the launches a stage holds.
     peaks, peak_kind = measured_peaks()
-    apass_ms = stages["apass"]["ms_avg"]
     upper_elems = n * (n + 1) // 2
+    N_PI = 10
+    steps_ = args.steps
+
+    def per_launch(stage, launches_per_stage):
+        st_ = stages[stage]
+        if not st_["launches"]:
+            return None
+        return st_["ms_total"] / (st_["launches"] * launches_per_stage)
+
+    def hbm_entry(name, kfile, kname, stage, lps, nbytes, flops=None):
+        ms = per_launch(stage, lps)
+        if ms is None:
+            return None
+        gbs = nbytes / (ms / 1e3) / 1e9
+        e = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+             "frac": gbs / peaks["hbm_gbs"], "per_launch_ms": ms, "algorithmic_bytes_per_launch": nbytes,
+             "launches_per_step": stages[stage]["launches"] * lps / steps_,
+             "ms_per_step": stages[stage]["ms_total"] / steps_,
+             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+             "traffic": traffic_from_profile(kfile, n, kname)}
+        if flops is not None:
+            e["algorithmic_flops_per_launch"] = flops
+            e["tensor_tflops"] = flops / (ms / 1e3) / 1e12
+        return e
+
     if prec == "fp32":
         # FP32 FMA on the CUDA cores: 2 n^2 m algorithmic FLOPs per pass,
         # peak = 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock
+        apass_ms = stages["apass"]["ms_avg"]
         flops = 2.0 * n * n * m
         achieved = flops / (apass_ms / 1e3) / 1e12
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -366,17 +398,38 @@ def main():
                 "frac": achieved / peak, "kernel": "sym_pass_simt",
                 "peak_source": f"derived: 152 SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
                 "hbm_frac_of_" + peak_kind: (upper_elems * 4 / (apass_ms / 1e3) / 1e9) / peaks["hbm_gbs"],
-                "traffic": traffic_from_profile("paper_2410_19208_gb300/csrc/sympass_simt.cu", n)}
+                "per_launch_ms": apass_ms, "algorithmic_bytes_per_launch": upper_elems * 4.0,
+                "algorithmic_flops_per_launch": flops,
+                "traffic": traffic_from_profile("paper_2410_19208_gb300/csrc/sympass_simt.cu", n,
+                                                "sym_pass_simt_kernel")}
+        path = None
     else:
-        bytes_alg = upper_elems * 4.0
-        achieved = bytes_alg / (apass_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "kernel": "sym_pass_bf16 (tcgen05)",
-                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": traffic_from_profile("paper_2410_19208_gb300/csrc/sympass_tc.cu", n)}
-    roof["per_launch_ms"] = apass_ms
-    roof["algorithmic_bytes_per_launch"] = upper_elems * 4.0
-    roof["algorithmic_flops_per_launch"] = 2.0 * n * n * m
+        cand = [
+            hbm_entry("sym_gemv_tiles (power iteration on the BF16 image)",
+                      "paper_2410_19208_gb300/csrc/gemv.cu", "sym_gemv_tiles_kernel", "gemv", 2 * (N_PI + 1),
+                      upper_elems * 2.0),
+            hbm_entry("sym_pass_bf16 (tcgen05, BF16 image)", "paper_2410_19208_gb300/csrc/sympass_tc.cu",
+                      "sym_pass_bf16_kernel", "apass", 1, upper_elems * 2.0, 2.0 * n * n * m),
+            hbm_entry("syrk_bf16x3 (tcgen05, P written)", "paper_2410_19208_gb300/csrc/syrk_tc.cu",
+                      "syrk_bf16x3_kernel", "syrk", 1, n * n * 4.0),
+            hbm_entry("pack_upper_bf16 (A read, image written)", "paper_2410_19208_gb300/csrc/sympass_tc.cu",
+                      "pack_upper_bf16_kernel", "pack", 1, upper_elems * 6.0),
+        ]
+        cand = [c for c in cand if c is not None]
+        dom = max(cand, key=lambda c: c["ms_per_step"])
+        roof = dict(dom)
+        roof["others"] = [c for c in cand if c is not dom]
+        # whole step: every algorithmic HBM byte of both projections
+        passes = 2 * q + 2
+        path_bytes = 2 * (6.0 * upper_elems + passes * 2.0 * upper_elems + 4.0 * n * n) \
+            + 2 * (N_PI + 1) * 2.0 * upper_elems
+        step_ms = elapsed_ms / args.steps
+        path = {"bytes_per_step": path_bytes, "achieved": path_bytes / (step_ms / 1e3) / 1e9,
+                "unit": "GB/s", "peak": peaks["hbm_gbs"],
+                "frac": path_bytes / (step_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "note": "per projection: pack + (2q+2) passes over the BF16 image + the P write; "
+                        "plus 2(N+1) power-iteration products for Alg. 3; the small steps "
+                        "(orthonormalisation, eigensolver) move almost no HBM bytes"}
 
     line = {
         "metric": f"PSD projections/s at n={n}", "value": value, "unit": "projections/s",
@@ -385,6 +438,7 @@ def main():
         "vs_baseline": None, "dtype": DTYPE_NAMES[prec], "data": "synthetic",
         "config": workload_config(args, prec, syrk_prec),
         "roofline": roof,
+        "path_roofline": path,
         "latency_ms": {"alg1_p50": pct(head["lat1"], 0.5), "alg1_p99": pct(head["lat1"], 0.99),
                        "alg2_p50": pct(head["lat2"], 0.5), "alg2_p99": pct(head["lat2"], 0.99)},
         "stages": stages, "gpu_launches": head["launches"], "clocks": head["clocks"],

@@ -107,7 +107,8 @@ size_t psdproj_workspace_bytes(const psdproj_ctx *ctx);
 #define PSDPROJ_STAGE_FACTOR  5  /* W = Q V sqrt(D+)                            */
 #define PSDPROJ_STAGE_SYRK    6  /* P = W W^T                                   */
 #define PSDPROJ_STAGE_OTHER   7  /* Omega, alpha, copies                        */
-#define PSDPROJ_NSTAGES       8
+#define PSDPROJ_STAGE_PACK    8  /* BF16 image of A (PSDPROJ_PREC_BF16)          */
+#define PSDPROJ_NSTAGES       9
 
 /* Turn per-stage CUDA-event timing on (1) or off (0).  When on, every stage
  * launched on the context's stream is bracketed by two events (at most 4096

@@ -195,7 +195,7 @@ int pack_bf16_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda)
         if (e != cudaSuccess) return cuda_status(e);
         ctx->Ab_bytes = bytes;
     }
-    stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
+    stage_scope st(ctx, PSDPROJ_STAGE_PACK);
     PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab), 1);
     return PSDPROJ_OK;
 }
