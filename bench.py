@@ -15,7 +15,10 @@ rest N(0, 0.01^2), formed in FP64 and rounded to FP32 (synth_inputs.py).
 A (1.6 GB) is larger than L2, so no flush is needed between steps.
 
 `value` = projections / s over all ranks (N > 1: independent replicas, one
-per GPU, no collective on the data path).  Extra keys: roofline of the
+per GPU, no collective on the data path), with the step's two projections on
+two independent contexts and CUDA streams (K Alg. 1 projections on one, K
+Alg. 2 on the other, timed until both finish); `sequential` gives the same
+steps on one stream, and latency, stage times and rooflines come from it.  Extra keys: roofline of the
 dominant kernel, cpu_baseline (the FP64 oracle on host cores), e2e (the
 host-buffer C-ABI call with copies inside the timed region), clocks, kernel
 launches, per-algorithm latency p50/p99, per-stage times and accuracy against
@@ -257,6 +260,15 @@ def main():
     W = ps.tall_empty(n, m, dev)
     rank_t = torch.zeros(1, dtype=torch.int32, device=dev)
     alpha_t = torch.zeros(1, dtype=torch.float64, device=dev)
+    # a second, independent context on its own stream: the headline runs the
+    # step's Alg. 1 projections on the first and its Alg. 2 projections on
+    # the second, concurrently
+    stream2 = torch.cuda.Stream(dev)
+    ctx2 = ps.Context(local, stream2)
+    P2 = torch.empty(n, n, device=dev)
+    W2 = ps.tall_empty(n, m, dev)
+    rank2 = torch.zeros(1, dtype=torch.int32, device=dev)
+    alpha2 = torch.zeros(1, dtype=torch.float64, device=dev)
     import ctypes
 
     def pct(v, q_):
@@ -332,6 +344,58 @@ def main():
         return dict(elapsed_ms=elapsed_ms, lat1=a1, lat2=a2, stages=stages, launches=launches,
                     clocks=clocks, W1=W1, W2=W2, opts=opts)
 
+    def measure_concurrent(prec_, syrk_, steps, sample_clocks):
+        """K steps with the Alg. 1 projections on (ctx, stream) and the Alg. 2
+        projections on (ctx2, stream2); timed from an event on stream before
+        the first to stream after both streams' last projection."""
+        opts = ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_])
+
+        def run(count):
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            stream2.wait_event(ev)
+            for _ in range(count):
+                ctx.alg1(A, k, p, q, SEED, P=P, W=W, rank=rank_t, opts=opts)
+                ctx2.alg2(A, k, p, q, SEED, alpha_out=alpha2, P=P2, W=W2, rank=rank2, opts=opts)
+            ev2 = torch.cuda.Event()
+            ev2.record(stream2)
+            stream.wait_event(ev2)
+
+        run(max(args.warmup, 3))
+        torch.cuda.synchronize(dev)
+        for c_ in (ctx, ctx2):
+            st = c_.sync_status()
+            if st != 0:
+                raise SystemExit(f"device status {ps.STATUS.get(st)} during warm-up (concurrent)")
+        sampler = ClockSampler(local) if sample_clocks else None
+        if sampler:
+            sampler.start()
+            time.sleep(0.4)
+        l0 = ps.lib().psdproj_kernel_launches()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        run(steps)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = int(ps.lib().psdproj_kernel_launches() - l0)
+        for c_ in (ctx, ctx2):
+            st = c_.sync_status()
+            if st != 0:
+                raise SystemExit(f"device status {ps.STATUS.get(st)} in the timed region (concurrent)")
+        elapsed_ms = t_start.elapsed_time(t_end)
+        if dist:
+            t = torch.tensor([elapsed_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            elapsed_ms = float(t.item())
+        return dict(elapsed_ms=elapsed_ms, launches=launches, clocks=clocks)
+
     # relative Frobenius error against the exact projection X+ = U diag(lam+) U^T,
     # in Gram form through the reflectors (no n x n matrix):
     #   ||X+ - W W^T||^2 = sum lam+^2 - 2 sum_i lam+_i ||(U^T W)_i||^2 + ||W^T W||^2
@@ -347,12 +411,16 @@ def main():
         d2 = float(np.sum(lam_p ** 2) - 2.0 * np.sum(lam_p * np.sum(X * X, axis=1)) + np.sum(G * G))
         return float(np.sqrt(max(d2, 0.0)) / xp)
 
-    head = measure(prec, syrk_prec, args.steps, True)
+    # sequential, one stream: per-projection latency, stage times, rooflines
+    head = measure(prec, syrk_prec, args.steps, False)
     elapsed_ms = head["elapsed_ms"]
-    total_proj = 2 * args.steps * world
-    value = total_proj / (elapsed_ms / 1e3)
     stages = head["stages"]
     opts = head["opts"]
+    seq_value = 2 * args.steps * world / (elapsed_ms / 1e3)
+    # headline: the same K steps with the two projections of a step on two streams
+    conc = measure_concurrent(prec, syrk_prec, args.steps, True)
+    total_proj = 2 * args.steps * world
+    value = total_proj / (conc["elapsed_ms"] / 1e3)
 
     # ---- rooflines: the dominant kernel and the other HBM-bound ones -------
     # algorithmic bytes per launch (stated in the design doc): U(n) = n(n+1)/2
@@ -434,14 +502,18 @@ def main():
     line = {
         "metric": f"PSD projections/s at n={n}", "value": value, "unit": "projections/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
-        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": conc["elapsed_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_NAMES[prec], "data": "synthetic",
         "config": workload_config(args, prec, syrk_prec),
         "roofline": roof,
         "path_roofline": path,
         "latency_ms": {"alg1_p50": pct(head["lat1"], 0.5), "alg1_p99": pct(head["lat1"], 0.99),
                        "alg2_p50": pct(head["lat2"], 0.5), "alg2_p99": pct(head["lat2"], 0.99)},
-        "stages": stages, "gpu_launches": head["launches"], "clocks": head["clocks"],
+        "sequential": {"value": seq_value, "unit": "projections/s", "ms_per_step": elapsed_ms / args.steps,
+                       "note": "the same steps on one context and one stream, Alg. 1 then Alg. 2; "
+                               "latency, stages and rooflines are from this run"},
+        "concurrency": "two contexts: Alg. 1 projections on one CUDA stream, Alg. 2 projections on another",
+        "stages": stages, "gpu_launches": conc["launches"], "clocks": conc["clocks"],
         "error_vs_exact": {"alg1": err_exact(head["W1"]), "alg2": err_exact(head["W2"])},
     }
     if prec != "fp32" and not args.no_plain:
@@ -460,14 +532,25 @@ def main():
     if not args.no_e2e:
         Ah = A.cpu().pin_memory()
         Ph = torch.empty(n, n, dtype=torch.float32).pin_memory()
+        Ph2 = torch.empty(n, n, dtype=torch.float32).pin_memory()
         ctx.alg1_host(Ah, k, p, q, SEED, P=Ph, opts=opts)
-        ctx.alg2_host(Ah, k, p, q, SEED, P=Ph, opts=opts)
+        ctx2.alg2_host(Ah, k, p, q, SEED, P=Ph2, opts=opts)
         if dist:
             dist.barrier()
+
+        def host_loop(fn):
+            for _ in range(args.e2e_steps):
+                fn()
+
+        # the two projections of a step from two host threads (the C calls
+        # release the GIL), each on its own context and stream
+        th1 = threading.Thread(target=host_loop, args=(lambda: ctx.alg1_host(Ah, k, p, q, SEED, P=Ph, opts=opts),))
+        th2 = threading.Thread(target=host_loop, args=(lambda: ctx2.alg2_host(Ah, k, p, q, SEED, P=Ph2, opts=opts),))
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            ctx.alg1_host(Ah, k, p, q, SEED, P=Ph, opts=opts)
-            ctx.alg2_host(Ah, k, p, q, SEED, P=Ph, opts=opts)
+        th1.start()
+        th2.start()
+        th1.join()
+        th2.join()
         dt = time.perf_counter() - t0
         if dist:
             t = torch.tensor([dt], device=dev)
@@ -475,14 +558,15 @@ def main():
             dt = float(t.item())
         line["e2e"] = {"value": 2 * args.e2e_steps * world / dt, "unit": "projections/s",
                        "h2d_bytes_per_step": 2 * 4 * n * n, "d2h_bytes_per_step": 2 * (4 * n * n + 4 + 8),
-                       "api": "psdproj_alg1_host + psdproj_alg2_host, pinned host buffers"}
-        del Ah, Ph
+                       "api": "psdproj_alg1_host + psdproj_alg2_host on two contexts from two host threads, "
+                              "pinned host buffers"}
+        del Ah, Ph, Ph2
 
     # ---- accuracy and the oracle baseline (rank 0, N = 1 only) -------------
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         A64 = A.cpu().numpy().astype(np.float64)
-        del P
+        del P, P2
         torch.cuda.empty_cache()
         t_or, Wo = oracle_sample(A64, n, k, p, q)
         del A64
@@ -500,6 +584,7 @@ def main():
                                           f"(k={k}, p={p}, q={q}), {t_or:.1f} s"}
     print(json.dumps(line), flush=True)
     ctx.close()
+    ctx2.close()
     if dist:
         dist.destroy_process_group()
 

@@ -161,6 +161,31 @@ int psdproj_alg2(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                  float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
                  const psdproj_opts *opts);
 
+/* A batch of independent projections (the many-small-matrices workload):
+ * one descriptor per problem, each with its own A, sizes, seed, algorithm
+ * and outputs (device pointers, meanings as in psdproj_alg1 /
+ * psdproj_alg2).  The context's workspace is sized once for the largest
+ * problem of the batch and the problems run in order on the context's
+ * stream; the call returns the first argument error (nothing runs then)
+ * or the first launch error.  opts applies to every problem. */
+typedef struct psdproj_problem {
+    const float *dA;     /* n x n FP32 row-major, upper triangle read       */
+    int64_t n, lda;
+    int k, p, q;
+    int algorithm;       /* 1: psdproj_alg1 (Alg. 2), 2: psdproj_alg2 (Alg. 3) */
+    uint64_t seed;
+    double alpha_in;     /* Alg. 3 only; <= 0: estimate by min_eig            */
+    double *d_alpha_out; /* Alg. 3 only, may be NULL                          */
+    int *d_info;         /* Alg. 3 only, may be NULL                          */
+    float *dP;           /* may be NULL with out_mode FACTOR                  */
+    int64_t ldp;
+    float *dW;           /* may be NULL                                       */
+    int64_t ldw;
+    int *d_rank;         /* may be NULL                                       */
+} psdproj_problem;
+int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
+                    const psdproj_opts *opts);
+
 /* Host-buffer forms of the two calls: hA, hP, hW, h_rank are HOST pointers
  * (pinned memory recommended).  The call copies A to a context-owned device
  * buffer, runs the projection, copies P (and W, r+) back, and synchronises

@@ -41,6 +41,16 @@ class Opts(ctypes.Structure):
                 ("out_mode", ctypes.c_int), ("eig", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
+class Problem(ctypes.Structure):
+    """psdproj_problem: one projection of a psdproj_batched call."""
+    _fields_ = [("dA", ctypes.c_void_p), ("n", ctypes.c_int64), ("lda", ctypes.c_int64),
+                ("k", ctypes.c_int), ("p", ctypes.c_int), ("q", ctypes.c_int),
+                ("algorithm", ctypes.c_int), ("seed", ctypes.c_uint64), ("alpha_in", ctypes.c_double),
+                ("d_alpha_out", ctypes.c_void_p), ("d_info", ctypes.c_void_p),
+                ("dP", ctypes.c_void_p), ("ldp", ctypes.c_int64),
+                ("dW", ctypes.c_void_p), ("ldw", ctypes.c_int64), ("d_rank", ctypes.c_void_p)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -66,6 +76,7 @@ def _load():
         "psdproj_workspace_bytes": (ctypes.c_size_t, [_P]),
         "psdproj_alg1": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, _P, _i64, _P, _i64,
                                 _P, ctypes.POINTER(Opts)]),
+        "psdproj_batched": (_int, [_P, _int, _P, _P]),
         "psdproj_alg2": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, ctypes.c_double,
                                 _P, _P, _P, _i64, _P, _i64, _P, ctypes.POINTER(Opts)]),
         "psdproj_alg1_host": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, _P, _i64, _P,
@@ -183,6 +194,21 @@ class Context:
                                     _ptr(alpha_out), _ptr(info), _ptr(P), ldp, _ptr(W), ldw,
                                     _ptr(rank), ctypes.byref(opts) if opts else None),
                "psdproj_alg2")
+
+    def batched(self, problems, opts: Opts | None = None):
+        """problems: list of dicts with keys A, k, p, q, seed, algorithm (1 or 2) and
+        optional P, W, rank, alpha_in, alpha_out, info (device tensors)."""
+        arr = (Problem * max(1, len(problems)))()
+        for i, d in enumerate(problems):
+            A = d["A"]
+            n, lda = _sq(A)
+            P, W = d.get("P"), d.get("W")
+            arr[i] = Problem(_ptr(A), n, lda, d["k"], d["p"], d["q"], d.get("algorithm", 1), d["seed"],
+                             float(d.get("alpha_in", 0.0)), _ptr(d.get("alpha_out")), _ptr(d.get("info")),
+                             _ptr(P), P.stride(0) if P is not None else n,
+                             _ptr(W), _tall(W, "W")[2] if W is not None else n, _ptr(d.get("rank")))
+        _check(_load().psdproj_batched(self.h, len(problems), ctypes.byref(arr),
+                                       ctypes.byref(opts) if opts else None), "psdproj_batched")
 
     def alg1_host(self, A, k, p, q, seed, P=None, W=None, opts: Opts | None = None):
         """Host tensors (CPU, pinned recommended); returns r+."""

@@ -212,7 +212,7 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
     }
     if (prec != PSDPROJ_PREC_BF16) return PSDPROJ_ENOTSUP;
     psd_workspace &ws = ctx->ws;
-    PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->sm_count, ctx->Ab, n, X, ldx, m, d_shift, Y, ldy,
+    PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, X, ldx, m, d_shift, Y, ldy,
                               ws.Xhi, ws.ld, ctx->d_status), 2);
     return PSDPROJ_OK;
 }
@@ -272,11 +272,11 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         if (!(alpha_in > 0.0)) {
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
             if (tc) {
-                PSD_KL(launch_power_iteration_bf16(s, ctx->sm_count, ctx->Ab, n, opts.N, seed, 3u, nullptr,
+                PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
                                                    ws.pv0, ws.pv1, sc, ws.counter, sc + SC_SIGMA1,
                                                    ctx->d_status),
                        opts.N + 3);
-                PSD_KL(launch_power_iteration_bf16(s, ctx->sm_count, ctx->Ab, n, opts.N, seed, 4u,
+                PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 4u,
                                                    sc + SC_SIGMA1, ws.pv0, ws.pv1, sc, ws.counter,
                                                    sc + SC_SIGMA2, ctx->d_status),
                        opts.N + 3);
@@ -330,7 +330,7 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         if (opts.syrk_prec == PSDPROJ_PREC_FP32)
             PSD_KL(launch_syrk_simt(s, Wd, ldwd, n, m, rk, dP, ldp, upper), 1);
         else
-            PSD_KL(launch_syrk_tc(s, ctx->sm_count, Wd, ldwd, n, m, rk, dP, ldp, upper, ws.Xhi,
+            PSD_KL(launch_syrk_tc(s, ctx->persist_sms, Wd, ldwd, n, m, rk, dP, ldp, upper, ws.Xhi,
                                   ws.Xlo, ws.ld, ctx->d_status), 2);
     }
     if (d_rank) PSD_CK(cudaMemcpyAsync(d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -414,6 +414,11 @@ int psdproj_create(psdproj_ctx **out, int device, void *stream)
     c->device = device;
     c->stream = static_cast<cudaStream_t>(stream);
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    // persistent kernels (one CTA per SM for the whole pass) leave one SM to
+    // single-block kernels that another stream may run at the same time: a
+    // CTA that found no free SM would otherwise start only when another
+    // finished, doubling the pass
+    c->persist_sms = c->sm_count > 8 ? c->sm_count - 1 : c->sm_count;
     cudaError_t e = cudaMalloc(&c->d_status, 64);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_misc, 64);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_misc_f, 64);
@@ -534,6 +539,37 @@ int psdproj_alg2(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int 
                           ldp, dW, ldw, d_rank, opts);
 }
 
+int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
+                    const psdproj_opts *opts_in)
+{
+    if (!ctx || count < 0 || (count > 0 && !probs)) return PSDPROJ_EINVAL;
+    psdproj_opts opts;
+    if (opts_in) opts = *opts_in; else psdproj_default_opts(&opts);
+    PSD_TRY(check_opts(&opts));
+    int64_t nmax = 0;
+    int mmax = 0;
+    for (int i = 0; i < count; ++i) {
+        const psdproj_problem &pb = probs[i];
+        PSD_TRY(validate(pb.n, pb.lda, pb.k, pb.p, pb.q, pb.dA));
+        if (pb.algorithm != 1 && pb.algorithm != 2) return PSDPROJ_EINVAL;
+        if (opts.out_mode != PSDPROJ_OUT_FACTOR && (!pb.dP || pb.ldp < pb.n)) return PSDPROJ_EINVAL;
+        if (pb.dW && pb.ldw < pb.n) return PSDPROJ_EINVAL;
+        if (pb.n > nmax) nmax = pb.n;
+        if (pb.k + pb.p > mmax) mmax = pb.k + pb.p;
+    }
+    if (count == 0) return PSDPROJ_OK;
+    device_guard g(ctx->device);
+    // one workspace for the whole batch
+    PSD_TRY(psd_ensure_workspace(ctx, nmax, mmax));
+    for (int i = 0; i < count; ++i) {
+        const psdproj_problem &pb = probs[i];
+        PSD_TRY(run_projection(ctx, pb.dA, pb.n, pb.lda, pb.k, pb.p, pb.q, pb.seed, pb.algorithm == 2,
+                               pb.alpha_in, pb.d_alpha_out, pb.d_info, pb.dP, pb.ldp, pb.dW, pb.ldw,
+                               pb.d_rank, &opts));
+    }
+    return PSDPROJ_OK;
+}
+
 int psdproj_alg1_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda, int k, int p,
                       int q, uint64_t seed, float *hP, int64_t ldp, float *hW, int64_t ldw,
                       int *h_rank, const psdproj_opts *opts)
@@ -647,7 +683,7 @@ int psdproj_syrk(psdproj_ctx *ctx, const float *dW, int64_t ldw, int64_t n, int 
     if (m > PSD_MAX_M) return PSDPROJ_ENOTSUP;
     PSD_TRY(psd_ensure_workspace(ctx, n, m));
     stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
-    PSD_KL(launch_syrk_tc(ctx->stream, ctx->sm_count, dW, ldw, n, m, d_rank, dP, ldp, upper,
+    PSD_KL(launch_syrk_tc(ctx->stream, ctx->persist_sms, dW, ldw, n, m, d_rank, dP, ldp, upper,
                           ctx->ws.Xhi, ctx->ws.Xlo, ctx->ws.ld, ctx->d_status), 2);
     return PSDPROJ_OK;
 }

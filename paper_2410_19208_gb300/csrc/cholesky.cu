@@ -354,6 +354,66 @@ tall_small_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m,
     }
 }
 
+// The same product for c <= 128 columns: one block covers 64 rows and all
+// c output columns (16 x 16 threads, thread (tx, ty) owns rows 4 tx .. 4 tx + 3
+// and columns ty T .. ty T + T-1, T = ceil(c / 16)), so B is staged once per
+// K chunk and the rows of Y are read with 16-byte loads.
+template <int T>
+__global__ void __launch_bounds__(256)
+tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m,
+                       const float *__restrict__ B, int c, const int *__restrict__ colmask,
+                       const int *__restrict__ d_cols, float *__restrict__ Z, int64_t ldz)
+{
+    constexpr int S = 16 * T;
+    constexpr int KW = 32;                      // K rows staged at a time
+    __shared__ __align__(16) float Ys[KW][TR];
+    __shared__ float Bs[KW][S + 1];
+    const int64_t r0 = (int64_t)blockIdx.x * TR;
+    const int ncols = d_cols ? min(*d_cols, c) : c;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][T];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < T; ++j) acc[i][j] = 0.0f;
+    for (int k0 = 0; k0 < m; k0 += KW) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < KW * TR; e += 256) {
+            const int k = e / TR, r = e % TR;
+            const int64_t gr = r0 + r;
+            Ys[k][r] = (gr < n && k0 + k < m) ? Y[(int64_t)(k0 + k) * ldy + gr] : 0.0f;
+        }
+        for (int e = threadIdx.x; e < KW * S; e += 256) {
+            const int cc = e / KW, k = e % KW;
+            Bs[k][cc] = (cc < ncols && k0 + k < m) ? B[(int64_t)cc * m + k0 + k] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < KW; ++k) {
+            const float4 y4 = *reinterpret_cast<const float4 *>(&Ys[k][4 * tx]);
+            const float y[4] = {y4.x, y4.y, y4.z, y4.w};
+            float b[T];
+#pragma unroll
+            for (int j = 0; j < T; ++j) b[j] = Bs[k][ty * T + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < T; ++j) acc[i][j] = fmaf(y[i], b[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+        const int gc = ty * T + j;
+        if (gc >= c) continue;
+        const bool zero = gc >= ncols || (colmask && colmask[gc]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t gr = r0 + 4 * tx + i;
+            if (gr < n) Z[(int64_t)gc * ldz + gr] = zero ? 0.0f : acc[i][j];
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv, int *dead,
@@ -394,7 +454,20 @@ cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64
                               const float *B, int c, const int *colmask, const int *d_cols,
                               float *Z, int64_t ldz)
 {
-    dim3 grid((unsigned)((n + TR - 1) / TR), (unsigned)((c + TC - 1) / TC));
-    tall_small_kernel<<<grid, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz);
+    const unsigned rb = (unsigned)((n + TR - 1) / TR);
+    switch ((c + 15) / 16) {
+    case 1: tall_small_wide_kernel<1><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    case 2: tall_small_wide_kernel<2><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    case 3: tall_small_wide_kernel<3><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    case 4: tall_small_wide_kernel<4><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    case 5: tall_small_wide_kernel<5><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    case 6: tall_small_wide_kernel<6><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    case 7: tall_small_wide_kernel<7><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    case 8: tall_small_wide_kernel<8><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    default: {
+        dim3 grid(rb, (unsigned)((c + TC - 1) / TC));
+        tall_small_kernel<<<grid, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz);
+    }
+    }
     return cudaGetLastError();
 }

@@ -83,6 +83,7 @@ struct psdproj_ctx {
     psd_timing timing;
     cudaStream_t stream = nullptr;
     int sm_count = 0;
+    int persist_sms = 0;         // grid of the persistent kernels
     int *d_status = nullptr;     // device status word
     psd_workspace ws;
     // host-API staging buffers

@@ -2,8 +2,8 @@
 //   G = Y^T Y           (CholeskyQR2, the QR 'econ' of Alg. 1)
 //   C = (Q^T Z + Z^T Q)/2 with Z = A Q  (the projected core Q^T A Q of Alg. 2)
 // Each thread block forms the FP32 partial product of one chunk of 64 rows
-// (8 x 8 register micro-tiles); a second kernel sums the chunk partials in
-// FP64 in a fixed order (deterministic, no atomics).
+// (register micro-tiles); a second kernel sums the chunk partials in FP64 in
+// a fixed order (deterministic, no atomics).
 #include "ctx.h"
 
 namespace {
@@ -85,6 +85,65 @@ gram_partial_kernel(const float *__restrict__ X, int64_t ldx, const float *__res
     }
 }
 
+// The same partial products for m <= 128 with every thread busy: a 16 x 16
+// thread grid covers the whole mp x mp square (thread (tx, ty) owns rows
+// ty T .. ty T + T-1 and columns tx T .. tx T + T-1, T = ceil(mp / 16), so
+// 16 T >= m), reading the staged rows with stride T (conflict-free for odd
+// T).  Symmetric products are formed in full; the reduction reads the half
+// it needs.
+template <int T>
+__global__ void __launch_bounds__(NT)
+gram_partial_sq_kernel(const float *__restrict__ X, int64_t ldx, const float *__restrict__ Z,
+                       int64_t ldz, int64_t n, int m, int mp, float *__restrict__ gpart)
+{
+    constexpr int S = 16 * T;
+    __shared__ float Xs[RS][S + 1];
+    __shared__ float Zs[RS][S + 1];
+    const int64_t row0 = (int64_t)blockIdx.x * CH;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const bool same = (X == Z) && (ldx == ldz);
+    float acc[T][T];
+#pragma unroll
+    for (int u = 0; u < T; ++u)
+#pragma unroll
+        for (int v = 0; v < T; ++v) acc[u][v] = 0.0f;
+    for (int rs = 0; rs < CH; rs += RS) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < RS * S; e += NT) {
+            const int a = e / RS, k = e - (e / RS) * RS;
+            const int64_t r = row0 + rs + k;
+            const bool ok = r < n && a < m;
+            Xs[k][a] = ok ? X[(int64_t)a * ldx + r] : 0.0f;
+            if (!same) Zs[k][a] = ok ? Z[(int64_t)a * ldz + r] : 0.0f;
+        }
+        __syncthreads();
+        const float (*Zsrc)[S + 1] = same ? Xs : Zs;
+#pragma unroll 4
+        for (int k = 0; k < RS; ++k) {
+            float x[T], z[T];
+#pragma unroll
+            for (int u = 0; u < T; ++u) {
+                x[u] = Xs[k][ty * T + u];
+                z[u] = Zsrc[k][tx * T + u];
+            }
+#pragma unroll
+            for (int u = 0; u < T; ++u)
+#pragma unroll
+                for (int v = 0; v < T; ++v) acc[u][v] = fmaf(x[u], z[v], acc[u][v]);
+        }
+    }
+    float *out = gpart + (int64_t)blockIdx.x * mp * mp;
+#pragma unroll
+    for (int u = 0; u < T; ++u) {
+        const int a = ty * T + u;
+#pragma unroll
+        for (int v = 0; v < T; ++v) {
+            const int b = tx * T + v;
+            if (a < m && b < m) out[a * mp + b] = acc[u][v];
+        }
+    }
+}
+
 // G[a + b*m] = sum over chunks of gpart (FP64); mode 0: full product,
 // mode 1: upper-only symmetric Gram (mirror), mode 2: symmetrise (S+S^T)/2.
 // Eight lanes share one entry of the partials (coalesced over the entry
@@ -127,11 +186,24 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
     const int mp = (int)psd_round_up(m, 8);
     const int nchunk = (int)((n + CH - 1) / CH);
     const size_t smem = sizeof(float) * 2 * RS * (size_t)mp;
-    cudaError_t e = cudaFuncSetAttribute(gram_partial_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    gram_partial_kernel<<<nchunk, NT, smem, s>>>(X, ldx, Z, ldz, n, m, mp, symmetrize == 1,
-                                                 gpart);
+    cudaError_t e = cudaSuccess;
+    const int T = (mp + 15) / 16;
+    switch (T) {
+    case 1: gram_partial_sq_kernel<1><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
+    case 2: gram_partial_sq_kernel<2><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
+    case 3: gram_partial_sq_kernel<3><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
+    case 4: gram_partial_sq_kernel<4><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
+    case 5: gram_partial_sq_kernel<5><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
+    case 6: gram_partial_sq_kernel<6><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
+    case 7: gram_partial_sq_kernel<7><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
+    case 8: gram_partial_sq_kernel<8><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
+    default:
+        e = cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        gram_partial_kernel<<<nchunk, NT, smem, s>>>(X, ldx, Z, ldz, n, m, mp, symmetrize == 1,
+                                                     gpart);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (symmetrize == 2) {

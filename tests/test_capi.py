@@ -61,3 +61,13 @@ def test_rejects_bad_arguments_without_a_gpu(lib):
 def test_built_for_sm_103a_only():
     src = open(os.path.join(ROOT, "paper_2410_19208_gb300", "build.py")).read()
     assert "arch=compute_103a,code=sm_103a" in src
+
+
+def test_batched_descriptor_layout_and_rejection(lib):
+    import ctypes
+    import paper_2410_19208_gb300 as ps
+    # the ctypes mirror of psdproj_problem has the C layout (8-byte members first)
+    assert ctypes.sizeof(ps.Problem) == 112
+    assert ps.Problem.seed.offset == 40 and ps.Problem.d_rank.offset == 104
+    # no context: argument error before any device work
+    assert lib.psdproj_batched(None, 1, None, None) == 1

@@ -258,3 +258,49 @@ def test_bf16_form_error_against_exact_projection(ctx, oracle_lib, alg):
     err_o = np.sqrt(max(oracle_lib.exact_dist2(Vr, lam, Wo), 0)) / xp
     assert err_g <= 1.1 * err_o
     assert _rel(got["P"], Wo @ Wo.T) <= 2e-2
+
+
+# ----------------------------------------------------------------------------
+# batched entry point (many small matrices, log-uniform sides)
+# ----------------------------------------------------------------------------
+def test_batched_matches_single_calls_and_oracle(ctx, oracle_lib):
+    # the batch recipe: sides log-uniform in [64, 600], k = min(n/8, 64),
+    # p = 8, q = 1, the two algorithms alternating
+    sizes = si.log_uniform_sizes(6, 64, 600, seed=11)
+    probs, singles, refs = [], [], []
+    for i, n in enumerate(int(x) for x in sizes):
+        k, p, q, seed, alg = max(2, min(n // 8, 64)), 8, 1, 100 + i, 1 + (i % 2)
+        Vr, lam = si.make_problem("batch", n, seed_u=i, seed_lam=50 + i)
+        A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
+        singles.append(_run(ctx, A32, k, p, q, seed, alg=alg))
+        Ad = torch.from_numpy(A32).cuda()
+        P = torch.full((n, n), float("nan"), device="cuda")
+        W = ps.tall_empty(n, k + p)
+        rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+        probs.append(dict(A=Ad, k=k, p=p, q=q, seed=seed, algorithm=alg, P=P, W=W, rank=rank))
+        ref = (oracle_lib.alg1(A32.astype(np.float64), k, p, q, seed) if alg == 1
+               else oracle_lib.alg2(A32.astype(np.float64), k, p, q, seed))
+        refs.append(ref["W"] @ ref["W"].T if alg == 1 else ref["W_red"] @ ref["W_red"].T)
+    ctx.batched(probs)
+    assert ctx.sync_status() == 0
+    for pb, one, Pref in zip(probs, singles, refs):
+        P = pb["P"].cpu().numpy().astype(np.float64)
+        # the batch runs the same kernels in the same order; only the order of
+        # the FP32 atomic additions in the symmetric pass differs between runs
+        assert _rel(P, one["P"]) <= 1e-5
+        assert int(pb["rank"].item()) == one["rank"]
+        assert _rel(P, Pref) <= TOL
+
+
+def test_batched_rejects_bad_problems_before_running(ctx):
+    n = 100
+    A = torch.zeros(n, n, device="cuda")
+    P = torch.full((n, n), 7.0, device="cuda")
+    good = dict(A=A, k=8, p=4, q=0, seed=1, algorithm=1, P=P)
+    bad = dict(A=A, k=8, p=4, q=0, seed=1, algorithm=3, P=P)
+    with pytest.raises(ps.PsdprojError) as ei:
+        ctx.batched([good, bad])
+    assert ei.value.code == 1
+    assert ctx.sync_status() == 0
+    assert torch.all(P == 7.0)          # nothing ran
+    ctx.batched([])                      # an empty batch is a no-op
