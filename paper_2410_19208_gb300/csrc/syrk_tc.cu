@@ -8,11 +8,15 @@
 // swizzle: atoms of 64 rows x 8 columns of W, two atoms along M (and N).
 // The kernel is store-bound (1.6 GB of P at n = 20000): D is double-buffered
 // in TMEM so the MMAs of the next tile overlap the stores of this one; eight
-// epilogue warps store the tile row-major and, off the diagonal, its mirror
-// (coalesced along the rows of the mirrored tile), with streaming stores.
+// epilogue warps write the tile and, off the diagonal, its mirror by TMA
+// tensor stores of 32 x 32 boxes staged in shared memory (128-byte swizzle,
+// one 4 KB staging box per warp), so P is written in whole lines.  Diagonal
+// tiles of the upper-only mode and P without 16-byte aligned rows take
+// per-thread streaming stores.
 // Warp roles (384 threads): warp 0 TMA, warp 1 TMEM owner + MMA issuer,
 // warps 4-11 epilogue.  Every mbarrier wait is bounded.
 #include <cuda_bf16.h>
+#include <cstring>
 #include <cudaTypedefs.h>
 
 #include "ctx.h"
@@ -28,8 +32,12 @@ constexpr uint32_t OP_BYTES = TS * KMAX * 2; // one BF16 operand image (32 KB)
 constexpr uint32_t ATOM_COL = 64 * 2 * KMAX; // bytes of one 64-row atom column (16 KB)
 constexpr uint32_t OFF_WI = 0;               // hi, lo
 constexpr uint32_t OFF_WJ = 2 * OP_BYTES;    // [2 buffers][hi, lo]
-constexpr uint32_t OFF_BAR = OFF_WJ + 4 * OP_BYTES;
+constexpr uint32_t STG_BYTES = 32 * 32 * 4;  // epilogue staging box per warp
+constexpr uint32_t OFF_STG = OFF_WJ + 4 * OP_BYTES;
+constexpr uint32_t OFF_BAR = OFF_STG + 8 * STG_BYTES;
 constexpr uint32_t SMEM_BYTES = OFF_BAR + 256;
+static_assert(SMEM_BYTES <= 232448, "shared memory");
+static_assert(OFF_STG % 1024 == 0, "swizzle atoms");
 constexpr int NT = 384;
 constexpr uint32_t TMEM_COLS = 256;
 constexpr long long WAIT_LIMIT = 4000000000LL;
@@ -55,6 +63,7 @@ struct Params {
     int nprod;        // 3: split BF16, 1: BF16 hi only
     int *d_status;
     int vec_ok;
+    int tma_p;        // P written by TMA stores (16-byte aligned rows)
 };
 
 __device__ __forceinline__ int64_t row_start(int I, int nb)
@@ -93,7 +102,7 @@ __device__ __forceinline__ void st_cs4(float *p, float a, float b, float c, floa
 
 __global__ void __launch_bounds__(NT, 1)
 syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_constant__ CUtensorMap tmLo,
-                   const Params P)
+                   const __grid_constant__ CUtensorMap tmP, const Params P)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
     Bars &B = *reinterpret_cast<Bars *>(sm + OFF_BAR);
@@ -252,6 +261,45 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
             const int64_t gi = (int64_t)TS * I + 32 * q + lane;   // row of P
             const int64_t gj0 = (int64_t)TS * J + 64 * g;          // first column
             const bool diag = (I == J);
+            if (P.tma_p && !(diag && P.upper_only)) {
+                // 32 x 32 boxes: rows 32q.. of the tile, columns gj0 + 32c ..; the
+                // mirror box holds the same entries transposed
+                uint8_t *stg = sm + OFF_STG + (warp - 4) * STG_BYTES;
+                const int64_t i0 = (int64_t)TS * I + 32 * q;
+                for (int c = 0; c < 2; ++c) {
+                    const int64_t j0 = gj0 + 32 * c;
+                    if (j0 >= P.n || i0 >= P.n) continue;           // box outside P
+                    if (lane == 0) bulk_wait_read();
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        *reinterpret_cast<float4 *>(stg + lane * 128 + ((k ^ (lane & 7)) << 4)) =
+                            make_float4(v[32 * c + 4 * k], v[32 * c + 4 * k + 1], v[32 * c + 4 * k + 2],
+                                        v[32 * c + 4 * k + 3]);
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&tmP, (int)j0, (int)i0, stg);
+                        bulk_commit();
+                    }
+                    if (diag || P.upper_only) continue;      // no mirror: diagonal tile or upper only
+                    if (lane == 0) bulk_wait_read();
+                    __syncwarp();
+                    // mirror: row e of the box is column j0 + e of the tile; this
+                    // lane's entry goes to its column (lane) of every row
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        *reinterpret_cast<float *>(stg + e * 128 + (((lane >> 2) ^ (e & 7)) << 4) + 4 * (lane & 3)) =
+                            v[32 * c + e];
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tma_store_2d(&tmP, (int)i0, (int)j0, stg);
+                        bulk_commit();
+                    }
+                }
+                continue;
+            }
             if (gi < P.n) {
                 float *row = P.P + gi * P.ldp;
 #pragma unroll
@@ -277,6 +325,8 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
             }
         }
     }
+
+    if (warp >= 4 && lane == 0 && P.tma_p) bulk_wait_all();
 
     tc_fence_before();
     __syncthreads();
@@ -363,11 +413,24 @@ cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t
     p.nprod = 3;
     p.d_status = d_status;
     p.vec_ok = ((ldp % 4) == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
+    p.tma_p = p.vec_ok;
+    CUtensorMap tmP;
+    memset(&tmP, 0, sizeof(tmP));
+    if (p.tma_p) {
+        cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+        cuuint64_t strides[1] = {(cuuint64_t)ldp * 4};
+        cuuint32_t box[2] = {32, 32};
+        cuuint32_t estr[2] = {1, 1};
+        if (enc(&tmP, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, P, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            p.tma_p = 0;
+    }
     cudaError_t e = cudaFuncSetAttribute(syrk_bf16x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
     int grid = sm_count > 0 ? sm_count : 148;
     if ((int64_t)grid > p.tiles) grid = (int)p.tiles;
-    syrk_bf16x3_kernel<<<grid, NT, SMEM_BYTES, s>>>(tmHi, tmLo, p);
+    syrk_bf16x3_kernel<<<grid, NT, SMEM_BYTES, s>>>(tmHi, tmLo, tmP, p);
     return cudaGetLastError();
 }
