@@ -16,8 +16,8 @@ A (1.6 GB) is larger than L2, so no flush is needed between steps.
 
 `value` = projections / s over all ranks (N > 1: independent replicas, one
 per GPU, no collective on the data path), with the step's two projections on
-two independent contexts and CUDA streams (K Alg. 1 projections on one, K
-Alg. 2 on the other, timed until both finish); `sequential` gives the same
+two independent contexts and CUDA streams (one projection of each step on
+each, the two algorithms alternating between them, timed until both finish); `sequential` gives the same
 steps on one stream, and latency, stage times and rooflines come from it.  Extra keys: roofline of the
 dominant kernel, cpu_baseline (the FP64 oracle on host cores), e2e (the
 host-buffer C-ABI call with copies inside the timed region), clocks, kernel
@@ -345,18 +345,26 @@ def main():
                     clocks=clocks, W1=W1, W2=W2, opts=opts)
 
     def measure_concurrent(prec_, syrk_, steps, sample_clocks):
-        """K steps with the Alg. 1 projections on (ctx, stream) and the Alg. 2
-        projections on (ctx2, stream2); timed from an event on stream before
-        the first to stream after both streams' last projection."""
+        """K steps, each one Alg. 1 and one Alg. 2 projection on the two
+        contexts (ctx on stream, ctx2 on stream2), alternating which stream
+        gets which; timed from an event on stream before the first to stream
+        after both streams' last projection."""
         opts = ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_])
 
         def run(count):
             ev = torch.cuda.Event()
             ev.record(stream)
             stream2.wait_event(ev)
-            for _ in range(count):
-                ctx.alg1(A, k, p, q, SEED, P=P, W=W, rank=rank_t, opts=opts)
-                ctx2.alg2(A, k, p, q, SEED, alpha_out=alpha2, P=P2, W=W2, rank=rank2, opts=opts)
+            # each step enqueues one projection per stream, the algorithms
+            # alternating between the streams so both carry the same work
+            for i in range(count):
+                c1, b1 = (ctx, (P, W, rank_t, alpha_t)), (ctx2, (P2, W2, rank2, alpha2))
+                if i % 2:
+                    c1, b1 = b1, c1
+                ctx_a, (Pa, Wa, ra, _) = c1
+                ctx_b, (Pb, Wb, rb, ab) = b1
+                ctx_a.alg1(A, k, p, q, SEED, P=Pa, W=Wa, rank=ra, opts=opts)
+                ctx_b.alg2(A, k, p, q, SEED, alpha_out=ab, P=Pb, W=Wb, rank=rb, opts=opts)
             ev2 = torch.cuda.Event()
             ev2.record(stream2)
             stream.wait_event(ev2)
@@ -512,7 +520,8 @@ def main():
         "sequential": {"value": seq_value, "unit": "projections/s", "ms_per_step": elapsed_ms / args.steps,
                        "note": "the same steps on one context and one stream, Alg. 1 then Alg. 2; "
                                "latency, stages and rooflines are from this run"},
-        "concurrency": "two contexts: Alg. 1 projections on one CUDA stream, Alg. 2 projections on another",
+        "concurrency": "two contexts on two CUDA streams, one projection of each step on each, "
+                       "the algorithms alternating between the streams from step to step",
         "stages": stages, "gpu_launches": conc["launches"], "clocks": conc["clocks"],
         "error_vs_exact": {"alg1": err_exact(head["W1"]), "alg2": err_exact(head["W2"])},
     }
@@ -538,14 +547,18 @@ def main():
         if dist:
             dist.barrier()
 
-        def host_loop(fn):
-            for _ in range(args.e2e_steps):
-                fn()
+        def host_loop(c_, Ph_, first):
+            for i in range(args.e2e_steps):
+                if (i + first) % 2 == 0:
+                    c_.alg1_host(Ah, k, p, q, SEED, P=Ph_, opts=opts)
+                else:
+                    c_.alg2_host(Ah, k, p, q, SEED, P=Ph_, opts=opts)
 
         # the two projections of a step from two host threads (the C calls
-        # release the GIL), each on its own context and stream
-        th1 = threading.Thread(target=host_loop, args=(lambda: ctx.alg1_host(Ah, k, p, q, SEED, P=Ph, opts=opts),))
-        th2 = threading.Thread(target=host_loop, args=(lambda: ctx2.alg2_host(Ah, k, p, q, SEED, P=Ph2, opts=opts),))
+        # release the GIL), each on its own context and stream, the
+        # algorithms alternating between them
+        th1 = threading.Thread(target=host_loop, args=(ctx, Ph, 0))
+        th2 = threading.Thread(target=host_loop, args=(ctx2, Ph2, 1))
         t0 = time.perf_counter()
         th1.start()
         th2.start()

@@ -416,28 +416,86 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     __syncthreads();
 
     // ---------------------------------------------------------------- 4
-    // Z <- H_j Z for j = m-3 .. 0, H_j = I - beta_j v_j v_j^T, v_j = A[j+1.., j]
-    // (the four quarters of the block form partial dot products over rows
-    // i = quarter mod 4; T holds them, 4 x m)
-    for (int j = m - 3; j >= 0; --j) {
-        const float bt = beta[j];
-        if (bt == 0.0f) continue;                   // uniform across the block
-        const int r0 = j + 1;
-        const int qtr = tid >> 7, cl = tid & 127;
-        for (int c = cl; c < m; c += 128) {
-            float s0 = 0.0f;
-            for (int i = r0 + qtr; i < m; i += 4) s0 = fmaf(A[i * ld + j], Z[i * ld + c], s0);
-            T[qtr * ld + c] = s0;
+    // Z <- H_0 H_1 ... H_{m-3} Z in blocks of NB reflectors, last block
+    // first, each block in compact WY form H_jb ... H_{jb+nb-1} = I - V T V^T
+    // (V: the block's reflector vectors A[i][jb+t], i > jb+t; T upper
+    // triangular by the forward recurrence T[t][t] = beta_t,
+    // T[0:t, t] = -beta_t T[0:t, 0:t] V^T v_t):  Z <- Z - V (T (V^T Z)).
+    // W = V^T Z and then T W live in the first nb rows of the T buffer.
+    {
+        constexpr int NB = 16;
+        __shared__ float sS[NB][NB + 1], sT[NB][NB + 1];
+        const int nref = m - 2;                               // reflectors 0 .. m-3
+        for (int jb = nref > 0 ? ((nref - 1) / NB) * NB : -1; jb >= 0; jb -= NB) {
+            const int nb = min(NB, nref - jb);
+            // (a) W[t][c] = v_t^T Z[:, c] and S[s][t] = v_s^T v_t (s < t)
+            for (int q = tid; q < nb * m; q += NT) {
+                const int t = q / m, c = q - (q / m) * m;
+                const int col = jb + t;
+                float s0 = 0.0f, s1 = 0.0f;
+                int i = col + 1;
+                for (; i + 1 < m; i += 2) {
+                    s0 = fmaf(A[i * ld + col], Z[i * ld + c], s0);
+                    s1 = fmaf(A[(i + 1) * ld + col], Z[(i + 1) * ld + c], s1);
+                }
+                if (i < m) s0 = fmaf(A[i * ld + col], Z[i * ld + c], s0);
+                T[t * ld + c] = s0 + s1;
+            }
+            for (int q = tid; q < nb * nb; q += NT) {
+                const int sI = q / nb, tI = q - (q / nb) * nb;
+                if (sI < tI) {
+                    float acc = 0.0f;
+                    for (int i = jb + tI + 1; i < m; ++i) acc = fmaf(A[i * ld + jb + sI], A[i * ld + jb + tI], acc);
+                    sS[sI][tI] = acc;
+                }
+            }
+            __syncthreads();
+            // (b) T, one warp, column by column
+            if (warp == 0) {
+                for (int t = 0; t < nb; ++t) {
+                    const float bt = beta[jb + t];
+                    float y = 0.0f;
+                    if (lane < t)
+                        for (int s2 = lane; s2 < t; ++s2) y = fmaf(sT[lane][s2], sS[s2][t], y);
+                    __syncwarp();
+                    if (lane < t) sT[lane][t] = -bt * y;
+                    if (lane == t) sT[t][t] = bt;
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            // (c) W <- T W, a thread per column
+            for (int c = tid; c < m; c += NT) {
+                float w[NB];
+#pragma unroll
+                for (int t = 0; t < NB; ++t) w[t] = t < nb ? T[t * ld + c] : 0.0f;
+#pragma unroll
+                for (int sI = 0; sI < NB; ++sI) {
+                    if (sI >= nb) break;
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int t = 0; t < NB; ++t)
+                        if (t >= sI && t < nb) acc = fmaf(sT[sI][t], w[t], acc);
+                    T[sI * ld + c] = acc;
+                }
+            }
+            __syncthreads();
+            // (d) Z[i][c] -= sum_t V[i][t] W[t][c], rows i > jb (a warp per row)
+            for (int i = jb + 1 + warp; i < m; i += NT / 32) {
+                float v[NB];
+#pragma unroll
+                for (int t = 0; t < NB; ++t) v[t] = (t < nb && i > jb + t) ? A[i * ld + jb + t] : 0.0f;
+                float *zr = Z + i * ld;
+                for (int c = lane; c < m; c += 32) {
+                    float acc = zr[c];
+#pragma unroll
+                    for (int t = 0; t < NB; ++t)
+                        if (t < nb) acc = fmaf(-v[t], T[t * ld + c], acc);   // rows >= nb are stale
+                    zr[c] = acc;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int c = tid; c < m; c += NT) pp[c] = bt * ((T[c] + T[ld + c]) + (T[2 * ld + c] + T[3 * ld + c]));
-        __syncthreads();
-        for (int i = r0 + warp; i < m; i += NT / 32) {
-            const float vi = A[i * ld + j];
-            float *zr = Z + i * ld;
-            for (int c = lane; c < m; c += 32) zr[c] = fmaf(-vi, pp[c], zr[c]);
-        }
-        __syncthreads();
     }
 
     // ---------------------------------------------------------------- 5
