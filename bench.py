@@ -15,10 +15,11 @@ rest N(0, 0.01^2), formed in FP64 and rounded to FP32 (synth_inputs.py).
 A (1.6 GB) is larger than L2, so no flush is needed between steps.
 
 `value` = projections / s over all ranks (N > 1: independent replicas, one
-per GPU, no collective on the data path), with the step's two projections on
-two independent contexts and CUDA streams (one projection of each step on
-each, the two algorithms alternating between them, timed until both finish); `sequential` gives the same
-steps on one stream, and latency, stage times and rooflines come from it.  Extra keys: roofline of the
+per GPU, no collective on the data path), with the 2K projections of the K
+steps spread over S = 4 independent contexts and CUDA streams (every stream
+gets both algorithms; timed until all streams finish; --streams sets S).
+`sequential` gives the same steps on one stream, and latency, stage times and
+rooflines come from it.  Extra keys: roofline of the
 dominant kernel, cpu_baseline (the FP64 oracle on host cores), e2e (the
 host-buffer C-ABI call with copies inside the timed region), clocks, kernel
 launches, per-algorithm latency p50/p99, per-stage times and accuracy against
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="independent contexts / CUDA streams the projections of the headline run on")
     return ap.parse_args()
 
 
@@ -260,15 +263,16 @@ def main():
     W = ps.tall_empty(n, m, dev)
     rank_t = torch.zeros(1, dtype=torch.int32, device=dev)
     alpha_t = torch.zeros(1, dtype=torch.float64, device=dev)
-    # a second, independent context on its own stream: the headline runs the
-    # step's Alg. 1 projections on the first and its Alg. 2 projections on
-    # the second, concurrently
-    stream2 = torch.cuda.Stream(dev)
-    ctx2 = ps.Context(local, stream2)
-    P2 = torch.empty(n, n, device=dev)
-    W2 = ps.tall_empty(n, m, dev)
-    rank2 = torch.zeros(1, dtype=torch.int32, device=dev)
-    alpha2 = torch.zeros(1, dtype=torch.float64, device=dev)
+    # further independent contexts, each on its own stream: the headline
+    # spreads the projections of the K steps over all of them
+    S = max(1, args.streams)
+    lanes = [(ctx, stream, P, W, rank_t, alpha_t)]
+    for _ in range(S - 1):
+        st_ = torch.cuda.Stream(dev)
+        lanes.append((ps.Context(local, st_), st_, torch.empty(n, n, device=dev), ps.tall_empty(n, m, dev),
+                      torch.zeros(1, dtype=torch.int32, device=dev),
+                      torch.zeros(1, dtype=torch.float64, device=dev)))
+    ctx2 = lanes[1][0] if S > 1 else ctx
     import ctypes
 
     def pct(v, q_):
@@ -345,33 +349,32 @@ def main():
                     clocks=clocks, W1=W1, W2=W2, opts=opts)
 
     def measure_concurrent(prec_, syrk_, steps, sample_clocks):
-        """K steps, each one Alg. 1 and one Alg. 2 projection on the two
-        contexts (ctx on stream, ctx2 on stream2), alternating which stream
-        gets which; timed from an event on stream before the first to stream
-        after both streams' last projection."""
+        """K steps (one Alg. 1 and one Alg. 2 projection each) spread over the S
+        contexts: projection j (step j // 2) goes to stream (j + j // 2) mod S,
+        so every stream gets both algorithms; timed from an event on the first
+        stream before the first projection to the first stream after every
+        stream's last one."""
         opts = ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_])
 
         def run(count):
             ev = torch.cuda.Event()
             ev.record(stream)
-            stream2.wait_event(ev)
-            # each step enqueues one projection per stream, the algorithms
-            # alternating between the streams so both carry the same work
-            for i in range(count):
-                c1, b1 = (ctx, (P, W, rank_t, alpha_t)), (ctx2, (P2, W2, rank2, alpha2))
-                if i % 2:
-                    c1, b1 = b1, c1
-                ctx_a, (Pa, Wa, ra, _) = c1
-                ctx_b, (Pb, Wb, rb, ab) = b1
-                ctx_a.alg1(A, k, p, q, SEED, P=Pa, W=Wa, rank=ra, opts=opts)
-                ctx_b.alg2(A, k, p, q, SEED, alpha_out=ab, P=Pb, W=Wb, rank=rb, opts=opts)
-            ev2 = torch.cuda.Event()
-            ev2.record(stream2)
-            stream.wait_event(ev2)
+            for ln in lanes[1:]:
+                ln[1].wait_event(ev)
+            for j in range(2 * count):
+                c_, _, P_, W_, r_, a_ = lanes[(j + j // 2) % S]
+                if j % 2 == 0:
+                    c_.alg1(A, k, p, q, SEED, P=P_, W=W_, rank=r_, opts=opts)
+                else:
+                    c_.alg2(A, k, p, q, SEED, alpha_out=a_, P=P_, W=W_, rank=r_, opts=opts)
+            for ln in lanes[1:]:
+                ev2 = torch.cuda.Event()
+                ev2.record(ln[1])
+                stream.wait_event(ev2)
 
         run(max(args.warmup, 3))
         torch.cuda.synchronize(dev)
-        for c_ in (ctx, ctx2):
+        for c_ in [ln[0] for ln in lanes]:
             st = c_.sync_status()
             if st != 0:
                 raise SystemExit(f"device status {ps.STATUS.get(st)} during warm-up (concurrent)")
@@ -393,7 +396,7 @@ def main():
             dist.barrier()
         clocks = sampler.stop() if sampler else None
         launches = int(ps.lib().psdproj_kernel_launches() - l0)
-        for c_ in (ctx, ctx2):
+        for c_ in [ln[0] for ln in lanes]:
             st = c_.sync_status()
             if st != 0:
                 raise SystemExit(f"device status {ps.STATUS.get(st)} in the timed region (concurrent)")
@@ -520,8 +523,8 @@ def main():
         "sequential": {"value": seq_value, "unit": "projections/s", "ms_per_step": elapsed_ms / args.steps,
                        "note": "the same steps on one context and one stream, Alg. 1 then Alg. 2; "
                                "latency, stages and rooflines are from this run"},
-        "concurrency": "two contexts on two CUDA streams, one projection of each step on each, "
-                       "the algorithms alternating between the streams from step to step",
+        "concurrency": f"{S} contexts on {S} CUDA streams; the 2K projections of the K steps are spread "
+                       "over them, every stream getting both algorithms",
         "stages": stages, "gpu_launches": conc["launches"], "clocks": conc["clocks"],
         "error_vs_exact": {"alg1": err_exact(head["W1"]), "alg2": err_exact(head["W2"])},
     }
@@ -579,7 +582,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         A64 = A.cpu().numpy().astype(np.float64)
-        del P, P2
+        del P, lanes
         torch.cuda.empty_cache()
         t_or, Wo = oracle_sample(A64, n, k, p, q)
         del A64
@@ -597,7 +600,8 @@ def main():
                                           f"(k={k}, p={p}, q={q}), {t_or:.1f} s"}
     print(json.dumps(line), flush=True)
     ctx.close()
-    ctx2.close()
+    for ln in (lanes[1:] if 'lanes' in locals() else []):
+        ln[0].close()
     if dist:
         dist.destroy_process_group()
 
