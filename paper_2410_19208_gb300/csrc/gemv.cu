@@ -271,6 +271,21 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
             }
         };
         load_xr(I);
+        // column values of x for tile column Jv (zero past n)
+        auto load_xc = [&](int Jv, float (&out)[8]) {
+            const int64_t c0 = (int64_t)Jv * PSD_TILE_N + 8 * k;
+            if (c0 + 8 <= n) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(x + c0));
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(x + c0 + 4));
+                out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+                out[4] = b.x; out[5] = b.y; out[6] = b.z; out[7] = b.w;
+            } else {
+#pragma unroll
+                for (int v = 0; v < 8; ++v) out[v] = (c0 + v < n) ? x[c0 + v] : 0.0f;
+            }
+        };
+        float xn[8];
+        load_xc(J, xn);
         int64_t it = 0;
         for (int64_t t = t0; t < t1; ++t, ++it) {
             if (J == PSD_TILE_R * I) has_diag = true;
@@ -286,16 +301,14 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
                 *abort = 1;
                 psd_set_status(d_status, PSDPROJ_ETIMEOUT);
             }
+            // this tile's column values of x (loaded one tile ahead), then the next tile's
             float xc[8];
-            const int64_t c0 = (int64_t)J * PSD_TILE_N + 8 * k;
-            if (c0 + 8 <= n) {
-                const float4 a = __ldg(reinterpret_cast<const float4 *>(x + c0));
-                const float4 b = __ldg(reinterpret_cast<const float4 *>(x + c0 + 4));
-                xc[0] = a.x * sc; xc[1] = a.y * sc; xc[2] = a.z * sc; xc[3] = a.w * sc;
-                xc[4] = b.x * sc; xc[5] = b.y * sc; xc[6] = b.z * sc; xc[7] = b.w * sc;
-            } else {
 #pragma unroll
-                for (int v = 0; v < 8; ++v) xc[v] = (c0 + v < n) ? x[c0 + v] * sc : 0.0f;
+            for (int v = 0; v < 8; ++v) xc[v] = xn[v] * sc;
+            {
+                int In = I, Jn = J + 1;
+                if (Jn == nbc) { ++In; Jn = PSD_TILE_R * In; }
+                load_xc(Jn, xn);
             }
             float colacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const uint8_t *tile = smt + s * gt::TILE_BYTES;

@@ -354,43 +354,54 @@ __global__ void to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t
 }
 
 // BF16 image A' of the block upper triangle of A (see the top of this file).
-// Block: 16 rows x 64 columns of one tile, 16 threads per row; a thread
-// converts 4 consecutive entries (one float4 of A) into the half of a
-// 16-byte chunk of its row.  grid.x: 64-column tiles J, grid.y: 16-row
-// chunks; tiles left of the diagonal block exit at once.
+// Block: 64 rows x 64 columns of one tile, 16 threads per row; a thread
+// converts 4 consecutive entries (one float4 of A) in each of 4 rows 16
+// apart, its four loads issued together, into halves of 16-byte chunks of
+// the swizzled rows.  grid.x: 64-column tiles J, grid.y: 64-row chunks;
+// tiles left of the diagonal block exit at once.
 __global__ void __launch_bounds__(256)
 pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
                        uint16_t *__restrict__ Ab, int nbc, int vec)
 {
+    constexpr int RPT = 4;                            // rows per thread
     const int J = blockIdx.x;
-    const int64_t r = (int64_t)blockIdx.y * 16 + (threadIdx.x >> 4);
-    const int I = (int)(((int64_t)blockIdx.y * 16) / BM);
+    const int I = (int)(((int64_t)blockIdx.y * 64) / BM);
     if (J < R * I) return;                            // uniform across the block
+    const int64_t rbase = (int64_t)blockIdx.y * 64 + (threadIdx.x >> 4);
     const int64_t c0 = (int64_t)J * BN + 4 * (threadIdx.x & 15);
-    float v[4];
-    if (r < n && vec && c0 + 4 <= n) {
-        const float4 a = __ldcs(reinterpret_cast<const float4 *>(A + r * lda + c0));
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    } else {
+    float v[RPT][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = (r < n && c0 + q < n) ? A[r * lda + c0 + q] : 0.0f;
-    }
-    if (J < R * (I + 1)) {
-        // diagonal block: keep the strict upper part, halve the diagonal
+    for (int u = 0; u < RPT; ++u) {
+        const int64_t r = rbase + 16 * u;
+        if (r < n && vec && c0 + 4 <= n) {
+            const float4 a = __ldcs(reinterpret_cast<const float4 *>(A + r * lda + c0));
+            v[u][0] = a.x; v[u][1] = a.y; v[u][2] = a.z; v[u][3] = a.w;
+        } else {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int64_t c = c0 + q;
-            v[q] = c > r ? v[q] : (c == r ? 0.5f * v[q] : 0.0f);
+            for (int qq = 0; qq < 4; ++qq) v[u][qq] = (r < n && c0 + qq < n) ? A[r * lda + c0 + qq] : 0.0f;
         }
     }
-    uint2 o;
-    o.x = pack_bf16(v[0], v[1]);
-    o.y = pack_bf16(v[2], v[3]);
-    const int rt = (int)(r - (int64_t)I * BM);         // row within the tile
+    const bool diagblk = J < R * (I + 1);
     const int k = (threadIdx.x & 15) >> 1;             // 16-byte chunk of the row
     const int64_t t = psd_tile_row_start(I, nbc) + (J - R * I);
     uint8_t *tile = reinterpret_cast<uint8_t *>(Ab + t * PSD_TILE_ELEMS);
-    *reinterpret_cast<uint2 *>(tile + rt * 128 + ((k ^ (rt & 7)) << 4) + 8 * (threadIdx.x & 1)) = o;
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+        const int64_t r = rbase + 16 * u;
+        if (diagblk) {
+            // diagonal block: keep the strict upper part, halve the diagonal
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const int64_t c = c0 + qq;
+                v[u][qq] = c > r ? v[u][qq] : (c == r ? 0.5f * v[u][qq] : 0.0f);
+            }
+        }
+        uint2 o;
+        o.x = pack_bf16(v[u][0], v[u][1]);
+        o.y = pack_bf16(v[u][2], v[u][3]);
+        const int rt = (int)(r - (int64_t)I * BM);     // row within the tile
+        *reinterpret_cast<uint2 *>(tile + rt * 128 + ((k ^ (rt & 7)) << 4) + 8 * (threadIdx.x & 1)) = o;
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
@@ -416,7 +427,7 @@ cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t 
     const int nbr = (int)((n + BM - 1) / BM);
     const int nbc = nbr * R;
     const int vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
-    dim3 grid((unsigned)nbc, (unsigned)(nbr * (BM / 16)));
+    dim3 grid((unsigned)nbc, (unsigned)(nbr * (BM / 64)));
     pack_upper_bf16_kernel<<<grid, 256, 0, s>>>(A, n, lda, Ab, nbc, vec);
     return cudaGetLastError();
 }
