@@ -54,8 +54,9 @@ extern "C" {
 #define PSDPROJ_PREC_TF32    1 /* reserved (A-passes: ENOTSUP)                  */
 #define PSDPROJ_PREC_BF16    2 /* tcgen05 kind::f16 on a BF16 image of A, FP32
                                   accumulation (see psdproj_alg1)              */
-#define PSDPROJ_PREC_BF16X3  3 /* split-BF16: hi*hi + hi*lo + lo*hi (SYRK only;
-                                  A-passes: ENOTSUP)                          */
+#define PSDPROJ_PREC_BF16X3  3 /* split-BF16: hi*hi + hi*lo + lo*hi, three
+                                  tcgen05 passes over BF16 images of A_hi and
+                                  A_lo = bf16(A - A_hi), FP32 accumulation    */
 
 /* ---- output modes -------------------------------------------------------- */
 #define PSDPROJ_OUT_FULL    0  /* P written in full (upper tiles mirrored)     */
@@ -139,7 +140,11 @@ uint64_t psdproj_kernel_launches(void);
  * context's BF16 image (256 x 64 tiles stored contiguously, about n^2 + 128 n
  * bytes; kept for later calls) and every product with A, the power
  * iterations of psdproj_alg2 included, reads that image on the tensor cores
- * or CUDA cores with FP32 accumulation. */
+ * or CUDA cores with FP32 accumulation.  opts->prec = PSDPROJ_PREC_BF16X3
+ * (also k+p <= 128) packs a second image of the residual A - bf16(A) (twice
+ * the memory) and computes every product with A as A_hi X_hi + A_hi X_lo +
+ * A_lo X_hi on the tensor cores (about 16 significant bits per product);
+ * its power iterations run on the CUDA cores in FP32. */
 int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                  int k, int p, int q, uint64_t seed,
                  float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
@@ -218,8 +223,10 @@ int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream,
  * (ldx, ldy >= n); dY is overwritten.  prec PSDPROJ_PREC_FP32: CUDA cores,
  * A read once.  PSDPROJ_PREC_BF16: A's block upper triangle is first packed
  * into the context's BF16 image (4 bytes read, 2 written per entry), which
- * the tensor-core pass then reads; requires m <= 128.  Other precisions and
- * m > 128 in BF16 return ENOTSUP. */
+ * the tensor-core pass then reads; requires m <= 128.  PSDPROJ_PREC_BF16X3:
+ * a second image holds bf16(A - A_hi) and three tensor-core passes add
+ * A_hi X_hi + A_hi X_lo + A_lo X_hi into dY (m <= 128).  PSDPROJ_PREC_TF32
+ * and m > 128 on the tensor cores return ENOTSUP. */
 int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                      const float *dX, int64_t ldx, int m, const double *d_shift,
                      float *dY, int64_t ldy, int prec);

@@ -180,28 +180,36 @@ int check_opts(const psdproj_opts *o)
 
 // The BF16 image of A used by the tensor-core passes: allocated on first
 // use (psd_tile_count(n) tiles of 32 KB, kept for later calls) and written
-// from A.
-int pack_bf16_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda)
+// from A; with_lo also writes the image of the low parts (split-BF16 form).
+int alloc_image(uint16_t **buf, size_t *cap, size_t bytes, cudaStream_t s)
 {
-    const size_t bytes = sizeof(uint16_t) * (size_t)psd_tile_count(n) * (size_t)PSD_TILE_ELEMS;
-    if (ctx->Ab_bytes < bytes) {
-        if (ctx->Ab) {
-            cudaStreamSynchronize(ctx->stream);
-            cudaFree(ctx->Ab);
-            ctx->Ab = nullptr;
-            ctx->Ab_bytes = 0;
-        }
-        cudaError_t e = cudaMalloc(&ctx->Ab, bytes);
-        if (e != cudaSuccess) return cuda_status(e);
-        ctx->Ab_bytes = bytes;
+    if (*cap >= bytes) return PSDPROJ_OK;
+    if (*buf) {
+        cudaStreamSynchronize(s);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
     }
-    stage_scope st(ctx, PSDPROJ_STAGE_PACK);
-    PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab), 1);
+    cudaError_t e = cudaMalloc(buf, bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    *cap = bytes;
     return PSDPROJ_OK;
 }
 
-// Y = A X + shift X in the requested precision (BF16: from the image that
-// pack_bf16_image wrote last)
+int pack_bf16_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, bool with_lo)
+{
+    const size_t bytes = sizeof(uint16_t) * (size_t)psd_tile_count(n) * (size_t)PSD_TILE_ELEMS;
+    PSD_TRY(alloc_image(&ctx->Ab, &ctx->Ab_bytes, bytes, ctx->stream));
+    if (with_lo) PSD_TRY(alloc_image(&ctx->Ab_lo, &ctx->Ab_lo_bytes, bytes, ctx->stream));
+    stage_scope st(ctx, PSDPROJ_STAGE_PACK);
+    PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab, 0), 1);
+    if (with_lo) PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab_lo, 1), 1);
+    return PSDPROJ_OK;
+}
+
+// Y = A X + shift X in the requested precision (BF16 forms: from the images
+// that pack_bf16_image wrote last).  Split BF16: A X ~ A_hi X_hi + A_hi X_lo
+// + A_lo X_hi, three tensor-core passes adding into Y.
 int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const float *X,
              int64_t ldx, int m, const double *d_shift, float *Y, int64_t ldy, int prec)
 {
@@ -210,10 +218,16 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
         PSD_KL(launch_sym_pass_simt(ctx->stream, A, n, lda, X, ldx, m, d_shift, Y, ldy), 1);
         return PSDPROJ_OK;
     }
-    if (prec != PSDPROJ_PREC_BF16) return PSDPROJ_ENOTSUP;
+    if (prec != PSDPROJ_PREC_BF16 && prec != PSDPROJ_PREC_BF16X3) return PSDPROJ_ENOTSUP;
     psd_workspace &ws = ctx->ws;
     PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, X, ldx, m, d_shift, Y, ldy,
-                              ws.Xhi, ws.ld, ctx->d_status), 2);
+                              ws.Xhi, ws.ld, ctx->d_status, 0, 0), 2);
+    if (prec == PSDPROJ_PREC_BF16X3) {
+        PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, X, ldx, m, nullptr, Y, ldy,
+                                  ws.Xlo, ws.ld, ctx->d_status, 1, 1), 2);
+        PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab_lo, n, X, ldx, m, nullptr, Y, ldy,
+                                  ws.Xhi, ws.ld, ctx->d_status, 0, 1), 2);
+    }
     return PSDPROJ_OK;
 }
 
@@ -262,16 +276,17 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     psd_workspace &ws = ctx->ws;
     cudaStream_t s = ctx->stream;
     const double *shift = nullptr;
-    const bool tc = opts.prec == PSDPROJ_PREC_BF16;
+    const bool split = opts.prec == PSDPROJ_PREC_BF16X3;
+    const bool tc = opts.prec == PSDPROJ_PREC_BF16 || split;
     if (opts.prec != PSDPROJ_PREC_FP32 && !tc) return PSDPROJ_ENOTSUP;
     if (tc && m > 128) return PSDPROJ_ENOTSUP;
-    // the BF16 form reads A once here and its 2-byte image in every later pass
-    if (tc) PSD_TRY(pack_bf16_image(ctx, dA, n, lda));
+    // the BF16 forms read A once here and the 2-byte image(s) in every later pass
+    if (tc) PSD_TRY(pack_bf16_image(ctx, dA, n, lda, split));
     if (scaled) {
         double *sc = ws.scal;
         if (!(alpha_in > 0.0)) {
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
-            if (tc) {
+            if (tc && !split) {
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
                                                    ws.pv0, ws.pv1, sc, ws.counter, sc + SC_SIGMA1,
                                                    ctx->d_status),
@@ -454,6 +469,7 @@ int psdproj_destroy(psdproj_ctx *ctx)
     if (ctx->dP_stage) cudaFree(ctx->dP_stage);
     if (ctx->dW_stage) cudaFree(ctx->dW_stage);
     if (ctx->Ab) cudaFree(ctx->Ab);
+    if (ctx->Ab_lo) cudaFree(ctx->Ab_lo);
     delete ctx;
     return PSDPROJ_OK;
 }
@@ -487,7 +503,10 @@ const char *psdproj_status_string(int s)
     }
 }
 
-size_t psdproj_workspace_bytes(const psdproj_ctx *ctx) { return ctx ? ctx->ws.bytes + ctx->Ab_bytes : 0; }
+size_t psdproj_workspace_bytes(const psdproj_ctx *ctx)
+{
+    return ctx ? ctx->ws.bytes + ctx->Ab_bytes + ctx->Ab_lo_bytes : 0;
+}
 
 int psdproj_timing_enable(psdproj_ctx *ctx, int on)
 {
@@ -601,12 +620,12 @@ int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, 
     if (!ctx || !dA || !dX || !dY || n < 1 || m < 1 || lda < n || ldx < n || ldy < n)
         return PSDPROJ_EINVAL;
     if (prec < PSDPROJ_PREC_FP32 || prec > PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
-    if (prec != PSDPROJ_PREC_FP32 && prec != PSDPROJ_PREC_BF16) return PSDPROJ_ENOTSUP;
-    if (prec == PSDPROJ_PREC_BF16 && m > 128) return PSDPROJ_ENOTSUP;
+    if (prec == PSDPROJ_PREC_TF32) return PSDPROJ_ENOTSUP;
+    if (prec != PSDPROJ_PREC_FP32 && m > 128) return PSDPROJ_ENOTSUP;
     device_guard g(ctx->device);
     if (prec == PSDPROJ_PREC_FP32) return sym_pass(ctx, dA, n, lda, dX, ldx, m, d_shift, dY, ldy, prec);
     PSD_TRY(psd_ensure_workspace(ctx, n, m));
-    PSD_TRY(pack_bf16_image(ctx, dA, n, lda));
+    PSD_TRY(pack_bf16_image(ctx, dA, n, lda, prec == PSDPROJ_PREC_BF16X3));
     return sym_pass(ctx, dA, n, lda, dX, ldx, m, d_shift, dY, ldy, prec);
 }
 

@@ -95,6 +95,8 @@ struct psdproj_ctx {
     // BF16 image of the block upper triangle of A (tensor-core passes)
     uint16_t *Ab = nullptr;
     size_t Ab_bytes = 0;
+    uint16_t *Ab_lo = nullptr;   // low parts (split-BF16 form)
+    size_t Ab_lo_bytes = 0;
 };
 
 // Make sure the workspace holds n rows x m columns; may synchronise the
@@ -114,16 +116,20 @@ cudaError_t launch_sym_pass_simt(cudaStream_t s, const float *A, int64_t n, int6
 // strictly upper, diagonal halved, zero below; A = A' + A'^T), in the tile
 // layout described with PSD_TILE_M (psd_tile_count(n) tiles of 32 KB), zero
 // padded past row / column n.  Ab 16-byte aligned.
-cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab);
+// part 1: the low parts bf16(a - bf16(a)) instead (split-BF16 form).
+cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab,
+                             int part);
 
 // Tensor-core symmetric pass Y = (A' + A'^T) X + shift X on the BF16 image;
 // Xh (ldh >= n, multiple of 8) receives the BF16 image of X.  Returns
 // cudaErrorNotSupported when the configuration is outside what the kernel
 // handles (m > 128, misaligned buffers).
+// x_part 0 / 1: multiply by the high / low BF16 part of X; accumulate != 0:
+// add to Y instead of overwriting it (pass d_shift = NULL then).
 cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t n, const float *X, int64_t ldx, int m,
                                const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
-                               int64_t ldh, int *d_status);
+                               int64_t ldh, int *d_status, int x_part, int accumulate);
 
 // Gram partials + FP64 reduction: G = X^T Z (sym = 1: X == Z, symmetric).
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,

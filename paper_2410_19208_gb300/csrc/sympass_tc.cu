@@ -341,16 +341,25 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// X (FP32, column-major) -> BF16 image used by the TMA loads of the pass
+// X (FP32, column-major) -> BF16 image used by the TMA loads of the pass:
+// part 0 = bf16(x) (the high part), part 1 = bf16(x - bf16(x)) (the low part
+// of the split-BF16 form)
 __global__ void to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t n, int m,
-                               __nv_bfloat16 *__restrict__ H, int64_t ldh)
+                               __nv_bfloat16 *__restrict__ H, int64_t ldh, int part)
 {
     const int64_t total = n * (int64_t)m;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e / n, i = e - c * n;
-        H[c * ldh + i] = __float2bfloat16_rn(X[c * ldx + i]);
+        const float x = X[c * ldx + i];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        H[c * ldh + i] = part ? __float2bfloat16_rn(x - __bfloat162float(hi)) : hi;
     }
+}
+
+__device__ __forceinline__ float lo_part(float v)
+{
+    return v - __bfloat162float(__float2bfloat16_rn(v));
 }
 
 // BF16 image A' of the block upper triangle of A (see the top of this file).
@@ -358,10 +367,11 @@ __global__ void to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t
 // converts 4 consecutive entries (one float4 of A) in each of 4 rows 16
 // apart, its four loads issued together, into halves of 16-byte chunks of
 // the swizzled rows.  grid.x: 64-column tiles J, grid.y: 64-row chunks;
-// tiles left of the diagonal block exit at once.
+// tiles left of the diagonal block exit at once.  part 1 writes the low
+// parts bf16(a - bf16(a)) instead (the split-BF16 form's second image).
 __global__ void __launch_bounds__(256)
 pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
-                       uint16_t *__restrict__ Ab, int nbc, int vec)
+                       uint16_t *__restrict__ Ab, int nbc, int vec, int part)
 {
     constexpr int RPT = 4;                            // rows per thread
     const int J = blockIdx.x;
@@ -396,6 +406,10 @@ pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
                 v[u][qq] = c > r ? v[u][qq] : (c == r ? 0.5f * v[u][qq] : 0.0f);
             }
         }
+        if (part) {
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) v[u][qq] = lo_part(v[u][qq]);
+        }
         uint2 o;
         o.x = pack_bf16(v[u][0], v[u][1]);
         o.y = pack_bf16(v[u][2], v[u][3]);
@@ -421,21 +435,22 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 
 }  // namespace
 
-cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab)
+cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab,
+                             int part)
 {
     if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0) return cudaErrorInvalidValue;
     const int nbr = (int)((n + BM - 1) / BM);
     const int nbc = nbr * R;
     const int vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
     dim3 grid((unsigned)nbc, (unsigned)(nbr * (BM / 64)));
-    pack_upper_bf16_kernel<<<grid, 256, 0, s>>>(A, n, lda, Ab, nbc, vec);
+    pack_upper_bf16_kernel<<<grid, 256, 0, s>>>(A, n, lda, Ab, nbc, vec, part);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t n, const float *X, int64_t ldx, int m,
                                const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
-                               int64_t ldh, int *d_status)
+                               int64_t ldh, int *d_status, int x_part, int accumulate)
 {
     if (m < 1 || m > 128) return cudaErrorNotSupported;
     if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0) return cudaErrorNotSupported;
@@ -449,7 +464,7 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
         const int64_t total = n * (int64_t)m;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4096) blocks = 4096;
-        to_bf16_kernel<<<blocks, 256, 0, s>>>(X, ldx, n, m, reinterpret_cast<__nv_bfloat16 *>(Xh), ldh);
+        to_bf16_kernel<<<blocks, 256, 0, s>>>(X, ldx, n, m, reinterpret_cast<__nv_bfloat16 *>(Xh), ldh, x_part);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -490,9 +505,11 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
             P.tma_y = 0;
     }
 
-    cudaError_t e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(float), 0, (size_t)n * sizeof(float),
-                                      (size_t)m, s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!accumulate) {
+        e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(float), 0, (size_t)n * sizeof(float), (size_t)m, s);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(sym_pass_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;

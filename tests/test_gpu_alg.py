@@ -245,10 +245,22 @@ def test_bf16_form_error_against_exact_projection(ctx, oracle_lib, alg):
     """Mixed precision (BF16 products on the tensor cores, FP32 accumulation):
     its error against the exact projection stays within 1.1x of the oracle's
     own randomized error, and it stays close to the oracle's output."""
+    _form_check(ctx, oracle_lib, alg, ps.PREC_BF16, ratio=1.1, close=2e-2)
+
+
+@pytest.mark.parametrize("alg", [1, 2])
+def test_split_bf16_form_error_against_exact_projection(ctx, oracle_lib, alg):
+    """Split BF16 (A X ~ A_hi X_hi + A_hi X_lo + A_lo X_hi, about 16 significant
+    bits per product): error against the exact projection within 1.01x of the
+    oracle's, output within 1e-3 of the oracle's."""
+    _form_check(ctx, oracle_lib, alg, ps.PREC_BF16X3, ratio=1.01, close=1e-3)
+
+
+def _form_check(ctx, oracle_lib, alg, prec, ratio, close):
     n, k, p, q, seed = 4096, 100, 10, 1, 1
     Vr, lam = si.make_problem("decay", n)
     A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
-    got = _run(ctx, A32, k, p, q, seed, alg=alg, opts=ps.make_opts(prec=ps.PREC_BF16))
+    got = _run(ctx, A32, k, p, q, seed, alg=alg, opts=ps.make_opts(prec=prec))
     if alg == 1:
         Wo = oracle_lib.alg1(A32.astype(np.float64), k, p, q, seed)["W"]
     else:
@@ -256,8 +268,8 @@ def test_bf16_form_error_against_exact_projection(ctx, oracle_lib, alg):
     xp = np.sqrt(np.sum(np.maximum(lam, 0) ** 2))
     err_g = np.sqrt(max(oracle_lib.exact_dist2(Vr, lam, got["W"]), 0)) / xp
     err_o = np.sqrt(max(oracle_lib.exact_dist2(Vr, lam, Wo), 0)) / xp
-    assert err_g <= 1.1 * err_o
-    assert _rel(got["P"], Wo @ Wo.T) <= 2e-2
+    assert err_g <= ratio * err_o
+    assert _rel(got["P"], Wo @ Wo.T) <= close
 
 
 # ----------------------------------------------------------------------------

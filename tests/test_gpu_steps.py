@@ -424,10 +424,30 @@ def test_sym_pass_tensor_core_unsupported(ctx):
     assert ei.value.code == 7
     X3 = ps.tall_empty(200, 8)
     Y3 = ps.tall_empty(200, 8)
-    for prec in (ps.PREC_TF32, ps.PREC_BF16X3):        # A-pass forms not provided
-        with pytest.raises(ps.PsdprojError) as ei:
-            ctx.sym_pass(A2, X3, Y3, prec=prec)
-        assert ei.value.code == 7
+    with pytest.raises(ps.PsdprojError) as ei:
+        ctx.sym_pass(A2, X3, Y3, prec=ps.PREC_TF32)    # A-pass form not provided
+    assert ei.value.code == 7
+
+
+@pytest.mark.parametrize("n", [1, 65, 257, 1000, 4099])
+@pytest.mark.parametrize("m", [1, 50, 112, 128])
+def test_sym_pass_split_bf16(ctx, oracle_lib, n, m):
+    # A X ~ A_hi X_hi + A_hi X_lo + A_lo X_hi with BF16 rounding (unit roundoff
+    # 2^-8): |a - hi - lo| <= 2^-16 |a|, same for x, and the dropped lo lo term
+    # is <= 2^-16 |a||x|, so each entry is within about 3 2^-16 |A||X| of the
+    # exact product (4 2^-16 allowed), plus the FP32 accumulation
+    A = _sym_A(n, seed=n + 7 * m)
+    rng = np.random.default_rng(m + 3)
+    X = rng.standard_normal((n, m)).astype(np.float32)
+    Y = ps.tall_empty(n, m, "cuda", ld=-(-n // 4) * 4)
+    shift = torch.tensor([0.5], dtype=torch.float64, device="cuda")
+    ctx.sym_pass(_padded_A(A), _tall_from_np(X), Y, shift=shift, prec=ps.PREC_BF16X3)
+    assert ctx.sync_status() == 0
+    A64, X64 = A.astype(np.float64), X.astype(np.float64)
+    ref = oracle_lib.sym_mul(A64, X64) + 0.5 * X64
+    bound = np.abs(A64) @ np.abs(X64) + 0.5 * np.abs(X64)
+    got = _np(Y)
+    assert np.all(np.abs(got - ref) <= (4 * 2.0 ** -16 + 8 * np.sqrt(n) * EPS32) * bound + 1e-30)
 
 
 # ----------------------------------------------------------------------------
