@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison")
+    ap.add_argument("--no-forms", action="store_true", help="skip the TF32 / split-BF16 comparison")
     ap.add_argument("--streams", type=int, default=4,
                     help="independent contexts / CUDA streams the projections of the headline run on")
     return ap.parse_args()
@@ -483,30 +484,53 @@ def main():
                                                 "sym_pass_simt_kernel")}
         path = None
     else:
-        cand = [
-            hbm_entry("sym_gemv_tiles (power iteration on the BF16 image)",
-                      "paper_2410_19208_gb300/csrc/gemv.cu", "sym_gemv_tiles_kernel", "gemv", 2 * (N_PI + 1),
-                      upper_elems * 2.0),
-            hbm_entry("sym_pass_bf16 (tcgen05, BF16 image)", "paper_2410_19208_gb300/csrc/sympass_tc.cu",
-                      "sym_pass_bf16_kernel", "apass", 1, upper_elems * 2.0, 2.0 * n * n * m),
-            hbm_entry("syrk_bf16x3 (tcgen05, P written)", "paper_2410_19208_gb300/csrc/syrk_tc.cu",
-                      "syrk_bf16x3_kernel", "syrk", 1, n * n * 4.0),
-            hbm_entry("pack_upper_bf16 (A read, image written)", "paper_2410_19208_gb300/csrc/sympass_tc.cu",
-                      "pack_upper_bf16_kernel", "pack", 1, upper_elems * 6.0),
-        ]
+        GEMV_FP32 = ("sym_gemv (power iteration, FP32 A)", "paper_2410_19208_gb300/csrc/gemv.cu",
+                     "sym_gemv_kernel", "gemv", 2 * (N_PI + 1), upper_elems * 4.0)
+        SYRK = ("syrk_bf16x3 (tcgen05, P written)", "paper_2410_19208_gb300/csrc/syrk_tc.cu",
+                "syrk_bf16x3_kernel", "syrk", 1, n * n * 4.0)
+        TC = "paper_2410_19208_gb300/csrc/sympass_tc.cu"
+        if prec == "bf16":
+            rows = [("sym_gemv_tiles (power iteration on the BF16 image)", "paper_2410_19208_gb300/csrc/gemv.cu",
+                     "sym_gemv_tiles_kernel", "gemv", 2 * (N_PI + 1), upper_elems * 2.0),
+                    ("sym_pass_bf16 (tcgen05, BF16 image)", TC, "sym_pass_bf16_kernel", "apass", 1,
+                     upper_elems * 2.0, 2.0 * n * n * m),
+                    SYRK,
+                    ("pack_upper_bf16 (A read, image written)", TC, "pack_upper_bf16_kernel", "pack", 1,
+                     upper_elems * 6.0)]
+        elif prec == "bf16x3":
+            # three tensor-core passes per product (A_hi X_hi, A_hi X_lo, A_lo X_hi)
+            rows = [GEMV_FP32,
+                    ("sym_pass_bf16 x3 (split BF16: hi and lo images)", TC, "sym_pass_bf16_kernel", "apass", 3,
+                     upper_elems * 2.0, 2.0 * n * n * m),
+                    SYRK,
+                    ("pack_upper_bf16 x2 (hi and lo images)", TC, "pack_upper_bf16_kernel", "pack", 2,
+                     upper_elems * 6.0)]
+        else:
+            # TF32: the pass streams the full image (n^2 x 4 bytes); its
+            # algorithmic bytes are the FP32 upper triangle's, U(n) x 4
+            TF = "paper_2410_19208_gb300/csrc/sympass_tf32.cu"
+            rows = [GEMV_FP32,
+                    ("sym_pass_tf32 (tcgen05 kind::tf32, full TF32 image)", TF, "sym_pass_tf32_kernel", "apass", 1,
+                     upper_elems * 4.0, 2.0 * n * n * m),
+                    SYRK,
+                    ("pack_full_tf32 (A upper read, full image written)", TF, "pack_full_tf32_kernel", "pack", 1,
+                     upper_elems * 4.0 + n * n * 4.0)]
+        cand = [hbm_entry(*r) for r in rows]
         cand = [c for c in cand if c is not None]
         dom = max(cand, key=lambda c: c["ms_per_step"])
         roof = dict(dom)
         roof["others"] = [c for c in cand if c is not dom]
         # whole step: every algorithmic HBM byte of both projections
         passes = 2 * q + 2
-        path_bytes = 2 * (6.0 * upper_elems + passes * 2.0 * upper_elems + 4.0 * n * n) \
-            + 2 * (N_PI + 1) * 2.0 * upper_elems
+        # algorithmic bytes per upper-triangle entry of the form: (pack, pass, power product)
+        per_entry = {"bf16": (6.0, 2.0, 2.0), "bf16x3": (8.0, 4.0, 4.0), "tf32": (8.0, 4.0, 4.0)}[prec]
+        path_bytes = 2 * (per_entry[0] * upper_elems + passes * per_entry[1] * upper_elems + 4.0 * n * n) \
+            + 2 * (N_PI + 1) * per_entry[2] * upper_elems
         step_ms = elapsed_ms / args.steps
         path = {"bytes_per_step": path_bytes, "achieved": path_bytes / (step_ms / 1e3) / 1e9,
                 "unit": "GB/s", "peak": peaks["hbm_gbs"],
                 "frac": path_bytes / (step_ms / 1e3) / 1e9 / peaks["hbm_gbs"],
-                "note": "per projection: pack + (2q+2) passes over the BF16 image + the P write; "
+                "note": "per projection: pack + (2q+2) passes over the image of A + the P write; "
                         "plus 2(N+1) power-iteration products for Alg. 3; the small steps "
                         "(orthonormalisation, eigensolver) move almost no HBM bytes"}
 
@@ -539,6 +563,17 @@ def main():
         Wg = plain["W1"]
     else:
         Wg = head["W1"]
+    if prec == "bf16" and not args.no_forms:
+        # the other tensor-core forms of the A-passes at the same (k, p, q,
+        # seed): one-stream time per step and error against the exact projection
+        forms = {}
+        for fp in ("tf32", "bf16x3"):
+            ks = max(2, min(args.steps, 3))
+            r = measure(fp, syrk_prec, ks, False)
+            forms[fp] = {"value": 2 * ks * world / (r["elapsed_ms"] / 1e3), "unit": "projections/s",
+                         "ms_per_step": r["elapsed_ms"] / ks, "streams": 1,
+                         "error_vs_exact": {"alg1": err_exact(r["W1"]), "alg2": err_exact(r["W2"])}}
+        line["forms"] = forms
 
     # ---- end to end through the host-buffer C-ABI call --------------------
     if not args.no_e2e:

@@ -51,7 +51,8 @@ extern "C" {
 
 /* ---- precision of the A-passes (sketch, power and core products) -------- */
 #define PSDPROJ_PREC_FP32    0 /* FP32 FMA on the CUDA cores (plain FP32)      */
-#define PSDPROJ_PREC_TF32    1 /* reserved (A-passes: ENOTSUP)                  */
+#define PSDPROJ_PREC_TF32    1 /* tcgen05 kind::tf32 on a full TF32 image of A
+                                  (both triangles), FP32 accumulation        */
 #define PSDPROJ_PREC_BF16    2 /* tcgen05 kind::f16 on a BF16 image of A, FP32
                                   accumulation (see psdproj_alg1)              */
 #define PSDPROJ_PREC_BF16X3  3 /* split-BF16: hi*hi + hi*lo + lo*hi, three
@@ -94,8 +95,8 @@ int psdproj_destroy(psdproj_ctx *ctx);
 int psdproj_sync_status(psdproj_ctx *ctx);
 /* Human-readable name of a status code (static storage). */
 const char *psdproj_status_string(int status);
-/* Bytes of device workspace the context holds now (the BF16 image of A
- * included). */
+/* Bytes of device workspace the context holds now (the tensor-core images
+ * of A included). */
 size_t psdproj_workspace_bytes(const psdproj_ctx *ctx);
 
 /* ---- diagnostics --------------------------------------------------------- */
@@ -144,7 +145,12 @@ uint64_t psdproj_kernel_launches(void);
  * (also k+p <= 128) packs a second image of the residual A - bf16(A) (twice
  * the memory) and computes every product with A as A_hi X_hi + A_hi X_lo +
  * A_lo X_hi on the tensor cores (about 16 significant bits per product);
- * its power iterations run on the CUDA cores in FP32. */
+ * its power iterations run on the CUDA cores in FP32.  opts->prec =
+ * PSDPROJ_PREC_TF32 (also k+p <= 128) packs a TF32 image of the full
+ * symmetric matrix (lower triangle mirrored from the upper one; about
+ * 4 n^2 bytes) and computes every product with A from it on the tensor cores
+ * (10 fraction bits per operand, products exact in FP32); its power
+ * iterations also run in FP32. */
 int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                  int k, int p, int q, uint64_t seed,
                  float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
@@ -225,8 +231,10 @@ int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream,
  * into the context's BF16 image (4 bytes read, 2 written per entry), which
  * the tensor-core pass then reads; requires m <= 128.  PSDPROJ_PREC_BF16X3:
  * a second image holds bf16(A - A_hi) and three tensor-core passes add
- * A_hi X_hi + A_hi X_lo + A_lo X_hi into dY (m <= 128).  PSDPROJ_PREC_TF32
- * and m > 128 on the tensor cores return ENOTSUP. */
+ * A_hi X_hi + A_hi X_lo + A_lo X_hi into dY (m <= 128).  PSDPROJ_PREC_TF32:
+ * A's upper triangle is mirrored into a full TF32 image (4 bytes written per
+ * entry of the n x n matrix) and one tensor-core pass reads it (m <= 128).
+ * m > 128 on the tensor cores returns ENOTSUP. */
 int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                      const float *dX, int64_t ldx, int m, const double *d_shift,
                      float *dY, int64_t ldy, int prec);

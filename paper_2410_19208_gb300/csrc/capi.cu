@@ -120,6 +120,7 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
         lay.Q = reinterpret_cast<float *>(take(tall));
         lay.T = reinterpret_cast<float *>(take(tall));
         lay.W = reinterpret_cast<float *>(take(tall));
+        lay.Xf = reinterpret_cast<float *>(take(tall));
         lay.Xhi = reinterpret_cast<uint16_t *>(take(half_tall));
         lay.Xlo = reinterpret_cast<uint16_t *>(take(half_tall));
         lay.gpart = reinterpret_cast<float *>(take(sizeof(float) * nchunk * lp * lp));
@@ -178,9 +179,11 @@ int check_opts(const psdproj_opts *o)
     return PSDPROJ_OK;
 }
 
-// The BF16 image of A used by the tensor-core passes: allocated on first
-// use (psd_tile_count(n) tiles of 32 KB, kept for later calls) and written
-// from A; with_lo also writes the image of the low parts (split-BF16 form).
+// The image of A read by the tensor-core passes: allocated on first use
+// (32 KB tiles, kept for later calls) and written from A.  BF16: the block
+// upper triangle, psd_tile_count(n) tiles; the split form also writes the
+// image of the low parts.  TF32: the full symmetric matrix,
+// psd_tile32_count(n) tiles, in the same buffer.
 int alloc_image(uint16_t **buf, size_t *cap, size_t bytes, cudaStream_t s)
 {
     if (*cap >= bytes) return PSDPROJ_OK;
@@ -196,9 +199,17 @@ int alloc_image(uint16_t **buf, size_t *cap, size_t bytes, cudaStream_t s)
     return PSDPROJ_OK;
 }
 
-int pack_bf16_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, bool with_lo)
+int pack_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, int prec)
 {
-    const size_t bytes = sizeof(uint16_t) * (size_t)psd_tile_count(n) * (size_t)PSD_TILE_ELEMS;
+    if (prec == PSDPROJ_PREC_TF32) {
+        const size_t bytes = (size_t)psd_tile32_count(n) * (size_t)PSD_TILE_BYTES;
+        PSD_TRY(alloc_image(&ctx->Ab, &ctx->Ab_bytes, bytes, ctx->stream));
+        stage_scope st(ctx, PSDPROJ_STAGE_PACK);
+        PSD_KL(launch_pack_tf32(ctx->stream, A, n, lda, reinterpret_cast<float *>(ctx->Ab)), 1);
+        return PSDPROJ_OK;
+    }
+    const bool with_lo = prec == PSDPROJ_PREC_BF16X3;
+    const size_t bytes = (size_t)psd_tile_count(n) * (size_t)PSD_TILE_BYTES;
     PSD_TRY(alloc_image(&ctx->Ab, &ctx->Ab_bytes, bytes, ctx->stream));
     if (with_lo) PSD_TRY(alloc_image(&ctx->Ab_lo, &ctx->Ab_lo_bytes, bytes, ctx->stream));
     stage_scope st(ctx, PSDPROJ_STAGE_PACK);
@@ -207,8 +218,8 @@ int pack_bf16_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, bo
     return PSDPROJ_OK;
 }
 
-// Y = A X + shift X in the requested precision (BF16 forms: from the images
-// that pack_bf16_image wrote last).  Split BF16: A X ~ A_hi X_hi + A_hi X_lo
+// Y = A X + shift X in the requested precision (tensor-core forms: from the
+// image(s) that pack_image wrote last).  Split BF16: A X ~ A_hi X_hi + A_hi X_lo
 // + A_lo X_hi, three tensor-core passes adding into Y.
 int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const float *X,
              int64_t ldx, int m, const double *d_shift, float *Y, int64_t ldy, int prec)
@@ -218,8 +229,13 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
         PSD_KL(launch_sym_pass_simt(ctx->stream, A, n, lda, X, ldx, m, d_shift, Y, ldy), 1);
         return PSDPROJ_OK;
     }
-    if (prec != PSDPROJ_PREC_BF16 && prec != PSDPROJ_PREC_BF16X3) return PSDPROJ_ENOTSUP;
     psd_workspace &ws = ctx->ws;
+    if (prec == PSDPROJ_PREC_TF32) {
+        PSD_KL(launch_sym_pass_tf32(ctx->stream, ctx->persist_sms, reinterpret_cast<const float *>(ctx->Ab), n,
+                                    X, ldx, m, d_shift, Y, ldy, ws.Xf, ws.ld, ctx->d_status), 2);
+        return PSDPROJ_OK;
+    }
+    if (prec != PSDPROJ_PREC_BF16 && prec != PSDPROJ_PREC_BF16X3) return PSDPROJ_ENOTSUP;
     PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, X, ldx, m, d_shift, Y, ldy,
                               ws.Xhi, ws.ld, ctx->d_status, 0, 0), 2);
     if (prec == PSDPROJ_PREC_BF16X3) {
@@ -276,17 +292,16 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     psd_workspace &ws = ctx->ws;
     cudaStream_t s = ctx->stream;
     const double *shift = nullptr;
-    const bool split = opts.prec == PSDPROJ_PREC_BF16X3;
-    const bool tc = opts.prec == PSDPROJ_PREC_BF16 || split;
-    if (opts.prec != PSDPROJ_PREC_FP32 && !tc) return PSDPROJ_ENOTSUP;
+    const bool bf16 = opts.prec == PSDPROJ_PREC_BF16;
+    const bool tc = opts.prec != PSDPROJ_PREC_FP32;
     if (tc && m > 128) return PSDPROJ_ENOTSUP;
-    // the BF16 forms read A once here and the 2-byte image(s) in every later pass
-    if (tc) PSD_TRY(pack_bf16_image(ctx, dA, n, lda, split));
+    // the tensor-core forms read A once here and their image(s) in every later pass
+    if (tc) PSD_TRY(pack_image(ctx, dA, n, lda, opts.prec));
     if (scaled) {
         double *sc = ws.scal;
         if (!(alpha_in > 0.0)) {
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
-            if (tc && !split) {
+            if (bf16) {
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
                                                    ws.pv0, ws.pv1, sc, ws.counter, sc + SC_SIGMA1,
                                                    ctx->d_status),
@@ -620,12 +635,11 @@ int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, 
     if (!ctx || !dA || !dX || !dY || n < 1 || m < 1 || lda < n || ldx < n || ldy < n)
         return PSDPROJ_EINVAL;
     if (prec < PSDPROJ_PREC_FP32 || prec > PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
-    if (prec == PSDPROJ_PREC_TF32) return PSDPROJ_ENOTSUP;
     if (prec != PSDPROJ_PREC_FP32 && m > 128) return PSDPROJ_ENOTSUP;
     device_guard g(ctx->device);
     if (prec == PSDPROJ_PREC_FP32) return sym_pass(ctx, dA, n, lda, dX, ldx, m, d_shift, dY, ldy, prec);
     PSD_TRY(psd_ensure_workspace(ctx, n, m));
-    PSD_TRY(pack_bf16_image(ctx, dA, n, lda, prec == PSDPROJ_PREC_BF16X3));
+    PSD_TRY(pack_image(ctx, dA, n, lda, prec));
     return sym_pass(ctx, dA, n, lda, dX, ldx, m, d_shift, dY, ldy, prec);
 }
 

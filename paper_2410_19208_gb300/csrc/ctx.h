@@ -33,6 +33,7 @@ constexpr int PSD_GRAM_CHUNK = 64;    // rows per Gram partial
 constexpr int PSD_TILE_M = 256, PSD_TILE_N = 64;
 constexpr int PSD_TILE_R = PSD_TILE_M / PSD_TILE_N;
 constexpr int64_t PSD_TILE_ELEMS = (int64_t)PSD_TILE_M * PSD_TILE_N;
+constexpr int64_t PSD_TILE_BYTES = 32768;
 // first tile of block row I (nbc = 64-column tiles of the padded matrix)
 __host__ __device__ inline int64_t psd_tile_row_start(int I, int nbc)
 {
@@ -42,6 +43,16 @@ __host__ __device__ inline int64_t psd_tile_count(int64_t n)
 {
     const int nbr = (int)((n + PSD_TILE_M - 1) / PSD_TILE_M);
     return psd_tile_row_start(nbr, nbr * PSD_TILE_R);
+}
+// The TF32 image holds the FULL symmetric matrix (both triangles, the lower
+// one mirrored from the upper) in tiles of 256 x 32 FP32 entries rounded to
+// TF32, again 128-byte swizzled rows (chunk k = columns 4k..4k+3), tile
+// (I, J) at index I * nbc + J with nbc = 8 * nbr.
+constexpr int PSD_TILE32_N = 32;
+__host__ __device__ inline int64_t psd_tile32_count(int64_t n)
+{
+    const int64_t nbr = (n + PSD_TILE_M - 1) / PSD_TILE_M;
+    return nbr * nbr * (PSD_TILE_M / PSD_TILE32_N);
 }
 constexpr int PSD_MAX_M = 256;        // largest sketch width
 
@@ -55,6 +66,7 @@ struct psd_workspace {
     float *Om = nullptr, *Y = nullptr, *Q = nullptr, *T = nullptr, *W = nullptr;
     // bf16 hi / lo images of a tall buffer (tensor-core passes)
     uint16_t *Xhi = nullptr, *Xlo = nullptr;
+    float *Xf = nullptr;  // X rounded to TF32 (TF32 pass operand)
     // Gram partials: nchunk x lpad x lpad floats
     float *gpart = nullptr;
     // small matrices
@@ -119,6 +131,17 @@ cudaError_t launch_sym_pass_simt(cudaStream_t s, const float *A, int64_t n, int6
 // part 1: the low parts bf16(a - bf16(a)) instead (split-BF16 form).
 cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t lda, uint16_t *Ab,
                              int part);
+
+// TF32 image of the full symmetric matrix (psd_tile32_count(n) tiles; the
+// lower triangle is mirrored from the upper one, which alone is read).
+cudaError_t launch_pack_tf32(cudaStream_t s, const float *A, int64_t n, int64_t lda, float *At);
+
+// Tensor-core symmetric pass in TF32 (tcgen05 kind::tf32, K-major operands
+// only) on the full TF32 image: Y = A X + shift X; Xf (ldf >= n, multiple of
+// 4, 16-byte aligned) receives X rounded to TF32.  Requires m <= 128.
+cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, int64_t n,
+                                 const float *X, int64_t ldx, int m, const double *d_shift,
+                                 float *Y, int64_t ldy, float *Xf, int64_t ldf, int *d_status);
 
 // Tensor-core symmetric pass Y = (A' + A'^T) X + shift X on the BF16 image;
 // Xh (ldh >= n, multiple of 8) receives the BF16 image of X.  Returns

@@ -256,6 +256,14 @@ def test_split_bf16_form_error_against_exact_projection(ctx, oracle_lib, alg):
     _form_check(ctx, oracle_lib, alg, ps.PREC_BF16X3, ratio=1.01, close=1e-3)
 
 
+@pytest.mark.parametrize("alg", [1, 2])
+def test_tf32_form_error_against_exact_projection(ctx, oracle_lib, alg):
+    """TF32 products (10 fraction bits, 8x finer than BF16) with FP32
+    accumulation: error within 1.01x of the oracle's, output within 2.5e-3 of
+    the oracle's (the BF16 form's 2e-2 scaled by the ratio of unit roundoffs)."""
+    _form_check(ctx, oracle_lib, alg, ps.PREC_TF32, ratio=1.01, close=2.5e-3)
+
+
 def _form_check(ctx, oracle_lib, alg, prec, ratio, close):
     n, k, p, q, seed = 4096, 100, 10, 1, 1
     Vr, lam = si.make_problem("decay", n)

@@ -422,11 +422,63 @@ def test_sym_pass_tensor_core_unsupported(ctx):
     with pytest.raises(ps.PsdprojError) as ei:
         ctx.sym_pass(A2, X2, Y2, prec=ps.PREC_BF16)   # m > 128
     assert ei.value.code == 7
-    X3 = ps.tall_empty(200, 8)
-    Y3 = ps.tall_empty(200, 8)
-    with pytest.raises(ps.PsdprojError) as ei:
-        ctx.sym_pass(A2, X3, Y3, prec=ps.PREC_TF32)    # A-pass form not provided
-    assert ei.value.code == 7
+    for prec in (ps.PREC_TF32, ps.PREC_BF16X3):
+        with pytest.raises(ps.PsdprojError) as ei:
+            ctx.sym_pass(A2, X2, Y2, prec=prec)          # m > 128
+        assert ei.value.code == 7
+
+
+def _tf32(x):
+    # FP32 -> TF32 by rounding to nearest, ties away from zero: add half of the
+    # last kept place to the magnitude bits, then clear the 13 dropped bits
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def test_tf32_rounding_helper():
+    one_ulp = 2.0 ** -10                       # TF32 keeps 10 fraction bits
+    x = np.array([1.0, 1.0 + one_ulp / 2, -(1.0 + one_ulp / 2), 1.0 + one_ulp / 4,
+                  1.0 + 0.75 * one_ulp, 3.0 * 2.0 ** -130], dtype=np.float32)
+    want = np.array([1.0, 1.0 + one_ulp, -(1.0 + one_ulp), 1.0, 1.0 + one_ulp, 3.0 * 2.0 ** -130])
+    assert np.array_equal(_tf32(x).astype(np.float64), want)
+
+
+@pytest.mark.parametrize("n", [1, 65, 257, 1000, 4099])
+@pytest.mark.parametrize("m", [1, 50, 110, 128])
+def test_sym_pass_tf32_tensor_cores(ctx, oracle_lib, n, m):
+    # full TF32 image of A (mirrored from the upper triangle) and TF32 copy of
+    # X, both rounded to nearest with ties away; products exact in FP32,
+    # accumulation in FP32
+    A = _sym_A(n, seed=n + 11 * m)
+    rng = np.random.default_rng(m + 5)
+    X = rng.standard_normal((n, m)).astype(np.float32)
+    Y = ps.tall_empty(n, m, "cuda", ld=-(-n // 4) * 4)
+    shift = torch.tensor([0.25], dtype=torch.float64, device="cuda")
+    ctx.sym_pass(_padded_A(A), _tall_from_np(X, ld=n + 2), Y, shift=shift, prec=ps.PREC_TF32)
+    assert ctx.sync_status() == 0
+    At, Xt = _tf32(A).astype(np.float64), _tf32(X).astype(np.float64)
+    ref = oracle_lib.sym_mul(At, Xt) + 0.25 * X.astype(np.float64)
+    bound = np.abs(At) @ np.abs(Xt) + 0.25 * np.abs(X)
+    assert np.all(np.abs(_np(Y) - ref) <= 8 * np.sqrt(n) * EPS32 * bound + 1e-30)
+
+
+def test_sym_pass_tf32_lower_triangle_and_strides(ctx, oracle_lib):
+    n, m = 777, 33
+    A = _sym_A(n, seed=8)
+    Ap = _sym_A(n, seed=8, poison=True)
+    X = np.random.default_rng(9).standard_normal((n, m)).astype(np.float32)
+    Y1 = ps.tall_empty(n, m, "cuda", ld=n + 3)   # ld not a multiple of 4: scalar atomics
+    Y2 = ps.tall_empty(n, m, "cuda", ld=n + 1)
+    ctx.sym_pass(torch.from_numpy(A).cuda(), _tall_from_np(X), Y1, prec=ps.PREC_TF32)   # lda = 777
+    ctx.sym_pass(_padded_A(Ap), _tall_from_np(X), Y2, prec=ps.PREC_TF32)
+    assert ctx.sync_status() == 0
+    y1, y2 = _np(Y1), _np(Y2)
+    assert np.all(np.isfinite(y2))
+    At, Xt = _tf32(A).astype(np.float64), _tf32(X).astype(np.float64)
+    ref = oracle_lib.sym_mul(At, Xt)
+    bound = np.abs(At) @ np.abs(Xt)
+    for y in (y1, y2):
+        assert np.all(np.abs(y - ref) <= 8 * np.sqrt(n) * EPS32 * bound)
 
 
 @pytest.mark.parametrize("n", [1, 65, 257, 1000, 4099])
