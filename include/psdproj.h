@@ -136,21 +136,24 @@ uint64_t psdproj_kernel_launches(void);
  * dP may be NULL only with out_mode FACTOR.  dW (n x (k+p), column-major)
  * may be NULL; its columns beyond r+ are zero.  d_rank (device int, may be
  * NULL) receives r+, the number of positive eigenvalues of Q^T A Q.
- * opts may be NULL (defaults).  With opts->prec = PSDPROJ_PREC_BF16 (needs
- * k+p <= 128) the call first packs A's block upper triangle into the
+ * opts may be NULL (defaults).  With opts->prec = PSDPROJ_PREC_BF16 the
+ * call first packs A's block upper triangle into the
  * context's BF16 image (256 x 64 tiles stored contiguously, about n^2 + 128 n
  * bytes; kept for later calls) and every product with A, the power
  * iterations of psdproj_alg2 included, reads that image on the tensor cores
  * or CUDA cores with FP32 accumulation.  opts->prec = PSDPROJ_PREC_BF16X3
- * (also k+p <= 128) packs a second image of the residual A - bf16(A) (twice
+ * packs a second image of the residual A - bf16(A) (twice
  * the memory) and computes every product with A as A_hi X_hi + A_hi X_lo +
  * A_lo X_hi on the tensor cores (about 16 significant bits per product);
  * its power iterations run on the CUDA cores in FP32.  opts->prec =
- * PSDPROJ_PREC_TF32 (also k+p <= 128) packs a TF32 image of the full
+ * PSDPROJ_PREC_TF32 packs a TF32 image of the full
  * symmetric matrix (lower triangle mirrored from the upper one; about
  * 4 n^2 bytes) and computes every product with A from it on the tensor cores
  * (10 fraction bits per operand, products exact in FP32); its power
- * iterations also run in FP32. */
+ * iterations also run in FP32.  In the tensor-core forms a sketch wider than
+ * 128 columns (k+p > 128) is multiplied in column slices of 128, one pass
+ * over the image each, and with syrk_prec BF16X3 such a P = W W^T is written
+ * by the FP32 kernel. */
 int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                  int k, int p, int q, uint64_t seed,
                  float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
@@ -175,10 +178,16 @@ int psdproj_alg2(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
 /* A batch of independent projections (the many-small-matrices workload):
  * one descriptor per problem, each with its own A, sizes, seed, algorithm
  * and outputs (device pointers, meanings as in psdproj_alg1 /
- * psdproj_alg2).  The context's workspace is sized once for the largest
- * problem of the batch and the problems run in order on the context's
- * stream; the call returns the first argument error (nothing runs then)
- * or the first launch error.  opts applies to every problem. */
+ * psdproj_alg2).  The problems are spread over up to S helper streams of
+ * the context (S = psdproj_set_batch_streams, default 8), each with its own
+ * workspace: longest-processing-time-first assignment on the cost n^2 x
+ * (passes over A), largest problems issued first.  The helper streams start
+ * after the work already queued on the context's stream and the context's
+ * stream waits for all of them, so the call is asynchronous on that stream
+ * like the others; device errors of any problem land in the context's status
+ * word.  With S = 1 the problems run in order on the context's stream.  The
+ * call returns the first argument error (nothing runs then) or the first
+ * launch error.  opts applies to every problem. */
 typedef struct psdproj_problem {
     const float *dA;     /* n x n FP32 row-major, upper triangle read       */
     int64_t n, lda;
@@ -196,6 +205,68 @@ typedef struct psdproj_problem {
 } psdproj_problem;
 int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
                     const psdproj_opts *opts);
+
+/* Number of helper streams psdproj_batched spreads a batch over (1..16,
+ * default 8; 1 = the context's own stream only).  Each helper holds its own
+ * workspace, sized for the largest problem it has run. */
+int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams);
+
+/* ---- request server (the served workload) --------------------------------
+ * Independent projections submitted by any host thread and run by `workers`
+ * threads, each with its own context and CUDA stream on `device`.  A request
+ * holds device pointers the caller owns until psdproj_server_wait reports it
+ * done.  Admission is first come, first served under a device-memory budget:
+ * the request at the head of the queue starts when its footprint
+ * (footprint_bytes, or when 0 the bytes of its A, P and W) fits under
+ * admit_bytes together with the admitted requests not yet finished; later
+ * requests wait behind it.  Each request's status is its own: the worker
+ * reads and clears its context's device status word after the request.  Not
+ * thread-safe against psdproj_server_destroy. */
+typedef struct psdproj_server psdproj_server;
+typedef struct psdproj_request {
+    const float *dA;     /* n x n FP32 row-major, upper triangle read         */
+    int64_t n, lda;
+    int k, p, q;
+    int algorithm;       /* 1: psdproj_alg1 (Alg. 2), 2: psdproj_alg2 (Alg. 3) */
+    uint64_t seed;
+    double alpha_in;     /* Alg. 3 only; <= 0: estimate by min_eig              */
+    double *d_alpha_out; /* Alg. 3 only, may be NULL                            */
+    int *d_info;         /* Alg. 3 only, may be NULL                            */
+    float *dP;           /* may be NULL with out_mode FACTOR                    */
+    int64_t ldp;
+    float *dW;           /* may be NULL                                         */
+    int64_t ldw;
+    int *d_rank;         /* may be NULL                                         */
+    int64_t footprint_bytes; /* device bytes held while admitted; 0: A + P + W  */
+} psdproj_request;
+typedef struct psdproj_server_stats {
+    uint64_t submitted, completed, failed;
+    int64_t queued;              /* waiting for admission                     */
+    int64_t running;             /* admitted, not finished                    */
+    int64_t inflight_bytes;      /* footprints of the admitted, unfinished    */
+    int64_t inflight_peak_bytes; /* largest inflight_bytes seen               */
+    int64_t admit_bytes;
+} psdproj_server_stats;
+/* opts (may be NULL) applies to every request.  EINVAL: workers outside
+ * 1..64, admit_bytes 0 or bad opts. */
+int psdproj_server_create(psdproj_server **srv, int device, int workers, size_t admit_bytes,
+                          const psdproj_opts *opts);
+/* Queue a request (never blocks on the device).  *ticket identifies it.
+ * EINVAL: bad sizes, algorithm or pointers (as psdproj_alg1/2 would report);
+ * ETOOLARGE: its footprint exceeds admit_bytes. */
+int psdproj_server_submit(psdproj_server *srv, const psdproj_request *req, uint64_t *ticket);
+/* Wait up to timeout_s seconds (0: poll) for a request.  PSDPROJ_OK: done;
+ * *status = its result (PSDPROJ_OK or the error of the call or of the
+ * device), *latency_ms = submit to completion; the ticket is then released.
+ * ETIMEOUT: not done yet; EINVAL: unknown or already collected ticket. */
+int psdproj_server_wait(psdproj_server *srv, uint64_t ticket, double timeout_s, int *status,
+                        double *latency_ms);
+/* Wait up to timeout_s seconds until nothing is queued or running (ETIMEOUT
+ * otherwise). */
+int psdproj_server_drain(psdproj_server *srv, double timeout_s);
+int psdproj_server_get_stats(psdproj_server *srv, psdproj_server_stats *stats);
+/* Requests not yet admitted are dropped; admitted ones finish first. */
+int psdproj_server_destroy(psdproj_server *srv);
 
 /* Host-buffer forms of the two calls: hA, hP, hW, h_rank are HOST pointers
  * (pinned memory recommended).  The call copies A to a context-owned device
@@ -229,12 +300,12 @@ int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream,
  * (ldx, ldy >= n); dY is overwritten.  prec PSDPROJ_PREC_FP32: CUDA cores,
  * A read once.  PSDPROJ_PREC_BF16: A's block upper triangle is first packed
  * into the context's BF16 image (4 bytes read, 2 written per entry), which
- * the tensor-core pass then reads; requires m <= 128.  PSDPROJ_PREC_BF16X3:
- * a second image holds bf16(A - A_hi) and three tensor-core passes add
- * A_hi X_hi + A_hi X_lo + A_lo X_hi into dY (m <= 128).  PSDPROJ_PREC_TF32:
- * A's upper triangle is mirrored into a full TF32 image (4 bytes written per
- * entry of the n x n matrix) and one tensor-core pass reads it (m <= 128).
- * m > 128 on the tensor cores returns ENOTSUP. */
+ * the tensor-core pass then reads.  PSDPROJ_PREC_BF16X3: a second image
+ * holds bf16(A - A_hi) and three tensor-core passes add A_hi X_hi +
+ * A_hi X_lo + A_lo X_hi into dY.  PSDPROJ_PREC_TF32: A's upper triangle is
+ * mirrored into a full TF32 image (4 bytes written per entry of the n x n
+ * matrix) and one tensor-core pass reads it.  The tensor-core passes take
+ * 128 columns at a time: wider X runs as column slices. */
 int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
                      const float *dX, int64_t ldx, int m, const double *d_shift,
                      float *dY, int64_t ldy, int prec);

@@ -51,6 +51,18 @@ class Problem(ctypes.Structure):
                 ("dW", ctypes.c_void_p), ("ldw", ctypes.c_int64), ("d_rank", ctypes.c_void_p)]
 
 
+class Request(ctypes.Structure):
+    """psdproj_request: one request to a psdproj_server."""
+    _fields_ = Problem._fields_ + [("footprint_bytes", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    """psdproj_server_stats."""
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("inflight_bytes", ctypes.c_int64),
+                ("inflight_peak_bytes", ctypes.c_int64), ("admit_bytes", ctypes.c_int64)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _i64 = ctypes.c_int64
@@ -77,6 +89,7 @@ def _load():
         "psdproj_alg1": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, _P, _i64, _P, _i64,
                                 _P, ctypes.POINTER(Opts)]),
         "psdproj_batched": (_int, [_P, _int, _P, _P]),
+        "psdproj_set_batch_streams": (_int, [_P, _int]),
         "psdproj_alg2": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, ctypes.c_double,
                                 _P, _P, _P, _i64, _P, _i64, _P, ctypes.POINTER(Opts)]),
         "psdproj_alg1_host": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, _P, _i64, _P,
@@ -94,6 +107,13 @@ def _load():
         "psdproj_syrk": (_int, [_P, _P, _i64, _i64, _int, _P, _P, _i64, _int, _int]),
         "psdproj_min_eig": (_int, [_P, _P, _i64, _i64, _int, _u64, _P, _P, _P]),
         "psdproj_min_eig_noalloc": (_int, [_P, _i64, _i64, _int, _u64, _P, _P, _P, _P]),
+        "psdproj_server_create": (_int, [ctypes.POINTER(_P), _int, _int, ctypes.c_size_t, ctypes.POINTER(Opts)]),
+        "psdproj_server_submit": (_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(_u64)]),
+        "psdproj_server_wait": (_int, [_P, _u64, ctypes.c_double, ctypes.POINTER(_int),
+                                       ctypes.POINTER(ctypes.c_double)]),
+        "psdproj_server_drain": (_int, [_P, ctypes.c_double]),
+        "psdproj_server_get_stats": (_int, [_P, ctypes.POINTER(ServerStats)]),
+        "psdproj_server_destroy": (_int, [_P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -210,6 +230,9 @@ class Context:
         _check(_load().psdproj_batched(self.h, len(problems), ctypes.byref(arr),
                                        ctypes.byref(opts) if opts else None), "psdproj_batched")
 
+    def set_batch_streams(self, streams: int):
+        _check(_load().psdproj_set_batch_streams(self.h, streams), "psdproj_set_batch_streams")
+
     def alg1_host(self, A, k, p, q, seed, P=None, W=None, opts: Opts | None = None):
         """Host tensors (CPU, pinned recommended); returns r+."""
         n = A.shape[0]
@@ -274,3 +297,57 @@ class Context:
         n, lda = _sq(A)
         _check(_load().psdproj_min_eig(self.h, _ptr(A), n, lda, N, seed, _ptr(alpha),
                                        _ptr(sigma1), _ptr(sigma2)), "min_eig")
+
+
+class Server:
+    """A psdproj_server: requests run by `workers` threads, each with its own
+    context and stream, admitted under `admit_bytes` of device memory."""
+
+    def __init__(self, device: int = 0, workers: int = 4, admit_bytes: int = 1 << 34,
+                 opts: Opts | None = None):
+        h = ctypes.c_void_p()
+        _check(_load().psdproj_server_create(ctypes.byref(h), device, workers, admit_bytes,
+                                             ctypes.byref(opts) if opts else None), "psdproj_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, A, k, p, q, seed, algorithm=1, P=None, W=None, rank=None, alpha_in=0.0,
+               alpha_out=None, info=None, footprint_bytes=0) -> int:
+        n, lda = _sq(A)
+        r = Request(_ptr(A), n, lda, k, p, q, algorithm, seed, float(alpha_in), _ptr(alpha_out), _ptr(info),
+                    _ptr(P), P.stride(0) if P is not None else n,
+                    _ptr(W), _tall(W, "W")[2] if W is not None else n, _ptr(rank), footprint_bytes)
+        t = _u64()
+        _check(_load().psdproj_server_submit(self.h, ctypes.byref(r), ctypes.byref(t)), "psdproj_server_submit")
+        self._keep[t.value] = (A, P, W, rank, alpha_out, info)   # tensors stay alive until collected
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = 60.0):
+        """(status, latency_ms) when done, None on timeout."""
+        st, lat = _int(), ctypes.c_double()
+        rc = _load().psdproj_server_wait(self.h, ticket, timeout, ctypes.byref(st), ctypes.byref(lat))
+        if rc == 5:
+            return None
+        _check(rc, "psdproj_server_wait")
+        self._keep.pop(ticket, None)
+        return st.value, lat.value
+
+    def drain(self, timeout: float = 600.0):
+        _check(_load().psdproj_server_drain(self.h, timeout), "psdproj_server_drain")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(_load().psdproj_server_get_stats(self.h, ctypes.byref(st)), "psdproj_server_get_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _load().psdproj_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

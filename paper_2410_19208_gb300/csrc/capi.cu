@@ -11,6 +11,8 @@
 #include <cstdlib>
 #include <atomic>
 #include <cstring>
+#include <vector>
+#include <algorithm>
 #include <new>
 
 #include "ctx.h"
@@ -230,19 +232,29 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
         return PSDPROJ_OK;
     }
     psd_workspace &ws = ctx->ws;
-    if (prec == PSDPROJ_PREC_TF32) {
-        PSD_KL(launch_sym_pass_tf32(ctx->stream, ctx->persist_sms, reinterpret_cast<const float *>(ctx->Ab), n,
-                                    X, ldx, m, d_shift, Y, ldy, ws.Xf, ws.ld, ctx->d_status), 2);
-        return PSDPROJ_OK;
-    }
-    if (prec != PSDPROJ_PREC_BF16 && prec != PSDPROJ_PREC_BF16X3) return PSDPROJ_ENOTSUP;
-    PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, X, ldx, m, d_shift, Y, ldy,
-                              ws.Xhi, ws.ld, ctx->d_status, 0, 0), 2);
-    if (prec == PSDPROJ_PREC_BF16X3) {
-        PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, X, ldx, m, nullptr, Y, ldy,
-                                  ws.Xlo, ws.ld, ctx->d_status, 1, 1), 2);
-        PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab_lo, n, X, ldx, m, nullptr, Y, ldy,
-                                  ws.Xhi, ws.ld, ctx->d_status, 0, 1), 2);
+    if (prec != PSDPROJ_PREC_TF32 && prec != PSDPROJ_PREC_BF16 && prec != PSDPROJ_PREC_BF16X3)
+        return PSDPROJ_ENOTSUP;
+    // the tensor-core passes take up to 128 columns (M = 128 rows of X^T):
+    // wider sketches run as column slices, one pass over the image each
+    for (int c0 = 0; c0 < m; c0 += 128) {
+        const int mc = m - c0 < 128 ? m - c0 : 128;
+        const float *Xc = X + (int64_t)c0 * ldx;
+        float *Yc = Y + (int64_t)c0 * ldy;
+        if (prec == PSDPROJ_PREC_TF32) {
+            PSD_KL(launch_sym_pass_tf32(ctx->stream, ctx->persist_sms, reinterpret_cast<const float *>(ctx->Ab), n,
+                                        Xc, ldx, mc, d_shift, Yc, ldy, ws.Xf + (int64_t)c0 * ws.ld, ws.ld,
+                                        ctx->d_status), 2);
+            continue;
+        }
+        uint16_t *Xhi = ws.Xhi + (int64_t)c0 * ws.ld, *Xlo = ws.Xlo + (int64_t)c0 * ws.ld;
+        PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, Xc, ldx, mc, d_shift, Yc, ldy,
+                                  Xhi, ws.ld, ctx->d_status, 0, 0), 2);
+        if (prec == PSDPROJ_PREC_BF16X3) {
+            PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, Xc, ldx, mc, nullptr, Yc, ldy,
+                                      Xlo, ws.ld, ctx->d_status, 1, 1), 2);
+            PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab_lo, n, Xc, ldx, mc, nullptr, Yc, ldy,
+                                      Xhi, ws.ld, ctx->d_status, 0, 1), 2);
+        }
     }
     return PSDPROJ_OK;
 }
@@ -294,7 +306,6 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     const double *shift = nullptr;
     const bool bf16 = opts.prec == PSDPROJ_PREC_BF16;
     const bool tc = opts.prec != PSDPROJ_PREC_FP32;
-    if (tc && m > 128) return PSDPROJ_ENOTSUP;
     // the tensor-core forms read A once here and their image(s) in every later pass
     if (tc) PSD_TRY(pack_image(ctx, dA, n, lda, opts.prec));
     if (scaled) {
@@ -357,7 +368,9 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     if (opts.out_mode != PSDPROJ_OUT_FACTOR) {
         stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
         const int upper = opts.out_mode == PSDPROJ_OUT_UPPER;
-        if (opts.syrk_prec == PSDPROJ_PREC_FP32)
+        // the tensor-core SYRK takes up to 128 columns of W; wider factors
+        // are written by the FP32 kernel (at least as accurate)
+        if (opts.syrk_prec == PSDPROJ_PREC_FP32 || m > 128)
             PSD_KL(launch_syrk_simt(s, Wd, ldwd, n, m, rk, dP, ldp, upper), 1);
         else
             PSD_KL(launch_syrk_tc(s, ctx->persist_sms, Wd, ldwd, n, m, rk, dP, ldp, upper, ws.Xhi,
@@ -477,7 +490,7 @@ int psdproj_destroy(psdproj_ctx *ctx)
     free_workspace(ctx->ws);
     if (ctx->timing.created)
         for (int i = 0; i < 2 * PSD_MAX_TIMED; ++i) cudaEventDestroy(ctx->timing.ev[i]);
-    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_status && ctx->owns_status) cudaFree(ctx->d_status);
     if (ctx->d_misc) cudaFree(ctx->d_misc);
     if (ctx->d_misc_f) cudaFree(ctx->d_misc_f);
     if (ctx->dA_stage) cudaFree(ctx->dA_stage);
@@ -485,7 +498,20 @@ int psdproj_destroy(psdproj_ctx *ctx)
     if (ctx->dW_stage) cudaFree(ctx->dW_stage);
     if (ctx->Ab) cudaFree(ctx->Ab);
     if (ctx->Ab_lo) cudaFree(ctx->Ab_lo);
+    for (int i = 0; i < PSD_MAX_LANES; ++i) {
+        if (ctx->lane[i]) psdproj_destroy(ctx->lane[i]);
+        if (ctx->lane_ev[i]) cudaEventDestroy(ctx->lane_ev[i]);
+    }
+    if (ctx->lane_ev[PSD_MAX_LANES]) cudaEventDestroy(ctx->lane_ev[PSD_MAX_LANES]);
+    if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
+    return PSDPROJ_OK;
+}
+
+int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams)
+{
+    if (!ctx || streams < 1 || streams > PSD_MAX_LANES) return PSDPROJ_EINVAL;
+    ctx->batch_streams = streams;
     return PSDPROJ_OK;
 }
 
@@ -520,7 +546,11 @@ const char *psdproj_status_string(int s)
 
 size_t psdproj_workspace_bytes(const psdproj_ctx *ctx)
 {
-    return ctx ? ctx->ws.bytes + ctx->Ab_bytes + ctx->Ab_lo_bytes : 0;
+    if (!ctx) return 0;
+    size_t b = ctx->ws.bytes + ctx->Ab_bytes + ctx->Ab_lo_bytes;
+    for (int i = 0; i < PSD_MAX_LANES; ++i)
+        if (ctx->lane[i]) b += psdproj_workspace_bytes(ctx->lane[i]);
+    return b;
 }
 
 int psdproj_timing_enable(psdproj_ctx *ctx, int on)
@@ -573,6 +603,35 @@ int psdproj_alg2(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int 
                           ldp, dW, ldw, d_rank, opts);
 }
 
+// Lane j of a batch: a helper context on its own non-blocking stream that
+// shares ctx's device status word; created on first use with its events.
+int ensure_lane(psdproj_ctx *ctx, int j)
+{
+    if (ctx->lane[j]) return PSDPROJ_OK;
+    if (!ctx->lane_ev[PSD_MAX_LANES])
+        PSD_CK(cudaEventCreateWithFlags(&ctx->lane_ev[PSD_MAX_LANES], cudaEventDisableTiming));
+    if (!ctx->lane_ev[j]) PSD_CK(cudaEventCreateWithFlags(&ctx->lane_ev[j], cudaEventDisableTiming));
+    psdproj_ctx *c = new (std::nothrow) psdproj_ctx();
+    if (!c) return PSDPROJ_ENOMEM;
+    c->device = ctx->device;
+    c->sm_count = ctx->sm_count;
+    c->persist_sms = ctx->persist_sms;
+    c->batch_streams = 1;
+    c->owns_status = false;
+    c->d_status = ctx->d_status;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) c->owns_stream = true;
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_misc, 64);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_misc_f, 64);
+    if (e == cudaSuccess) e = cudaMemset(c->d_misc, 0, 64);
+    if (e != cudaSuccess) {
+        psdproj_destroy(c);
+        return cuda_status(e);
+    }
+    ctx->lane[j] = c;
+    return PSDPROJ_OK;
+}
+
 int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
                     const psdproj_opts *opts_in)
 {
@@ -593,15 +652,52 @@ int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
     }
     if (count == 0) return PSDPROJ_OK;
     device_guard g(ctx->device);
-    // one workspace for the whole batch
-    PSD_TRY(psd_ensure_workspace(ctx, nmax, mmax));
+    auto run_one = [&](psdproj_ctx *c, const psdproj_problem &pb) {
+        return run_projection(c, pb.dA, pb.n, pb.lda, pb.k, pb.p, pb.q, pb.seed, pb.algorithm == 2, pb.alpha_in,
+                              pb.d_alpha_out, pb.d_info, pb.dP, pb.ldp, pb.dW, pb.ldw, pb.d_rank, &opts);
+    };
+    const int S = count < ctx->batch_streams ? count : ctx->batch_streams;
+    if (S <= 1) {
+        // one workspace for the whole batch, problems one after another
+        PSD_TRY(psd_ensure_workspace(ctx, nmax, mmax));
+        for (int i = 0; i < count; ++i) PSD_TRY(run_one(ctx, probs[i]));
+        return PSDPROJ_OK;
+    }
+    // Grouped: the problems are spread over S lanes (own stream and workspace)
+    // by longest-processing-time-first on the cost n^2 (2q + 2 + [alg 2] 22),
+    // issued largest first so the long ones start early; the lanes fork from
+    // and join back to the context's stream.
+    for (int j = 0; j < S; ++j) PSD_TRY(ensure_lane(ctx, j));
+    std::vector<int> order(count), lane_of(count);
+    std::vector<double> cost(count), load(S, 0.0);
     for (int i = 0; i < count; ++i) {
         const psdproj_problem &pb = probs[i];
-        PSD_TRY(run_projection(ctx, pb.dA, pb.n, pb.lda, pb.k, pb.p, pb.q, pb.seed, pb.algorithm == 2,
-                               pb.alpha_in, pb.d_alpha_out, pb.d_info, pb.dP, pb.ldp, pb.dW, pb.ldw,
-                               pb.d_rank, &opts));
+        order[i] = i;
+        cost[i] = (double)pb.n * (double)pb.n * (2.0 * pb.q + 2.0 + (pb.algorithm == 2 ? 2.0 * (opts.N + 1) : 0.0));
     }
-    return PSDPROJ_OK;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    for (int i : order) {
+        int best = 0;
+        for (int j = 1; j < S; ++j)
+            if (load[j] < load[best]) best = j;
+        lane_of[i] = best;
+        load[best] += cost[i];
+    }
+    cudaEvent_t fork = ctx->lane_ev[PSD_MAX_LANES];
+    PSD_CK(cudaEventRecord(fork, ctx->stream));
+    for (int j = 0; j < S; ++j) PSD_CK(cudaStreamWaitEvent(ctx->lane[j]->stream, fork, 0));
+    int rc = PSDPROJ_OK;
+    for (int i : order) {
+        rc = run_one(ctx->lane[lane_of[i]], probs[i]);
+        if (rc != PSDPROJ_OK) break;
+    }
+    // join every lane back, also after an error, so that the context's stream
+    // orders after all the work the batch issued
+    for (int j = 0; j < S; ++j) {
+        cudaEventRecord(ctx->lane_ev[j], ctx->lane[j]->stream);
+        cudaStreamWaitEvent(ctx->stream, ctx->lane_ev[j], 0);
+    }
+    return rc;
 }
 
 int psdproj_alg1_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda, int k, int p,
@@ -635,7 +731,6 @@ int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, 
     if (!ctx || !dA || !dX || !dY || n < 1 || m < 1 || lda < n || ldx < n || ldy < n)
         return PSDPROJ_EINVAL;
     if (prec < PSDPROJ_PREC_FP32 || prec > PSDPROJ_PREC_BF16X3) return PSDPROJ_EINVAL;
-    if (prec != PSDPROJ_PREC_FP32 && m > 128) return PSDPROJ_ENOTSUP;
     device_guard g(ctx->device);
     if (prec == PSDPROJ_PREC_FP32) return sym_pass(ctx, dA, n, lda, dX, ldx, m, d_shift, dY, ldy, prec);
     PSD_TRY(psd_ensure_workspace(ctx, n, m));

@@ -90,6 +90,8 @@ struct psd_timing {
     int kind[PSD_MAX_TIMED];
 };
 
+constexpr int PSD_MAX_LANES = 16;     // most streams a batch is spread over
+
 struct psdproj_ctx {
     int device = 0;
     psd_timing timing;
@@ -109,6 +111,14 @@ struct psdproj_ctx {
     size_t Ab_bytes = 0;
     uint16_t *Ab_lo = nullptr;   // low parts (split-BF16 form)
     size_t Ab_lo_bytes = 0;
+    // psdproj_batched: helper contexts ("lanes"), each with its own stream,
+    // workspace and images, sharing this context's status word; the batch
+    // forks from `stream` to the lanes and joins back by events
+    int batch_streams = 8;
+    psdproj_ctx *lane[PSD_MAX_LANES] = {};
+    cudaEvent_t lane_ev[PSD_MAX_LANES + 1] = {};
+    bool owns_status = true;     // false for a lane (the status word is its parent's)
+    bool owns_stream = false;    // true for a lane (stream created by the library)
 };
 
 // Make sure the workspace holds n rows x m columns; may synchronise the

@@ -10,20 +10,20 @@
 
 namespace tc {
 
-// cuTensorMapEncodeTiled, fetched from the driver once per translation unit
-// (no link-time dependency on libcuda); nullptr when unavailable
+// cuTensorMapEncodeTiled, fetched from the driver once (no link-time
+// dependency on libcuda; the function-local static makes the first lookup
+// thread-safe); nullptr when unavailable
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess)
             return nullptr;
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
     return fn;
 }
 

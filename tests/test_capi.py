@@ -71,3 +71,39 @@ def test_batched_descriptor_layout_and_rejection(lib):
     assert ps.Problem.seed.offset == 40 and ps.Problem.d_rank.offset == 104
     # no context: argument error before any device work
     assert lib.psdproj_batched(None, 1, None, None) == 1
+
+
+def test_struct_layouts_match_the_c_header(tmp_path):
+    # the ctypes mirrors against offsetof / sizeof from the header itself
+    import subprocess
+    import paper_2410_19208_gb300 as ps
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "psdproj.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu\\n", sizeof(psdproj_problem), sizeof(psdproj_request),\n'
+        "         offsetof(psdproj_request, footprint_bytes), sizeof(psdproj_server_stats));\n"
+        '  printf("%zu %zu\\n", offsetof(psdproj_server_stats, inflight_peak_bytes), sizeof(psdproj_opts));\n'
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    got = [int(x) for x in out]
+    want = [ctypes.sizeof(ps.Problem), ctypes.sizeof(ps.Request), ps.Request.footprint_bytes.offset,
+            ctypes.sizeof(ps.ServerStats), ps.ServerStats.inflight_peak_bytes.offset, ctypes.sizeof(ps.Opts)]
+    assert got == want
+
+
+def test_server_rejects_bad_arguments_without_a_gpu(lib):
+    import paper_2410_19208_gb300 as ps
+    h = ctypes.c_void_p()
+    assert lib.psdproj_server_create(None, 0, 4, 1 << 30, None) == 1
+    assert lib.psdproj_server_create(ctypes.byref(h), 0, 0, 1 << 30, None) == 1      # no workers
+    assert lib.psdproj_server_create(ctypes.byref(h), 0, 4, 0, None) == 1            # no budget
+    t = ctypes.c_uint64()
+    assert lib.psdproj_server_submit(None, None, ctypes.byref(t)) == 1
+    assert lib.psdproj_server_wait(None, 1, 0.0, None, None) == 1
+    assert lib.psdproj_server_drain(None, 0.0) == 1
+    st = ps.ServerStats()
+    assert lib.psdproj_server_get_stats(None, ctypes.byref(st)) == 1
+    assert lib.psdproj_server_destroy(None) == 0

@@ -264,6 +264,22 @@ def test_tf32_form_error_against_exact_projection(ctx, oracle_lib, alg):
     _form_check(ctx, oracle_lib, alg, ps.PREC_TF32, ratio=1.01, close=2.5e-3)
 
 
+@pytest.mark.parametrize("prec,close", [(ps.PREC_BF16, 2e-2), (ps.PREC_TF32, 2.5e-3), (ps.PREC_BF16X3, 1e-3)])
+def test_wide_sketch_in_tensor_core_forms(ctx, oracle_lib, prec, close):
+    # k + p = 160 > 128: column slices in the passes, FP32 SYRK for P
+    n, k, p, q, seed = 1000, 150, 10, 1, 3
+    Vr, lam = si.make_problem("small", n)
+    A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
+    for alg in (1, 2):
+        got = _run(ctx, A32, k, p, q, seed, alg=alg,
+                   opts=ps.make_opts(prec=prec, syrk_prec=ps.PREC_BF16X3))
+        if alg == 1:
+            Wo = oracle_lib.alg1(A32.astype(np.float64), k, p, q, seed)["W"]
+        else:
+            Wo = oracle_lib.alg2(A32.astype(np.float64), k, p, q, seed, N=10)["W_red"]
+        assert _rel(got["P"], Wo @ Wo.T) <= close
+
+
 def _form_check(ctx, oracle_lib, alg, prec, ratio, close):
     n, k, p, q, seed = 4096, 100, 10, 1, 1
     Vr, lam = si.make_problem("decay", n)
@@ -312,6 +328,42 @@ def test_batched_matches_single_calls_and_oracle(ctx, oracle_lib):
         assert _rel(P, Pref) <= TOL
 
 
+@pytest.mark.parametrize("prec", [ps.PREC_FP32, ps.PREC_BF16])
+def test_batched_streams_agree_and_order_on_the_context_stream(ctx, prec):
+    # the batch recipe at sides log-uniform in [64, 2048]: one helper stream,
+    # four and sixteen (more than the problems) give the same projections,
+    # and a read queued on the context's stream after the call sees them
+    sizes = [int(x) for x in si.log_uniform_sizes(10, 64, 2048, seed=17)]
+    opts = ps.make_opts(prec=prec)
+    results = []
+    for S in (1, 4, 16):
+        ctx.set_batch_streams(S)
+        probs = []
+        for i, n in enumerate(sizes):
+            k, p, q, alg = max(2, min(n // 8, 64)), 8, 1, 1 + (i % 2)
+            Vr, lam = si.make_problem("batch", n, seed_u=200 + i, seed_lam=300 + i)
+            Ad = si.form_A_torch(Vr, lam, "cuda")
+            P = torch.full((n, n), float("nan"), device="cuda")
+            rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+            probs.append(dict(A=Ad, k=k, p=p, q=q, seed=900 + i, algorithm=alg, P=P, rank=rank))
+        torch.cuda.synchronize()
+        ctx.batched(probs, opts=opts)
+        # copies on the context's (torch's current) stream, no host sync first
+        results.append([(pb["P"].cpu().numpy().astype(np.float64), int(pb["rank"].cpu().item()))
+                        for pb in probs])
+        assert ctx.sync_status() == 0
+    ctx.set_batch_streams(8)
+    # run to run, only the order of FP32 additions across CTAs differs; in the
+    # BF16 form such a last-bit change of X can move its BF16 rounding by one
+    # BF16 ulp (2^-8 relative), so the runs agree to that form's own accuracy
+    tol = 1e-5 if prec == ps.PREC_FP32 else 2e-3
+    for (P1, r1), (P4, r4), (P16, r16) in zip(*results):
+        assert np.all(np.isfinite(P1))
+        assert r1 == r4 == r16
+        assert _rel(P4, P1) <= tol
+        assert _rel(P16, P1) <= tol
+
+
 def test_batched_rejects_bad_problems_before_running(ctx):
     n = 100
     A = torch.zeros(n, n, device="cuda")
@@ -324,3 +376,103 @@ def test_batched_rejects_bad_problems_before_running(ctx):
     assert ctx.sync_status() == 0
     assert torch.all(P == 7.0)          # nothing ran
     ctx.batched([])                      # an empty batch is a no-op
+
+
+# ----------------------------------------------------------------------------
+# request server (served workload: sides log-uniform, random algorithm)
+# ----------------------------------------------------------------------------
+def _served_requests(count, lo, hi, seed):
+    rng = np.random.default_rng(seed)
+    sizes = [int(x) for x in si.log_uniform_sizes(count, lo, hi, seed=seed)]
+    out = []
+    for i, n in enumerate(sizes):
+        k = int(rng.choice([16, 32, 64, 128]))
+        k = min(k, n - 8)
+        out.append(dict(n=n, k=k, p=8, q=int(rng.integers(0, 2)), alg=int(rng.integers(1, 3)),
+                        seed=4000 + i, mseed=(600 + i, 700 + i)))
+    return out
+
+
+def test_server_matches_direct_calls_and_oracle(ctx, oracle_lib):
+    opts = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3)
+    reqs = _served_requests(16, 256, 1100, seed=21)
+    srv = ps.Server(0, workers=4, admit_bytes=1 << 32, opts=opts)
+    tickets, Ps, As = [], [], []
+    for r in reqs:
+        Vr, lam = si.make_problem("batch", r["n"], seed_u=r["mseed"][0], seed_lam=r["mseed"][1])
+        A = si.form_A_torch(Vr, lam, "cuda")
+        P = torch.full((r["n"], r["n"]), float("nan"), device="cuda")
+        torch.cuda.synchronize()
+        tickets.append(srv.submit(A, r["k"], r["p"], r["q"], r["seed"], algorithm=r["alg"], P=P))
+        Ps.append(P)
+        As.append(A)
+    for t in tickets:
+        res = srv.wait(t, timeout=120.0)
+        assert res is not None and res[0] == 0 and res[1] > 0.0
+    st = srv.stats()
+    assert st["submitted"] == st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["inflight_bytes"] == 0 and st["queued"] == 0
+    srv.close()
+    for i, (r, A, P) in enumerate(zip(reqs, As, Ps)):
+        one = _run(ctx, A.cpu().numpy(), r["k"], r["p"], r["q"], r["seed"], alg=r["alg"], opts=opts)
+        got = P.cpu().numpy().astype(np.float64)
+        # same kernels on another stream: equal to the BF16 form's run-to-run spread
+        assert _rel(got, one["P"]) <= 2e-3
+        if i < 3:
+            A64 = A.cpu().numpy().astype(np.float64)
+            ref = (oracle_lib.alg1(A64, r["k"], r["p"], r["q"], r["seed"])["W"] if r["alg"] == 1
+                   else oracle_lib.alg2(A64, r["k"], r["p"], r["q"], r["seed"])["W_red"])
+            assert _rel(got, ref @ ref.T) <= 2e-2
+
+
+def test_server_admission_bounds_device_memory():
+    # budget for three of the largest requests: the admitted footprint never
+    # exceeds it, everything still completes, first come first served
+    reqs = _served_requests(24, 256, 700, seed=5)
+    foot = [2 * 4 * r["n"] * r["n"] for r in reqs]          # A + P, lda = ldp = n
+    budget = 3 * max(foot)
+    srv = ps.Server(0, workers=6, admit_bytes=budget, opts=ps.make_opts(prec=ps.PREC_FP32))
+    tickets, keep = [], []
+    for r in reqs:
+        Vr, lam = si.make_problem("batch", r["n"], seed_u=r["mseed"][0], seed_lam=r["mseed"][1])
+        A = si.form_A_torch(Vr, lam, "cuda")
+        P = torch.empty(r["n"], r["n"], device="cuda")
+        keep.append((A, P))
+    torch.cuda.synchronize()
+    for r, (A, P) in zip(reqs, keep):
+        tickets.append(srv.submit(A, r["k"], r["p"], r["q"], r["seed"], algorithm=r["alg"], P=P))
+    srv.drain(300.0)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert 0 < st["inflight_peak_bytes"] <= budget
+    assert st["inflight_bytes"] == 0
+    for t in tickets:
+        assert srv.wait(t, 0.0)[0] == 0
+    # a request larger than the whole budget is refused at submit
+    n = 2048
+    A = torch.zeros(n, n, device="cuda")
+    with pytest.raises(ps.PsdprojError) as ei:
+        srv.submit(A, 16, 8, 0, 1, P=torch.empty(n, n, device="cuda"), footprint_bytes=budget + 1)
+    assert ei.value.code == 8
+    # collected or unknown tickets are argument errors
+    with pytest.raises(ps.PsdprojError):
+        srv.wait(tickets[0], 0.0)
+    srv.close()
+
+
+def test_server_charges_a_device_error_to_its_request_only():
+    # one request's A holds a NaN in its upper triangle: that request reports
+    # ENOTFINITE, the others (same worker contexts, before and after) succeed
+    srv = ps.Server(0, workers=2, admit_bytes=1 << 32, opts=ps.make_opts(prec=ps.PREC_FP32))
+    n = 300
+    Vr, lam = si.make_problem("batch", n, seed_u=1, seed_lam=2)
+    A = si.form_A_torch(Vr, lam, "cuda")
+    Abad = A.clone()
+    Abad[3, 7] = float("nan")
+    Ps = [torch.empty(n, n, device="cuda") for _ in range(5)]
+    torch.cuda.synchronize()
+    ts = [srv.submit(Abad if i == 2 else A, 16, 8, 1, 10 + i, algorithm=1 + (i % 2), P=Ps[i]) for i in range(5)]
+    res = [srv.wait(t, 120.0) for t in ts]
+    assert [r[0] for r in res] == [0, 0, 3, 0, 0]
+    assert srv.stats()["failed"] == 1
+    srv.close()

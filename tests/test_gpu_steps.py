@@ -415,17 +415,27 @@ def test_sym_pass_bf16_any_lda(ctx, oracle_lib):
     assert np.all(np.abs(_np(Y) - ref) <= 8 * np.sqrt(n) * EPS32 * bound + 1e-30)
 
 
-def test_sym_pass_tensor_core_unsupported(ctx):
-    A2 = torch.zeros(200, 200, device="cuda")
-    X2 = ps.tall_empty(200, 129)
-    Y2 = ps.tall_empty(200, 129)
-    with pytest.raises(ps.PsdprojError) as ei:
-        ctx.sym_pass(A2, X2, Y2, prec=ps.PREC_BF16)   # m > 128
-    assert ei.value.code == 7
-    for prec in (ps.PREC_TF32, ps.PREC_BF16X3):
-        with pytest.raises(ps.PsdprojError) as ei:
-            ctx.sym_pass(A2, X2, Y2, prec=prec)          # m > 128
-        assert ei.value.code == 7
+@pytest.mark.parametrize("prec", [ps.PREC_BF16, ps.PREC_BF16X3, ps.PREC_TF32])
+@pytest.mark.parametrize("m", [129, 256])
+def test_sym_pass_tensor_core_wide_sketch(ctx, oracle_lib, prec, m):
+    # more than 128 columns: column slices of 128, one pass each
+    n = 700
+    A = _sym_A(n, seed=m + prec)
+    X = np.random.default_rng(m).standard_normal((n, m)).astype(np.float32)
+    Y = ps.tall_empty(n, m, "cuda", ld=704)
+    shift = torch.tensor([-0.5], dtype=torch.float64, device="cuda")
+    ctx.sym_pass(_padded_A(A), _tall_from_np(X), Y, shift=shift, prec=prec)
+    assert ctx.sync_status() == 0
+    if prec == ps.PREC_BF16:
+        Ar, Xr, extra = _bf16(A), _bf16(X), 0.0
+    elif prec == ps.PREC_TF32:
+        Ar, Xr, extra = _tf32(A), _tf32(X), 0.0
+    else:
+        Ar, Xr, extra = A, X, 4 * 2.0 ** -16
+    Ar, Xr = Ar.astype(np.float64), Xr.astype(np.float64)
+    ref = oracle_lib.sym_mul(Ar, Xr) - 0.5 * X.astype(np.float64)
+    bound = np.abs(Ar) @ np.abs(Xr) + 0.5 * np.abs(X)
+    assert np.all(np.abs(_np(Y) - ref) <= (extra + 8 * np.sqrt(n) * EPS32) * bound + 1e-30)
 
 
 def _tf32(x):
