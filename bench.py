@@ -65,8 +65,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison")
     ap.add_argument("--no-forms", action="store_true", help="skip the TF32 / split-BF16 comparison")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batched"],
-                    help="batched: 512 matrices, sides log-uniform in [64, 2048], through psdproj_batched")
+    ap.add_argument("--workload", default="headline", choices=["headline", "batched", "serve"],
+                    help="batched: 512 matrices, sides log-uniform in [64, 2048], through psdproj_batched; "
+                         "serve: Poisson arrivals through psdproj_server")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests per second")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-pool", type=int, default=48, help="distinct matrices the requests draw from")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--streams", type=int, default=4,
                     help="independent contexts / CUDA streams the projections of the headline run on")
@@ -296,6 +301,120 @@ def run_batched(args):
     print(json.dumps(line))
 
 
+def run_serve(args):
+    """The served workload: requests arrive as a Poisson process (rate
+    --serve-rate, --serve-seconds long), each a matrix of side log-uniform in
+    [256, 8192] (batch recipe; drawn from a pool of --serve-pool matrices
+    generated on the device beforehand), k in {16, 32, 64, 128}, p = 8,
+    q in {0, 1} and a random algorithm, submitted to a psdproj_server with a
+    120 GB admission budget.  Latency runs from submit to completion (the
+    server's clock); throughput = completed requests / (last completion -
+    first submit)."""
+    import numpy as np
+    import torch
+    import paper_2410_19208_gb300 as ps
+    import synth_inputs as si
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prec = args.prec if args.prec != "auto" else "bf16"
+    syrk_prec = args.syrk_prec if args.syrk_prec != "auto" else ("fp32" if prec == "fp32" else "bf16x3")
+    opts = ps.make_opts(prec=PREC_NAMES[prec], syrk_prec=PREC_NAMES[syrk_prec])
+    rng = np.random.default_rng(SEED)
+    sizes = [int(x) for x in si.log_uniform_sizes(args.serve_pool, 256, 8192, seed=13)]
+    pool = []
+    for i, n in enumerate(sizes):
+        Vr, lam = si.make_problem("batch", n, seed_u=3000 + i, seed_lam=7000 + i)
+        pool.append(si.form_A_torch(Vr, lam, dev))
+    free_P = [[] for _ in sizes]
+    torch.cuda.synchronize()
+    srv = ps.Server(0, workers=args.serve_workers, admit_bytes=120 * 10 ** 9, opts=opts)
+
+    def draw(i):
+        n = sizes[i]
+        k = int(rng.choice([16, 32, 64, 128]))
+        return dict(k=min(k, n - 8), q=int(rng.integers(0, 2)), alg=int(rng.integers(1, 3)),
+                    seed=int(rng.integers(1, 1 << 62)))
+
+    # warm-up: one request per pool matrix (workspaces and images sized)
+    t_w = []
+    for i in range(len(sizes)):
+        P = torch.empty(sizes[i], sizes[i], device=dev)
+        d = draw(i)
+        t_w.append((srv.submit(pool[i], d["k"], 8, d["q"], d["seed"], algorithm=d["alg"], P=P), i, P))
+    for t, i, P in t_w:
+        st_ = srv.wait(t, 600.0)
+        if st_ is None or st_[0] != 0:
+            raise SystemExit(f"warm-up request failed: {st_}")
+        free_P[i].append(P)
+
+    l0 = ps.lib().psdproj_kernel_launches()
+    inflight, params, failures = {}, {}, []
+    lat, statuses = [], []
+    n_req = int(args.serve_rate * args.serve_seconds)
+    gaps = rng.exponential(1.0 / args.serve_rate, n_req)
+    arrivals = np.cumsum(gaps)
+    pick = rng.integers(0, len(sizes), n_req)
+    late = 0
+
+    def reap(block=False):
+        for t in list(inflight):
+            r = srv.wait(t, 600.0 if block else 0.0)
+            if r is None:
+                continue
+            i, P = inflight.pop(t)
+            free_P[i].append(P)
+            statuses.append(r[0])
+            lat.append(r[1])
+            if r[0] != 0 and len(failures) < 8:
+                failures.append({"status": ps.STATUS.get(r[0], r[0]), "n,pool,k,q,alg,seed": params[t]})
+            params.pop(t, None)
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    for j in range(n_req):
+        target = t0 + arrivals[j]
+        while time.perf_counter() < target:
+            pass
+        if time.perf_counter() - target > 0.005:
+            late += 1
+        i = int(pick[j])
+        if not free_P[i]:
+            reap()
+        P = free_P[i].pop() if free_P[i] else torch.empty(sizes[i], sizes[i], device=dev)
+        d = draw(i)
+        t = srv.submit(pool[i], d["k"], 8, d["q"], d["seed"], algorithm=d["alg"], P=P)
+        inflight[t] = (i, P)
+        params[t] = (sizes[i], i, d["k"], d["q"], d["alg"], d["seed"])
+        if j % 16 == 0:
+            reap()
+    reap(block=True)
+    t1 = time.perf_counter()
+    clocks = sampler.stop()
+    st = srv.stats()
+    launches = int(ps.lib().psdproj_kernel_launches() - l0)
+    srv.close()
+    lat_s = sorted(lat)
+
+    def pq(q_):
+        return lat_s[min(len(lat_s) - 1, int(round(q_ * (len(lat_s) - 1))))]
+
+    line = {"metric": "served PSD projections/s (Poisson arrivals, sides log-uniform 256..8192)",
+            "value": len(lat) / (t1 - t0), "unit": "requests/s", "n_gpus": 1, "steps": n_req, "warmup": len(sizes),
+            "ms_per_step": 1e3 * (t1 - t0) / max(1, len(lat)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE_NAMES[prec], "data": "synthetic",
+            "config": {"workload": f"psdproj_server, {args.serve_workers} workers, offered {args.serve_rate:g} req/s "
+                                   f"for {args.serve_seconds:g} s, k in {{16,32,64,128}}, p = 8, q in {{0,1}}, "
+                                   "random algorithm, 120 GB admission budget",
+                       "pool_matrices": len(sizes), "mean_n2": float(np.mean(np.square(sizes)))},
+            "offered_rate": args.serve_rate, "requests": n_req, "completed": len(lat),
+            "failed": int(sum(1 for x in statuses if x != 0)), "failures": failures,
+            "arrivals_late_over_5ms": late,
+            "latency_ms": {"p50": pq(0.5), "p90": pq(0.9), "p99": pq(0.99), "max": lat_s[-1]},
+            "server": st, "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -303,6 +422,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "serve":
+        run_serve(args)
         return
 
     import numpy as np

@@ -69,6 +69,10 @@ extern "C" {
 #define PSDPROJ_EIG_JACOBI   1 /* parallel cyclic Jacobi only                     */
 #define PSDPROJ_EIG_TRIDIAG  2 /* tridiagonal solver only (failure: ENOCONV)      */
 
+/* Test matrix Omega of the randomized range finder (Alg. 1) */
+#define PSDPROJ_SKETCH_GAUSS 0 /* i.i.d. N(0,1) (psdproj_gaussian, stream 0)       */
+#define PSDPROJ_SKETCH_SRHT  1 /* subsampled randomized Hadamard (psdproj_srht)     */
+
 typedef struct psdproj_ctx psdproj_ctx;
 
 typedef struct psdproj_opts {
@@ -77,7 +81,8 @@ typedef struct psdproj_opts {
     int N;           /* iterations of Alg. 4 inside Alg. 5 (default 10)          */
     int out_mode;    /* PSDPROJ_OUT_* (default FULL)                             */
     int eig;         /* PSDPROJ_EIG_* (default AUTO)                             */
-    int reserved[3]; /* must be zero                                             */
+    int sketch;      /* PSDPROJ_SKETCH_* test matrix of Alg. 1 (default GAUSS)   */
+    int reserved[2]; /* must be zero                                             */
 } psdproj_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -211,6 +216,11 @@ int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
  * workspace, sized for the largest problem it has run. */
 int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams);
 
+/* The cudaError_t behind the last PSDPROJ_ECUDA / ENOMEM / ENOTSUP that a
+ * call on this host thread returned (0 if none), and in *line (may be NULL)
+ * the line of the library's C-ABI source where it was seen. */
+int psdproj_last_cuda_error(int *line);
+
 /* ---- request server (the served workload) --------------------------------
  * Independent projections submitted by any host thread and run by `workers`
  * threads, each with its own context and CUDA stream on `device`.  A request
@@ -246,6 +256,10 @@ typedef struct psdproj_server_stats {
     int64_t inflight_bytes;      /* footprints of the admitted, unfinished    */
     int64_t inflight_peak_bytes; /* largest inflight_bytes seen               */
     int64_t admit_bytes;
+    int last_error_status;       /* status of the last failed request         */
+    int last_error_cuda;         /* its psdproj_last_cuda_error (0: none)     */
+    int last_error_line;
+    int reserved;
 } psdproj_server_stats;
 /* opts (may be NULL) applies to every request.  EINVAL: workers outside
  * 1..64, admit_bytes 0 or bad opts. */
@@ -293,6 +307,18 @@ int psdproj_alg2_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda,
  * Requires n >= 1, 1 <= m, ldx >= n. */
 int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream,
                      int64_t n, int m, float *dX, int64_t ldx);
+
+/* Structured test matrix, the real counterpart of the subsampled randomized
+ * Fourier transform that the footnote to Alg. 1 names: with N the smallest
+ * power of two >= n,
+ *   dX[c*ldx + i] = d_i * (-1)^popcount(i & s_c),   i < n, c < m,
+ * i.e. rows 0..n-1 of D H_N S: d_i = -1 exactly when bit 0 of output word 0
+ * of Philox4x32-10 (counter (i, 0, 17, 0), key = seed) is 1; s_c is the
+ * first value of word 0 of Philox(counter (c, t, 16, 0)) mod N, t = 0, 1, ...,
+ * not taken by a column before c (so the m columns of H_N are distinct).
+ * Entries are exactly +-1 (exact in every operand format).  Requires
+ * 1 <= m <= min(n, 256), ldx >= n. */
+int psdproj_srht(psdproj_ctx *ctx, uint64_t seed, int64_t n, int m, float *dX, int64_t ldx);
 
 /* Symmetric pass over A (Alg. 1 products, and Z = A Q of Alg. 2 line 2):
  *   dY = A dX + shift dX,   shift = (d_shift ? *d_shift : 0),

@@ -10,6 +10,8 @@ Functions (each docstring cites the passage it follows):
 
 * ``philox4x32_10``, ``gauss``, ``omega``  - the test-matrix generator (Alg. 1
   ``randn``; Philox4x32-10 of Salmon et al. SC'11 as our reading).
+* ``omega_srht``                          - the structured test matrix of the
+  footnote to Alg. 1 (subsampled randomized Hadamard transform reading).
 * ``jacobi_eig``, ``exact_proj``          - Thm 1 (X+ = U D+ U^T).
 * ``orth``, ``range_finder``              - Alg. 1 (QR 'econ').
 * ``alg1``                                 - Alg. 2 (the C ABI's "Algorithm 1").
@@ -147,6 +149,38 @@ def omega(seed: int, n: int, m: int, stream: int = 0) -> np.ndarray:
     out = np.empty((n, m), dtype=np.float64)
     _load().orc_omega(seed, n, m, stream, _dp(out))
     return out
+
+
+def omega_srht(seed: int, n: int, m: int) -> np.ndarray:
+    """Structured test matrix for Alg. 1.  The footnote to Alg. 1 names the
+    subsampled randomized Fourier transform; the reading taken is its real
+    counterpart, the subsampled randomized Hadamard transform: with N the
+    smallest power of two >= n, Omega = rows 0..n-1 of D H_N S, where
+      D = diag(d), d_i = -1 when bit 0 of word 0 of Philox(counter (i, 0, 17, 0))
+          is set, else +1;
+      H_N = the Sylvester-Hadamard matrix, H_N[i, j] = (-1)^popcount(i & j);
+      S = the columns s_0..s_{m-1}: s_c is the first word-0 value of
+          Philox(counter (c, t, 16, 0)) mod N, t = 0, 1, ..., not already
+          taken by an earlier column.
+    Key = (seed low 32 bits, seed high 32 bits).  Entries are +-1."""
+    N = 1
+    while N < n:
+        N *= 2
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    picks = []
+    for c in range(m):
+        t = 0
+        while True:
+            x = philox4x32_10((c, t, 16, 0), key)[0] % N
+            if x not in picks:
+                picks.append(x)
+                break
+            t += 1
+    d = np.array([-1.0 if philox4x32_10((i, 0, 17, 0), key)[0] & 1 else 1.0 for i in range(n)])
+    i = np.arange(n, dtype=np.uint64)[:, None]
+    s = np.array(picks, dtype=np.uint64)[None, :]
+    H = 1.0 - 2.0 * (np.bitwise_count(i & s) % 2)
+    return d[:, None] * H
 
 
 # --------------------------------------------------------------------------

@@ -26,6 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpsdproj.so")
 PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
 OUT_FULL, OUT_UPPER, OUT_FACTOR = 0, 1, 2
 EIG_AUTO, EIG_JACOBI, EIG_TRIDIAG = 0, 1, 2
+SKETCH_GAUSS, SKETCH_SRHT = 0, 1
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTFINITE", 4: "ENOCONV", 5: "ETIMEOUT",
           6: "ECUDA", 7: "ENOTSUP", 8: "ETOOLARGE"}
 
@@ -38,7 +39,8 @@ class PsdprojError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("syrk_prec", ctypes.c_int), ("N", ctypes.c_int),
-                ("out_mode", ctypes.c_int), ("eig", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("out_mode", ctypes.c_int), ("eig", ctypes.c_int), ("sketch", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Problem(ctypes.Structure):
@@ -60,7 +62,9 @@ class ServerStats(ctypes.Structure):
     """psdproj_server_stats."""
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
                 ("queued", ctypes.c_int64), ("running", ctypes.c_int64), ("inflight_bytes", ctypes.c_int64),
-                ("inflight_peak_bytes", ctypes.c_int64), ("admit_bytes", ctypes.c_int64)]
+                ("inflight_peak_bytes", ctypes.c_int64), ("admit_bytes", ctypes.c_int64),
+                ("last_error_status", ctypes.c_int), ("last_error_cuda", ctypes.c_int),
+                ("last_error_line", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 _lib = None
@@ -98,6 +102,7 @@ def _load():
                                      ctypes.c_double, _P, _P, _i64, _P, _i64, _P,
                                      ctypes.POINTER(Opts)]),
         "psdproj_gaussian": (_int, [_P, _u64, ctypes.c_uint32, _i64, _int, _P, _i64]),
+        "psdproj_srht": (_int, [_P, _u64, _i64, _int, _P, _i64]),
         "psdproj_sym_pass": (_int, [_P, _P, _i64, _i64, _P, _i64, _int, _P, _P, _i64, _int]),
         "psdproj_cholqr2": (_int, [_P, _P, _i64, _i64, _int, _P, _i64, _P]),
         "psdproj_core": (_int, [_P, _P, _i64, _P, _i64, _i64, _int, _P]),
@@ -114,6 +119,7 @@ def _load():
         "psdproj_server_drain": (_int, [_P, ctypes.c_double]),
         "psdproj_server_get_stats": (_int, [_P, ctypes.POINTER(ServerStats)]),
         "psdproj_server_destroy": (_int, [_P]),
+        "psdproj_last_cuda_error": (_int, [ctypes.POINTER(_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -156,10 +162,10 @@ def tall_empty(n: int, m: int, device="cuda", ld: int | None = None):
 
 
 def make_opts(prec=PREC_FP32, syrk_prec=PREC_FP32, N=10, out_mode=OUT_FULL,
-              eig=EIG_AUTO) -> Opts:
+              eig=EIG_AUTO, sketch=SKETCH_GAUSS) -> Opts:
     o = Opts()
     _load().psdproj_default_opts(ctypes.byref(o))
-    o.prec, o.syrk_prec, o.N, o.out_mode, o.eig = prec, syrk_prec, N, out_mode, eig
+    o.prec, o.syrk_prec, o.N, o.out_mode, o.eig, o.sketch = prec, syrk_prec, N, out_mode, eig, sketch
     return o
 
 
@@ -259,6 +265,10 @@ class Context:
     def gaussian(self, seed, stream_id, X):
         n, m, ld = _tall(X)
         _check(_load().psdproj_gaussian(self.h, seed, stream_id, n, m, _ptr(X), ld), "gaussian")
+
+    def srht(self, seed, X):
+        n, m, ld = _tall(X)
+        _check(_load().psdproj_srht(self.h, seed, n, m, _ptr(X), ld), "psdproj_srht")
 
     def sym_pass(self, A, X, Y, shift=None, prec=PREC_FP32):
         n, lda = _sq(A)

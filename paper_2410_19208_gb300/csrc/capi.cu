@@ -19,9 +19,14 @@
 
 namespace {
 
-int cuda_status(cudaError_t e)
+// the last CUDA error this host thread turned into a status, and where
+thread_local int t_last_cuda = 0, t_last_line = 0;
+
+int cuda_status(cudaError_t e, int line = 0)
 {
     if (e == cudaSuccess) return PSDPROJ_OK;
+    t_last_cuda = (int)e;
+    t_last_line = line;
     if (e == cudaErrorMemoryAllocation) return PSDPROJ_ENOMEM;
     if (e == cudaErrorNotSupported) return PSDPROJ_ENOTSUP;
     return PSDPROJ_ECUDA;
@@ -30,7 +35,7 @@ int cuda_status(cudaError_t e)
 #define PSD_CK(expr)                              \
     do {                                          \
         cudaError_t _e = (expr);                  \
-        if (_e != cudaSuccess) return cuda_status(_e); \
+        if (_e != cudaSuccess) return cuda_status(_e, __LINE__); \
     } while (0)
 
 #define PSD_TRY(expr)                 \
@@ -62,7 +67,7 @@ std::atomic<uint64_t> g_launches{0};
 #define PSD_KL(expr, nk)                                   \
     do {                                                   \
         cudaError_t _e = (expr);                           \
-        if (_e != cudaSuccess) return cuda_status(_e);     \
+        if (_e != cudaSuccess) return cuda_status(_e, __LINE__); \
         g_launches.fetch_add((uint64_t)(nk));              \
     } while (0)
 
@@ -141,6 +146,7 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
         lay.scal = reinterpret_cast<double *>(take(sizeof(double) * 16));
         lay.counter = reinterpret_cast<unsigned *>(take(sizeof(unsigned) * 16));
         lay.ints = reinterpret_cast<int *>(take(sizeof(int) * 16));
+        lay.picks = reinterpret_cast<int *>(take(sizeof(int) * PSD_MAX_M));
         return off;
     };
     const size_t total = carve(nullptr);
@@ -150,7 +156,7 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
     }
     void *base = nullptr;
     cudaError_t e = cudaMalloc(&base, total);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e, __LINE__);
     carve(static_cast<char *>(base));
     ws = lay;
     ws.base = base;
@@ -160,7 +166,7 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
     ws.ld = ld;
     // zero everything once: padded rows / columns of the tall buffers stay 0
     e = cudaMemsetAsync(base, 0, total, ctx->stream);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e, __LINE__);
     return PSDPROJ_OK;
 }
 
@@ -178,6 +184,7 @@ int check_opts(const psdproj_opts *o)
     if (o->out_mode < PSDPROJ_OUT_FULL || o->out_mode > PSDPROJ_OUT_FACTOR) return PSDPROJ_EINVAL;
     if (o->N < 0 || o->N > 10000) return PSDPROJ_EINVAL;
     if (o->eig < PSDPROJ_EIG_AUTO || o->eig > PSDPROJ_EIG_TRIDIAG) return PSDPROJ_EINVAL;
+    if (o->sketch != PSDPROJ_SKETCH_GAUSS && o->sketch != PSDPROJ_SKETCH_SRHT) return PSDPROJ_EINVAL;
     return PSDPROJ_OK;
 }
 
@@ -196,7 +203,7 @@ int alloc_image(uint16_t **buf, size_t *cap, size_t bytes, cudaStream_t s)
         *cap = 0;
     }
     cudaError_t e = cudaMalloc(buf, bytes);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e, __LINE__);
     *cap = bytes;
     return PSDPROJ_OK;
 }
@@ -338,7 +345,10 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     // Omega (Alg. 1), then Y = (A + shift I) Omega
     {
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
-        PSD_KL(launch_gaussian(s, seed, 0u, n, m, lpad, ws.ld, ws.Om, ws.ld), 1);
+        if (opts.sketch == PSDPROJ_SKETCH_SRHT)
+            PSD_KL(launch_srht(s, seed, n, m, lpad, ws.ld, ws.picks, ctx->d_status, ws.Om, ws.ld), 2);
+        else
+            PSD_KL(launch_gaussian(s, seed, 0u, n, m, lpad, ws.ld, ws.Om, ws.ld), 1);
     }
     PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, shift, ws.Y, ws.ld, opts.prec));
     PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
@@ -390,7 +400,7 @@ int ensure_stage(float **buf, size_t *cap, size_t bytes, cudaStream_t s)
         *cap = 0;
     }
     cudaError_t e = cudaMalloc(buf, bytes);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e, __LINE__);
     *cap = bytes;
     return PSDPROJ_OK;
 }
@@ -469,7 +479,7 @@ int psdproj_create(psdproj_ctx **out, int device, void *stream)
     if (e == cudaSuccess) e = cudaMemset(c->d_misc, 0, 64);
     if (e != cudaSuccess) {
         psdproj_destroy(c);
-        return cuda_status(e);
+        return cuda_status(e, __LINE__);
     }
     *out = c;
     return PSDPROJ_OK;
@@ -520,12 +530,18 @@ int psdproj_sync_status(psdproj_ctx *ctx)
     if (!ctx) return PSDPROJ_EINVAL;
     device_guard g(ctx->device);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e, __LINE__);
     int st = 0;
     e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_status(e);
+    if (e != cudaSuccess) return cuda_status(e, __LINE__);
     if (st) cudaMemset(ctx->d_status, 0, sizeof(int));
     return st;
+}
+
+int psdproj_last_cuda_error(int *line)
+{
+    if (line) *line = t_last_line;
+    return t_last_cuda;
 }
 
 const char *psdproj_status_string(int s)
@@ -626,7 +642,7 @@ int ensure_lane(psdproj_ctx *ctx, int j)
     if (e == cudaSuccess) e = cudaMemset(c->d_misc, 0, 64);
     if (e != cudaSuccess) {
         psdproj_destroy(c);
-        return cuda_status(e);
+        return cuda_status(e, __LINE__);
     }
     ctx->lane[j] = c;
     return PSDPROJ_OK;
@@ -722,6 +738,15 @@ int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream, int64_t n
     if (!ctx || !dX || n < 1 || m < 1 || ldx < n) return PSDPROJ_EINVAL;
     device_guard g(ctx->device);
     PSD_KL(launch_gaussian(ctx->stream, seed, stream, n, m, m, n, dX, ldx), 1);
+    return PSDPROJ_OK;
+}
+
+int psdproj_srht(psdproj_ctx *ctx, uint64_t seed, int64_t n, int m, float *dX, int64_t ldx)
+{
+    if (!ctx || !dX || n < 1 || m < 1 || m > PSD_MAX_M || m > n || ldx < n) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    PSD_KL(launch_srht(ctx->stream, seed, n, m, m, n, ctx->ws.picks, ctx->d_status, dX, ldx), 2);
     return PSDPROJ_OK;
 }
 

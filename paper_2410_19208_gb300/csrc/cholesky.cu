@@ -428,7 +428,11 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv,
     if (first_pass && sm_path) {
         const size_t smem = sizeof(df) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1);
         auto kern = cholesky_kernel<df, SMEM_M / 32>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // the attribute is process-wide: always the largest size (m = SMEM_M),
+        // so that threads launching for different m never undercut each other
+        constexpr size_t smem_max = sizeof(df) * ((size_t)SMEM_M * (SMEM_M + 1) + SMEM_M) +
+                                    sizeof(float) * SMEM_M * (SMEM_M + 1);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
         if (e != cudaSuccess) return e;
         kern<<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, nullptr, nullptr, nullptr, d_status);
     } else if (first_pass) {
@@ -439,7 +443,9 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv,
         if (sm_path) {
             const size_t smem = sizeof(float) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1);
             auto kern = cholesky_kernel<float, SMEM_M / 32>;
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            constexpr size_t smem_max = sizeof(float) * ((size_t)SMEM_M * (SMEM_M + 1) + SMEM_M) +
+                                        sizeof(float) * SMEM_M * (SMEM_M + 1);
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
             if (e != cudaSuccess) return e;
             kern<<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, fs, fs + (size_t)m * m, gRf, d_status);
         } else {

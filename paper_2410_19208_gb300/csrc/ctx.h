@@ -78,6 +78,7 @@ struct psd_workspace {
     double *scal = nullptr;     // 16 doubles
     unsigned *counter = nullptr; // 16 counters
     int *ints = nullptr;         // 16 ints (ranks, info)
+    int *picks = nullptr;        // PSD_MAX_M ints (SRHT column picks)
 };
 
 constexpr int PSD_MAX_TIMED = 4096;
@@ -129,6 +130,12 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m);
 cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, uint32_t stream_id,
                             int64_t n, int m, int mpad, int64_t rows_pad,
                             float *X, int64_t ldx);
+
+// Philox streams of the SRHT test matrix: column picks and row signs
+constexpr uint32_t PSD_SRHT_PICKS = 16u, PSD_SRHT_SIGNS = 17u;
+// SRHT test matrix (see gauss.cu); picks: m ints of device scratch; n >= m.
+cudaError_t launch_srht(cudaStream_t s, uint64_t seed, int64_t n, int m, int mpad, int64_t rows_pad,
+                        int *picks, int *d_status, float *X, int64_t ldx);
 
 cudaError_t launch_sym_pass_simt(cudaStream_t s, const float *A, int64_t n, int64_t lda,
                                  const float *X, int64_t ldx, int m, const double *d_shift,

@@ -230,8 +230,9 @@ cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double 
     if (smem > 200 * 1024) { smem_A = 0; smem = 0; }
     float *gA = scratch;
     float *gV = scratch + matA / sizeof(float);
+    // process-wide attribute: the largest size this launcher uses (200 KB)
     cudaError_t e = cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         200 * 1024);
     if (e != cudaSuccess) return e;
     eig_kernel<<<1, NT, smem, s>>>(C, m, V, d, gA, gV, smem_A, smem_V, d_status, only_if);
     return cudaGetLastError();

@@ -602,8 +602,10 @@ cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V,
     // three m x (m+1) buffers plus 8 slack rows read (never used) by the
     // edge tiles of the Newton-Schulz products
     const size_t smem = m <= SMEM_M ? sizeof(float) * (3 * (size_t)m + 8) * (m + 1) : 0;
+    // process-wide attribute: the largest size (m = SMEM_M) for every launch
+    constexpr size_t smem_max = sizeof(float) * (3 * (size_t)SMEM_M + 8) * (SMEM_M + 1);
     cudaError_t e = cudaFuncSetAttribute(eig_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)smem_max);
     if (e != cudaSuccess) return e;
     eig_tridiag_kernel<<<1, NT, smem, s>>>(C, m, V, d, scratch, d_fail, d_status_on_fail);
     return cudaGetLastError();

@@ -1,5 +1,6 @@
-// Test matrix of the randomized range finder (Alg. 1, "Omega = randn") and the
-// start vectors of power_iteration (Alg. 4).
+// Test matrix of the randomized range finder (Alg. 1, "Omega = randn"), its
+// structured SRHT alternative, and the start vectors of power_iteration
+// (Alg. 4).
 //
 // Element (i, c) of random stream s is keyed by the Philox4x32-10 counter
 // (i, c, s, 0) with key (seed lo, seed hi) (Salmon, Moraes, Dror, Shaw, SC'11),
@@ -71,7 +72,81 @@ __global__ void gaussian_kernel(uint64_t seed, uint32_t stream_id, int64_t n, in
     }
 }
 
+// SRHT test matrix (the real counterpart of the subsampled randomized
+// Fourier transform named in the footnote to Alg. 1): with N the power of two
+// >= n, Omega = D H_N S restricted to rows 0..n-1, i.e.
+//   Omega[i, c] = d_i (-1)^popcount(i & s_c),
+// D = diag(d) random signs, H_N the Sylvester-Hadamard matrix (entries +-1),
+// S the columns s_0..s_{m-1} of H_N drawn without replacement.
+//   d_i = -1 when bit 0 of word 0 of Philox(i, 0, PSD_SRHT_SIGNS, 0) is 1;
+//   s_c = the first draw (word 0 of Philox(c, t, PSD_SRHT_PICKS, 0)) mod N,
+//         t = 0, 1, ..., not already taken by a column before c.
+// The picks run in one thread (m <= 256 draws, each checked against the
+// earlier ones); an exhausted bound on t sets PSDPROJ_ETIMEOUT.
+__global__ void srht_pick_kernel(uint64_t seed, int m, uint32_t nmask, int *__restrict__ picks,
+                                 int *d_status)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    for (int c = 0; c < m; ++c) {
+        int got = -1;
+        for (uint32_t t = 0; t < (1u << 20) && got < 0; ++t) {
+            uint32_t w0, w1;
+            philox4x32_10((uint32_t)c, t, PSD_SRHT_PICKS, 0u, k0, k1, w0, w1);
+            const int x = (int)(w0 & nmask);
+            bool dup = false;
+            for (int j = 0; j < c && !dup; ++j) dup = picks[j] == x;
+            if (!dup) got = x;
+        }
+        if (got < 0) {
+            psd_set_status(d_status, PSDPROJ_ETIMEOUT);
+            got = 0;
+        }
+        picks[c] = got;
+    }
+}
+
+__global__ void srht_fill_kernel(uint64_t seed, int64_t n, int m, int mpad, int64_t rows_pad,
+                                 const int *__restrict__ picks, float *__restrict__ X, int64_t ldx)
+{
+    __shared__ int sp[PSD_MAX_M];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) sp[c] = picks[c];
+    __syncthreads();
+    const uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    const int64_t total = rows_pad * (int64_t)mpad;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / rows_pad);
+        const int64_t i = idx - (int64_t)c * rows_pad;
+        float v = 0.0f;
+        if (i < n && c < m) {
+            uint32_t w0, w1;
+            philox4x32_10((uint32_t)i, 0u, PSD_SRHT_SIGNS, 0u, k0, k1, w0, w1);
+            const int par = (__popc((uint32_t)i & (uint32_t)sp[c]) + (int)(w0 & 1u)) & 1;
+            v = par ? -1.0f : 1.0f;
+        }
+        X[(int64_t)c * ldx + i] = v;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_srht(cudaStream_t s, uint64_t seed, int64_t n, int m, int mpad, int64_t rows_pad,
+                        int *picks, int *d_status, float *X, int64_t ldx)
+{
+    if (m < 1 || m > PSD_MAX_M || n < m || n > (int64_t)1 << 30) return cudaErrorInvalidValue;
+    uint32_t N = 1;
+    while ((int64_t)N < n) N <<= 1;
+    srht_pick_kernel<<<1, 32, 0, s>>>(seed, m, N - 1, picks, d_status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t total = rows_pad * (int64_t)mpad;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    srht_fill_kernel<<<blocks, 256, 0, s>>>(seed, n, m, mpad, rows_pad, picks, X, ldx);
+    return cudaGetLastError();
+}
 
 // Writes rows [0, rows_pad) x columns [0, mpad); entries with i >= n or
 // c >= m are zero (padding of context-owned buffers).

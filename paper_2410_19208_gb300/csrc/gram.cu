@@ -198,8 +198,9 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
     case 7: gram_partial_sq_kernel<7><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
     case 8: gram_partial_sq_kernel<8><<<nchunk, NT, 0, s>>>(X, ldx, Z, ldz, n, m, mp, gpart); break;
     default:
+        // process-wide attribute: the largest size (m = PSD_MAX_M)
         e = cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+                                 (int)(sizeof(float) * 2 * RS * (size_t)psd_round_up(PSD_MAX_M, 8)));
         if (e != cudaSuccess) return e;
         gram_partial_kernel<<<nchunk, NT, smem, s>>>(X, ldx, Z, ldz, n, m, mp, symmetrize == 1,
                                                      gpart);

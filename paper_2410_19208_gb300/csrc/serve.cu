@@ -80,6 +80,7 @@ struct psdproj_server {
     size_t inflight = 0, inflight_peak = 0;
     int running = 0;
     uint64_t submitted = 0, completed = 0, failed = 0;
+    int last_status = 0, last_cuda = 0, last_line = 0;
     bool stop = false;
 
     // called with mu held: admit from the head of the queue while it fits
@@ -127,8 +128,18 @@ struct psdproj_server {
             // device status: it belongs to this request alone
             cudaError_t e = cudaEventRecord(done_ev[w], streams[w]);
             if (e == cudaSuccess) e = cudaEventSynchronize(done_ev[w]);
+            int cuda_err = 0, cuda_line = 0;
+            if (rc != PSDPROJ_OK) cuda_err = psdproj_last_cuda_error(&cuda_line);
             const int st = psdproj_sync_status(ctx[w]);
-            if (rc == PSDPROJ_OK) rc = (e != cudaSuccess) ? PSDPROJ_ECUDA : st;
+            if (rc == PSDPROJ_OK && e != cudaSuccess) {
+                rc = PSDPROJ_ECUDA;
+                cuda_err = (int)e;
+                cuda_line = -__LINE__;          // negative: a line of this file
+            }
+            if (rc == PSDPROJ_OK && st != PSDPROJ_OK) {
+                rc = st;
+                if (st == PSDPROJ_ECUDA) cuda_err = psdproj_last_cuda_error(&cuda_line);
+            }
             {
                 std::lock_guard<std::mutex> lk(mu);
                 Ticket &t = tickets[id];
@@ -138,7 +149,12 @@ struct psdproj_server {
                 inflight -= t.bytes;
                 --running;
                 ++completed;
-                if (rc != PSDPROJ_OK) ++failed;
+                if (rc != PSDPROJ_OK) {
+                    ++failed;
+                    last_status = rc;
+                    last_cuda = cuda_err;
+                    last_line = cuda_line;
+                }
                 admit();
             }
             cv_done.notify_all();
@@ -265,6 +281,9 @@ int psdproj_server_get_stats(psdproj_server *s, psdproj_server_stats *out)
     out->inflight_bytes = (int64_t)s->inflight;
     out->inflight_peak_bytes = (int64_t)s->inflight_peak;
     out->admit_bytes = (int64_t)s->admit_bytes;
+    out->last_error_status = s->last_status;
+    out->last_error_cuda = s->last_cuda;
+    out->last_error_line = s->last_line;
     return PSDPROJ_OK;
 }
 

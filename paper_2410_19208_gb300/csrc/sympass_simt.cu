@@ -160,8 +160,12 @@ cudaError_t launch_sym_pass_simt(cudaStream_t s, const float *A, int64_t n, int6
     cudaError_t e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(float), 0, (size_t)n * sizeof(float),
                                       (size_t)m, s);
     if (e != cudaSuccess) return e;
+    // process-wide attribute: the largest size (m = PSD_MAX_M) for every launch
+    const int mchunks_max = (PSD_MAX_M + LC - 1) / LC;
+    const size_t smem_max = sizeof(float) * ((size_t)BT * (BT + 1) + 2 * (size_t)BT * (LC + 1) +
+                                             (size_t)BT * mchunks_max * LC);
     e = cudaFuncSetAttribute(sym_pass_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+                             (int)smem_max);
     if (e != cudaSuccess) return e;
     sym_pass_simt_kernel<<<(unsigned)segs, NT, smem, s>>>(A, n, lda, X, ldx, m, mchunks, d_shift,
                                                           Y, ldy, nb);

@@ -541,3 +541,16 @@ def test_syrk_split_bf16_tensor_cores(ctx, n, m, r):
     assert np.array_equal(pu[iu], p[iu])
     if n > 1:
         assert np.all(np.isnan(pu[np.tril_indices(n, -1)]))
+
+
+# ----------------------------------------------------------------------------
+# SRHT test matrix (footnote to Alg. 1): bit-exact against the oracle
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("n,m,seed", [(64, 64, 5), (100, 40, 123456789012345), (1000, 110, 1),
+                                      (777, 256, 2 ** 40 + 3), (20000, 112, 1)])
+def test_srht_matches_oracle_bit_exactly(ctx, oracle_lib, n, m, seed):
+    X = ps.tall_empty(n, m, "cuda", ld=n + 3)
+    ctx.srht(seed, X)
+    assert ctx.sync_status() == 0
+    # integer work (Philox words, picks, popcounts) decides +-1: bit-exact
+    assert np.array_equal(_np(X), oracle_lib.omega_srht(seed, n, m))

@@ -210,6 +210,31 @@ def test_cor3_inequality(oracle_lib):
     assert oracle_lib.eps1(shifted, n // 2, l) < oracle_lib.eps1(sig, n // 2, l)
 
 
+def test_cor3_class_crossover_of_the_two_algorithms(oracle_lib):
+    # the first numerical example of Sec. 4 (Fig. 5): on the Cor. 3 class the
+    # scaled projection (Alg. 3) is no better than Alg. 2 while k <= n/4 and
+    # far better once k > n/4, where Alg. 2 spends its sketch on the beta_1
+    # cluster of negative eigenvalues.  n = 400 instead of 1000 keeps k + p
+    # inside the sketch widths the GPU path takes (<= 256) across the
+    # crossover at n/4 = 100; beta, oversampling 5 and q = 2 as in the example.
+    g = json.load(open(os.path.join(GOLD, "cor3_class.json")))
+    n, (b1, b2, b3, b4), p, q = 400, g["beta"], g["oversampling"], g["q"]
+    Vr = si.householder_vectors(n, 3, 0)
+    lam = si.spectrum_cor3(n, b1, b2, b3, b4)
+    A = si.form_A_numpy(Vr, lam).astype(np.float32).astype(np.float64)
+    xp = np.sqrt(np.sum(np.maximum(lam, 0) ** 2))
+    err = {}
+    for k in (60, 100, 200, 250):
+        w1 = oracle_lib.alg1(A, k, p, q, 1)["W"]
+        w2 = oracle_lib.alg2(A, k, p, q, 1, N=10)["W_red"]
+        err[k] = (np.sqrt(max(oracle_lib.exact_dist2(Vr, lam, w1), 0)) / xp,
+                  np.sqrt(max(oracle_lib.exact_dist2(Vr, lam, w2), 0)) / xp)
+    for k in (60, 100):
+        assert err[k][1] >= 0.98 * err[k][0]
+    for k in (200, 250):
+        assert err[k][1] <= 0.5 * err[k][0]
+
+
 def test_cor1_prop3_frobenius_bounds_mean(oracle_lib):
     Vr, lam, A = _decay_problem(200, 3)
     n, k, p = 200, 15, 5

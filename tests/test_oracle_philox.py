@@ -94,3 +94,53 @@ def test_streams_and_columns_independent(oracle_lib):
         assert abs(r) < 0.1
     r01 = np.corrcoef(a[:, 0], a[:, 1])[0, 1]
     assert abs(r01) < 0.1
+
+
+# ----------------------------------------------------------------------------
+# SRHT test matrix (footnote to Alg. 1)
+# ----------------------------------------------------------------------------
+def test_srht_columns_are_signed_hadamard_columns(oracle_lib):
+    # n = N = 64: Omega = D H_64[:, S] means the products of column 0 with each
+    # column c, H[:, s_0] * H[:, s_c], are columns of H_64 (the Sylvester
+    # matrix is closed under entrywise products) and distinct when the s_c
+    # are; H_64 comes from scipy's Sylvester construction (a library routine)
+    from scipy.linalg import hadamard
+    Om = oracle_lib.omega_srht(5, 64, 12)
+    H = hadamard(64).astype(np.float64)
+    assert set(np.unique(Om)) == {-1.0, 1.0}
+    cols = []
+    for c in range(12):
+        match = [j for j in range(64) if np.array_equal(Om[:, 0] * Om[:, c], H[:, j])]
+        assert len(match) == 1
+        cols.append(match[0])
+    assert cols[0] == 0 and len(set(cols)) == 12
+    # orthogonal columns: Omega^T Omega = N I when n is a power of two
+    assert np.array_equal(Om.T @ Om, 64.0 * np.eye(12))
+
+
+def test_srht_rows_not_a_power_of_two(oracle_lib):
+    # n = 100 -> N = 128: the first 100 rows of the signed, subsampled H_128
+    Om = oracle_lib.omega_srht(123456789012345, 100, 40)
+    assert Om.shape == (100, 40)
+    assert set(np.unique(Om)) == {-1.0, 1.0}
+    # no two columns equal up to sign (distinct columns of H_128 restricted
+    # to 100 rows stay distinct: they differ in a row below 100)
+    G = Om.T @ Om
+    assert np.all(np.abs(G[~np.eye(40, dtype=bool)]) < 100)
+    assert np.all(np.diag(G) == 100)
+    # different seeds give different picks and signs
+    assert not np.array_equal(Om, oracle_lib.omega_srht(123456789012346, 100, 40))
+
+
+def test_srht_sketch_recovers_a_low_rank_psd_matrix(oracle_lib):
+    # rank(A) = 6 <= sketch width 10: range(A Omega) = range(A), so the
+    # projection is A itself (Alg. 2 exact-recovery case) with the SRHT too
+    rng = np.random.default_rng(3)
+    n, r = 90, 6
+    U, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    A = (U * np.linspace(1.0, 4.0, r)) @ U.T
+    Om = oracle_lib.omega_srht(9, n, 10)
+    Q, rank = oracle_lib.range_finder(A, Om, 1)
+    W, rp = oracle_lib.core_project(A, Q)
+    assert rank == r and rp == r
+    assert np.max(np.abs(W @ W.T - A)) < 1e-12
