@@ -472,8 +472,8 @@ def main():
         v = sorted(v)
         return v[min(len(v) - 1, int(round(q_ * (len(v) - 1))))]
 
-    def measure(prec_, syrk_, steps, sample_clocks):
-        opts = ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_])
+    def measure(prec_, syrk_, steps, sample_clocks, alpha_mode=0):
+        opts = ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_], alpha_mode=alpha_mode)
 
         def step(lat=None):
             if lat is not None:
@@ -536,7 +536,7 @@ def main():
         W1 = W.cpu().numpy().astype(np.float64)
         ctx.alg2(A, k, p, q, SEED, alpha_out=alpha_t, P=None, W=W, rank=rank_t,
                  opts=ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_],
-                                   out_mode=ps.OUT_FACTOR))
+                                   out_mode=ps.OUT_FACTOR, alpha_mode=alpha_mode))
         W2 = W.cpu().numpy().astype(np.float64)
         return dict(elapsed_ms=elapsed_ms, lat1=a1, lat2=a2, stages=stages, launches=launches,
                     clocks=clocks, W1=W1, W2=W2, opts=opts)
@@ -766,6 +766,16 @@ def main():
                          "ms_per_step": r["elapsed_ms"] / ks, "streams": 1,
                          "error_vs_exact": {"alg1": err_exact(r["W1"]), "alg2": err_exact(r["W2"])}}
         line["forms"] = forms
+        # variant: Alg. 3 with alpha from the Ritz values of the unshifted
+        # sketch (one extra pass over A instead of the 2(N+1) power-iteration
+        # products), same form as the headline
+        ks = max(2, min(args.steps, 3))
+        r = measure(prec, syrk_prec, ks, False, alpha_mode=1)
+        line["variant_alpha_ritz"] = {
+            "value": 2 * ks * world / (r["elapsed_ms"] / 1e3), "unit": "projections/s",
+            "ms_per_step": r["elapsed_ms"] / ks, "streams": 1,
+            "alg2_ms_p50": pct(r["lat2"], 0.5), "alg2_ms_p50_min_eig": pct(head["lat2"], 0.5),
+            "error_vs_exact": {"alg1": err_exact(r["W1"]), "alg2": err_exact(r["W2"])}}
 
     # ---- end to end through the host-buffer C-ABI call --------------------
     if not args.no_e2e:

@@ -73,6 +73,13 @@ extern "C" {
 #define PSDPROJ_SKETCH_GAUSS 0 /* i.i.d. N(0,1) (psdproj_gaussian, stream 0)       */
 #define PSDPROJ_SKETCH_SRHT  1 /* subsampled randomized Hadamard (psdproj_srht)     */
 
+/* How psdproj_alg2 estimates alpha when alpha_in <= 0 */
+#define PSDPROJ_ALPHA_MINEIG 0 /* Alg. 5 (two power iterations, 2(N+1) products)   */
+#define PSDPROJ_ALPHA_RITZ   1 /* variant: -(most negative Ritz value) of the sketch
+                                  Q0 = orth(A Omega), whose product A Omega is
+                                  reused as the first product of Alg. 3: one
+                                  extra pass over A instead of 2(N+1)          */
+
 typedef struct psdproj_ctx psdproj_ctx;
 
 typedef struct psdproj_opts {
@@ -82,7 +89,8 @@ typedef struct psdproj_opts {
     int out_mode;    /* PSDPROJ_OUT_* (default FULL)                             */
     int eig;         /* PSDPROJ_EIG_* (default AUTO)                             */
     int sketch;      /* PSDPROJ_SKETCH_* test matrix of Alg. 1 (default GAUSS)   */
-    int reserved[2]; /* must be zero                                             */
+    int alpha_mode;  /* PSDPROJ_ALPHA_* estimate of alpha in Alg. 3 (default MINEIG) */
+    int reserved[1]; /* must be zero                                             */
 } psdproj_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -166,7 +174,10 @@ int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
 
 /* Scaled randomized PSD projection (Alg. 3):
  *   alpha = alpha_in if alpha_in > 0, else min_eig(A, N) (Alg. 5, start
- *   vectors from Philox streams 3 and 4 of `seed`);
+ *   vectors from Philox streams 3 and 4 of `seed`), or with
+ *   opts->alpha_mode = PSDPROJ_ALPHA_RITZ the variant
+ *   alpha = -min(eig(Q0^T A Q0)), Q0 = orth(A Omega) (same Omega), whose
+ *   product A Omega then serves as (A + alpha I) Omega - alpha Omega;
  *   Q = orth((A + alpha I)^(2q+1) Omega)  -- the range of B = (A+alpha I)/alpha,
  *   output Q (Q^T A Q)_+ Q^T, which equals the literal
  *   alpha Q V (max(D,1) - I) V^T Q^T with V D V^T = Q^T B Q (Lemma 4).

@@ -27,6 +27,7 @@ PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3
 OUT_FULL, OUT_UPPER, OUT_FACTOR = 0, 1, 2
 EIG_AUTO, EIG_JACOBI, EIG_TRIDIAG = 0, 1, 2
 SKETCH_GAUSS, SKETCH_SRHT = 0, 1
+ALPHA_MINEIG, ALPHA_RITZ = 0, 1
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTFINITE", 4: "ENOCONV", 5: "ETIMEOUT",
           6: "ECUDA", 7: "ENOTSUP", 8: "ETOOLARGE"}
 
@@ -40,7 +41,7 @@ class PsdprojError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("syrk_prec", ctypes.c_int), ("N", ctypes.c_int),
                 ("out_mode", ctypes.c_int), ("eig", ctypes.c_int), ("sketch", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("alpha_mode", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Problem(ctypes.Structure):
@@ -162,10 +163,11 @@ def tall_empty(n: int, m: int, device="cuda", ld: int | None = None):
 
 
 def make_opts(prec=PREC_FP32, syrk_prec=PREC_FP32, N=10, out_mode=OUT_FULL,
-              eig=EIG_AUTO, sketch=SKETCH_GAUSS) -> Opts:
+              eig=EIG_AUTO, sketch=SKETCH_GAUSS, alpha_mode=ALPHA_MINEIG) -> Opts:
     o = Opts()
     _load().psdproj_default_opts(ctypes.byref(o))
-    o.prec, o.syrk_prec, o.N, o.out_mode, o.eig, o.sketch = prec, syrk_prec, N, out_mode, eig, sketch
+    o.prec, o.syrk_prec, o.N, o.out_mode, o.eig = prec, syrk_prec, N, out_mode, eig
+    o.sketch, o.alpha_mode = sketch, alpha_mode
     return o
 
 

@@ -185,6 +185,7 @@ int check_opts(const psdproj_opts *o)
     if (o->N < 0 || o->N > 10000) return PSDPROJ_EINVAL;
     if (o->eig < PSDPROJ_EIG_AUTO || o->eig > PSDPROJ_EIG_TRIDIAG) return PSDPROJ_EINVAL;
     if (o->sketch != PSDPROJ_SKETCH_GAUSS && o->sketch != PSDPROJ_SKETCH_SRHT) return PSDPROJ_EINVAL;
+    if (o->alpha_mode != PSDPROJ_ALPHA_MINEIG && o->alpha_mode != PSDPROJ_ALPHA_RITZ) return PSDPROJ_EINVAL;
     return PSDPROJ_OK;
 }
 
@@ -315,7 +316,9 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     const bool tc = opts.prec != PSDPROJ_PREC_FP32;
     // the tensor-core forms read A once here and their image(s) in every later pass
     if (tc) PSD_TRY(pack_image(ctx, dA, n, lda, opts.prec));
-    if (scaled) {
+    // variant: alpha from the Ritz values of the unshifted sketch (below)
+    const bool ritz = scaled && !(alpha_in > 0.0) && opts.alpha_mode == PSDPROJ_ALPHA_RITZ;
+    if (scaled && !ritz) {
         double *sc = ws.scal;
         if (!(alpha_in > 0.0)) {
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
@@ -350,7 +353,32 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         else
             PSD_KL(launch_gaussian(s, seed, 0u, n, m, lpad, ws.ld, ws.Om, ws.ld), 1);
     }
-    PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, shift, ws.Y, ws.ld, opts.prec));
+    if (ritz) {
+        // Alg. 3's first product without the shift, A Omega, does not depend
+        // on alpha: its sketch Q0 = orth(A Omega) gives Ritz values
+        // eig(Q0^T A Q0) whose most negative one sets alpha; then
+        // (A + alpha I) Omega = A Omega + alpha Omega needs no further pass.
+        double *sc = ws.scal;
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec));
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.W, ws.ld, opts.prec));
+        {
+            stage_scope st(ctx, PSDPROJ_STAGE_CORE);
+            PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.W, ws.ld, n, m, ws.gpart, ws.C, 2), 2);
+        }
+        {
+            stage_scope st(ctx, PSDPROJ_STAGE_EIG);
+            PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, opts.eig,
+                              ws.ints + IN_EIGFAIL), opts.eig == PSDPROJ_EIG_AUTO ? 2 : 1);
+        }
+        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
+        PSD_KL(launch_ritz_alpha(s, ws.d, m, d_alpha_out ? d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
+                                 d_info ? d_info : ws.ints + IN_INFO), 1);
+        PSD_KL(launch_add_shift(s, ws.Y, ws.Om, n, m, ws.ld, sc + SC_SHIFT), 1);
+        shift = sc + SC_SHIFT;
+    } else {
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, shift, ws.Y, ws.ld, opts.prec));
+    }
     PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
     for (int t = 0; t < 2 * q; ++t) {
         PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, shift, ws.Y, ws.ld, opts.prec));

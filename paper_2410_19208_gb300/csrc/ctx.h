@@ -131,6 +131,13 @@ cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, uint32_t stream_id,
                             int64_t n, int m, int mpad, int64_t rows_pad,
                             float *X, int64_t ldx);
 
+// alpha = -min(d) (Ritz values of an unshifted sketch's core), shift and
+// info as launch_alpha_finish; Y += shift X (n x m, leading dimension ld)
+cudaError_t launch_ritz_alpha(cudaStream_t s, const double *d, int m, double *d_alpha, double *d_shift,
+                              int *d_info);
+cudaError_t launch_add_shift(cudaStream_t s, float *Y, const float *X, int64_t n, int m, int64_t ld,
+                             const double *d_shift);
+
 // Philox streams of the SRHT test matrix: column picks and row signs
 constexpr uint32_t PSD_SRHT_PICKS = 16u, PSD_SRHT_SIGNS = 17u;
 // SRHT test matrix (see gauss.cu); picks: m ints of device scratch; n >= m.

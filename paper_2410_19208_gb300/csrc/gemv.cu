@@ -421,7 +421,56 @@ __global__ void alpha_finish_kernel(const double *d_s1, const double *d_s2, doub
     if (d_info) *d_info = ok ? 0 : 1;
 }
 
+// Variant of Alg. 5 (alpha from the sketch's Ritz values): alpha = -min_i d_i
+// over the eigenvalues d of the core C = Q^T A Q of an unshifted sketch
+// (Ritz values lie in [lambda_min(A), lambda_max(A)], so this estimates
+// |lambda_min| from inside); outputs as alpha_finish_kernel.
+__global__ void ritz_alpha_kernel(const double *d, int m, double *d_alpha, double *d_shift, int *d_info)
+{
+    double lo = 0.0;
+    bool finite = true;
+    for (int i = 0; i < m; ++i) {
+        finite = finite && isfinite(d[i]);
+        lo = fmin(lo, d[i]);
+    }
+    const double a = finite ? -lo : nan("");
+    const bool ok = finite && a > 1e-300;
+    if (d_alpha) *d_alpha = a;
+    *d_shift = ok ? a : 0.0;
+    if (d_info) *d_info = ok ? 0 : 1;
+}
+
+// Y += shift X for n x m column-major blocks (leading dimension ld each)
+__global__ void add_shift_kernel(float *__restrict__ Y, const float *__restrict__ X, int64_t n, int m,
+                                 int64_t ld, const double *d_shift)
+{
+    const float a = (float)*d_shift;
+    if (a == 0.0f) return;
+    const int64_t total = n * (int64_t)m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / n, i = e - c * n;
+        Y[c * ld + i] = fmaf(a, X[c * ld + i], Y[c * ld + i]);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_ritz_alpha(cudaStream_t s, const double *d, int m, double *d_alpha, double *d_shift,
+                              int *d_info)
+{
+    ritz_alpha_kernel<<<1, 1, 0, s>>>(d, m, d_alpha, d_shift, d_info);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_shift(cudaStream_t s, float *Y, const float *X, int64_t n, int m, int64_t ld,
+                             const double *d_shift)
+{
+    int64_t blocks = (n * (int64_t)m + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    add_shift_kernel<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(Y, X, n, m, ld, d_shift);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, int64_t lda, int N,
                                    uint64_t seed, uint32_t stream_id, const double *d_shift_neg,

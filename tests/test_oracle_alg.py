@@ -272,3 +272,19 @@ def test_alg2_degrades_to_alg1_when_alpha_vanishes(oracle_lib):
     ref = oracle_lib.alg1(A, 4, 2, 0, seed=3)["W"]
     assert out["degraded"] == 1
     assert np.array_equal(out["W_red"], ref)
+
+
+def test_ritz_alpha_is_a_lower_estimate_of_the_most_negative_eigenvalue(oracle_lib):
+    # the variant's alpha = -(smallest Ritz value of Q0^T A Q0): by the
+    # Poincare separation theorem every Ritz value of a symmetric A lies in
+    # [lambda_min, lambda_max], so 0 <= alpha_ritz <= |lambda_min(A)|; with
+    # the most negative eigenvector well inside the sketch it is close
+    Vr, lam, A = _decay_problem(600, 4)
+    for k in (20, 100):
+        Om = oracle_lib.omega(3, 600, k + 10)
+        Q0, _ = oracle_lib.range_finder(A, Om, 0)
+        C = Q0.T @ oracle_lib.sym_mul(A, Q0)
+        d, _, _ = oracle_lib.jacobi_eig(0.5 * (C + C.T))
+        a = -min(d.min(), 0.0)
+        assert 0.0 <= a <= -lam.min() + 1e-12
+    assert a >= 0.5 * -lam.min()
