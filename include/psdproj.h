@@ -227,6 +227,41 @@ int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
  * workspace, sized for the largest problem it has run. */
 int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams);
 
+/* ---- dual gradient descent for semidefinite least squares (Alg. 6) ------
+ *   min over PSD X of 1/2 ||X - C/rho||_F^2   s.t.  <A_i, X> = b_i, i < mc.
+ * Each iteration t forms X_t = C/rho + sum_i y_i A_i (upper triangle; the
+ * minimiser of the partial Lagrangian is (X_t)_+), projects it with
+ * psdproj_alg1 (algorithm 1, the paper's Alg. 2) or psdproj_alg2 (algorithm
+ * 2, Alg. 3; alpha as opts->alpha_mode says) in factor form W (sketch seed
+ * = seed + t; with warm_start the test matrix of iteration t > 0 is the
+ * previous iteration's orthonormal basis Q, columns that its
+ * orthonormalisation dropped replaced by the Gaussian columns of seed + t),
+ * takes grad_i = <A_i, W W^T> - b_i (FP32 passes, FP64 sums) and steps
+ * y <- y - beta grad.  It stops after the first iteration whose ||grad||_2
+ * <= eps, or after max_iter iterations.  Synchronous: the gradient is read
+ * back every iteration.  */
+typedef struct psdproj_sdls {
+    const float *dC;             /* n x n symmetric, row-major (ld), upper read */
+    const float *const *dA;      /* HOST array of mc DEVICE pointers, n x n each */
+    const double *b;             /* host, mc                                   */
+    int64_t n, ld;               /* n <= 65535                                 */
+    double rho, beta, eps;       /* rho > 0, step beta > 0, tolerance eps >= 0 */
+    uint64_t seed;
+    int mc, k, p, q;             /* constraints; sketch of each projection     */
+    int algorithm;               /* 1 or 2                                     */
+    int max_iter;                /* >= 1                                       */
+    int warm_start;              /* 0 or 1                                     */
+    int reserved;                /* must be zero                               */
+} psdproj_sdls;
+/* y (host, mc): the initial multipliers in, the final ones out.  dX (device,
+ * may be NULL): the last iterate's projection W W^T, n x n row-major (ldx);
+ * its syrk_prec as in opts.  *iters (may be NULL): iterations run;
+ * *grad_norm (may be NULL): the last ||grad||; grad_hist (host, max_iter
+ * doubles, may be NULL): ||grad|| per iteration.  Returns device errors
+ * (non-finite data, ...) as their status. */
+int psdproj_sdls_dual_gd(psdproj_ctx *ctx, const psdproj_sdls *problem, double *y, float *dX, int64_t ldx,
+                         int *iters, double *grad_norm, double *grad_hist, const psdproj_opts *opts);
+
 /* The cudaError_t behind the last PSDPROJ_ECUDA / ENOMEM / ENOTSUP that a
  * call on this host thread returned (0 if none), and in *line (may be NULL)
  * the line of the library's C-ABI source where it was seen. */

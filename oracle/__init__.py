@@ -19,6 +19,8 @@ Functions (each docstring cites the passage it follows):
 * ``alg2``                                 - Alg. 3 (the C ABI's "Algorithm 2"),
   literal last step and the reduced form of Lemma 4.
 * ``eps1``, ``eps2``                       - Eqs. (eps1), (eps2).
+* ``sdls_dual_gd``                         - Alg. 6 (dual gradient descent for
+  the semidefinite least-squares problem).
 * ``factor_dist2``, ``exact_dist2``        - Frobenius errors in Gram form.
 
 Parity status: every function above is pinned by a ``-m "not gpu"`` test in
@@ -292,6 +294,56 @@ def alg2(A, k: int, p: int, q: int, seed: int, alpha: float = 0.0, N: int = 10,
                             ctypes.byref(rp)), "alg2")
     return dict(W_lit=Wl, W_red=Wr, alpha=a.value, degraded=deg.value, rank=rank.value,
                 rplus=rp.value)
+
+
+def sdls_dual_gd(C, As, b, rho: float, k: int, p: int, q: int, algorithm: int, beta: float,
+                 eps: float, max_iter: int, seed: int, y0, N: int = 10, warm_start: bool = False,
+                 exact: bool = False):
+    """Alg. 6: dual gradient descent for min 1/2 ||X - C/rho||_F^2 over PSD X
+    with <A_i, X> = b_i.  Each iteration forms X = C/rho + sum_i y_i A_i
+    (Lemma: X*(y) = X_+), projects it (exact: Thm 1; else Alg. 2 or Alg. 3
+    with alpha from Alg. 5, the sketch of iteration t drawn with seed + t,
+    or with warm_start its Omega = the previous iteration's Q, columns that
+    the orthonormalisation dropped taken from the fresh Gaussian draw), takes
+    the gradient grad_i = <A_i, X_hat> - b_i and steps y <- y - beta grad;
+    it stops after the iteration whose gradient norm is <= eps, or after
+    max_iter iterations.  Returns dict(y, iters, gnorm, hist, W)."""
+    C = _mat(C)
+    n = C.shape[0]
+    m = k + p
+    As = [_mat(A) for A in As]
+    b = np.asarray(b, dtype=np.float64)
+    y = np.array(y0, dtype=np.float64)
+    hist, Qprev, W, g = [], None, None, float("inf")
+    t = -1
+    for t in range(max_iter):
+        X = C / rho
+        for yi, Ai in zip(y, As):
+            X = X + yi * Ai
+        if exact:
+            P = exact_proj(X)
+            grad = np.array([float(np.sum(Ai * P)) for Ai in As]) - b
+        else:
+            s = seed + t
+            Om = omega(s, n, m)
+            if warm_start and Qprev is not None:
+                alive = np.any(Qprev != 0.0, axis=0)
+                Om[:, alive] = Qprev[:, alive]
+            shift, scale = 0.0, 1.0
+            if algorithm == 2:
+                a = min_eig(X, N, s)[0]
+                if np.isfinite(a) and a > 1e-300:
+                    shift, scale = a, 1.0 / a
+            Q, _ = range_finder(X, Om, q, shift=shift, scale=scale)
+            W, _ = core_project(X, Q)
+            Qprev = Q
+            grad = np.array([float(np.sum(W * sym_mul(Ai, W))) for Ai in As]) - b
+        g = float(np.linalg.norm(grad))
+        hist.append(g)
+        y = y - beta * grad
+        if g <= eps:
+            break
+    return dict(y=y, iters=t + 1, gnorm=g, hist=hist, W=W)
 
 
 def core_project(A, Q):

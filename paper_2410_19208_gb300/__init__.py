@@ -59,6 +59,15 @@ class Request(ctypes.Structure):
     _fields_ = Problem._fields_ + [("footprint_bytes", ctypes.c_int64)]
 
 
+class Sdls(ctypes.Structure):
+    """psdproj_sdls: the semidefinite least-squares problem of Alg. 6."""
+    _fields_ = [("dC", ctypes.c_void_p), ("dA", ctypes.POINTER(ctypes.c_void_p)), ("b", ctypes.POINTER(ctypes.c_double)),
+                ("n", ctypes.c_int64), ("ld", ctypes.c_int64), ("rho", ctypes.c_double), ("beta", ctypes.c_double),
+                ("eps", ctypes.c_double), ("seed", ctypes.c_uint64), ("mc", ctypes.c_int), ("k", ctypes.c_int),
+                ("p", ctypes.c_int), ("q", ctypes.c_int), ("algorithm", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("warm_start", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
 class ServerStats(ctypes.Structure):
     """psdproj_server_stats."""
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
@@ -121,6 +130,9 @@ def _load():
         "psdproj_server_get_stats": (_int, [_P, ctypes.POINTER(ServerStats)]),
         "psdproj_server_destroy": (_int, [_P]),
         "psdproj_last_cuda_error": (_int, [ctypes.POINTER(_int)]),
+        "psdproj_sdls_dual_gd": (_int, [_P, ctypes.POINTER(Sdls), ctypes.POINTER(ctypes.c_double), _P, _i64,
+                                        ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Opts)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -237,6 +249,27 @@ class Context:
                              _ptr(W), _tall(W, "W")[2] if W is not None else n, _ptr(d.get("rank")))
         _check(_load().psdproj_batched(self.h, len(problems), ctypes.byref(arr),
                                        ctypes.byref(opts) if opts else None), "psdproj_batched")
+
+    def sdls(self, C, As, b, rho, k, p, q, algorithm, beta, eps, max_iter, seed, y0, warm_start=False,
+             X=None, opts: Opts | None = None):
+        """Alg. 6 on device matrices C, As (n x n, row-major, upper read) and host b.
+        Returns dict(y, iters, gnorm, hist)."""
+        n, ld = _sq(C, "C")
+        for A in As:
+            assert _sq(A, "A_i") == (n, ld)
+        mc = len(As)
+        ptrs = (ctypes.c_void_p * mc)(*[_ptr(A) for A in As])
+        bb = (ctypes.c_double * mc)(*[float(x) for x in b])
+        pr = Sdls(_ptr(C), ctypes.cast(ptrs, ctypes.POINTER(ctypes.c_void_p)),
+                  ctypes.cast(bb, ctypes.POINTER(ctypes.c_double)), n, ld, float(rho), float(beta), float(eps),
+                  seed, mc, k, p, q, algorithm, max_iter, int(bool(warm_start)), 0)
+        y = (ctypes.c_double * mc)(*[float(v) for v in y0])
+        hist = (ctypes.c_double * max_iter)()
+        it, gn = _int(), ctypes.c_double()
+        _check(_load().psdproj_sdls_dual_gd(self.h, ctypes.byref(pr), y, _ptr(X), X.stride(0) if X is not None else n,
+                                            ctypes.byref(it), ctypes.byref(gn), hist,
+                                            ctypes.byref(opts) if opts else None), "psdproj_sdls_dual_gd")
+        return dict(y=list(y), iters=it.value, gnorm=gn.value, hist=list(hist)[: it.value])
 
     def set_batch_streams(self, streams: int):
         _check(_load().psdproj_set_batch_streams(self.h, streams), "psdproj_set_batch_streams")

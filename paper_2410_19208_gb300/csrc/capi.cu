@@ -7,6 +7,7 @@
 //                 form Q (Q^T A Q)_+ Q^T of Lemma 4.
 // Every step is a kernel of this library; nothing runs on the host but
 // argument checks, workspace management and launches.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <atomic>
@@ -294,10 +295,12 @@ int validate(int64_t n, int64_t lda, int k, int p, int q, const void *A)
     return PSDPROJ_OK;
 }
 
+// omega_ready: the workspace's Omega already holds the test matrix (warm
+// start of Alg. 6); it is not drawn again
 int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int k, int p,
                    int q, uint64_t seed, bool scaled, double alpha_in, double *d_alpha_out,
                    int *d_info, float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
-                   const psdproj_opts *opts_in)
+                   const psdproj_opts *opts_in, bool omega_ready = false)
 {
     if (!ctx) return PSDPROJ_EINVAL;
     psdproj_opts opts;
@@ -346,7 +349,7 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     }
     const int lpad = psd_lpad(m);
     // Omega (Alg. 1), then Y = (A + shift I) Omega
-    {
+    if (!omega_ready) {
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
         if (opts.sketch == PSDPROJ_SKETCH_SRHT)
             PSD_KL(launch_srht(s, seed, n, m, lpad, ws.ld, ws.picks, ctx->d_status, ws.Om, ws.ld), 2);
@@ -742,6 +745,94 @@ int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
         cudaStreamWaitEvent(ctx->stream, ctx->lane_ev[j], 0);
     }
     return rc;
+}
+
+int psdproj_sdls_dual_gd(psdproj_ctx *ctx, const psdproj_sdls *pr, double *y, float *dX, int64_t ldx,
+                         int *iters_out, double *gnorm_out, double *ghist, const psdproj_opts *opts_in)
+{
+    if (!ctx || !pr || !y || !pr->dC || !pr->dA || !pr->b || pr->mc < 1 || pr->mc > 4096) return PSDPROJ_EINVAL;
+    if (!(pr->rho > 0.0) || !(pr->beta > 0.0) || !(pr->eps >= 0.0) || pr->max_iter < 1) return PSDPROJ_EINVAL;
+    if (pr->algorithm != 1 && pr->algorithm != 2) return PSDPROJ_EINVAL;
+    if (pr->n > 65535) return PSDPROJ_ETOOLARGE;
+    for (int i = 0; i < pr->mc; ++i)
+        if (!pr->dA[i]) return PSDPROJ_EINVAL;
+    if (dX && ldx < pr->n) return PSDPROJ_EINVAL;
+    psdproj_opts opts;
+    if (opts_in) opts = *opts_in; else psdproj_default_opts(&opts);
+    PSD_TRY(check_opts(&opts));
+    PSD_TRY(validate(pr->n, pr->ld, pr->k, pr->p, pr->q, pr->dC));
+    const int64_t n = pr->n;
+    const int m = pr->k + pr->p, mc = pr->mc;
+    device_guard g(ctx->device);
+    PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    psd_workspace &ws = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    // X = C / rho + sum y_i A_i lives in the host-API staging buffer (n x n)
+    const int64_t ldX = (n + 3) / 4 * 4;
+    PSD_TRY(ensure_stage(&ctx->dA_stage, &ctx->dA_stage_bytes, sizeof(float) * (size_t)n * ldX, s));
+    // device scratch: y (mc doubles), g (mc doubles), the mc pointers to A_i
+    const size_t scratch = sizeof(double) * 2 * mc + sizeof(float *) * mc;
+    PSD_TRY(ensure_stage(&ctx->dP_stage, &ctx->dP_stage_bytes, scratch + 256, s));
+    double *d_y = reinterpret_cast<double *>(ctx->dP_stage);
+    double *d_g = d_y + mc;
+    const float **d_A = reinterpret_cast<const float **>(d_g + mc);
+    std::vector<double> neg_b(mc), gh(mc);
+    for (int i = 0; i < mc; ++i) neg_b[i] = -pr->b[i];
+    PSD_CK(cudaMemcpyAsync(d_A, pr->dA, sizeof(float *) * mc, cudaMemcpyHostToDevice, s));
+    psdproj_opts po = opts;
+    po.out_mode = PSDPROJ_OUT_FACTOR;
+    double gn = 0.0;
+    int t = 0;
+    for (; t < pr->max_iter; ++t) {
+        PSD_CK(cudaMemcpyAsync(d_y, y, sizeof(double) * mc, cudaMemcpyHostToDevice, s));
+        PSD_CK(cudaMemcpyAsync(d_g, neg_b.data(), sizeof(double) * mc, cudaMemcpyHostToDevice, s));
+        PSD_KL(launch_sdls_combine(s, pr->dC, d_A, mc, d_y, pr->rho, n, pr->ld, ctx->dA_stage, ldX), 1);
+        const uint64_t seed_t = pr->seed + (uint64_t)t;
+        bool warm = false;
+        if (pr->warm_start && t > 0) {
+            // the previous iterate's basis, with fresh Gaussian columns where
+            // the orthonormalisation dropped one
+            PSD_KL(launch_gaussian(s, seed_t, 0u, n, m, psd_lpad(m), ws.ld, ws.Om, ws.ld), 1);
+            PSD_KL(launch_sdls_warm_omega(s, ws.Om, ws.Q, ws.dead, n, m, ws.ld), 1);
+            warm = true;
+        }
+        PSD_TRY(run_projection(ctx, ctx->dA_stage, n, ldX, pr->k, pr->p, pr->q, seed_t, pr->algorithm == 2, 0.0,
+                               nullptr, nullptr, nullptr, 0, nullptr, 0, nullptr, &po, warm));
+        // grad_i = <A_i, W W^T> - b_i = sum_c w_c^T (A_i w_c) - b_i
+        for (int i = 0; i < mc; ++i) {
+            PSD_TRY(sym_pass(ctx, pr->dA[i], n, pr->ld, ws.W, ws.ld, m, nullptr, ws.Y, ws.ld, PSDPROJ_PREC_FP32));
+            PSD_KL(launch_sdls_dot(s, ws.W, ws.Y, n, m, ws.ld, d_g + i), 1);
+        }
+        PSD_CK(cudaMemcpyAsync(gh.data(), d_g, sizeof(double) * mc, cudaMemcpyDeviceToHost, s));
+        PSD_CK(cudaStreamSynchronize(s));
+        int st = 0;
+        PSD_CK(cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st) {
+            cudaMemset(ctx->d_status, 0, sizeof(int));
+            return st;
+        }
+        gn = 0.0;
+        for (int i = 0; i < mc; ++i) gn += gh[i] * gh[i];
+        gn = sqrt(gn);
+        if (ghist) ghist[t] = gn;
+        for (int i = 0; i < mc; ++i) y[i] -= pr->beta * gh[i];
+        if (gn <= pr->eps) {
+            ++t;
+            break;
+        }
+    }
+    if (iters_out) *iters_out = t;
+    if (gnorm_out) *gnorm_out = gn;
+    if (dX) {
+        // the last iterate's projection: X_hat = W W^T
+        stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
+        if (opts.syrk_prec == PSDPROJ_PREC_FP32 || m > 128)
+            PSD_KL(launch_syrk_simt(s, ws.W, ws.ld, n, m, ws.ints + IN_RANK, dX, ldx, 0), 1);
+        else
+            PSD_KL(launch_syrk_tc(s, ctx->persist_sms, ws.W, ws.ld, n, m, ws.ints + IN_RANK, dX, ldx, 0, ws.Xhi,
+                                  ws.Xlo, ws.ld, ctx->d_status), 2);
+    }
+    return PSDPROJ_OK;
 }
 
 int psdproj_alg1_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda, int k, int p,

@@ -138,6 +138,17 @@ cudaError_t launch_ritz_alpha(cudaStream_t s, const double *d, int m, double *d_
 cudaError_t launch_add_shift(cudaStream_t s, float *Y, const float *X, int64_t n, int m, int64_t ld,
                              const double *d_shift);
 
+// Alg. 6 (dual gradient descent for semidefinite least squares):
+// X = C / rho + sum_i y_i A_i on the upper triangle (dA: device array of mc
+// device pointers, y: device doubles; n <= 65535); g += <W, Z> (FP64);
+// Om[:, c] = Q[:, c] where dead[c] == 0.
+cudaError_t launch_sdls_combine(cudaStream_t s, const float *C, const float *const *dA, int mc, const double *y,
+                                double rho, int64_t n, int64_t ld, float *X, int64_t ldx);
+cudaError_t launch_sdls_dot(cudaStream_t s, const float *W, const float *Z, int64_t n, int m, int64_t ld,
+                            double *g);
+cudaError_t launch_sdls_warm_omega(cudaStream_t s, float *Om, const float *Q, const int *dead, int64_t n,
+                                   int m, int64_t ld);
+
 // Philox streams of the SRHT test matrix: column picks and row signs
 constexpr uint32_t PSD_SRHT_PICKS = 16u, PSD_SRHT_SIGNS = 17u;
 // SRHT test matrix (see gauss.cu); picks: m ints of device scratch; n >= m.

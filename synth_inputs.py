@@ -15,6 +15,8 @@ Recipes (seeds: U from seed_u, eigenvalues from seed_lam, both numpy PCG64):
 * ``spectrum_batch``   batched / served matrices: 10% U[0.5,5], rest
   N(0, 0.1^2) (10% rounded half-up).
 * ``spectrum_cor3``    the block spectrum of Cor. 3 (quarters -b1, -b2, b3, b4).
+* ``sdls_problem``     C, A_i, b of the semidefinite least-squares example
+  (Sec. 6), the input of the dual gradient descent of Alg. 6.
 
 Eigenvalues are placed on the diagonal in generation order before U is
 applied (positives, negatives, noise).
@@ -133,3 +135,26 @@ def log_uniform_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Matrix sides log-uniform in [lo, hi] (batched and served recipes)."""
     rng = np.random.default_rng(seed)
     return np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi), count))).astype(np.int64)
+
+
+def sdls_problem(n: int, mc: int, seed: int = 0):
+    """The semidefinite least-squares example of Sec. 6 (dual gradient
+    descent, Alg. 6): A_i = (T_i + T_i^T) / (2 ||T_i||) with T_i Gaussian
+    n x n and ||.|| the Frobenius norm (the paper writes ||.||_2 for the
+    Frobenius norm of a matrix elsewhere, and only with it does its step
+    size 0.5 lie below 2 / Lipschitz constant of the dual gradient);
+    b_i = <A_i, X0> for a PSD X0 = G G^T / n (G Gaussian), so the problem is
+    feasible; C = (H + H^T) / 2 with H Gaussian.  numpy PCG64 stream `seed`.
+    Returns (C, [A_i], b) in FP64 (rounded to FP32 by the caller when it is
+    the device input)."""
+    rng = np.random.default_rng(seed)
+    As = []
+    for _ in range(mc):
+        T = rng.standard_normal((n, n))
+        As.append((T + T.T) / (2.0 * np.linalg.norm(T)))
+    G = rng.standard_normal((n, n))
+    X0 = G @ G.T / n
+    b = np.array([float(np.sum(Ai * X0)) for Ai in As])
+    H = rng.standard_normal((n, n))
+    C = (H + H.T) / 2.0
+    return C, As, b

@@ -621,3 +621,54 @@ def test_ritz_alpha_on_a_psd_matrix_degrades_to_alg1(ctx):
     one = _run(ctx, A32, k, p, q, seed, alg=1)
     assert got["info"] == 1 and got["alpha"] <= 1e-300
     assert _rel(got["P"], one["P"]) <= 1e-5
+
+
+# ----------------------------------------------------------------------------
+# Alg. 6: dual gradient descent for semidefinite least squares
+# ----------------------------------------------------------------------------
+def _sdls_inputs(n, mc, seed):
+    C, As, b = si.sdls_problem(n, mc, seed=seed)
+    C32 = C.astype(np.float32)
+    A32 = [A.astype(np.float32) for A in As]
+    # b and every oracle input from the FP32-rounded matrices the GPU reads
+    return C32, A32, b
+
+
+@pytest.mark.parametrize("alg,q,warm", [(2, 6, False), (1, 2, False), (2, 1, True)])
+def test_sdls_dual_gd_follows_the_oracle(ctx, oracle_lib, alg, q, warm):
+    # the example of Sec. 6 (n = 200, two constraints, rho = 1, beta = 0.5,
+    # k = 75, p = 10, y0 = (1.2753, 0.2418)), 25 iterations
+    n, mc, iters = 200, 2, 25
+    C32, A32, b = _sdls_inputs(n, mc, 3)
+    y0 = [1.2753, 0.2418]
+    Cd = torch.from_numpy(C32).cuda()
+    Ad = [torch.from_numpy(A).cuda() for A in A32]
+    X = torch.full((n, n), float("nan"), device="cuda")
+    got = ctx.sdls(Cd, Ad, b, 1.0, 75, 10, q, alg, 0.5, 0.0, iters, 1, y0, warm_start=warm, X=X)
+    ref = oracle_lib.sdls_dual_gd(C32.astype(np.float64), [A.astype(np.float64) for A in A32], b, 1.0, 75, 10,
+                                  q, alg, 0.5, 0.0, iters, 1, y0, warm_start=warm)
+    assert got["iters"] == ref["iters"] == iters
+    assert np.allclose(got["hist"], ref["hist"], rtol=2e-3, atol=1e-5)
+    assert np.allclose(got["y"], ref["y"], rtol=1e-3, atol=1e-5)
+    # the returned X is the last iterate's projection: PSD, and its
+    # constraint residual is the last gradient
+    Xh = X.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(Xh))
+    res = np.array([np.sum(A.astype(np.float64) * Xh) for A in A32]) - b
+    assert abs(np.linalg.norm(res) - got["hist"][-1]) <= 1e-3 * got["hist"][-1] + 1e-5
+    assert np.linalg.eigvalsh(0.5 * (Xh + Xh.T)).min() >= -1e-4 * np.abs(Xh).max()
+
+
+def test_sdls_stops_at_the_tolerance_and_rejects_bad_arguments(ctx):
+    n, mc = 120, 3
+    C32, A32, b = _sdls_inputs(n, mc, 8)
+    Cd = torch.from_numpy(C32).cuda()
+    Ad = [torch.from_numpy(A).cuda() for A in A32]
+    r = ctx.sdls(Cd, Ad, b, 1.0, 100, 10, 1, 2, 0.5, 1e-3, 200, 1, [0.0, 0.0, 0.0], warm_start=True)
+    assert r["gnorm"] <= 1e-3 and r["iters"] < 200
+    assert r["hist"][-1] == r["gnorm"] and all(h > 1e-3 for h in r["hist"][:-1])
+    with pytest.raises(ps.PsdprojError) as ei:
+        ctx.sdls(Cd, Ad, b, 1.0, 100, 10, 1, 3, 0.5, 1e-3, 10, 1, [0.0] * 3)     # no algorithm 3
+    assert ei.value.code == 1
+    with pytest.raises(ps.PsdprojError):
+        ctx.sdls(Cd, Ad, b, -1.0, 100, 10, 1, 2, 0.5, 1e-3, 10, 1, [0.0] * 3)     # rho <= 0

@@ -288,3 +288,41 @@ def test_ritz_alpha_is_a_lower_estimate_of_the_most_negative_eigenvalue(oracle_l
         a = -min(d.min(), 0.0)
         assert 0.0 <= a <= -lam.min() + 1e-12
     assert a >= 0.5 * -lam.min()
+
+
+# ----------------------------------------------------------------------------
+# Alg. 6 (dual gradient descent for semidefinite least squares)
+# ----------------------------------------------------------------------------
+def _theta(oracle_lib, C, As, b, rho, y):
+    # dual function theta(y) = L(X*(y), y), X*(y) = (C/rho + sum y_i A_i)_+
+    X = C / rho + sum(yi * Ai for yi, Ai in zip(y, As))
+    P = oracle_lib.exact_proj(X)
+    return 0.5 * np.sum((P - C / rho) ** 2) - sum(yi * (np.sum(Ai * P) - bi) for yi, Ai, bi in zip(y, As, b))
+
+
+def test_sdls_exact_gradient_descent_reaches_the_dual_optimum(oracle_lib):
+    # with exact projections Alg. 6 is gradient ascent on the concave dual:
+    # the gradient vanishes and theta is maximal there (checked by moving y)
+    n, mc, rho = 100, 2, 1.0
+    C, As, b = si.sdls_problem(n, mc, seed=3)
+    r = oracle_lib.sdls_dual_gd(C, As, b, rho, 10, 5, 0, 2, 0.5, 1e-9, 400, 1, [1.2753, 0.2418], exact=True)
+    assert r["gnorm"] <= 1e-9 and r["iters"] < 400
+    assert all(h2 <= h1 * 1.0001 for h1, h2 in zip(r["hist"][5:], r["hist"][6:]))
+    t0 = _theta(oracle_lib, C, As, b, rho, r["y"])
+    for i in range(mc):
+        for d in (-1e-3, 1e-3):
+            yy = np.array(r["y"]); yy[i] += d
+            assert _theta(oracle_lib, C, As, b, rho, yy) <= t0 + 1e-12
+
+
+def test_sdls_full_width_sketch_follows_the_exact_iteration(oracle_lib):
+    # a sketch as wide as the matrix spans everything: the randomized
+    # projection is the exact one, so both iterations coincide
+    n, mc = 60, 2
+    C, As, b = si.sdls_problem(n, mc, seed=4)
+    y0 = [0.3, -0.7]
+    ex = oracle_lib.sdls_dual_gd(C, As, b, 1.0, 50, 10, 0, 1, 0.5, 0.0, 15, 1, y0, exact=True)
+    for alg, warm in ((1, False), (2, False), (1, True)):
+        rr = oracle_lib.sdls_dual_gd(C, As, b, 1.0, 50, 10, 0, alg, 0.5, 0.0, 15, 1, y0, warm_start=warm)
+        assert np.allclose(rr["hist"], ex["hist"], rtol=1e-8, atol=1e-10)
+        assert np.allclose(rr["y"], ex["y"], rtol=1e-8, atol=1e-10)
