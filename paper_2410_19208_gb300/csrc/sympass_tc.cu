@@ -24,8 +24,8 @@
 // added by TMA bulk reduce-add from a swizzled 32 x 32 staging box per warp
 // (scalar atomics when Y is not 16-byte aligned with ld % 4 == 0).
 //
-// Warp roles (256 threads, one CTA per SM, persistent over an equal share of
-// the tiles in row-major order): warp 0 issues the copies, warp 1 owns TMEM and
+// Warp roles (256 threads, one CTA per SM, persistent over a cost-balanced
+// range of the tiles in row-major order): warp 0 issues the copies, warp 1 owns TMEM and
 // issues tcgen05.mma from one thread, warps 4-7 drain TMEM.  Every mbarrier
 // wait is bounded; on a timeout the CTA records PSDPROJ_ETIMEOUT, unwinds and
 // frees its TMEM.
@@ -155,8 +155,23 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     extern __shared__ __align__(1024) uint8_t sm[];
     Bars &B = *reinterpret_cast<Bars *>(sm + OFF_BAR);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t0 = P.tiles * blockIdx.x / gridDim.x;
-    const int64_t t1 = P.tiles * (blockIdx.x + 1) / gridDim.x;
+    // equal shares of cost(t) = t + SEGC * (row of t): a block-row start costs
+    // about SEGC tiles (D1 drained, X_I reloaded, the pipeline refilled), so
+    // CTAs whose range crosses many short rows near the end get fewer tiles
+    auto first_tile = [&](int64_t b) -> int64_t {
+        constexpr int64_t SEGC = 2;
+        const int64_t target = (P.tiles + SEGC * P.nbr) * b / gridDim.x;
+        int64_t lo = 0, hi = P.tiles;                // smallest t with cost(t) >= target
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            int Im, Jm;
+            tile_of(mid, P.nbc, P.nbr, Im, Jm);
+            if (mid + SEGC * Im >= target) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    const int64_t t0 = first_tile(blockIdx.x);
+    const int64_t t1 = blockIdx.x + 1 == gridDim.x ? P.tiles : first_tile(blockIdx.x + 1);
     if ((smem_u32(sm) & 1023u) != 0u) {
         if (threadIdx.x == 0) psd_set_status(P.d_status, PSDPROJ_ECUDA);
         return;
@@ -245,19 +260,23 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 const uint32_t a_tile = smem_u32(sm + OFF_A + s * STAGE);
                 const uint32_t xj = a_tile + A_BYTES;
                 const uint32_t xi = smem_u32(sm + OFF_XI);
-                // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns)
-#pragma unroll
-                for (int kk = 0; kk < BN / 16; ++kk) {
-                    const uint64_t ad = sdesc_sw128(xj + kk * 32, 16, 1024);
-                    const uint64_t bd = sdesc_sw128(a_tile + kk * 32, 16, 1024);
-                    mma_bf16_ss(tmem + D1_COL, ad, bd, id1, (!first || kk > 0) ? 1u : 0u);
-                }
+                // P2 first: its sixteen short MMAs, then P1's four long ones,
+                // which stay queued on the tensor pipe while this thread does
+                // the next tile's bookkeeping (tcgen05.mma issue blocks once
+                // the pipe's queue is full)
                 // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows)
 #pragma unroll
                 for (int kk = 0; kk < BM / 16; ++kk) {
                     const uint64_t ad = sdesc_sw128(xi + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
                     const uint64_t bd = sdesc_sw128(a_tile + kk * 2048, 16384, 1024);
                     mma_bf16_ss(tmem + D2_COL + BN * b, ad, bd, id2, kk > 0 ? 1u : 0u);
+                }
+                // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns)
+#pragma unroll
+                for (int kk = 0; kk < BN / 16; ++kk) {
+                    const uint64_t ad = sdesc_sw128(xj + kk * 32, 16, 1024);
+                    const uint64_t bd = sdesc_sw128(a_tile + kk * 32, 16, 1024);
+                    mma_bf16_ss(tmem + D1_COL, ad, bd, id1, (!first || kk > 0) ? 1u : 0u);
                 }
                 issued = true;
                 mma_commit(&B.empty[s]);
@@ -343,9 +362,11 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
 
 // X (FP32, column-major) -> BF16 image used by the TMA loads of the pass:
 // part 0 = bf16(x) (the high part), part 1 = bf16(x - bf16(x)) (the low part
-// of the split-BF16 form)
+// of the split-BF16 form).  Yz (may be NULL): Y to clear in the same sweep
+// (X and Y are different buffers), saving the separate memset launch.
 __global__ void to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t n, int m,
-                               __nv_bfloat16 *__restrict__ H, int64_t ldh, int part)
+                               __nv_bfloat16 *__restrict__ H, int64_t ldh, int part, float *__restrict__ Yz,
+                               int64_t ldy)
 {
     const int64_t total = n * (int64_t)m;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -354,6 +375,7 @@ __global__ void to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t
         const float x = X[c * ldx + i];
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
         H[c * ldh + i] = part ? __float2bfloat16_rn(x - __bfloat162float(hi)) : hi;
+        if (Yz) Yz[c * ldy + i] = 0.0f;
     }
 }
 
@@ -451,7 +473,8 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
         const int64_t total = n * (int64_t)m;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4096) blocks = 4096;
-        to_bf16_kernel<<<blocks, 256, 0, s>>>(X, ldx, n, m, reinterpret_cast<__nv_bfloat16 *>(Xh), ldh, x_part);
+        to_bf16_kernel<<<blocks, 256, 0, s>>>(X, ldx, n, m, reinterpret_cast<__nv_bfloat16 *>(Xh), ldh, x_part,
+                                              accumulate ? nullptr : Y, ldy);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -492,12 +515,7 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
             P.tma_y = 0;
     }
 
-    cudaError_t e = cudaSuccess;
-    if (!accumulate) {
-        e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(float), 0, (size_t)n * sizeof(float), (size_t)m, s);
-        if (e != cudaSuccess) return e;
-    }
-    e = cudaFuncSetAttribute(sym_pass_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sym_pass_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
     int grid = sm_count > 0 ? sm_count : 148;

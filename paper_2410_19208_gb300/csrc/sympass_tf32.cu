@@ -281,15 +281,16 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
 }
 
 // X (FP32, column-major) -> X rounded to TF32 in the aligned buffer that the
-// pass loads by TMA
+// pass loads by TMA; Y (a different buffer) is cleared in the same sweep
 __global__ void to_tf32_kernel(const float *__restrict__ X, int64_t ldx, int64_t n, int m,
-                               float *__restrict__ Xf, int64_t ldf)
+                               float *__restrict__ Xf, int64_t ldf, float *__restrict__ Y, int64_t ldy)
 {
     const int64_t total = n * (int64_t)m;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = e / n, i = e - c * n;
         Xf[c * ldf + i] = tf32_rna(X[c * ldx + i]);
+        Y[c * ldy + i] = 0.0f;
     }
 }
 
@@ -405,7 +406,7 @@ cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, 
     if ((ldf % 4) != 0 || (reinterpret_cast<uintptr_t>(Xf) & 15) != 0 || ldf < n) return cudaErrorNotSupported;
     if (!tensor_map_encoder()) return cudaErrorNotSupported;
 
-    to_tf32_kernel<<<grid_for(n * (int64_t)m), 256, 0, s>>>(X, ldx, n, m, Xf, ldf);
+    to_tf32_kernel<<<grid_for(n * (int64_t)m), 256, 0, s>>>(X, ldx, n, m, Xf, ldf, Y, ldy);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // X_J^T: 32 rows of X (128 bytes) x 128 columns; columns >= m read as zero
@@ -437,8 +438,6 @@ cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, 
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             P.tma_y = 0;
     }
-    e = cudaMemset2DAsync(Y, (size_t)ldy * sizeof(float), 0, (size_t)n * sizeof(float), (size_t)m, s);
-    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(sym_pass_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
     int grid = sm_count > 0 ? sm_count : 148;
