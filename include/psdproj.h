@@ -329,9 +329,12 @@ int psdproj_server_get_stats(psdproj_server *srv, psdproj_server_stats *stats);
 int psdproj_server_destroy(psdproj_server *srv);
 
 /* Host-buffer forms of the two calls: hA, hP, hW, h_rank are HOST pointers
- * (pinned memory recommended).  The call copies A to a context-owned device
- * buffer, runs the projection, copies P (and W, r+) back, and synchronises
- * the stream before returning.  Returns the first error, device-side status
+ * (pinned memory recommended).  From pinned host memory the device reads
+ * only A's upper triangle, over the host link: the BF16 form packs its image
+ * straight from it, the other forms gather it into a context-owned device
+ * buffer; other host memory is copied whole.  The call then runs the
+ * projection, copies P (and W, r+) back, and synchronises the stream before
+ * returning.  Returns the first error, device-side status
  * included. */
 int psdproj_alg1_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda,
                       int k, int p, int q, uint64_t seed,

@@ -454,9 +454,28 @@ int run_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda, int k, i
     PSD_TRY(ensure_stage(&ctx->dA_stage, &ctx->dA_stage_bytes, sizeof(float) * n * n, s));
     if (wantP) PSD_TRY(ensure_stage(&ctx->dP_stage, &ctx->dP_stage_bytes, sizeof(float) * n * n, s));
     if (hW) PSD_TRY(ensure_stage(&ctx->dW_stage, &ctx->dW_stage_bytes, sizeof(float) * n * m, s));
-    PSD_CK(cudaMemcpy2DAsync(ctx->dA_stage, sizeof(float) * n, hA, sizeof(float) * lda,
-                             sizeof(float) * n, n, cudaMemcpyHostToDevice, s));
-    PSD_TRY(run_projection(ctx, ctx->dA_stage, n, n, k, p, q, seed, scaled, alpha_in,
+    // Only A's upper triangle is ever read.  Pinned host memory is reachable
+    // from the GPU (NVLink-C2C), so the device reads that half of A over the
+    // link: the BF16 form packs its image straight from the host buffer (it
+    // reads A nowhere else), the others gather it into the staging buffer
+    // with a kernel.  Other host memory is copied whole (one contiguous copy
+    // when lda == n).
+    cudaPointerAttributes pa;
+    const bool mapped = cudaPointerGetAttributes(&pa, hA) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                        pa.devicePointer != nullptr;
+    if (!mapped) cudaGetLastError();            // clear the query's error for unregistered memory
+    const float *dA = ctx->dA_stage;
+    int64_t ldA = n;
+    if (mapped && opts.prec == PSDPROJ_PREC_BF16) {
+        dA = static_cast<const float *>(pa.devicePointer);
+        ldA = lda;
+    } else if (mapped) {
+        PSD_KL(launch_copy_upper(s, static_cast<const float *>(pa.devicePointer), n, lda, ctx->dA_stage, n), 1);
+    } else {
+        PSD_CK(cudaMemcpy2DAsync(ctx->dA_stage, sizeof(float) * n, hA, sizeof(float) * lda,
+                                 sizeof(float) * n, n, cudaMemcpyHostToDevice, s));
+    }
+    PSD_TRY(run_projection(ctx, dA, n, ldA, k, p, q, seed, scaled, alpha_in,
                            ctx->d_misc_f, ctx->d_misc + 1, wantP ? ctx->dP_stage : nullptr, n,
                            hW ? ctx->dW_stage : nullptr, n, ctx->d_misc, &opts));
     if (wantP)

@@ -131,6 +131,10 @@ cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, uint32_t stream_id,
                             int64_t n, int m, int mpad, int64_t rows_pad,
                             float *X, int64_t ldx);
 
+// D[i*ldd + j] = S[i*lds + j] for j >= i (the upper triangle; S may be
+// pinned host memory read over the host link)
+cudaError_t launch_copy_upper(cudaStream_t s, const float *S, int64_t n, int64_t lds, float *D, int64_t ldd);
+
 // alpha = -min(d) (Ritz values of an unshifted sketch's core), shift and
 // info as launch_alpha_finish; Y += shift X (n x m, leading dimension ld)
 cudaError_t launch_ritz_alpha(cudaStream_t s, const double *d, int m, double *d_alpha, double *d_shift,

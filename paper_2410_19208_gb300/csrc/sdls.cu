@@ -1,6 +1,7 @@
 // Kernels of the dual gradient descent for the semidefinite least-squares
 // problem (Alg. 6): forming X = C / rho + sum_i y_i A_i, the gradient terms
-// <A_i, W W^T> = sum_c w_c^T (A_i w_c), and the warm-started test matrix.
+// <A_i, W W^T> = sum_c w_c^T (A_i w_c), and the warm-started test matrix;
+// and the upper-triangle gather of the host-buffer calls.
 #include "ctx.h"
 
 namespace {
@@ -55,6 +56,27 @@ __global__ void sdls_warm_omega_kernel(float *__restrict__ Om, const float *__re
     }
 }
 
+// D[i*ldd + j] = S[i*lds + j], j >= i: one block per row, float4 where both
+// rows allow it (16-byte aligned starts)
+__global__ void copy_upper_kernel(const float *__restrict__ S, int64_t n, int64_t lds, float *__restrict__ D,
+                                  int64_t ldd, int vec)
+{
+    const int64_t i = blockIdx.x;
+    const float *src = S + i * lds;
+    float *dst = D + i * ldd;
+    int64_t j0 = i;
+    if (vec) {
+        const int64_t a = (i + 3) & ~(int64_t)3;                 // first 4-aligned column >= i
+        for (int64_t j = i + threadIdx.x; j < a && j < n; j += blockDim.x) dst[j] = src[j];
+        const int64_t nv = (n - a) >> 2;
+        for (int64_t v = threadIdx.x; v < nv; v += blockDim.x)
+            reinterpret_cast<float4 *>(dst + a)[v] = __ldcs(reinterpret_cast<const float4 *>(src + a) + v);
+        j0 = a + 4 * (nv > 0 ? nv : 0);
+        if (j0 < a) j0 = a;
+    }
+    for (int64_t j = j0 + threadIdx.x; j < n; j += blockDim.x) dst[j] = src[j];
+}
+
 unsigned blocks_for(int64_t total, int64_t cap)
 {
     int64_t b = (total + 255) / 256;
@@ -84,5 +106,14 @@ cudaError_t launch_sdls_warm_omega(cudaStream_t s, float *Om, const float *Q, co
                                    int m, int64_t ld)
 {
     sdls_warm_omega_kernel<<<blocks_for(n * (int64_t)m, 152 * 8), 256, 0, s>>>(Om, Q, dead, n, m, ld);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_upper(cudaStream_t s, const float *S, int64_t n, int64_t lds, float *D, int64_t ldd)
+{
+    if (n > 0x7fffffff) return cudaErrorInvalidValue;
+    const int vec = (lds % 4) == 0 && (ldd % 4) == 0 && (reinterpret_cast<uintptr_t>(S) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(D) & 15) == 0;
+    copy_upper_kernel<<<(unsigned)n, 256, 0, s>>>(S, n, lds, D, ldd, vec);
     return cudaGetLastError();
 }

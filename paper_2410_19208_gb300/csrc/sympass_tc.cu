@@ -393,13 +393,16 @@ __device__ __forceinline__ float lo_part(float v)
 // parts bf16(a - bf16(a)) instead (the split-BF16 form's second image).
 __global__ void __launch_bounds__(256)
 pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
-                       uint16_t *__restrict__ Ab, int nbc, int vec, int part)
+                       uint16_t *__restrict__ Ab, int nbc, int vec, int part, int64_t nblocks)
 {
     constexpr int RPT = 4;                            // rows per thread
-    const int J = blockIdx.x;
-    const int I = (int)(((int64_t)blockIdx.y * 64) / BM);
-    if (J < R * I) return;                            // uniform across the block
-    const int64_t rbase = (int64_t)blockIdx.y * 64 + (threadIdx.x >> 4);
+    // grid-strided over the (tile column J, 64-row chunk) blocks
+    for (int64_t bid = blockIdx.x; bid < nblocks; bid += gridDim.x) {
+    const int J = (int)(bid % nbc);
+    const int64_t chunk = bid / nbc;
+    const int I = (int)((chunk * 64) / BM);
+    if (J < R * I) continue;                          // uniform across the block
+    const int64_t rbase = chunk * 64 + (threadIdx.x >> 4);
     const int64_t c0 = (int64_t)J * BN + 4 * (threadIdx.x & 15);
     float v[RPT][4];
 #pragma unroll
@@ -438,6 +441,7 @@ pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
         const int rt = (int)(r - (int64_t)I * BM);     // row within the tile
         *reinterpret_cast<uint2 *>(tile + rt * 128 + ((k ^ (rt & 7)) << 4) + 8 * (threadIdx.x & 1)) = o;
     }
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() { return tensor_map_encoder(); }
@@ -451,8 +455,16 @@ cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t 
     const int nbr = (int)((n + BM - 1) / BM);
     const int nbc = nbr * R;
     const int vec = (lda % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
-    dim3 grid((unsigned)nbc, (unsigned)(nbr * (BM / 64)));
-    pack_upper_bf16_kernel<<<grid, 256, 0, s>>>(A, n, lda, Ab, nbc, vec, part);
+    const int64_t nblocks = (int64_t)nbc * nbr * (BM / 64);
+    // A in host memory (read over the host link): a few blocks per SM keep
+    // the link busy without taking every SM from the other streams' kernels
+    cudaPointerAttributes pa;
+    const bool host = cudaPointerGetAttributes(&pa, A) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    if (!host) cudaGetLastError();
+    int64_t grid = nblocks;
+    if (host && grid > 152 * 2) grid = 152 * 2;
+    if (grid > 0x7fffffff) grid = 0x7fffffff;
+    pack_upper_bf16_kernel<<<(unsigned)grid, 256, 0, s>>>(A, n, lda, Ab, nbc, vec, part, nblocks);
     return cudaGetLastError();
 }
 

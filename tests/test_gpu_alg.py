@@ -167,6 +167,34 @@ def test_output_modes_and_host_api(ctx):
     assert al > 0
 
 
+@pytest.mark.parametrize("prec", [ps.PREC_FP32, ps.PREC_BF16, ps.PREC_TF32])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_api_reads_only_the_upper_triangle(ctx, prec, pinned):
+    # pinned A is read over the host link (upper triangle only: a poisoned
+    # lower triangle changes nothing); pageable A is copied whole; both equal
+    # the device-buffer call; ld larger than n
+    n, k, p, q, seed = 777, 30, 10, 1, 5
+    Vr, lam, A32 = _A("small", n)
+    opts = ps.make_opts(prec=prec)
+    ref = _run(ctx, A32, k, p, q, seed, opts=opts)
+    ref2 = _run(ctx, A32, k, p, q, seed, alg=2, opts=opts)
+    Apad = np.full((n, n + 5), np.nan, dtype=np.float32)
+    Apad[:, :n] = np.triu(A32) + np.tril(np.full((n, n), np.nan, dtype=np.float32), -1)
+    Ah = torch.from_numpy(Apad)[:, :n]
+    if pinned:
+        Ah = torch.from_numpy(Apad).pin_memory()[:, :n]
+    Ph = torch.empty(n, n)
+    if pinned:
+        Ph = Ph.pin_memory()
+    rk = ctx.alg1_host(Ah, k, p, q, seed, P=Ph, opts=opts)
+    assert rk == ref["rank"]
+    tol = 1e-5 if prec == ps.PREC_FP32 else 2e-3
+    assert _rel(Ph.numpy().astype(np.float64), ref["P"]) <= tol
+    rk2, al = ctx.alg2_host(Ah, k, p, q, seed, P=Ph, opts=opts)
+    assert al > 0 and np.all(np.isfinite(Ph.numpy()))
+    assert _rel(Ph.numpy().astype(np.float64), ref2["P"]) <= tol
+
+
 def test_edge_cases(ctx, oracle_lib):
     # n = 1
     A = np.array([[-2.0]], dtype=np.float32)
