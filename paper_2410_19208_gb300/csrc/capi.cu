@@ -329,16 +329,16 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
                                                    ws.pv0, ws.pv1, sc, ws.counter, sc + SC_SIGMA1,
                                                    ctx->d_status),
-                       opts.N + 3);
+                       2 * opts.N + 4);
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 4u,
                                                    sc + SC_SIGMA1, ws.pv0, ws.pv1, sc, ws.counter,
                                                    sc + SC_SIGMA2, ctx->d_status),
-                       opts.N + 3);
+                       2 * opts.N + 4);
             } else {
                 PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
-                                              sc, ws.counter, sc + SC_SIGMA1), opts.N + 3);
+                                              sc, ws.counter, sc + SC_SIGMA1), 2 * opts.N + 4);
                 PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0,
-                                              ws.pv1, sc, ws.counter, sc + SC_SIGMA2), opts.N + 3);
+                                              ws.pv1, sc, ws.counter, sc + SC_SIGMA2), 2 * opts.N + 4);
             }
         }
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
@@ -990,9 +990,9 @@ int psdproj_min_eig(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, i
     double *sc = ws.scal;
     stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
     PSD_KL(launch_power_iteration(s, dA, n, lda, N, seed, 3u, nullptr, ws.pv0, ws.pv1, sc,
-                                  ws.counter, sc + SC_SIGMA1), N + 3);
+                                  ws.counter, sc + SC_SIGMA1), 2 * N + 4);
     PSD_KL(launch_power_iteration(s, dA, n, lda, N, seed, 4u, sc + SC_SIGMA1, ws.pv0, ws.pv1, sc,
-                                  ws.counter, sc + SC_SIGMA2), N + 3);
+                                  ws.counter, sc + SC_SIGMA2), 2 * N + 4);
     PSD_KL(launch_alpha_finish(s, sc + SC_SIGMA1, sc + SC_SIGMA2, 0.0, d_alpha, sc + SC_SHIFT,
                                ws.ints + IN_INFO), 1);
     if (d_sigma1)

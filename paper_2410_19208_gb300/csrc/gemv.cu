@@ -4,10 +4,10 @@
 // triangle only, in 32 x 128 tiles.  A thread block owns a segment of one
 // block row: the row sums accumulate in registers, the transposed
 // contributions of each tile are summed over the block's 8 warps and added
-// with atomics.  The last block to finish (atomic ticket) forms ||w|| in
-// FP64, stores the scale 1/||w|| that the next product applies on load,
-// clears the other vector for the next product, and resets the ticket.
-// sigma = ||A v|| after the N normalised steps is written to *d_sigma.
+// with atomics.  A small kernel after each product (pi_norm_kernel) forms
+// ||w|| in FP64, stores the scale 1/||w|| that the next product applies on
+// load and clears the other vector for the next product.  sigma = ||A v||
+// after the N normalised steps is written to *d_sigma.
 #include "ctx.h"
 #include "tc_common.cuh"
 
@@ -25,15 +25,12 @@ constexpr int NTW = 256;
 // partial sums stay in registers until the segment ends (one barrier).
 __global__ void __launch_bounds__(NTW)
 sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
-                const float *__restrict__ x, float *__restrict__ y, float *__restrict__ other,
-                double *scal, unsigned *counter, const double *d_shift_neg, double *d_sigma,
-                unsigned nactive, int vec)
+                const float *__restrict__ x, float *__restrict__ y, const double *scal,
+                const double *d_shift_neg, int vec)
 {
     __shared__ float colsum[8][SEGW * TCW];
-    __shared__ double red[NTW / 32];
-    __shared__ bool s_last;
     // grid: x = segment within the block row, y = block row; segments past
-    // the end of a row exit at once (and take no completion ticket)
+    // the end of a row exit at once
     const int I = blockIdx.y;
     const int64_t row0 = (int64_t)I * TRW;
     const int tiles = (int)((n - row0 + TCW - 1) / TCW);
@@ -139,31 +136,6 @@ sym_gemv_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
         }
     }
 
-    // ticket: the last block finishes the product
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == nactive - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += NTW) {
-        const double v = (double)__ldcg(&y[i]);
-        acc += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < NTW / 32; ++w) s += red[w];
-        const double nrm = sqrt(s);
-        scal[1] = nrm;
-        scal[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
-        if (d_sigma) *d_sigma = nrm;
-        *counter = 0u;
-    }
-    for (int64_t i = threadIdx.x; i < n; i += NTW) other[i] = 0.0f;
 }
 
 // The same product on the tiled BF16 image A' of the block upper triangle
@@ -197,18 +169,15 @@ __device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
 
 __global__ void __launch_bounds__(gt::NTG, gt::CTAS_PER_SM)
 sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64_t tiles,
-                      const float *__restrict__ x, float *__restrict__ y, float *__restrict__ other,
-                      double *scal, unsigned *counter, const double *d_shift_neg, double *d_sigma,
-                      int *d_status)
+                      const float *__restrict__ x, float *__restrict__ y, const double *scal,
+                      const double *d_shift_neg, int *d_status)
 {
     using namespace tc;
     extern __shared__ __align__(1024) uint8_t smt[];
     __shared__ uint64_t full[gt::STAGES], empty[gt::STAGES];
     __shared__ float colred[2][8][PSD_TILE_N];
-    __shared__ double red[gt::NTG / 32];
     __shared__ int s_abort;       // any role gave up: stop waiting
     __shared__ int s_cabort;      // compute warps: written before, read after their barrier
-    __shared__ bool s_last;
     const int nbc = nbr * PSD_TILE_R;
     const int64_t t0 = tiles * blockIdx.x / gridDim.x;
     const int64_t t1 = tiles * (blockIdx.x + 1) / gridDim.x;
@@ -372,31 +341,48 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
         }
     }
 
-    // ticket: the last CTA finishes the product
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+}
+
+// ||y|| of a finished product and the clearing of the next product's output
+// (the previous input, no longer read), as a kernel of its own after the
+// product: each block sums a slice in FP64 into partial[block], the last
+// block to finish (ticket) adds the partials and writes scal[0] = 1/||y||,
+// scal[1] = ||y|| and, when asked, *d_sigma = ||y||.  (Done by the product's
+// last CTA alone this took several times longer.)
+constexpr int PI_NORM_BLOCKS = 8;
+__global__ void __launch_bounds__(1024)
+pi_norm_kernel(const float *__restrict__ y, float *__restrict__ other, int64_t n, double *scal,
+               unsigned *counter, double *partial, double *d_sigma)
+{
+    __shared__ double red[32];
+    __shared__ bool last;
     double acc = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += gt::NTG) {
-        const double v = (double)__ldcg(&y[i]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)y[i];
         acc += v * v;
+        other[i] = 0.0f;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) red[warp] = acc;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double sacc = 0.0;
-        for (int w = 0; w < gt::NTG / 32; ++w) sacc += red[w];
-        const double nrm = sqrt(sacc);
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        partial[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(&partial[b]);
+        const double nrm = sqrt(t);
         scal[1] = nrm;
         scal[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
         if (d_sigma) *d_sigma = nrm;
         *counter = 0u;
     }
-    for (int64_t i = threadIdx.x; i < n; i += gt::NTG) other[i] = 0.0f;
 }
 
 __global__ void pi_init_kernel(double *scal, float *v1, int64_t n)
@@ -483,18 +469,16 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = (int)((n + TRW - 1) / TRW);
-    int64_t blocks = 0;
-    for (int I = 0; I < nb; ++I) {
-        const int tiles = (int)((n - (int64_t)I * TRW + TCW - 1) / TCW);
-        blocks += (tiles + SEGW - 1) / SEGW;
-    }
     const int maxseg = (int)(((n + TCW - 1) / TCW + SEGW - 1) / SEGW);  // row 0 has the most
     const dim3 grid((unsigned)maxseg, (unsigned)nb);
     const int vec = ((lda % 4) == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     float *in = v0, *out = v1;
     for (int it = 0; it <= N; ++it) {
-        sym_gemv_kernel<<<grid, NTW, 0, s>>>(A, n, lda, in, out, in, scal, counter, d_shift_neg,
-                                             it == N ? d_sigma : nullptr, (unsigned)blocks, vec);
+        sym_gemv_kernel<<<grid, NTW, 0, s>>>(A, n, lda, in, out, scal, d_shift_neg, vec);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        pi_norm_kernel<<<PI_NORM_BLOCKS, 1024, 0, s>>>(out, in, n, scal, counter, scal + 8,
+                                                       it == N ? d_sigma : nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         float *t = in; in = out; out = t;
@@ -524,9 +508,12 @@ cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint
     if ((int64_t)grid > tiles) grid = (int)tiles;
     float *in = v0, *out = v1;
     for (int it = 0; it <= N; ++it) {
-        sym_gemv_tiles_kernel<<<grid, gt::NTG, gt::SMEM, s>>>(Ab, n, nbr, tiles, in, out, in, scal, counter,
-                                                              d_shift_neg, it == N ? d_sigma : nullptr,
+        sym_gemv_tiles_kernel<<<grid, gt::NTG, gt::SMEM, s>>>(Ab, n, nbr, tiles, in, out, scal, d_shift_neg,
                                                               d_status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        pi_norm_kernel<<<PI_NORM_BLOCKS, 1024, 0, s>>>(out, in, n, scal, counter, scal + 8,
+                                                       it == N ? d_sigma : nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         float *t = in; in = out; out = t;
