@@ -25,8 +25,9 @@
 // (scalar atomics when Y is not 16-byte aligned with ld % 4 == 0).
 //
 // Warp roles (256 threads, one CTA per SM, persistent over a cost-balanced
-// range of the tiles in row-major order): warp 0 issues the copies, warp 1 owns TMEM and
-// issues tcgen05.mma from one thread, warps 4-7 drain TMEM.  Every mbarrier
+// range of the tiles in row-major order): warp 0 issues the copies, warp 1
+// owns TMEM and issues the row-product MMAs, warp 2 the transposed-product
+// MMAs (one thread each), warps 4-7 drain TMEM.  Every mbarrier
 // wait is bounded; on a timeout the CTA records PSDPROJ_ETIMEOUT, unwinds and
 // frees its TMEM.
 #include <cuda_bf16.h>
@@ -179,7 +180,7 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGE; ++s) {
             mbar_init(&B.full[s], 1);
-            mbar_init(&B.empty[s], 1);
+            mbar_init(&B.empty[s], 2);    // both MMA threads
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&B.d2full[b], 1);
@@ -189,7 +190,7 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
         mbar_init(&B.emptyXI, 1);
         mbar_init(&B.d1full, 1);
         mbar_init(&B.d1empty, 4);
-        mbar_init(&B.mmadone, 1);
+        mbar_init(&B.mmadone, 2);
         B.abort = 0;
         fence_proxy_async_smem();
         prefetch_tmap(&tmX);
@@ -234,9 +235,15 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 mbar_wait(&B.full[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1), abort, WAIT_LIMIT);
             if (xi_uses > 0) mbar_wait(&B.fullXI, (uint32_t)((xi_uses - 1) & 1), abort, WAIT_LIMIT);
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 || warp == 2) {
         // ------------------------------------------------------------ MMA
+        // two issuing threads: warp 1 the four long row-product MMAs (P1,
+        // D1), warp 2 the sixteen short transposed-product MMAs (P2, D2).
+        // tcgen05.mma issue blocks once the tensor pipe's queue is full, so
+        // while one thread does its bookkeeping the other's MMAs keep the
+        // pipe busy; each commits its own MMAs (a stage is free after both).
         if (lane == 0) {
+            const bool p1 = (warp == 1);
             const uint32_t id1 = idesc_bf16(128, BM, 0, 0);
             const uint32_t id2 = idesc_bf16(128, BN, 0, 1);
             int I = I0, J = J0, curI = -1, seg = 0;
@@ -246,8 +253,9 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 const bool first = (I != curI);
                 const bool last = (J == P.nbc - 1) || (t + 1 == t1);
                 if (first) {
-                    if (!mbar_wait(&B.fullXI, seg & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                    if (!mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                    const bool ok = p1 ? mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT)
+                                       : mbar_wait(&B.fullXI, seg & 1, abort, WAIT_LIMIT);
+                    if (!ok) { fail(B, P.d_status); break; }
                     curI = I;
                 }
                 const int s = (int)(it % NSTAGE);
@@ -255,42 +263,40 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
                 if (!mbar_wait(&B.full[s], us & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                if (!p1 && !mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
                 tc_fence_after();
                 const uint32_t a_tile = smem_u32(sm + OFF_A + s * STAGE);
-                const uint32_t xj = a_tile + A_BYTES;
-                const uint32_t xi = smem_u32(sm + OFF_XI);
-                // P2 first: its sixteen short MMAs, then P1's four long ones,
-                // which stay queued on the tensor pipe while this thread does
-                // the next tile's bookkeeping (tcgen05.mma issue blocks once
-                // the pipe's queue is full)
-                // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows)
+                if (p1) {
+                    // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns)
+                    const uint32_t xj = a_tile + A_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < BM / 16; ++kk) {
-                    const uint64_t ad = sdesc_sw128(xi + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
-                    const uint64_t bd = sdesc_sw128(a_tile + kk * 2048, 16384, 1024);
-                    mma_bf16_ss(tmem + D2_COL + BN * b, ad, bd, id2, kk > 0 ? 1u : 0u);
-                }
-                // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns)
+                    for (int kk = 0; kk < BN / 16; ++kk) {
+                        const uint64_t ad = sdesc_sw128(xj + kk * 32, 16, 1024);
+                        const uint64_t bd = sdesc_sw128(a_tile + kk * 32, 16, 1024);
+                        mma_bf16_ss(tmem + D1_COL, ad, bd, id1, (!first || kk > 0) ? 1u : 0u);
+                    }
+                } else {
+                    // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows)
+                    const uint32_t xi = smem_u32(sm + OFF_XI);
 #pragma unroll
-                for (int kk = 0; kk < BN / 16; ++kk) {
-                    const uint64_t ad = sdesc_sw128(xj + kk * 32, 16, 1024);
-                    const uint64_t bd = sdesc_sw128(a_tile + kk * 32, 16, 1024);
-                    mma_bf16_ss(tmem + D1_COL, ad, bd, id1, (!first || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < BM / 16; ++kk) {
+                        const uint64_t ad = sdesc_sw128(xi + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
+                        const uint64_t bd = sdesc_sw128(a_tile + kk * 2048, 16384, 1024);
+                        mma_bf16_ss(tmem + D2_COL + BN * b, ad, bd, id2, kk > 0 ? 1u : 0u);
+                    }
                 }
                 issued = true;
                 mma_commit(&B.empty[s]);
-                mma_commit(&B.d2full[b]);
+                if (!p1) mma_commit(&B.d2full[b]);
                 if (last) {
-                    mma_commit(&B.d1full);
-                    mma_commit(&B.emptyXI);
+                    mma_commit(p1 ? &B.d1full : &B.emptyXI);
                     ++seg;
                 }
             }
             if (issued) {
-                // all MMAs of this CTA complete before TMEM is released
+                // all MMAs of this CTA (both threads) complete before TMEM is released
                 mma_commit(&B.mmadone);
-                mbar_wait(&B.mmadone, 0, abort, WAIT_LIMIT);
+                if (p1) mbar_wait(&B.mmadone, 0, abort, WAIT_LIMIT);
             }
         }
     } else if (warp >= 4) {
