@@ -19,8 +19,10 @@
 //   P2  D2^T (m x 64)   = X_I^T (m x BM) . A'_IJ    (B operand MN-major)
 // with M = 128 rows of X^T (m <= 128; rows m..127 are zero).  D1^T
 // accumulates over the run of tiles a CTA owns in one block row and is
-// flushed once (with the shift term when the run holds the diagonal block);
-// D2^T is double-buffered in TMEM and added to Y after every tile.  Both are
+// flushed once; D2^T is double-buffered in TMEM and added to Y after every
+// tile.  The shift term is not in the pass: the sweep that converts X to
+// BF16 starts Y at shift X (or adds it), so a run that holds a diagonal
+// block drains D1 without extra global reads.  Both are
 // added by TMA bulk reduce-add from a swizzled 32 x 32 staging box per warp
 // (scalar atomics when Y is not 16-byte aligned with ld % 4 == 0).
 //
@@ -78,11 +80,8 @@ struct Params {
     int m;
     int nbr, nbc;
     int64_t tiles;
-    const float *X;
-    int64_t ldx;
     float *Y;
     int64_t ldy;
-    const double *d_shift;
     int *d_status;
     int tma_y;          // Y reduced by TMA (aligned Y); else scalar atomics
 };
@@ -160,7 +159,7 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     // about SEGC tiles (D1 drained, X_I reloaded, the pipeline refilled), so
     // CTAs whose range crosses many short rows near the end get fewer tiles
     auto first_tile = [&](int64_t b) -> int64_t {
-        constexpr int64_t SEGC = 2;
+        constexpr int64_t SEGC = 4;
         const int64_t target = (P.tiles + SEGC * P.nbr) * b / gridDim.x;
         int64_t lo = 0, hi = P.tiles;                // smallest t with cost(t) >= target
         while (lo < hi) {
@@ -302,14 +301,10 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     } else if (warp >= 4) {
         // ------------------------------------------------------- epilogue
         const int q = warp & 3;                // TMEM lane quarter of this warp
-        const int c = 32 * q + lane;           // column of X / Y held by this thread
         uint8_t *stg = sm + OFF_STG + q * STG_BYTES;
-        const double shift = P.d_shift ? *P.d_shift : 0.0;
         int I = I0, J = J0, seg = 0;
-        bool has_diag = false;
         int64_t it = 0;
         for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
-            if (J == R * I) has_diag = true;   // this run holds the diagonal block's first tile
             const bool last = (J == P.nbc - 1) || (t + 1 == t1);
             const int b = (int)(it & 1);
             const uint32_t ub = (uint32_t)(it >> 1);
@@ -341,20 +336,12 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 for (int ch = 0; ch < BM / 32; ++ch) {
                     float v[32];
                     tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + D1_COL + 32 * ch, v);
-                    const int64_t rb = r0 + 32 * ch;
-                    if (has_diag && shift != 0.0 && c < P.m) {
-                        const float *xc = P.X + (int64_t)c * P.ldx;
-#pragma unroll
-                        for (int e = 0; e < 32; ++e)
-                            if (rb + e < P.n) v[e] = fmaf((float)shift, xc[rb + e], v[e]);
-                    }
-                    flush32(P, &tmY, stg, q, lane, rb, v);
+                    flush32(P, &tmY, stg, q, lane, r0 + 32 * ch, v);
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&B.d1empty);
                 ++seg;
-                has_diag = false;
             }
         }
         if (lane == 0 && P.tma_y) bulk_wait_all();
@@ -368,20 +355,28 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
 
 // X (FP32, column-major) -> BF16 image used by the TMA loads of the pass:
 // part 0 = bf16(x) (the high part), part 1 = bf16(x - bf16(x)) (the low part
-// of the split-BF16 form).  Yz (may be NULL): Y to clear in the same sweep
-// (X and Y are different buffers), saving the separate memset launch.
-__global__ void to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t n, int m,
-                               __nv_bfloat16 *__restrict__ H, int64_t ldh, int part, float *__restrict__ Yz,
-                               int64_t ldy)
+// of the split-BF16 form).  The same sweep starts Y for the pass (Y is a
+// different buffer): y_mode 1 sets Y = shift X, y_mode 2 adds shift X to Y,
+// y_mode 0 leaves Y alone; shift = *d_shift, 0 when d_shift is NULL.  Grid:
+// x over 1024-row chunks, y over the m columns (coalesced, no division).
+__global__ void __launch_bounds__(256)
+to_bf16_kernel(const float *__restrict__ X, int64_t ldx, int64_t n, __nv_bfloat16 *__restrict__ H, int64_t ldh,
+               int part, float *__restrict__ Y, int64_t ldy, const double *__restrict__ d_shift, int y_mode)
 {
-    const int64_t total = n * (int64_t)m;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = e / n, i = e - c * n;
-        const float x = X[c * ldx + i];
+    const int c = blockIdx.y;
+    const float *xc = X + (int64_t)c * ldx;
+    __nv_bfloat16 *hc = H + (int64_t)c * ldh;
+    float *yc = Y + (int64_t)c * ldy;
+    const float shift = d_shift ? (float)*d_shift : 0.0f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = (int64_t)blockIdx.x * 1024 + r * 256 + threadIdx.x;
+        if (i >= n) break;
+        const float x = xc[i];
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        H[c * ldh + i] = part ? __float2bfloat16_rn(x - __bfloat162float(hi)) : hi;
-        if (Yz) Yz[c * ldy + i] = 0.0f;
+        hc[i] = part ? __float2bfloat16_rn(x - __bfloat162float(hi)) : hi;
+        if (y_mode == 1) yc[i] = shift * x;
+        else if (y_mode == 2) yc[i] = fmaf(shift, x, yc[i]);
     }
 }
 
@@ -486,13 +481,13 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
     auto encode = get_encode();
     if (!encode) return cudaErrorNotSupported;
 
-    // BF16 image of X (rows n, columns m; TMA fills the rest with zeros)
-    {
-        const int64_t total = n * (int64_t)m;
-        int blocks = (int)((total + 255) / 256);
-        if (blocks > 4096) blocks = 4096;
-        to_bf16_kernel<<<blocks, 256, 0, s>>>(X, ldx, n, m, reinterpret_cast<__nv_bfloat16 *>(Xh), ldh, x_part,
-                                              accumulate ? nullptr : Y, ldy);
+    // BF16 image of X (rows n, columns m; TMA fills the rest with zeros);
+    // Y starts at shift X (accumulate = 0) or gains it (accumulate = 1)
+    if (n > 0) {
+        const int y_mode = accumulate ? (d_shift ? 2 : 0) : 1;
+        const dim3 grid((unsigned)((n + 1023) / 1024), (unsigned)m);
+        to_bf16_kernel<<<grid, 256, 0, s>>>(X, ldx, n, reinterpret_cast<__nv_bfloat16 *>(Xh), ldh, x_part, Y, ldy,
+                                            d_shift, y_mode);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -513,11 +508,8 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
     P.nbr = (int)((n + BM - 1) / BM);
     P.nbc = P.nbr * R;
     P.tiles = psd_tile_count(n);
-    P.X = X;
-    P.ldx = ldx;
     P.Y = Y;
     P.ldy = ldy;
-    P.d_shift = d_shift;
     P.d_status = d_status;
     P.tma_y = ((ldy % 4) == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0);
     CUtensorMap tmY;

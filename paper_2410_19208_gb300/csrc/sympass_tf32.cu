@@ -24,7 +24,8 @@
 // and issues tcgen05.mma from one thread, warps 4-7 drain TMEM.  The
 // accumulator of a run of tiles in one block row is double-buffered in TMEM
 // (2 x 256 columns) and added to Y by TMA bulk reduce-add (scalar atomics when
-// Y is not 16-byte aligned with ld % 4 == 0).  Every mbarrier wait is
+// Y is not 16-byte aligned with ld % 4 == 0).  The sweep that rounds X to
+// TF32 starts Y at shift X, so the pass itself has no shift term.  Every mbarrier wait is
 // bounded; on a timeout the CTA records PSDPROJ_ETIMEOUT, unwinds and frees
 // its TMEM.
 #include <cstring>
@@ -85,11 +86,8 @@ struct Params {
     int m;
     int nbc;
     int64_t tiles;
-    const float *X;
-    int64_t ldx;
     float *Y;
     int64_t ldy;
-    const double *d_shift;
     int *d_status;
     int tma_y;
 };
@@ -236,13 +234,10 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
     } else if (warp >= 4) {
         // ------------------------------------------------------- epilogue
         const int q = warp & 3;                // TMEM lane quarter of this warp
-        const int c = 32 * q + lane;           // column of X / Y held by this thread
         uint8_t *stg = sm + OFF_STG + q * STG_BYTES;
-        const double shift = P.d_shift ? *P.d_shift : 0.0;
         int seg = 0;
         for (int64_t t = t0; t < t1; ++seg) {
             const int64_t I = t / P.nbc;
-            const bool has_diag = (t % P.nbc) == 0;      // the run holds the row's first tile
             const int64_t row_end = (I + 1) * P.nbc;
             const int b = seg & 1;
             {
@@ -257,14 +252,7 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
             for (int ch = 0; ch < BM / 32; ++ch) {
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(BM * b + 32 * ch), v);
-                const int64_t rb = r0 + 32 * ch;
-                if (has_diag && shift != 0.0 && c < P.m) {
-                    const float *xc = P.X + (int64_t)c * P.ldx;
-#pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        if (rb + e < P.n) v[e] = fmaf((float)shift, xc[rb + e], v[e]);
-                }
-                flush32(P, &tmY, stg, q, lane, rb, v);
+                flush32(P, &tmY, stg, q, lane, r0 + 32 * ch, v);
             }
             tc_fence_before();
             __syncwarp();
@@ -281,16 +269,22 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
 }
 
 // X (FP32, column-major) -> X rounded to TF32 in the aligned buffer that the
-// pass loads by TMA; Y (a different buffer) is cleared in the same sweep
-__global__ void to_tf32_kernel(const float *__restrict__ X, int64_t ldx, int64_t n, int m,
-                               float *__restrict__ Xf, int64_t ldf, float *__restrict__ Y, int64_t ldy)
+// pass loads by TMA; Y (a different buffer) starts at shift X in the same
+// sweep (shift = *d_shift, 0 when d_shift is NULL).  Grid: x over 1024-row
+// chunks, y over the m columns.
+__global__ void __launch_bounds__(256)
+to_tf32_kernel(const float *__restrict__ X, int64_t ldx, int64_t n, float *__restrict__ Xf, int64_t ldf,
+               float *__restrict__ Y, int64_t ldy, const double *__restrict__ d_shift)
 {
-    const int64_t total = n * (int64_t)m;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = e / n, i = e - c * n;
-        Xf[c * ldf + i] = tf32_rna(X[c * ldx + i]);
-        Y[c * ldy + i] = 0.0f;
+    const int c = blockIdx.y;
+    const float shift = d_shift ? (float)*d_shift : 0.0f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int64_t i = (int64_t)blockIdx.x * 1024 + r * 256 + threadIdx.x;
+        if (i >= n) break;
+        const float x = X[(int64_t)c * ldx + i];
+        Xf[(int64_t)c * ldf + i] = tf32_rna(x);
+        Y[(int64_t)c * ldy + i] = shift * x;
     }
 }
 
@@ -377,12 +371,6 @@ bool encode_tall(CUtensorMap *tm, const float *base, int64_t n, int m, int64_t l
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int grid_for(int64_t total)
-{
-    const int64_t blocks = (total + 255) / 256;
-    return (int)(blocks > 4096 ? 4096 : (blocks < 1 ? 1 : blocks));
-}
-
 }  // namespace
 
 cudaError_t launch_pack_tf32(cudaStream_t s, const float *A, int64_t n, int64_t lda, float *At)
@@ -406,7 +394,9 @@ cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, 
     if ((ldf % 4) != 0 || (reinterpret_cast<uintptr_t>(Xf) & 15) != 0 || ldf < n) return cudaErrorNotSupported;
     if (!tensor_map_encoder()) return cudaErrorNotSupported;
 
-    to_tf32_kernel<<<grid_for(n * (int64_t)m), 256, 0, s>>>(X, ldx, n, m, Xf, ldf, Y, ldy);
+    if (n > 0)
+        to_tf32_kernel<<<dim3((unsigned)((n + 1023) / 1024), (unsigned)m), 256, 0, s>>>(X, ldx, n, Xf, ldf, Y, ldy,
+                                                                                  d_shift);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // X_J^T: 32 rows of X (128 bytes) x 128 columns; columns >= m read as zero
@@ -418,11 +408,8 @@ cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, 
     P.m = m;
     P.nbc = (int)((n + BM - 1) / BM) * (BM / BN);
     P.tiles = psd_tile32_count(n);
-    P.X = X;
-    P.ldx = ldx;
     P.Y = Y;
     P.ldy = ldy;
-    P.d_shift = d_shift;
     P.d_status = d_status;
     P.tma_y = ((ldy % 4) == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0);
     CUtensorMap tmY;
