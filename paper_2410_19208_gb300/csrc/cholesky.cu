@@ -3,9 +3,11 @@
 //   of the raw product can be ill-conditioned; FP32 for the second, whose
 //   Gram is I + O(eps)), with the dependent-column rule; R^-1 in FP32; and
 //   Q = Y R^-1 (a tall x small product on the CUDA cores).
-// The factorization is right-looking in one thread block with two block
-// barriers per column; each thread owns a fixed set of upper-triangle
-// entries and every thread computes the pivot itself.  Double-float numbers
+// For m <= 128 the factorization is blocked (16-column blocks, three block
+// barriers per block, the diagonal block in one warp's registers) and R^-1
+// is formed blockwise (cholesky_blocked_kernel); larger m use a right-looking
+// kernel in global memory with one barrier per column, each thread owning a
+// fixed set of upper-triangle entries.  Double-float numbers
 // are unevaluated sums hi + lo of two FP32 values (about 48 significant
 // bits; Dekker's two-product by FMA and Knuth's two-sum), which keeps the
 // O(m^3) update off the FP64 pipe (about 2 FMA/clk/SM on this GPU).  Sizes
@@ -66,11 +68,16 @@ template <> struct num<float> {
     __device__ static float zero() { return 0.0f; }
     __device__ static float mul(float a, float b) { return a * b; }
     __device__ static float fms(float u, float a, float b) { return fmaf(-a, b, u); }
-    // r = sqrt(p), inv = 1 / r
+    // inv = 1 / sqrt(p) from the hardware estimate and one Newton step,
+    // y <- y (3 - p y^2) / 2 (error about 1 ulp), r = p inv: the root is on
+    // the factorization's critical path, where correctly rounded sqrt and
+    // division cost several times more latency
     __device__ static void root(float p, float &r, float &inv)
     {
-        r = sqrtf(p);
-        inv = 1.0f / r;
+        float y = rsqrtf(p);
+        y = y * fmaf(-0.5f * p, y * y, 1.5f);
+        inv = y;
+        r = p * y;
     }
     __device__ static float one() { return 1.0f; }
 };
@@ -99,19 +106,22 @@ template <> struct num<df> {
     __device__ static df zero() { return {0.0f, 0.0f}; }
     __device__ static df mul(df a, df b) { return df_mul(a, b); }
     __device__ static df fms(df u, df a, df b) { return df_sub(u, df_mul(a, b)); }
-    // one Newton step from the FP32 root: r = x + (p - x^2) / (2x); then
-    // inv = q + q (1 - q r) from q = 1 / r.hi
+    // from y ~ 1/sqrt(p.hi) (hardware estimate + one FP32 Newton step,
+    // about 1 ulp) and x = p.hi y ~ sqrt(p.hi), one Newton step in
+    // double-float for each: r = x + (p - x^2) y / 2, inv = y + y (1 - y r);
+    // each doubles the ~23 correct bits (about 46 bits)
     __device__ static void root(df p, df &r, df &inv)
     {
-        const float x = sqrtf(p.hi);
+        float y = rsqrtf(p.hi);
+        y = y * fmaf(-0.5f * p.hi, y * y, 1.5f);
+        const float x = p.hi * y;
         const float x2 = x * x;
         const df sq = {x2, fmaf(x, x, -x2)};
         const df dlt = df_sub(p, sq);
-        r = quick_two_sum(x, dlt.hi / (2.0f * x));
-        const float q = 1.0f / r.hi;
-        const df qr = df_mul({q, 0.0f}, r);
+        r = quick_two_sum(x, dlt.hi * (0.5f * y));
+        const df qr = df_mul({y, 0.0f}, r);
         const df res = df_sub({1.0f, 0.0f}, qr);
-        inv = quick_two_sum(q, res.hi * q);
+        inv = quick_two_sum(y, res.hi * y);
     }
     __device__ static df one() { return {1.0f, 0.0f}; }
 };
@@ -295,6 +305,267 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
     }
 }
 
+// ---- blocked factorization for m <= SMEM_M -------------------------------
+// The same R and the same dependent-column rule, in blocks of NB = 16
+// columns with three block barriers per block instead of one per column:
+//   (1) one warp factors the diagonal block column by column (pivot test,
+//       root, the block's part of row j of R, update of the rest of the
+//       diagonal block);
+//   (2) one thread per later column k finishes the block's 16 rows of R in
+//       that column (forward substitution down the rows);
+//   (3) the trailing upper triangle loses the block's contribution,
+//       U(i,k) -= sum_j R(j,i) R(j,k), in 4 x 4 register tiles.
+// R^-1 (FP32, from the FP32 copy of R) then comes blockwise: each diagonal
+// block inverted by one warp (a lane per column), the off-diagonal blocks
+// from the last block row up,
+//   X(b, c) = -X(b, b) sum_{d > b} R(b, d) X(d, c),
+// two barriers per block row.
+constexpr int NB = 16;
+constexpr int NTB = 512;
+
+// warp shuffle of a number (width: the lane group)
+__device__ __forceinline__ float shfl_num(float v, int src, int width = 32)
+{
+    return __shfl_sync(0xffffffffu, v, src, width);
+}
+
+__device__ __forceinline__ df shfl_num(df v, int src, int width = 32)
+{
+    return {__shfl_sync(0xffffffffu, v.hi, src, width), __shfl_sync(0xffffffffu, v.lo, src, width)};
+}
+
+template <typename T>
+size_t blocked_smem(int m)
+{
+    const size_t ldu = (size_t)m + 1;
+    return sizeof(T) * m * ldu + sizeof(float) * m * ldu + sizeof(float) * NB * m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTB, 1)
+cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__ Rinv,
+                        int *__restrict__ dead, int *__restrict__ d_qrank, double tau, int *d_status)
+{
+    using N = num<T>;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int ldu = m + 1;
+    T *U = reinterpret_cast<T *>(smraw);                               // m x ldu, row-major, upper part
+    float *Rf = reinterpret_cast<float *>(U + (size_t)m * ldu);        // FP32 R, m x ldu
+    float *Tmp = Rf + (size_t)m * ldu;                                 // NB x m
+    float *X = reinterpret_cast<float *>(smraw);                       // R^-1, m x ldu (U's bytes, once U is done)
+    __shared__ double s_gmax;
+    __shared__ int s_bad;
+    __shared__ int s_dead[SMEM_M];
+    __shared__ float s_rdinv[SMEM_M];
+    __shared__ T s_inv[SMEM_M];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int e = tid; e < m * m; e += NTB) {
+        const int i = e / m, k = e - (e / m) * m;
+        if (k >= i) U[i * ldu + k] = N::from(G[(int64_t)k * m + i]);
+    }
+    if (tid < 32) {
+        double g = 0.0;
+        int bad = 0;
+        for (int i = tid; i < m; i += 32) {
+            const double v = G[(int64_t)i * m + i];
+            if (!isfinite(v)) bad = 1;
+            else if (v > g) g = v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+            bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        }
+        if (tid == 0) {
+            s_gmax = g;
+            s_bad = bad;
+        }
+    }
+    __syncthreads();
+    if (s_bad && tid == 0) psd_set_status(d_status, PSDPROJ_ENOTFINITE);
+    const float thr = (float)(tau * s_gmax);
+    const bool any = s_gmax > 0.0;
+    const int nblk = (m + NB - 1) / NB;
+
+    for (int b = 0; b < nblk; ++b) {
+        const int j0 = b * NB, j1 = min(j0 + NB, m), w = j1 - j0;
+        // (1) the diagonal block, one warp, in registers: lane c (and its
+        // mirror c + 16) holds column c of the block, col[a] = U(j0+a, j0+c)
+        if (warp == 0) {
+            const int c = lane & 15;
+            T col[NB];
+#pragma unroll
+            for (int a = 0; a < NB; ++a) col[a] = (a <= c && c < w) ? U[(j0 + a) * ldu + j0 + c] : N::zero();
+#pragma unroll
+            for (int a = 0; a < NB; ++a) {
+                if (a < w) {
+                    const int j = j0 + a;
+                    const T piv = shfl_num(col[a], a);
+                    const bool dj = !(N::hi(piv) > thr) || !any;
+                    T r = N::one(), inv = N::one();
+                    if (!dj) N::root(piv, r, inv);
+                    if (c > a) col[a] = dj ? N::zero() : N::mul(col[a], inv);      // R(j, j0+c)
+                    else if (c == a) col[a] = r;
+                    if (!dj) {
+#pragma unroll
+                        for (int i = a + 1; i < NB; ++i) {
+                            const T ri = shfl_num(col[a], i);                      // R(j, j0+i)
+                            if (i <= c && c < w) col[i] = N::fms(col[i], ri, col[a]);
+                        }
+                    }
+                    if (lane == 0) {
+                        s_dead[j] = dj ? 1 : 0;
+                        s_inv[j] = inv;
+                        s_rdinv[j] = N::hi(inv);                                  // 1 / R(j,j) in FP32
+                    }
+                }
+            }
+            if (lane < 16 && c < w) {
+#pragma unroll
+                for (int a = 0; a < NB; ++a)
+                    if (a <= c) {
+                        U[(j0 + a) * ldu + j0 + c] = col[a];
+                        Rf[(j0 + a) * ldu + j0 + c] = N::hi(col[a]);
+                    }
+            }
+        }
+        __syncthreads();
+        // (2) rows j0 .. j1-1 of R in the later columns: 16 lanes per column k,
+        // lane a holding U(j0+a, k), forward substitution down the rows
+        {
+            const int a = lane & 15;
+            T rcol[NB];                               // R(j0+a2, j0+a), a2 < a
+#pragma unroll
+            for (int a2 = 0; a2 < NB; ++a2) rcol[a2] = (a2 < a && a < w) ? U[(j0 + a2) * ldu + j0 + a] : N::zero();
+            const int ncol = m - j1;
+            for (int g = tid >> 4; g < ((ncol + 1) & ~1); g += NTB / 16) {
+                // g runs over an even count so that both half-warps stay in the loop together
+                const int k = j1 + g;
+                const bool act = g < ncol && a < w;
+                T x = act ? U[(j0 + a) * ldu + k] : N::zero();
+#pragma unroll
+                for (int a2 = 0; a2 < NB; ++a2) {
+                    if (a2 < w) {
+                        const int j = j0 + a2;
+                        T v = shfl_num(x, a2, 16);
+                        v = s_dead[j] ? N::zero() : N::mul(v, s_inv[j]);
+                        if (a == a2) x = v;
+                        else if (a > a2) x = N::fms(x, rcol[a2], v);
+                    }
+                }
+                if (act) {
+                    U[(j0 + a) * ldu + k] = x;
+                    Rf[(j0 + a) * ldu + k] = N::hi(x);
+                }
+            }
+        }
+        __syncthreads();
+        // (3) trailing update, 2 x 2 tiles of the upper triangle
+        const int t = m - j1;
+        if (t > 0) {
+            const int nt = (t + 1) >> 1;
+            for (int q = tid; q < nt * nt; q += NTB) {
+                const int ti = q / nt, tk = q - (q / nt) * nt;
+                if (tk < ti) continue;
+                const int i0 = j1 + 2 * ti, k0 = j1 + 2 * tk;
+                T acc[2][2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) {
+                        const int i = i0 + u, k = k0 + v;
+                        acc[u][v] = (i <= k && k < m) ? U[i * ldu + k] : N::zero();
+                    }
+#pragma unroll 4
+                for (int a = 0; a < w; ++a) {
+                    const int j = j0 + a;
+                    T ri[2], rk[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        ri[u] = i0 + u < m ? U[j * ldu + i0 + u] : N::zero();
+                        rk[u] = k0 + u < m ? U[j * ldu + k0 + u] : N::zero();
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u)
+#pragma unroll
+                        for (int v = 0; v < 2; ++v) acc[u][v] = N::fms(acc[u][v], ri[u], rk[v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) {
+                        const int i = i0 + u, k = k0 + v;
+                        if (i <= k && k < m) U[i * ldu + k] = acc[u][v];
+                    }
+            }
+        }
+        __syncthreads();
+    }
+
+    // R^-1 into X (U is no longer read).  (a) diagonal blocks: warp b, lane c
+    // solves R(b,b) x = e_c by back substitution
+    if (warp < nblk) {
+        const int j0 = warp * NB, w = min(NB, m - j0), c = lane;
+        float x[NB];
+#pragma unroll
+        for (int a = 0; a < NB; ++a) x[a] = 0.0f;
+#pragma unroll
+        for (int a = NB - 1; a >= 0; --a) {
+            if (a <= c && a < w && c < w) {
+                float sacc = (a == c) ? 1.0f : 0.0f;
+#pragma unroll
+                for (int q = a + 1; q < NB; ++q)
+                    if (q <= c && q < w) sacc = fmaf(-Rf[(j0 + a) * ldu + j0 + q], x[q], sacc);
+                x[a] = sacc * s_rdinv[j0 + a];
+            }
+        }
+        if (c < w) {
+#pragma unroll
+            for (int a = 0; a < NB; ++a)
+                if (a < w) X[(j0 + a) * ldu + j0 + c] = a <= c ? x[a] : 0.0f;
+        }
+    }
+    __syncthreads();
+    // (b) off-diagonal blocks, last block row first
+    for (int b = nblk - 2; b >= 0; --b) {
+        const int j0 = b * NB, j1 = j0 + NB, ncol = m - j1;
+        // Tmp(a, s) = sum_{q = j1 .. s} R(j0 + a, q) X(q, s)
+        for (int e = tid; e < NB * ncol; e += NTB) {
+            const int a = e / ncol, s = j1 + (e - (e / ncol) * ncol);
+            const float *rr = Rf + (j0 + a) * ldu;
+            float s0 = 0.0f, s1 = 0.0f;
+            int q = j1;
+            for (; q + 1 <= s; q += 2) {
+                s0 = fmaf(rr[q], X[q * ldu + s], s0);
+                s1 = fmaf(rr[q + 1], X[(q + 1) * ldu + s], s1);
+            }
+            if (q <= s) s0 = fmaf(rr[q], X[q * ldu + s], s0);
+            Tmp[a * m + s] = s0 + s1;
+        }
+        __syncthreads();
+        // X(j0 + a, s) = -sum_{a2 >= a} X(j0 + a, j0 + a2) Tmp(a2, s)
+        for (int e = tid; e < NB * ncol; e += NTB) {
+            const int a = e / ncol, s = j1 + (e - (e / ncol) * ncol);
+            const float *xr = X + (j0 + a) * ldu + j0;
+            float acc = 0.0f;
+            for (int a2 = a; a2 < NB; ++a2) acc = fmaf(xr[a2], Tmp[a2 * m + s], acc);
+            X[(j0 + a) * ldu + s] = -acc;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < m * m; e += NTB) {
+        const int j = e / m, r = e - (e / m) * m;          // column j, row r
+        Rinv[(int64_t)j * m + r] = r <= j ? X[r * ldu + j] : 0.0f;
+    }
+    for (int j = tid; j < m; j += NTB) dead[j] = s_dead[j];
+    if (tid == 0 && d_qrank) {
+        int r = 0;
+        for (int j = 0; j < m; ++j) r += !s_dead[j];
+        *d_qrank = r;
+    }
+}
+
 // Z (n x c) = Y (n x m) * B (m x c, column-major ld m).  Block: 64 rows x 64
 // output columns; 256 threads with 4 x 4 micro-tiles.
 constexpr int TR = 64, TC = 64, KC = 64;
@@ -425,33 +696,29 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv,
     const bool sm_path = m <= SMEM_M;
     float *gRf = reinterpret_cast<float *>(gscratch + (size_t)m * m + m);
     cudaError_t e;
-    if (first_pass && sm_path) {
-        const size_t smem = sizeof(df) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1);
-        auto kern = cholesky_kernel<df, SMEM_M / 32>;
+    if (sm_path) {
         // the attribute is process-wide: always the largest size (m = SMEM_M),
         // so that threads launching for different m never undercut each other
-        constexpr size_t smem_max = sizeof(df) * ((size_t)SMEM_M * (SMEM_M + 1) + SMEM_M) +
-                                    sizeof(float) * SMEM_M * (SMEM_M + 1);
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-        if (e != cudaSuccess) return e;
-        kern<<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, nullptr, nullptr, nullptr, d_status);
+        if (first_pass) {
+            e = cudaFuncSetAttribute(cholesky_blocked_kernel<df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)blocked_smem<df>(SMEM_M));
+            if (e != cudaSuccess) return e;
+            cholesky_blocked_kernel<df><<<1, NTB, blocked_smem<df>(m), s>>>(G, m, Rinv, dead, d_qrank, tau,
+                                                                            d_status);
+        } else {
+            e = cudaFuncSetAttribute(cholesky_blocked_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)blocked_smem<float>(SMEM_M));
+            if (e != cudaSuccess) return e;
+            cholesky_blocked_kernel<float><<<1, NTB, blocked_smem<float>(m), s>>>(G, m, Rinv, dead, d_qrank,
+                                                                                  tau, d_status);
+        }
     } else if (first_pass) {
         cholesky_kernel<double, PSD_MAX_M / 32><<<1, NT, 0, s>>>(G, m, Rinv, dead, d_qrank, tau, gscratch,
                                                                  gscratch + (size_t)m * m, gRf, d_status);
     } else {
         float *fs = reinterpret_cast<float *>(gscratch);
-        if (sm_path) {
-            const size_t smem = sizeof(float) * ((size_t)m * (m + 1) + m) + sizeof(float) * m * (m + 1);
-            auto kern = cholesky_kernel<float, SMEM_M / 32>;
-            constexpr size_t smem_max = sizeof(float) * ((size_t)SMEM_M * (SMEM_M + 1) + SMEM_M) +
-                                        sizeof(float) * SMEM_M * (SMEM_M + 1);
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
-            if (e != cudaSuccess) return e;
-            kern<<<1, NT, smem, s>>>(G, m, Rinv, dead, d_qrank, tau, fs, fs + (size_t)m * m, gRf, d_status);
-        } else {
-            cholesky_kernel<float, PSD_MAX_M / 32><<<1, NT, 0, s>>>(G, m, Rinv, dead, d_qrank, tau, fs,
-                                                                   fs + (size_t)m * m, gRf, d_status);
-        }
+        cholesky_kernel<float, PSD_MAX_M / 32><<<1, NT, 0, s>>>(G, m, Rinv, dead, d_qrank, tau, fs,
+                                                               fs + (size_t)m * m, gRf, d_status);
     }
     return cudaGetLastError();
 }
