@@ -267,17 +267,32 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
             __syncthreads();
             continue;
         }
-        // p = bt A22 v (a warp per row, lanes split the row) and v^T p
+        // p = bt A22 v (four lanes per row, lane q summing the columns
+        // k = r0 + q mod 4; the row loop's trip count is the same for every
+        // thread, so the shuffles see full warps) and v^T p
         float pv = 0.0f;
-        for (int i = r0 + warp; i < m; i += NT / 32) {
-            const float *row = A + i * ld;
-            float s0 = 0.0f;
-            for (int k = r0 + lane; k < m; k += 32) s0 = fmaf(row[k], vv[k], s0);
-            s0 = warp_sum(s0);
-            const float p = bt * s0;
-            if (lane == 0) pp[i] = p;
-            pv = fmaf(p, vv[i], pv);
+        for (int base = r0; base < m; base += NT / 4) {
+            const int i = base + (tid >> 2), q = tid & 3;
+            float s0 = 0.0f, s1 = 0.0f;
+            if (i < m) {
+                const float *row = A + i * ld;
+                int k = r0 + q;
+                for (; k + 4 < m; k += 8) {
+                    s0 = fmaf(row[k], vv[k], s0);
+                    s1 = fmaf(row[k + 4], vv[k + 4], s1);
+                }
+                if (k < m) s0 = fmaf(row[k], vv[k], s0);
+            }
+            s0 += s1;
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+            if (i < m && q == 0) {
+                const float p = bt * s0;
+                pp[i] = p;
+                pv = fmaf(p, vv[i], pv);
+            }
         }
+        pv = warp_sum(pv);
         if (lane == 0) red[warp] = pv;
         __syncthreads();
         const float vtp = sum16(red);
