@@ -109,7 +109,12 @@ def _cond_tall(n, m, cond, seed):
 
 
 @pytest.mark.parametrize("n,m,cond", [(1000, 50, 10.0), (4099, 112, 100.0), (300, 7, 1e3),
-                                      (129, 128, 10.0), (600, 200, 10.0)])
+                                      (129, 128, 10.0), (600, 200, 10.0),
+                                      # 16-column block edges of the blocked factorization
+                                      (500, 16, 10.0), (500, 17, 10.0), (700, 33, 100.0),
+                                      (900, 127, 10.0),
+                                      # Gram of condition 1e8: the double-float first pass
+                                      (3000, 110, 1e4)])
 def test_cholqr2_orthonormal_same_range(ctx, oracle_lib, n, m, cond):
     Y = _cond_tall(n, m, cond, seed=m)
     Yd = _tall_from_np(Y)
@@ -149,6 +154,35 @@ def test_cholqr2_dependent_columns(ctx, oracle_lib):
     live = q[:, :8]
     assert np.abs(live.T @ live - np.eye(8)).max() < 2e-5
     assert np.linalg.norm(live @ (live.T @ Qo[:, :8]) - Qo[:, :8]) < 1e-4
+
+
+def test_cholqr2_dependent_columns_at_block_edges(ctx, oracle_lib):
+    """Exactly dependent columns on both sides of the 16-column block edges
+    (the last column of a block, the first of the next) and a zero column
+    at the start of the last block: zero Q columns there, the rest
+    orthonormal with the oracle's range."""
+    n, m = 700, 50
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((n, m)).astype(np.float32)
+    Y[:, 15] = Y[:, 2]
+    Y[:, 16] = 4.0 * Y[:, 9]
+    Y[:, 32] = Y[:, 15] + 0.0
+    Y[:, 48] = 0.0
+    Yd = _tall_from_np(Y)
+    Q = ps.tall_empty(n, m)
+    qr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.cholqr2(Yd, Q, qrank=qr)
+    assert ctx.sync_status() == 0
+    q = _np(Q)
+    Qo, r = oracle_lib.orth(Y.astype(np.float64))
+    dead = [15, 16, 32, 48]
+    assert int(qr.item()) == r == m - len(dead)
+    assert np.all(q[:, dead] == 0)
+    live_idx = [j for j in range(m) if j not in dead]
+    live = q[:, live_idx]
+    assert np.abs(live.T @ live - np.eye(len(live_idx))).max() < 2e-5
+    Qr = Qo[:, np.abs(Qo).sum(axis=0) > 0]
+    assert np.linalg.norm(live @ (live.T @ Qr) - Qr) < 1e-4 * np.sqrt(len(live_idx))
 
 
 def test_cholqr2_nearly_dependent_columns_keep_range(ctx):
