@@ -145,7 +145,6 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
         lay.pv0 = reinterpret_cast<float *>(take(sizeof(float) * ld));
         lay.pv1 = reinterpret_cast<float *>(take(sizeof(float) * ld));
         lay.scal = reinterpret_cast<double *>(take(sizeof(double) * 16));
-        lay.counter = reinterpret_cast<unsigned *>(take(sizeof(unsigned) * 16));
         lay.ints = reinterpret_cast<int *>(take(sizeof(int) * 16));
         lay.picks = reinterpret_cast<int *>(take(sizeof(int) * PSD_MAX_M));
         return off;
@@ -327,18 +326,18 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
             if (bf16) {
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
-                                                   ws.pv0, ws.pv1, sc, ws.counter, sc + SC_SIGMA1,
+                                                   ws.pv0, ws.pv1, sc, sc + SC_SIGMA1,
                                                    ctx->d_status),
                        2 * opts.N + 4);
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 4u,
-                                                   sc + SC_SIGMA1, ws.pv0, ws.pv1, sc, ws.counter,
+                                                   sc + SC_SIGMA1, ws.pv0, ws.pv1, sc,
                                                    sc + SC_SIGMA2, ctx->d_status),
                        2 * opts.N + 4);
             } else {
                 PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
-                                              sc, ws.counter, sc + SC_SIGMA1), 2 * opts.N + 4);
+                                              sc, sc + SC_SIGMA1), 2 * opts.N + 4);
                 PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0,
-                                              ws.pv1, sc, ws.counter, sc + SC_SIGMA2), 2 * opts.N + 4);
+                                              ws.pv1, sc, sc + SC_SIGMA2), 2 * opts.N + 4);
             }
         }
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
@@ -990,9 +989,9 @@ int psdproj_min_eig(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, i
     double *sc = ws.scal;
     stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
     PSD_KL(launch_power_iteration(s, dA, n, lda, N, seed, 3u, nullptr, ws.pv0, ws.pv1, sc,
-                                  ws.counter, sc + SC_SIGMA1), 2 * N + 4);
+                                  sc + SC_SIGMA1), 2 * N + 4);
     PSD_KL(launch_power_iteration(s, dA, n, lda, N, seed, 4u, sc + SC_SIGMA1, ws.pv0, ws.pv1, sc,
-                                  ws.counter, sc + SC_SIGMA2), 2 * N + 4);
+                                  sc + SC_SIGMA2), 2 * N + 4);
     PSD_KL(launch_alpha_finish(s, sc + SC_SIGMA1, sc + SC_SIGMA2, 0.0, d_alpha, sc + SC_SHIFT,
                                ws.ints + IN_INFO), 1);
     if (d_sigma1)

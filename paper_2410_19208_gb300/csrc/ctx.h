@@ -76,7 +76,6 @@ struct psd_workspace {
     // power iteration: two n-vectors (ld floats) and scalars
     float *pv0 = nullptr, *pv1 = nullptr;
     double *scal = nullptr;     // 16 doubles
-    unsigned *counter = nullptr; // 16 counters
     int *ints = nullptr;         // 16 ints (ranks, info)
     int *picks = nullptr;        // PSD_MAX_M ints (SRHT column picks)
 };
@@ -238,13 +237,13 @@ cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t
 cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, int64_t lda,
                                    int N, uint64_t seed, uint32_t stream_id,
                                    const double *d_shift_neg, float *v0, float *v1,
-                                   double *scal, unsigned *counter, double *d_sigma);
+                                   double *scal, double *d_sigma);
 
 // The same on the BF16 image (launch_pack_bf16); v0, v1 16-byte aligned.
 cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t n,
                                         int N, uint64_t seed, uint32_t stream_id,
                                         const double *d_shift_neg, float *v0, float *v1, double *scal,
-                                        unsigned *counter, double *d_sigma, int *d_status);
+                                        double *d_sigma, int *d_status);
 
 cudaError_t launch_alpha_finish(cudaStream_t s, const double *d_s1, const double *d_s2,
                                 double alpha_in, double *d_alpha, double *d_shift,

@@ -345,43 +345,77 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
 
 // ||y|| of a finished product and the clearing of the next product's output
 // (the previous input, no longer read), as a kernel of its own after the
-// product: each block sums a slice in FP64 into partial[block], the last
-// block to finish (ticket) adds the partials and writes scal[0] = 1/||y||,
-// scal[1] = ||y|| and, when asked, *d_sigma = ||y||.  (Done by the product's
-// last CTA alone this took several times longer.)
-constexpr int PI_NORM_BLOCKS = 8;
+// product: one block of 1024 threads, each summing y_i^2 over a strided slice
+// as an unevaluated double-float sum hi + lo (the square split exactly by
+// FMA, Knuth's two-sum per term), the partial sums added in double-float over
+// the warps; the root and its reciprocal by Newton steps in double-float
+// from the FP32 estimate.  Writes scal[0] = 1/||y||, scal[1] = ||y|| and,
+// when asked, *d_sigma = ||y|| (0 and 0 when y = 0).  FP64 arithmetic, a
+// handful of operations per SM and clock on this GPU, is kept out of the
+// sum; this replaced an eight-block FP64 kernel with an atomic ticket
+// (9.8 us -> a few us per product).
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = err + a.lo + b.lo;
+    const float h = s + lo;
+    return {h, lo - (h - s)};
+}
+
 __global__ void __launch_bounds__(1024)
 pi_norm_kernel(const float *__restrict__ y, float *__restrict__ other, int64_t n, double *scal,
-               unsigned *counter, double *partial, double *d_sigma)
+               double *d_sigma)
 {
-    __shared__ double red[32];
-    __shared__ bool last;
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = (double)y[i];
-        acc += v * v;
+    __shared__ dfl red[32];
+    float hi = 0.0f, lo = 0.0f;
+#pragma unroll 4
+    for (int64_t i = threadIdx.x; i < n; i += 1024) {
+        const float v = y[i];
+        const float p = v * v, e = fmaf(v, v, -p);          // v^2 = p + e exactly
+        const float s = hi + p;
+        const float bb = s - hi;
+        lo += ((hi - (s - bb)) + (p - bb)) + e;
+        hi = s;
         other[i] = 0.0f;
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    dfl acc = {hi + lo, lo - ((hi + lo) - hi)};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc = dfl_add(acc, {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        partial[blockIdx.x] = t;
-        __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double t = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) t += __ldcg(&partial[b]);
-        const double nrm = sqrt(t);
-        scal[1] = nrm;
-        scal[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
-        if (d_sigma) *d_sigma = nrm;
-        *counter = 0u;
+    if (threadIdx.x < 32) {
+        acc = red[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            acc = dfl_add(acc, {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+        if (threadIdx.x == 0) {
+            double nrm = 0.0, inv = 0.0;
+            if (acc.hi > 0.0f) {
+                // y ~ 1/sqrt(t) (estimate + one FP32 Newton step), then one
+                // double-float Newton step each: r = x + (t - x^2) y / 2 with
+                // x = t y, and 1/r = y + y (1 - y r)
+                float q = rsqrtf(acc.hi);
+                q = q * fmaf(-0.5f * acc.hi, q * q, 1.5f);
+                const float x = acc.hi * q;
+                const float x2 = x * x;
+                const dfl d = dfl_add(acc, {-x2, -fmaf(x, x, -x2)});          // t - x^2
+                const float rc = d.hi * (0.5f * q);
+                const float rh = x + rc, rl = rc - (rh - x);                  // r = rh + rl
+                const float yr = q * rh, yre = fmaf(q, rh, -yr);
+                const float res = ((1.0f - yr) - yre) - q * rl;               // 1 - q r
+                nrm = (double)rh + (double)rl;
+                inv = (double)q + (double)(q * res);
+            }
+            scal[1] = nrm;
+            scal[0] = inv;
+            if (d_sigma) *d_sigma = nrm;
+        }
     }
 }
 
@@ -460,8 +494,7 @@ cudaError_t launch_add_shift(cudaStream_t s, float *Y, const float *X, int64_t n
 
 cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, int64_t lda, int N,
                                    uint64_t seed, uint32_t stream_id, const double *d_shift_neg,
-                                   float *v0, float *v1, double *scal, unsigned *counter,
-                                   double *d_sigma)
+                                   float *v0, float *v1, double *scal, double *d_sigma)
 {
     cudaError_t e = launch_gaussian(s, seed, stream_id, n, 1, 1, n, v0, n);
     if (e != cudaSuccess) return e;
@@ -477,8 +510,7 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
         sym_gemv_kernel<<<grid, NTW, 0, s>>>(A, n, lda, in, out, scal, d_shift_neg, vec);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        pi_norm_kernel<<<PI_NORM_BLOCKS, 1024, 0, s>>>(out, in, n, scal, counter, scal + 8,
-                                                       it == N ? d_sigma : nullptr);
+        pi_norm_kernel<<<1, 1024, 0, s>>>(out, in, n, scal, it == N ? d_sigma : nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         float *t = in; in = out; out = t;
@@ -489,7 +521,7 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
 cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t n,
                                         int N, uint64_t seed, uint32_t stream_id,
                                         const double *d_shift_neg, float *v0, float *v1, double *scal,
-                                        unsigned *counter, double *d_sigma, int *d_status)
+                                        double *d_sigma, int *d_status)
 {
     if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0 || (reinterpret_cast<uintptr_t>(v0) & 15) != 0 ||
         (reinterpret_cast<uintptr_t>(v1) & 15) != 0)
@@ -512,8 +544,7 @@ cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint
                                                               d_status);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        pi_norm_kernel<<<PI_NORM_BLOCKS, 1024, 0, s>>>(out, in, n, scal, counter, scal + 8,
-                                                       it == N ? d_sigma : nullptr);
+        pi_norm_kernel<<<1, 1024, 0, s>>>(out, in, n, scal, it == N ? d_sigma : nullptr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         float *t = in; in = out; out = t;
@@ -543,12 +574,10 @@ namespace {
 
 constexpr int64_t NOALLOC_MAX_N = PSDPROJ_NOALLOC_MAX_N;
 constexpr size_t NOALLOC_VEC_BYTES = sizeof(float) * (size_t)NOALLOC_MAX_N;
-constexpr size_t NOALLOC_BYTES = 2 * NOALLOC_VEC_BYTES + 32 * sizeof(double) + 16 * sizeof(unsigned);
+constexpr size_t NOALLOC_BYTES = 2 * NOALLOC_VEC_BYTES + 32 * sizeof(double);
 
-// the shared scratch: v0, v1, then 32 doubles (scales, sigmas, shift, info), then tickets
+// the shared scratch: v0, v1, then 32 doubles (scales, sigmas, shift, info)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
-
-__global__ void noalloc_reset_kernel(unsigned *counter) { if (threadIdx.x < 16) counter[threadIdx.x] = 0u; }
 
 __global__ void noalloc_copy_kernel(const double *s1, const double *s2, double *d1, double *d2)
 {
@@ -585,16 +614,12 @@ extern "C" int psdproj_min_eig_noalloc(const float *dA, int64_t n, int64_t lda, 
     float *v0 = reinterpret_cast<float *>(base);
     float *v1 = reinterpret_cast<float *>(base + NOALLOC_VEC_BYTES);
     double *scal = reinterpret_cast<double *>(base + 2 * NOALLOC_VEC_BYTES);
-    unsigned *counter = reinterpret_cast<unsigned *>(base + 2 * NOALLOC_VEC_BYTES + 32 * sizeof(double));
     double *sig1 = scal + 16, *sig2 = scal + 17, *shift = scal + 18;
     int *info = reinterpret_cast<int *>(scal + 19);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the ticket must start at zero whatever an earlier call left behind
-    noalloc_reset_kernel<<<1, 32, 0, s>>>(counter);
-    if (cudaGetLastError() != cudaSuccess) return PSDPROJ_ECUDA;
-    if (launch_power_iteration(s, dA, n, lda, N, seed, 3u, nullptr, v0, v1, scal, counter, sig1) != cudaSuccess)
+    if (launch_power_iteration(s, dA, n, lda, N, seed, 3u, nullptr, v0, v1, scal, sig1) != cudaSuccess)
         return PSDPROJ_ECUDA;
-    if (launch_power_iteration(s, dA, n, lda, N, seed, 4u, sig1, v0, v1, scal, counter, sig2) != cudaSuccess)
+    if (launch_power_iteration(s, dA, n, lda, N, seed, 4u, sig1, v0, v1, scal, sig2) != cudaSuccess)
         return PSDPROJ_ECUDA;
     if (launch_alpha_finish(s, sig1, sig2, 0.0, d_alpha, shift, info) != cudaSuccess) return PSDPROJ_ECUDA;
     if (d_sigma1 || d_sigma2) {
