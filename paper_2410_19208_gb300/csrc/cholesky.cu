@@ -649,14 +649,21 @@ tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int 
         for (int j = 0; j < T; ++j) acc[i][j] = 0.0f;
     for (int k0 = 0; k0 < m; k0 += KW) {
         __syncthreads();
-        for (int e = threadIdx.x; e < KW * TR; e += 256) {
+        // fixed trip counts, unrolled, so that a thread's loads are in flight together
+#pragma unroll
+        for (int e0 = 0; e0 < KW * TR; e0 += 256) {
+            const int e = e0 + threadIdx.x;
             const int k = e / TR, r = e % TR;
             const int64_t gr = r0 + r;
             Ys[k][r] = (gr < n && k0 + k < m) ? Y[(int64_t)(k0 + k) * ldy + gr] : 0.0f;
         }
-        for (int e = threadIdx.x; e < KW * S; e += 256) {
-            const int cc = e / KW, k = e % KW;
-            Bs[k][cc] = (cc < ncols && k0 + k < m) ? B[(int64_t)cc * m + k0 + k] : 0.0f;
+#pragma unroll
+        for (int e0 = 0; e0 < KW * S; e0 += 256) {
+            const int e = e0 + threadIdx.x;
+            if (KW * S % 256 == 0 || e < KW * S) {
+                const int cc = e / KW, k = e % KW;
+                Bs[k][cc] = (cc < ncols && k0 + k < m) ? B[(int64_t)cc * m + k0 + k] : 0.0f;
+            }
         }
         __syncthreads();
 #pragma unroll 4

@@ -109,12 +109,18 @@ gram_partial_sq_kernel(const float *__restrict__ X, int64_t ldx, const float *__
         for (int v = 0; v < T; ++v) acc[u][v] = 0.0f;
     for (int rs = 0; rs < CH; rs += RS) {
         __syncthreads();
-        for (int e = threadIdx.x; e < RS * S; e += NT) {
-            const int a = e / RS, k = e - (e / RS) * RS;
-            const int64_t r = row0 + rs + k;
-            const bool ok = r < n && a < m;
-            Xs[k][a] = ok ? X[(int64_t)a * ldx + r] : 0.0f;
-            if (!same) Zs[k][a] = ok ? Z[(int64_t)a * ldz + r] : 0.0f;
+        // a fixed trip count, unrolled: the loads of a thread are in flight
+        // together instead of one L2 round trip each
+#pragma unroll
+        for (int e0 = 0; e0 < RS * S; e0 += NT) {
+            const int e = e0 + threadIdx.x;
+            if (RS * S % NT == 0 || e < RS * S) {
+                const int a = e / RS, k = e % RS;
+                const int64_t r = row0 + rs + k;
+                const bool ok = r < n && a < m;
+                Xs[k][a] = ok ? X[(int64_t)a * ldx + r] : 0.0f;
+                if (!same) Zs[k][a] = ok ? Z[(int64_t)a * ldz + r] : 0.0f;
+            }
         }
         __syncthreads();
         const float (*Zsrc)[S + 1] = same ? Xs : Zs;
@@ -144,10 +150,25 @@ gram_partial_sq_kernel(const float *__restrict__ X, int64_t ldx, const float *__
     }
 }
 
-// G[a + b*m] = sum over chunks of gpart (FP64); mode 0: full product,
-// mode 1: upper-only symmetric Gram (mirror), mode 2: symmetrise (S+S^T)/2.
-// Eight lanes share one entry of the partials (coalesced over the entry
-// index) and split the chunk sum; the FP64 adds spread over the whole GPU.
+// Sum of two unevaluated FP32 pairs hi + lo (Knuth's two-sum on the high
+// parts, about 48 significant bits): the chunk sums below in FP32
+// arithmetic, off the FP64 pipe (a few operations per SM and clock here).
+struct fsum {
+    float hi, lo;
+};
+__device__ __forceinline__ fsum fsum_add(fsum a, fsum b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float lo = ((a.hi - (s - bb)) + (b.hi - bb)) + a.lo + b.lo;
+    const float h = s + lo;
+    return {h, lo - (h - s)};
+}
+
+// G[a + b*m] = sum over chunks of gpart (double-float, then FP64); mode 0:
+// full product, mode 1: upper-only symmetric Gram (mirror), mode 2:
+// symmetrise (S+S^T)/2.  Eight lanes share one entry of the partials
+// (coalesced over the entry index) and split the chunk sum in a fixed order.
 __global__ void gram_reduce_kernel(const float *__restrict__ gpart, int nchunk, int m, int mp,
                                    int mode, double *__restrict__ G)
 {
@@ -155,12 +176,15 @@ __global__ void gram_reduce_kernel(const float *__restrict__ gpart, int nchunk, 
     const int f = (int)(tid >> 3), sub = (int)(tid & 7);
     const bool act = f < mp * mp;
     const int ia = act ? f / mp : 0, ib = act ? f - (f / mp) * mp : 0;
-    double s = 0.0;
-    if (act && ia < m && ib < m && (mode != 1 || ia <= ib))
-        for (int c = sub; c < nchunk; c += 8) s += (double)gpart[(int64_t)c * mp * mp + f];
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    fsum acc = {0.0f, 0.0f};
+    if (act && ia < m && ib < m && (mode != 1 || ia <= ib)) {
+#pragma unroll 4
+        for (int c = sub; c < nchunk; c += 8) acc = fsum_add(acc, {gpart[(int64_t)c * mp * mp + f], 0.0f});
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1)
+        acc = fsum_add(acc, {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+    const double s = (double)acc.hi + (double)acc.lo;
     if (!act || sub != 0 || ia >= m || ib >= m) return;
     if (mode == 0) {
         G[(int64_t)ib * m + ia] = s;
