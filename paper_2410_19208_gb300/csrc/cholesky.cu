@@ -23,7 +23,6 @@ namespace {
 
 constexpr int NT = 1024;
 constexpr int SMEM_M = 128;  // largest m kept in shared memory
-constexpr int EPT = (SMEM_M * (SMEM_M + 1) / 2 + NT - 1) / NT;  // upper entries per thread
 
 // ---- double-float arithmetic ------------------------------------------
 struct df {
@@ -126,8 +125,9 @@ template <> struct num<df> {
     __device__ static df one() { return {1.0f, 0.0f}; }
 };
 
-// T: df (first pass, m <= 128), double (first pass, m > 128) or float (second
-// pass).  CPL: entries of an R^-1 column per lane (m <= 32 CPL).
+// Sizes above SMEM_M: the factorization in global memory (gscratch), one
+// barrier per column.  T: double (first pass) or float (second pass).  CPL:
+// entries of an R^-1 column per lane (m <= 32 CPL).
 template <typename T, int CPL>
 __global__ void __launch_bounds__(NT)
 cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restrict__ dead,
@@ -135,19 +135,16 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
                 int *d_status)
 {
     using N = num<T>;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    const bool in_smem = m <= SMEM_M;
-    const int ldu = in_smem ? (m + 1) : m;
-    T *U = in_smem ? reinterpret_cast<T *>(smraw) : gU;             // row-major upper triangle
-    T *rowj = in_smem ? (U + m * (m + 1)) : growj;                  // scaled row j
-    float *Rf = in_smem ? reinterpret_cast<float *>(rowj + m) : gRf; // FP32 R (row-major, ldu)
+    const int ldu = m;
+    T *U = gU;             // row-major upper triangle
+    T *rowj = growj;       // scaled row j
+    float *Rf = gRf;       // FP32 R (row-major, ldu)
     __shared__ double s_gmax;
     __shared__ int s_dead[PSD_MAX_M];
     __shared__ float s_rdinv[PSD_MAX_M];
     __shared__ T s_r[PSD_MAX_M], s_inv[PSD_MAX_M];
     __shared__ int s_bad;
     const int tid = threadIdx.x;
-    const int nup = m * (m + 1) / 2;
 
     // U = upper(G)
     for (int e = tid; e < m * m; e += NT) {
@@ -172,26 +169,6 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
             s_bad = bad;
         }
     }
-    // this thread's upper-triangle entries (fixed for the whole factorization),
-    // packed as i | k << 16.  They are counted from the END of the row-major
-    // order (slot c holds entry nup - 1 - (tid + c NT)), so the entries still
-    // to update at column j, rows >= j, are slot prefixes: a thread stops at
-    // its first finished slot.
-    int eik[EPT];
-#pragma unroll
-    for (int c = 0; c < EPT; ++c) {
-        const int e = nup - 1 - (tid + c * NT);
-        eik[c] = -1;
-        if (in_smem && e >= 0) {
-            // e -> (i <= k), row-major over the upper triangle
-            const float hb = 2.0f * m + 1.0f;
-            int i = (int)((hb - sqrtf(fmaxf(hb * hb - 8.0f * e, 0.0f))) * 0.5f);
-            i = max(0, min(i, m - 1));
-            while (i > 0 && i * m - i * (i - 1) / 2 > e) --i;
-            while (i + 1 < m && (i + 1) * m - (i + 1) * i / 2 <= e) ++i;
-            eik[c] = i | ((i + (e - (i * m - i * (i - 1) / 2))) << 16);
-        }
-    }
     __syncthreads();
     if (s_bad) psd_set_status(d_status, PSDPROJ_ENOTFINITE);
     const float thr = (float)(tau * s_gmax);
@@ -209,60 +186,29 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
     if (tid == 0) pivot(0, U[0]);
     __syncthreads();
 
-    if (in_smem) {
-        // One phase and one barrier per column.  Row j of U is final when
-        // column j starts and is only read in its phase: the owners of
-        // (j, k) write row j of R, the owners of (i, k), i > j, update
-        //   U(i,k) -= U(j,i) U(j,k) / R_jj^2,
-        // and the owner of (j+1, j+1) forms the next pivot.  A thread takes
-        // its entries in groups of G, loads first, so the loads overlap.
-        for (int j = 0; j < m; ++j) {
-            const bool dj = s_dead[j] != 0;
-            const T inv = s_inv[j];
-            const T inv2 = N::mul(inv, inv);
-            const T *rowU = U + j * ldu;
-            const int nact = nup - (j * m - j * (j - 1) / 2);   // entries (i, k), i >= j
-#pragma unroll
-            for (int c = 0; c < EPT; ++c) {
-                if (tid + c * NT >= nact) break;
-                const int i = eik[c] & 0xFFFF, k = eik[c] >> 16;
-                const T u0 = U[i * ldu + k];
-                if (i == j) {
-                    Rf[j * ldu + k] = (k == j) ? N::hi(s_r[j]) : (dj ? 0.0f : N::hi(N::mul(u0, inv)));
-                } else {
-                    T u = u0;
-                    if (!dj) u = N::fms(u, N::mul(rowU[i], inv2), rowU[k]);
-                    U[i * ldu + k] = u;
-                    if (i == j + 1 && k == j + 1) pivot(j + 1, u);
-                }
-            }
-            __syncthreads();
+    for (int j = 0; j < m; ++j) {
+        // phase A: row j of R into rowj (the update's operand) and Rf
+        const bool dj = s_dead[j] != 0;
+        const T inv = s_inv[j];
+        for (int k = j + tid; k < m; k += NT) {
+            const T v = (k == j) ? s_r[j] : (dj ? N::zero() : N::mul(U[j * ldu + k], inv));
+            rowj[k] = (k == j) ? N::zero() : v;
+            Rf[j * ldu + k] = N::hi(v);
         }
-    } else {
-        for (int j = 0; j < m; ++j) {
-            // phase A: row j of R into rowj (the update's operand) and Rf
-            const bool dj = s_dead[j] != 0;
-            const T inv = s_inv[j];
-            for (int k = j + tid; k < m; k += NT) {
-                const T v = (k == j) ? s_r[j] : (dj ? N::zero() : N::mul(U[j * ldu + k], inv));
-                rowj[k] = (k == j) ? N::zero() : v;
-                Rf[j * ldu + k] = N::hi(v);
+        __syncthreads();
+        // phase B: trailing update U(i,k) -= R(j,i) R(j,k), j < i <= k
+        const int t = m - j - 1;
+        if (!dj) {
+            for (int e = tid; e < t * t; e += NT) {
+                const int a = e / t, b = e - (e / t) * t;
+                if (b < a) continue;
+                const int i = j + 1 + a, k = j + 1 + b;
+                U[i * ldu + k] = N::fms(U[i * ldu + k], rowj[i], rowj[k]);
             }
-            __syncthreads();
-            // phase B: trailing update U(i,k) -= R(j,i) R(j,k), j < i <= k
-            const int t = m - j - 1;
-            if (!dj) {
-                for (int e = tid; e < t * t; e += NT) {
-                    const int a = e / t, b = e - (e / t) * t;
-                    if (b < a) continue;
-                    const int i = j + 1 + a, k = j + 1 + b;
-                    U[i * ldu + k] = N::fms(U[i * ldu + k], rowj[i], rowj[k]);
-                }
-            }
-            // e = 0 is entry (j+1, j+1), updated by thread 0 above
-            if (tid == 0 && t > 0) pivot(j + 1, U[(j + 1) * ldu + (j + 1)]);
-            __syncthreads();
         }
+        // e = 0 is entry (j+1, j+1), updated by thread 0 above
+        if (tid == 0 && t > 0) pivot(j + 1, U[(j + 1) * ldu + (j + 1)]);
+        __syncthreads();
     }
 
     // R^-1 (upper, FP32), one warp per column j: back substitution in axpy

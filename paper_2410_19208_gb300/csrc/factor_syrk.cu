@@ -7,21 +7,22 @@
 
 namespace {
 
+// M = V diag(sqrt(max(d, 0))) and the count of positive eigenvalues; one
+// root per column (FP64 roots are slow on this GPU), then the scaling
 __global__ void factor_prep_kernel(const float *__restrict__ V, const double *__restrict__ d,
                                    int m, float *__restrict__ M, int *__restrict__ d_rank)
 {
     __shared__ int s_r;
+    __shared__ float s_g[PSD_MAX_M];
     if (threadIdx.x == 0) s_r = 0;
     __syncthreads();
-    for (int j = threadIdx.x; j < m; j += blockDim.x)
-        if (d[j] > 0.0) atomicAdd(&s_r, 1);
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int j = e / m;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
         const double dj = d[j];
-        const float g = dj > 0.0 ? (float)sqrt(dj) : 0.0f;
-        M[e] = V[e] * g;
+        if (dj > 0.0) atomicAdd(&s_r, 1);
+        s_g[j] = dj > 0.0 ? sqrtf((float)dj) : 0.0f;
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) M[e] = V[e] * s_g[e / m];
     if (threadIdx.x == 0 && d_rank) *d_rank = s_r;
 }
 
