@@ -593,25 +593,40 @@ tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int 
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < T; ++j) acc[i][j] = 0.0f;
-    for (int k0 = 0; k0 < m; k0 += KW) {
-        __syncthreads();
-        // fixed trip counts, unrolled, so that a thread's loads are in flight together
+    // the next K chunk is read into registers while the current one is
+    // multiplied (fixed trip counts, so a thread's loads are in flight together)
+    constexpr int NY = KW * TR / 256, NB2 = (KW * S + 255) / 256;
+    float ry[NY], rb[NB2];
+    auto fetch = [&](int k0) {
 #pragma unroll
-        for (int e0 = 0; e0 < KW * TR; e0 += 256) {
-            const int e = e0 + threadIdx.x;
+        for (int i = 0; i < NY; ++i) {
+            const int e = i * 256 + threadIdx.x;
             const int k = e / TR, r = e % TR;
             const int64_t gr = r0 + r;
-            Ys[k][r] = (gr < n && k0 + k < m) ? Y[(int64_t)(k0 + k) * ldy + gr] : 0.0f;
+            ry[i] = (gr < n && k0 + k < m) ? Y[(int64_t)(k0 + k) * ldy + gr] : 0.0f;
         }
 #pragma unroll
-        for (int e0 = 0; e0 < KW * S; e0 += 256) {
-            const int e = e0 + threadIdx.x;
-            if (KW * S % 256 == 0 || e < KW * S) {
-                const int cc = e / KW, k = e % KW;
-                Bs[k][cc] = (cc < ncols && k0 + k < m) ? B[(int64_t)cc * m + k0 + k] : 0.0f;
-            }
+        for (int i = 0; i < NB2; ++i) {
+            const int e = i * 256 + threadIdx.x;
+            const int cc = e / KW, k = e % KW;
+            rb[i] = (e < KW * S && cc < ncols && k0 + k < m) ? B[(int64_t)cc * m + k0 + k] : 0.0f;
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < m; k0 += KW) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NY; ++i) {
+            const int e = i * 256 + threadIdx.x;
+            Ys[e / TR][e % TR] = ry[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NB2; ++i) {
+            const int e = i * 256 + threadIdx.x;
+            if (e < KW * S) Bs[e % KW][e / KW] = rb[i];
         }
         __syncthreads();
+        if (k0 + KW < m) fetch(k0 + KW);
 #pragma unroll 4
         for (int k = 0; k < KW; ++k) {
             const float4 y4 = *reinterpret_cast<const float4 *>(&Ys[k][4 * tx]);

@@ -107,22 +107,33 @@ gram_partial_sq_kernel(const float *__restrict__ X, int64_t ldx, const float *__
     for (int u = 0; u < T; ++u)
 #pragma unroll
         for (int v = 0; v < T; ++v) acc[u][v] = 0.0f;
+    // the next RS rows are read into registers while the current ones are
+    // multiplied (fixed trip counts, so a thread's loads are in flight together)
+    constexpr int NE = RS * S / NT;
+    static_assert(RS * S % NT == 0, "staging split");
+    float rx[NE], rz[NE];
+    auto fetch = [&](int rs) {
+#pragma unroll
+        for (int i = 0; i < NE; ++i) {
+            const int e = i * NT + threadIdx.x;
+            const int a = e / RS, k = e % RS;
+            const int64_t r = row0 + rs + k;
+            const bool ok = r < n && a < m;
+            rx[i] = ok ? X[(int64_t)a * ldx + r] : 0.0f;
+            if (!same) rz[i] = ok ? Z[(int64_t)a * ldz + r] : 0.0f;
+        }
+    };
+    fetch(0);
     for (int rs = 0; rs < CH; rs += RS) {
         __syncthreads();
-        // a fixed trip count, unrolled: the loads of a thread are in flight
-        // together instead of one L2 round trip each
 #pragma unroll
-        for (int e0 = 0; e0 < RS * S; e0 += NT) {
-            const int e = e0 + threadIdx.x;
-            if (RS * S % NT == 0 || e < RS * S) {
-                const int a = e / RS, k = e % RS;
-                const int64_t r = row0 + rs + k;
-                const bool ok = r < n && a < m;
-                Xs[k][a] = ok ? X[(int64_t)a * ldx + r] : 0.0f;
-                if (!same) Zs[k][a] = ok ? Z[(int64_t)a * ldz + r] : 0.0f;
-            }
+        for (int i = 0; i < NE; ++i) {
+            const int e = i * NT + threadIdx.x;
+            Xs[e % RS][e / RS] = rx[i];
+            if (!same) Zs[e % RS][e / RS] = rz[i];
         }
         __syncthreads();
+        if (rs + RS < CH) fetch(rs + RS);
         const float (*Zsrc)[S + 1] = same ? Xs : Zs;
 #pragma unroll 4
         for (int k = 0; k < RS; ++k) {
