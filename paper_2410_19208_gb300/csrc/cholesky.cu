@@ -3,7 +3,7 @@
 //   of the raw product can be ill-conditioned; FP32 for the second, whose
 //   Gram is I + O(eps)), with the dependent-column rule; R^-1 in FP32; and
 //   Q = Y R^-1 (a tall x small product on the CUDA cores).
-// For m <= 128 the factorization is blocked (16-column blocks, three block
+// For m <= 128 the factorization is blocked (8- or 16-column blocks, three block
 // barriers per block, the diagonal block in one warp's registers) and R^-1
 // is formed blockwise (cholesky_blocked_kernel); larger m use a right-looking
 // kernel in global memory with one barrier per column, each thread owning a
@@ -252,8 +252,8 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
 }
 
 // ---- blocked factorization for m <= SMEM_M -------------------------------
-// The same R and the same dependent-column rule, in blocks of NB = 16
-// columns with three block barriers per block instead of one per column:
+// The same R and the same dependent-column rule, in blocks of NB columns
+// (8 or 16) with three block barriers per block instead of one per column:
 //   (1) one warp factors the diagonal block column by column (pivot test,
 //       root, the block's part of row j of R, update of the rest of the
 //       diagonal block);
@@ -266,8 +266,11 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
 // from the last block row up,
 //   X(b, c) = -X(b, b) sum_{d > b} R(b, d) X(d, c),
 // two barriers per block row.
-constexpr int NB = 16;
 constexpr int NTB = 512;
+// block width NB: 8 for the double-float pass (shorter dependent chain in the
+// diagonal block, measured 185 vs 204 us at m = 110), 16 for FP32 (94 vs 98 us)
+template <typename T> struct chol_nb { static constexpr int value = 16; };
+template <> struct chol_nb<df> { static constexpr int value = 8; };
 
 // warp shuffle of a number (width: the lane group)
 __device__ __forceinline__ float shfl_num(float v, int src, int width = 32)
@@ -284,7 +287,7 @@ template <typename T>
 size_t blocked_smem(int m)
 {
     const size_t ldu = (size_t)m + 1;
-    return sizeof(T) * m * ldu + sizeof(float) * m * ldu + sizeof(float) * NB * m;
+    return sizeof(T) * m * ldu + sizeof(float) * m * ldu + sizeof(float) * chol_nb<T>::value * m;
 }
 
 template <typename T>
@@ -293,6 +296,8 @@ cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__
                         int *__restrict__ dead, int *__restrict__ d_qrank, double tau, int *d_status)
 {
     using N = num<T>;
+    constexpr int NB = chol_nb<T>::value;
+    static_assert(NB == 8 || NB == 16, "block width: lane groups divide a warp");
     extern __shared__ __align__(16) unsigned char smraw[];
     const int ldu = m + 1;
     T *U = reinterpret_cast<T *>(smraw);                               // m x ldu, row-major, upper part
@@ -337,9 +342,9 @@ cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__
     for (int b = 0; b < nblk; ++b) {
         const int j0 = b * NB, j1 = min(j0 + NB, m), w = j1 - j0;
         // (1) the diagonal block, one warp, in registers: lane c (and its
-        // mirror c + 16) holds column c of the block, col[a] = U(j0+a, j0+c)
+        // mirrors c + NB, ...) holds column c of the block, col[a] = U(j0+a, j0+c)
         if (warp == 0) {
-            const int c = lane & 15;
+            const int c = lane & (NB - 1);
             T col[NB];
 #pragma unroll
             for (int a = 0; a < NB; ++a) col[a] = (a <= c && c < w) ? U[(j0 + a) * ldu + j0 + c] : N::zero();
@@ -367,7 +372,7 @@ cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__
                     }
                 }
             }
-            if (lane < 16 && c < w) {
+            if (lane < NB && c < w) {
 #pragma unroll
                 for (int a = 0; a < NB; ++a)
                     if (a <= c) {
@@ -377,16 +382,17 @@ cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__
             }
         }
         __syncthreads();
-        // (2) rows j0 .. j1-1 of R in the later columns: 16 lanes per column k,
+        // (2) rows j0 .. j1-1 of R in the later columns: NB lanes per column k,
         // lane a holding U(j0+a, k), forward substitution down the rows
         {
-            const int a = lane & 15;
+            const int a = lane & (NB - 1);
             T rcol[NB];                               // R(j0+a2, j0+a), a2 < a
 #pragma unroll
             for (int a2 = 0; a2 < NB; ++a2) rcol[a2] = (a2 < a && a < w) ? U[(j0 + a2) * ldu + j0 + a] : N::zero();
             const int ncol = m - j1;
-            for (int g = tid >> 4; g < ((ncol + 1) & ~1); g += NTB / 16) {
-                // g runs over an even count so that both half-warps stay in the loop together
+            constexpr int GPW = 32 / NB;              // lane groups per warp
+            for (int g = tid / NB; g < (ncol + GPW - 1) / GPW * GPW; g += NTB / NB) {
+                // g runs over a multiple of GPW so that all groups of a warp stay in the loop together
                 const int k = j1 + g;
                 const bool act = g < ncol && a < w;
                 T x = act ? U[(j0 + a) * ldu + k] : N::zero();
@@ -394,7 +400,7 @@ cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__
                 for (int a2 = 0; a2 < NB; ++a2) {
                     if (a2 < w) {
                         const int j = j0 + a2;
-                        T v = shfl_num(x, a2, 16);
+                        T v = shfl_num(x, a2, NB);
                         v = s_dead[j] ? N::zero() : N::mul(v, s_inv[j]);
                         if (a == a2) x = v;
                         else if (a > a2) x = N::fms(x, rcol[a2], v);
