@@ -443,18 +443,32 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
         const int nref = m - 2;                               // reflectors 0 .. m-3
         for (int jb = nref > 0 ? ((nref - 1) / NB) * NB : -1; jb >= 0; jb -= NB) {
             const int nb = min(NB, nref - jb);
-            // (a) W[t][c] = v_t^T Z[:, c] and S[s][t] = v_s^T v_t (s < t)
-            for (int q = tid; q < nb * m; q += NT) {
-                const int t = q / m, c = q - (q / m) * m;
-                const int col = jb + t;
-                float s0 = 0.0f, s1 = 0.0f;
-                int i = col + 1;
-                for (; i + 1 < m; i += 2) {
-                    s0 = fmaf(A[i * ld + col], Z[i * ld + c], s0);
-                    s1 = fmaf(A[(i + 1) * ld + col], Z[(i + 1) * ld + c], s1);
+            // (a) W[t][c] = v_t^T Z[:, c] (v_t lives in rows > jb + t of column
+            // jb + t), four reflectors per thread so that each Z entry read
+            // serves four products; and S[s][t] = v_s^T v_t (s < t)
+            for (int q = tid; q < 4 * m; q += NT) {
+                const int tg = q / m, c = q - (q / m) * m;
+                const int t0 = 4 * tg, col0 = jb + t0;
+                if (t0 >= nb) continue;
+                float w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                int i = col0 + 1;
+                for (; i < m && i < col0 + 4; ++i) {           // the first rows, where some v_t start
+                    const float z = Z[i * ld + c];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (t0 + u < nb && i > col0 + u) w[u] = fmaf(A[i * ld + col0 + u], z, w[u]);
                 }
-                if (i < m) s0 = fmaf(A[i * ld + col], Z[i * ld + c], s0);
-                T[t * ld + c] = s0 + s1;
+                const int nu = min(4, nb - t0);                  // reflectors of this group
+                for (; i < m; ++i) {
+                    const float z = Z[i * ld + c];
+                    const float *ar = A + i * ld + col0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (u < nu) w[u] = fmaf(ar[u], z, w[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (t0 + u < nb) T[(t0 + u) * ld + c] = w[u];
             }
             for (int q = tid; q < nb * nb; q += NT) {
                 const int sI = q / nb, tI = q - (q / nb) * nb;
@@ -495,18 +509,32 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
                 }
             }
             __syncthreads();
-            // (d) Z[i][c] -= sum_t V[i][t] W[t][c], rows i > jb (a warp per row)
-            for (int i = jb + 1 + warp; i < m; i += NT / 32) {
-                float v[NB];
+            // (d) Z[i][c] -= sum_t V[i][t] W[t][c], rows i > jb (a warp per row);
+            // a lane keeps W of its four columns (c = cb + lane + 32 k) in
+            // registers over all of its warp's rows
+            for (int cb = 0; cb < m; cb += 128) {
+                float wr[4][NB];
 #pragma unroll
-                for (int t = 0; t < NB; ++t) v[t] = (t < nb && i > jb + t) ? A[i * ld + jb + t] : 0.0f;
-                float *zr = Z + i * ld;
-                for (int c = lane; c < m; c += 32) {
-                    float acc = zr[c];
+                for (int k = 0; k < 4; ++k) {
+                    const int c = cb + lane + 32 * k;
 #pragma unroll
-                    for (int t = 0; t < NB; ++t)
-                        if (t < nb) acc = fmaf(-v[t], T[t * ld + c], acc);   // rows >= nb are stale
-                    zr[c] = acc;
+                    for (int t = 0; t < NB; ++t) wr[k][t] = (c < m && t < nb) ? T[t * ld + c] : 0.0f;
+                }
+                for (int i = jb + 1 + warp; i < m; i += NT / 32) {
+                    float v[NB];
+#pragma unroll
+                    for (int t = 0; t < NB; ++t) v[t] = (t < nb && i > jb + t) ? A[i * ld + jb + t] : 0.0f;
+                    float *zr = Z + i * ld;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int c = cb + lane + 32 * k;
+                        if (c < m) {
+                            float acc = zr[c];
+#pragma unroll
+                            for (int t = 0; t < NB; ++t) acc = fmaf(-v[t], wr[k][t], acc);
+                            zr[c] = acc;
+                        }
+                    }
                 }
             }
             __syncthreads();
