@@ -566,7 +566,7 @@ cudaError_t launch_alpha_finish(cudaStream_t s, const double *d_s1, const double
 // library's memory manager or a custom allocator that forbids allocations in
 // its hot path, plug-ins whose host cannot grant device allocations, or
 // contexts whose memory is capped and fully reserved up front.  Its scratch
-// (the two power-iteration vectors, the norms and the completion ticket) is a
+// (the two power-iteration vectors and the norms and scales) is a
 // fixed file-scope device array, present on every GPU that loads this
 // library until the process exits.
 // ---------------------------------------------------------------------------
