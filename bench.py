@@ -466,6 +466,14 @@ def main():
                       torch.zeros(1, dtype=torch.int32, device=dev),
                       torch.zeros(1, dtype=torch.float64, device=dev)))
     ctx2 = lanes[1][0] if S > 1 else ctx
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    def set_reserve(r):
+        # SMs that every context's persistent grids leave to the other
+        # contexts' single-block steps while the contexts run at once
+        # (psdproj_set_reserved_sms; 1, the library default, for one stream)
+        for ln in lanes:
+            ln[0].set_reserved_sms(max(0, min(r, sm_count - 1)))
     import ctypes
 
     def pct(v, q_):
@@ -548,6 +556,7 @@ def main():
         stream before the first projection to the first stream after every
         stream's last one."""
         opts = ps.make_opts(prec=PREC_NAMES[prec_], syrk_prec=PREC_NAMES[syrk_])
+        set_reserve(2 * S if S > 1 else 1)
 
         def run(count):
             ev = torch.cuda.Event()
@@ -598,6 +607,7 @@ def main():
             t = torch.tensor([elapsed_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             elapsed_ms = float(t.item())
+        set_reserve(1)
         return dict(elapsed_ms=elapsed_ms, launches=launches, clocks=clocks)
 
     # relative Frobenius error against the exact projection X+ = U diag(lam+) U^T,
@@ -740,7 +750,9 @@ def main():
                        "note": "the same steps on one context and one stream, Alg. 1 then Alg. 2; "
                                "latency, stages and rooflines are from this run"},
         "concurrency": f"{S} contexts on {S} CUDA streams; the 2K projections of the K steps are spread "
-                       "over them, every stream getting both algorithms",
+                       "over them, every stream getting both algorithms; each context's persistent grids "
+                       f"leave {min(2 * S, sm_count - 1) if S > 1 else 1} SMs free "
+                       "(psdproj_set_reserved_sms)",
         "stages": stages, "gpu_launches": conc["launches"], "clocks": conc["clocks"],
         "error_vs_exact": {"alg1": err_exact(head["W1"]), "alg2": err_exact(head["W2"])},
     }
@@ -805,12 +817,14 @@ def main():
         # and stream, so that copies in both directions and the computation
         # of different projections overlap
         ths = [threading.Thread(target=host_loop, args=(j,)) for j in range(T)]
+        set_reserve(2 * T if T > 1 else 1)
         t0 = time.perf_counter()
         for th in ths:
             th.start()
         for th in ths:
             th.join()
         dt = time.perf_counter() - t0
+        set_reserve(1)
         if dist:
             t = torch.tensor([dt], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -227,6 +227,17 @@ int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
  * workspace, sized for the largest problem it has run. */
 int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams);
 
+/* SMs that this context's persistent kernels (the tensor-core passes, the
+ * BF16 power iteration, the SYRK) leave free: 0 .. SMs - 1, default 1; also
+ * applied to the context's batch helpers.  A persistent grid that finds no
+ * free SM for one of its CTAs runs that CTA only when another finishes, so
+ * when several contexts run projections on one GPU at once, their
+ * single-block steps (Cholesky, eigensolver) need SMs that the others'
+ * grids do not take: two per concurrent context measured best for four
+ * contexts (4 % more projections/s than the default).  Returns
+ * PSDPROJ_EINVAL for a null context or a count outside that range. */
+int psdproj_set_reserved_sms(psdproj_ctx *ctx, int sms);
+
 /* ---- dual gradient descent for semidefinite least squares (Alg. 6) ------
  *   min over PSD X of 1/2 ||X - C/rho||_F^2   s.t.  <A_i, X> = b_i, i < mc.
  * Each iteration t forms X_t = C/rho + sum_i y_i A_i (upper triangle; the

@@ -104,6 +104,7 @@ def _load():
                                 _P, ctypes.POINTER(Opts)]),
         "psdproj_batched": (_int, [_P, _int, _P, _P]),
         "psdproj_set_batch_streams": (_int, [_P, _int]),
+        "psdproj_set_reserved_sms": (_int, [_P, _int]),
         "psdproj_alg2": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, ctypes.c_double,
                                 _P, _P, _P, _i64, _P, _i64, _P, ctypes.POINTER(Opts)]),
         "psdproj_alg1_host": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, _P, _i64, _P,
@@ -273,6 +274,9 @@ class Context:
 
     def set_batch_streams(self, streams: int):
         _check(_load().psdproj_set_batch_streams(self.h, streams), "psdproj_set_batch_streams")
+
+    def set_reserved_sms(self, sms: int):
+        _check(_load().psdproj_set_reserved_sms(self.h, sms), "psdproj_set_reserved_sms")
 
     def alg1_host(self, A, k, p, q, seed, P=None, W=None, opts: Opts | None = None):
         """Host tensors (CPU, pinned recommended); returns r+."""

@@ -574,6 +574,15 @@ int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams)
     return PSDPROJ_OK;
 }
 
+int psdproj_set_reserved_sms(psdproj_ctx *ctx, int sms)
+{
+    if (!ctx || sms < 0 || sms >= ctx->sm_count) return PSDPROJ_EINVAL;
+    ctx->persist_sms = ctx->sm_count - sms;
+    for (int i = 0; i < PSD_MAX_LANES; ++i)
+        if (ctx->lane[i]) ctx->lane[i]->persist_sms = ctx->persist_sms;
+    return PSDPROJ_OK;
+}
+
 int psdproj_sync_status(psdproj_ctx *ctx)
 {
     if (!ctx) return PSDPROJ_EINVAL;

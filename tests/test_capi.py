@@ -53,6 +53,8 @@ def test_rejects_bad_arguments_without_a_gpu(lib):
     assert lib.psdproj_destroy(None) == 0
     assert lib.psdproj_sync_status(None) == 1
     assert lib.psdproj_create(None, 0, None) == 1
+    assert lib.psdproj_set_reserved_sms(None, 1) == 1
+    assert lib.psdproj_set_batch_streams(None, 4) == 1
     h = ctypes.c_void_p()
     # device index out of range (no device here, or index too large)
     assert lib.psdproj_create(ctypes.byref(h), 1 << 20, None) != 0

@@ -392,6 +392,29 @@ def test_batched_streams_agree_and_order_on_the_context_stream(ctx, prec):
         assert _rel(P16, P1) <= tol
 
 
+def test_reserved_sms_give_the_same_projection(ctx):
+    """Leaving more SMs free of the persistent grids changes only how the
+    passes' tiles are split over CTAs (FP32 addition order); out-of-range
+    counts are rejected and change nothing."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    _, _, A32 = _A("decay", 3000, seed_u=41, seed_lam=42)
+    opts = ps.make_opts(prec=ps.PREC_BF16)
+    ref = _run(ctx, A32, 60, 10, 1, 5, alg=1, opts=opts)
+    with pytest.raises(ps.PsdprojError):
+        ctx.set_reserved_sms(-1)
+    with pytest.raises(ps.PsdprojError):
+        ctx.set_reserved_sms(sms)
+    try:
+        for r in (8, sms - 1):
+            ctx.set_reserved_sms(r)
+            out = _run(ctx, A32, 60, 10, 1, 5, alg=1, opts=opts)
+            assert out["rank"] == ref["rank"]
+            # BF16 form: a last-bit change of X can move its BF16 rounding
+            assert _rel(out["P"], ref["P"]) <= 2e-3
+    finally:
+        ctx.set_reserved_sms(1)
+
+
 def test_batched_rejects_bad_problems_before_running(ctx):
     n = 100
     A = torch.zeros(n, n, device="cuda")
