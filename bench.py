@@ -48,6 +48,24 @@ PREC_NAMES = {"fp32": 0, "tf32": 1, "bf16": 2, "bf16x3": 3}
 DTYPE_NAMES = {"fp32": "f32", "tf32": "tf32", "bf16": "bf16", "bf16x3": "bf16x3"}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time from each rank's own: the largest x over all ranks
+    (rank-local x when there is one rank).  Backend-agnostic: NCCL with a CUDA
+    device on the GPUs, gloo with the CPU in the multi-process tests."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput with every rank doing the same units (weak
+    scaling, independent replicas): all ranks' units over the slowest rank."""
+    return units_per_rank * world / max_seconds
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -528,11 +546,7 @@ def main():
         st = ctx.sync_status()
         if st != 0:
             raise SystemExit(f"device status {ps.STATUS.get(st)} in the timed region ({prec_})")
-        elapsed_ms = t_start.elapsed_time(t_end)
-        if dist:
-            t = torch.tensor([elapsed_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            elapsed_ms = float(t.item())
+        elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
         a1 = [x[0].elapsed_time(x[1]) for x in lat]
         a2 = [x[1].elapsed_time(x[2]) for x in lat]
         stages = {STAGES[i]: {"ms_total": ms_k[i], "launches": cnt_k[i],
@@ -602,11 +616,7 @@ def main():
             st = c_.sync_status()
             if st != 0:
                 raise SystemExit(f"device status {ps.STATUS.get(st)} in the timed region (concurrent)")
-        elapsed_ms = t_start.elapsed_time(t_end)
-        if dist:
-            t = torch.tensor([elapsed_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            elapsed_ms = float(t.item())
+        elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
         set_reserve(1)
         return dict(elapsed_ms=elapsed_ms, launches=launches, clocks=clocks)
 
@@ -630,11 +640,10 @@ def main():
     elapsed_ms = head["elapsed_ms"]
     stages = head["stages"]
     opts = head["opts"]
-    seq_value = 2 * args.steps * world / (elapsed_ms / 1e3)
+    seq_value = job_rate(2 * args.steps, world, elapsed_ms / 1e3)
     # headline: the same K steps with the two projections of a step on two streams
     conc = measure_concurrent(prec, syrk_prec, args.steps, True)
-    total_proj = 2 * args.steps * world
-    value = total_proj / (conc["elapsed_ms"] / 1e3)
+    value = job_rate(2 * args.steps, world, conc["elapsed_ms"] / 1e3)
 
     # ---- rooflines: the dominant kernel and the other HBM-bound ones -------
     # algorithmic bytes per launch (stated in the design doc): U(n) = n(n+1)/2
@@ -825,12 +834,9 @@ def main():
             th.join()
         dt = time.perf_counter() - t0
         set_reserve(1)
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist, dev)
         upper_bytes = 4 * (n * (n + 1) // 2)          # read over the host link from the pinned A
-        line["e2e"] = {"value": 2 * steps_e2e * world / dt, "unit": "projections/s",
+        line["e2e"] = {"value": job_rate(2 * steps_e2e, world, dt), "unit": "projections/s",
                        "h2d_bytes_per_step": 2 * upper_bytes, "d2h_bytes_per_step": 2 * (4 * n * n + 4 + 8),
                        "api": f"psdproj_alg1_host + psdproj_alg2_host from {T} host threads (one context "
                               "each), pinned host buffers; A's upper triangle in, the full P out",
