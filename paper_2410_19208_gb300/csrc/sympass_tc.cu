@@ -13,25 +13,32 @@
 // a contiguous range of the image, one bulk copy per tile, and every later
 // pass over A reads 2 bytes per upper-triangle entry instead of 4.
 //
-// Each tile (with the X_J tile loaded by TMA beside it, three stages in
-// flight) feeds two products straight from shared memory:
+// Each tile (with the X_J tile loaded by TMA beside it, two to four stages
+// in flight) feeds two products:
 //   P1  D1^T (m x BM) += X_J^T (m x 64) . A'_IJ^T   (B operand K-major)
 //   P2  D2^T (m x 64)   = X_I^T (m x BM) . A'_IJ    (B operand MN-major)
-// with M = 128 rows of X^T (m <= 128; rows m..127 are zero).  D1^T
-// accumulates over the run of tiles a CTA owns in one block row and is
-// flushed once; D2^T is double-buffered in TMEM and added to Y after every
-// tile.  The shift term is not in the pass: the sweep that converts X to
-// BF16 starts Y at shift X (or adds it), so a run that holds a diagonal
-// block drains D1 without extra global reads.  Both are
-// added by TMA bulk reduce-add from a swizzled 32 x 32 staging box per warp
-// (scalar atomics when Y is not 16-byte aligned with ld % 4 == 0).
+// with M = 128 rows of X^T.  The A operand of P1 and both B operands are
+// read from shared memory; X_I^T, the A operand of P2, is copied into TMEM
+// once per block row (shared-memory bandwidth, not the tensor pipe, bounds
+// the pass, and P2 would otherwise read X_I from shared memory sixteen
+// times per tile).  Only MR = 64, 112 or 128 rows of X^T (m <= MR)
+// are staged, which leaves shared memory for the stages and eight staging
+// boxes; accumulator lanes >= m are never stored.  D1^T accumulates over the
+// run of tiles a CTA owns in one block row and is flushed once; D2^T is
+// double-buffered in TMEM and added to Y after every tile.  The shift term
+// is not in the pass: the sweep that converts X to BF16 starts Y at shift X
+// (or adds it), so a run that holds a diagonal block drains D1 without extra
+// global reads.  Both are added by TMA bulk reduce-add from a swizzled
+// 32 x 32 staging box per epilogue warp (scalar atomics when Y is not
+// 16-byte aligned with ld % 4 == 0).
 //
-// Warp roles (256 threads, one CTA per SM, persistent over a cost-balanced
+// Warp roles (384 threads, one CTA per SM, persistent over a cost-balanced
 // range of the tiles in row-major order): warp 0 issues the copies, warp 1
 // owns TMEM and issues the row-product MMAs, warp 2 the transposed-product
-// MMAs (one thread each), warps 4-7 drain TMEM.  Every mbarrier
-// wait is bounded; on a timeout the CTA records PSDPROJ_ETIMEOUT, unwinds and
-// frees its TMEM.
+// MMAs (one thread each), warps 4-11 drain TMEM, two per TMEM lane quarter,
+// so that every epilogue warp stages and reduces one 32 x 32 box of D2 per
+// tile.  Every mbarrier wait is bounded; on a timeout the CTA records
+// PSDPROJ_ETIMEOUT, unwinds and frees its TMEM.
 #include <cuda_bf16.h>
 #include <cstring>
 #include <cudaTypedefs.h>
@@ -46,29 +53,49 @@ using namespace tc;
 constexpr int BN = PSD_TILE_N;
 constexpr int BM = PSD_TILE_M;
 constexpr int R = PSD_TILE_R;                    // column tiles per block-row step
-constexpr int NSTAGE = 3;
-constexpr uint32_t A_BYTES = BM * BN * 2;        // BF16 tile of A'
-constexpr uint32_t XJ_BYTES = 128 * BN * 2;      // X_J^T rows 0..127 (16 KB)
-constexpr uint32_t STAGE = A_BYTES + XJ_BYTES;   // one stage: A' tile, then X_J
-constexpr uint32_t XI_BYTES = 128 * BM * 2;      // 64 KB
+constexpr uint32_t A_BYTES = BM * BN * 2;        // BF16 tile of A' (32 KB)
 constexpr uint32_t STG_BYTES = 32 * 32 * 4;      // epilogue staging box per warp
-constexpr uint32_t OFF_A = 0;
-constexpr uint32_t OFF_XI = NSTAGE * STAGE;
-constexpr uint32_t OFF_STG = OFF_XI + XI_BYTES;
-constexpr uint32_t OFF_BAR = OFF_STG + 4 * STG_BYTES;
-constexpr uint32_t SMEM_BYTES = OFF_BAR + 256;
-constexpr uint32_t D1_COL = 0, D2_COL = BM;      // TMEM columns: D1 256, D2 2 x 64
+constexpr int NEPI = 8;                          // epilogue warps (two per TMEM lane quarter)
+constexpr int NT = 32 * (4 + NEPI);
+// TMEM columns: D1^T 256, D2^T 2 x 64, X_I^T (the A operand of P2, K = 256
+// BF16 values per lane) 128
+constexpr uint32_t D1_COL = 0, D2_COL = BM, XI_COL = BM + 2 * BN;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int NT = 256;
+static_assert(XI_COL + BM / 2 == TMEM_COLS, "tensor memory");
 constexpr long long WAIT_LIMIT = 4000000000LL;  // ~2 s at 2 GHz
-static_assert(SMEM_BYTES <= 232448, "shared memory");
-static_assert(STAGE % 1024 == 0 && OFF_XI % 1024 == 0 && OFF_STG % 1024 == 0, "swizzle atoms");
+constexpr int MAX_GRID = 160;                    // CTAs a launch may have (tile ranges in the parameters)
+// A block-row start costs about SEGC tiles (D1 drained, X_I reloaded into
+// TMEM, the pipelines refilled): CTAs whose range crosses many short rows
+// near the end of the triangle get fewer tiles.
+constexpr int64_t SEGC = 2;
+
+// Shared-memory layout for MR staged rows of X^T (the sketch width m <= MR,
+// MR a multiple of 8): a ring of NA tiles of A' and a ring of NX boxes of
+// X^T (64 rows of X each: an X_J operand, or one of the four 64-row chunks
+// of X_I on their way into TMEM), then the staging boxes.  The UMMA A
+// operand spans M = 128 rows; rows MR..127 read whatever follows the box
+// (the next box or the staging boxes, all inside the allocation) and only
+// produce accumulator lanes >= m, which the epilogue never stores.
+template <int MR>
+struct Lay {
+    static constexpr int NA = MR <= 64 ? 5 : 4;
+    static constexpr int NX = MR <= 64 ? 4 : (MR <= 112 ? 4 : 3);
+    static constexpr uint32_t XB = MR * 128;                  // one box: MR rows x 64 bf16
+    static constexpr uint32_t OFF_X = NA * A_BYTES;
+    static constexpr uint32_t OFF_STG = OFF_X + NX * XB;
+    static constexpr uint32_t OFF_BAR = OFF_STG + NEPI * STG_BYTES;
+    static constexpr uint32_t SMEM = OFF_BAR + 256;
+    static_assert(MR % 8 == 0 && MR <= 128, "staged rows");
+    static_assert(SMEM <= 232448, "shared memory");
+    static_assert(XB % 1024 == 0 && OFF_X % 1024 == 0 && OFF_STG % 1024 == 0, "swizzle atoms");
+};
 
 struct Bars {
-    uint64_t full[NSTAGE], empty[NSTAGE];
-    uint64_t fullXI, emptyXI;
+    uint64_t fullA[5], emptyA[5];
+    uint64_t fullX[4], emptyX[4];
     uint64_t d2full[2], d2empty[2];
     uint64_t d1full, d1empty;
+    uint64_t xidone;     // a block row's P2 MMAs (readers of X_I in TMEM) are complete
     uint64_t mmadone;
     uint32_t tmem_base;
     int abort;
@@ -83,7 +110,8 @@ struct Params {
     float *Y;
     int64_t ldy;
     int *d_status;
-    int tma_y;          // Y reduced by TMA (aligned Y); else scalar atomics
+    int tma_y;                  // Y reduced by TMA (aligned Y); else scalar atomics
+    int64_t tstart[MAX_GRID + 1];  // CTA b owns tiles tstart[b] .. tstart[b + 1] - 1
 };
 
 __device__ __forceinline__ void tile_of(int64_t t, int nbc, int nbr, int &I, int &J)
@@ -148,47 +176,46 @@ __device__ __forceinline__ void flush32(const Params &P, const CUtensorMap *tmY,
     }
 }
 
+// The X ring carries, in production order, the four X_I chunks of every
+// block row the CTA enters, then the X_J box of every tile; each consumer
+// (P2 for the chunks, P1 for the boxes) counts the items the same way.
+struct XSeq {
+    int64_t item = 0;
+    __device__ __forceinline__ int slot(int nx) const { return (int)(item % nx); }
+    __device__ __forceinline__ uint32_t phase(int nx) const { return (uint32_t)((item / nx) & 1); }
+};
+
+template <int MR>
 __global__ void __launch_bounds__(NT, 1)
 sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CUtensorMap tmX,
-                     const __grid_constant__ CUtensorMap tmY, const Params P)
+                     const __grid_constant__ CUtensorMap tmY, const __grid_constant__ Params P)
 {
+    using L = Lay<MR>;
+    constexpr int NA = L::NA, NX = L::NX;
     extern __shared__ __align__(1024) uint8_t sm[];
-    Bars &B = *reinterpret_cast<Bars *>(sm + OFF_BAR);
+    Bars &B = *reinterpret_cast<Bars *>(sm + L::OFF_BAR);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // equal shares of cost(t) = t + SEGC * (row of t): a block-row start costs
-    // about SEGC tiles (D1 drained, X_I reloaded, the pipeline refilled), so
-    // CTAs whose range crosses many short rows near the end get fewer tiles
-    auto first_tile = [&](int64_t b) -> int64_t {
-        constexpr int64_t SEGC = 4;
-        const int64_t target = (P.tiles + SEGC * P.nbr) * b / gridDim.x;
-        int64_t lo = 0, hi = P.tiles;                // smallest t with cost(t) >= target
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            int Im, Jm;
-            tile_of(mid, P.nbc, P.nbr, Im, Jm);
-            if (mid + SEGC * Im >= target) hi = mid; else lo = mid + 1;
-        }
-        return lo;
-    };
-    const int64_t t0 = first_tile(blockIdx.x);
-    const int64_t t1 = blockIdx.x + 1 == gridDim.x ? P.tiles : first_tile(blockIdx.x + 1);
+    const int64_t t0 = P.tstart[blockIdx.x], t1 = P.tstart[blockIdx.x + 1];
     if ((smem_u32(sm) & 1023u) != 0u) {
         if (threadIdx.x == 0) psd_set_status(P.d_status, PSDPROJ_ECUDA);
         return;
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(&B.full[s], 1);
-            mbar_init(&B.empty[s], 2);    // both MMA threads
+        for (int s = 0; s < NA; ++s) {
+            mbar_init(&B.fullA[s], 1);
+            mbar_init(&B.emptyA[s], 2);   // both MMA threads
+        }
+        for (int s = 0; s < NX; ++s) {
+            mbar_init(&B.fullX[s], 1);
+            mbar_init(&B.emptyX[s], 1);   // the one consumer of the item
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&B.d2full[b], 1);
-            mbar_init(&B.d2empty[b], 4);
+            mbar_init(&B.d2empty[b], NEPI);
         }
-        mbar_init(&B.fullXI, 1);
-        mbar_init(&B.emptyXI, 1);
         mbar_init(&B.d1full, 1);
-        mbar_init(&B.d1empty, 4);
+        mbar_init(&B.d1empty, NEPI);
+        mbar_init(&B.xidone, 1);
         mbar_init(&B.mmadone, 2);
         B.abort = 0;
         fence_proxy_async_smem();
@@ -210,29 +237,38 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     if (warp == 0) {
         // ------------------------------------------------------------ TMA
         if (lane == 0) {
-            int I = I0, J = J0, curI = -1, xi_uses = 0;
+            int I = I0, J = J0, curI = -1;
             int64_t it = 0;
-            for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
+            XSeq xs;
+            bool ok = true;
+            auto push_x = [&](int x) -> bool {      // one 64-row box of X^T at row x
+                const int sl = xs.slot(NX);
+                if (!mbar_wait(&B.emptyX[sl], xs.phase(NX) ^ 1, abort, WAIT_LIMIT)) return false;
+                mbar_arrive_expect_tx(&B.fullX[sl], L::XB);
+                tma_load_2d(sm + L::OFF_X + sl * L::XB, &tmX, x, 0, &B.fullX[sl]);
+                ++xs.item;
+                return true;
+            };
+            for (int64_t t = t0; t < t1 && ok; ++t, ++it, tile_next(I, J, P.nbc)) {
                 if (I != curI) {
-                    if (!mbar_wait(&B.emptyXI, (xi_uses & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                    mbar_arrive_expect_tx(&B.fullXI, XI_BYTES);
-                    for (int kk = 0; kk < BM / 64; ++kk)
-                        tma_load_2d(sm + OFF_XI + kk * 16384, &tmX, BM * I + 64 * kk, 0, &B.fullXI);
-                    ++xi_uses;
+                    for (int kk = 0; kk < BM / 64 && ok; ++kk) ok = push_x(BM * I + 64 * kk);
                     curI = I;
                 }
-                const int s = (int)(it % NSTAGE);
-                const uint32_t us = (uint32_t)(it / NSTAGE);
-                if (!mbar_wait(&B.empty[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                mbar_arrive_expect_tx(&B.full[s], STAGE);
-                bulk_load(sm + OFF_A + s * STAGE, Ab + t * PSD_TILE_ELEMS, A_BYTES, &B.full[s]);
-                tma_load_2d(sm + OFF_A + s * STAGE + A_BYTES, &tmX, BN * J, 0, &B.full[s]);
+                const int s = (int)(it % NA);
+                const uint32_t us = (uint32_t)(it / NA);
+                if (ok && !mbar_wait(&B.emptyA[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) ok = false;
+                if (ok) {
+                    mbar_arrive_expect_tx(&B.fullA[s], A_BYTES);
+                    bulk_load(sm + s * A_BYTES, Ab + t * PSD_TILE_ELEMS, A_BYTES, &B.fullA[s]);
+                    ok = push_x(BN * J);
+                }
             }
+            if (!ok) fail(B, P.d_status);
             // wait (bounded) for the copies still in flight to land
-            const int64_t n_it = it;
-            for (int64_t k = (n_it > NSTAGE ? n_it - NSTAGE : 0); k < n_it; ++k)
-                mbar_wait(&B.full[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1), abort, WAIT_LIMIT);
-            if (xi_uses > 0) mbar_wait(&B.fullXI, (uint32_t)((xi_uses - 1) & 1), abort, WAIT_LIMIT);
+            for (int64_t k = (it > NA ? it - NA : 0); k < it; ++k)
+                mbar_wait(&B.fullA[k % NA], (uint32_t)((k / NA) & 1), abort, WAIT_LIMIT);
+            for (int64_t k = (xs.item > NX ? xs.item - NX : 0); k < xs.item; ++k)
+                mbar_wait(&B.fullX[k % NX], (uint32_t)((k / NX) & 1), abort, WAIT_LIMIT);
         }
     } else if (warp == 1 || warp == 2) {
         // ------------------------------------------------------------ MMA
@@ -240,58 +276,88 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
         // D1), warp 2 the sixteen short transposed-product MMAs (P2, D2).
         // tcgen05.mma issue blocks once the tensor pipe's queue is full, so
         // while one thread does its bookkeeping the other's MMAs keep the
-        // pipe busy; each commits its own MMAs (a stage is free after both).
+        // pipe busy; each commits its own MMAs (an A' tile is free after both).
+        // Descriptors: one per operand base, advanced by constants (the
+        // start-address field holds addr >> 4 in its low 14 bits, and every
+        // shared-memory address here is below 2^18, so adding never carries).
         if (lane == 0) {
             const bool p1 = (warp == 1);
-            const uint32_t id1 = idesc_bf16(128, BM, 0, 0);
-            const uint32_t id2 = idesc_bf16(128, BN, 0, 1);
+            constexpr uint32_t id1 = idesc_bf16(128, BM, 0, 0);
+            constexpr uint32_t id2 = idesc_bf16(128, BN, 0, 1);
+            const uint64_t dA0 = sdesc_sw128(smem_u32(sm), 16, 1024);              // A' tile, K-major (P1)
+            const uint64_t dAmn0 = sdesc_sw128(smem_u32(sm), 16384, 1024);         // A' tile, MN-major (P2)
+            const uint64_t dX0 = sdesc_sw128(smem_u32(sm + L::OFF_X), 16, 1024);   // X^T box, K-major
             int I = I0, J = J0, curI = -1, seg = 0;
             int64_t it = 0;
-            bool issued = false;
+            XSeq xs;
+            bool issued = false, ok = true;
             for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
                 const bool first = (I != curI);
                 const bool last = (J == P.nbc - 1) || (t + 1 == t1);
                 if (first) {
-                    const bool ok = p1 ? mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT)
-                                       : mbar_wait(&B.fullXI, seg & 1, abort, WAIT_LIMIT);
-                    if (!ok) { fail(B, P.d_status); break; }
+                    if (p1) {
+                        // D1 drained by the epilogue
+                        ok = mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT);
+                        xs.item += BM / 64;
+                    } else {
+                        // the previous row's MMAs are done with X_I in TMEM;
+                        // copy the four chunks of the new X_I^T into TMEM,
+                        // freeing each ring slot once its copies complete
+                        if (seg > 0) ok = mbar_wait(&B.xidone, (seg - 1) & 1, abort, WAIT_LIMIT);
+                        for (int kk = 0; kk < BM / 64 && ok; ++kk) {
+                            const int sl = xs.slot(NX);
+                            ok = mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WAIT_LIMIT);
+                            if (!ok) break;
+                            tc_fence_after();
+                            const uint64_t xd = dX0 + (uint64_t)((sl * L::XB) >> 4);
+#pragma unroll
+                            for (int k2 = 0; k2 < 4; ++k2)
+                                tmem_cp_128x256b(tmem + XI_COL + 8 * (4 * kk + k2), xd + 2 * k2);
+                            mma_commit(&B.emptyX[sl]);
+                            ++xs.item;
+                        }
+                    }
+                    if (!ok) break;
                     curI = I;
                 }
-                const int s = (int)(it % NSTAGE);
-                const uint32_t us = (uint32_t)(it / NSTAGE);
+                const int s = (int)(it % NA);
+                const uint32_t us = (uint32_t)(it / NA);
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
-                if (!mbar_wait(&B.full[s], us & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                if (!p1 && !mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                tc_fence_after();
-                const uint32_t a_tile = smem_u32(sm + OFF_A + s * STAGE);
+                if (!mbar_wait(&B.fullA[s], us & 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                const uint64_t aoff = (uint64_t)((s * A_BYTES) >> 4);
                 if (p1) {
                     // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns)
-                    const uint32_t xj = a_tile + A_BYTES;
+                    const int sl = xs.slot(NX);
+                    if (!mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WAIT_LIMIT)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t ad = dX0 + (uint64_t)((sl * L::XB) >> 4), bd = dA0 + aoff;
 #pragma unroll
-                    for (int kk = 0; kk < BN / 16; ++kk) {
-                        const uint64_t ad = sdesc_sw128(xj + kk * 32, 16, 1024);
-                        const uint64_t bd = sdesc_sw128(a_tile + kk * 32, 16, 1024);
-                        mma_bf16_ss(tmem + D1_COL, ad, bd, id1, (!first || kk > 0) ? 1u : 0u);
-                    }
+                    for (int kk = 0; kk < BN / 16; ++kk)
+                        mma_bf16_ss(tmem + D1_COL, ad + 2 * kk, bd + 2 * kk, id1, (!first || kk > 0) ? 1u : 0u);
+                    mma_commit(&B.emptyX[sl]);
+                    ++xs.item;
                 } else {
-                    // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows)
-                    const uint32_t xi = smem_u32(sm + OFF_XI);
+                    // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows; X_I^T from TMEM)
+                    if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t bd = dAmn0 + aoff;
+                    const uint32_t dcol = tmem + D2_COL + BN * b;
 #pragma unroll
-                    for (int kk = 0; kk < BM / 16; ++kk) {
-                        const uint64_t ad = sdesc_sw128(xi + (kk >> 2) * 16384 + (kk & 3) * 32, 16, 1024);
-                        const uint64_t bd = sdesc_sw128(a_tile + kk * 2048, 16384, 1024);
-                        mma_bf16_ss(tmem + D2_COL + BN * b, ad, bd, id2, kk > 0 ? 1u : 0u);
-                    }
+                    for (int kk = 0; kk < BM / 16; ++kk)
+                        mma_bf16_ts(dcol, tmem + XI_COL + 8 * kk, bd + (uint64_t)((kk * 2048) >> 4), id2,
+                                    kk > 0 ? 1u : 0u);
+                    mma_commit(&B.d2full[b]);
+                    ++xs.item;       // the tile's X_J box (P1's)
                 }
                 issued = true;
-                mma_commit(&B.empty[s]);
-                if (!p1) mma_commit(&B.d2full[b]);
+                mma_commit(&B.emptyA[s]);
                 if (last) {
-                    mma_commit(p1 ? &B.d1full : &B.emptyXI);
+                    mma_commit(p1 ? &B.d1full : &B.xidone);
                     ++seg;
                 }
             }
+            if (!ok) fail(B, P.d_status);
             if (issued) {
                 // all MMAs of this CTA (both threads) complete before TMEM is released
                 mma_commit(&B.mmadone);
@@ -300,8 +366,13 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
         }
     } else if (warp >= 4) {
         // ------------------------------------------------------- epilogue
-        const int q = warp & 3;                // TMEM lane quarter of this warp
-        uint8_t *stg = sm + OFF_STG + q * STG_BYTES;
+        // two warps per TMEM lane quarter q (a warp reads only its own
+        // quarter): half h drains columns 32 h .. 32 h + 31 of D2 after every
+        // tile and the 32-column chunks h, h + 2, ... of D1 after a block row
+        const int q = warp & 3;
+        const int h = (warp - 4) >> 2;
+        uint8_t *stg = sm + L::OFF_STG + (warp - 4) * STG_BYTES;
+        const uint32_t lane_base = (uint32_t)(32 * q) << 16;
         int I = I0, J = J0, seg = 0;
         int64_t it = 0;
         for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
@@ -316,15 +387,12 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 if (!ok) { if (lane == 0) fail(B, P.d_status); break; }
             }
             tc_fence_after();
-            float v0[32], v1[32];
-            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + D2_COL + BN * b;
-            tmem_ld32(ta, v0);
-            tmem_ld32(ta + 32, v1);
+            float v[32];
+            tmem_ld32(tmem + lane_base + D2_COL + BN * b + 32 * h, v);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&B.d2empty[b]);
-            flush32(P, &tmY, stg, q, lane, (int64_t)BN * J, v0);
-            flush32(P, &tmY, stg, q, lane, (int64_t)BN * J + 32, v1);
+            flush32(P, &tmY, stg, q, lane, (int64_t)BN * J + 32 * h, v);
             if (last) {
                 int ok = 1;
                 if (lane == 0) ok = mbar_wait(&B.d1full, seg & 1, abort, WAIT_LIMIT) ? 1 : 0;
@@ -333,10 +401,10 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 tc_fence_after();
                 const int64_t r0 = (int64_t)BM * I;
 #pragma unroll 1
-                for (int ch = 0; ch < BM / 32; ++ch) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + D1_COL + 32 * ch, v);
-                    flush32(P, &tmY, stg, q, lane, r0 + 32 * ch, v);
+                for (int ch = h; ch < BM / 32; ch += 2) {
+                    float w[32];
+                    tmem_ld32(tmem + lane_base + D1_COL + 32 * ch, w);
+                    flush32(P, &tmY, stg, q, lane, r0 + 32 * ch, w);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -480,6 +548,8 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
         return cudaErrorNotSupported;
     auto encode = get_encode();
     if (!encode) return cudaErrorNotSupported;
+    // rows of X^T staged in shared memory: the sketch width rounded up
+    const int mr = m <= 64 ? 64 : (m <= 112 ? 112 : 128);
 
     // BF16 image of X (rows n, columns m; TMA fills the rest with zeros);
     // Y starts at shift X (accumulate = 0) or gains it (accumulate = 1)
@@ -495,7 +565,7 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
     {
         cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
         cuuint64_t strides[1] = {(cuuint64_t)ldh * 2};
-        cuuint32_t box[2] = {64, 128};
+        cuuint32_t box[2] = {64, (cuuint32_t)mr};
         cuuint32_t estr[2] = {1, 1};
         if (encode(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, Xh, dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -524,12 +594,29 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             P.tma_y = 0;
     }
-
-    cudaError_t e = cudaFuncSetAttribute(sym_pass_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
     int grid = sm_count > 0 ? sm_count : 148;
+    if (grid > MAX_GRID) grid = MAX_GRID;
     if ((int64_t)grid > P.tiles) grid = (int)P.tiles;
-    sym_pass_bf16_kernel<<<grid, NT, SMEM_BYTES, s>>>(Ab, tmX, tmY, P);
-    return cudaGetLastError();
+    // contiguous tile ranges of equal cost(t) = t + SEGC * (block row of t):
+    // CTA b starts at the smallest t with cost(t) >= total cost * b / grid
+    {
+        const int64_t total = P.tiles + SEGC * P.nbr;
+        int b = 0, I = 0;
+        P.tstart[0] = 0;
+        for (int64_t t = 0; t < P.tiles && b + 1 < grid; ++t) {
+            while (I + 1 < P.nbr && psd_tile_row_start(I + 1, P.nbc) <= t) ++I;
+            while (b + 1 < grid && t + SEGC * I >= total * (b + 1) / grid) P.tstart[++b] = t;
+        }
+        while (b + 1 < grid) P.tstart[++b] = P.tiles;
+        P.tstart[grid] = P.tiles;
+    }
+    auto go = [&](auto kern, uint32_t smem) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, NT, smem, s>>>(Ab, tmX, tmY, P);
+        return cudaGetLastError();
+    };
+    if (mr == 64) return go(sym_pass_bf16_kernel<64>, Lay<64>::SMEM);
+    if (mr == 112) return go(sym_pass_bf16_kernel<112>, Lay<112>::SMEM);
+    return go(sym_pass_bf16_kernel<128>, Lay<128>::SMEM);
 }

@@ -192,6 +192,28 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t d_tmem, uint64_t adesc, uin
         : "memory");
 }
 
+// The same with the A operand in tensor memory (a_tmem: its first column;
+// M = 128 lanes, K = 16 BF16 values in 8 consecutive 32-bit columns).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Asynchronous copy of 128 rows x 256 bits of a shared-memory matrix
+// (descriptor sdesc) into tensor memory: row r to lane r, 8 columns from
+// taddr; the layout the A operand of mma_bf16_ts reads.  Ordered with the
+// issuing thread's later tcgen05.mma; tracked by its tcgen05.commit.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc)
+{
+    asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile(

@@ -398,7 +398,7 @@ def _padded_A(A, pad=4):
 
 
 @pytest.mark.parametrize("n", [1, 63, 64, 65, 255, 256, 257, 1000, 4099])
-@pytest.mark.parametrize("m", [1, 7, 50, 112, 128])
+@pytest.mark.parametrize("m", [1, 7, 50, 64, 65, 110, 112, 113, 128])
 def test_sym_pass_bf16_tensor_cores(ctx, oracle_lib, n, m):
     A = _sym_A(n, seed=n + 13 * m)
     rng = np.random.default_rng(m + 1)
