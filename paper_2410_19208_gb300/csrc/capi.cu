@@ -231,8 +231,12 @@ int pack_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, int pre
 // Y = A X + shift X in the requested precision (tensor-core forms: from the
 // image(s) that pack_image wrote last).  Split BF16: A X ~ A_hi X_hi + A_hi X_lo
 // + A_lo X_hi, three tensor-core passes adding into Y.
+// prepared: the producer of X already wrote the BF16 form's side outputs
+// (ws.Xhi = bf16(X), Y = shift X; see psd_bf16_side), so the pass skips its
+// conversion sweep (BF16 form, m <= 128 only).
 int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const float *X,
-             int64_t ldx, int m, const double *d_shift, float *Y, int64_t ldy, int prec)
+             int64_t ldx, int m, const double *d_shift, float *Y, int64_t ldy, int prec,
+             bool prepared = false)
 {
     stage_scope st(ctx, PSDPROJ_STAGE_APASS);
     if (prec == PSDPROJ_PREC_FP32) {
@@ -255,8 +259,9 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
             continue;
         }
         uint16_t *Xhi = ws.Xhi + (int64_t)c0 * ws.ld, *Xlo = ws.Xlo + (int64_t)c0 * ws.ld;
+        const bool prep = prepared && prec == PSDPROJ_PREC_BF16 && m <= 128;
         PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, Xc, ldx, mc, d_shift, Yc, ldy,
-                                  Xhi, ws.ld, ctx->d_status, 0, 0), 2);
+                                  Xhi, ws.ld, ctx->d_status, 0, 0, prep ? 1 : 0), prep ? 1 : 2);
         if (prec == PSDPROJ_PREC_BF16X3) {
             PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, Xc, ldx, mc, nullptr, Yc, ldy,
                                       Xlo, ws.ld, ctx->d_status, 1, 1), 2);
@@ -267,9 +272,10 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
     return PSDPROJ_OK;
 }
 
-// CholeskyQR2: Q = orth(Y); Y is read only in the first half.
+// CholeskyQR2: Q = orth(Y); Y is read only in the first half.  side (may be
+// NULL): the final product also writes the BF16 pass's side outputs of Q.
 int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, float *Q,
-            int64_t ldq, int *d_qrank)
+            int64_t ldq, int *d_qrank, const psd_bf16_side *side = nullptr)
 {
     psd_workspace &ws = ctx->ws;
     cudaStream_t s = ctx->stream;
@@ -282,7 +288,7 @@ int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, flo
     PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1), 2);
     PSD_KL(launch_cholesky(s, ws.G, m, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
                            ws.cholscr), 1);
-    PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq), 1);
+    PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq, side), 1);
     return PSDPROJ_OK;
 }
 
@@ -347,13 +353,24 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         shift = sc + SC_SHIFT;
     }
     const int lpad = psd_lpad(m);
+    // BF16 form: every kernel that writes the next pass's X (Omega, the last
+    // product of each CholeskyQR2) also writes that pass's BF16 image of X
+    // and starts its Y, so the passes need no conversion sweep
+    const bool fuse = bf16 && m <= 128 && !ritz;
+    auto side_for = [&](const double *next_shift) {
+        return psd_bf16_side{ws.Xhi, ws.ld, ws.Y, ws.ld, next_shift};
+    };
+    bool prepared = false;
     // Omega (Alg. 1), then Y = (A + shift I) Omega
     if (!omega_ready) {
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
-        if (opts.sketch == PSDPROJ_SKETCH_SRHT)
+        if (opts.sketch == PSDPROJ_SKETCH_SRHT) {
             PSD_KL(launch_srht(s, seed, n, m, lpad, ws.ld, ws.picks, ctx->d_status, ws.Om, ws.ld), 2);
-        else
-            PSD_KL(launch_gaussian(s, seed, 0u, n, m, lpad, ws.ld, ws.Om, ws.ld), 1);
+        } else {
+            const psd_bf16_side sd = side_for(shift);
+            PSD_KL(launch_gaussian(s, seed, 0u, n, m, lpad, ws.ld, ws.Om, ws.ld, fuse ? &sd : nullptr), 1);
+            prepared = fuse;
+        }
     }
     if (ritz) {
         // Alg. 3's first product without the shift, A Omega, does not depend
@@ -379,15 +396,21 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         PSD_KL(launch_add_shift(s, ws.Y, ws.Om, n, m, ws.ld, sc + SC_SHIFT), 1);
         shift = sc + SC_SHIFT;
     } else {
-        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, shift, ws.Y, ws.ld, opts.prec));
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, shift, ws.Y, ws.ld, opts.prec, prepared));
     }
-    PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
+    // the orthonormalisation after product t writes the side outputs of the
+    // next pass: a power product (shifted) while t < 2q, else the core (Y = 0)
+    {
+        const psd_bf16_side sd = side_for(q > 0 ? shift : nullptr);
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, fuse ? &sd : nullptr));
+    }
     for (int t = 0; t < 2 * q; ++t) {
-        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, shift, ws.Y, ws.ld, opts.prec));
-        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, shift, ws.Y, ws.ld, opts.prec, fuse));
+        const psd_bf16_side sd = side_for(t + 1 < 2 * q ? shift : nullptr);
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, fuse ? &sd : nullptr));
     }
     // core C = Q^T A Q (Lemma 4: the unshifted A in both algorithms)
-    PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec));
+    PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec, fuse));
     {
         stage_scope st(ctx, PSDPROJ_STAGE_CORE);
         PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.Y, ws.ld, n, m, ws.gpart, ws.C, 2), 2);

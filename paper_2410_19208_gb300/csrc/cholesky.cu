@@ -17,6 +17,8 @@
 // norm of y_j after removing the earlier columns) is <= tau * max_i G_ii, or
 // is not a number.  Its row of R becomes e_j^T, so it feeds no other column,
 // and its column of Q is written as zero (it then adds nothing to Q^T A Q).
+#include <cuda_bf16.h>
+
 #include "ctx.h"
 
 namespace {
@@ -585,7 +587,8 @@ template <int T>
 __global__ void __launch_bounds__(256)
 tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m,
                        const float *__restrict__ B, int c, const int *__restrict__ colmask,
-                       const int *__restrict__ d_cols, float *__restrict__ Z, int64_t ldz)
+                       const int *__restrict__ d_cols, float *__restrict__ Z, int64_t ldz,
+                       psd_bf16_side side)
 {
     constexpr int S = 16 * T;
     constexpr int KW = 32;                      // K rows staged at a time
@@ -646,6 +649,7 @@ tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int 
                 for (int j = 0; j < T; ++j) acc[i][j] = fmaf(y[i], b[j], acc[i][j]);
         }
     }
+    const float shift = side.d_shift ? (float)*side.d_shift : 0.0f;
 #pragma unroll
     for (int j = 0; j < T; ++j) {
         const int gc = ty * T + j;
@@ -654,7 +658,12 @@ tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int 
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int64_t gr = r0 + 4 * tx + i;
-            if (gr < n) Z[(int64_t)gc * ldz + gr] = zero ? 0.0f : acc[i][j];
+            if (gr >= n) continue;
+            const float z = zero ? 0.0f : acc[i][j];
+            Z[(int64_t)gc * ldz + gr] = z;
+            // side outputs for the BF16 pass that reads Z next
+            if (side.Xh) side.Xh[(int64_t)gc * side.ldh + gr] = __bfloat16_as_ushort(__float2bfloat16_rn(z));
+            if (side.Y) side.Y[(int64_t)gc * side.ldy + gr] = shift * z;
         }
     }
 }
@@ -699,18 +708,20 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv,
 
 cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64_t n, int m,
                               const float *B, int c, const int *colmask, const int *d_cols,
-                              float *Z, int64_t ldz)
+                              float *Z, int64_t ldz, const psd_bf16_side *side)
 {
     const unsigned rb = (unsigned)((n + TR - 1) / TR);
+    const psd_bf16_side sd = side ? *side : psd_bf16_side{nullptr, 0, nullptr, 0, nullptr};
+    if (side && c > 128) return cudaErrorNotSupported;
     switch ((c + 15) / 16) {
-    case 1: tall_small_wide_kernel<1><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
-    case 2: tall_small_wide_kernel<2><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
-    case 3: tall_small_wide_kernel<3><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
-    case 4: tall_small_wide_kernel<4><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
-    case 5: tall_small_wide_kernel<5><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
-    case 6: tall_small_wide_kernel<6><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
-    case 7: tall_small_wide_kernel<7><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
-    case 8: tall_small_wide_kernel<8><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz); break;
+    case 1: tall_small_wide_kernel<1><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
+    case 2: tall_small_wide_kernel<2><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
+    case 3: tall_small_wide_kernel<3><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
+    case 4: tall_small_wide_kernel<4><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
+    case 5: tall_small_wide_kernel<5><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
+    case 6: tall_small_wide_kernel<6><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
+    case 7: tall_small_wide_kernel<7><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
+    case 8: tall_small_wide_kernel<8><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
     default: {
         dim3 grid(rb, (unsigned)((c + TC - 1) / TC));
         tall_small_kernel<<<grid, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz);

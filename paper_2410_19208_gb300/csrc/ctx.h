@@ -126,9 +126,22 @@ struct psdproj_ctx {
 int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m);
 
 // ---- launchers (all asynchronous on `s`; return cudaGetLastError) -------
+// Side outputs of a kernel that writes a tall matrix Z (n x m) which the
+// BF16 tensor-core pass reads next: Xh = bf16(Z) (column-major, ldh >= n)
+// and Y = shift Z with shift = *d_shift (Y = 0 when d_shift is NULL; ldy >=
+// n), both over rows < n and columns < m, so that the pass needs no
+// conversion sweep of its own.  Xh / Y may be NULL.
+struct psd_bf16_side {
+    uint16_t *Xh;
+    int64_t ldh;
+    float *Y;
+    int64_t ldy;
+    const double *d_shift;
+};
+
 cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, uint32_t stream_id,
                             int64_t n, int m, int mpad, int64_t rows_pad,
-                            float *X, int64_t ldx);
+                            float *X, int64_t ldx, const psd_bf16_side *side = nullptr);
 
 // D[i*ldd + j] = S[i*lds + j] for j >= i (the upper triangle; S may be
 // pinned host memory read over the host link)
@@ -187,10 +200,13 @@ cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, 
 // handles (m > 128, misaligned buffers).
 // x_part 0 / 1: multiply by the high / low BF16 part of X; accumulate != 0:
 // add to Y instead of overwriting it (pass d_shift = NULL then).
+// prepared != 0: the producer of X already wrote Xh = bf16(X) and Y = shift X
+// (psd_bf16_side; x_part 0, accumulate 0 only): no conversion sweep.
 cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t n, const float *X, int64_t ldx, int m,
                                const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
-                               int64_t ldh, int *d_status, int x_part, int accumulate);
+                               int64_t ldh, int *d_status, int x_part, int accumulate,
+                               int prepared = 0);
 
 // Gram partials + FP64 reduction: G = X^T Z (sym = 1: X == Z, symmetric).
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
@@ -209,9 +225,10 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv,
 // colmask (may be NULL): columns j with colmask[j] != 0 are written as zero.
 // d_cols (may be NULL): device int; only the first *d_cols columns of B are
 // used and the rest of Z is written as zero.
+// side (may be NULL, c <= 128 only): the BF16 pass's side outputs of Z.
 cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64_t n, int m,
                               const float *B, int c, const int *colmask, const int *d_cols,
-                              float *Z, int64_t ldz);
+                              float *Z, int64_t ldz, const psd_bf16_side *side = nullptr);
 
 // scratch: 3 (m+2)^2 floats of device memory (used when m is too large for
 // shared memory); d_flag: one device int (the tridiagonal solver's failure

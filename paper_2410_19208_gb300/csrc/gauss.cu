@@ -9,6 +9,8 @@
 // width and of the launch shape.  The transform runs in FP32 with CUDA's logf,
 // log1pf and cospif; -2 ln u is taken through log1p when u >= 1/2 so that no
 // cancellation occurs.
+#include <cuda_bf16.h>
+
 #include "ctx.h"
 
 namespace {
@@ -53,8 +55,9 @@ __device__ __forceinline__ float box_muller(uint32_t w0, uint32_t w1)
 
 __global__ void gaussian_kernel(uint64_t seed, uint32_t stream_id, int64_t n, int m,
                                 int mpad, int64_t rows_pad, float *__restrict__ X,
-                                int64_t ldx)
+                                int64_t ldx, psd_bf16_side side)
 {
+    const float shift = side.d_shift ? (float)*side.d_shift : 0.0f;
     const uint32_t k0 = (uint32_t)(seed & 0xffffffffu);
     const uint32_t k1 = (uint32_t)(seed >> 32);
     const int64_t total = rows_pad * (int64_t)mpad;
@@ -67,6 +70,8 @@ __global__ void gaussian_kernel(uint64_t seed, uint32_t stream_id, int64_t n, in
             uint32_t w0, w1;
             philox4x32_10((uint32_t)i, (uint32_t)c, stream_id, 0u, k0, k1, w0, w1);
             v = box_muller(w0, w1);
+            if (side.Xh) side.Xh[(int64_t)c * side.ldh + i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+            if (side.Y) side.Y[(int64_t)c * side.ldy + i] = shift * v;
         }
         X[(int64_t)c * ldx + i] = v;
     }
@@ -151,12 +156,14 @@ cudaError_t launch_srht(cudaStream_t s, uint64_t seed, int64_t n, int m, int mpa
 // Writes rows [0, rows_pad) x columns [0, mpad); entries with i >= n or
 // c >= m are zero (padding of context-owned buffers).
 cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, uint32_t stream_id, int64_t n,
-                            int m, int mpad, int64_t rows_pad, float *X, int64_t ldx)
+                            int m, int mpad, int64_t rows_pad, float *X, int64_t ldx,
+                            const psd_bf16_side *side)
 {
+    const psd_bf16_side none = {nullptr, 0, nullptr, 0, nullptr};
     const int64_t total = rows_pad * (int64_t)mpad;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    gaussian_kernel<<<blocks, 256, 0, s>>>(seed, stream_id, n, m, mpad, rows_pad, X, ldx);
+    gaussian_kernel<<<blocks, 256, 0, s>>>(seed, stream_id, n, m, mpad, rows_pad, X, ldx, side ? *side : none);
     return cudaGetLastError();
 }

@@ -214,7 +214,7 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
             }
             const int64_t n_it = it;
             for (int64_t k = (n_it > gt::STAGES ? n_it - gt::STAGES : 0); k < n_it; ++k)
-                mbar_wait(&full[k % gt::STAGES], (uint32_t)((k / gt::STAGES) & 1), abort, gt::WAIT_LIMIT);
+                mbar_wait_drain(&full[k % gt::STAGES], (uint32_t)((k / gt::STAGES) & 1), gt::WAIT_LIMIT);
         }
     } else if (t0 < t1) {
         // ---- compute: thread (g, k): rows 8g..8g+7, columns 8k..8k+7 of each tile

@@ -34,10 +34,9 @@
 //
 // Warp roles (384 threads, one CTA per SM, persistent over a cost-balanced
 // range of the tiles in row-major order): warp 0 issues the copies, warp 1
-// owns TMEM and issues the row-product MMAs, warp 2 the transposed-product
-// MMAs (one thread each), warps 4-11 drain TMEM, two per TMEM lane quarter,
-// so that every epilogue warp stages and reduces one 32 x 32 box of D2 per
-// tile.  Every mbarrier wait is bounded; on a timeout the CTA records
+// owns TMEM and issues every tcgen05 operation (one thread), warps 4-11
+// drain TMEM, two per TMEM lane quarter, so that every epilogue warp stages
+// and reduces one 32 x 32 box of D2 per tile.  Every mbarrier wait is bounded; on a timeout the CTA records
 // PSDPROJ_ETIMEOUT, unwinds and frees its TMEM.
 #include <cuda_bf16.h>
 #include <cstring>
@@ -70,19 +69,20 @@ constexpr int MAX_GRID = 160;                    // CTAs a launch may have (tile
 constexpr int64_t SEGC = 2;
 
 // Shared-memory layout for MR staged rows of X^T (the sketch width m <= MR,
-// MR a multiple of 8): a ring of NA tiles of A' and a ring of NX boxes of
+// MR a multiple of 8): a ring of NA tiles of A' and a ring of NX slots of
 // X^T (64 rows of X each: an X_J operand, or one of the four 64-row chunks
-// of X_I on their way into TMEM), then the staging boxes.  The UMMA A
-// operand spans M = 128 rows; rows MR..127 read whatever follows the box
-// (the next box or the staging boxes, all inside the allocation) and only
-// produce accumulator lanes >= m, which the epilogue never stores.
+// of X_I on their way into TMEM), then the staging boxes.  A slot holds the
+// 128 rows that the UMMA A operand (M = 128) reads; the copy fills rows
+// 0..MR-1 and rows MR..127 stay zero (written once at the start), so no
+// operand read reaches memory that a copy is writing.
 template <int MR>
 struct Lay {
-    static constexpr int NA = MR <= 64 ? 5 : 4;
-    static constexpr int NX = MR <= 64 ? 4 : (MR <= 112 ? 4 : 3);
-    static constexpr uint32_t XB = MR * 128;                  // one box: MR rows x 64 bf16
+    static constexpr int NA = 4;
+    static constexpr int NX = 4;
+    static constexpr uint32_t XB = MR * 128;                  // bytes a copy fills: MR rows x 64 bf16
+    static constexpr uint32_t XS = 128 * 128;                 // slot stride: 128 rows
     static constexpr uint32_t OFF_X = NA * A_BYTES;
-    static constexpr uint32_t OFF_STG = OFF_X + NX * XB;
+    static constexpr uint32_t OFF_STG = OFF_X + NX * XS;
     static constexpr uint32_t OFF_BAR = OFF_STG + NEPI * STG_BYTES;
     static constexpr uint32_t SMEM = OFF_BAR + 256;
     static_assert(MR % 8 == 0 && MR <= 128, "staged rows");
@@ -91,11 +91,11 @@ struct Lay {
 };
 
 struct Bars {
-    uint64_t fullA[5], emptyA[5];
+    uint64_t fullA[4], emptyA[4];
     uint64_t fullX[4], emptyX[4];
     uint64_t d2full[2], d2empty[2];
     uint64_t d1full, d1empty;
-    uint64_t xidone;     // a block row's P2 MMAs (readers of X_I in TMEM) are complete
+    uint64_t xidone;     // the issuer's MMAs so far (X_I in TMEM may be overwritten) are complete
     uint64_t mmadone;
     uint32_t tmem_base;
     int abort;
@@ -200,10 +200,19 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
         if (threadIdx.x == 0) psd_set_status(P.d_status, PSDPROJ_ECUDA);
         return;
     }
+    // rows MR..127 of every X slot: zero, written once (the copies fill rows
+    // 0..MR-1 only); visible to the tensor core's reads through the fence below
+    if (MR < 128) {
+        constexpr int PADV = (128 - MR) * 128 / 16;          // 16-byte words per slot
+        for (int e = threadIdx.x; e < NX * PADV; e += NT) {
+            const int slot = e / PADV, w = e % PADV;
+            *reinterpret_cast<uint4 *>(sm + L::OFF_X + slot * L::XS + L::XB + 16 * w) = make_uint4(0, 0, 0, 0);
+        }
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < NA; ++s) {
             mbar_init(&B.fullA[s], 1);
-            mbar_init(&B.emptyA[s], 2);   // both MMA threads
+            mbar_init(&B.emptyA[s], 1);   // the MMA issuer
         }
         for (int s = 0; s < NX; ++s) {
             mbar_init(&B.fullX[s], 1);
@@ -216,9 +225,11 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
         mbar_init(&B.d1full, 1);
         mbar_init(&B.d1empty, NEPI);
         mbar_init(&B.xidone, 1);
-        mbar_init(&B.mmadone, 2);
+        mbar_init(&B.mmadone, 1);
         B.abort = 0;
-        fence_proxy_async_smem();
+    }
+    fence_proxy_async_smem();
+    if (threadIdx.x == 0) {
         prefetch_tmap(&tmX);
         if (P.tma_y) prefetch_tmap(&tmY);
     }
@@ -238,84 +249,80 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
         // ------------------------------------------------------------ TMA
         if (lane == 0) {
             int I = I0, J = J0, curI = -1;
-            int64_t it = 0;
-            XSeq xs;
+            int64_t na = 0;         // A' tiles whose copy was issued (ring position)
+            XSeq xs;                // X boxes whose copy was issued
             bool ok = true;
             auto push_x = [&](int x) -> bool {      // one 64-row box of X^T at row x
                 const int sl = xs.slot(NX);
                 if (!mbar_wait(&B.emptyX[sl], xs.phase(NX) ^ 1, abort, WAIT_LIMIT)) return false;
                 mbar_arrive_expect_tx(&B.fullX[sl], L::XB);
-                tma_load_2d(sm + L::OFF_X + sl * L::XB, &tmX, x, 0, &B.fullX[sl]);
+                tma_load_2d(sm + L::OFF_X + sl * L::XS, &tmX, x, 0, &B.fullX[sl]);
                 ++xs.item;
                 return true;
             };
-            for (int64_t t = t0; t < t1 && ok; ++t, ++it, tile_next(I, J, P.nbc)) {
+            for (int64_t t = t0; t < t1 && ok; ++t, tile_next(I, J, P.nbc)) {
                 if (I != curI) {
                     for (int kk = 0; kk < BM / 64 && ok; ++kk) ok = push_x(BM * I + 64 * kk);
+                    if (!ok) break;
                     curI = I;
                 }
-                const int s = (int)(it % NA);
-                const uint32_t us = (uint32_t)(it / NA);
-                if (ok && !mbar_wait(&B.emptyA[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) ok = false;
-                if (ok) {
-                    mbar_arrive_expect_tx(&B.fullA[s], A_BYTES);
-                    bulk_load(sm + s * A_BYTES, Ab + t * PSD_TILE_ELEMS, A_BYTES, &B.fullA[s]);
-                    ok = push_x(BN * J);
-                }
+                const int s = (int)(na % NA);
+                const uint32_t us = (uint32_t)(na / NA);
+                if (!mbar_wait(&B.emptyA[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                mbar_arrive_expect_tx(&B.fullA[s], A_BYTES);
+                bulk_load(sm + s * A_BYTES, Ab + t * PSD_TILE_ELEMS, A_BYTES, &B.fullA[s]);
+                ++na;
+                ok = push_x(BN * J);
             }
             if (!ok) fail(B, P.d_status);
-            // wait (bounded) for the copies still in flight to land
-            for (int64_t k = (it > NA ? it - NA : 0); k < it; ++k)
-                mbar_wait(&B.fullA[k % NA], (uint32_t)((k / NA) & 1), abort, WAIT_LIMIT);
+            // wait (bounded, also after giving up) for the copies in flight to land
+            for (int64_t k = (na > NA ? na - NA : 0); k < na; ++k)
+                mbar_wait_drain(&B.fullA[k % NA], (uint32_t)((k / NA) & 1), WAIT_LIMIT);
             for (int64_t k = (xs.item > NX ? xs.item - NX : 0); k < xs.item; ++k)
-                mbar_wait(&B.fullX[k % NX], (uint32_t)((k / NX) & 1), abort, WAIT_LIMIT);
+                mbar_wait_drain(&B.fullX[k % NX], (uint32_t)((k / NX) & 1), WAIT_LIMIT);
         }
-    } else if (warp == 1 || warp == 2) {
+    } else if (warp == 1) {
         // ------------------------------------------------------------ MMA
-        // two issuing threads: warp 1 the four long row-product MMAs (P1,
-        // D1), warp 2 the sixteen short transposed-product MMAs (P2, D2).
-        // tcgen05.mma issue blocks once the tensor pipe's queue is full, so
-        // while one thread does its bookkeeping the other's MMAs keep the
-        // pipe busy; each commits its own MMAs (an A' tile is free after both).
-        // Descriptors: one per operand base, advanced by constants (the
-        // start-address field holds addr >> 4 in its low 14 bits, and every
-        // shared-memory address here is below 2^18, so adding never carries).
+        // One issuing thread (it also owns TMEM): per tile the sixteen short
+        // transposed-product MMAs (P2, into the double-buffered D2), then
+        // the four long row-product MMAs (P1, into D1); at a block-row start
+        // the four chunks of X_I^T are first copied into TMEM, after the
+        // thread's own earlier MMAs (readers of the previous X_I) are
+        // complete.  Every tcgen05 operation is issued by this thread, in
+        // program order.  Descriptors: one per operand base, advanced by
+        // constants (the start-address field holds addr >> 4 in its low 14
+        // bits, and every shared-memory address here is below 2^18, so
+        // adding never carries).
         if (lane == 0) {
-            const bool p1 = (warp == 1);
             constexpr uint32_t id1 = idesc_bf16(128, BM, 0, 0);
             constexpr uint32_t id2 = idesc_bf16(128, BN, 0, 1);
             const uint64_t dA0 = sdesc_sw128(smem_u32(sm), 16, 1024);              // A' tile, K-major (P1)
             const uint64_t dAmn0 = sdesc_sw128(smem_u32(sm), 16384, 1024);         // A' tile, MN-major (P2)
-            const uint64_t dX0 = sdesc_sw128(smem_u32(sm + L::OFF_X), 16, 1024);   // X^T box, K-major
+            const uint64_t dX0 = sdesc_sw128(smem_u32(sm + L::OFF_X), 16, 1024);   // X^T slot, K-major
             int I = I0, J = J0, curI = -1, seg = 0;
             int64_t it = 0;
             XSeq xs;
-            bool issued = false, ok = true;
+            bool ok = true;
             for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
                 const bool first = (I != curI);
                 const bool last = (J == P.nbc - 1) || (t + 1 == t1);
                 if (first) {
-                    if (p1) {
-                        // D1 drained by the epilogue
-                        ok = mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT);
-                        xs.item += BM / 64;
-                    } else {
-                        // the previous row's MMAs are done with X_I in TMEM;
-                        // copy the four chunks of the new X_I^T into TMEM,
-                        // freeing each ring slot once its copies complete
-                        if (seg > 0) ok = mbar_wait(&B.xidone, (seg - 1) & 1, abort, WAIT_LIMIT);
-                        for (int kk = 0; kk < BM / 64 && ok; ++kk) {
-                            const int sl = xs.slot(NX);
-                            ok = mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WAIT_LIMIT);
-                            if (!ok) break;
-                            tc_fence_after();
-                            const uint64_t xd = dX0 + (uint64_t)((sl * L::XB) >> 4);
+                    if (seg > 0) {
+                        // the previous row's MMAs read X_I in TMEM: let them complete
+                        mma_commit(&B.xidone);
+                        ok = mbar_wait(&B.xidone, (seg - 1) & 1, abort, WAIT_LIMIT);
+                    }
+                    for (int kk = 0; kk < BM / 64 && ok; ++kk) {
+                        const int sl = xs.slot(NX);
+                        ok = mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WAIT_LIMIT);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint64_t xd = dX0 + (uint64_t)((sl * L::XS) >> 4);
 #pragma unroll
-                            for (int k2 = 0; k2 < 4; ++k2)
-                                tmem_cp_128x256b(tmem + XI_COL + 8 * (4 * kk + k2), xd + 2 * k2);
-                            mma_commit(&B.emptyX[sl]);
-                            ++xs.item;
-                        }
+                        for (int k2 = 0; k2 < 4; ++k2)
+                            tmem_cp_128x256b(tmem + XI_COL + 8 * (4 * kk + k2), xd + 2 * k2);
+                        mma_commit(&B.emptyX[sl]);
+                        ++xs.item;
                     }
                     if (!ok) break;
                     curI = I;
@@ -324,23 +331,12 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 const uint32_t us = (uint32_t)(it / NA);
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
-                if (!mbar_wait(&B.fullA[s], us & 1, abort, WAIT_LIMIT)) { ok = false; break; }
                 const uint64_t aoff = (uint64_t)((s * A_BYTES) >> 4);
-                if (p1) {
-                    // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns)
-                    const int sl = xs.slot(NX);
-                    if (!mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WAIT_LIMIT)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint64_t ad = dX0 + (uint64_t)((sl * L::XB) >> 4), bd = dA0 + aoff;
-#pragma unroll
-                    for (int kk = 0; kk < BN / 16; ++kk)
-                        mma_bf16_ss(tmem + D1_COL, ad + 2 * kk, bd + 2 * kk, id1, (!first || kk > 0) ? 1u : 0u);
-                    mma_commit(&B.emptyX[sl]);
-                    ++xs.item;
-                } else {
-                    // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows; X_I^T from TMEM)
-                    if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { ok = false; break; }
-                    tc_fence_after();
+                if (!mbar_wait(&B.fullA[s], us & 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows; X_I^T from TMEM)
+                if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                tc_fence_after();
+                {
                     const uint64_t bd = dAmn0 + aoff;
                     const uint32_t dcol = tmem + D2_COL + BN * b;
 #pragma unroll
@@ -348,21 +344,32 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                         mma_bf16_ts(dcol, tmem + XI_COL + 8 * kk, bd + (uint64_t)((kk * 2048) >> 4), id2,
                                     kk > 0 ? 1u : 0u);
                     mma_commit(&B.d2full[b]);
-                    ++xs.item;       // the tile's X_J box (P1's)
                 }
-                issued = true;
+                // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns); D1 drained
+                // by the epilogue before a block row's first tile
+                if (first && !mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                {
+                    const int sl = xs.slot(NX);
+                    if (!mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WAIT_LIMIT)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t ad = dX0 + (uint64_t)((sl * L::XS) >> 4), bd = dA0 + aoff;
+#pragma unroll
+                    for (int kk = 0; kk < BN / 16; ++kk)
+                        mma_bf16_ss(tmem + D1_COL, ad + 2 * kk, bd + 2 * kk, id1, (!first || kk > 0) ? 1u : 0u);
+                    mma_commit(&B.emptyX[sl]);
+                    ++xs.item;
+                }
                 mma_commit(&B.emptyA[s]);
                 if (last) {
-                    mma_commit(p1 ? &B.d1full : &B.xidone);
+                    mma_commit(&B.d1full);
                     ++seg;
                 }
             }
             if (!ok) fail(B, P.d_status);
-            if (issued) {
-                // all MMAs of this CTA (both threads) complete before TMEM is released
-                mma_commit(&B.mmadone);
-                if (p1) mbar_wait(&B.mmadone, 0, abort, WAIT_LIMIT);
-            }
+            // every tcgen05 operation of this CTA completes before TMEM is
+            // released, also when the CTA gave up
+            mma_commit(&B.mmadone);
+            mbar_wait_drain(&B.mmadone, 0, WAIT_LIMIT);
         }
     } else if (warp >= 4) {
         // ------------------------------------------------------- epilogue
@@ -540,9 +547,10 @@ cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t 
 cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t n, const float *X, int64_t ldx, int m,
                                const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
-                               int64_t ldh, int *d_status, int x_part, int accumulate)
+                               int64_t ldh, int *d_status, int x_part, int accumulate, int prepared)
 {
     if (m < 1 || m > 128) return cudaErrorNotSupported;
+    if (prepared && (x_part != 0 || accumulate != 0)) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0) return cudaErrorNotSupported;
     if ((ldh % 8) != 0 || (reinterpret_cast<uintptr_t>(Xh) & 15) != 0 || ldh < n)
         return cudaErrorNotSupported;
@@ -552,8 +560,9 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
     const int mr = m <= 64 ? 64 : (m <= 112 ? 112 : 128);
 
     // BF16 image of X (rows n, columns m; TMA fills the rest with zeros);
-    // Y starts at shift X (accumulate = 0) or gains it (accumulate = 1)
-    if (n > 0) {
+    // Y starts at shift X (accumulate = 0) or gains it (accumulate = 1),
+    // unless the producer of X wrote both already
+    if (n > 0 && !prepared) {
         const int y_mode = accumulate ? (d_shift ? 2 : 0) : 1;
         const dim3 grid((unsigned)((n + 1023) / 1024), (unsigned)m);
         to_bf16_kernel<<<grid, 256, 0, s>>>(X, ldx, n, reinterpret_cast<__nv_bfloat16 *>(Xh), ldh, x_part, Y, ldy,

@@ -190,14 +190,13 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
             }
             // wait (bounded) for the copies still in flight to land
             for (int64_t k = (it > NSTAGE ? it - NSTAGE : 0); k < it; ++k)
-                mbar_wait(&B.full[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1), abort, WAIT_LIMIT);
+                mbar_wait_drain(&B.full[k % NSTAGE], (uint32_t)((k / NSTAGE) & 1), WAIT_LIMIT);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA
         if (lane == 0) {
             int seg = 0;
             int64_t it = 0;
-            bool issued = false;
             for (int64_t t = t0; t < t1; ++t, ++it) {
                 const int J = (int)(t % P.nbc);
                 const bool first = (t == t0) || (J == 0);
@@ -219,17 +218,16 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
                     const uint64_t bd = sdesc_sw128(a_tile + kk * 32, 16, 1024);
                     mma_tf32_ss(tmem + (uint32_t)(BM * b), ad, bd, (!first || kk > 0) ? 1u : 0u);
                 }
-                issued = true;
                 mma_commit(&B.empty[s]);
                 if (last) {
                     mma_commit(&B.dfull[b]);
                     ++seg;
                 }
             }
-            if (issued) {
-                mma_commit(&B.mmadone);
-                mbar_wait(&B.mmadone, 0, abort, WAIT_LIMIT);
-            }
+            // every MMA of this CTA completes before TMEM is released, also
+            // when the CTA gave up (a commit with none pending arrives at once)
+            mma_commit(&B.mmadone);
+            mbar_wait_drain(&B.mmadone, 0, WAIT_LIMIT);
         }
     } else if (warp >= 4) {
         // ------------------------------------------------------- epilogue

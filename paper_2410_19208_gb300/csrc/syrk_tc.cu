@@ -175,8 +175,8 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
             }
             const int64_t n_it = it;
             for (int64_t k = (n_it > 2 ? n_it - 2 : 0); k < n_it; ++k)
-                mbar_wait(&B.fullWJ[k & 1], (uint32_t)((k >> 1) & 1), abort, WAIT_LIMIT);
-            if (wi_uses > 0) mbar_wait(&B.fullWI, (uint32_t)((wi_uses - 1) & 1), abort, WAIT_LIMIT);
+                mbar_wait_drain(&B.fullWJ[k & 1], (uint32_t)((k >> 1) & 1), WAIT_LIMIT);
+            if (wi_uses > 0) mbar_wait_drain(&B.fullWI, (uint32_t)((wi_uses - 1) & 1), WAIT_LIMIT);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA
@@ -184,7 +184,6 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
             const uint32_t id = idesc_bf16(TS, TS, 1, 1);
             int curI = -1, seg = 0;
             int64_t it = 0;
-            bool issued = false;
             for (int64_t t = t0; t < t1; ++t, ++it) {
                 int I, J;
                 tile_of(t, P.nb, I, J);
@@ -213,7 +212,6 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
                         mma_bf16_ss(d, sdesc_sw128(alo + off, ATOM_COL, 1024), sdesc_sw128(bhi + off, ATOM_COL, 1024), id, 1);
                     }
                 }
-                issued = issued || ksteps > 0;
                 mma_commit(&B.emptyWJ[b]);
                 mma_commit(&B.dfull[b]);
                 if (last) {
@@ -221,10 +219,10 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
                     ++seg;
                 }
             }
-            if (issued) {
-                mma_commit(&B.mmadone);
-                mbar_wait(&B.mmadone, 0, abort, WAIT_LIMIT);
-            }
+            // every MMA of this CTA completes before TMEM is released, also
+            // when the CTA gave up (a commit with none pending arrives at once)
+            mma_commit(&B.mmadone);
+            mbar_wait_drain(&B.mmadone, 0, WAIT_LIMIT);
         }
     } else if (warp >= 4) {
         // ------------------------------------------------------- epilogue

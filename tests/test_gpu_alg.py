@@ -773,3 +773,50 @@ def test_sdls_stops_at_the_tolerance_and_rejects_bad_arguments(ctx):
     assert ei.value.code == 1
     with pytest.raises(ps.PsdprojError):
         ctx.sdls(Cd, Ad, b, -1.0, 100, 10, 1, 2, 0.5, 1e-3, 10, 1, [0.0] * 3)     # rho <= 0
+
+
+def test_concurrent_contexts_on_separate_streams_agree(ctx, oracle_lib):
+    """Four contexts on four CUDA streams run BF16-form projections of the same
+    matrix at the same time (the benchmark's concurrency: persistent
+    tensor-core grids of different contexts and their single-block steps
+    overlapping on the GPU), several rounds: every device status stays clear
+    and every result matches a single context's within the BF16 form's
+    spread (the passes' transposed products are added in a timing-dependent
+    order, so results agree to rounding, not bit for bit)."""
+    n, k, p, q = 6144, 100, 10, 1
+    Vr, lam = si.make_problem("decay", n)
+    A = si.form_A_torch(Vr, lam, "cuda")
+    opts = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3)
+    S = 4
+    streams = [torch.cuda.Stream() for _ in range(S)]
+    ctxs = [ps.Context(0, st) for st in streams]
+    for c in ctxs:
+        c.set_reserved_sms(2 * S)
+    Ws = [[ps.tall_empty(n, k + p) for _ in range(2)] for _ in range(S)]
+    Ps = [torch.empty(n, n, device="cuda") for _ in range(S)]
+    torch.cuda.synchronize()
+    ref = {}
+    for alg in (1, 2):
+        W = ps.tall_empty(n, k + p)
+        P = torch.empty(n, n, device="cuda")
+        if alg == 1:
+            ctx.alg1(A, k, p, q, 1, P=P, W=W, opts=opts)
+        else:
+            ctx.alg2(A, k, p, q, 1, P=P, W=W, opts=opts)
+        assert ctx.sync_status() == 0
+        ref[alg] = W.cpu().numpy().astype(np.float64)
+    try:
+        for _ in range(6):
+            for i, c in enumerate(ctxs):
+                c.alg1(A, k, p, q, 1, P=Ps[i], W=Ws[i][0], opts=opts)
+                c.alg2(A, k, p, q, 1, P=Ps[i], W=Ws[i][1], opts=opts)
+            torch.cuda.synchronize()
+            assert [c.sync_status() for c in ctxs] == [0] * S
+        for i in range(S):
+            for alg in (1, 2):
+                W = Ws[i][alg - 1].cpu().numpy().astype(np.float64)
+                rel = np.sqrt(max(oracle_lib.factor_dist2(W, ref[alg]), 0.0) / oracle_lib.factor_norm2(ref[alg]))
+                assert rel <= 2e-3, (i, alg, rel)
+    finally:
+        for c in ctxs:
+            c.close()
