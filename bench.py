@@ -83,11 +83,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP32 comparison")
     ap.add_argument("--no-forms", action="store_true", help="skip the TF32 / split-BF16 comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched workload in the headline run")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served workload in the headline run")
     ap.add_argument("--workload", default="headline", choices=["headline", "batched", "serve"],
                     help="batched: 512 matrices, sides log-uniform in [64, 2048], through psdproj_batched; "
                          "serve: Poisson arrivals through psdproj_server")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests per second")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-pool", type=int, default=48, help="distinct matrices the requests draw from")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -177,6 +179,35 @@ def oracle_sample(A64_or_none, n, k, p, q, Vr=None, lam=None):
     return time.perf_counter() - t0, out["W"]
 
 
+def oracle_step(A64, k, p, q):
+    """One step of the headline workload in the FP64 oracle: an Algorithm 1
+    and an Algorithm 2 projection (N = 10) of A64.  Returns (seconds, W of
+    Algorithm 1, W of Algorithm 2)."""
+    import oracle
+    t0 = time.perf_counter()
+    o1 = oracle.alg1(A64, k, p, q, SEED)
+    o2 = oracle.alg2(A64, k, p, q, SEED, N=10)
+    return time.perf_counter() - t0, o1["W"], o2["W_red"]
+
+
+def oracle_single_core(n, k, p, q):
+    """The oracle on ONE host core: one Algorithm 1 projection of the decay
+    recipe at side n, in a child process started with OMP_NUM_THREADS=1 (the
+    oracle's OpenMP regions then run on one thread).  Returns seconds or None."""
+    code = ("import sys, time; sys.path.insert(0, %r)\n"
+            "import numpy as np, oracle, synth_inputs as si\n"
+            "Vr, lam = si.make_problem('decay', %d)\n"
+            "A = si.form_A_numpy(Vr, lam).astype(np.float32).astype(np.float64)\n"
+            "oracle.build(); t0 = time.perf_counter(); oracle.alg1(A, %d, %d, %d, %d)\n"
+            "print(time.perf_counter() - t0)\n") % (ROOT, n, k, p, q, SEED)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return float(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def cores_used():
     try:
         return len(os.sched_getaffinity(0))
@@ -185,33 +216,28 @@ def cores_used():
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the host cores, rank 0 only.
-    Each step is a bounded sample: one Algorithm-1 projection at n_s = n/4
-    with the same recipe and (k, p, q); its time is scaled to n by the
-    O(k n^2) cost of the passes, (n / n_s)^2."""
+    """The reference arm: the FP64 oracle on the host cores, rank 0 only, at
+    the headline configuration itself (n, k, p, q of the run, both
+    algorithms, no scaling).  One step (one Algorithm 1 and one Algorithm 2
+    projection, about 15-25 s on 16 cores at n = 20000) is timed whatever
+    --steps asks for, so that the arm ends within a minute; no warm-up (the
+    oracle keeps no state between calls)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import numpy as np
     import synth_inputs as si
-    n_s = max(args.k + args.p + 1, args.n // 4)
-    Vr, lam = si.make_problem("decay", n_s)
+    Vr, lam = si.make_problem("decay", args.n)
     A64 = si.form_A_numpy(Vr, lam).astype(np.float32).astype(np.float64)
-    for _ in range(args.warmup):
-        oracle_sample(A64, n_s, args.k, args.p, args.q)
-    times = []
-    for _ in range(args.steps):
-        t, _ = oracle_sample(A64, n_s, args.k, args.p, args.q)
-        times.append(t)
-    scale = (args.n / n_s) ** 2
-    per_proj = statistics.mean(times) * scale
-    value = 1.0 / per_proj
-    sample = (f"one FP64 oracle Algorithm-1 projection per step at n={n_s} (k={args.k}, "
-              f"p={args.p}, q={args.q}), time scaled by (n/{n_s})^2 to n={args.n}")
+    t_step, _, _ = oracle_step(A64, args.k, args.p, args.q)
+    value = 2.0 / t_step
+    sample = (f"one step of the headline workload in the FP64 oracle: an Algorithm 1 and an Algorithm 2 "
+              f"(N = 10) projection at n={args.n}, k={args.k}, p={args.p}, q={args.q}, {t_step:.1f} s; "
+              f"one step timed (requested {args.steps}), no warm-up")
     line = {
         "metric": f"PSD projections/s at n={args.n}", "value": value, "unit": "projections/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": per_proj * 1e3, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": args.gpus, "steps": 1, "warmup": 0, "steps_requested": args.steps,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": workload_config(args, "fp64-oracle", "n/a"),
         "cpu_baseline": {"value": value, "unit": "projections/s", "cores": cores_used(),
@@ -255,7 +281,7 @@ def traffic_from_profile(kernel_file: str, n: int, kernel: str):
     return None
 
 
-def run_batched(args):
+def run_batched(args, emit=True):
     """The many-small-matrices workload: a batch of independent projections
     (batch recipe: sides log-uniform in [64, 2048], k = min(n/8, 64), p = 8,
     q = 1, the two algorithms alternating) through one psdproj_batched call per
@@ -305,21 +331,64 @@ def run_batched(args):
             raise SystemExit("device status set during the batched run")
         per[S] = {"value": len(probs) * steps / (ms / 1e3), "ms_per_step": ms / steps,
                   "gpu_launches": launches, "clocks": clocks}
+    # the same batch recorded once into a CUDA graph and replayed
+    # (psdproj_batched_graph), with the stream counts that pay most
+    for S in (8, 16):
+        ctx.set_batch_streams(S)
+        for _ in range(max(args.warmup, 3)):
+            ctx.batched(probs, opts=opts, graph=True)
+        if ctx.sync_status() != 0:
+            raise SystemExit("device status set during the graph batched warm-up")
+        steps = max(2, args.steps // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ps.lib().psdproj_kernel_launches()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.batched(probs, opts=opts, graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if ctx.sync_status() != 0:
+            raise SystemExit("device status set during the graph batched run")
+        per[f"graph{S}"] = {"value": len(probs) * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                            "gpu_launches": int(ps.lib().psdproj_kernel_launches() - l0), "clocks": None}
     best = max(per, key=lambda S: per[S]["value"])
+    # HBM roofline of the batch: the algorithmic bytes of every projection
+    # (BF16 form: the pack reads A's upper triangle and writes the image, 6 B
+    # per entry; 2q + 2 passes over the image, 2 B per entry; P written,
+    # 4 n^2; Alg. 3 adds 2(N + 1) power-iteration products over the image)
+    peaks, peak_kind = measured_peaks()
+    per_entry = {"bf16": (6.0, 2.0, 2.0), "bf16x3": (8.0, 4.0, 4.0), "tf32": (8.0, 4.0, 4.0),
+                 "fp32": (0.0, 4.0, 4.0)}[prec]
+    batch_bytes = 0.0
+    for d in probs:
+        nn = d["A"].shape[0]
+        up = nn * (nn + 1) / 2.0
+        batch_bytes += (per_entry[0] + (2 * d["q"] + 2) * per_entry[1]) * up + 4.0 * nn * nn
+        if d["algorithm"] == 2:
+            batch_bytes += 2 * (10 + 1) * per_entry[2] * up
+    ach = batch_bytes / (per[best]["ms_per_step"] / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "algorithmic_bytes_per_batch": batch_bytes,
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
     line = {"metric": "batched PSD projections/s (512 matrices, sides log-uniform 64..2048)",
             "value": per[best]["value"], "unit": "projections/s", "n_gpus": 1, "steps": max(1, args.steps // 4),
             "warmup": max(args.warmup, 3), "ms_per_step": per[best]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[prec], "data": "synthetic",
-            "config": {"workload": f"psdproj_batched, {len(probs)} problems per step, batch recipe, "
-                                   "k = min(n/8, 64), p = 8, q = 1, Alg. 1 / Alg. 2 alternating",
+            "config": {"workload": f"psdproj_batched (graph: psdproj_batched_graph), {len(probs)} problems per "
+                                   "step, batch recipe, k = min(n/8, 64), p = 8, q = 1, Alg. 1 / Alg. 2 alternating",
                        "helper_streams": best, "batch_bytes_A": nbytes,
                        "l2": "inputs larger than L2 (the batch's A is %.2f GB)" % (nbytes / 1e9)},
-            "by_streams": {str(S): per[S] for S in per},
-            "gpu_launches": per[best]["gpu_launches"], "clocks": per[best]["clocks"]}
-    print(json.dumps(line))
+            "by_streams": {str(S): per[S] for S in per}, "roofline": roof,
+            "gpu_launches": per[best]["gpu_launches"], "clocks": per[best]["clocks"] or per[1]["clocks"]}
+    if emit:
+        print(json.dumps(line))
+    ctx.close()
+    return line
 
 
-def run_serve(args):
+def run_serve(args, emit=True):
     """The served workload: requests arrive as a Poisson process (rate
     --serve-rate, --serve-seconds long), each a matrix of side log-uniform in
     [256, 8192] (batch recipe; drawn from a pool of --serve-pool matrices
@@ -430,7 +499,9 @@ def run_serve(args):
             "arrivals_late_over_5ms": late,
             "latency_ms": {"p50": pq(0.5), "p90": pq(0.9), "p99": pq(0.99), "max": lat_s[-1]},
             "server": st, "gpu_launches": launches, "clocks": clocks}
-    print(json.dumps(line))
+    if emit:
+        print(json.dumps(line))
+    return line
 
 
 def main():
@@ -646,7 +717,7 @@ def main():
     value = job_rate(2 * args.steps, world, conc["elapsed_ms"] / 1e3)
 
     # ---- rooflines: the dominant kernel and the other HBM-bound ones -------
-    # algorithmic bytes per launch (stated in the design doc): U(n) = n(n+1)/2
+    # algorithmic bytes per launch: U(n) = n(n+1)/2
     # upper-triangle entries; the BF16 form reads 2 bytes per entry from its
     # image, the FP32 form 4 bytes from A.  Per-launch times come from the
     # context's CUDA-event stage timing over the timed region (events on the
@@ -684,10 +755,10 @@ def main():
         apass_ms = stages["apass"]["ms_avg"]
         flops = 2.0 * n * n * m
         achieved = flops / (apass_ms / 1e3) / 1e12
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak = sm_count * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "kernel": "sym_pass_simt",
-                "peak_source": f"derived: 152 SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
+                "peak_source": f"derived: {sm_count} SMs x 128 FP32 FMA lanes x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
                 "hbm_frac_of_" + peak_kind: (upper_elems * 4 / (apass_ms / 1e3) / 1e9) / peaks["hbm_gbs"],
                 "per_launch_ms": apass_ms, "algorithmic_bytes_per_launch": upper_elems * 4.0,
                 "algorithmic_flops_per_launch": flops,
@@ -766,11 +837,20 @@ def main():
         "error_vs_exact": {"alg1": err_exact(head["W1"]), "alg2": err_exact(head["W2"])},
     }
     if prec != "fp32" and not args.no_plain:
-        plain = measure("fp32", "fp32", max(2, min(args.steps, 5)), False)
-        pv = 2 * max(2, min(args.steps, 5)) * world / (plain["elapsed_ms"] / 1e3)
-        line["plain_fp32"] = {"value": pv, "unit": "projections/s",
-                              "ms_per_step": plain["elapsed_ms"] / max(2, min(args.steps, 5)),
-                              "speedup_of_headline": value / pv,
+        # the plain FP32 form at the same (k, p, q, seed), timed both ways the
+        # headline is: on one stream, and spread over the same S contexts
+        ks = max(2, min(args.steps, 5))
+        plain = measure("fp32", "fp32", ks, False)
+        pv1 = 2 * ks * world / (plain["elapsed_ms"] / 1e3)
+        pconc = measure_concurrent("fp32", "fp32", ks, False)
+        pvS = 2 * ks * world / (pconc["elapsed_ms"] / 1e3)
+        line["plain_fp32"] = {"value": pvS, "unit": "projections/s", "streams": S,
+                              "ms_per_step": pconc["elapsed_ms"] / ks,
+                              "one_stream": {"value": pv1, "ms_per_step": plain["elapsed_ms"] / ks},
+                              "speedup_of_headline": value / pvS,
+                              "speedup_one_stream": seq_value / pv1,
+                              "note": f"speedup_of_headline: the headline form over plain FP32, both on {S} "
+                                      "streams; speedup_one_stream: both on one stream",
                               "error_vs_exact": {"alg1": err_exact(plain["W1"]),
                                                  "alg2": err_exact(plain["W2"])}}
         Wg = plain["W1"]
@@ -797,6 +877,23 @@ def main():
             "ms_per_step": r["elapsed_ms"] / ks, "streams": 1,
             "alg2_ms_p50": pct(r["lat2"], 0.5), "alg2_ms_p50_min_eig": pct(head["lat2"], 0.5),
             "error_vs_exact": {"alg1": err_exact(r["W1"]), "alg2": err_exact(r["W2"])}}
+
+    # ---- the batched and the served workloads (their own recipes) ----------
+    if world == 1 and not args.no_batched:
+        b = run_batched(args, emit=False)
+        line["batched"] = {"value": b["value"], "unit": b["unit"], "ms_per_step": b["ms_per_step"],
+                           "workload": b["config"]["workload"], "helper_streams": b["config"]["helper_streams"],
+                           "by_streams": {k_: v_["value"] for k_, v_ in b["by_streams"].items()},
+                           "roofline": b["roofline"], "gpu_launches": b["gpu_launches"], "clocks": b["clocks"]}
+        torch.cuda.empty_cache()
+    if world == 1 and not args.no_serve:
+        v = run_serve(args, emit=False)
+        line["served"] = {"value": v["value"], "unit": v["unit"], "workload": v["config"]["workload"],
+                          "seconds": args.serve_seconds, "offered_rate": v["offered_rate"],
+                          "requests": v["requests"], "completed": v["completed"], "failed": v["failed"],
+                          "latency_ms": v["latency_ms"], "arrivals_late_over_5ms": v["arrivals_late_over_5ms"],
+                          "clocks": v["clocks"]}
+        torch.cuda.empty_cache()
 
     # ---- end to end through the host-buffer C-ABI call --------------------
     if not args.no_e2e:
@@ -851,20 +948,33 @@ def main():
         A64 = A.cpu().numpy().astype(np.float64)
         del P, lanes
         torch.cuda.empty_cache()
-        t_or, Wo = oracle_sample(A64, n, k, p, q)
+        t_or, Wo, Wo2 = oracle_step(A64, k, p, q)
         del A64
-        rel = lambda Wx: float(np.sqrt(max(oracle.factor_dist2(Wx, Wo), 0.0) / oracle.factor_norm2(Wo)))
-        err_o = err_exact(Wo)
+        rel = lambda Wx, Wr: float(np.sqrt(max(oracle.factor_dist2(Wx, Wr), 0.0) / oracle.factor_norm2(Wr)))
+        err_o, err_o2 = err_exact(Wo), err_exact(Wo2)
         line["accuracy_alg1"] = {
-            "headline_rel_fro_vs_oracle": rel(head["W1"]),
-            "plain_fp32_rel_fro_vs_oracle": rel(Wg),
+            "headline_rel_fro_vs_oracle": rel(head["W1"], Wo),
+            "plain_fp32_rel_fro_vs_oracle": rel(Wg, Wo),
             "headline_rel_fro_vs_exact": err_exact(head["W1"]),
             "oracle_rel_fro_vs_exact": err_o,
             "headline_ratio_to_oracle_error": err_exact(head["W1"]) / err_o}
-        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "projections/s", "cores": cores_used(),
+        line["accuracy_alg2"] = {
+            "headline_rel_fro_vs_oracle": rel(head["W2"], Wo2),
+            "headline_rel_fro_vs_exact": err_exact(head["W2"]),
+            "oracle_rel_fro_vs_exact": err_o2,
+            "headline_ratio_to_oracle_error": err_exact(head["W2"]) / err_o2}
+        line["cpu_baseline"] = {"value": 2.0 / t_or, "unit": "projections/s", "cores": cores_used(),
                                 "kind": "oracle",
-                                "sample": f"one FP64 oracle Algorithm-1 projection at n={n} "
-                                          f"(k={k}, p={p}, q={q}), {t_or:.1f} s"}
+                                "sample": f"one step of the workload in the FP64 oracle (an Algorithm 1 and an "
+                                          f"Algorithm 2 projection at n={n}, k={k}, p={p}, q={q}), {t_or:.1f} s"}
+        n1 = min(n, 4096)
+        t1 = oracle_single_core(n1, k, p, q)
+        if t1 is not None:
+            line["cpu_baseline_single_core"] = {
+                "value": 1.0 / t1, "unit": "projections/s", "cores": 1, "kind": "oracle",
+                "sample": f"one FP64 oracle Algorithm 1 projection at n={n1} (k={k}, p={p}, q={q}) on one "
+                          f"core (OMP_NUM_THREADS=1), {t1:.1f} s; a smaller side than the headline's so that "
+                          "the sample stays bounded"}
     print(json.dumps(line), flush=True)
     ctx.close()
     for ln in (lanes[1:] if 'lanes' in locals() else []):

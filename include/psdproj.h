@@ -41,7 +41,8 @@ extern "C" {
 /* ---- status codes ------------------------------------------------------- */
 #define PSDPROJ_OK          0
 #define PSDPROJ_EINVAL      1  /* bad argument (sizes, leading dims, NULL)     */
-#define PSDPROJ_ENOMEM      2  /* device allocation failed                      */
+#define PSDPROJ_ENOMEM      2  /* device allocation failed, or it would exceed the
+                                  context's device-memory budget (psdproj_create) */
 #define PSDPROJ_ENOTFINITE  3  /* non-finite value met on the device            */
 #define PSDPROJ_ENOCONV     4  /* the l x l eigensolver hit its sweep limit     */
 #define PSDPROJ_ETIMEOUT    5  /* a bounded device wait gave up                 */
@@ -90,15 +91,36 @@ typedef struct psdproj_opts {
     int eig;         /* PSDPROJ_EIG_* (default AUTO)                             */
     int sketch;      /* PSDPROJ_SKETCH_* test matrix of Alg. 1 (default GAUSS)   */
     int alpha_mode;  /* PSDPROJ_ALPHA_* estimate of alpha in Alg. 3 (default MINEIG) */
-    int reserved[1]; /* must be zero                                             */
+    int deterministic; /* 1: every product with A (passes and power iterations)
+                          runs in a fixed summation order, in FP32 on the CUDA
+                          cores (prec then applies to nothing but is checked),
+                          so that a repeated call with the same inputs and
+                          options returns bitwise the same P, W, rank and
+                          alpha; such a pass reads each upper-triangle entry
+                          twice.  0 (default): the faster forms, whose
+                          cross-block sums are added in a timing-dependent
+                          order (results agree to rounding). */
+    int64_t spin_limit; /* SM clock cycles a device-side wait of the
+                          tensor-core and power-iteration kernels may spin
+                          for another part of its kernel before it gives up
+                          and the call's device status becomes
+                          PSDPROJ_ETIMEOUT (the kernel then waits for its own
+                          copies and MMAs in flight, frees TMEM and returns);
+                          0 (default): 4e9 cycles, about two seconds. */
+    int reserved[2];   /* must be zero                                         */
 } psdproj_opts;
 
 /* Fill *o with the defaults listed above. */
 void psdproj_default_opts(psdproj_opts *o);
 
 /* Create a context bound to CUDA device `device` and CUDA stream `stream`
- * (a cudaStream_t; NULL = the legacy default stream).  Returns a status. */
-int psdproj_create(psdproj_ctx **ctx, int device, void *stream);
+ * (a cudaStream_t; NULL = the legacy default stream).  hbm_budget_bytes > 0
+ * caps the device memory the context may hold for its workspaces, images
+ * of A and host-call staging buffers (its batch helpers included, see
+ * psdproj_workspace_bytes): a call that would grow them past the budget
+ * returns PSDPROJ_ENOMEM before it launches anything; 0 = no cap.  Returns
+ * a status. */
+int psdproj_create(psdproj_ctx **ctx, int device, void *stream, size_t hbm_budget_bytes);
 /* Re-bind the context to another stream of the same device. */
 int psdproj_set_stream(psdproj_ctx *ctx, void *stream);
 /* Free the context and its workspaces (synchronises its stream first). */
@@ -108,9 +130,17 @@ int psdproj_destroy(psdproj_ctx *ctx);
 int psdproj_sync_status(psdproj_ctx *ctx);
 /* Human-readable name of a status code (static storage). */
 const char *psdproj_status_string(int status);
-/* Bytes of device workspace the context holds now (the tensor-core images
- * of A included). */
+/* Bytes of device memory the context holds now: workspaces, the tensor-core
+ * images of A, host-call staging buffers and those of its batch helpers
+ * (the quantity the budget of psdproj_create caps). */
 size_t psdproj_workspace_bytes(const psdproj_ctx *ctx);
+
+/* Device bytes a context allocates to run one projection of side n with
+ * sketch width k + p under opts (NULL = defaults): its workspace and the
+ * image(s) of A of the form (or, with opts->deterministic, the partial-sum
+ * scratch instead), as psdproj_workspace_bytes would count them; 0 for bad
+ * sizes.  For sizing a budget (psdproj_create) or an admission footprint. */
+size_t psdproj_projection_bytes(int64_t n, int k, int p, const psdproj_opts *opts);
 
 /* ---- diagnostics --------------------------------------------------------- */
 /* Stage classes timed by the context when timing is on. */
@@ -222,6 +252,21 @@ typedef struct psdproj_problem {
 int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
                     const psdproj_opts *opts);
 
+/* psdproj_batched with the batch's launches recorded once in a CUDA graph
+ * and replayed: the first call with a given problem table (the descriptors
+ * compared byte for byte), options, helper-stream count and reserved SMs
+ * allocates every workspace and image the batch needs, records the whole
+ * batch (its fork to the helper streams, every projection, the join) into a
+ * graph kept by the context and launches it; a later call with the same
+ * table and settings launches that graph again, with no per-projection host
+ * work.  A call with a different table records a new graph in place of the
+ * old one.  The graph reads and writes the buffers the table names, so it
+ * replays only while those pointers stay valid.  Stage timing is not
+ * recorded into the graph.  Results and errors as for psdproj_batched; the
+ * context's stream must not be capturing already. */
+int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
+                          const psdproj_opts *opts);
+
 /* Number of helper streams psdproj_batched spreads a batch over (1..16,
  * default 8; 1 = the context's own stream only).  Each helper holds its own
  * workspace, sized for the largest problem it has run. */
@@ -284,7 +329,8 @@ int psdproj_last_cuda_error(int *line);
  * holds device pointers the caller owns until psdproj_server_wait reports it
  * done.  Admission is first come, first served under a device-memory budget:
  * the request at the head of the queue starts when its footprint
- * (footprint_bytes, or when 0 the bytes of its A, P and W) fits under
+ * (footprint_bytes, or when 0 the bytes of its A, P and W plus
+ * psdproj_projection_bytes for its size and the server's opts) fits under
  * admit_bytes together with the admitted requests not yet finished; later
  * requests wait behind it.  Each request's status is its own: the worker
  * reads and clears its context's device status word after the request.  Not
@@ -304,7 +350,8 @@ typedef struct psdproj_request {
     float *dW;           /* may be NULL                                         */
     int64_t ldw;
     int *d_rank;         /* may be NULL                                         */
-    int64_t footprint_bytes; /* device bytes held while admitted; 0: A + P + W  */
+    int64_t footprint_bytes; /* device bytes held while admitted; 0: A + P + W and
+                                the context memory (psdproj_projection_bytes) */
 } psdproj_request;
 typedef struct psdproj_server_stats {
     uint64_t submitted, completed, failed;
@@ -463,8 +510,11 @@ int psdproj_min_eig(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
  *   d_alpha (required), d_sigma1, d_sigma2 (may be NULL): device doubles;
  *   stream: the cudaStream_t to enqueue on (NULL = legacy default stream).
  * The first call on a device (with that device current) looks up the device
- * address of the scratch array; make that first call before any stream
- * capture.  Every call shares the one array per device and leaves its
+ * address of the scratch array and keeps it for later calls; make that first
+ * call before any stream capture.  The kept address does not survive a reset
+ * of the device's primary context (cudaDeviceReset): do not call this entry
+ * point again in a process after such a reset.  dA must be device memory of
+ * the current device (otherwise PSDPROJ_EINVAL) and stream a stream of it.  Every call shares the one array per device and leaves its
  * contents behind: calls that overlap on the GPU (other streams, or
  * concurrent host threads) race and must be serialised by the caller.
  * Errors found on the host are returned; nothing is synchronised. */

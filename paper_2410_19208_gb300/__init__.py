@@ -41,7 +41,8 @@ class PsdprojError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("syrk_prec", ctypes.c_int), ("N", ctypes.c_int),
                 ("out_mode", ctypes.c_int), ("eig", ctypes.c_int), ("sketch", ctypes.c_int),
-                ("alpha_mode", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("alpha_mode", ctypes.c_int), ("deterministic", ctypes.c_int), ("spin_limit", ctypes.c_int64),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Problem(ctypes.Structure):
@@ -94,15 +95,17 @@ def _load():
     lib = ctypes.CDLL(LIB_PATH)
     sig = {
         "psdproj_default_opts": (None, [ctypes.POINTER(Opts)]),
-        "psdproj_create": (_int, [ctypes.POINTER(_P), _int, _P]),
+        "psdproj_create": (_int, [ctypes.POINTER(_P), _int, _P, ctypes.c_size_t]),
         "psdproj_set_stream": (_int, [_P, _P]),
         "psdproj_destroy": (_int, [_P]),
         "psdproj_sync_status": (_int, [_P]),
         "psdproj_status_string": (ctypes.c_char_p, [_int]),
         "psdproj_workspace_bytes": (ctypes.c_size_t, [_P]),
+        "psdproj_projection_bytes": (ctypes.c_size_t, [_i64, _int, _int, ctypes.POINTER(Opts)]),
         "psdproj_alg1": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, _P, _i64, _P, _i64,
                                 _P, ctypes.POINTER(Opts)]),
         "psdproj_batched": (_int, [_P, _int, _P, _P]),
+        "psdproj_batched_graph": (_int, [_P, _int, _P, _P]),
         "psdproj_set_batch_streams": (_int, [_P, _int]),
         "psdproj_set_reserved_sms": (_int, [_P, _int]),
         "psdproj_alg2": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, ctypes.c_double,
@@ -149,6 +152,11 @@ def lib():
 
 def _check(code: int, what: str):
     if code != 0:
+        if code in (2, 6, 7):     # ENOMEM, ECUDA, ENOTSUP: name the CUDA error behind it
+            line = _int(0)
+            err = _load().psdproj_last_cuda_error(ctypes.byref(line))
+            if err:
+                what = f"{what} (cudaError {err} at C-ABI line {line.value})"
         raise PsdprojError(code, what)
 
 
@@ -175,25 +183,33 @@ def tall_empty(n: int, m: int, device="cuda", ld: int | None = None):
     return torch.empty(m, ld, dtype=torch.float32, device=device).t()[:n]
 
 
+def projection_bytes(n: int, k: int, p: int, opts: Opts | None = None) -> int:
+    """Device bytes a context allocates for one projection (psdproj_projection_bytes)."""
+    return int(_load().psdproj_projection_bytes(n, k, p, ctypes.byref(opts) if opts else None))
+
+
 def make_opts(prec=PREC_FP32, syrk_prec=PREC_FP32, N=10, out_mode=OUT_FULL,
-              eig=EIG_AUTO, sketch=SKETCH_GAUSS, alpha_mode=ALPHA_MINEIG) -> Opts:
+              eig=EIG_AUTO, sketch=SKETCH_GAUSS, alpha_mode=ALPHA_MINEIG, deterministic=0,
+              spin_limit=0) -> Opts:
     o = Opts()
     _load().psdproj_default_opts(ctypes.byref(o))
     o.prec, o.syrk_prec, o.N, o.out_mode, o.eig = prec, syrk_prec, N, out_mode, eig
     o.sketch, o.alpha_mode = sketch, alpha_mode
+    o.deterministic, o.spin_limit = int(deterministic), int(spin_limit)
     return o
 
 
 class Context:
-    """A psdproj context bound to one device and one CUDA stream."""
+    """A psdproj context bound to one device and one CUDA stream; hbm_budget
+    (bytes, 0 = no cap) caps the device memory it may hold."""
 
-    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None, hbm_budget: int = 0):
         lib = _load()
         self.device = device
         self.stream = stream or torch.cuda.current_stream(device)
         h = ctypes.c_void_p()
-        _check(lib.psdproj_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream)),
-               "psdproj_create")
+        _check(lib.psdproj_create(ctypes.byref(h), device, ctypes.c_void_p(self.stream.cuda_stream),
+                                  int(hbm_budget)), "psdproj_create")
         self.h = h
 
     def close(self):
@@ -236,9 +252,11 @@ class Context:
                                     _ptr(rank), ctypes.byref(opts) if opts else None),
                "psdproj_alg2")
 
-    def batched(self, problems, opts: Opts | None = None):
+    def batched(self, problems, opts: Opts | None = None, graph: bool = False):
         """problems: list of dicts with keys A, k, p, q, seed, algorithm (1 or 2) and
-        optional P, W, rank, alpha_in, alpha_out, info (device tensors)."""
+        optional P, W, rank, alpha_in, alpha_out, info (device tensors).
+        graph=True: psdproj_batched_graph (recorded once into a CUDA graph and
+        replayed while the table is unchanged)."""
         arr = (Problem * max(1, len(problems)))()
         for i, d in enumerate(problems):
             A = d["A"]
@@ -248,8 +266,9 @@ class Context:
                              float(d.get("alpha_in", 0.0)), _ptr(d.get("alpha_out")), _ptr(d.get("info")),
                              _ptr(P), P.stride(0) if P is not None else n,
                              _ptr(W), _tall(W, "W")[2] if W is not None else n, _ptr(d.get("rank")))
-        _check(_load().psdproj_batched(self.h, len(problems), ctypes.byref(arr),
-                                       ctypes.byref(opts) if opts else None), "psdproj_batched")
+        fn = _load().psdproj_batched_graph if graph else _load().psdproj_batched
+        _check(fn(self.h, len(problems), ctypes.byref(arr), ctypes.byref(opts) if opts else None),
+               "psdproj_batched_graph" if graph else "psdproj_batched")
 
     def sdls(self, C, As, b, rho, k, p, q, algorithm, beta, eps, max_iter, seed, y0, warm_start=False,
              X=None, opts: Opts | None = None):

@@ -103,6 +103,71 @@ void free_workspace(psd_workspace &ws)
 
 }  // namespace
 
+int psd_budget_check(const psdproj_ctx *ctx, size_t old_bytes, size_t new_bytes)
+{
+    const psdproj_ctx *root = ctx->root ? ctx->root : ctx;
+    if (root->budget == 0 || new_bytes <= old_bytes) return PSDPROJ_OK;
+    const size_t held = psdproj_workspace_bytes(root);
+    if (held - old_bytes + new_bytes > root->budget) return PSDPROJ_ENOMEM;
+    return PSDPROJ_OK;
+}
+
+namespace {
+
+// The workspace's carve-up for nn rows and lp columns: one function serves
+// both the size (base == nullptr: offsets only) and the pointers, so the two
+// cannot disagree.  Returns the total bytes.
+size_t carve_workspace(psd_workspace &lay, char *base, int64_t nn, int lp)
+{
+    const int64_t ld = psd_ld(nn);
+    const int64_t nchunk = (nn + PSD_GRAM_CHUNK - 1) / PSD_GRAM_CHUNK;
+    const size_t tall = align256(sizeof(float) * (size_t)ld * lp);
+    const size_t half_tall = align256(sizeof(uint16_t) * (size_t)ld * lp);
+    const size_t small_d = align256(sizeof(double) * (size_t)lp * lp);
+    const size_t small_f = align256(sizeof(float) * (size_t)lp * lp);
+    const size_t chol_scr = align256(sizeof(double) * ((size_t)lp * lp + lp) + sizeof(float) * (size_t)lp * lp);
+    size_t off = 0;
+    auto take = [&](size_t b) { char *q = base ? base + off : nullptr; off += align256(b); return q; };
+    lay.Om = reinterpret_cast<float *>(take(tall));
+    lay.Y = reinterpret_cast<float *>(take(tall));
+    lay.Q = reinterpret_cast<float *>(take(tall));
+    lay.T = reinterpret_cast<float *>(take(tall));
+    lay.W = reinterpret_cast<float *>(take(tall));
+    lay.Xf = reinterpret_cast<float *>(take(tall));
+    lay.Xhi = reinterpret_cast<uint16_t *>(take(half_tall));
+    lay.Xlo = reinterpret_cast<uint16_t *>(take(half_tall));
+    lay.gpart = reinterpret_cast<float *>(take(sizeof(float) * nchunk * lp * lp));
+    lay.G = reinterpret_cast<double *>(take(small_d));
+    lay.R = reinterpret_cast<double *>(take(small_d));
+    lay.C = reinterpret_cast<double *>(take(small_d));
+    lay.cholscr = reinterpret_cast<double *>(take(chol_scr));
+    lay.d = reinterpret_cast<double *>(take(sizeof(double) * lp));
+    lay.Rinv = reinterpret_cast<float *>(take(small_f));
+    lay.V = reinterpret_cast<float *>(take(small_f));
+    lay.M = reinterpret_cast<float *>(take(small_f));
+    lay.eigscr = reinterpret_cast<float *>(take(sizeof(float) * 3 * (size_t)(lp + 2) * (lp + 2)));
+    lay.dead = reinterpret_cast<int *>(take(sizeof(int) * lp));
+    lay.pv0 = reinterpret_cast<float *>(take(sizeof(float) * ld));
+    lay.pv1 = reinterpret_cast<float *>(take(sizeof(float) * ld));
+    lay.scal = reinterpret_cast<double *>(take(sizeof(double) * 16));
+    lay.ints = reinterpret_cast<int *>(take(sizeof(int) * 16));
+    lay.picks = reinterpret_cast<int *>(take(sizeof(int) * PSD_MAX_M));
+    return off;
+}
+
+}  // namespace
+
+size_t psd_projection_device_bytes(int64_t n, int m, int prec, int deterministic)
+{
+    psd_workspace lay;
+    size_t b = carve_workspace(lay, nullptr, n, psd_lpad(m));
+    if (deterministic) return b + sizeof(float) * (size_t)psd_det_part_floats(n, m);
+    if (prec == PSDPROJ_PREC_TF32) b += (size_t)psd_tile32_count(n) * (size_t)PSD_TILE_BYTES;
+    else if (prec == PSDPROJ_PREC_BF16) b += (size_t)psd_tile_count(n) * (size_t)PSD_TILE_BYTES;
+    else if (prec == PSDPROJ_PREC_BF16X3) b += 2 * (size_t)psd_tile_count(n) * (size_t)PSD_TILE_BYTES;
+    return b;
+}
+
 int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
 {
     psd_workspace &ws = ctx->ws;
@@ -111,45 +176,10 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
     const int64_t nn = ws.base ? (n > ws.n ? n : ws.n) : n;
     const int lp = ws.base ? (lpad > ws.lpad ? lpad : ws.lpad) : lpad;
     const int64_t ld = psd_ld(nn);
-    const int64_t nchunk = (nn + PSD_GRAM_CHUNK - 1) / PSD_GRAM_CHUNK;
-    const size_t tall = align256(sizeof(float) * (size_t)ld * lp);
-    const size_t half_tall = align256(sizeof(uint16_t) * (size_t)ld * lp);
-    const size_t small_d = align256(sizeof(double) * (size_t)lp * lp);
-    const size_t small_f = align256(sizeof(float) * (size_t)lp * lp);
-    const size_t chol_scr = align256(sizeof(double) * ((size_t)lp * lp + lp) + sizeof(float) * (size_t)lp * lp);
-    // One carve-up serves both the size (base == nullptr: offsets only) and
-    // the pointers, so the two cannot disagree.
     psd_workspace lay;
-    auto carve = [&](char *base) -> size_t {
-        size_t off = 0;
-        auto take = [&](size_t b) { char *q = base ? base + off : nullptr; off += align256(b); return q; };
-        lay.Om = reinterpret_cast<float *>(take(tall));
-        lay.Y = reinterpret_cast<float *>(take(tall));
-        lay.Q = reinterpret_cast<float *>(take(tall));
-        lay.T = reinterpret_cast<float *>(take(tall));
-        lay.W = reinterpret_cast<float *>(take(tall));
-        lay.Xf = reinterpret_cast<float *>(take(tall));
-        lay.Xhi = reinterpret_cast<uint16_t *>(take(half_tall));
-        lay.Xlo = reinterpret_cast<uint16_t *>(take(half_tall));
-        lay.gpart = reinterpret_cast<float *>(take(sizeof(float) * nchunk * lp * lp));
-        lay.G = reinterpret_cast<double *>(take(small_d));
-        lay.R = reinterpret_cast<double *>(take(small_d));
-        lay.C = reinterpret_cast<double *>(take(small_d));
-        lay.cholscr = reinterpret_cast<double *>(take(chol_scr));
-        lay.d = reinterpret_cast<double *>(take(sizeof(double) * lp));
-        lay.Rinv = reinterpret_cast<float *>(take(small_f));
-        lay.V = reinterpret_cast<float *>(take(small_f));
-        lay.M = reinterpret_cast<float *>(take(small_f));
-        lay.eigscr = reinterpret_cast<float *>(take(sizeof(float) * 3 * (size_t)(lp + 2) * (lp + 2)));
-        lay.dead = reinterpret_cast<int *>(take(sizeof(int) * lp));
-        lay.pv0 = reinterpret_cast<float *>(take(sizeof(float) * ld));
-        lay.pv1 = reinterpret_cast<float *>(take(sizeof(float) * ld));
-        lay.scal = reinterpret_cast<double *>(take(sizeof(double) * 16));
-        lay.ints = reinterpret_cast<int *>(take(sizeof(int) * 16));
-        lay.picks = reinterpret_cast<int *>(take(sizeof(int) * PSD_MAX_M));
-        return off;
-    };
+    auto carve = [&](char *base) -> size_t { return carve_workspace(lay, base, nn, lp); };
     const size_t total = carve(nullptr);
+    PSD_TRY(psd_budget_check(ctx, ws.bytes, total));
     if (ws.base) {
         cudaStreamSynchronize(ctx->stream);
         free_workspace(ws);
@@ -172,6 +202,8 @@ int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m)
 
 namespace {
 
+int ensure_stage(psdproj_ctx *ctx, float **buf, size_t *cap, size_t bytes, cudaStream_t s);
+
 // scalar slots in ws.scal
 enum { SC_SHIFT = 4, SC_SIGMA1 = 5, SC_SIGMA2 = 6, SC_ALPHA = 7 };
 // int slots in ws.ints
@@ -186,6 +218,9 @@ int check_opts(const psdproj_opts *o)
     if (o->eig < PSDPROJ_EIG_AUTO || o->eig > PSDPROJ_EIG_TRIDIAG) return PSDPROJ_EINVAL;
     if (o->sketch != PSDPROJ_SKETCH_GAUSS && o->sketch != PSDPROJ_SKETCH_SRHT) return PSDPROJ_EINVAL;
     if (o->alpha_mode != PSDPROJ_ALPHA_MINEIG && o->alpha_mode != PSDPROJ_ALPHA_RITZ) return PSDPROJ_EINVAL;
+    if (o->deterministic != 0 && o->deterministic != 1) return PSDPROJ_EINVAL;
+    if (o->spin_limit < 0) return PSDPROJ_EINVAL;
+    if (o->reserved[0] != 0 || o->reserved[1] != 0) return PSDPROJ_EINVAL;
     return PSDPROJ_OK;
 }
 
@@ -194,9 +229,10 @@ int check_opts(const psdproj_opts *o)
 // upper triangle, psd_tile_count(n) tiles; the split form also writes the
 // image of the low parts.  TF32: the full symmetric matrix,
 // psd_tile32_count(n) tiles, in the same buffer.
-int alloc_image(uint16_t **buf, size_t *cap, size_t bytes, cudaStream_t s)
+int alloc_image(psdproj_ctx *ctx, uint16_t **buf, size_t *cap, size_t bytes, cudaStream_t s)
 {
     if (*cap >= bytes) return PSDPROJ_OK;
+    PSD_TRY(psd_budget_check(ctx, *cap, bytes));
     if (*buf) {
         cudaStreamSynchronize(s);
         cudaFree(*buf);
@@ -213,15 +249,15 @@ int pack_image(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, int pre
 {
     if (prec == PSDPROJ_PREC_TF32) {
         const size_t bytes = (size_t)psd_tile32_count(n) * (size_t)PSD_TILE_BYTES;
-        PSD_TRY(alloc_image(&ctx->Ab, &ctx->Ab_bytes, bytes, ctx->stream));
+        PSD_TRY(alloc_image(ctx, &ctx->Ab, &ctx->Ab_bytes, bytes, ctx->stream));
         stage_scope st(ctx, PSDPROJ_STAGE_PACK);
         PSD_KL(launch_pack_tf32(ctx->stream, A, n, lda, reinterpret_cast<float *>(ctx->Ab)), 1);
         return PSDPROJ_OK;
     }
     const bool with_lo = prec == PSDPROJ_PREC_BF16X3;
     const size_t bytes = (size_t)psd_tile_count(n) * (size_t)PSD_TILE_BYTES;
-    PSD_TRY(alloc_image(&ctx->Ab, &ctx->Ab_bytes, bytes, ctx->stream));
-    if (with_lo) PSD_TRY(alloc_image(&ctx->Ab_lo, &ctx->Ab_lo_bytes, bytes, ctx->stream));
+    PSD_TRY(alloc_image(ctx, &ctx->Ab, &ctx->Ab_bytes, bytes, ctx->stream));
+    if (with_lo) PSD_TRY(alloc_image(ctx, &ctx->Ab_lo, &ctx->Ab_lo_bytes, bytes, ctx->stream));
     stage_scope st(ctx, PSDPROJ_STAGE_PACK);
     PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab, 0), 1);
     if (with_lo) PSD_KL(launch_pack_bf16(ctx->stream, A, n, lda, ctx->Ab_lo, 1), 1);
@@ -238,6 +274,14 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
              int64_t ldx, int m, const double *d_shift, float *Y, int64_t ldy, int prec,
              bool prepared = false)
 {
+    if (ctx->det) {
+        // fixed summation order, FP32 on the CUDA cores (opts.deterministic)
+        const size_t bytes = sizeof(float) * (size_t)psd_det_part_floats(n, m);
+        PSD_TRY(ensure_stage(ctx, &ctx->det_part, &ctx->det_part_bytes, bytes, ctx->stream));
+        stage_scope st(ctx, PSDPROJ_STAGE_APASS);
+        PSD_KL(launch_sym_pass_det(ctx->stream, A, n, lda, X, ldx, m, d_shift, Y, ldy, ctx->det_part), 2);
+        return PSDPROJ_OK;
+    }
     stage_scope st(ctx, PSDPROJ_STAGE_APASS);
     if (prec == PSDPROJ_PREC_FP32) {
         PSD_KL(launch_sym_pass_simt(ctx->stream, A, n, lda, X, ldx, m, d_shift, Y, ldy), 1);
@@ -255,18 +299,18 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
         if (prec == PSDPROJ_PREC_TF32) {
             PSD_KL(launch_sym_pass_tf32(ctx->stream, ctx->persist_sms, reinterpret_cast<const float *>(ctx->Ab), n,
                                         Xc, ldx, mc, d_shift, Yc, ldy, ws.Xf + (int64_t)c0 * ws.ld, ws.ld,
-                                        ctx->d_status), 2);
+                                        ctx->d_status, ctx->wait_limit), 2);
             continue;
         }
         uint16_t *Xhi = ws.Xhi + (int64_t)c0 * ws.ld, *Xlo = ws.Xlo + (int64_t)c0 * ws.ld;
         const bool prep = prepared && prec == PSDPROJ_PREC_BF16 && m <= 128;
         PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, Xc, ldx, mc, d_shift, Yc, ldy,
-                                  Xhi, ws.ld, ctx->d_status, 0, 0, prep ? 1 : 0), prep ? 1 : 2);
+                                  Xhi, ws.ld, ctx->d_status, 0, 0, prep ? 1 : 0, ctx->wait_limit), prep ? 1 : 2);
         if (prec == PSDPROJ_PREC_BF16X3) {
             PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab, n, Xc, ldx, mc, nullptr, Yc, ldy,
-                                      Xlo, ws.ld, ctx->d_status, 1, 1), 2);
+                                      Xlo, ws.ld, ctx->d_status, 1, 1, 0, ctx->wait_limit), 2);
             PSD_KL(launch_sym_pass_tc(ctx->stream, ctx->persist_sms, ctx->Ab_lo, n, Xc, ldx, mc, nullptr, Yc, ldy,
-                                      Xhi, ws.ld, ctx->d_status, 0, 1), 2);
+                                      Xhi, ws.ld, ctx->d_status, 0, 1, 0, ctx->wait_limit), 2);
         }
     }
     return PSDPROJ_OK;
@@ -316,7 +360,19 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     if (dW && ldw < n) return PSDPROJ_EINVAL;
     const int m = k + p;
     device_guard g(ctx->device);
+    // per-call settings read by the launches below, cleared again on return
+    // (the step-level entry points take neither)
+    struct call_settings {
+        psdproj_ctx *c;
+        ~call_settings() { c->wait_limit = 0; c->det = false; }
+    } settings_scope{ctx};
+    ctx->wait_limit = (long long)opts.spin_limit;
+    ctx->det = opts.deterministic != 0;
+    if (ctx->det) opts.prec = PSDPROJ_PREC_FP32;     // every product with A: the fixed-order FP32 kernels
     PSD_TRY(psd_ensure_workspace(ctx, n, m));
+    if (ctx->det)
+        PSD_TRY(ensure_stage(ctx, &ctx->det_part, &ctx->det_part_bytes,
+                             sizeof(float) * (size_t)psd_det_part_floats(n, m), ctx->stream));
     psd_workspace &ws = ctx->ws;
     cudaStream_t s = ctx->stream;
     const double *shift = nullptr;
@@ -330,14 +386,19 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         double *sc = ws.scal;
         if (!(alpha_in > 0.0)) {
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
-            if (bf16) {
+            if (ctx->det) {
+                PSD_KL(launch_power_iteration_det(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1, sc,
+                                                  sc + SC_SIGMA1, ctx->det_part), 3 * opts.N + 5);
+                PSD_KL(launch_power_iteration_det(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0, ws.pv1,
+                                                  sc, sc + SC_SIGMA2, ctx->det_part), 3 * opts.N + 5);
+            } else if (bf16) {
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
                                                    ws.pv0, ws.pv1, sc, sc + SC_SIGMA1,
-                                                   ctx->d_status),
+                                                   ctx->d_status, ctx->wait_limit),
                        2 * opts.N + 4);
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 4u,
                                                    sc + SC_SIGMA1, ws.pv0, ws.pv1, sc,
-                                                   sc + SC_SIGMA2, ctx->d_status),
+                                                   sc + SC_SIGMA2, ctx->d_status, ctx->wait_limit),
                        2 * opts.N + 4);
             } else {
                 PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
@@ -437,15 +498,16 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
             PSD_KL(launch_syrk_simt(s, Wd, ldwd, n, m, rk, dP, ldp, upper), 1);
         else
             PSD_KL(launch_syrk_tc(s, ctx->persist_sms, Wd, ldwd, n, m, rk, dP, ldp, upper, ws.Xhi,
-                                  ws.Xlo, ws.ld, ctx->d_status), 2);
+                                  ws.Xlo, ws.ld, ctx->d_status, ctx->wait_limit), 2);
     }
     if (d_rank) PSD_CK(cudaMemcpyAsync(d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, s));
     return PSDPROJ_OK;
 }
 
-int ensure_stage(float **buf, size_t *cap, size_t bytes, cudaStream_t s)
+int ensure_stage(psdproj_ctx *ctx, float **buf, size_t *cap, size_t bytes, cudaStream_t s)
 {
     if (*cap >= bytes) return PSDPROJ_OK;
+    PSD_TRY(psd_budget_check(ctx, *cap, bytes));
     if (*buf) {
         cudaStreamSynchronize(s);
         cudaFree(*buf);
@@ -473,9 +535,9 @@ int run_host(psdproj_ctx *ctx, const float *hA, int64_t n, int64_t lda, int k, i
     device_guard g(ctx->device);
     cudaStream_t s = ctx->stream;
     const int m = k + p;
-    PSD_TRY(ensure_stage(&ctx->dA_stage, &ctx->dA_stage_bytes, sizeof(float) * n * n, s));
-    if (wantP) PSD_TRY(ensure_stage(&ctx->dP_stage, &ctx->dP_stage_bytes, sizeof(float) * n * n, s));
-    if (hW) PSD_TRY(ensure_stage(&ctx->dW_stage, &ctx->dW_stage_bytes, sizeof(float) * n * m, s));
+    PSD_TRY(ensure_stage(ctx, &ctx->dA_stage, &ctx->dA_stage_bytes, sizeof(float) * n * n, s));
+    if (wantP) PSD_TRY(ensure_stage(ctx, &ctx->dP_stage, &ctx->dP_stage_bytes, sizeof(float) * n * n, s));
+    if (hW) PSD_TRY(ensure_stage(ctx, &ctx->dW_stage, &ctx->dW_stage_bytes, sizeof(float) * n * m, s));
     // Only A's upper triangle is ever read.  Pinned host memory is reachable
     // from the GPU (NVLink-C2C), so the device reads that half of A over the
     // link: the BF16 form packs its image straight from the host buffer (it
@@ -526,7 +588,7 @@ void psdproj_default_opts(psdproj_opts *o)
     o->out_mode = PSDPROJ_OUT_FULL;
 }
 
-int psdproj_create(psdproj_ctx **out, int device, void *stream)
+int psdproj_create(psdproj_ctx **out, int device, void *stream, size_t hbm_budget_bytes)
 {
     if (!out) return PSDPROJ_EINVAL;
     *out = nullptr;
@@ -538,6 +600,8 @@ int psdproj_create(psdproj_ctx **out, int device, void *stream)
     if (!c) return PSDPROJ_ENOMEM;
     c->device = device;
     c->stream = static_cast<cudaStream_t>(stream);
+    c->budget = hbm_budget_bytes;
+    c->root = c;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     // persistent kernels (one CTA per SM for the whole pass) leave one SM to
     // single-block kernels that another stream may run at the same time: a
@@ -578,6 +642,9 @@ int psdproj_destroy(psdproj_ctx *ctx)
     if (ctx->dA_stage) cudaFree(ctx->dA_stage);
     if (ctx->dP_stage) cudaFree(ctx->dP_stage);
     if (ctx->dW_stage) cudaFree(ctx->dW_stage);
+    if (ctx->det_part) cudaFree(ctx->det_part);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->Ab) cudaFree(ctx->Ab);
     if (ctx->Ab_lo) cudaFree(ctx->Ab_lo);
     for (int i = 0; i < PSD_MAX_LANES; ++i) {
@@ -644,7 +711,8 @@ const char *psdproj_status_string(int s)
 size_t psdproj_workspace_bytes(const psdproj_ctx *ctx)
 {
     if (!ctx) return 0;
-    size_t b = ctx->ws.bytes + ctx->Ab_bytes + ctx->Ab_lo_bytes;
+    size_t b = ctx->ws.bytes + ctx->Ab_bytes + ctx->Ab_lo_bytes + ctx->dA_stage_bytes + ctx->dP_stage_bytes +
+               ctx->dW_stage_bytes + ctx->det_part_bytes;
     for (int i = 0; i < PSD_MAX_LANES; ++i)
         if (ctx->lane[i]) b += psdproj_workspace_bytes(ctx->lane[i]);
     return b;
@@ -684,6 +752,15 @@ int psdproj_timing_read(psdproj_ctx *ctx, double *ms, int *count, int nkinds)
 
 uint64_t psdproj_kernel_launches(void) { return g_launches.load(); }
 
+size_t psdproj_projection_bytes(int64_t n, int k, int p, const psdproj_opts *opts_in)
+{
+    psdproj_opts o;
+    if (opts_in) o = *opts_in; else psdproj_default_opts(&o);
+    if (n < 1 || k < 1 || p < 0 || (int64_t)k + p > n || k + p > PSD_MAX_M || check_opts(&o) != PSDPROJ_OK)
+        return 0;
+    return psd_projection_device_bytes(n, k + p, o.prec, o.deterministic);
+}
+
 int psdproj_alg1(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int k, int p, int q,
                  uint64_t seed, float *dP, int64_t ldp, float *dW, int64_t ldw, int *d_rank,
                  const psdproj_opts *opts)
@@ -713,6 +790,7 @@ int ensure_lane(psdproj_ctx *ctx, int j)
     c->device = ctx->device;
     c->sm_count = ctx->sm_count;
     c->persist_sms = ctx->persist_sms;
+    c->root = ctx->root ? ctx->root : ctx;
     c->batch_streams = 1;
     c->owns_status = false;
     c->d_status = ctx->d_status;
@@ -729,15 +807,22 @@ int ensure_lane(psdproj_ctx *ctx, int j)
     return PSDPROJ_OK;
 }
 
-int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
-                    const psdproj_opts *opts_in)
+}  // extern "C"
+
+namespace {
+
+// A batch's plan: the problems spread over S lanes (own stream and
+// workspace) by longest-processing-time-first on the cost n^2 (2q + 2 +
+// [alg 2] 2(N + 1)), issued largest first so that the long ones start early.
+struct batch_plan {
+    int S = 1;
+    std::vector<int> order, lane_of;
+};
+
+int batch_validate(const psdproj_opts &opts, int count, const psdproj_problem *probs, int64_t &nmax, int &mmax)
 {
-    if (!ctx || count < 0 || (count > 0 && !probs)) return PSDPROJ_EINVAL;
-    psdproj_opts opts;
-    if (opts_in) opts = *opts_in; else psdproj_default_opts(&opts);
-    PSD_TRY(check_opts(&opts));
-    int64_t nmax = 0;
-    int mmax = 0;
+    nmax = 0;
+    mmax = 0;
     for (int i = 0; i < count; ++i) {
         const psdproj_problem &pb = probs[i];
         PSD_TRY(validate(pb.n, pb.lda, pb.k, pb.p, pb.q, pb.dA));
@@ -747,54 +832,196 @@ int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
         if (pb.n > nmax) nmax = pb.n;
         if (pb.k + pb.p > mmax) mmax = pb.k + pb.p;
     }
-    if (count == 0) return PSDPROJ_OK;
-    device_guard g(ctx->device);
+    return PSDPROJ_OK;
+}
+
+batch_plan batch_make_plan(const psdproj_ctx *ctx, const psdproj_opts &opts, int count, const psdproj_problem *probs)
+{
+    batch_plan pl;
+    pl.S = count < ctx->batch_streams ? count : ctx->batch_streams;
+    pl.order.resize(count);
+    pl.lane_of.assign(count, 0);
+    std::vector<double> cost(count), load(pl.S > 0 ? pl.S : 1, 0.0);
+    for (int i = 0; i < count; ++i) {
+        const psdproj_problem &pb = probs[i];
+        pl.order[i] = i;
+        cost[i] = (double)pb.n * (double)pb.n * (2.0 * pb.q + 2.0 + (pb.algorithm == 2 ? 2.0 * (opts.N + 1) : 0.0));
+    }
+    std::stable_sort(pl.order.begin(), pl.order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    if (pl.S > 1)
+        for (int i : pl.order) {
+            int best = 0;
+            for (int j = 1; j < pl.S; ++j)
+                if (load[j] < load[best]) best = j;
+            pl.lane_of[i] = best;
+            load[best] += cost[i];
+        }
+    return pl;
+}
+
+// Every workspace and image a plan's problems will use, allocated now (so
+// that issuing the batch allocates nothing: required inside a graph capture).
+int batch_presize(psdproj_ctx *ctx, const batch_plan &pl, const psdproj_opts &opts, int count,
+                  const psdproj_problem *probs)
+{
+    const int nl = pl.S > 1 ? pl.S : 1;
+    for (int j = 0; j < nl; ++j) {
+        psdproj_ctx *c = pl.S > 1 ? ctx->lane[j] : ctx;
+        int64_t nmax = 0;
+        int mmax = 0;
+        for (int i = 0; i < count; ++i) {
+            if (pl.S > 1 && pl.lane_of[i] != j) continue;
+            if (probs[i].n > nmax) nmax = probs[i].n;
+            if (probs[i].k + probs[i].p > mmax) mmax = probs[i].k + probs[i].p;
+        }
+        if (nmax == 0) continue;
+        PSD_TRY(psd_ensure_workspace(c, nmax, mmax));
+        if (opts.deterministic) {
+            PSD_TRY(ensure_stage(c, &c->det_part, &c->det_part_bytes,
+                                 sizeof(float) * (size_t)psd_det_part_floats(nmax, mmax), c->stream));
+        } else if (opts.prec == PSDPROJ_PREC_TF32) {
+            PSD_TRY(alloc_image(c, &c->Ab, &c->Ab_bytes, (size_t)psd_tile32_count(nmax) * PSD_TILE_BYTES, c->stream));
+        } else if (opts.prec != PSDPROJ_PREC_FP32) {
+            const size_t b = (size_t)psd_tile_count(nmax) * PSD_TILE_BYTES;
+            PSD_TRY(alloc_image(c, &c->Ab, &c->Ab_bytes, b, c->stream));
+            if (opts.prec == PSDPROJ_PREC_BF16X3) PSD_TRY(alloc_image(c, &c->Ab_lo, &c->Ab_lo_bytes, b, c->stream));
+        }
+    }
+    return PSDPROJ_OK;
+}
+
+// Issue a planned batch on the context's stream (fork to the lanes, join back).
+int batch_issue(psdproj_ctx *ctx, const batch_plan &pl, const psdproj_opts &opts, int count,
+                const psdproj_problem *probs)
+{
     auto run_one = [&](psdproj_ctx *c, const psdproj_problem &pb) {
         return run_projection(c, pb.dA, pb.n, pb.lda, pb.k, pb.p, pb.q, pb.seed, pb.algorithm == 2, pb.alpha_in,
                               pb.d_alpha_out, pb.d_info, pb.dP, pb.ldp, pb.dW, pb.ldw, pb.d_rank, &opts);
     };
-    const int S = count < ctx->batch_streams ? count : ctx->batch_streams;
-    if (S <= 1) {
-        // one workspace for the whole batch, problems one after another
-        PSD_TRY(psd_ensure_workspace(ctx, nmax, mmax));
+    if (pl.S <= 1) {
         for (int i = 0; i < count; ++i) PSD_TRY(run_one(ctx, probs[i]));
         return PSDPROJ_OK;
     }
-    // Grouped: the problems are spread over S lanes (own stream and workspace)
-    // by longest-processing-time-first on the cost n^2 (2q + 2 + [alg 2] 22),
-    // issued largest first so the long ones start early; the lanes fork from
-    // and join back to the context's stream.
-    for (int j = 0; j < S; ++j) PSD_TRY(ensure_lane(ctx, j));
-    std::vector<int> order(count), lane_of(count);
-    std::vector<double> cost(count), load(S, 0.0);
-    for (int i = 0; i < count; ++i) {
-        const psdproj_problem &pb = probs[i];
-        order[i] = i;
-        cost[i] = (double)pb.n * (double)pb.n * (2.0 * pb.q + 2.0 + (pb.algorithm == 2 ? 2.0 * (opts.N + 1) : 0.0));
-    }
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    for (int i : order) {
-        int best = 0;
-        for (int j = 1; j < S; ++j)
-            if (load[j] < load[best]) best = j;
-        lane_of[i] = best;
-        load[best] += cost[i];
-    }
     cudaEvent_t fork = ctx->lane_ev[PSD_MAX_LANES];
     PSD_CK(cudaEventRecord(fork, ctx->stream));
-    for (int j = 0; j < S; ++j) PSD_CK(cudaStreamWaitEvent(ctx->lane[j]->stream, fork, 0));
+    for (int j = 0; j < pl.S; ++j) PSD_CK(cudaStreamWaitEvent(ctx->lane[j]->stream, fork, 0));
     int rc = PSDPROJ_OK;
-    for (int i : order) {
-        rc = run_one(ctx->lane[lane_of[i]], probs[i]);
+    for (int i : pl.order) {
+        rc = run_one(ctx->lane[pl.lane_of[i]], probs[i]);
         if (rc != PSDPROJ_OK) break;
     }
     // join every lane back, also after an error, so that the context's stream
     // orders after all the work the batch issued
-    for (int j = 0; j < S; ++j) {
+    for (int j = 0; j < pl.S; ++j) {
         cudaEventRecord(ctx->lane_ev[j], ctx->lane[j]->stream);
         cudaStreamWaitEvent(ctx->stream, ctx->lane_ev[j], 0);
     }
     return rc;
+}
+
+void batch_graph_free(psdproj_ctx *ctx)
+{
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = nullptr;
+    ctx->graph_probs.clear();
+    ctx->graph_launches = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
+                    const psdproj_opts *opts_in)
+{
+    if (!ctx || count < 0 || (count > 0 && !probs)) return PSDPROJ_EINVAL;
+    psdproj_opts opts;
+    if (opts_in) opts = *opts_in; else psdproj_default_opts(&opts);
+    PSD_TRY(check_opts(&opts));
+    int64_t nmax = 0;
+    int mmax = 0;
+    PSD_TRY(batch_validate(opts, count, probs, nmax, mmax));
+    if (count == 0) return PSDPROJ_OK;
+    device_guard g(ctx->device);
+    const batch_plan pl = batch_make_plan(ctx, opts, count, probs);
+    if (pl.S <= 1) {
+        // one workspace for the whole batch, problems one after another
+        PSD_TRY(psd_ensure_workspace(ctx, nmax, mmax));
+    } else {
+        for (int j = 0; j < pl.S; ++j) PSD_TRY(ensure_lane(ctx, j));
+    }
+    return batch_issue(ctx, pl, opts, count, probs);
+}
+
+int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
+                          const psdproj_opts *opts_in)
+{
+    if (!ctx || count < 0 || (count > 0 && !probs)) return PSDPROJ_EINVAL;
+    psdproj_opts opts;
+    if (opts_in) opts = *opts_in; else psdproj_default_opts(&opts);
+    PSD_TRY(check_opts(&opts));
+    int64_t nmax = 0;
+    int mmax = 0;
+    PSD_TRY(batch_validate(opts, count, probs, nmax, mmax));
+    if (count == 0) return PSDPROJ_OK;
+    device_guard g(ctx->device);
+    // the same table, options and lane settings as the recorded graph: replay
+    const bool same = ctx->graph_exec && (int)ctx->graph_probs.size() == count &&
+                      memcmp(ctx->graph_probs.data(), probs, sizeof(psdproj_problem) * (size_t)count) == 0 &&
+                      memcmp(&ctx->graph_opts, &opts, sizeof(opts)) == 0 &&
+                      ctx->graph_streams == ctx->batch_streams && ctx->graph_persist == ctx->persist_sms;
+    if (!same) {
+        batch_graph_free(ctx);
+        const batch_plan pl = batch_make_plan(ctx, opts, count, probs);
+        if (pl.S > 1)
+            for (int j = 0; j < pl.S; ++j) PSD_TRY(ensure_lane(ctx, j));
+        PSD_TRY(batch_presize(ctx, pl, opts, count, probs));
+        // record with the stage timers off (events inside a graph are not read back)
+        int timing_was = ctx->timing.on;
+        ctx->timing.on = 0;
+        int lane_timing[PSD_MAX_LANES] = {};
+        for (int j = 0; j < PSD_MAX_LANES; ++j)
+            if (ctx->lane[j]) {
+                lane_timing[j] = ctx->lane[j]->timing.on;
+                ctx->lane[j]->timing.on = 0;
+            }
+        // record on a stream of the context's own (the caller's stream may be
+        // the legacy default stream, which cannot be captured); the graph is
+        // then launched into the caller's stream
+        if (!ctx->capture_stream)
+            PSD_CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t user = ctx->stream;
+        const uint64_t l0 = g_launches.load();
+        PSD_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed));
+        ctx->stream = ctx->capture_stream;
+        const int rc = batch_issue(ctx, pl, opts, count, probs);
+        ctx->stream = user;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        const uint64_t nk = g_launches.load() - l0;
+        ctx->timing.on = timing_was;
+        for (int j = 0; j < PSD_MAX_LANES; ++j)
+            if (ctx->lane[j]) ctx->lane[j]->timing.on = lane_timing[j];
+        if (rc != PSDPROJ_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            g_launches.fetch_sub(nk);
+            return rc != PSDPROJ_OK ? rc : cuda_status(ec, __LINE__);
+        }
+        g_launches.fetch_sub(nk);      // recorded, not launched: counted on each replay
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return cuda_status(ei, __LINE__);
+        ctx->graph_exec = exec;
+        ctx->graph_probs.assign(probs, probs + count);
+        ctx->graph_opts = opts;
+        ctx->graph_streams = ctx->batch_streams;
+        ctx->graph_persist = ctx->persist_sms;
+        ctx->graph_launches = nk;
+    }
+    PSD_CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    g_launches.fetch_add(ctx->graph_launches);
+    return PSDPROJ_OK;
 }
 
 int psdproj_sdls_dual_gd(psdproj_ctx *ctx, const psdproj_sdls *pr, double *y, float *dX, int64_t ldx,
@@ -819,10 +1046,10 @@ int psdproj_sdls_dual_gd(psdproj_ctx *ctx, const psdproj_sdls *pr, double *y, fl
     cudaStream_t s = ctx->stream;
     // X = C / rho + sum y_i A_i lives in the host-API staging buffer (n x n)
     const int64_t ldX = (n + 3) / 4 * 4;
-    PSD_TRY(ensure_stage(&ctx->dA_stage, &ctx->dA_stage_bytes, sizeof(float) * (size_t)n * ldX, s));
+    PSD_TRY(ensure_stage(ctx, &ctx->dA_stage, &ctx->dA_stage_bytes, sizeof(float) * (size_t)n * ldX, s));
     // device scratch: y (mc doubles), g (mc doubles), the mc pointers to A_i
     const size_t scratch = sizeof(double) * 2 * mc + sizeof(float *) * mc;
-    PSD_TRY(ensure_stage(&ctx->dP_stage, &ctx->dP_stage_bytes, scratch + 256, s));
+    PSD_TRY(ensure_stage(ctx, &ctx->dP_stage, &ctx->dP_stage_bytes, scratch + 256, s));
     double *d_y = reinterpret_cast<double *>(ctx->dP_stage);
     double *d_g = d_y + mc;
     const float **d_A = reinterpret_cast<const float **>(d_g + mc);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/psdproj.h"
 
 // Device status word: the first error code recorded wins.
@@ -119,11 +121,34 @@ struct psdproj_ctx {
     cudaEvent_t lane_ev[PSD_MAX_LANES + 1] = {};
     bool owns_status = true;     // false for a lane (the status word is its parent's)
     bool owns_stream = false;    // true for a lane (stream created by the library)
+    // device-memory budget (psdproj_create): held by this context and its
+    // lanes together; a lane's root is its parent, a context's is itself
+    size_t budget = 0;           // 0: no cap
+    psdproj_ctx *root = nullptr;
+    long long wait_limit = 0;    // opts.spin_limit of the call in progress
+    bool det = false;            // opts.deterministic of the call in progress
+    // partial sums of the deterministic products (psd_det_part_floats)
+    float *det_part = nullptr;  size_t det_part_bytes = 0;
+    // psdproj_batched_graph: the recorded batch and what it was recorded for
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<psdproj_problem> graph_probs;
+    psdproj_opts graph_opts = {};
+    int graph_streams = 0, graph_persist = 0;
+    uint64_t graph_launches = 0;     // kernels in the graph (counted per replay)
+    cudaStream_t capture_stream = nullptr;   // the stream a graph is recorded on
 };
+
+// PSDPROJ_OK when the budget of ctx's root allows replacing `old_bytes` of
+// device memory by `new_bytes`, else PSDPROJ_ENOMEM.
+int psd_budget_check(const psdproj_ctx *ctx, size_t old_bytes, size_t new_bytes);
 
 // Make sure the workspace holds n rows x m columns; may synchronise the
 // stream and reallocate.  Returns a PSDPROJ_* status.
 int psd_ensure_workspace(psdproj_ctx *ctx, int64_t n, int m);
+// Device bytes a context allocates for one projection of side n and sketch
+// width m in form prec: its workspace and image(s) of A (or, deterministic,
+// the partial sums instead of the images).
+size_t psd_projection_device_bytes(int64_t n, int m, int prec, int deterministic);
 
 // ---- launchers (all asynchronous on `s`; return cudaGetLastError) -------
 // Side outputs of a kernel that writes a tall matrix Z (n x m) which the
@@ -192,7 +217,8 @@ cudaError_t launch_pack_tf32(cudaStream_t s, const float *A, int64_t n, int64_t 
 // 4, 16-byte aligned) receives X rounded to TF32.  Requires m <= 128.
 cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, int64_t n,
                                  const float *X, int64_t ldx, int m, const double *d_shift,
-                                 float *Y, int64_t ldy, float *Xf, int64_t ldf, int *d_status);
+                                 float *Y, int64_t ldy, float *Xf, int64_t ldf, int *d_status,
+                                 long long wait_limit = 0);
 
 // Tensor-core symmetric pass Y = (A' + A'^T) X + shift X on the BF16 image;
 // Xh (ldh >= n, multiple of 8) receives the BF16 image of X.  Returns
@@ -206,7 +232,7 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t n, const float *X, int64_t ldx, int m,
                                const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
                                int64_t ldh, int *d_status, int x_part, int accumulate,
-                               int prepared = 0);
+                               int prepared = 0, long long wait_limit = 0);
 
 // Gram partials + FP64 reduction: G = X^T Z (sym = 1: X == Z, symmetric).
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
@@ -247,7 +273,7 @@ cudaError_t launch_syrk_simt(cudaStream_t s, const float *W, int64_t ldw, int64_
 cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t ldw,
                            int64_t n, int m, const int *d_rank, float *P, int64_t ldp,
                            int upper_only, uint16_t *Whi, uint16_t *Wlo, int64_t ldh,
-                           int *d_status);
+                           int *d_status, long long wait_limit = 0);
 
 // Power iteration (Alg. 4) with optional shift taken from *d_shift_in
 // (negated sigma); writes sigma to *d_sigma.
@@ -260,7 +286,23 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
 cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t n,
                                         int N, uint64_t seed, uint32_t stream_id,
                                         const double *d_shift_neg, float *v0, float *v1, double *scal,
-                                        double *d_sigma, int *d_status);
+                                        double *d_sigma, int *d_status, long long wait_limit = 0);
+
+// The power iteration's start (scal[0] = 1, v1 = 0) and its norm step
+// (scal[0] = 1/||y||, scal[1] = ||y||, *d_sigma = ||y|| when asked; other = 0).
+cudaError_t launch_pi_init(cudaStream_t s, double *scal, float *v1, int64_t n);
+cudaError_t launch_pi_norm(cudaStream_t s, const float *y, float *other, int64_t n, double *scal,
+                           double *d_sigma);
+
+// Deterministic (fixed summation order, no atomics) forms of the FP32 pass
+// and of the power iteration (csrc/detpass.cu).  part: psd_det_part_floats(n,
+// m) floats of device scratch.
+int64_t psd_det_part_floats(int64_t n, int m);
+cudaError_t launch_sym_pass_det(cudaStream_t s, const float *A, int64_t n, int64_t lda, const float *X,
+                                int64_t ldx, int m, const double *d_shift, float *Y, int64_t ldy, float *part);
+cudaError_t launch_power_iteration_det(cudaStream_t s, const float *A, int64_t n, int64_t lda, int N,
+                                       uint64_t seed, uint32_t stream_id, const double *d_shift_neg,
+                                       float *v0, float *v1, double *scal, double *d_sigma, float *part);
 
 cudaError_t launch_alpha_finish(cudaStream_t s, const double *d_s1, const double *d_s2,
                                 double alpha_in, double *d_alpha, double *d_shift,

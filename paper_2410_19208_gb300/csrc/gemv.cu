@@ -170,8 +170,9 @@ __device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
 __global__ void __launch_bounds__(gt::NTG, gt::CTAS_PER_SM)
 sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64_t tiles,
                       const float *__restrict__ x, float *__restrict__ y, const double *scal,
-                      const double *d_shift_neg, int *d_status)
+                      const double *d_shift_neg, int *d_status, long long wait_limit)
 {
+    const long long WL = wait_limit > 0 ? wait_limit : gt::WAIT_LIMIT;
     using namespace tc;
     extern __shared__ __align__(1024) uint8_t smt[];
     __shared__ uint64_t full[gt::STAGES], empty[gt::STAGES];
@@ -204,7 +205,7 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
             for (int64_t t = t0; t < t1; ++t, ++it) {
                 const int s = (int)(it % gt::STAGES);
                 const uint32_t us = (uint32_t)(it / gt::STAGES);
-                if (!mbar_wait(&empty[s], (us & 1) ^ 1, abort, gt::WAIT_LIMIT)) {
+                if (!mbar_wait(&empty[s], (us & 1) ^ 1, abort, WL)) {
                     s_abort = 1;
                     psd_set_status(d_status, PSDPROJ_ETIMEOUT);
                     break;
@@ -263,7 +264,7 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
             // a warp whose bounded wait fails records the abort but still
             // reaches the barrier below; every warp leaves after it together
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(&full[s], us & 1, abort, gt::WAIT_LIMIT) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait(&full[s], us & 1, abort, WL) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok && lane == 0) {
                 *cabort = 1;
@@ -521,7 +522,7 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
 cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t n,
                                         int N, uint64_t seed, uint32_t stream_id,
                                         const double *d_shift_neg, float *v0, float *v1, double *scal,
-                                        double *d_sigma, int *d_status)
+                                        double *d_sigma, int *d_status, long long wait_limit)
 {
     if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0 || (reinterpret_cast<uintptr_t>(v0) & 15) != 0 ||
         (reinterpret_cast<uintptr_t>(v1) & 15) != 0)
@@ -541,7 +542,7 @@ cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint
     float *in = v0, *out = v1;
     for (int it = 0; it <= N; ++it) {
         sym_gemv_tiles_kernel<<<grid, gt::NTG, gt::SMEM, s>>>(Ab, n, nbr, tiles, in, out, scal, d_shift_neg,
-                                                              d_status);
+                                                              d_status, wait_limit);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         pi_norm_kernel<<<1, 1024, 0, s>>>(out, in, n, scal, it == N ? d_sigma : nullptr);
@@ -550,6 +551,19 @@ cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint
         float *t = in; in = out; out = t;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_pi_init(cudaStream_t s, double *scal, float *v1, int64_t n)
+{
+    pi_init_kernel<<<64, 256, 0, s>>>(scal, v1, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pi_norm(cudaStream_t s, const float *y, float *other, int64_t n, double *scal,
+                           double *d_sigma)
+{
+    pi_norm_kernel<<<1, 1024, 0, s>>>(y, other, n, scal, d_sigma);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_alpha_finish(cudaStream_t s, const double *d_s1, const double *d_s2,
@@ -601,6 +615,14 @@ extern "C" int psdproj_min_eig_noalloc(const float *dA, int64_t n, int64_t lda, 
     static void *addr[64] = {nullptr};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PSDPROJ_ECUDA;
+    // A must live on the current device (the scratch address is that device's)
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, dA) != cudaSuccess) {
+        cudaGetLastError();
+        return PSDPROJ_EINVAL;
+    }
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) return PSDPROJ_EINVAL;
+    if (pa.device != dev) return PSDPROJ_EINVAL;
     unsigned char *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(mu);

@@ -40,11 +40,16 @@ struct Ticket {
     clock_type::time_point t_submit, t_done;
 };
 
-size_t default_footprint(const psdproj_request &r)
+// Device memory a request holds while admitted: its A, P and W, and the
+// workspace and image of A that the worker context running it needs for
+// this request's size, sketch width and form (a worker keeps what it grew
+// to for its largest request; the charge is this request's own need).
+size_t default_footprint(const psdproj_request &r, const psdproj_opts &o)
 {
     size_t b = (size_t)r.n * (size_t)r.lda * sizeof(float);
     if (r.dP) b += (size_t)r.n * (size_t)r.ldp * sizeof(float);
     if (r.dW) b += (size_t)r.ldw * (size_t)(r.k + r.p) * sizeof(float);
+    b += psdproj_projection_bytes(r.n, r.k, r.p, &o);
     return b;
 }
 
@@ -196,7 +201,7 @@ int psdproj_server_create(psdproj_server **out, int device, int workers, size_t 
         }
         s->done_ev.push_back(ev);
         psdproj_ctx *c = nullptr;
-        rc = psdproj_create(&c, device, st);
+        rc = psdproj_create(&c, device, st, 0);
         if (rc == PSDPROJ_OK) s->ctx.push_back(c);
     }
     if (rc != PSDPROJ_OK) {
@@ -214,7 +219,7 @@ int psdproj_server_submit(psdproj_server *s, const psdproj_request *req, uint64_
     *ticket = 0;
     const int rc = check_request(*req, s->opts.out_mode);
     if (rc != PSDPROJ_OK) return rc;
-    const size_t bytes = req->footprint_bytes > 0 ? (size_t)req->footprint_bytes : default_footprint(*req);
+    const size_t bytes = req->footprint_bytes > 0 ? (size_t)req->footprint_bytes : default_footprint(*req, s->opts);
     if (bytes > s->admit_bytes) return PSDPROJ_ETOOLARGE;
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return PSDPROJ_EINVAL;

@@ -110,6 +110,7 @@ struct Params {
     float *Y;
     int64_t ldy;
     int *d_status;
+    long long wait_limit;   // cycles a pipeline wait may spin (opts.spin_limit; 0: WAIT_LIMIT)
     int tma_y;                  // Y reduced by TMA (aligned Y); else scalar atomics
     int64_t tstart[MAX_GRID + 1];  // CTA b owns tiles tstart[b] .. tstart[b + 1] - 1
 };
@@ -196,13 +197,14 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     Bars &B = *reinterpret_cast<Bars *>(sm + L::OFF_BAR);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t0 = P.tstart[blockIdx.x], t1 = P.tstart[blockIdx.x + 1];
+    const long long WL = P.wait_limit > 0 ? P.wait_limit : WAIT_LIMIT;
     if ((smem_u32(sm) & 1023u) != 0u) {
         if (threadIdx.x == 0) psd_set_status(P.d_status, PSDPROJ_ECUDA);
         return;
     }
     // rows MR..127 of every X slot: zero, written once (the copies fill rows
     // 0..MR-1 only); visible to the tensor core's reads through the fence below
-    if (MR < 128) {
+    if constexpr (MR < 128) {
         constexpr int PADV = (128 - MR) * 128 / 16;          // 16-byte words per slot
         for (int e = threadIdx.x; e < NX * PADV; e += NT) {
             const int slot = e / PADV, w = e % PADV;
@@ -254,7 +256,7 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
             bool ok = true;
             auto push_x = [&](int x) -> bool {      // one 64-row box of X^T at row x
                 const int sl = xs.slot(NX);
-                if (!mbar_wait(&B.emptyX[sl], xs.phase(NX) ^ 1, abort, WAIT_LIMIT)) return false;
+                if (!mbar_wait(&B.emptyX[sl], xs.phase(NX) ^ 1, abort, WL)) return false;
                 mbar_arrive_expect_tx(&B.fullX[sl], L::XB);
                 tma_load_2d(sm + L::OFF_X + sl * L::XS, &tmX, x, 0, &B.fullX[sl]);
                 ++xs.item;
@@ -268,7 +270,7 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 }
                 const int s = (int)(na % NA);
                 const uint32_t us = (uint32_t)(na / NA);
-                if (!mbar_wait(&B.emptyA[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                if (!mbar_wait(&B.emptyA[s], (us & 1) ^ 1, abort, WL)) { ok = false; break; }
                 mbar_arrive_expect_tx(&B.fullA[s], A_BYTES);
                 bulk_load(sm + s * A_BYTES, Ab + t * PSD_TILE_ELEMS, A_BYTES, &B.fullA[s]);
                 ++na;
@@ -310,11 +312,11 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                     if (seg > 0) {
                         // the previous row's MMAs read X_I in TMEM: let them complete
                         mma_commit(&B.xidone);
-                        ok = mbar_wait(&B.xidone, (seg - 1) & 1, abort, WAIT_LIMIT);
+                        ok = mbar_wait(&B.xidone, (seg - 1) & 1, abort, WL);
                     }
                     for (int kk = 0; kk < BM / 64 && ok; ++kk) {
                         const int sl = xs.slot(NX);
-                        ok = mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WAIT_LIMIT);
+                        ok = mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WL);
                         if (!ok) break;
                         tc_fence_after();
                         const uint64_t xd = dX0 + (uint64_t)((sl * L::XS) >> 4);
@@ -332,9 +334,9 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
                 const uint64_t aoff = (uint64_t)((s * A_BYTES) >> 4);
-                if (!mbar_wait(&B.fullA[s], us & 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                if (!mbar_wait(&B.fullA[s], us & 1, abort, WL)) { ok = false; break; }
                 // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows; X_I^T from TMEM)
-                if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WL)) { ok = false; break; }
                 tc_fence_after();
                 {
                     const uint64_t bd = dAmn0 + aoff;
@@ -347,10 +349,10 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 }
                 // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns); D1 drained
                 // by the epilogue before a block row's first tile
-                if (first && !mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WAIT_LIMIT)) { ok = false; break; }
+                if (first && !mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WL)) { ok = false; break; }
                 {
                     const int sl = xs.slot(NX);
-                    if (!mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WAIT_LIMIT)) { ok = false; break; }
+                    if (!mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WL)) { ok = false; break; }
                     tc_fence_after();
                     const uint64_t ad = dX0 + (uint64_t)((sl * L::XS) >> 4), bd = dA0 + aoff;
 #pragma unroll
@@ -389,7 +391,7 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
             {
                 // lane 0 waits (bounded); the warp leaves together
                 int ok = 1;
-                if (lane == 0) ok = mbar_wait(&B.d2full[b], ub & 1, abort, WAIT_LIMIT) ? 1 : 0;
+                if (lane == 0) ok = mbar_wait(&B.d2full[b], ub & 1, abort, WL) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { if (lane == 0) fail(B, P.d_status); break; }
             }
@@ -402,7 +404,7 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
             flush32(P, &tmY, stg, q, lane, (int64_t)BN * J + 32 * h, v);
             if (last) {
                 int ok = 1;
-                if (lane == 0) ok = mbar_wait(&B.d1full, seg & 1, abort, WAIT_LIMIT) ? 1 : 0;
+                if (lane == 0) ok = mbar_wait(&B.d1full, seg & 1, abort, WL) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { if (lane == 0) fail(B, P.d_status); break; }
                 tc_fence_after();
@@ -547,7 +549,8 @@ cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t 
 cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t n, const float *X, int64_t ldx, int m,
                                const double *d_shift, float *Y, int64_t ldy, uint16_t *Xh,
-                               int64_t ldh, int *d_status, int x_part, int accumulate, int prepared)
+                               int64_t ldh, int *d_status, int x_part, int accumulate, int prepared,
+                               long long wait_limit)
 {
     if (m < 1 || m > 128) return cudaErrorNotSupported;
     if (prepared && (x_part != 0 || accumulate != 0)) return cudaErrorInvalidValue;
@@ -590,6 +593,7 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
     P.Y = Y;
     P.ldy = ldy;
     P.d_status = d_status;
+    P.wait_limit = wait_limit;
     P.tma_y = ((ldy % 4) == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0);
     CUtensorMap tmY;
     memset(&tmY, 0, sizeof(tmY));

@@ -89,6 +89,7 @@ struct Params {
     float *Y;
     int64_t ldy;
     int *d_status;
+    long long wait_limit;   // cycles a pipeline wait may spin (opts.spin_limit; 0: WAIT_LIMIT)
     int tma_y;
 };
 
@@ -142,6 +143,7 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
                      const __grid_constant__ CUtensorMap tmY, const Params P)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
+    const long long WL = P.wait_limit > 0 ? P.wait_limit : WAIT_LIMIT;
     Bars &B = *reinterpret_cast<Bars *>(sm + OFF_BAR);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t0 = P.tiles * blockIdx.x / gridDim.x;
@@ -183,7 +185,7 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
                 const int J = (int)(t % P.nbc);
                 const int s = (int)(it % NSTAGE);
                 const uint32_t us = (uint32_t)(it / NSTAGE);
-                if (!mbar_wait(&B.empty[s], (us & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                if (!mbar_wait(&B.empty[s], (us & 1) ^ 1, abort, WL)) { fail(B, P.d_status); break; }
                 mbar_arrive_expect_tx(&B.full[s], STAGE);
                 bulk_load(sm + s * STAGE, At + t * PSD_TILE_BYTES, A_BYTES, &B.full[s]);
                 tma_load_2d(sm + s * STAGE + A_BYTES, &tmX, BN * J, 0, &B.full[s]);
@@ -202,13 +204,13 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
                 const bool first = (t == t0) || (J == 0);
                 const bool last = (J == P.nbc - 1) || (t + 1 == t1);
                 const int b = seg & 1;
-                if (first && !mbar_wait(&B.dempty[b], ((uint32_t)(seg >> 1) & 1) ^ 1, abort, WAIT_LIMIT)) {
+                if (first && !mbar_wait(&B.dempty[b], ((uint32_t)(seg >> 1) & 1) ^ 1, abort, WL)) {
                     fail(B, P.d_status);
                     break;
                 }
                 const int s = (int)(it % NSTAGE);
                 const uint32_t us = (uint32_t)(it / NSTAGE);
-                if (!mbar_wait(&B.full[s], us & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                if (!mbar_wait(&B.full[s], us & 1, abort, WL)) { fail(B, P.d_status); break; }
                 tc_fence_after();
                 const uint32_t a_tile = smem_u32(sm + s * STAGE);
                 const uint32_t xj = a_tile + A_BYTES;
@@ -240,7 +242,7 @@ sym_pass_tf32_kernel(const uint8_t *__restrict__ At, const __grid_constant__ CUt
             const int b = seg & 1;
             {
                 int ok = 1;
-                if (lane == 0) ok = mbar_wait(&B.dfull[b], (uint32_t)(seg >> 1) & 1, abort, WAIT_LIMIT) ? 1 : 0;
+                if (lane == 0) ok = mbar_wait(&B.dfull[b], (uint32_t)(seg >> 1) & 1, abort, WL) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { if (lane == 0) fail(B, P.d_status); break; }
             }
@@ -385,7 +387,8 @@ cudaError_t launch_pack_tf32(cudaStream_t s, const float *A, int64_t n, int64_t 
 
 cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, int64_t n,
                                  const float *X, int64_t ldx, int m, const double *d_shift,
-                                 float *Y, int64_t ldy, float *Xf, int64_t ldf, int *d_status)
+                                 float *Y, int64_t ldy, float *Xf, int64_t ldf, int *d_status,
+                                 long long wait_limit)
 {
     if (m < 1 || m > 128) return cudaErrorNotSupported;
     if ((reinterpret_cast<uintptr_t>(At) & 15) != 0) return cudaErrorNotSupported;
@@ -409,6 +412,7 @@ cudaError_t launch_sym_pass_tf32(cudaStream_t s, int sm_count, const float *At, 
     P.Y = Y;
     P.ldy = ldy;
     P.d_status = d_status;
+    P.wait_limit = wait_limit;
     P.tma_y = ((ldy % 4) == 0) && ((reinterpret_cast<uintptr_t>(Y) & 15) == 0);
     CUtensorMap tmY;
     memset(&tmY, 0, sizeof(tmY));

@@ -62,6 +62,7 @@ struct Params {
     int upper_only;
     int nprod;        // 3: split BF16, 1: BF16 hi only
     int *d_status;
+    long long wait_limit;   // cycles a pipeline wait may spin (opts.spin_limit; 0: WAIT_LIMIT)
     int vec_ok;
     int tma_p;        // P written by TMA stores (16-byte aligned rows)
 };
@@ -105,6 +106,7 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
                    const __grid_constant__ CUtensorMap tmP, const Params P)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
+    const long long WL = P.wait_limit > 0 ? P.wait_limit : WAIT_LIMIT;
     Bars &B = *reinterpret_cast<Bars *>(sm + OFF_BAR);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t0 = P.tiles * blockIdx.x / gridDim.x;
@@ -153,7 +155,7 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
                 int I, J;
                 tile_of(t, P.nb, I, J);
                 if (I != curI) {
-                    if (!mbar_wait(&B.emptyWI, (wi_uses & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                    if (!mbar_wait(&B.emptyWI, (wi_uses & 1) ^ 1, abort, WL)) { fail(B, P.d_status); break; }
                     mbar_arrive_expect_tx(&B.fullWI, op_tx * (lo_too ? 2u : 1u));
                     for (int a = 0; a < 2; ++a) {
                         tma_load_2d(sm + OFF_WI + a * ATOM_COL, &tmHi, TS * I + 64 * a, 0, &B.fullWI);
@@ -165,7 +167,7 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
                 }
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
-                if (!mbar_wait(&B.emptyWJ[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                if (!mbar_wait(&B.emptyWJ[b], (ub & 1) ^ 1, abort, WL)) { fail(B, P.d_status); break; }
                 mbar_arrive_expect_tx(&B.fullWJ[b], op_tx * (lo_too ? 2u : 1u));
                 uint8_t *dst = sm + OFF_WJ + b * 2 * OP_BYTES;
                 for (int a = 0; a < 2; ++a) {
@@ -189,13 +191,13 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
                 tile_of(t, P.nb, I, J);
                 const bool last = (t + 1 == t1) || (I + 1 < P.nb && t + 1 == row_start(I + 1, P.nb));
                 if (I != curI) {
-                    if (!mbar_wait(&B.fullWI, seg & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                    if (!mbar_wait(&B.fullWI, seg & 1, abort, WL)) { fail(B, P.d_status); break; }
                     curI = I;
                 }
                 const int b = (int)(it & 1);
                 const uint32_t ub = (uint32_t)(it >> 1);
-                if (!mbar_wait(&B.fullWJ[b], ub & 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
-                if (!mbar_wait(&B.dempty[b], (ub & 1) ^ 1, abort, WAIT_LIMIT)) { fail(B, P.d_status); break; }
+                if (!mbar_wait(&B.fullWJ[b], ub & 1, abort, WL)) { fail(B, P.d_status); break; }
+                if (!mbar_wait(&B.dempty[b], (ub & 1) ^ 1, abort, WL)) { fail(B, P.d_status); break; }
                 tc_fence_after();
                 const uint32_t ahi = smem_u32(sm + OFF_WI), alo = ahi + OP_BYTES;
                 const uint32_t bhi = smem_u32(sm + OFF_WJ + b * 2 * OP_BYTES), blo = bhi + OP_BYTES;
@@ -235,7 +237,7 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
             const int b = (int)(it & 1);
             const uint32_t ub = (uint32_t)(it >> 1);
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(&B.dfull[b], ub & 1, abort, WAIT_LIMIT) ? 1 : 0;
+            if (lane == 0) ok = mbar_wait(&B.dfull[b], ub & 1, abort, WL) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) { if (lane == 0) fail(B, P.d_status); break; }
             tc_fence_after();
@@ -366,7 +368,7 @@ bool encode_w(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *map, void *bas
 
 cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t ldw, int64_t n,
                            int m, const int *d_rank, float *P, int64_t ldp, int upper_only,
-                           uint16_t *Whi, uint16_t *Wlo, int64_t ldh, int *d_status)
+                           uint16_t *Whi, uint16_t *Wlo, int64_t ldh, int *d_status, long long wait_limit)
 {
     if (m < 1 || m > KMAX) return cudaErrorNotSupported;
     if ((ldh % 8) != 0 || ldh < n || (reinterpret_cast<uintptr_t>(Whi) & 15) ||
@@ -397,6 +399,7 @@ cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t
     p.upper_only = upper_only;
     p.nprod = 3;
     p.d_status = d_status;
+    p.wait_limit = wait_limit;
     p.vec_ok = ((ldp % 4) == 0) && ((reinterpret_cast<uintptr_t>(P) & 15) == 0);
     p.tma_p = p.vec_ok;
     CUtensorMap tmP;

@@ -40,6 +40,7 @@ def test_defaults_and_status_strings(lib):
     o = ps.Opts()
     lib.psdproj_default_opts(ctypes.byref(o))
     assert (o.prec, o.syrk_prec, o.N, o.out_mode) == (0, 0, 10, 0)
+    assert (o.deterministic, o.spin_limit, list(o.reserved)) == (0, 0, [0, 0])
     for code in range(8):
         s = lib.psdproj_status_string(code)
         assert s.startswith(b"PSDPROJ")
@@ -52,12 +53,12 @@ def test_rejects_bad_arguments_without_a_gpu(lib):
     assert lib.psdproj_alg1(None, None, 10, 10, 2, 2, 0, 1, None, 10, None, 10, None, None) == 1
     assert lib.psdproj_destroy(None) == 0
     assert lib.psdproj_sync_status(None) == 1
-    assert lib.psdproj_create(None, 0, None) == 1
+    assert lib.psdproj_create(None, 0, None, 0) == 1
     assert lib.psdproj_set_reserved_sms(None, 1) == 1
     assert lib.psdproj_set_batch_streams(None, 4) == 1
     h = ctypes.c_void_p()
     # device index out of range (no device here, or index too large)
-    assert lib.psdproj_create(ctypes.byref(h), 1 << 20, None) != 0
+    assert lib.psdproj_create(ctypes.byref(h), 1 << 20, None, 0) != 0
 
 
 def test_built_for_sm_103a_only():
@@ -85,14 +86,16 @@ def test_struct_layouts_match_the_c_header(tmp_path):
         "int main(void) {\n"
         '  printf("%zu %zu %zu %zu\\n", sizeof(psdproj_problem), sizeof(psdproj_request),\n'
         "         offsetof(psdproj_request, footprint_bytes), sizeof(psdproj_server_stats));\n"
-        '  printf("%zu %zu\\n", offsetof(psdproj_server_stats, inflight_peak_bytes), sizeof(psdproj_opts));\n'
+        '  printf("%zu %zu %zu\\n", offsetof(psdproj_server_stats, inflight_peak_bytes), sizeof(psdproj_opts),\n'
+        "         offsetof(psdproj_opts, spin_limit));\n"
         "  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     got = [int(x) for x in out]
     want = [ctypes.sizeof(ps.Problem), ctypes.sizeof(ps.Request), ps.Request.footprint_bytes.offset,
-            ctypes.sizeof(ps.ServerStats), ps.ServerStats.inflight_peak_bytes.offset, ctypes.sizeof(ps.Opts)]
+            ctypes.sizeof(ps.ServerStats), ps.ServerStats.inflight_peak_bytes.offset, ctypes.sizeof(ps.Opts),
+            ps.Opts.spin_limit.offset]
     assert got == want
 
 

@@ -530,9 +530,11 @@ def test_server_admission_bounds_device_memory():
     # budget for three of the largest requests: the admitted footprint never
     # exceeds it, everything still completes, first come first served
     reqs = _served_requests(24, 256, 700, seed=5)
-    foot = [2 * 4 * r["n"] * r["n"] for r in reqs]          # A + P, lda = ldp = n
+    opts = ps.make_opts(prec=ps.PREC_FP32)
+    # A + P (lda = ldp = n) and the worker context's memory for the request
+    foot = [2 * 4 * r["n"] * r["n"] + ps.projection_bytes(r["n"], r["k"], r["p"], opts) for r in reqs]
     budget = 3 * max(foot)
-    srv = ps.Server(0, workers=6, admit_bytes=budget, opts=ps.make_opts(prec=ps.PREC_FP32))
+    srv = ps.Server(0, workers=6, admit_bytes=budget, opts=opts)
     tickets, keep = [], []
     for r in reqs:
         Vr, lam = si.make_problem("batch", r["n"], seed_u=r["mseed"][0], seed_lam=r["mseed"][1])
@@ -820,3 +822,140 @@ def test_concurrent_contexts_on_separate_streams_agree(ctx, oracle_lib):
     finally:
         for c in ctxs:
             c.close()
+
+
+# ----------------------------------------------------------------------------
+# boundary: device-memory budget, bounded waits, deterministic mode
+# ----------------------------------------------------------------------------
+def test_budget_returns_enomem_before_anything_runs():
+    n, k, p, q = 1024, 40, 8, 1
+    Vr, lam = si.make_problem("small", n)
+    A = si.form_A_torch(Vr, lam, "cuda")
+    P = torch.full((n, n), float("nan"), device="cuda")
+    torch.cuda.synchronize()
+    small = ps.Context(0, hbm_budget=1 << 20)          # 1 MB: not even the workspace fits
+    with pytest.raises(ps.PsdprojError) as e:
+        small.alg1(A, k, p, q, 1, P=P)
+    assert e.value.code == 2                           # PSDPROJ_ENOMEM
+    assert small.sync_status() == 0
+    assert small.workspace_bytes() == 0                # nothing was allocated
+    assert torch.isnan(P).all()                        # and nothing ran
+    small.close()
+    # room for the FP32 form's workspace, not for the BF16 image of A as well
+    fp32 = ps.Context(0)
+    fp32.alg1(A, k, p, q, 1, P=P)
+    assert fp32.sync_status() == 0
+    ws = fp32.workspace_bytes()
+    fp32.close()
+    mid = ps.Context(0, hbm_budget=ws + (1 << 16))
+    mid.alg1(A, k, p, q, 1, P=P)
+    assert mid.sync_status() == 0
+    with pytest.raises(ps.PsdprojError) as e:
+        mid.alg1(A, k, p, q, 1, P=P, opts=ps.make_opts(prec=ps.PREC_BF16))
+    assert e.value.code == 2
+    assert mid.workspace_bytes() <= ws + (1 << 16)
+    mid.close()
+
+
+@pytest.mark.parametrize("alg", [1, 2])
+def test_spin_limit_gives_etimeout_and_the_context_recovers(oracle_lib, alg):
+    """A one-cycle spin limit makes the tensor-core kernels' first unready
+    wait give up: the call's device status is PSDPROJ_ETIMEOUT, the kernels
+    return (after draining their own copies and MMAs), and the next call on
+    the same context with the default limit is correct."""
+    n, k, p, q, seed = 2304, 60, 10, 1, 4
+    Vr, lam = si.make_problem("decay", n)
+    A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
+    A = torch.from_numpy(A32).cuda()
+    c = ps.Context(0)
+    P = torch.empty(n, n, device="cuda")
+    W = ps.tall_empty(n, k + p)
+    tight = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3, spin_limit=1)
+    run = c.alg1 if alg == 1 else c.alg2
+    run(A, k, p, q, seed, P=P, W=W, opts=tight)
+    assert c.sync_status() == 5                        # PSDPROJ_ETIMEOUT
+    assert c.sync_status() == 0                        # read and cleared
+    run(A, k, p, q, seed, P=P, W=W, opts=ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3))
+    assert c.sync_status() == 0
+    Wg = W.cpu().numpy().astype(np.float64)
+    if alg == 1:
+        Wo = oracle_lib.alg1(A32.astype(np.float64), k, p, q, seed)["W"]
+    else:
+        Wo = oracle_lib.alg2(A32.astype(np.float64), k, p, q, seed, N=10)["W_red"]
+    rel = np.sqrt(max(oracle_lib.factor_dist2(Wg, Wo), 0.0) / oracle_lib.factor_norm2(Wo))
+    assert rel <= 2e-2
+    c.close()
+
+
+@pytest.mark.parametrize("alg", [1, 2])
+def test_deterministic_mode_is_bitwise_repeatable(ctx, oracle_lib, alg):
+    n, k, p, q, seed = 1777, 50, 10, 1, 6
+    Vr, lam = si.make_problem("decay", n)
+    A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
+    opts = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3, deterministic=1)
+    outs = [_run(ctx, A32, k, p, q, seed, alg=alg, opts=opts) for _ in range(3)]
+    for o in outs[1:]:
+        assert np.array_equal(o["P"], outs[0]["P"]) and np.array_equal(o["W"], outs[0]["W"])
+        assert o["rank"] == outs[0]["rank"]
+        if alg == 2:
+            assert o["alpha"] == outs[0]["alpha"]
+    if alg == 1:
+        Wo = oracle_lib.alg1(A32.astype(np.float64), k, p, q, seed)["W"]
+    else:
+        Wo = oracle_lib.alg2(A32.astype(np.float64), k, p, q, seed, N=10)["W_red"]
+    # the deterministic products are FP32: the plain FP32 form's bound
+    assert _rel(outs[0]["P"], Wo @ Wo.T) <= TOL
+
+
+def test_batched_graph_replays_the_batch(ctx, oracle_lib):
+    """psdproj_batched_graph: the first call records the batch into a CUDA
+    graph, later calls with the same table replay it; each result matches a
+    single call's (BF16 form, within its spread) and a changed table (other
+    seeds) is recorded anew and matches its own single calls."""
+    sizes = [96, 300, 517, 1024, 200, 777]
+    probs, singles = [], []
+    opts = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3)
+    for i, n in enumerate(sizes):
+        Vr, lam = si.make_problem("batch", n, seed_u=50 + i, seed_lam=60 + i)
+        A = si.form_A_torch(Vr, lam, "cuda")
+        probs.append(dict(A=A, k=max(2, min(n // 8, 64)), p=8, q=1, seed=20 + i, algorithm=1 + (i % 2),
+                          P=torch.empty(n, n, device="cuda"), W=ps.tall_empty(n, max(2, min(n // 8, 64)) + 8)))
+    # the default stream (the legacy stream, which cannot be captured itself)
+    c = ps.Context(0, torch.cuda.default_stream())
+    c.set_batch_streams(4)
+
+    def single_W(d, seed):
+        n = d["A"].shape[0]
+        W = ps.tall_empty(n, d["k"] + d["p"])
+        if d["algorithm"] == 1:
+            ctx.alg1(d["A"], d["k"], d["p"], d["q"], seed, W=W, P=torch.empty(n, n, device="cuda"), opts=opts)
+        else:
+            ctx.alg2(d["A"], d["k"], d["p"], d["q"], seed, W=W, P=torch.empty(n, n, device="cuda"), opts=opts)
+        assert ctx.sync_status() == 0
+        return W.cpu().numpy().astype(np.float64)
+
+    def check(seed_of):
+        for d in probs:
+            ref = single_W(d, seed_of(d))
+            got = d["W"].cpu().numpy().astype(np.float64)
+            rel = np.sqrt(max(oracle_lib.factor_dist2(got, ref), 0.0) / oracle_lib.factor_norm2(ref))
+            assert rel <= 2e-3, (d["A"].shape[0], rel)
+            Pg = d["P"].cpu().numpy().astype(np.float64)
+            assert np.abs(Pg - got @ got.T).max() <= 3e-5 * (np.abs(got) @ np.abs(got).T).max() + 1e-7
+
+    try:
+        l0 = ps.lib().psdproj_kernel_launches()
+        for _ in range(3):                       # record, then two replays
+            for d in probs:
+                d["W"].fill_(float("nan"))
+            c.batched(probs, opts=opts, graph=True)
+            assert c.sync_status() == 0
+            check(lambda d: d["seed"])
+        assert ps.lib().psdproj_kernel_launches() - l0 > 0    # replays are counted
+        for d in probs:                          # a different table: recorded anew
+            d["seed"] += 1000
+        c.batched(probs, opts=opts, graph=True)
+        assert c.sync_status() == 0
+        check(lambda d: d["seed"])
+    finally:
+        c.close()
