@@ -85,9 +85,11 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the TF32 / split-BF16 comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload in the headline run")
     ap.add_argument("--no-serve", action="store_true", help="skip the served workload in the headline run")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batched", "serve"],
+    ap.add_argument("--workload", default="headline", choices=["headline", "batched", "serve", "profile"],
                     help="batched: 512 matrices, sides log-uniform in [64, 2048], through psdproj_batched; "
-                         "serve: Poisson arrivals through psdproj_server")
+                         "serve: Poisson arrivals through psdproj_server; profile: the small case the ncu "
+                         "summaries under profiles/ are captured on (three Alg. 2 projections, BF16 form, "
+                         "split-BF16 SYRK, side --n)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="offered requests per second")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-workers", type=int, default=8)
@@ -504,8 +506,35 @@ def run_serve(args, emit=True):
     return line
 
 
+def run_profile_case(args):
+    """The ncu capture workload: three Algorithm 2 projections (BF16 form,
+    split-BF16 SYRK) of the decay recipe at side args.n, each launching
+    pack_upper_bf16_kernel once, sym_pass_bf16_kernel four times,
+    sym_gemv_tiles_kernel 22 times and syrk_bf16x3_kernel once."""
+    import torch
+    import paper_2410_19208_gb300 as ps
+    import synth_inputs as si
+    n, k, p, q = args.n, args.k, args.p, args.q
+    Vr, lam = si.make_problem("decay", n)
+    A = si.form_A_torch(Vr, lam, "cuda")
+    ctx = ps.Context(0)
+    P = torch.empty(n, n, device="cuda")
+    W = ps.tall_empty(n, k + p)
+    opts = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3)
+    for _ in range(3):
+        ctx.alg2(A, k, p, q, SEED, P=P, W=W, opts=opts)
+    st = ctx.sync_status()
+    if st != 0:
+        raise SystemExit(f"device status {ps.STATUS.get(st)}")
+    print(json.dumps({"workload": "profile", "n": n, "status": "ok"}))
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.workload == "profile":
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
