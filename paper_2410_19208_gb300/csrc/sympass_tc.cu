@@ -56,8 +56,8 @@ constexpr uint32_t A_BYTES = BM * BN * 2;        // BF16 tile of A' (32 KB)
 constexpr uint32_t STG_BYTES = 32 * 32 * 4;      // epilogue staging box per warp
 constexpr int NEPI = 8;                          // epilogue warps (two per TMEM lane quarter)
 constexpr int NT = 32 * (4 + NEPI);
-// TMEM columns: D1^T 256, D2^T 2 x 64, X_I^T (the A operand of P2, K = 256
-// BF16 values per lane) 128
+// TMEM columns: D1^T 256, D2^T 128 (a group of two tiles), X_I^T (the A
+// operand of P2, K = 256 BF16 values per lane) 128
 constexpr uint32_t D1_COL = 0, D2_COL = BM, XI_COL = BM + 2 * BN;
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(XI_COL + BM / 2 == TMEM_COLS, "tensor memory");
@@ -91,9 +91,9 @@ struct Lay {
 };
 
 struct Bars {
-    uint64_t fullA[4], emptyA[4];
+    uint64_t fullG[2], emptyG[2];   // the A' tiles of a group (ring slots 2 gs, 2 gs + 1)
     uint64_t fullX[4], emptyX[4];
-    uint64_t d2full[2], d2empty[2];
+    uint64_t d2full, d2empty;
     uint64_t d1full, d1empty;
     uint64_t xidone;     // the issuer's MMAs so far (X_I in TMEM may be overwritten) are complete
     uint64_t mmadone;
@@ -186,6 +186,37 @@ struct XSeq {
     __device__ __forceinline__ uint32_t phase(int nx) const { return (uint32_t)((item / nx) & 1); }
 };
 
+// Tiles are taken in groups of one or two consecutive tiles of one block row
+// (two when the range's next tile is in the same row): the group's
+// transposed product is one MMA chain of N = 64 per tile.  Group g holds the
+// A' ring slots 2 (g % 2) and 2 (g % 2) + 1, so the two tiles of a pair sit
+// one slot (32 KB, the descriptor's leading byte offset) apart.  Every role
+// walks the same groups.
+struct Groups {
+    int64_t t, t1;
+    int I, J, nbc, curI = -1;
+    int sz = 1;
+    bool first = false, last = false;
+    __device__ Groups(int64_t a, int64_t b, int I0, int J0, int nbc_) : t(a), t1(b), I(I0), J(J0), nbc(nbc_) {}
+    __device__ bool more() const { return t < t1; }
+    __device__ void fill()
+    {
+        sz = (t + 1 < t1 && J + 1 < nbc) ? 2 : 1;
+        first = (I != curI);
+        last = (J + sz == nbc) || (t + sz == t1);
+    }
+    __device__ void next()
+    {
+        curI = I;
+        t += sz;
+        J += sz;
+        if (J == nbc) {
+            ++I;
+            J = R * I;
+        }
+    }
+};
+
 template <int MR>
 __global__ void __launch_bounds__(NT, 1)
 sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CUtensorMap tmX,
@@ -212,18 +243,16 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
         }
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NA; ++s) {
-            mbar_init(&B.fullA[s], 1);
-            mbar_init(&B.emptyA[s], 1);   // the MMA issuer
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&B.fullG[s], 1);
+            mbar_init(&B.emptyG[s], 1);   // the MMA issuer
         }
         for (int s = 0; s < NX; ++s) {
             mbar_init(&B.fullX[s], 1);
             mbar_init(&B.emptyX[s], 1);   // the one consumer of the item
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&B.d2full[b], 1);
-            mbar_init(&B.d2empty[b], NEPI);
-        }
+        mbar_init(&B.d2full, 1);
+        mbar_init(&B.d2empty, NEPI);
         mbar_init(&B.d1full, 1);
         mbar_init(&B.d1empty, NEPI);
         mbar_init(&B.xidone, 1);
@@ -250,8 +279,8 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     if (warp == 0) {
         // ------------------------------------------------------------ TMA
         if (lane == 0) {
-            int I = I0, J = J0, curI = -1;
-            int64_t na = 0;         // A' tiles whose copy was issued (ring position)
+            Groups gr(t0, t1, I0, J0, P.nbc);
+            int64_t g = 0;          // groups whose copies were issued
             XSeq xs;                // X boxes whose copy was issued
             bool ok = true;
             auto push_x = [&](int x) -> bool {      // one 64-row box of X^T at row x
@@ -262,53 +291,55 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                 ++xs.item;
                 return true;
             };
-            for (int64_t t = t0; t < t1 && ok; ++t, tile_next(I, J, P.nbc)) {
-                if (I != curI) {
-                    for (int kk = 0; kk < BM / 64 && ok; ++kk) ok = push_x(BM * I + 64 * kk);
-                    if (!ok) break;
-                    curI = I;
-                }
-                const int s = (int)(na % NA);
-                const uint32_t us = (uint32_t)(na / NA);
-                if (!mbar_wait(&B.emptyA[s], (us & 1) ^ 1, abort, WL)) { ok = false; break; }
-                mbar_arrive_expect_tx(&B.fullA[s], A_BYTES);
-                bulk_load(sm + s * A_BYTES, Ab + t * PSD_TILE_ELEMS, A_BYTES, &B.fullA[s]);
-                ++na;
-                ok = push_x(BN * J);
+            for (; gr.more() && ok; gr.next()) {
+                gr.fill();
+                if (gr.first)
+                    for (int kk = 0; kk < BM / 64 && ok; ++kk) ok = push_x(BM * gr.I + 64 * kk);
+                if (!ok) break;
+                const int gs = (int)(g & 1);
+                if (!mbar_wait(&B.emptyG[gs], (uint32_t)((g >> 1) & 1) ^ 1, abort, WL)) { ok = false; break; }
+                mbar_arrive_expect_tx(&B.fullG[gs], A_BYTES * (uint32_t)gr.sz);
+                for (int u = 0; u < gr.sz; ++u)
+                    bulk_load(sm + (2 * gs + u) * A_BYTES, Ab + (gr.t + u) * PSD_TILE_ELEMS, A_BYTES, &B.fullG[gs]);
+                ++g;
+                for (int u = 0; u < gr.sz && ok; ++u) ok = push_x(BN * (gr.J + u));
             }
             if (!ok) fail(B, P.d_status);
             // wait (bounded, also after giving up) for the copies in flight to land
-            for (int64_t k = (na > NA ? na - NA : 0); k < na; ++k)
-                mbar_wait_drain(&B.fullA[k % NA], (uint32_t)((k / NA) & 1), WAIT_LIMIT);
+            for (int64_t k = (g > 2 ? g - 2 : 0); k < g; ++k)
+                mbar_wait_drain(&B.fullG[k & 1], (uint32_t)((k >> 1) & 1), WAIT_LIMIT);
             for (int64_t k = (xs.item > NX ? xs.item - NX : 0); k < xs.item; ++k)
                 mbar_wait_drain(&B.fullX[k % NX], (uint32_t)((k / NX) & 1), WAIT_LIMIT);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA
-        // One issuing thread (it also owns TMEM): per tile the sixteen short
-        // transposed-product MMAs (P2, into the double-buffered D2), then
-        // the four long row-product MMAs (P1, into D1); at a block-row start
-        // the four chunks of X_I^T are first copied into TMEM, after the
-        // thread's own earlier MMAs (readers of the previous X_I) are
-        // complete.  Every tcgen05 operation is issued by this thread, in
-        // program order.  Descriptors: one per operand base, advanced by
-        // constants (the start-address field holds addr >> 4 in its low 14
-        // bits, and every shared-memory address here is below 2^18, so
-        // adding never carries).
+        // One issuing thread (it also owns TMEM), per group of one or two
+        // tiles: the transposed product (P2, sixteen MMAs of N = 64 per tile
+        // of the group, into D2), then the row products of its tiles (P1,
+        // four N = 256 MMAs each, into D1); at a block-row start the four
+        // chunks of X_I^T are first copied into TMEM, after the thread's own
+        // earlier MMAs (readers of the previous X_I) are complete.  Every
+        // tcgen05 operation is issued by this thread, in program order.
+        // Descriptors: one per operand base, advanced by constants (the
+        // start-address field holds addr >> 4 in its low 14 bits, and every
+        // shared-memory address here is below 2^18, so adding never carries).
         if (lane == 0) {
             constexpr uint32_t id1 = idesc_bf16(128, BM, 0, 0);
-            constexpr uint32_t id2 = idesc_bf16(128, BN, 0, 1);
+            constexpr uint32_t id2a = idesc_bf16(128, BN, 0, 1);        // one tile
+            constexpr uint32_t id2b = idesc_bf16(128, 2 * BN, 0, 1);    // a pair
             const uint64_t dA0 = sdesc_sw128(smem_u32(sm), 16, 1024);              // A' tile, K-major (P1)
-            const uint64_t dAmn0 = sdesc_sw128(smem_u32(sm), 16384, 1024);         // A' tile, MN-major (P2)
+            // A' tiles, MN-major (P2): the pair's second tile is the next
+            // 64-column atom, one slot (A_BYTES) further
+            const uint64_t dAmn0 = sdesc_sw128(smem_u32(sm), A_BYTES, 1024);
             const uint64_t dX0 = sdesc_sw128(smem_u32(sm + L::OFF_X), 16, 1024);   // X^T slot, K-major
-            int I = I0, J = J0, curI = -1, seg = 0;
-            int64_t it = 0;
+            Groups gr(t0, t1, I0, J0, P.nbc);
+            int64_t g = 0;
+            int seg = 0;
             XSeq xs;
             bool ok = true;
-            for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
-                const bool first = (I != curI);
-                const bool last = (J == P.nbc - 1) || (t + 1 == t1);
-                if (first) {
+            for (; gr.more(); gr.next(), ++g) {
+                gr.fill();
+                if (gr.first) {
                     if (seg > 0) {
                         // the previous row's MMAs read X_I in TMEM: let them complete
                         mma_commit(&B.xidone);
@@ -327,42 +358,41 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                         ++xs.item;
                     }
                     if (!ok) break;
-                    curI = I;
                 }
-                const int s = (int)(it % NA);
-                const uint32_t us = (uint32_t)(it / NA);
-                const int b = (int)(it & 1);
-                const uint32_t ub = (uint32_t)(it >> 1);
-                const uint64_t aoff = (uint64_t)((s * A_BYTES) >> 4);
-                if (!mbar_wait(&B.fullA[s], us & 1, abort, WL)) { ok = false; break; }
-                // P2: D2^T = X_I^T A_IJ   (K = 256 tile rows; X_I^T from TMEM)
-                if (!mbar_wait(&B.d2empty[b], (ub & 1) ^ 1, abort, WL)) { ok = false; break; }
+                const int gs = (int)(g & 1);
+                const uint64_t goff = (uint64_t)((2 * gs * A_BYTES) >> 4);
+                if (!mbar_wait(&B.fullG[gs], (uint32_t)((g >> 1) & 1), abort, WL)) { ok = false; break; }
+                // P2: D2^T = X_I^T [A_IJ | A_I,J+1]   (K = 256 tile rows; X_I^T from TMEM)
+                if (!mbar_wait(&B.d2empty, (uint32_t)(g & 1) ^ 1, abort, WL)) { ok = false; break; }
                 tc_fence_after();
                 {
-                    const uint64_t bd = dAmn0 + aoff;
-                    const uint32_t dcol = tmem + D2_COL + BN * b;
+                    const uint64_t bd = dAmn0 + goff;
+                    const uint32_t id2 = gr.sz == 2 ? id2b : id2a;
 #pragma unroll
                     for (int kk = 0; kk < BM / 16; ++kk)
-                        mma_bf16_ts(dcol, tmem + XI_COL + 8 * kk, bd + (uint64_t)((kk * 2048) >> 4), id2,
+                        mma_bf16_ts(tmem + D2_COL, tmem + XI_COL + 8 * kk, bd + (uint64_t)((kk * 2048) >> 4), id2,
                                     kk > 0 ? 1u : 0u);
-                    mma_commit(&B.d2full[b]);
+                    mma_commit(&B.d2full);
                 }
-                // P1: D1^T += X_J^T A_IJ^T   (K = 64 tile columns); D1 drained
-                // by the epilogue before a block row's first tile
-                if (first && !mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WL)) { ok = false; break; }
-                {
+                // P1: D1^T += X_J^T A_IJ^T per tile (K = 64 tile columns); D1
+                // drained by the epilogue before a block row's first group
+                if (gr.first && !mbar_wait(&B.d1empty, (seg & 1) ^ 1, abort, WL)) { ok = false; break; }
+                for (int u = 0; u < gr.sz; ++u) {
                     const int sl = xs.slot(NX);
                     if (!mbar_wait(&B.fullX[sl], xs.phase(NX), abort, WL)) { ok = false; break; }
                     tc_fence_after();
-                    const uint64_t ad = dX0 + (uint64_t)((sl * L::XS) >> 4), bd = dA0 + aoff;
+                    const uint64_t ad = dX0 + (uint64_t)((sl * L::XS) >> 4);
+                    const uint64_t bd = dA0 + goff + (uint64_t)((u * A_BYTES) >> 4);
 #pragma unroll
                     for (int kk = 0; kk < BN / 16; ++kk)
-                        mma_bf16_ss(tmem + D1_COL, ad + 2 * kk, bd + 2 * kk, id1, (!first || kk > 0) ? 1u : 0u);
+                        mma_bf16_ss(tmem + D1_COL, ad + 2 * kk, bd + 2 * kk, id1,
+                                    (!gr.first || u > 0 || kk > 0) ? 1u : 0u);
                     mma_commit(&B.emptyX[sl]);
                     ++xs.item;
                 }
-                mma_commit(&B.emptyA[s]);
-                if (last) {
+                if (!ok) break;
+                mma_commit(&B.emptyG[gs]);
+                if (gr.last) {
                     mma_commit(&B.d1full);
                     ++seg;
                 }
@@ -376,44 +406,48 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
     } else if (warp >= 4) {
         // ------------------------------------------------------- epilogue
         // two warps per TMEM lane quarter q (a warp reads only its own
-        // quarter): half h drains columns 32 h .. 32 h + 31 of D2 after every
-        // tile and the 32-column chunks h, h + 2, ... of D1 after a block row
+        // quarter): half h drains its half of D2 after every group (32
+        // columns of a single tile, 64 of a pair) and the 32-column chunks
+        // h, h + 2, ... of D1 after a block row
         const int q = warp & 3;
         const int h = (warp - 4) >> 2;
         uint8_t *stg = sm + L::OFF_STG + (warp - 4) * STG_BYTES;
         const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-        int I = I0, J = J0, seg = 0;
-        int64_t it = 0;
-        for (int64_t t = t0; t < t1; ++t, ++it, tile_next(I, J, P.nbc)) {
-            const bool last = (J == P.nbc - 1) || (t + 1 == t1);
-            const int b = (int)(it & 1);
-            const uint32_t ub = (uint32_t)(it >> 1);
+        Groups gr(t0, t1, I0, J0, P.nbc);
+        int64_t g = 0;
+        int seg = 0;
+        for (; gr.more(); gr.next(), ++g) {
+            gr.fill();
             {
                 // lane 0 waits (bounded); the warp leaves together
                 int ok = 1;
-                if (lane == 0) ok = mbar_wait(&B.d2full[b], ub & 1, abort, WL) ? 1 : 0;
+                if (lane == 0) ok = mbar_wait(&B.d2full, (uint32_t)(g & 1), abort, WL) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { if (lane == 0) fail(B, P.d_status); break; }
             }
             tc_fence_after();
-            float v[32];
-            tmem_ld32(tmem + lane_base + D2_COL + BN * b + 32 * h, v);
+            const int w = 32 * gr.sz;                   // D2 columns of this half
+            float v0[32], v1[32];
+            tmem_ld32(tmem + lane_base + D2_COL + w * h, v0);
+            if (gr.sz == 2) tmem_ld32(tmem + lane_base + D2_COL + w * h + 32, v1);
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&B.d2empty[b]);
-            flush32(P, &tmY, stg, q, lane, (int64_t)BN * J + 32 * h, v);
-            if (last) {
+            if (lane == 0) mbar_arrive(&B.d2empty);
+            const int64_t r0 = (int64_t)BN * gr.J + w * h;
+            flush32(P, &tmY, stg, q, lane, r0, v0);
+            if (gr.sz == 2) flush32(P, &tmY, stg, q, lane, r0 + 32, v1);
+            if (gr.last) {
                 int ok = 1;
                 if (lane == 0) ok = mbar_wait(&B.d1full, seg & 1, abort, WL) ? 1 : 0;
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { if (lane == 0) fail(B, P.d_status); break; }
                 tc_fence_after();
-                const int64_t r0 = (int64_t)BM * I;
+                const int64_t rr = (int64_t)BM * gr.I;
 #pragma unroll 1
                 for (int ch = h; ch < BM / 32; ch += 2) {
-                    float w[32];
-                    tmem_ld32(tmem + lane_base + D1_COL + 32 * ch, w);
-                    flush32(P, &tmY, stg, q, lane, r0 + 32 * ch, w);
+                    float wv[32];
+                    tmem_ld32(tmem + lane_base + D1_COL + 32 * ch, wv);
+                    flush32(P, &tmY, stg, q, lane, rr + 32 * ch, wv);
                 }
                 tc_fence_before();
                 __syncwarp();
