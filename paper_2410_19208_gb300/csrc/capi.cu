@@ -149,6 +149,7 @@ size_t carve_workspace(psd_workspace &lay, char *base, int64_t nn, int lp)
     lay.dead = reinterpret_cast<int *>(take(sizeof(int) * lp));
     lay.pv0 = reinterpret_cast<float *>(take(sizeof(float) * ld));
     lay.pv1 = reinterpret_cast<float *>(take(sizeof(float) * ld));
+    lay.pv2 = reinterpret_cast<float *>(take(sizeof(float) * ld));
     lay.scal = reinterpret_cast<double *>(take(sizeof(double) * 16));
     lay.ints = reinterpret_cast<int *>(take(sizeof(int) * 16));
     lay.picks = reinterpret_cast<int *>(take(sizeof(int) * PSD_MAX_M));
@@ -393,13 +394,13 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
                                                   sc, sc + SC_SIGMA2, ctx->det_part), 3 * opts.N + 5);
             } else if (bf16) {
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
-                                                   ws.pv0, ws.pv1, sc, sc + SC_SIGMA1,
+                                                   ws.pv0, ws.pv1, ws.pv2, sc, sc + SC_SIGMA1,
                                                    ctx->d_status, ctx->wait_limit),
-                       2 * opts.N + 4);
+                       opts.N + 4);
                 PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 4u,
-                                                   sc + SC_SIGMA1, ws.pv0, ws.pv1, sc,
+                                                   sc + SC_SIGMA1, ws.pv0, ws.pv1, ws.pv2, sc,
                                                    sc + SC_SIGMA2, ctx->d_status, ctx->wait_limit),
-                       2 * opts.N + 4);
+                       opts.N + 4);
             } else {
                 PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
                                               sc, sc + SC_SIGMA1), 2 * opts.N + 4);

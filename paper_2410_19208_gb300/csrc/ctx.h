@@ -76,7 +76,7 @@ struct psd_workspace {
     float *Rinv = nullptr, *V = nullptr, *M = nullptr, *eigscr = nullptr;
     int *dead = nullptr;
     // power iteration: two n-vectors (ld floats) and scalars
-    float *pv0 = nullptr, *pv1 = nullptr;
+    float *pv0 = nullptr, *pv1 = nullptr, *pv2 = nullptr;   // power-iteration vectors (a rotation of three)
     double *scal = nullptr;     // 16 doubles
     int *ints = nullptr;         // 16 ints (ranks, info)
     int *picks = nullptr;        // PSD_MAX_M ints (SRHT column picks)
@@ -282,11 +282,15 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
                                    const double *d_shift_neg, float *v0, float *v1,
                                    double *scal, double *d_sigma);
 
-// The same on the BF16 image (launch_pack_bf16); v0, v1 16-byte aligned.
+// The same on the BF16 image (launch_pack_bf16), N + 4 launches: each
+// product normalises its own input and clears the next product's output,
+// the three vectors v0, v1, v2 (16-byte aligned) taking turns; the products
+// are chained by programmatic dependent launch.
 cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t n,
                                         int N, uint64_t seed, uint32_t stream_id,
-                                        const double *d_shift_neg, float *v0, float *v1, double *scal,
-                                        double *d_sigma, int *d_status, long long wait_limit = 0);
+                                        const double *d_shift_neg, float *v0, float *v1, float *v2,
+                                        double *scal, double *d_sigma, int *d_status,
+                                        long long wait_limit = 0);
 
 // The power iteration's start (scal[0] = 1, v1 = 0) and its norm step
 // (scal[0] = 1/||y||, scal[1] = ||y||, *d_sigma = ||y|| when asked; other = 0).

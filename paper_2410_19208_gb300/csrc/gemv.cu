@@ -159,6 +159,113 @@ constexpr uint32_t SMEM = STAGES * TILE_BYTES + 1024;
 constexpr long long WAIT_LIMIT = 4000000000LL;
 }
 
+struct dfl {
+    float hi, lo;
+};
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = err + a.lo + b.lo;
+    const float h = s + lo;
+    return {h, lo - (h - s)};
+}
+
+// ||v|| and 1/||v|| of a sum of squares t = acc (double-float): the FP32
+// estimate of 1/sqrt(t) with one FP32 Newton step, then one double-float
+// Newton step for each, r = x + (t - x^2) y / 2 with x = t y, and
+// 1/r = y + y (1 - y r); 0 and 0 when t = 0.
+__device__ __forceinline__ void dfl_norm_inv(dfl acc, double &nrm, double &inv)
+{
+    nrm = 0.0;
+    inv = 0.0;
+    if (acc.hi > 0.0f) {
+        float q = rsqrtf(acc.hi);
+        q = q * fmaf(-0.5f * acc.hi, q * q, 1.5f);
+        const float x = acc.hi * q;
+        const float x2 = x * x;
+        const dfl d = dfl_add(acc, {-x2, -fmaf(x, x, -x2)});          // t - x^2
+        const float rc = d.hi * (0.5f * q);
+        const float rh = x + rc, rl = rc - (rh - x);                  // r = rh + rl
+        const float yr = q * rh, yre = fmaf(q, rh, -yr);
+        const float res = ((1.0f - yr) - yre) - q * rl;               // 1 - q r
+        nrm = (double)rh + (double)rl;
+        inv = (double)q + (double)(q * res);
+    }
+}
+
+// Per-thread part of sum v_i^2 over i = first, first + stride, ... < n, as
+// an unevaluated double-float sum (the square split exactly by FMA, Knuth's
+// two-sum per term).
+__device__ __forceinline__ dfl dfl_sumsq(const float *__restrict__ v, int64_t n, int64_t first, int64_t stride,
+                                         float *__restrict__ clear)
+{
+    float hi = 0.0f, lo = 0.0f;
+#pragma unroll 4
+    for (int64_t i = first; i < n; i += stride) {
+        const float a = v[i];
+        const float p = a * a, e = fmaf(a, a, -p);          // a^2 = p + e exactly
+        const float s = hi + p;
+        const float bb = s - hi;
+        lo += ((hi - (s - bb)) + (p - bb)) + e;
+        hi = s;
+        if (clear) clear[i] = 0.0f;
+    }
+    return {hi + lo, lo - ((hi + lo) - hi)};
+}
+
+// The same over all of v by nthr threads (thread tid), four float4 loads in
+// flight per thread: v 16-byte aligned.  The order of the terms depends only
+// on (n, tid, nthr), so every block that calls it gets the same sum.
+__device__ __forceinline__ void dfl_sq_acc(float a, float &hi, float &lo)
+{
+    const float p = a * a, e = fmaf(a, a, -p);
+    const float s = hi + p;
+    const float bb = s - hi;
+    lo += ((hi - (s - bb)) + (p - bb)) + e;
+    hi = s;
+}
+__device__ __forceinline__ dfl dfl_sumsq_vec(const float *__restrict__ v, int64_t n, int tid, int nthr)
+{
+    float hi = 0.0f, lo = 0.0f;
+    const int64_t n4 = n >> 2;
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);
+    int64_t j = tid;
+    for (; j + 3 * (int64_t)nthr < n4; j += 4 * (int64_t)nthr) {
+        float4 a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = v4[j + u * (int64_t)nthr];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            dfl_sq_acc(a[u].x, hi, lo); dfl_sq_acc(a[u].y, hi, lo);
+            dfl_sq_acc(a[u].z, hi, lo); dfl_sq_acc(a[u].w, hi, lo);
+        }
+    }
+    for (; j < n4; j += nthr) {
+        const float4 a = v4[j];
+        dfl_sq_acc(a.x, hi, lo); dfl_sq_acc(a.y, hi, lo); dfl_sq_acc(a.z, hi, lo); dfl_sq_acc(a.w, hi, lo);
+    }
+    for (int64_t i = 4 * n4 + tid; i < n; i += nthr) dfl_sq_acc(v[i], hi, lo);
+    return {hi + lo, lo - ((hi + lo) - hi)};
+}
+
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start before the previous kernel on
+// its stream has finished; griddep_wait() returns once that kernel has
+// completed and its writes are visible, and griddep_launch_dependents() lets
+// the next such kernel start.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+__device__ __forceinline__ dfl dfl_warp_sum(dfl acc)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc = dfl_add(acc, {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+    return acc;
+}
+
 __device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
 {
     a[0] = __uint_as_float(u.x << 16); a[1] = __uint_as_float(u.x & 0xFFFF0000u);
@@ -167,10 +274,17 @@ __device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
     a[6] = __uint_as_float(u.w << 16); a[7] = __uint_as_float(u.w & 0xFFFF0000u);
 }
 
+// Launched with programmatic stream serialization: the producer streams the
+// image (written before the previous kernel started) at once; the compute
+// warps wait for the previous kernel before they touch x, y, scal, the
+// shift or `clear`.  self_norm: x is scaled by 1/||x||, computed by every
+// CTA in the same order (so every CTA uses the same scale); else by
+// scal[0].  clear (may be NULL): zeroed, each CTA its slice (the next
+// product's output, this product's input no longer being read).
 __global__ void __launch_bounds__(gt::NTG, gt::CTAS_PER_SM)
 sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64_t tiles,
-                      const float *__restrict__ x, float *__restrict__ y, const double *scal,
-                      const double *d_shift_neg, int *d_status, long long wait_limit)
+                      const float *__restrict__ x, float *__restrict__ y, const double *scal, int self_norm,
+                      float *__restrict__ clear, const double *d_shift_neg, int *d_status, long long wait_limit)
 {
     const long long WL = wait_limit > 0 ? wait_limit : gt::WAIT_LIMIT;
     using namespace tc;
@@ -179,6 +293,8 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
     __shared__ float colred[2][8][PSD_TILE_N];
     __shared__ int s_abort;       // any role gave up: stop waiting
     __shared__ int s_cabort;      // compute warps: written before, read after their barrier
+    __shared__ dfl s_red[8];
+    __shared__ float s_sc;
     const int nbc = nbr * PSD_TILE_R;
     const int64_t t0 = tiles * blockIdx.x / gridDim.x;
     const int64_t t1 = tiles * (blockIdx.x + 1) / gridDim.x;
@@ -195,8 +311,8 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
     __syncthreads();
     volatile int *abort = &s_abort;
     volatile int *cabort = &s_cabort;
-    const float sc = (float)scal[0];
-    const float shift = d_shift_neg ? (float)(-(*d_shift_neg)) : 0.0f;
+    // the next product's loads do not depend on this one
+    griddep_launch_dependents();
 
     if (warp == 8) {
         // ---- producer: one bulk copy per tile
@@ -217,7 +333,32 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
             for (int64_t k = (n_it > gt::STAGES ? n_it - gt::STAGES : 0); k < n_it; ++k)
                 mbar_wait_drain(&full[k % gt::STAGES], (uint32_t)((k / gt::STAGES) & 1), gt::WAIT_LIMIT);
         }
-    } else if (t0 < t1) {
+    } else {
+        griddep_wait();
+        if (clear) {
+            const int64_t c0 = n * blockIdx.x / gridDim.x, c1 = n * (blockIdx.x + 1) / gridDim.x;
+            for (int64_t i = c0 + threadIdx.x; i < c1; i += gt::NCOMP) clear[i] = 0.0f;
+        }
+        if (t0 >= t1) return;      // no tile: the producer issues no copy either
+        float sc;
+        if (self_norm) {
+            dfl acc = dfl_warp_sum(dfl_sumsq_vec(x, n, threadIdx.x, gt::NCOMP));
+            if (lane == 0) s_red[warp] = acc;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (warp == 0) {
+                acc = dfl_warp_sum(lane < 8 ? s_red[lane] : dfl{0.0f, 0.0f});
+                if (lane == 0) {
+                    double nrm, inv;
+                    dfl_norm_inv(acc, nrm, inv);
+                    s_sc = (float)inv;
+                }
+            }
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            sc = s_sc;
+        } else {
+            sc = (float)scal[0];
+        }
+        const float shift = d_shift_neg ? (float)(-(*d_shift_neg)) : 0.0f;
         // ---- compute: thread (g, k): rows 8g..8g+7, columns 8k..8k+7 of each tile
         const int g = threadIdx.x >> 3, k = threadIdx.x & 7;
         int I = 0, J = 0;
@@ -355,64 +496,19 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
 // handful of operations per SM and clock on this GPU, is kept out of the
 // sum; this replaced an eight-block FP64 kernel with an atomic ticket
 // (9.8 us -> a few us per product).
-struct dfl {
-    float hi, lo;
-};
-__device__ __forceinline__ dfl dfl_add(dfl a, dfl b)
-{
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float err = (a.hi - (s - bb)) + (b.hi - bb);
-    const float lo = err + a.lo + b.lo;
-    const float h = s + lo;
-    return {h, lo - (h - s)};
-}
-
 __global__ void __launch_bounds__(1024)
 pi_norm_kernel(const float *__restrict__ y, float *__restrict__ other, int64_t n, double *scal,
                double *d_sigma)
 {
     __shared__ dfl red[32];
-    float hi = 0.0f, lo = 0.0f;
-#pragma unroll 4
-    for (int64_t i = threadIdx.x; i < n; i += 1024) {
-        const float v = y[i];
-        const float p = v * v, e = fmaf(v, v, -p);          // v^2 = p + e exactly
-        const float s = hi + p;
-        const float bb = s - hi;
-        lo += ((hi - (s - bb)) + (p - bb)) + e;
-        hi = s;
-        other[i] = 0.0f;
-    }
-    dfl acc = {hi + lo, lo - ((hi + lo) - hi)};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        acc = dfl_add(acc, {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+    dfl acc = dfl_warp_sum(dfl_sumsq(y, n, threadIdx.x, 1024, other));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
-        acc = red[threadIdx.x];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            acc = dfl_add(acc, {__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)});
+        acc = dfl_warp_sum(red[threadIdx.x]);
         if (threadIdx.x == 0) {
-            double nrm = 0.0, inv = 0.0;
-            if (acc.hi > 0.0f) {
-                // y ~ 1/sqrt(t) (estimate + one FP32 Newton step), then one
-                // double-float Newton step each: r = x + (t - x^2) y / 2 with
-                // x = t y, and 1/r = y + y (1 - y r)
-                float q = rsqrtf(acc.hi);
-                q = q * fmaf(-0.5f * acc.hi, q * q, 1.5f);
-                const float x = acc.hi * q;
-                const float x2 = x * x;
-                const dfl d = dfl_add(acc, {-x2, -fmaf(x, x, -x2)});          // t - x^2
-                const float rc = d.hi * (0.5f * q);
-                const float rh = x + rc, rl = rc - (rh - x);                  // r = rh + rl
-                const float yr = q * rh, yre = fmaf(q, rh, -yr);
-                const float res = ((1.0f - yr) - yre) - q * rl;               // 1 - q r
-                nrm = (double)rh + (double)rl;
-                inv = (double)q + (double)(q * res);
-            }
+            double nrm, inv;
+            dfl_norm_inv(acc, nrm, inv);
             scal[1] = nrm;
             scal[0] = inv;
             if (d_sigma) *d_sigma = nrm;
@@ -521,11 +617,11 @@ cudaError_t launch_power_iteration(cudaStream_t s, const float *A, int64_t n, in
 
 cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint16_t *Ab, int64_t n,
                                         int N, uint64_t seed, uint32_t stream_id,
-                                        const double *d_shift_neg, float *v0, float *v1, double *scal,
-                                        double *d_sigma, int *d_status, long long wait_limit)
+                                        const double *d_shift_neg, float *v0, float *v1, float *v2,
+                                        double *scal, double *d_sigma, int *d_status, long long wait_limit)
 {
     if ((reinterpret_cast<uintptr_t>(Ab) & 15) != 0 || (reinterpret_cast<uintptr_t>(v0) & 15) != 0 ||
-        (reinterpret_cast<uintptr_t>(v1) & 15) != 0)
+        (reinterpret_cast<uintptr_t>(v1) & 15) != 0 || (reinterpret_cast<uintptr_t>(v2) & 15) != 0)
         return cudaErrorInvalidValue;
     cudaError_t e = launch_gaussian(s, seed, stream_id, n, 1, 1, n, v0, n);
     if (e != cudaSuccess) return e;
@@ -539,18 +635,30 @@ cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint
     const int64_t tiles = psd_tile_count(n);
     int grid = (sm_count > 0 ? sm_count : 148) * gt::CTAS_PER_SM;
     if ((int64_t)grid > tiles) grid = (int)tiles;
-    float *in = v0, *out = v1;
+    // product it reads v[it % 3] (v0: the Gaussian start, scaled by
+    // scal[0] = 1; later ones by their own norm), accumulates into
+    // v[(it + 1) % 3] (zeroed by pi_init or by the product before) and
+    // clears v[(it + 2) % 3], its predecessor's input
+    float *v[3] = {v0, v1, v2};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(gt::NTG);
+    cfg.dynamicSmemBytes = gt::SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     for (int it = 0; it <= N; ++it) {
-        sym_gemv_tiles_kernel<<<grid, gt::NTG, gt::SMEM, s>>>(Ab, n, nbr, tiles, in, out, scal, d_shift_neg,
-                                                              d_status, wait_limit);
-        e = cudaGetLastError();
+        e = cudaLaunchKernelEx(&cfg, sym_gemv_tiles_kernel, Ab, n, nbr, tiles, (const float *)v[it % 3],
+                               v[(it + 1) % 3], (const double *)scal, it > 0 ? 1 : 0, v[(it + 2) % 3],
+                               d_shift_neg, d_status, wait_limit);
         if (e != cudaSuccess) return e;
-        pi_norm_kernel<<<1, 1024, 0, s>>>(out, in, n, scal, it == N ? d_sigma : nullptr);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        float *t = in; in = out; out = t;
     }
-    return cudaSuccess;
+    // ||y|| of the last product (sigma)
+    pi_norm_kernel<<<1, 1024, 0, s>>>(v[(N + 1) % 3], v[(N + 2) % 3], n, scal, d_sigma);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pi_init(cudaStream_t s, double *scal, float *v1, int64_t n)

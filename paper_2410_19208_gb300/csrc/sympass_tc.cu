@@ -126,15 +126,6 @@ __device__ __forceinline__ void tile_of(int64_t t, int nbc, int nbr, int &I, int
     J = R * lo + (int)(t - psd_tile_row_start(lo, nbc));
 }
 
-// the next tile in row-major order over the block upper triangle
-__device__ __forceinline__ void tile_next(int &I, int &J, int nbc)
-{
-    if (++J == nbc) {
-        ++I;
-        J = R * I;
-    }
-}
-
 __device__ __forceinline__ void fail(Bars &B, int *st)
 {
     B.abort = 1;
@@ -223,7 +214,7 @@ sym_pass_bf16_kernel(const uint16_t *__restrict__ Ab, const __grid_constant__ CU
                      const __grid_constant__ CUtensorMap tmY, const __grid_constant__ Params P)
 {
     using L = Lay<MR>;
-    constexpr int NA = L::NA, NX = L::NX;
+    constexpr int NX = L::NX;
     extern __shared__ __align__(1024) uint8_t sm[];
     Bars &B = *reinterpret_cast<Bars *>(sm + L::OFF_BAR);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
