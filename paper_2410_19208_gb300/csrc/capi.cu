@@ -326,12 +326,14 @@ int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, flo
     cudaStream_t s = ctx->stream;
     const double tau = 1e-10;
     stage_scope st(ctx, PSDPROJ_STAGE_ORTH);
-    PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1), 2);
-    PSD_KL(launch_cholesky(s, ws.G, m, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status, 1,
+    // m <= 128: the Gram also as double-float pairs, in the (then unused) large-m scratch
+    float *gdf = m <= 128 ? reinterpret_cast<float *>(ws.cholscr) : nullptr;
+    PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1, gdf), 2);
+    PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status, 1,
                            ws.cholscr), 1);
     PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, ws.T, ws.ld), 1);
-    PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1), 2);
-    PSD_KL(launch_cholesky(s, ws.G, m, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
+    PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1, gdf), 2);
+    PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
                            ws.cholscr), 1);
     PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq, side), 1);
     return PSDPROJ_OK;

@@ -65,6 +65,7 @@ template <typename T> struct num;
 
 template <> struct num<float> {
     __device__ static float from(double v) { return (float)v; }
+    __device__ static float from2(float2 v) { return v.x; }
     __device__ static float hi(float v) { return v; }
     __device__ static float zero() { return 0.0f; }
     __device__ static float mul(float a, float b) { return a * b; }
@@ -85,6 +86,7 @@ template <> struct num<float> {
 
 template <> struct num<double> {
     __device__ static double from(double v) { return v; }
+    __device__ static double from2(float2 v) { return (double)v.x + (double)v.y; }
     __device__ static float hi(double v) { return (float)v; }
     __device__ static double zero() { return 0.0; }
     __device__ static double mul(double a, double b) { return a * b; }
@@ -103,6 +105,7 @@ template <> struct num<df> {
         const float h = (float)v;
         return {h, (float)(v - (double)h)};
     }
+    __device__ static df from2(float2 v) { return {v.x, v.y}; }
     __device__ static float hi(df v) { return v.hi; }
     __device__ static df zero() { return {0.0f, 0.0f}; }
     __device__ static df mul(df a, df b) { return df_mul(a, b); }
@@ -294,8 +297,8 @@ size_t blocked_smem(int m)
 
 template <typename T>
 __global__ void __launch_bounds__(NTB, 1)
-cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__ Rinv,
-                        int *__restrict__ dead, int *__restrict__ d_qrank, double tau, int *d_status)
+cholesky_blocked_kernel(const float2 *__restrict__ Gd, int m, float *__restrict__ Rinv,
+                        int *__restrict__ dead, int *__restrict__ d_qrank, float tau, int *d_status)
 {
     using N = num<T>;
     constexpr int NB = chol_nb<T>::value;
@@ -306,28 +309,30 @@ cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__
     float *Rf = reinterpret_cast<float *>(U + (size_t)m * ldu);        // FP32 R, m x ldu
     float *Tmp = Rf + (size_t)m * ldu;                                 // NB x m
     float *X = reinterpret_cast<float *>(smraw);                       // R^-1, m x ldu (U's bytes, once U is done)
-    __shared__ double s_gmax;
+    __shared__ float s_gmax;
     __shared__ int s_bad;
     __shared__ int s_dead[SMEM_M];
     __shared__ float s_rdinv[SMEM_M];
     __shared__ T s_inv[SMEM_M];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+    // G as double-float pairs, symmetric: row-major reads are coalesced,
+    // and no FP64 arithmetic is needed to split it
     for (int e = tid; e < m * m; e += NTB) {
         const int i = e / m, k = e - (e / m) * m;
-        if (k >= i) U[i * ldu + k] = N::from(G[(int64_t)k * m + i]);
+        if (k >= i) U[i * ldu + k] = N::from2(Gd[e]);
     }
     if (tid < 32) {
-        double g = 0.0;
+        float g = 0.0f;
         int bad = 0;
         for (int i = tid; i < m; i += 32) {
-            const double v = G[(int64_t)i * m + i];
+            const float v = Gd[(int64_t)i * m + i].x;
             if (!isfinite(v)) bad = 1;
             else if (v > g) g = v;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+            g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
             bad |= __shfl_xor_sync(0xffffffffu, bad, o);
         }
         if (tid == 0) {
@@ -337,8 +342,8 @@ cholesky_blocked_kernel(const double *__restrict__ G, int m, float *__restrict__
     }
     __syncthreads();
     if (s_bad && tid == 0) psd_set_status(d_status, PSDPROJ_ENOTFINITE);
-    const float thr = (float)(tau * s_gmax);
-    const bool any = s_gmax > 0.0;
+    const float thr = tau * s_gmax;
+    const bool any = s_gmax > 0.0f;
     const int nblk = (m + NB - 1) / NB;
 
     for (int b = 0; b < nblk; ++b) {
@@ -670,8 +675,8 @@ tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int 
 
 }  // namespace
 
-cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv, int *dead,
-                            int *d_qrank, double tau, int *d_status, int first_pass,
+cudaError_t launch_cholesky(cudaStream_t s, const double *G, const float *Gdf, int m, float *Rinv,
+                            int *dead, int *d_qrank, double tau, int *d_status, int first_pass,
                             double *gscratch)
 {
     // large m works in global memory: gscratch holds U (m*m), rowj (m) in
@@ -680,20 +685,22 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv,
     float *gRf = reinterpret_cast<float *>(gscratch + (size_t)m * m + m);
     cudaError_t e;
     if (sm_path) {
+        if (!Gdf) return cudaErrorInvalidValue;
+        const float2 *gd = reinterpret_cast<const float2 *>(Gdf);
         // the attribute is process-wide: always the largest size (m = SMEM_M),
         // so that threads launching for different m never undercut each other
         if (first_pass) {
             e = cudaFuncSetAttribute(cholesky_blocked_kernel<df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)blocked_smem<df>(SMEM_M));
             if (e != cudaSuccess) return e;
-            cholesky_blocked_kernel<df><<<1, NTB, blocked_smem<df>(m), s>>>(G, m, Rinv, dead, d_qrank, tau,
-                                                                            d_status);
+            cholesky_blocked_kernel<df><<<1, NTB, blocked_smem<df>(m), s>>>(gd, m, Rinv, dead, d_qrank,
+                                                                            (float)tau, d_status);
         } else {
             e = cudaFuncSetAttribute(cholesky_blocked_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)blocked_smem<float>(SMEM_M));
             if (e != cudaSuccess) return e;
-            cholesky_blocked_kernel<float><<<1, NTB, blocked_smem<float>(m), s>>>(G, m, Rinv, dead, d_qrank,
-                                                                                  tau, d_status);
+            cholesky_blocked_kernel<float><<<1, NTB, blocked_smem<float>(m), s>>>(gd, m, Rinv, dead, d_qrank,
+                                                                                  (float)tau, d_status);
         }
     } else if (first_pass) {
         cholesky_kernel<double, PSD_MAX_M / 32><<<1, NT, 0, s>>>(G, m, Rinv, dead, d_qrank, tau, gscratch,

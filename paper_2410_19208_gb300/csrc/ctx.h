@@ -235,16 +235,19 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int prepared = 0, long long wait_limit = 0);
 
 // Gram partials + FP64 reduction: G = X^T Z (sym = 1: X == Z, symmetric).
+// Gdf (may be NULL): the same sums as double-float pairs (hi, lo), m x m.
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
                         int64_t ldz, int64_t n, int m, float *gpart, double *G,
-                        int symmetrize);
+                        int symmetrize, float *Gdf = nullptr);
 
 // first_pass = 1: double-float factorization (FP64 when m > 128); 0: FP32.
 // Writes R^-1 (m x m column-major FP32), the dependent-column flags and
-// (d_qrank, may be NULL) the number of independent columns.  gscratch:
-// (m*m + m) doubles + m*m floats of device memory, used when m > 128.
-cudaError_t launch_cholesky(cudaStream_t s, const double *G, int m, float *Rinv, int *dead,
-                            int *d_qrank, double tau, int *d_status, int first_pass,
+// (d_qrank, may be NULL) the number of independent columns.  m <= 128
+// reads Gdf (the Gram as double-float pairs, symmetric, both halves), larger
+// m read G; gscratch: (m*m + m) doubles + m*m floats of device memory, used
+// when m > 128.
+cudaError_t launch_cholesky(cudaStream_t s, const double *G, const float *Gdf, int m, float *Rinv,
+                            int *dead, int *d_qrank, double tau, int *d_status, int first_pass,
                             double *gscratch);
 
 // Y (n x m) times a small m x c matrix B (column-major, ld = m) -> Z (n x c).

@@ -181,7 +181,7 @@ __device__ __forceinline__ fsum fsum_add(fsum a, fsum b)
 // symmetrise (S+S^T)/2.  Eight lanes share one entry of the partials
 // (coalesced over the entry index) and split the chunk sum in a fixed order.
 __global__ void gram_reduce_kernel(const float *__restrict__ gpart, int nchunk, int m, int mp,
-                                   int mode, double *__restrict__ G)
+                                   int mode, double *__restrict__ G, float2 *__restrict__ Gdf)
 {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int f = (int)(tid >> 3), sub = (int)(tid & 7);
@@ -199,10 +199,15 @@ __global__ void gram_reduce_kernel(const float *__restrict__ gpart, int nchunk, 
     if (!act || sub != 0 || ia >= m || ib >= m) return;
     if (mode == 0) {
         G[(int64_t)ib * m + ia] = s;
+        if (Gdf) Gdf[(int64_t)ib * m + ia] = make_float2(acc.hi, acc.lo);
     } else if (mode == 1) {
         if (ia <= ib) {
             G[(int64_t)ib * m + ia] = s;
             G[(int64_t)ia * m + ib] = s;
+            if (Gdf) {
+                Gdf[(int64_t)ib * m + ia] = make_float2(acc.hi, acc.lo);
+                Gdf[(int64_t)ia * m + ib] = make_float2(acc.hi, acc.lo);
+            }
         }
     } else {
         // (S + S^T)/2: entry (ia, ib) contributes half to both positions
@@ -216,8 +221,9 @@ __global__ void gram_reduce_kernel(const float *__restrict__ gpart, int nchunk, 
 // symmetrize: 0 = G = X^T Z as is; 1 = X == Z (upper computed, mirrored);
 // 2 = (X^T Z + Z^T X)/2.
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
-                        int64_t ldz, int64_t n, int m, float *gpart, double *G, int symmetrize)
+                        int64_t ldz, int64_t n, int m, float *gpart, double *G, int symmetrize, float *Gdf)
 {
+    if (Gdf && symmetrize == 2) return cudaErrorInvalidValue;
     const int mp = (int)psd_round_up(m, 8);
     const int nchunk = (int)((n + CH - 1) / CH);
     const size_t smem = sizeof(float) * 2 * RS * (size_t)mp;
@@ -247,6 +253,7 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
         if (e != cudaSuccess) return e;
     }
     const int64_t threads = (int64_t)mp * mp * 8;
-    gram_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(gpart, nchunk, m, mp, symmetrize, G);
+    gram_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(gpart, nchunk, m, mp, symmetrize, G,
+                                                                          reinterpret_cast<float2 *>(Gdf));
     return cudaGetLastError();
 }
