@@ -240,88 +240,246 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     }
     if (m > 0) {
     // ---------------------------------------------------------------- 1
-    for (int j = 0; j + 2 < m; ++j) {
-        const int r0 = j + 1;                       // first row of the trailing block
-        // squared norm of x = A[r0.., j] below its first entry
-        float part = 0.0f;
-        for (int i = r0 + 1 + tid; i < m; i += NT) part = fmaf(A[i * ld + j], A[i * ld + j], part);
-        part = warp_sum(part);
-        if (lane == 0) red[warp] = part;
-        __syncthreads();
-        const float tail = sum16(red);
-        const float x0 = A[r0 * ld + j];
-        const bool skip = !(tail > 0.0f);           // column already tridiagonal
-        const float sigma = sqrtf(fmaf(x0, x0, tail));
-        const float alpha = -copysignf(sigma, x0);
-        const float bt = skip ? 0.0f : 1.0f / (sigma * sigma - alpha * x0);
-        for (int i = r0 + tid; i < m; i += NT) vv[i] = (i == r0) ? (x0 - alpha) : A[i * ld + j];
-        if (tid == 0) {
-            d[j] = A[j * ld + j];
-            e[j] = skip ? x0 : alpha;
-            beta[j] = bt;
-        }
-        __syncthreads();                            // vv ready; red reusable
-        if (skip) {
-            // keep a zero reflector below the subdiagonal
-            for (int i = r0 + tid; i < m; i += NT) A[i * ld + j] = 0.0f;
-            __syncthreads();
-            continue;
-        }
-        // p = bt A22 v (four lanes per row, lane q summing the columns
-        // k = r0 + q mod 4; the row loop's trip count is the same for every
-        // thread, so the shuffles see full warps) and v^T p
-        float pv = 0.0f;
-        for (int base = r0; base < m; base += NT / 4) {
-            const int i = base + (tid >> 2), q = tid & 3;
-            float s0 = 0.0f, s1 = 0.0f;
-            if (i < m) {
-                const float *row = A + i * ld;
-                int k = r0 + q;
-                for (; k + 4 < m; k += 8) {
-                    s0 = fmaf(row[k], vv[k], s0);
-                    s1 = fmaf(row[k + 4], vv[k + 4], s1);
+    if (m <= SMEM_M) {
+        // The trailing matrix in registers: lane l of warp w holds rows
+        // 8 (l % 16) .. + 7, columns 8 w + 4 (l / 16) .. + 3 (zero past m),
+        // so a half-warp holds four whole columns.  Step j: the warp owning
+        // column j forms the reflector v (zero outside rows >= j + 1) and
+        // beta from its own registers; p = beta A v comes from column sums
+        // (A is symmetric) reduced over each half-warp; K = beta v^T p / 2 and
+        // w = p - K v; the rank-2 update A -= v w^T + w v^T touches only the
+        // registers, and the next column's warp can start at once.  v and p
+        // are zero outside the trailing block, so finished rows and columns
+        // are left alone.  Two barriers per step.
+        __shared__ __align__(16) float vq[SMEM_M], pq[SMEM_M];
+        __shared__ __align__(16) float rq[NT / 32];
+        __shared__ float s_bt;
+        const int rb = 8 * (lane & 15), cb = 8 * warp + 4 * (lane >> 4);
+        float a[8][4];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = rb + r, k = cb + c;
+                a[r][c] = (i < m && k < m) ? A[i * ld + k] : 0.0f;
+            }
+        for (int j = 0; j + 2 < m; ++j) {
+            const int r0 = j + 1;
+            // (A) the reflector, from column j in its warp's registers (the
+            // half-warp holding it; the other half contributes zeros)
+            if (warp == (j >> 3)) {
+                const bool mine = (lane >> 4) == ((j >> 2) & 1);
+                const int cj = j & 3;
+                float x[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    x[r] = a[r][0];
+#pragma unroll
+                    for (int c = 1; c < 4; ++c)
+                        if (cj == c) x[r] = a[r][c];
+                    if (!mine) x[r] = 0.0f;
                 }
-                if (k < m) s0 = fmaf(row[k], vv[k], s0);
+                float part = 0.0f;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = rb + r;
+                    if (i > r0 && i < m) part = fmaf(x[r], x[r], part);
+                }
+                const float tail = warp_sum(part);
+                float x0l = x[0], xjl = x[0];
+#pragma unroll
+                for (int r = 1; r < 8; ++r) {
+                    if ((r0 & 7) == r) x0l = x[r];
+                    if ((j & 7) == r) xjl = x[r];
+                }
+                const int hsrc = 16 * ((j >> 2) & 1);
+                const float x0 = __shfl_sync(0xffffffffu, x0l, hsrc + (r0 >> 3));
+                const float xj = __shfl_sync(0xffffffffu, xjl, hsrc + (j >> 3));
+                const bool skip = !(tail > 0.0f);           // column already tridiagonal
+                const float sigma = sqrtf(fmaf(x0, x0, tail));
+                const float alpha = -copysignf(sigma, x0);
+                const float bt = skip ? 0.0f : 1.0f / (sigma * sigma - alpha * x0);
+                if (mine) {
+                    float vv8[8];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const int i = rb + r;
+                        const float v = (i < r0 || i >= m || skip) ? 0.0f : (i == r0 ? x0 - alpha : x[r]);
+                        vv8[r] = v;
+                        if (i >= r0 && i < m) A[i * ld + j] = v;   // kept for the back-transformation
+                    }
+                    *reinterpret_cast<float4 *>(vq + rb) = make_float4(vv8[0], vv8[1], vv8[2], vv8[3]);
+                    *reinterpret_cast<float4 *>(vq + rb + 4) = make_float4(vv8[4], vv8[5], vv8[6], vv8[7]);
+                }
+                if (lane == 0) {
+                    d[j] = xj;
+                    e[j] = skip ? x0 : alpha;
+                    beta[j] = bt;
+                    s_bt = bt;
+                }
             }
-            s0 += s1;
-            s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-            s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-            if (i < m && q == 0) {
-                const float p = bt * s0;
-                pp[i] = p;
-                pv = fmaf(p, vv[i], pv);
+            __syncthreads();
+            // (B) p = beta A v from column sums over each half-warp; the warp's part of v^T p.
+            // A warp whose columns are all finished (< r0) has p = w = 0 there
+            // and nothing to update: it only writes its zeros.
+            const bool live = 8 * warp + 7 >= r0;
+            const float bt = s_bt;
+            const float4 vr0 = *reinterpret_cast<const float4 *>(vq + rb);
+            const float4 vr1 = *reinterpret_cast<const float4 *>(vq + rb + 4);
+            const float4 vc4 = *reinterpret_cast<const float4 *>(vq + cb);
+            const float vr[8] = {vr0.x, vr0.y, vr0.z, vr0.w, vr1.x, vr1.y, vr1.z, vr1.w};
+            const float vc[4] = {vc4.x, vc4.y, vc4.z, vc4.w};
+            float pc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            if (live) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float t0 = fmaf(a[0][c], vr[0], fmaf(a[1][c], vr[1], fmaf(a[2][c], vr[2], a[3][c] * vr[3])));
+                    const float t1 = fmaf(a[4][c], vr[4], fmaf(a[5][c], vr[5], fmaf(a[6][c], vr[6], a[7][c] * vr[7])));
+                    pc[c] = t0 + t1;
+                }
+#pragma unroll
+                for (int o = 1; o < 16; o <<= 1)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) pc[c] += __shfl_xor_sync(0xffffffffu, pc[c], o);
             }
+            float vtp = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int k = cb + c;
+                pc[c] = (k >= r0 && k < m) ? bt * pc[c] : 0.0f;
+                vtp = fmaf(vc[c], pc[c], vtp);
+            }
+            vtp += __shfl_xor_sync(0xffffffffu, vtp, 16);
+            if ((lane & 15) == 0) *reinterpret_cast<float4 *>(pq + cb) = make_float4(pc[0], pc[1], pc[2], pc[3]);
+            if (lane == 0) rq[warp] = vtp;
+            __syncthreads();
+            // (C) K and w, then the rank-2 update of the registers
+            if (!live) continue;
+            float vt = 0.0f;
+#pragma unroll
+            for (int q = 0; q < NT / 32; q += 4) {
+                const float4 t = *reinterpret_cast<const float4 *>(rq + q);
+                vt += (t.x + t.y) + (t.z + t.w);
+            }
+            const float K = 0.5f * bt * vt;
+            const float4 pr0 = *reinterpret_cast<const float4 *>(pq + rb);
+            const float4 pr1 = *reinterpret_cast<const float4 *>(pq + rb + 4);
+            const float pr[8] = {pr0.x, pr0.y, pr0.z, pr0.w, pr1.x, pr1.y, pr1.z, pr1.w};
+            float wc[4], wr[8];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) wc[c] = fmaf(-K, vc[c], pc[c]);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) wr[r] = fmaf(-K, vr[r], pr[r]);
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    a[r][c] = fmaf(-vr[r], wc[c], a[r][c]);
+                    a[r][c] = fmaf(-wr[r], vc[c], a[r][c]);
+                }
         }
-        pv = warp_sum(pv);
-        if (lane == 0) red[warp] = pv;
+        // the last 2 x 2 block of T
         __syncthreads();
-        const float vtp = sum16(red);
-        const float K = 0.5f * bt * vtp;
-        // A22 -= v w^T + w v^T with w = p - K v (rows by warp, columns by
-        // lane); the reflector goes below the subdiagonal
-        for (int i = r0 + warp; i < m; i += NT / 32) {
-            const float vi = vv[i], wi = pp[i] - K * vv[i];
-            float *row = A + i * ld;
-            for (int k = r0 + lane; k < m; k += 32) {
-                const float wk = pp[k] - K * vv[k];
-                row[k] -= vi * wk + wi * vv[k];
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = rb + r, k = cb + c;
+                if (m >= 2 && i == m - 2 && k == m - 2) d[m - 2] = a[r][c];
+                if (m >= 2 && i == m - 1 && k == m - 2) e[m - 2] = a[r][c];
+                if (i == m - 1 && k == m - 1) d[m - 1] = a[r][c];
             }
+        if (tid == 0) {
+            if (m >= 2) beta[m - 2] = 0.0f;
+            e[m - 1] = 0.0f;
+            beta[m - 1] = 0.0f;
         }
-        for (int i = r0 + tid; i < m; i += NT) A[i * ld + j] = vv[i];
         __syncthreads();
-    }
-    if (tid == 0) {
-        if (m >= 2) {
-            d[m - 2] = A[(m - 2) * ld + (m - 2)];
-            e[m - 2] = A[(m - 1) * ld + (m - 2)];
-            beta[m - 2] = 0.0f;
+    } else {
+        for (int j = 0; j + 2 < m; ++j) {
+            const int r0 = j + 1;                       // first row of the trailing block
+            // squared norm of x = A[r0.., j] below its first entry
+            float part = 0.0f;
+            for (int i = r0 + 1 + tid; i < m; i += NT) part = fmaf(A[i * ld + j], A[i * ld + j], part);
+            part = warp_sum(part);
+            if (lane == 0) red[warp] = part;
+            __syncthreads();
+            const float tail = sum16(red);
+            const float x0 = A[r0 * ld + j];
+            const bool skip = !(tail > 0.0f);           // column already tridiagonal
+            const float sigma = sqrtf(fmaf(x0, x0, tail));
+            const float alpha = -copysignf(sigma, x0);
+            const float bt = skip ? 0.0f : 1.0f / (sigma * sigma - alpha * x0);
+            for (int i = r0 + tid; i < m; i += NT) vv[i] = (i == r0) ? (x0 - alpha) : A[i * ld + j];
+            if (tid == 0) {
+                d[j] = A[j * ld + j];
+                e[j] = skip ? x0 : alpha;
+                beta[j] = bt;
+            }
+            __syncthreads();                            // vv ready; red reusable
+            if (skip) {
+                // keep a zero reflector below the subdiagonal
+                for (int i = r0 + tid; i < m; i += NT) A[i * ld + j] = 0.0f;
+                __syncthreads();
+                continue;
+            }
+            // p = bt A22 v (four lanes per row, lane q summing the columns
+            // k = r0 + q mod 4; the row loop's trip count is the same for every
+            // thread, so the shuffles see full warps) and v^T p
+            float pv = 0.0f;
+            for (int base = r0; base < m; base += NT / 4) {
+                const int i = base + (tid >> 2), q = tid & 3;
+                float s0 = 0.0f, s1 = 0.0f;
+                if (i < m) {
+                    const float *row = A + i * ld;
+                    int k = r0 + q;
+                    for (; k + 4 < m; k += 8) {
+                        s0 = fmaf(row[k], vv[k], s0);
+                        s1 = fmaf(row[k + 4], vv[k + 4], s1);
+                    }
+                    if (k < m) s0 = fmaf(row[k], vv[k], s0);
+                }
+                s0 += s1;
+                s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+                s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+                if (i < m && q == 0) {
+                    const float p = bt * s0;
+                    pp[i] = p;
+                    pv = fmaf(p, vv[i], pv);
+                }
+            }
+            pv = warp_sum(pv);
+            if (lane == 0) red[warp] = pv;
+            __syncthreads();
+            const float vtp = sum16(red);
+            const float K = 0.5f * bt * vtp;
+            // A22 -= v w^T + w v^T with w = p - K v (rows by warp, columns by
+            // lane); the reflector goes below the subdiagonal
+            for (int i = r0 + warp; i < m; i += NT / 32) {
+                const float vi = vv[i], wi = pp[i] - K * vv[i];
+                float *row = A + i * ld;
+                for (int k = r0 + lane; k < m; k += 32) {
+                    const float wk = pp[k] - K * vv[k];
+                    row[k] -= vi * wk + wi * vv[k];
+                }
+            }
+            for (int i = r0 + tid; i < m; i += NT) A[i * ld + j] = vv[i];
+            __syncthreads();
         }
-        d[m - 1] = A[(m - 1) * ld + (m - 1)];
-        e[m - 1] = 0.0f;
-        beta[m - 1] = 0.0f;
-    }
-    __syncthreads();
+        if (tid == 0) {
+            if (m >= 2) {
+                d[m - 2] = A[(m - 2) * ld + (m - 2)];
+                e[m - 2] = A[(m - 1) * ld + (m - 2)];
+                beta[m - 2] = 0.0f;
+            }
+            d[m - 1] = A[(m - 1) * ld + (m - 1)];
+            e[m - 1] = 0.0f;
+            beta[m - 1] = 0.0f;
+        }
+        __syncthreads();
 
+
+    }
     // ---------------------------------------------------------------- 2
     __shared__ float s_gl, s_gu, s_pivmin, s_tnorm;
     if (tid == 0) {
