@@ -328,11 +328,11 @@ int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, flo
     stage_scope st(ctx, PSDPROJ_STAGE_ORTH);
     // m <= 128: the Gram also as double-float pairs, in the (then unused) large-m scratch
     float *gdf = m <= 128 ? reinterpret_cast<float *>(ws.cholscr) : nullptr;
-    PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1, gdf), 2);
+    PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1, gdf, ctx->persist_sms), 2);
     PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status, 1,
                            ws.cholscr), 1);
     PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, ws.T, ws.ld), 1);
-    PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1, gdf), 2);
+    PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1, gdf, ctx->persist_sms), 2);
     PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
                            ws.cholscr), 1);
     PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq, side), 1);
@@ -447,7 +447,7 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.W, ws.ld, opts.prec));
         {
             stage_scope st(ctx, PSDPROJ_STAGE_CORE);
-            PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.W, ws.ld, n, m, ws.gpart, ws.C, 2), 2);
+            PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.W, ws.ld, n, m, ws.gpart, ws.C, 2, nullptr, ctx->persist_sms), 2);
         }
         {
             stage_scope st(ctx, PSDPROJ_STAGE_EIG);
@@ -477,7 +477,7 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec, fuse));
     {
         stage_scope st(ctx, PSDPROJ_STAGE_CORE);
-        PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.Y, ws.ld, n, m, ws.gpart, ws.C, 2), 2);
+        PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.Y, ws.ld, n, m, ws.gpart, ws.C, 2, nullptr, ctx->persist_sms), 2);
     }
     {
         stage_scope st(ctx, PSDPROJ_STAGE_EIG);
@@ -1180,7 +1180,7 @@ int psdproj_core(psdproj_ctx *ctx, const float *dX, int64_t ldx, const float *dZ
     device_guard g(ctx->device);
     PSD_TRY(psd_ensure_workspace(ctx, n, m));
     stage_scope st(ctx, PSDPROJ_STAGE_CORE);
-    PSD_KL(launch_gram(ctx->stream, dX, ldx, dZ, ldz, n, m, ctx->ws.gpart, dC, 2), 2);
+    PSD_KL(launch_gram(ctx->stream, dX, ldx, dZ, ldz, n, m, ctx->ws.gpart, dC, 2, nullptr, ctx->persist_sms), 2);
     return PSDPROJ_OK;
 }
 

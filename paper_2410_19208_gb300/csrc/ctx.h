@@ -234,11 +234,13 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
                                int64_t ldh, int *d_status, int x_part, int accumulate,
                                int prepared = 0, long long wait_limit = 0);
 
-// Gram partials + FP64 reduction: G = X^T Z (sym = 1: X == Z, symmetric).
-// Gdf (may be NULL): the same sums as double-float pairs (hi, lo), m x m.
+// Gram partials + FP64 reduction: G = X^T Z (sym = 1: X == Z, symmetric;
+// 2: (X^T Z + Z^T X)/2).  Gdf (may be NULL; symmetric forms): the same sums
+// as double-float pairs (hi, lo), m x m.  sm_count: SMs the partial
+// products may spread over (0: a default).
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
                         int64_t ldz, int64_t n, int m, float *gpart, double *G,
-                        int symmetrize, float *Gdf = nullptr);
+                        int symmetrize, float *Gdf = nullptr, int sm_count = 0);
 
 // first_pass = 1: double-float factorization (FP64 when m > 128); 0: FP32.
 // Writes R^-1 (m x m column-major FP32), the dependent-column flags and

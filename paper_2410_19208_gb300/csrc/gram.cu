@@ -216,13 +216,190 @@ __global__ void gram_reduce_kernel(const float *__restrict__ gpart, int nchunk, 
     }
 }
 
+// The symmetric products for m <= 128 (G = X^T X, or S = (X^T Z + Z^T X)/2)
+// on the upper triangle only: 2 blocks per SM, block b owning rows
+// [b R, (b + 1) R) (R = rows, a multiple of 8), staged SR rows at a time;
+// thread t owns the t-th 8 x 8 tile (bi <= bj) of the upper triangle (64
+// FMAs per four 16-byte shared loads; twice that for the two-sided form)
+// and writes one FP32 partial per block, tile-major.
+constexpr int SR = 64;            // rows staged at a time
+constexpr int NTU = 160;          // >= tiles of the upper triangle for m <= 128 (136)
+
+template <bool TWO>
+__global__ void __launch_bounds__(NTU)
+gram_upper_kernel(const float *__restrict__ X, int64_t ldx, const float *__restrict__ Z, int64_t ldz, int64_t n,
+                  int m, int mp, int rows, float *__restrict__ gpart)
+{
+    extern __shared__ __align__(16) float sgu[];
+    const int ld = mp + 4;
+    float *Xs = sgu;                       // SR x ld
+    float *Zs = sgu + SR * ld;             // (two-sided form)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nt8 = mp / 8, ntiles = nt8 * (nt8 + 1) / 2;
+    int bi = 0, bj = 0;
+    {
+        int t = tid < ntiles ? tid : 0;
+        while (t >= nt8 - bi) {
+            t -= nt8 - bi;
+            ++bi;
+        }
+        bj = bi + t;
+    }
+    const bool act = tid < ntiles;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
+    const int64_t rbeg = (int64_t)blockIdx.x * rows;
+    const int64_t rend = min(rbeg + rows, n);
+    for (int64_t r0 = rbeg; r0 < rend; r0 += SR) {
+        const int nr = (int)min((int64_t)SR, rend - r0);
+        __syncthreads();
+        // stage rows r0 .. r0 + nr - 1: element e = (column e / SR, row e % SR),
+        // consecutive threads on consecutive rows (coalesced), a batch of
+        // loads in flight per thread before their stores
+        constexpr int BT = TWO ? 8 : 16;
+        for (int base = 0; base < mp * SR; base += NTU * BT) {
+            float vx[BT], vz[BT];
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                const int e = base + tid + NTU * u;
+                const int c = e / SR, r = e % SR;
+                const bool ok = e < mp * SR && r < nr && c < m;
+                vx[u] = ok ? X[(int64_t)c * ldx + r0 + r] : 0.0f;
+                if (TWO) vz[u] = ok ? Z[(int64_t)c * ldz + r0 + r] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < BT; ++u) {
+                const int e = base + tid + NTU * u;
+                if (e < mp * SR) {
+                    Xs[(e % SR) * ld + e / SR] = vx[u];
+                    if (TWO) Zs[(e % SR) * ld + e / SR] = vz[u];
+                }
+            }
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll 2
+            for (int r = 0; r < nr; ++r) {
+                const float4 *xi = reinterpret_cast<const float4 *>(Xs + r * ld + 8 * bi);
+                const float4 *xj = reinterpret_cast<const float4 *>(Xs + r * ld + 8 * bj);
+                const float4 a0 = xi[0], a1 = xi[1], b0 = xj[0], b1 = xj[1];
+                const float x[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float y[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                if (TWO) {
+                    const float4 *zi = reinterpret_cast<const float4 *>(Zs + r * ld + 8 * bi);
+                    const float4 *zj = reinterpret_cast<const float4 *>(Zs + r * ld + 8 * bj);
+                    const float4 c0 = zi[0], c1 = zi[1], d0 = zj[0], d1 = zj[1];
+                    const float zi8[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                    const float zj8[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(x[i], zj8[j], fmaf(zi8[i], y[j], acc[i][j]));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(x[i], y[j], acc[i][j]);
+                }
+            }
+        }
+    }
+    if (act) {
+        float *out = gpart + ((int64_t)blockIdx.x * ntiles + tid) * 64;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            reinterpret_cast<float4 *>(out + 8 * i)[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            reinterpret_cast<float4 *>(out + 8 * i)[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+        }
+    }
+}
+
+// G from the per-block partials of gram_upper_kernel: a block takes 32
+// consecutive positions q of the tile-major partial (lane = position, so the
+// loads are coalesced) and its 8 warps split the block partials (warp g:
+// partials g, g + 8, ...), each summing in double-float; the 8 sums are
+// added in a fixed order (deterministic).  Both (a, b) and (b, a) are
+// written (scale: 1 for X^T X, 1/2 for the two-sided form).
+__global__ void __launch_bounds__(256)
+gram_upper_reduce_kernel(const float *__restrict__ gpart, int nblk, int m, int mp, float scale,
+                         double *__restrict__ G, float2 *__restrict__ Gdf)
+{
+    __shared__ fsum part[8][32];
+    const int nt8 = mp / 8, ntiles = nt8 * (nt8 + 1) / 2;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int q = blockIdx.x * 32 + lane;
+    const bool inr = q < ntiles * 64;
+    fsum acc = {0.0f, 0.0f};
+    if (inr) {
+#pragma unroll 4
+        for (int b = g; b < nblk; b += 8) acc = fsum_add(acc, {gpart[(int64_t)b * ntiles * 64 + q], 0.0f});
+    }
+    part[g][lane] = acc;
+    __syncthreads();
+    if (g != 0 || !inr) return;
+#pragma unroll
+    for (int w = 1; w < 8; ++w) acc = fsum_add(acc, part[w][lane]);
+    const int t = q >> 6, ij = q & 63, i = ij >> 3, j = ij & 7;
+    int bi = 0, tt = t;
+    while (tt >= nt8 - bi) {
+        tt -= nt8 - bi;
+        ++bi;
+    }
+    const int bj = bi + tt;
+    const int ia = 8 * bi + i, ib = 8 * bj + j;
+    if (ia >= m || ib >= m || (bi == bj && i > j)) return;
+    acc.hi *= scale;          // exact: scale is a power of two
+    acc.lo *= scale;
+    const double sv = (double)acc.hi + (double)acc.lo;
+    G[(int64_t)ib * m + ia] = sv;
+    G[(int64_t)ia * m + ib] = sv;
+    if (Gdf) {
+        Gdf[(int64_t)ib * m + ia] = make_float2(acc.hi, acc.lo);
+        Gdf[(int64_t)ia * m + ib] = make_float2(acc.hi, acc.lo);
+    }
+}
+
 }  // namespace
 
 // symmetrize: 0 = G = X^T Z as is; 1 = X == Z (upper computed, mirrored);
 // 2 = (X^T Z + Z^T X)/2.
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
-                        int64_t ldz, int64_t n, int m, float *gpart, double *G, int symmetrize, float *Gdf)
+                        int64_t ldz, int64_t n, int m, float *gpart, double *G, int symmetrize, float *Gdf,
+                        int sm_count)
 {
+    if (Gdf && symmetrize == 0) return cudaErrorInvalidValue;
+    if (symmetrize != 0 && m <= 128 && n > 0) {
+        // rows per block: at least PSD_GRAM_CHUNK (so that the blocks' partials
+        // fit the workspace sized for ceil(n / PSD_GRAM_CHUNK) chunks of mp^2),
+        // about two blocks per SM
+        const int mp = (int)psd_round_up(m, 8);
+        if (sm_count <= 0) sm_count = 148;
+        int64_t rows = (n + 2 * sm_count - 1) / (2 * sm_count);
+        rows = psd_round_up(rows < PSD_GRAM_CHUNK ? PSD_GRAM_CHUNK : rows, 8);
+        const int nblk = (int)((n + rows - 1) / rows);
+        const bool two = symmetrize == 2;
+        const size_t smem = sizeof(float) * (size_t)SR * (mp + 4) * (two ? 2 : 1);
+        if (two) {
+            // the attribute is process-wide: the largest size (m = 128)
+            cudaError_t ea = cudaFuncSetAttribute(gram_upper_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)(sizeof(float) * SR * (128 + 4) * 2));
+            if (ea != cudaSuccess) return ea;
+        }
+        if (two)
+            gram_upper_kernel<true><<<nblk, NTU, smem, s>>>(X, ldx, Z, ldz, n, m, mp, (int)rows, gpart);
+        else
+            gram_upper_kernel<false><<<nblk, NTU, smem, s>>>(X, ldx, X, ldx, n, m, mp, (int)rows, gpart);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int nt8 = mp / 8;
+        const int npos = nt8 * (nt8 + 1) / 2 * 64;
+        gram_upper_reduce_kernel<<<(unsigned)((npos + 31) / 32), 256, 0, s>>>(
+            gpart, nblk, m, mp, two ? 0.5f : 1.0f, G, reinterpret_cast<float2 *>(Gdf));
+        return cudaGetLastError();
+    }
     if (Gdf && symmetrize == 2) return cudaErrorInvalidValue;
     const int mp = (int)psd_round_up(m, 8);
     const int nchunk = (int)((n + CH - 1) / CH);
