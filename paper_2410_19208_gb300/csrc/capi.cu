@@ -331,11 +331,11 @@ int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, flo
     PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1, gdf, ctx->persist_sms), 2);
     PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status, 1,
                            ws.cholscr), 1);
-    PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, ws.T, ws.ld), 1);
+    PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, ws.T, ws.ld, nullptr, ctx->persist_sms), 1);
     PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1, gdf, ctx->persist_sms), 2);
     PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
                            ws.cholscr), 1);
-    PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq, side), 1);
+    PSD_KL(launch_tall_small(s, ws.T, ws.ld, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq, side, ctx->persist_sms), 1);
     return PSDPROJ_OK;
 }
 
@@ -490,7 +490,7 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     {
         stage_scope st(ctx, PSDPROJ_STAGE_FACTOR);
         PSD_KL(launch_factor_prep(s, ws.V, ws.d, m, ws.M, rk), 1);
-        PSD_KL(launch_tall_small(s, ws.Q, ws.ld, n, m, ws.M, m, nullptr, rk, Wd, ldwd), 1);
+        PSD_KL(launch_tall_small(s, ws.Q, ws.ld, n, m, ws.M, m, nullptr, rk, Wd, ldwd, nullptr, ctx->persist_sms), 1);
     }
     if (opts.out_mode != PSDPROJ_OUT_FACTOR) {
         stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
@@ -1213,7 +1213,7 @@ int psdproj_factor(psdproj_ctx *ctx, const float *dQ, int64_t ldq, int64_t n, in
     int *rk = ws.ints + IN_RANK;
     stage_scope st(ctx, PSDPROJ_STAGE_FACTOR);
     PSD_KL(launch_factor_prep(ctx->stream, dV, dd, m, ws.M, rk), 1);
-    PSD_KL(launch_tall_small(ctx->stream, dQ, ldq, n, m, ws.M, m, nullptr, rk, dW, ldw), 1);
+    PSD_KL(launch_tall_small(ctx->stream, dQ, ldq, n, m, ws.M, m, nullptr, rk, dW, ldw, nullptr, ctx->persist_sms), 1);
     if (d_rank)
         PSD_CK(cudaMemcpyAsync(d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream));
     return PSDPROJ_OK;

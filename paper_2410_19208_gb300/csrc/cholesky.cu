@@ -673,6 +673,90 @@ tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int 
     }
 }
 
+// The same product for m <= 128 and c <= 128 with B resident: a persistent
+// block (three per SM) copies B (zero past *d_cols) into shared memory once
+// and walks 32-row tiles of Y (tiles b, b + grid, ...); thread (tx, ty) =
+// (tid % 8, tid / 8) owns rows 4 tx .. 4 tx + 3 of the tile and columns
+// 4 ty .. 4 ty + 3 (16 FMAs per two 16-byte shared loads per K step).  The
+// tile is staged K-major with batched, coalesced loads; stores are coalesced
+// over the rows.
+constexpr int RT = 32;              // rows per tile
+constexpr int LDB = 132, LDT = 36;  // shared row strides (floats) of B and of the Y tile
+
+__global__ void __launch_bounds__(256)
+tall_small_res_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m, const float *__restrict__ B,
+                      int c, const int *__restrict__ colmask, const int *__restrict__ d_cols, float *__restrict__ Z,
+                      int64_t ldz, psd_bf16_side side, int ntiles)
+{
+    extern __shared__ __align__(16) float smt[];
+    float *Bs = smt;                              // Bs[k * LDB + col] = B(k, col)
+    float *Ys = smt + (size_t)m * LDB;            // Ys[k * LDT + r] = Y(row0 + r, k)
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const int ncols = d_cols ? min(*d_cols, c) : c;
+    for (int e = tid; e < m * 128; e += 256) {
+        const int col = e / m, k = e - (e / m) * m;
+        Bs[k * LDB + col] = col < ncols ? B[(int64_t)col * m + k] : 0.0f;
+    }
+    const float shift = side.d_shift ? (float)*side.d_shift : 0.0f;
+    bool zero[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int gc = 4 * ty + j;
+        zero[j] = gc >= ncols || (colmask && gc < c && colmask[gc]);
+    }
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row0 = (int64_t)tile * RT;
+        __syncthreads();
+        // stage Y(row0 .. row0 + 31, 0 .. m-1), 8 loads in flight per thread
+        for (int base = 0; base < m * RT; base += 256 * 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = base + tid + 256 * u;
+                const int k = e / RT, r = e % RT;
+                v[u] = (e < m * RT && row0 + r < n) ? Y[(int64_t)k * ldy + row0 + r] : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = base + tid + 256 * u;
+                if (e < m * RT) Ys[(e / RT) * LDT + e % RT] = v[u];
+            }
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+        for (int k = 0; k < m; ++k) {
+            const float4 y4 = *reinterpret_cast<const float4 *>(Ys + k * LDT + 4 * tx);
+            const float4 b4 = *reinterpret_cast<const float4 *>(Bs + k * LDB + 4 * ty);
+            const float y[4] = {y4.x, y4.y, y4.z, y4.w};
+            const float bb[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(y[i], bb[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gc = 4 * ty + j;
+            if (gc >= c) continue;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t gr = row0 + 4 * tx + i;
+                if (gr >= n) continue;
+                const float z = zero[j] ? 0.0f : acc[i][j];
+                Z[(int64_t)gc * ldz + gr] = z;
+                // side outputs for the BF16 pass that reads Z next
+                if (side.Xh) side.Xh[(int64_t)gc * side.ldh + gr] = __bfloat16_as_ushort(__float2bfloat16_rn(z));
+                if (side.Y) side.Y[(int64_t)gc * side.ldy + gr] = shift * z;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_cholesky(cudaStream_t s, const double *G, const float *Gdf, int m, float *Rinv,
@@ -715,11 +799,24 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, const float *Gdf, i
 
 cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64_t n, int m,
                               const float *B, int c, const int *colmask, const int *d_cols,
-                              float *Z, int64_t ldz, const psd_bf16_side *side)
+                              float *Z, int64_t ldz, const psd_bf16_side *side, int sm_count)
 {
     const unsigned rb = (unsigned)((n + TR - 1) / TR);
     const psd_bf16_side sd = side ? *side : psd_bf16_side{nullptr, 0, nullptr, 0, nullptr};
     if (side && c > 128) return cudaErrorNotSupported;
+    if (m <= 128 && c <= 128 && n > 0) {
+        const size_t smem = sizeof(float) * (size_t)m * (LDB + LDT);
+        // the attribute is process-wide: the largest size (m = 128)
+        cudaError_t e = cudaFuncSetAttribute(tall_small_res_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(sizeof(float) * 128 * (LDB + LDT)));
+        if (e != cudaSuccess) return e;
+        const int ntiles = (int)((n + RT - 1) / RT);
+        const int per_sm = smem <= 227 * 1024 / 3 ? 3 : 2;
+        int grid = (sm_count > 0 ? sm_count : 148) * per_sm;
+        if (grid > ntiles) grid = ntiles;
+        tall_small_res_kernel<<<grid, 256, smem, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd, ntiles);
+        return cudaGetLastError();
+    }
     switch ((c + 15) / 16) {
     case 1: tall_small_wide_kernel<1><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;
     case 2: tall_small_wide_kernel<2><<<rb, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, sd); break;

@@ -259,7 +259,7 @@ cudaError_t launch_cholesky(cudaStream_t s, const double *G, const float *Gdf, i
 // side (may be NULL, c <= 128 only): the BF16 pass's side outputs of Z.
 cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64_t n, int m,
                               const float *B, int c, const int *colmask, const int *d_cols,
-                              float *Z, int64_t ldz, const psd_bf16_side *side = nullptr);
+                              float *Z, int64_t ldz, const psd_bf16_side *side = nullptr, int sm_count = 0);
 
 // scratch: 3 (m+2)^2 floats of device memory (used when m is too large for
 // shared memory); d_flag: one device int (the tridiagonal solver's failure
