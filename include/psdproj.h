@@ -38,6 +38,9 @@
 extern "C" {
 #endif
 
+/* Largest sketch width l = k + p (and m of the per-step calls). */
+#define PSDPROJ_MAX_M 512
+
 /* ---- status codes ------------------------------------------------------- */
 #define PSDPROJ_OK          0
 #define PSDPROJ_EINVAL      1  /* bad argument (sizes, leading dims, NULL)     */
@@ -174,7 +177,7 @@ uint64_t psdproj_kernel_launches(void);
  *   Omega = randn(n, k+p) (Philox4x32-10 stream 0 of `seed`),
  *   Q = orth(A^(2q+1) Omega), orthonormalised after every product,
  *   Q^T A Q = V D V^T,  W = Q V sqrt(max(D,0)),  P = W W^T.
- * Requires n >= 1, k >= 1, p >= 0, 1 <= k+p <= min(n, 256), 0 <= q <= 16,
+ * Requires n >= 1, k >= 1, p >= 0, 1 <= k+p <= min(n, 512), 0 <= q <= 16,
  * lda >= n, ldp >= n (when P is written), ldw >= n (when dW != NULL).
  * dP may be NULL only with out_mode FACTOR.  dW (n x (k+p), column-major)
  * may be NULL; its columns beyond r+ are zero.  d_rank (device int, may be
@@ -424,7 +427,7 @@ int psdproj_gaussian(psdproj_ctx *ctx, uint64_t seed, uint32_t stream,
  * first value of word 0 of Philox(counter (c, t, 16, 0)) mod N, t = 0, 1, ...,
  * not taken by a column before c (so the m columns of H_N are distinct).
  * Entries are exactly +-1 (exact in every operand format).  Requires
- * 1 <= m <= min(n, 256), ldx >= n. */
+ * 1 <= m <= min(n, 512), ldx >= n. */
 int psdproj_srht(psdproj_ctx *ctx, uint64_t seed, int64_t n, int m, float *dX, int64_t ldx);
 
 /* Symmetric pass over A (Alg. 1 products, and Z = A Q of Alg. 2 line 2):
@@ -448,7 +451,7 @@ int psdproj_sym_pass(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda,
  * twice.  A column whose pivot R_jj^2 <= 1e-10 * max_i G_ii is dependent: its
  * Q column is set to zero.  dY (input) and dQ (output) are n x m column-major;
  * they may alias.  d_qrank (device int, may be NULL) receives the number of
- * independent columns.  Requires 1 <= m <= 256. */
+ * independent columns.  Requires 1 <= m <= 512. */
 int psdproj_cholqr2(psdproj_ctx *ctx, const float *dY, int64_t n, int64_t ldy,
                     int m, float *dQ, int64_t ldq, int *d_qrank);
 
@@ -460,7 +463,7 @@ int psdproj_core(psdproj_ctx *ctx, const float *dX, int64_t ldx, const float *dZ
 /* Small symmetric eigensolver of Alg. 2 line 2 ("eig(Q^T X Q)") on dC (m x m
  * FP64 in, read only), in FP32 in one thread block.  dV (m x m column-major
  * FP32) receives orthonormal eigenvectors, dd (m doubles) the eigenvalues;
- * eigenpairs are sorted by decreasing eigenvalue.  Requires 1 <= m <= 256.
+ * eigenpairs are sorted by decreasing eigenvalue.  Requires 1 <= m <= 512.
  * psdproj_eig uses PSDPROJ_EIG_AUTO: Householder tridiagonalization,
  * bisection, twisted-factorization eigenvectors and one Newton-Schulz
  * orthogonalization step; when that solver flags a failure (a non-finite or

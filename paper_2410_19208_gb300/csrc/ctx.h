@@ -56,7 +56,7 @@ __host__ __device__ inline int64_t psd_tile32_count(int64_t n)
     const int64_t nbr = (n + PSD_TILE_M - 1) / PSD_TILE_M;
     return nbr * nbr * (PSD_TILE_M / PSD_TILE32_N);
 }
-constexpr int PSD_MAX_M = 256;        // largest sketch width
+constexpr int PSD_MAX_M = PSDPROJ_MAX_M;  // largest sketch width
 
 struct psd_workspace {
     int64_t n = 0;      // rows the tall buffers hold

@@ -58,7 +58,7 @@ int check_request(const psdproj_request &r, int out_mode)
     if (!r.dA || r.n < 1 || r.lda < r.n || r.k < 1 || r.p < 0 || r.q < 0 || r.q > 16) return PSDPROJ_EINVAL;
     if (r.algorithm != 1 && r.algorithm != 2) return PSDPROJ_EINVAL;
     const int64_t m = (int64_t)r.k + r.p;
-    if (m > r.n || m > 256) return PSDPROJ_EINVAL;
+    if (m > r.n || m > PSDPROJ_MAX_M) return PSDPROJ_EINVAL;
     if (out_mode != PSDPROJ_OUT_FACTOR && (!r.dP || r.ldp < r.n)) return PSDPROJ_EINVAL;
     if (r.dW && r.ldw < r.n) return PSDPROJ_EINVAL;
     return PSDPROJ_OK;

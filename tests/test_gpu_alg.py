@@ -613,17 +613,20 @@ def test_server_many_widths_concurrently_all_succeed():
 # ----------------------------------------------------------------------------
 @pytest.mark.parametrize("prec", [ps.PREC_FP32, ps.PREC_BF16])
 def test_cor3_class_crossover_matches_oracle(ctx, oracle_lib, prec):
-    # n = 400, beta = (3, 1, 6, 2), oversampling 5, q = 2: Alg. 3 is no better
-    # than Alg. 2 for k <= n/4 and far better beyond; each GPU error within 2 %
-    # of the oracle's for the same seed (BF16: plus the rounding of A)
-    n, p, q = 400, 5, 2
+    # the example's own size: n = 1000, beta = (3, 1, 6, 2), oversampling 5,
+    # q = 2, k past n/4 = 250 (sketch widths up to 405): Alg. 3 is no better
+    # than Alg. 2 below n/4 and better beyond, increasingly with k (the
+    # oracle's error ratios: 1.01 at k = 200, 0.91 at 300, 0.63 at 400); each
+    # GPU error within 2 % of the oracle's for the same seed (BF16: plus the
+    # rounding of A)
+    n, p, q = 1000, 5, 2
     Vr = si.householder_vectors(n, 3, 0)
     lam = si.spectrum_cor3(n, 3.0, 1.0, 6.0, 2.0)
     A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
     xp = np.sqrt(np.sum(np.maximum(lam, 0) ** 2))
     opts = ps.make_opts(prec=prec, syrk_prec=ps.PREC_BF16X3 if prec != ps.PREC_FP32 else ps.PREC_FP32)
     err = {}
-    for k in (60, 100, 200, 250):
+    for k in (200, 300, 400):
         g1 = _run(ctx, A32, k, p, q, 1, alg=1, opts=opts)["W"]
         g2 = _run(ctx, A32, k, p, q, 1, alg=2, opts=opts)["W"]
         e = [np.sqrt(max(oracle_lib.exact_dist2(Vr, lam, w), 0)) / xp for w in (g1, g2)]
@@ -636,10 +639,9 @@ def test_cor3_class_crossover_matches_oracle(ctx, oracle_lib, prec):
         for a, b in zip(e, eo):
             assert abs(a - b) <= 0.02 * b + slack
         err[k] = e
-    for k in (60, 100):
-        assert err[k][1] >= 0.98 * err[k][0]
-    for k in (200, 250):
-        assert err[k][1] <= 0.5 * err[k][0]
+    assert err[200][1] >= 0.98 * err[200][0]
+    assert err[300][1] <= 0.95 * err[300][0]
+    assert err[400][1] <= 0.7 * err[400][0]
 
 
 # ----------------------------------------------------------------------------

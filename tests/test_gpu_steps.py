@@ -114,7 +114,9 @@ def _cond_tall(n, m, cond, seed):
                                       (500, 16, 10.0), (500, 17, 10.0), (700, 33, 100.0),
                                       (900, 127, 10.0),
                                       # Gram of condition 1e8: the double-float first pass
-                                      (3000, 110, 1e4)])
+                                      (3000, 110, 1e4),
+                                      # wider than 256 columns (global-memory factorization)
+                                      (1000, 305, 10.0), (1200, 512, 10.0)])
 def test_cholqr2_orthonormal_same_range(ctx, oracle_lib, n, m, cond):
     Y = _cond_tall(n, m, cond, seed=m)
     Yd = _tall_from_np(Y)
@@ -224,7 +226,7 @@ def test_core_matches_oracle(ctx, oracle_lib):
     assert np.array_equal(got, got.T)
 
 
-@pytest.mark.parametrize("m", [1, 2, 3, 17, 60, 110, 112, 161, 210, 256])
+@pytest.mark.parametrize("m", [1, 2, 3, 17, 60, 110, 112, 161, 210, 256, 305, 512])
 @pytest.mark.parametrize("method", [ps.EIG_AUTO, ps.EIG_JACOBI, ps.EIG_TRIDIAG])
 def test_eig_matches_lapack(ctx, m, method):
     rng = np.random.default_rng(m)
@@ -450,7 +452,7 @@ def test_sym_pass_bf16_any_lda(ctx, oracle_lib):
 
 
 @pytest.mark.parametrize("prec", [ps.PREC_BF16, ps.PREC_BF16X3, ps.PREC_TF32])
-@pytest.mark.parametrize("m", [129, 256])
+@pytest.mark.parametrize("m", [129, 256, 305])
 def test_sym_pass_tensor_core_wide_sketch(ctx, oracle_lib, prec, m):
     # more than 128 columns: column slices of 128, one pass each
     n = 700
