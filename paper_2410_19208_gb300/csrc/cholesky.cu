@@ -267,10 +267,8 @@ cholesky_kernel(const double *__restrict__ G, int m, float *Rinv, int *__restric
 //   (3) the trailing upper triangle loses the block's contribution,
 //       U(i,k) -= sum_j R(j,i) R(j,k), in 4 x 4 register tiles.
 // R^-1 (FP32, from the FP32 copy of R) then comes blockwise: each diagonal
-// block inverted by one warp (a lane per column), the off-diagonal blocks
-// from the last block row up,
-//   X(b, c) = -X(b, b) sum_{d > b} R(b, d) X(d, c),
-// two barriers per block row.
+// block inverted by one warp (a lane per column), the off-diagonal blocks by
+// recursive doubling (below), two barriers per level.
 constexpr int NTB = 512;
 // block width NB: 8 for the double-float pass (shorter dependent chain in the
 // diagonal block, measured 185 vs 204 us at m = 110), 16 for FP32 (94 vs 98 us)
@@ -292,7 +290,11 @@ template <typename T>
 size_t blocked_smem(int m)
 {
     const size_t ldu = (size_t)m + 1;
-    return sizeof(T) * m * ldu + sizeof(float) * m * ldu + sizeof(float) * chol_nb<T>::value * m;
+    // Tmp: the NB x m panel of the factorization, then the products of the
+    // R^-1 doubling (at most SMEM_M / 2 squared floats over all pairs of a level)
+    const size_t tmp = (size_t)chol_nb<T>::value * m > (size_t)(SMEM_M / 2) * (SMEM_M / 2)
+                           ? (size_t)chol_nb<T>::value * m : (size_t)(SMEM_M / 2) * (SMEM_M / 2);
+    return sizeof(T) * m * ldu + sizeof(float) * m * ldu + sizeof(float) * tmp;
 }
 
 template <typename T>
@@ -307,7 +309,7 @@ cholesky_blocked_kernel(const float2 *__restrict__ Gd, int m, float *__restrict_
     const int ldu = m + 1;
     T *U = reinterpret_cast<T *>(smraw);                               // m x ldu, row-major, upper part
     float *Rf = reinterpret_cast<float *>(U + (size_t)m * ldu);        // FP32 R, m x ldu
-    float *Tmp = Rf + (size_t)m * ldu;                                 // NB x m
+    float *Tmp = Rf + (size_t)m * ldu;      // NB x m (panel), then the R^-1 doubling products
     float *X = reinterpret_cast<float *>(smraw);                       // R^-1, m x ldu (U's bytes, once U is done)
     __shared__ float s_gmax;
     __shared__ int s_bad;
@@ -486,30 +488,71 @@ cholesky_blocked_kernel(const float2 *__restrict__ Gd, int m, float *__restrict_
         }
     }
     __syncthreads();
-    // (b) off-diagonal blocks, last block row first
-    for (int b = nblk - 2; b >= 0; --b) {
-        const int j0 = b * NB, j1 = j0 + NB, ncol = m - j1;
-        // Tmp(a, s) = sum_{q = j1 .. s} R(j0 + a, q) X(q, s)
-        for (int e = tid; e < NB * ncol; e += NTB) {
-            const int a = e / ncol, s = j1 + (e - (e / ncol) * ncol);
-            const float *rr = Rf + (j0 + a) * ldu;
-            float s0 = 0.0f, s1 = 0.0f;
-            int q = j1;
-            for (; q + 1 <= s; q += 2) {
-                s0 = fmaf(rr[q], X[q * ldu + s], s0);
-                s1 = fmaf(rr[q + 1], X[(q + 1) * ldu + s], s1);
+    // (b) off-diagonal blocks by recursive doubling: with the diagonal blocks
+    // of size h inverted, each pair of adjacent ones [R11 R12; 0 R22] gets
+    //   X12 = -X11 (R12 X22),
+    // both products in 4 x 4 register tiles over the triangular ranges only
+    // (X11, X22 upper triangular; entries below their diagonals are never
+    // read), two barriers per level: log2(m / NB) levels.
+    for (int h = NB; h < m; h *= 2) {
+        const int s2 = 2 * h, npair = (m + s2 - 1) / s2, nt = (h + 3) / 4;
+        // Tmp(pair) = R12 X22, h x h per pair
+        for (int e = tid; e < npair * nt * nt; e += NTB) {
+            const int pidx = e / (nt * nt), rem = e - pidx * (nt * nt);
+            const int ti = rem / nt, tc = rem - ti * nt;
+            const int j0 = pidx * s2, j1 = j0 + h, h2 = min(h, m - j1);
+            if (h2 <= 0 || 4 * tc >= h2) continue;
+            float acc[4][4] = {};
+            const int kend = min(4 * tc + 4, h2);              // k <= c
+            for (int k = 0; k < kend; ++k) {
+                float r[4], x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) r[i] = (4 * ti + i < h) ? Rf[(j0 + 4 * ti + i) * ldu + j1 + k] : 0.0f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int cc = 4 * tc + c;
+                    x[c] = (cc < h2 && k <= cc) ? X[(j1 + k) * ldu + j1 + cc] : 0.0f;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(r[i], x[c], acc[i][c]);
             }
-            if (q <= s) s0 = fmaf(rr[q], X[q * ldu + s], s0);
-            Tmp[a * m + s] = s0 + s1;
+            float *tp = Tmp + (size_t)pidx * h * h;
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (4 * ti + i < h && 4 * tc + c < h2) tp[(4 * ti + i) * h + 4 * tc + c] = acc[i][c];
         }
         __syncthreads();
-        // X(j0 + a, s) = -sum_{a2 >= a} X(j0 + a, j0 + a2) Tmp(a2, s)
-        for (int e = tid; e < NB * ncol; e += NTB) {
-            const int a = e / ncol, s = j1 + (e - (e / ncol) * ncol);
-            const float *xr = X + (j0 + a) * ldu + j0;
-            float acc = 0.0f;
-            for (int a2 = a; a2 < NB; ++a2) acc = fmaf(xr[a2], Tmp[a2 * m + s], acc);
-            X[(j0 + a) * ldu + s] = -acc;
+        // X12 = -X11 Tmp(pair)
+        for (int e = tid; e < npair * nt * nt; e += NTB) {
+            const int pidx = e / (nt * nt), rem = e - pidx * (nt * nt);
+            const int ti = rem / nt, tc = rem - ti * nt;
+            const int j0 = pidx * s2, j1 = j0 + h, h2 = min(h, m - j1);
+            if (h2 <= 0 || 4 * tc >= h2) continue;
+            const float *tp = Tmp + (size_t)pidx * h * h;
+            float acc[4][4] = {};
+            for (int k = 4 * ti; k < h; ++k) {                  // k >= i
+                float xx[4], t[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int ii = 4 * ti + i;
+                    xx[i] = (ii < h && k >= ii) ? X[(j0 + ii) * ldu + j0 + k] : 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) t[c] = (4 * tc + c < h2) ? tp[k * h + 4 * tc + c] : 0.0f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(xx[i], t[c], acc[i][c]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (4 * ti + i < h && 4 * tc + c < h2) X[(j0 + 4 * ti + i) * ldu + j1 + 4 * tc + c] = -acc[i][c];
         }
         __syncthreads();
     }
