@@ -109,8 +109,9 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
     const long long WL = P.wait_limit > 0 ? P.wait_limit : WAIT_LIMIT;
     Bars &B = *reinterpret_cast<Bars *>(sm + OFF_BAR);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t0 = P.tiles * blockIdx.x / gridDim.x;
-    const int64_t t1 = P.tiles * (blockIdx.x + 1) / gridDim.x;
+    // tiles dealt round-robin (tile t to CTA t % grid): CTAs running at the
+    // same time write neighbouring 128-column blocks of the same 128 rows
+    const int64_t t0 = blockIdx.x, t1 = P.tiles, tstep = gridDim.x;
     if ((smem_u32(sm) & 1023u) != 0u) {
         if (threadIdx.x == 0) psd_set_status(P.d_status, PSDPROJ_ECUDA);
         return;
@@ -151,7 +152,7 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
         if (lane == 0) {
             int curI = -1, wi_uses = 0;
             int64_t it = 0;
-            for (int64_t t = t0; t < t1; ++t, ++it) {
+            for (int64_t t = t0; t < t1; t += tstep, ++it) {
                 int I, J;
                 tile_of(t, P.nb, I, J);
                 if (I != curI) {
@@ -186,10 +187,11 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
             const uint32_t id = idesc_bf16(TS, TS, 1, 1);
             int curI = -1, seg = 0;
             int64_t it = 0;
-            for (int64_t t = t0; t < t1; ++t, ++it) {
+            for (int64_t t = t0; t < t1; t += tstep, ++it) {
                 int I, J;
                 tile_of(t, P.nb, I, J);
-                const bool last = (t + 1 == t1) || (I + 1 < P.nb && t + 1 == row_start(I + 1, P.nb));
+                // the CTA's next tile is in another block row (or there is none)
+                const bool last = (t + tstep >= t1) || (I + 1 < P.nb && t + tstep >= row_start(I + 1, P.nb));
                 if (I != curI) {
                     if (!mbar_wait(&B.fullWI, seg & 1, abort, WL)) { fail(B, P.d_status); break; }
                     curI = I;
@@ -231,7 +233,7 @@ syrk_bf16x3_kernel(const __grid_constant__ CUtensorMap tmHi, const __grid_consta
         const int q = warp & 3;               // TMEM lane quarter
         const int g = (warp - 4) >> 2;        // column half of the tile
         int64_t it = 0;
-        for (int64_t t = t0; t < t1; ++t, ++it) {
+        for (int64_t t = t0; t < t1; t += tstep, ++it) {
             int I, J;
             tile_of(t, P.nb, I, J);
             const int b = (int)(it & 1);
