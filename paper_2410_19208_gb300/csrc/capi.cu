@@ -452,7 +452,7 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         {
             stage_scope st(ctx, PSDPROJ_STAGE_EIG);
             PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, opts.eig,
-                              ws.ints + IN_EIGFAIL), opts.eig == PSDPROJ_EIG_AUTO ? 2 : 1);
+                              ws.ints + IN_EIGFAIL), psd_eig_launches(opts.eig));
         }
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
         PSD_KL(launch_ritz_alpha(s, ws.d, m, d_alpha_out ? d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
@@ -482,7 +482,7 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     {
         stage_scope st(ctx, PSDPROJ_STAGE_EIG);
         PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, opts.eig,
-                          ws.ints + IN_EIGFAIL), opts.eig == PSDPROJ_EIG_AUTO ? 2 : 1);
+                          ws.ints + IN_EIGFAIL), psd_eig_launches(opts.eig));
     }
     int *rk = ws.ints + IN_RANK;
     float *Wd = dW ? dW : ws.W;
@@ -1193,7 +1193,7 @@ int psdproj_eig_method(psdproj_ctx *ctx, const double *dC, int m, float *dV, dou
     PSD_TRY(psd_ensure_workspace(ctx, 1, m));
     stage_scope st(ctx, PSDPROJ_STAGE_EIG);
     PSD_KL(launch_eig(ctx->stream, dC, m, dV, dd, ctx->ws.eigscr, ctx->d_status, method,
-                      ctx->ws.ints + IN_EIGFAIL), method == PSDPROJ_EIG_AUTO ? 2 : 1);
+                      ctx->ws.ints + IN_EIGFAIL), psd_eig_launches(method));
     return PSDPROJ_OK;
 }
 

@@ -18,7 +18,11 @@
 //      V <- V (3I - V^T V)/2: the twisted vectors of neighbouring eigenvalues
 //      are orthogonal only to ~eps ||T|| / gap (~1e-5 here); the step makes
 //      the error quadratic (~1e-10) and mixes each pair symmetrically, which
-//      moves V Lambda_+ V^T by O(eps ||T||) only.
+//      moves V Lambda_+ V^T by O(eps ||T||) only.  It runs on the sorted
+//      output (it commutes with reordering the columns, and leaves the unit
+//      columns of removed zero rows alone) in two many-block kernels,
+//      ns_gram_kernel (S = (3I - V^T V)/2, the orthogonality check) and
+//      ns_apply_kernel (V S).
 // Output as the Jacobi solver: V (m x m column-major, orthonormal columns)
 // and the eigenvalues, sorted by decreasing eigenvalue.  *d_fail is set to
 // 1 when a vector is not finite, a twisted residual is large, or V^T V is
@@ -195,11 +199,9 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     __shared__ int cl_start[PSD_MAX_M];
     __shared__ int s_pos[PSD_MAX_M], s_src[PSD_MAX_M];
     __shared__ int s_fail, s_mc;
-    __shared__ unsigned s_dev;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         s_fail = 0;
-        s_dev = 0u;
     }
 
     for (int e0 = tid; e0 < mfull * mfull; e0 += NT) {
@@ -700,65 +702,8 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     }
 
     // ---------------------------------------------------------------- 5
-    // S = (3I - Z^T Z)/2 into T, then Z S into A
-    // 8 x 8 register tiles; loads past column m - 1 or row m - 1 read the
-    // next row or the slack after the buffers and only feed entries that are
-    // not stored
-    const int nt8 = (m + 7) >> 3;
-    for (int q = tid; q < nt8 * nt8; q += NT) {
-        const int a0 = (q / nt8) * 8, b0 = (q - (q / nt8) * nt8) * 8;
-        float acc[8][8] = {};
-        for (int i = 0; i < m; ++i) {
-            const float *zr = Z + i * ld;
-            float x[8], y[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                x[u] = zr[a0 + u];
-                y[u] = zr[b0 + u];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
-        }
-        float dev = 0.0f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                const int a = a0 + u, b = b0 + v;
-                if (a < m && b < m) {
-                    const float g = acc[u][v] - (a == b ? 1.0f : 0.0f);
-                    dev = fmaxf(dev, isfinite(g) ? fabsf(g) : 3.0e38f);
-                    T[a * ld + b] = -0.5f * g + (a == b ? 1.0f : 0.0f);
-                }
-            }
-        atomicMax(&s_dev, __float_as_uint(dev));
-    }
-    __syncthreads();
-    for (int q = tid; q < nt8 * nt8; q += NT) {
-        const int i0 = (q / nt8) * 8, b0 = (q - (q / nt8) * nt8) * 8;
-        float acc[8][8] = {};
-        for (int a = 0; a < m; ++a) {
-            const float *sr = T + a * ld;
-            float x[8], y[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                x[u] = Z[(i0 + u) * ld + a];
-                y[u] = sr[b0 + u];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int v = 0; v < 8; ++v)
-                if (i0 + u < m && b0 + v < m) A[(i0 + u) * ld + b0 + v] = acc[u][v];
-    }
-    __syncthreads();
+    // the Newton-Schulz step runs after the output, in ns_gram_kernel and
+    // ns_apply_kernel (many blocks; it commutes with the column ordering)
 
     }  // m > 0
 
@@ -766,7 +711,7 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     // exact zeros of the removed rows, then the rest of the block (lam is
     // ascending).  s_src[position] = block index k, or -(i+1) for removed row i.
     if (tid == 0) {
-        int bad = s_fail || !(__uint_as_float(s_dev) <= 1e-2f);
+        int bad = s_fail;
         int npos = 0;
         for (int k = 0; k < m; ++k) {
             bad |= !isfinite(lam[k]);
@@ -785,7 +730,7 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
         const int row = e0 % mfull, col = e0 / mfull;
         const int src = s_src[col];
         float v;
-        if (src >= 0) v = s_pos[row] >= 0 ? A[s_pos[row] * ld + src] : 0.0f;
+        if (src >= 0) v = s_pos[row] >= 0 ? Z[s_pos[row] * ld + src] : 0.0f;
         else v = (row == -src - 1) ? 1.0f : 0.0f;
         Vout[(int64_t)col * mfull + row] = v;
     }
@@ -793,6 +738,83 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
         const int src = s_src[col];
         dout[col] = src >= 0 ? (double)lam[src] : 0.0;
     }
+}
+
+}  // namespace
+
+namespace {
+
+// V (m x m, column-major): S = (3I - V^T V)/2 and a copy of V (blocks of the
+// first block column), both m x m column-major; a block of 16 x 16 entries of
+// V^T V per 256 threads, columns staged 32 rows at a time.  V^T V further than
+// 1e-2 from I (or not finite) fails the solver: *d_fail = 1 and, when asked,
+// ENOCONV.
+__global__ void __launch_bounds__(256)
+ns_gram_kernel(const float *__restrict__ V, int m, float *__restrict__ S, float *__restrict__ Vc, int *d_fail,
+               int *d_status_on_fail)
+{
+    __shared__ float Va[32][17], Vb[32][17];
+    __shared__ float s_dev[8];
+    const int a0 = blockIdx.x * 16, b0 = blockIdx.y * 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc = 0.0f;
+    for (int r0 = 0; r0 < m; r0 += 32) {
+        for (int e = threadIdx.x; e < 512; e += 256) {
+            const int c = e >> 5, r = e & 31;
+            const bool okr = r0 + r < m;
+            const float va = (okr && a0 + c < m) ? V[(int64_t)(a0 + c) * m + r0 + r] : 0.0f;
+            Va[r][c] = va;
+            Vb[r][c] = (okr && b0 + c < m) ? V[(int64_t)(b0 + c) * m + r0 + r] : 0.0f;
+            if (blockIdx.y == 0 && okr && a0 + c < m) Vc[(int64_t)(a0 + c) * m + r0 + r] = va;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) acc = fmaf(Va[r][ty], Vb[r][tx], acc);
+        __syncthreads();
+    }
+    const int a = a0 + ty, b = b0 + tx;
+    float dev = 0.0f;
+    if (a < m && b < m) {
+        const float g = acc - (a == b ? 1.0f : 0.0f);
+        dev = isfinite(g) ? fabsf(g) : 3.0e38f;
+        S[(int64_t)b * m + a] = (a == b ? 1.0f : 0.0f) - 0.5f * g;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if ((threadIdx.x & 31) == 0) s_dev[threadIdx.x >> 5] = dev;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mx = 0.0f;
+        for (int w = 0; w < 8; ++w) mx = fmaxf(mx, s_dev[w]);
+        if (!(mx <= 1e-2f)) {
+            *d_fail = 1;
+            if (d_status_on_fail) psd_set_status(d_status_on_fail, PSDPROJ_ENOCONV);
+        }
+    }
+}
+
+// Vout = V S (m x m, column-major): a block of 16 x 16 entries per 256 threads
+__global__ void __launch_bounds__(256)
+ns_apply_kernel(const float *__restrict__ V, const float *__restrict__ S, int m, float *__restrict__ Vout)
+{
+    __shared__ float Vr[16][33], Sc[32][17];
+    const int r0 = blockIdx.x * 16, c0 = blockIdx.y * 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc = 0.0f;
+    for (int k0 = 0; k0 < m; k0 += 32) {
+        for (int e = threadIdx.x; e < 512; e += 256) {
+            const int k = e >> 4, r = e & 15;                 // V(r0 + r, k0 + k)
+            Vr[r][k] = (r0 + r < m && k0 + k < m) ? V[(int64_t)(k0 + k) * m + r0 + r] : 0.0f;
+            const int kk = e & 31, c = e >> 5;                // S(k0 + kk, c0 + c)
+            Sc[kk][c] = (k0 + kk < m && c0 + c < m) ? S[(int64_t)(c0 + c) * m + k0 + kk] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) acc = fmaf(Vr[tx][k], Sc[k][ty], acc);
+        __syncthreads();
+    }
+    const int r = r0 + tx, c = c0 + ty;
+    if (r < m && c < m) Vout[(int64_t)c * m + r] = acc;
 }
 
 }  // namespace
@@ -809,5 +831,15 @@ cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V,
                                          (int)smem_max);
     if (e != cudaSuccess) return e;
     eig_tridiag_kernel<<<1, NT, smem, s>>>(C, m, V, d, scratch, d_fail, d_status_on_fail);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the Newton-Schulz step on the output (scratch: S, then the copy of V;
+    // the tridiagonal kernel's use of it is over)
+    const dim3 g((unsigned)((m + 15) / 16), (unsigned)((m + 15) / 16));
+    float *S = scratch, *Vc = scratch + (size_t)m * m;
+    ns_gram_kernel<<<g, 256, 0, s>>>(V, m, S, Vc, d_fail, d_status_on_fail);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ns_apply_kernel<<<g, 256, 0, s>>>(Vc, S, m, V);
     return cudaGetLastError();
 }

@@ -234,7 +234,7 @@ gram_upper_kernel(const float *__restrict__ X, int64_t ldx, const float *__restr
     const int ld = mp + 4;
     float *Xs = sgu;                       // SR x ld
     float *Zs = sgu + SR * ld;             // (two-sided form)
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int nt8 = mp / 8, ntiles = nt8 * (nt8 + 1) / 2;
     int bi = 0, bj = 0;
     {
