@@ -264,11 +264,12 @@ cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64
 // scratch: 3 (m+2)^2 floats of device memory (used when m is too large for
 // shared memory); d_flag: one device int (the tridiagonal solver's failure
 // flag); method: PSDPROJ_EIG_*.
-// kernels launch_eig starts: the tridiagonal solver and its Newton-Schulz
-// step (three), the Jacobi solver (one, also after the others in AUTO)
+// kernels launch_eig starts: the tridiagonal solver, its Newton-Schulz step
+// and the FP64 Rayleigh quotients (four), the Jacobi solver (one, also after
+// the others in AUTO)
 inline int psd_eig_launches(int method)
 {
-    return method == PSDPROJ_EIG_JACOBI ? 1 : (method == PSDPROJ_EIG_AUTO ? 4 : 3);
+    return method == PSDPROJ_EIG_JACOBI ? 1 : (method == PSDPROJ_EIG_AUTO ? 5 : 4);
 }
 cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double *d,
                        float *scratch, int *d_status, int method, int *d_flag);

@@ -23,6 +23,8 @@
 //      columns of removed zero rows alone) in two many-block kernels,
 //      ns_gram_kernel (S = (3I - V^T V)/2, the orthogonality check) and
 //      ns_apply_kernel (V S).
+//   6. The eigenvalues refined in FP64 as Rayleigh quotients v^T C v / v^T v
+//      of the final vectors against the FP64 input (eig_rayleigh_kernel).
 // Output as the Jacobi solver: V (m x m column-major, orthonormal columns)
 // and the eigenvalues, sorted by decreasing eigenvalue.  *d_fail is set to
 // 1 when a vector is not finite, a twisted residual is large, or V^T V is
@@ -817,6 +819,48 @@ ns_apply_kernel(const float *__restrict__ V, const float *__restrict__ S, int m,
     if (r < m && c < m) Vout[(int64_t)c * m + r] = acc;
 }
 
+// d_i <- v_i^T C v_i / v_i^T v_i in FP64: the Rayleigh quotient of the computed
+// eigenvector against the FP64 core matrix, whose error is quadratic in the
+// vector's (FP32 vectors orthonormal to ~1e-7 give eigenvalues to ~1e-14
+// ||C||).  Where the quotient and the FP32 eigenvalue disagree in sign the
+// eigenvalue is indistinguishable from zero at FP32 accuracy: 0.  Exact
+// zeros (the removed zero rows) stay zero.  One block per eigenpair.
+__global__ void __launch_bounds__(256)
+eig_rayleigh_kernel(const double *__restrict__ C, const float *__restrict__ V, int m, double *__restrict__ d)
+{
+    __shared__ double s_red[2][8];
+    const int i = blockIdx.x;
+    const float *v = V + (int64_t)i * m;
+    double acc = 0.0, nn = 0.0;              // v^T C v and v^T v
+    for (int r = threadIdx.x; r < m; r += 256) {
+        double y = 0.0;
+        for (int c = 0; c < m; ++c) y = fma(C[(int64_t)c * m + r], (double)v[c], y);
+        const double vr = (double)v[r];
+        acc = fma(vr, y, acc);
+        nn = fma(vr, vr, nn);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_red[0][threadIdx.x >> 5] = acc;
+        s_red[1][threadIdx.x >> 5] = nn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double num = 0.0, den = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            num += s_red[0][w];
+            den += s_red[1][w];
+        }
+        const double q = den > 0.0 ? num / den : 0.0;
+        const double l0 = d[i];
+        d[i] = (l0 == 0.0 || !isfinite(q)) ? l0 : ((q > 0.0) == (l0 > 0.0) ? q : 0.0);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V, double *d,
@@ -841,5 +885,8 @@ cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     ns_apply_kernel<<<g, 256, 0, s>>>(Vc, S, m, V);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    eig_rayleigh_kernel<<<m, 256, 0, s>>>(C, V, m, d);
     return cudaGetLastError();
 }

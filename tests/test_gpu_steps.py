@@ -242,8 +242,16 @@ def test_eig_matches_lapack(ctx, m, method):
     Vv = V.cpu().numpy().T.astype(np.float64)  # column-major -> (row, col)
     ref = np.linalg.eigvalsh(C)[::-1]
     nrm = np.linalg.norm(C)
-    assert np.all(np.diff(dv) <= 0)
-    assert np.abs(dv - ref).max() <= 2e-6 * nrm
+    if method == ps.EIG_JACOBI:
+        assert np.all(np.diff(dv) <= 0)
+        assert np.abs(dv - ref).max() <= 2e-6 * nrm
+    else:
+        # the tridiagonal solver refines its eigenvalues in FP64 (Rayleigh
+        # quotients of the FP32 vectors, error quadratic in theirs): within
+        # 1e-9 ||C|| of LAPACK, against 2e-6 for FP32 eigenvalues; the
+        # ordering is the FP32 one, so values closer than that may swap
+        assert np.all(np.diff(dv) <= 1e-9 * nrm)
+        assert np.abs(dv - ref).max() <= 1e-9 * nrm
     assert np.abs(Vv.T @ Vv - np.eye(m)).max() <= 2e-5
     assert np.linalg.norm(Vv @ np.diag(dv) @ Vv.T - C) <= 5e-6 * nrm * np.sqrt(m)
 
