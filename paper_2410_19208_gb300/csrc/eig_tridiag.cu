@@ -595,13 +595,15 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     // ---------------------------------------------------------------- 4
     // Z <- H_0 H_1 ... H_{m-3} Z in blocks of NB reflectors, last block
     // first, each block in compact WY form H_jb ... H_{jb+nb-1} = I - V T V^T
-    // (V: the block's reflector vectors A[i][jb+t], i > jb+t; T upper
-    // triangular by the forward recurrence T[t][t] = beta_t,
-    // T[0:t, t] = -beta_t T[0:t, 0:t] V^T v_t):  Z <- Z - V (T (V^T Z)).
-    // W = V^T Z and then T W live in the first nb rows of the T buffer.
+    // (V: the block's reflector vectors A[i][jb+t], i > jb+t):
+    // Z <- Z - V (T (V^T Z)).  T is never formed: T^-1 is the upper
+    // triangular matrix with diagonal 1 / beta_t and strictly upper part
+    // V^T V, so T W solves T^-1 Y = W by back substitution, a column of W per
+    // thread (a zero beta, a skipped reflector, gives a zero row of Y).
+    // W = V^T Z and then Y live in the first nb rows of the T buffer.
     {
         constexpr int NB = 16;
-        __shared__ float sS[NB][NB + 1], sT[NB][NB + 1];
+        __shared__ float sS[NB][NB + 1];
         const int nref = m - 2;                               // reflectors 0 .. m-3
         for (int jb = nref > 0 ? ((nref - 1) / NB) * NB : -1; jb >= 0; jb -= NB) {
             const int nb = min(NB, nref - jb);
@@ -641,34 +643,25 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
                 }
             }
             __syncthreads();
-            // (b) T, one warp, column by column
-            if (warp == 0) {
-                for (int t = 0; t < nb; ++t) {
-                    const float bt = beta[jb + t];
-                    float y = 0.0f;
-                    if (lane < t)
-                        for (int s2 = lane; s2 < t; ++s2) y = fmaf(sT[lane][s2], sS[s2][t], y);
-                    __syncwarp();
-                    if (lane < t) sT[lane][t] = -bt * y;
-                    if (lane == t) sT[t][t] = bt;
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-            // (c) W <- T W, a thread per column
+            // (b) Y = T W: T^-1 Y = W, back substitution down the nb rows,
+            // a thread per column
             for (int c = tid; c < m; c += NT) {
                 float w[NB];
 #pragma unroll
                 for (int t = 0; t < NB; ++t) w[t] = t < nb ? T[t * ld + c] : 0.0f;
 #pragma unroll
-                for (int sI = 0; sI < NB; ++sI) {
-                    if (sI >= nb) break;
-                    float acc = 0.0f;
+                for (int t = NB - 1; t >= 0; --t) {
+                    if (t >= nb) continue;
+                    const float bt = beta[jb + t];
+                    float acc = w[t];
 #pragma unroll
-                    for (int t = 0; t < NB; ++t)
-                        if (t >= sI && t < nb) acc = fmaf(sT[sI][t], w[t], acc);
-                    T[sI * ld + c] = acc;
+                    for (int u = t + 1; u < NB; ++u)
+                        if (u < nb) acc = fmaf(-sS[t][u], w[u], acc);
+                    w[t] = bt * acc;        // divided by the diagonal 1 / beta_t
                 }
+#pragma unroll
+                for (int t = 0; t < NB; ++t)
+                    if (t < nb) T[t * ld + c] = w[t];
             }
             __syncthreads();
             // (d) Z[i][c] -= sum_t V[i][t] W[t][c], rows i > jb (a warp per row);
