@@ -275,6 +275,31 @@ int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *pr
  * workspace, sized for the largest problem it has run. */
 int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams);
 
+/* Batch autotuning.  psdproj_tune_batch runs `probs` (as psdproj_batched_graph
+ * does) on 2, 4, 8 and 16 helper streams, one recording run and `reps` timed
+ * replays each on the context's stream, keeps the fastest, sets it on the
+ * context (as psdproj_set_batch_streams) and stores it in the tuning table
+ * under the batch's bucket: (device name, SM count, floor(log2 of the median
+ * side), floor(log2 of count)).  Synchronises the context's stream; the
+ * results in P and W are those of the last run.  *best_streams and *best_ms
+ * (time per batch; either may be NULL) report the choice.
+ *
+ * psdproj_batched and psdproj_batched_graph use, in this order: the
+ * environment variable PSDPROJ_BATCH_STREAMS (1..16); the context's own lane
+ * count if set; the tuning table's entry for the batch's bucket; the default
+ * 8.  The table lives in the process and, when PSDPROJ_TUNE_CACHE names a
+ * file, in that file (one "key<TAB>streams" line per entry; when the
+ * variable names another file the table becomes that file's contents; every
+ * store rewrites the file).  psdproj_tune_lookup
+ * (EINVAL when there is no entry) and psdproj_tune_store read and write it
+ * directly; neither needs a GPU. */
+int psdproj_tune_batch(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
+                       const psdproj_opts *opts, int reps, int *best_streams, double *best_ms);
+int psdproj_tune_lookup(const char *device_name, int sm_count, int64_t median_n, int count,
+                        int *streams);
+int psdproj_tune_store(const char *device_name, int sm_count, int64_t median_n, int count,
+                       int streams);
+
 /* SMs that this context's persistent kernels (the tensor-core passes, the
  * BF16 power iteration, the SYRK) leave free: 0 .. SMs - 1, default 1; also
  * applied to the context's batch helpers.  A persistent grid that finds no

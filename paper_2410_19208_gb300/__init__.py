@@ -107,6 +107,9 @@ def _load():
         "psdproj_batched": (_int, [_P, _int, _P, _P]),
         "psdproj_batched_graph": (_int, [_P, _int, _P, _P]),
         "psdproj_set_batch_streams": (_int, [_P, _int]),
+        "psdproj_tune_batch": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double)]),
+        "psdproj_tune_lookup": (_int, [ctypes.c_char_p, _int, _i64, _int, ctypes.POINTER(_int)]),
+        "psdproj_tune_store": (_int, [ctypes.c_char_p, _int, _i64, _int, _int]),
         "psdproj_set_reserved_sms": (_int, [_P, _int]),
         "psdproj_alg2": (_int, [_P, _P, _i64, _i64, _int, _int, _int, _u64, ctypes.c_double,
                                 _P, _P, _P, _i64, _P, _i64, _P, ctypes.POINTER(Opts)]),
@@ -252,11 +255,8 @@ class Context:
                                     _ptr(rank), ctypes.byref(opts) if opts else None),
                "psdproj_alg2")
 
-    def batched(self, problems, opts: Opts | None = None, graph: bool = False):
-        """problems: list of dicts with keys A, k, p, q, seed, algorithm (1 or 2) and
-        optional P, W, rank, alpha_in, alpha_out, info (device tensors).
-        graph=True: psdproj_batched_graph (recorded once into a CUDA graph and
-        replayed while the table is unchanged)."""
+    @staticmethod
+    def _problem_table(problems):
         arr = (Problem * max(1, len(problems)))()
         for i, d in enumerate(problems):
             A = d["A"]
@@ -266,6 +266,14 @@ class Context:
                              float(d.get("alpha_in", 0.0)), _ptr(d.get("alpha_out")), _ptr(d.get("info")),
                              _ptr(P), P.stride(0) if P is not None else n,
                              _ptr(W), _tall(W, "W")[2] if W is not None else n, _ptr(d.get("rank")))
+        return arr
+
+    def batched(self, problems, opts: Opts | None = None, graph: bool = False):
+        """problems: list of dicts with keys A, k, p, q, seed, algorithm (1 or 2) and
+        optional P, W, rank, alpha_in, alpha_out, info (device tensors).
+        graph=True: psdproj_batched_graph (recorded once into a CUDA graph and
+        replayed while the table is unchanged)."""
+        arr = self._problem_table(problems)
         fn = _load().psdproj_batched_graph if graph else _load().psdproj_batched
         _check(fn(self.h, len(problems), ctypes.byref(arr), ctypes.byref(opts) if opts else None),
                "psdproj_batched_graph" if graph else "psdproj_batched")
@@ -290,6 +298,15 @@ class Context:
                                             ctypes.byref(it), ctypes.byref(gn), hist,
                                             ctypes.byref(opts) if opts else None), "psdproj_sdls_dual_gd")
         return dict(y=list(y), iters=it.value, gnorm=gn.value, hist=list(hist)[: it.value])
+
+    def tune_batch(self, problems, opts: Opts | None = None, reps: int = 3):
+        """psdproj_tune_batch: returns (best lane count, ms per batch)."""
+        arr = self._problem_table(problems)
+        best, ms = _int(), ctypes.c_double()
+        _check(_load().psdproj_tune_batch(self.h, len(problems), ctypes.byref(arr),
+                                          ctypes.byref(opts) if opts else None, reps,
+                                          ctypes.byref(best), ctypes.byref(ms)), "psdproj_tune_batch")
+        return best.value, ms.value
 
     def set_batch_streams(self, streams: int):
         _check(_load().psdproj_set_batch_streams(self.h, streams), "psdproj_set_batch_streams")
@@ -419,3 +436,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tune_lookup(device_name: str, sm_count: int, median_n: int, count: int):
+    """The tuning table's lane count for a batch bucket, or None."""
+    v = _int()
+    rc = _load().psdproj_tune_lookup(device_name.encode(), sm_count, median_n, count, ctypes.byref(v))
+    return v.value if rc == 0 else None
+
+
+def tune_store(device_name: str, sm_count: int, median_n: int, count: int, streams: int):
+    _check(_load().psdproj_tune_store(device_name.encode(), sm_count, median_n, count, streams),
+           "psdproj_tune_store")

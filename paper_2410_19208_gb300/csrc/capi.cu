@@ -15,6 +15,9 @@
 #include <vector>
 #include <algorithm>
 #include <new>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "ctx.h"
 
@@ -664,6 +667,122 @@ int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams)
 {
     if (!ctx || streams < 1 || streams > PSD_MAX_LANES) return PSDPROJ_EINVAL;
     ctx->batch_streams = streams;
+    ctx->lanes_explicit = true;
+    return PSDPROJ_OK;
+}
+
+// ---- batch tuning table ----------------------------------------------------
+// (device name, SM count, floor(log2 median side), floor(log2 count)) ->
+// lane count; kept in memory and, when PSDPROJ_TUNE_CACHE names a file, in
+// that file (one "key<TAB>streams" line per entry); when the variable names
+// another file than the one last read, the table becomes that file's contents.
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+std::string g_tune_file;          // the file g_tune was last read from
+
+int ilog2(int64_t x)
+{
+    int r = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+std::string tune_key(const char *device, int sm_count, int64_t median_n, int count)
+{
+    std::string name = device ? device : "";
+    for (char &c : name)
+        if (c == ' ' || c == '\t' || c == '\n') c = '_';
+    return name + ":" + std::to_string(sm_count) + ":" + std::to_string(ilog2(median_n)) + ":" +
+           std::to_string(ilog2(count));
+}
+
+// with g_tune_mu held
+void tune_sync_file()
+{
+    const char *f = getenv("PSDPROJ_TUNE_CACHE");
+    const std::string path = f ? f : "";
+    if (path == g_tune_file) return;
+    // another file: the table becomes its contents
+    g_tune_file = path;
+    g_tune.clear();
+    if (path.empty()) return;
+    FILE *fp = fopen(path.c_str(), "r");
+    if (!fp) return;
+    char line[512];
+    while (fgets(line, sizeof line, fp)) {
+        char *tab = strchr(line, '\t');
+        if (!tab) continue;
+        *tab = 0;
+        const int v = atoi(tab + 1);
+        if (v >= 1 && v <= PSD_MAX_LANES) g_tune[line] = v;
+    }
+    fclose(fp);
+}
+
+int env_batch_streams()
+{
+    const char *e = getenv("PSDPROJ_BATCH_STREAMS");
+    if (!e) return 0;
+    const int v = atoi(e);
+    return (v >= 1 && v <= PSD_MAX_LANES) ? v : 0;
+}
+
+struct dev_ident {
+    char name[256];
+    int sms;
+};
+
+dev_ident device_ident(int device)
+{
+    dev_ident d{};
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) {
+        snprintf(d.name, sizeof d.name, "%s", prop.name);
+        d.sms = prop.multiProcessorCount;
+    } else {
+        snprintf(d.name, sizeof d.name, "device%d", device);
+    }
+    return d;
+}
+
+int64_t median_side(int count, const psdproj_problem *probs)
+{
+    std::vector<int64_t> v((size_t)count);
+    for (int i = 0; i < count; ++i) v[(size_t)i] = probs[i].n;
+    std::nth_element(v.begin(), v.begin() + count / 2, v.end());
+    return v[(size_t)count / 2];
+}
+
+}  // namespace
+
+int psdproj_tune_lookup(const char *device_name, int sm_count, int64_t median_n, int count, int *streams)
+{
+    if (!device_name || !streams || median_n < 1 || count < 1) return PSDPROJ_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_sync_file();
+    const auto it = g_tune.find(tune_key(device_name, sm_count, median_n, count));
+    if (it == g_tune.end()) return PSDPROJ_EINVAL;
+    *streams = it->second;
+    return PSDPROJ_OK;
+}
+
+int psdproj_tune_store(const char *device_name, int sm_count, int64_t median_n, int count, int streams)
+{
+    if (!device_name || median_n < 1 || count < 1 || streams < 1 || streams > PSD_MAX_LANES) return PSDPROJ_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_sync_file();
+    g_tune[tune_key(device_name, sm_count, median_n, count)] = streams;
+    if (!g_tune_file.empty()) {
+        FILE *fp = fopen(g_tune_file.c_str(), "w");
+        if (!fp) return PSDPROJ_EINVAL;
+        for (const auto &kv : g_tune) fprintf(fp, "%s\t%d\n", kv.first.c_str(), kv.second);
+        fclose(fp);
+    }
     return PSDPROJ_OK;
 }
 
@@ -838,10 +957,26 @@ int batch_validate(const psdproj_opts &opts, int count, const psdproj_problem *p
     return PSDPROJ_OK;
 }
 
-batch_plan batch_make_plan(const psdproj_ctx *ctx, const psdproj_opts &opts, int count, const psdproj_problem *probs)
+// The lane count of a batch: PSDPROJ_BATCH_STREAMS if set; a trial of
+// psdproj_tune_batch; the context's own setting if it was made
+// (psdproj_set_batch_streams, or a finished tuning); the tuning table's entry
+// for the batch's bucket; else the default (8).
+int batch_lanes(const psdproj_ctx *ctx, int count, const psdproj_problem *probs)
+{
+    if (const int e = env_batch_streams()) return e;
+    if (ctx->tune_force > 0) return ctx->tune_force;
+    if (ctx->lanes_explicit || count < 1) return ctx->batch_streams;
+    const dev_ident d = device_ident(ctx->device);
+    int v = 0;
+    if (psdproj_tune_lookup(d.name, d.sms, median_side(count, probs), count, &v) == PSDPROJ_OK) return v;
+    return ctx->batch_streams;
+}
+
+batch_plan batch_make_plan(const psdproj_ctx *ctx, const psdproj_opts &opts, int count, const psdproj_problem *probs,
+                           int lanes)
 {
     batch_plan pl;
-    pl.S = count < ctx->batch_streams ? count : ctx->batch_streams;
+    pl.S = count < lanes ? count : lanes;
     pl.order.resize(count);
     pl.lane_of.assign(count, 0);
     std::vector<double> cost(count), load(pl.S > 0 ? pl.S : 1, 0.0);
@@ -946,7 +1081,7 @@ int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
     PSD_TRY(batch_validate(opts, count, probs, nmax, mmax));
     if (count == 0) return PSDPROJ_OK;
     device_guard g(ctx->device);
-    const batch_plan pl = batch_make_plan(ctx, opts, count, probs);
+    const batch_plan pl = batch_make_plan(ctx, opts, count, probs, batch_lanes(ctx, count, probs));
     if (pl.S <= 1) {
         // one workspace for the whole batch, problems one after another
         PSD_TRY(psd_ensure_workspace(ctx, nmax, mmax));
@@ -969,13 +1104,14 @@ int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *pr
     if (count == 0) return PSDPROJ_OK;
     device_guard g(ctx->device);
     // the same table, options and lane settings as the recorded graph: replay
+    const int lanes = batch_lanes(ctx, count, probs);
     const bool same = ctx->graph_exec && (int)ctx->graph_probs.size() == count &&
                       memcmp(ctx->graph_probs.data(), probs, sizeof(psdproj_problem) * (size_t)count) == 0 &&
                       memcmp(&ctx->graph_opts, &opts, sizeof(opts)) == 0 &&
-                      ctx->graph_streams == ctx->batch_streams && ctx->graph_persist == ctx->persist_sms;
+                      ctx->graph_streams == lanes && ctx->graph_persist == ctx->persist_sms;
     if (!same) {
         batch_graph_free(ctx);
-        const batch_plan pl = batch_make_plan(ctx, opts, count, probs);
+        const batch_plan pl = batch_make_plan(ctx, opts, count, probs, lanes);
         if (pl.S > 1)
             for (int j = 0; j < pl.S; ++j) PSD_TRY(ensure_lane(ctx, j));
         PSD_TRY(batch_presize(ctx, pl, opts, count, probs));
@@ -1018,12 +1154,57 @@ int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *pr
         ctx->graph_exec = exec;
         ctx->graph_probs.assign(probs, probs + count);
         ctx->graph_opts = opts;
-        ctx->graph_streams = ctx->batch_streams;
+        ctx->graph_streams = lanes;
         ctx->graph_persist = ctx->persist_sms;
         ctx->graph_launches = nk;
     }
     PSD_CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
     g_launches.fetch_add(ctx->graph_launches);
+    return PSDPROJ_OK;
+}
+
+int psdproj_tune_batch(psdproj_ctx *ctx, int count, const psdproj_problem *probs, const psdproj_opts *opts,
+                       int reps, int *best_streams, double *best_ms)
+{
+    if (!ctx || count < 1 || !probs || reps < 1) return PSDPROJ_EINVAL;
+    device_guard g(ctx->device);
+    static const int trial[] = {2, 4, 8, 16};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PSD_CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return PSDPROJ_ECUDA;
+    }
+    int best = 0, rc = PSDPROJ_OK;
+    float best_t = 0.0f;
+    for (int S : trial) {
+        if (S > PSD_MAX_LANES) continue;
+        ctx->tune_force = S;
+        rc = psdproj_batched_graph(ctx, count, probs, opts);          // records the graph, one warm-up run
+        if (rc == PSDPROJ_OK && cudaEventRecord(e0, ctx->stream) != cudaSuccess) rc = PSDPROJ_ECUDA;
+        for (int r = 0; r < reps && rc == PSDPROJ_OK; ++r) rc = psdproj_batched_graph(ctx, count, probs, opts);
+        if (rc == PSDPROJ_OK && cudaEventRecord(e1, ctx->stream) != cudaSuccess) rc = PSDPROJ_ECUDA;
+        if (rc == PSDPROJ_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = PSDPROJ_ECUDA;
+        if (rc == PSDPROJ_OK) rc = psdproj_sync_status(ctx);
+        if (rc != PSDPROJ_OK) break;
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, e0, e1);
+        t /= (float)reps;
+        if (best == 0 || t < best_t) {
+            best = S;
+            best_t = t;
+        }
+    }
+    ctx->tune_force = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != PSDPROJ_OK) return rc;
+    ctx->batch_streams = best;
+    ctx->lanes_explicit = true;
+    const dev_ident d = device_ident(ctx->device);
+    PSD_TRY(psdproj_tune_store(d.name, d.sms, median_side(count, probs), count, best));
+    if (best_streams) *best_streams = best;
+    if (best_ms) *best_ms = (double)best_t;
     return PSDPROJ_OK;
 }
 

@@ -117,6 +117,8 @@ struct psdproj_ctx {
     // workspace and images, sharing this context's status word; the batch
     // forks from `stream` to the lanes and joins back by events
     int batch_streams = 8;
+    bool lanes_explicit = false; // set by psdproj_set_batch_streams or psdproj_tune_batch
+    int tune_force = 0;          // psdproj_tune_batch: lane count under trial (0: none)
     psdproj_ctx *lane[PSD_MAX_LANES] = {};
     cudaEvent_t lane_ev[PSD_MAX_LANES + 1] = {};
     bool owns_status = true;     // false for a lane (the status word is its parent's)

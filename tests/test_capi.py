@@ -112,3 +112,28 @@ def test_server_rejects_bad_arguments_without_a_gpu(lib):
     st = ps.ServerStats()
     assert lib.psdproj_server_get_stats(None, ctypes.byref(st)) == 1
     assert lib.psdproj_server_destroy(None) == 0
+
+
+def test_tuning_table_and_its_cache_file(lib, tmp_path, monkeypatch):
+    # the batch tuning table needs no GPU: entries by bucket (log2 of the
+    # median side and of the count), kept in the file PSDPROJ_TUNE_CACHE names
+    import paper_2410_19208_gb300 as ps
+    f1 = tmp_path / "tune1.txt"
+    monkeypatch.setenv("PSDPROJ_TUNE_CACHE", str(f1))
+    assert ps.tune_lookup("Test GPU", 7, 1000, 40) is None
+    ps.tune_store("Test GPU", 7, 1000, 40, 4)
+    assert ps.tune_lookup("Test GPU", 7, 1000, 40) == 4
+    assert ps.tune_lookup("Test GPU", 7, 600, 33) == 4      # same bucket: 2^9 <= 600 < 2^10, 2^5 <= 33
+    assert ps.tune_lookup("Test GPU", 7, 2048, 40) is None   # another side bucket
+    assert ps.tune_lookup("Test GPU", 8, 1000, 40) is None   # another SM count
+    assert ps.tune_lookup("Other", 7, 1000, 40) is None
+    text = f1.read_text()
+    assert "Test_GPU:7:9:5\t4" in text
+    # a second file starts from its own contents
+    f2 = tmp_path / "tune2.txt"
+    f2.write_text("Test_GPU:7:9:5\t16\nbad line\nTest_GPU:7:3:1\t99\n")
+    monkeypatch.setenv("PSDPROJ_TUNE_CACHE", str(f2))
+    assert ps.tune_lookup("Test GPU", 7, 1000, 40) == 16
+    assert ps.tune_lookup("Test GPU", 7, 8, 2) is None       # 99 is out of range (1..16): dropped
+    with pytest.raises(RuntimeError):
+        ps.tune_store("Test GPU", 7, 1000, 40, 17)

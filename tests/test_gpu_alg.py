@@ -961,3 +961,48 @@ def test_batched_graph_replays_the_batch(ctx, oracle_lib):
         check(lambda d: d["seed"])
     finally:
         c.close()
+
+
+@pytest.mark.gpu
+def test_tune_batch_picks_a_lane_count_and_stores_it(ctx, oracle_lib, tmp_path, monkeypatch):
+    """psdproj_tune_batch times the batch on 2, 4, 8 and 16 lanes, sets the
+    fastest on the context and stores it under the batch's bucket; a fresh
+    context then finds it in the table (and in the cache file), and the last
+    run's results are correct (each factor matches a single call's)."""
+    monkeypatch.delenv("PSDPROJ_BATCH_STREAMS", raising=False)
+    monkeypatch.setenv("PSDPROJ_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    sizes = [64, 96, 130, 200, 256, 300, 400, 512] * 3
+    opts = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3)
+    probs = []
+    for i, n in enumerate(sizes):
+        Vr, lam = si.make_problem("batch", n, seed_u=70 + i, seed_lam=80 + i)
+        k = max(2, min(n // 8, 32))
+        probs.append(dict(A=si.form_A_torch(Vr, lam, "cuda"), k=k, p=8, q=1, seed=30 + i, algorithm=1 + (i % 2),
+                          P=torch.empty(n, n, device="cuda"), W=ps.tall_empty(n, k + 8)))
+    c = ps.Context(0)
+    best, ms = c.tune_batch(probs, opts=opts, reps=2)
+    assert best in (2, 4, 8, 16) and ms > 0.0
+    assert c.sync_status() == 0
+    prop = torch.cuda.get_device_properties(0)
+    med = sorted(sizes)[len(sizes) // 2]
+    assert ps.tune_lookup(prop.name, prop.multi_processor_count, med, len(sizes)) == best
+    assert (tmp_path / "tune.txt").read_text().count("\t") >= 1
+    for d in probs[:6]:
+        n = d["A"].shape[0]
+        W = ps.tall_empty(n, d["k"] + d["p"])
+        fn = ctx.alg1 if d["algorithm"] == 1 else ctx.alg2
+        fn(d["A"], d["k"], d["p"], d["q"], d["seed"], W=W, P=torch.empty(n, n, device="cuda"), opts=opts)
+        assert ctx.sync_status() == 0
+        ref = W.cpu().numpy().astype(np.float64)
+        got = d["W"].cpu().numpy().astype(np.float64)
+        rel = np.sqrt(max(oracle_lib.factor_dist2(got, ref), 0.0) / oracle_lib.factor_norm2(ref))
+        assert rel <= 2e-3, (n, rel)
+    # a new context uses the table's entry for this bucket (and the override wins)
+    c2 = ps.Context(0)
+    c2.batched(probs, opts=opts, graph=True)
+    assert c2.sync_status() == 0
+    monkeypatch.setenv("PSDPROJ_BATCH_STREAMS", "3")
+    c2.batched(probs, opts=opts)
+    assert c2.sync_status() == 0
+    c.close()
+    c2.close()
