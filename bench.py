@@ -355,6 +355,12 @@ def run_batched(args, emit=True):
             raise SystemExit("device status set during the graph batched run")
         per[f"graph{S}"] = {"value": len(probs) * steps / (ms / 1e3), "ms_per_step": ms / steps,
                             "gpu_launches": int(ps.lib().psdproj_kernel_launches() - l0), "clocks": None}
+    # the autotuner (psdproj_tune_batch) picks a lane count for this batch's
+    # bucket from graph replays; the choice and its time are reported beside
+    # the fixed counts
+    tuned_S, tuned_ms = ctx.tune_batch(probs, opts=opts, reps=3)
+    if ctx.sync_status() != 0:
+        raise SystemExit("device status set during the batch autotuning")
     best = max(per, key=lambda S: per[S]["value"])
     # HBM roofline of the batch: the algorithmic bytes of every projection
     # (BF16 form: the pack reads A's upper triangle and writes the image, 6 B
@@ -381,6 +387,8 @@ def run_batched(args, emit=True):
             "config": {"workload": f"psdproj_batched (graph: psdproj_batched_graph), {len(probs)} problems per "
                                    "step, batch recipe, k = min(n/8, 64), p = 8, q = 1, Alg. 1 / Alg. 2 alternating",
                        "helper_streams": best, "batch_bytes_A": nbytes,
+                       "autotuned": {"helper_streams": tuned_S, "ms_per_batch": tuned_ms,
+                                     "value": len(probs) / (tuned_ms / 1e3) if tuned_ms > 0 else None},
                        "l2": "inputs larger than L2 (the batch's A is %.2f GB)" % (nbytes / 1e9)},
             "by_streams": {str(S): per[S] for S in per}, "roofline": roof,
             "gpu_launches": per[best]["gpu_launches"], "clocks": per[best]["clocks"] or per[1]["clocks"]}
