@@ -288,7 +288,8 @@ def run_batched(args, emit=True):
     (batch recipe: sides log-uniform in [64, 2048], k = min(n/8, 64), p = 8,
     q = 1, the two algorithms alternating) through one psdproj_batched call per
     step, timed with CUDA events on the context's stream; the same batch with
-    1, 4, 8 and 16 helper streams."""
+    1, 4, 8 and 16 helper streams, replayed from a CUDA graph, and grouped
+    (psdproj_batched_grouped)."""
     import numpy as np
     import torch
     import paper_2410_19208_gb300 as ps
@@ -355,6 +356,32 @@ def run_batched(args, emit=True):
             raise SystemExit("device status set during the graph batched run")
         per[f"graph{S}"] = {"value": len(probs) * steps / (ms / 1e3), "ms_per_step": ms / steps,
                             "gpu_launches": int(ps.lib().psdproj_kernel_launches() - l0), "clocks": None}
+    # the grouped batch (psdproj_batched_grouped): the small steps of all
+    # problems as one launch per step, the streaming steps on the lanes, the
+    # whole batch recorded once into a CUDA graph and replayed
+    for S in (8, 16):
+        ctx.set_batch_streams(S)
+        for _ in range(max(args.warmup, 3)):
+            ctx.batched(probs, opts=opts, grouped=True)
+        if ctx.sync_status() != 0:
+            raise SystemExit("device status set during the grouped batched warm-up")
+        steps = max(2, args.steps // 4)
+        sampler = ClockSampler(0)
+        sampler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ps.lib().psdproj_kernel_launches()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.batched(probs, opts=opts, grouped=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        if ctx.sync_status() != 0:
+            raise SystemExit("device status set during the grouped batched run")
+        per[f"grouped{S}"] = {"value": len(probs) * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                              "gpu_launches": int(ps.lib().psdproj_kernel_launches() - l0), "clocks": clocks}
     # the autotuner (psdproj_tune_batch) picks a lane count for this batch's
     # bucket from graph replays; the choice and its time are reported beside
     # the fixed counts
@@ -384,7 +411,8 @@ def run_batched(args, emit=True):
             "value": per[best]["value"], "unit": "projections/s", "n_gpus": 1, "steps": max(1, args.steps // 4),
             "warmup": max(args.warmup, 3), "ms_per_step": per[best]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAMES[prec], "data": "synthetic",
-            "config": {"workload": f"psdproj_batched (graph: psdproj_batched_graph), {len(probs)} problems per "
+            "config": {"workload": f"psdproj_batched (graph: psdproj_batched_graph; grouped: "
+                                   f"psdproj_batched_grouped), {len(probs)} problems per "
                                    "step, batch recipe, k = min(n/8, 64), p = 8, q = 1, Alg. 1 / Alg. 2 alternating",
                        "helper_streams": best, "batch_bytes_A": nbytes,
                        "autotuned": {"helper_streams": tuned_S, "ms_per_batch": tuned_ms,

@@ -270,6 +270,26 @@ int psdproj_batched(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
 int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
                           const psdproj_opts *opts);
 
+/* The same batch with its small steps grouped: every problem gets a
+ * workspace and image of its own (one allocation held by the context, sized
+ * to the sum of the problems' psdproj_projection_bytes), and the batch runs
+ * phase by phase, each phase for all problems before the next: the image,
+ * alpha (Alg. 3) and Y = (A + shift I) Omega per problem on the helper
+ * streams; then each CholeskyQR2 of Alg. 1's orthonormalisations (Gram,
+ * Cholesky, tall x small product, twice) as six grouped launches over the
+ * problems whose product it follows; the power and core products per problem
+ * on the helper streams; the core Q^T A Q, the l x l eigensolver (Alg. 2)
+ * and the factor W = Q V sqrt(max(D, 0)) as grouped launches; P = W W^T per
+ * problem.  A grouped launch runs, for each problem, the blocks its own
+ * launch would run, so results equal psdproj_batched's up to the order of
+ * the passes' floating-point additions.  Recorded once into a CUDA graph and
+ * replayed like psdproj_batched_graph (same rules for the table, settings
+ * and buffers).  Requires k + p <= 128 in every problem (else
+ * PSDPROJ_ENOTSUP) and opts.deterministic = 0 (else PSDPROJ_ENOTSUP).  The
+ * first call of a table synchronises the context's stream. */
+int psdproj_batched_grouped(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
+                            const psdproj_opts *opts);
+
 /* Number of helper streams psdproj_batched spreads a batch over (1..16,
  * default 8; 1 = the context's own stream only).  Each helper holds its own
  * workspace, sized for the largest problem it has run. */

@@ -106,6 +106,7 @@ def _load():
                                 _P, ctypes.POINTER(Opts)]),
         "psdproj_batched": (_int, [_P, _int, _P, _P]),
         "psdproj_batched_graph": (_int, [_P, _int, _P, _P]),
+        "psdproj_batched_grouped": (_int, [_P, _int, _P, _P]),
         "psdproj_set_batch_streams": (_int, [_P, _int]),
         "psdproj_tune_batch": (_int, [_P, _int, _P, _P, _int, ctypes.POINTER(_int), ctypes.POINTER(ctypes.c_double)]),
         "psdproj_tune_lookup": (_int, [ctypes.c_char_p, _int, _i64, _int, ctypes.POINTER(_int)]),
@@ -268,15 +269,17 @@ class Context:
                              _ptr(W), _tall(W, "W")[2] if W is not None else n, _ptr(d.get("rank")))
         return arr
 
-    def batched(self, problems, opts: Opts | None = None, graph: bool = False):
+    def batched(self, problems, opts: Opts | None = None, graph: bool = False, grouped: bool = False):
         """problems: list of dicts with keys A, k, p, q, seed, algorithm (1 or 2) and
         optional P, W, rank, alpha_in, alpha_out, info (device tensors).
         graph=True: psdproj_batched_graph (recorded once into a CUDA graph and
-        replayed while the table is unchanged)."""
+        replayed while the table is unchanged); grouped=True:
+        psdproj_batched_grouped (the small steps as grouped launches, also
+        recorded and replayed)."""
         arr = self._problem_table(problems)
-        fn = _load().psdproj_batched_graph if graph else _load().psdproj_batched
-        _check(fn(self.h, len(problems), ctypes.byref(arr), ctypes.byref(opts) if opts else None),
-               "psdproj_batched_graph" if graph else "psdproj_batched")
+        name = "psdproj_batched_grouped" if grouped else ("psdproj_batched_graph" if graph else "psdproj_batched")
+        _check(getattr(_load(), name)(self.h, len(problems), ctypes.byref(arr),
+                                      ctypes.byref(opts) if opts else None), name)
 
     def sdls(self, C, As, b, rho, k, p, q, algorithm, beta, eps, max_iter, seed, y0, warm_start=False,
              X=None, opts: Opts | None = None):

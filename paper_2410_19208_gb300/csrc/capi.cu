@@ -350,6 +350,219 @@ int validate(int64_t n, int64_t lda, int k, int p, int q, const void *A)
     return PSDPROJ_OK;
 }
 
+// One projection's arguments and the state its phases share.  A projection
+// runs as: proj_begin (image, alpha, Omega, the first product), the
+// orthonormalisation after each product with A, proj_power_pass for each
+// power product, proj_core_pass, proj_core_small (core, eigensolver, factor)
+// and proj_finish (P = W W^T).  run_projection issues them in that order on
+// one context; psdproj_batched_grouped issues each phase for all problems of
+// a batch before the next, the small steps as grouped launches.
+struct proj_call {
+    const float *dA = nullptr;
+    int64_t n = 0, lda = 0;
+    int k = 0, p = 0, q = 0, m = 0;
+    uint64_t seed = 0;
+    bool scaled = false;                 // Alg. 3 (the shifted form)
+    double alpha_in = 0.0;
+    double *d_alpha_out = nullptr;
+    int *d_info = nullptr;
+    float *dP = nullptr;
+    int64_t ldp = 0;
+    float *dW = nullptr;
+    int64_t ldw = 0;
+    int *d_rank = nullptr;
+    psdproj_opts opts = {};
+    bool omega_ready = false;            // Omega already in the workspace (warm start of Alg. 6)
+    // set by proj_begin
+    const double *shift = nullptr;       // device shift of the power products (NULL: none)
+    bool fuse = false;                   // BF16 side outputs written by X's producers
+};
+
+// Alg. 3 with alpha from the Ritz values of the unshifted sketch
+bool proj_ritz(const proj_call &pc)
+{
+    return pc.scaled && !(pc.alpha_in > 0.0) && pc.opts.alpha_mode == PSDPROJ_ALPHA_RITZ;
+}
+// BF16 form: the producers of each pass's X write its side outputs
+bool proj_fuse(const proj_call &pc)
+{
+    return pc.opts.prec == PSDPROJ_PREC_BF16 && pc.m <= 128 && !proj_ritz(pc);
+}
+// where the shift of the power products lives (Alg. 3), else NULL
+const double *proj_shift(const proj_call &pc, const psd_workspace &ws)
+{
+    return pc.scaled ? ws.scal + SC_SHIFT : nullptr;
+}
+
+// The BF16 pass's side outputs for the next pass over ctx's workspace
+psd_bf16_side proj_side(psdproj_ctx *ctx, const double *next_shift)
+{
+    psd_workspace &ws = ctx->ws;
+    return psd_bf16_side{ws.Xhi, ws.ld, ws.Y, ws.ld, next_shift};
+}
+
+// The image of A, alpha (Alg. 3), Omega (Alg. 1) and Y = (A + shift I) Omega
+int proj_begin(psdproj_ctx *ctx, proj_call &pc)
+{
+    psdproj_opts &opts = pc.opts;
+    psd_workspace &ws = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    const float *dA = pc.dA;
+    const int64_t n = pc.n, lda = pc.lda;
+    const int m = pc.m;
+    const uint64_t seed = pc.seed;
+    const double alpha_in = pc.alpha_in;
+    const double *shift = nullptr;
+    const bool bf16 = opts.prec == PSDPROJ_PREC_BF16;
+    const bool tc = opts.prec != PSDPROJ_PREC_FP32;
+    // the tensor-core forms read A once here and their image(s) in every later pass
+    if (tc) PSD_TRY(pack_image(ctx, dA, n, lda, opts.prec));
+    // variant: alpha from the Ritz values of the unshifted sketch (below)
+    const bool ritz = proj_ritz(pc);
+    if (pc.scaled && !ritz) {
+        double *sc = ws.scal;
+        if (!(alpha_in > 0.0)) {
+            stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
+            if (ctx->det) {
+                PSD_KL(launch_power_iteration_det(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1, sc,
+                                                  sc + SC_SIGMA1, ctx->det_part), 3 * opts.N + 5);
+                PSD_KL(launch_power_iteration_det(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0, ws.pv1,
+                                                  sc, sc + SC_SIGMA2, ctx->det_part), 3 * opts.N + 5);
+            } else if (bf16) {
+                PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
+                                                   ws.pv0, ws.pv1, ws.pv2, sc, sc + SC_SIGMA1,
+                                                   ctx->d_status, ctx->wait_limit),
+                       opts.N + 4);
+                PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 4u,
+                                                   sc + SC_SIGMA1, ws.pv0, ws.pv1, ws.pv2, sc,
+                                                   sc + SC_SIGMA2, ctx->d_status, ctx->wait_limit),
+                       opts.N + 4);
+            } else {
+                PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
+                                              sc, sc + SC_SIGMA1), 2 * opts.N + 4);
+                PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0,
+                                              ws.pv1, sc, sc + SC_SIGMA2), 2 * opts.N + 4);
+            }
+        }
+        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
+        PSD_KL(launch_alpha_finish(s, sc + SC_SIGMA1, sc + SC_SIGMA2, alpha_in,
+                                   pc.d_alpha_out ? pc.d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
+                                   pc.d_info ? pc.d_info : ws.ints + IN_INFO), 1);
+        shift = sc + SC_SHIFT;
+    }
+    const int lpad = psd_lpad(m);
+    // BF16 form: every kernel that writes the next pass's X (Omega, the last
+    // product of each CholeskyQR2) also writes that pass's BF16 image of X
+    // and starts its Y, so the passes need no conversion sweep
+    const bool fuse = proj_fuse(pc);
+    bool prepared = false;
+    // Omega (Alg. 1), then Y = (A + shift I) Omega
+    if (!pc.omega_ready) {
+        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
+        if (opts.sketch == PSDPROJ_SKETCH_SRHT) {
+            PSD_KL(launch_srht(s, seed, n, m, lpad, ws.ld, ws.picks, ctx->d_status, ws.Om, ws.ld), 2);
+        } else {
+            const psd_bf16_side sd = proj_side(ctx, shift);
+            PSD_KL(launch_gaussian(s, seed, 0u, n, m, lpad, ws.ld, ws.Om, ws.ld, fuse ? &sd : nullptr), 1);
+            prepared = fuse;
+        }
+    }
+    if (ritz) {
+        // Alg. 3's first product without the shift, A Omega, does not depend
+        // on alpha: its sketch Q0 = orth(A Omega) gives Ritz values
+        // eig(Q0^T A Q0) whose most negative one sets alpha; then
+        // (A + alpha I) Omega = A Omega + alpha Omega needs no further pass.
+        double *sc = ws.scal;
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec));
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.W, ws.ld, opts.prec));
+        {
+            stage_scope st(ctx, PSDPROJ_STAGE_CORE);
+            PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.W, ws.ld, n, m, ws.gpart, ws.C, 2, nullptr, ctx->persist_sms), 2);
+        }
+        {
+            stage_scope st(ctx, PSDPROJ_STAGE_EIG);
+            PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, opts.eig,
+                              ws.ints + IN_EIGFAIL), psd_eig_launches(opts.eig));
+        }
+        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
+        PSD_KL(launch_ritz_alpha(s, ws.d, m, pc.d_alpha_out ? pc.d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
+                                 pc.d_info ? pc.d_info : ws.ints + IN_INFO), 1);
+        PSD_KL(launch_add_shift(s, ws.Y, ws.Om, n, m, ws.ld, sc + SC_SHIFT), 1);
+        shift = sc + SC_SHIFT;
+    } else {
+        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, shift, ws.Y, ws.ld, opts.prec, prepared));
+    }
+    pc.shift = shift;
+    pc.fuse = fuse;
+    return PSDPROJ_OK;
+}
+
+// power product: Y = (A + shift I) Q
+int proj_power_pass(psdproj_ctx *ctx, const proj_call &pc)
+{
+    psd_workspace &ws = ctx->ws;
+    return sym_pass(ctx, pc.dA, pc.n, pc.lda, ws.Q, ws.ld, pc.m, pc.shift, ws.Y, ws.ld, pc.opts.prec, pc.fuse);
+}
+
+// core product Y = A Q (Lemma 4: the unshifted A in both algorithms)
+int proj_core_pass(psdproj_ctx *ctx, const proj_call &pc)
+{
+    psd_workspace &ws = ctx->ws;
+    return sym_pass(ctx, pc.dA, pc.n, pc.lda, ws.Q, ws.ld, pc.m, nullptr, ws.Y, ws.ld, pc.opts.prec, pc.fuse);
+}
+
+float *proj_w(psdproj_ctx *ctx, const proj_call &pc) { return pc.dW ? pc.dW : ctx->ws.W; }
+int64_t proj_ldw(psdproj_ctx *ctx, const proj_call &pc) { return pc.dW ? pc.ldw : ctx->ws.ld; }
+
+// C = Q^T A Q, its eigenpairs, M = V sqrt(max(D, 0)) and W = Q M
+int proj_core_small(psdproj_ctx *ctx, const proj_call &pc)
+{
+    psd_workspace &ws = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    const int64_t n = pc.n;
+    const int m = pc.m;
+    {
+        stage_scope st(ctx, PSDPROJ_STAGE_CORE);
+        PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.Y, ws.ld, n, m, ws.gpart, ws.C, 2, nullptr, ctx->persist_sms), 2);
+    }
+    {
+        stage_scope st(ctx, PSDPROJ_STAGE_EIG);
+        PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, pc.opts.eig,
+                          ws.ints + IN_EIGFAIL), psd_eig_launches(pc.opts.eig));
+    }
+    int *rk = ws.ints + IN_RANK;
+    stage_scope st(ctx, PSDPROJ_STAGE_FACTOR);
+    PSD_KL(launch_factor_prep(s, ws.V, ws.d, m, ws.M, rk), 1);
+    PSD_KL(launch_tall_small(s, ws.Q, ws.ld, n, m, ws.M, m, nullptr, rk, proj_w(ctx, pc), proj_ldw(ctx, pc), nullptr,
+                             ctx->persist_sms), 1);
+    return PSDPROJ_OK;
+}
+
+// P = W W^T (unless only the factor is asked for) and the rank
+int proj_finish(psdproj_ctx *ctx, const proj_call &pc)
+{
+    psd_workspace &ws = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    const int m = pc.m;
+    int *rk = ws.ints + IN_RANK;
+    float *Wd = proj_w(ctx, pc);
+    const int64_t ldwd = proj_ldw(ctx, pc);
+    if (pc.opts.out_mode != PSDPROJ_OUT_FACTOR) {
+        stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
+        const int upper = pc.opts.out_mode == PSDPROJ_OUT_UPPER;
+        // the tensor-core SYRK takes up to 128 columns of W; wider factors
+        // are written by the FP32 kernel (at least as accurate)
+        if (pc.opts.syrk_prec == PSDPROJ_PREC_FP32 || m > 128)
+            PSD_KL(launch_syrk_simt(s, Wd, ldwd, pc.n, m, rk, pc.dP, pc.ldp, upper), 1);
+        else
+            PSD_KL(launch_syrk_tc(s, ctx->persist_sms, Wd, ldwd, pc.n, m, rk, pc.dP, pc.ldp, upper, ws.Xhi,
+                                  ws.Xlo, ws.ld, ctx->d_status, ctx->wait_limit), 2);
+    }
+    if (pc.d_rank) PSD_CK(cudaMemcpyAsync(pc.d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    return PSDPROJ_OK;
+}
+
 // omega_ready: the workspace's Omega already holds the test matrix (warm
 // start of Alg. 6); it is not drawn again
 int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, int k, int p,
@@ -380,134 +593,41 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
         PSD_TRY(ensure_stage(ctx, &ctx->det_part, &ctx->det_part_bytes,
                              sizeof(float) * (size_t)psd_det_part_floats(n, m), ctx->stream));
     psd_workspace &ws = ctx->ws;
-    cudaStream_t s = ctx->stream;
-    const double *shift = nullptr;
-    const bool bf16 = opts.prec == PSDPROJ_PREC_BF16;
-    const bool tc = opts.prec != PSDPROJ_PREC_FP32;
-    // the tensor-core forms read A once here and their image(s) in every later pass
-    if (tc) PSD_TRY(pack_image(ctx, dA, n, lda, opts.prec));
-    // variant: alpha from the Ritz values of the unshifted sketch (below)
-    const bool ritz = scaled && !(alpha_in > 0.0) && opts.alpha_mode == PSDPROJ_ALPHA_RITZ;
-    if (scaled && !ritz) {
-        double *sc = ws.scal;
-        if (!(alpha_in > 0.0)) {
-            stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
-            if (ctx->det) {
-                PSD_KL(launch_power_iteration_det(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1, sc,
-                                                  sc + SC_SIGMA1, ctx->det_part), 3 * opts.N + 5);
-                PSD_KL(launch_power_iteration_det(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0, ws.pv1,
-                                                  sc, sc + SC_SIGMA2, ctx->det_part), 3 * opts.N + 5);
-            } else if (bf16) {
-                PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 3u, nullptr,
-                                                   ws.pv0, ws.pv1, ws.pv2, sc, sc + SC_SIGMA1,
-                                                   ctx->d_status, ctx->wait_limit),
-                       opts.N + 4);
-                PSD_KL(launch_power_iteration_bf16(s, ctx->persist_sms, ctx->Ab, n, opts.N, seed, 4u,
-                                                   sc + SC_SIGMA1, ws.pv0, ws.pv1, ws.pv2, sc,
-                                                   sc + SC_SIGMA2, ctx->d_status, ctx->wait_limit),
-                       opts.N + 4);
-            } else {
-                PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 3u, nullptr, ws.pv0, ws.pv1,
-                                              sc, sc + SC_SIGMA1), 2 * opts.N + 4);
-                PSD_KL(launch_power_iteration(s, dA, n, lda, opts.N, seed, 4u, sc + SC_SIGMA1, ws.pv0,
-                                              ws.pv1, sc, sc + SC_SIGMA2), 2 * opts.N + 4);
-            }
-        }
-        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
-        PSD_KL(launch_alpha_finish(s, sc + SC_SIGMA1, sc + SC_SIGMA2, alpha_in,
-                                   d_alpha_out ? d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
-                                   d_info ? d_info : ws.ints + IN_INFO), 1);
-        shift = sc + SC_SHIFT;
-    }
-    const int lpad = psd_lpad(m);
-    // BF16 form: every kernel that writes the next pass's X (Omega, the last
-    // product of each CholeskyQR2) also writes that pass's BF16 image of X
-    // and starts its Y, so the passes need no conversion sweep
-    const bool fuse = bf16 && m <= 128 && !ritz;
-    auto side_for = [&](const double *next_shift) {
-        return psd_bf16_side{ws.Xhi, ws.ld, ws.Y, ws.ld, next_shift};
-    };
-    bool prepared = false;
-    // Omega (Alg. 1), then Y = (A + shift I) Omega
-    if (!omega_ready) {
-        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
-        if (opts.sketch == PSDPROJ_SKETCH_SRHT) {
-            PSD_KL(launch_srht(s, seed, n, m, lpad, ws.ld, ws.picks, ctx->d_status, ws.Om, ws.ld), 2);
-        } else {
-            const psd_bf16_side sd = side_for(shift);
-            PSD_KL(launch_gaussian(s, seed, 0u, n, m, lpad, ws.ld, ws.Om, ws.ld, fuse ? &sd : nullptr), 1);
-            prepared = fuse;
-        }
-    }
-    if (ritz) {
-        // Alg. 3's first product without the shift, A Omega, does not depend
-        // on alpha: its sketch Q0 = orth(A Omega) gives Ritz values
-        // eig(Q0^T A Q0) whose most negative one sets alpha; then
-        // (A + alpha I) Omega = A Omega + alpha Omega needs no further pass.
-        double *sc = ws.scal;
-        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec));
-        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
-        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.W, ws.ld, opts.prec));
-        {
-            stage_scope st(ctx, PSDPROJ_STAGE_CORE);
-            PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.W, ws.ld, n, m, ws.gpart, ws.C, 2, nullptr, ctx->persist_sms), 2);
-        }
-        {
-            stage_scope st(ctx, PSDPROJ_STAGE_EIG);
-            PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, opts.eig,
-                              ws.ints + IN_EIGFAIL), psd_eig_launches(opts.eig));
-        }
-        stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
-        PSD_KL(launch_ritz_alpha(s, ws.d, m, d_alpha_out ? d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
-                                 d_info ? d_info : ws.ints + IN_INFO), 1);
-        PSD_KL(launch_add_shift(s, ws.Y, ws.Om, n, m, ws.ld, sc + SC_SHIFT), 1);
-        shift = sc + SC_SHIFT;
-    } else {
-        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, shift, ws.Y, ws.ld, opts.prec, prepared));
-    }
+    proj_call pc;
+    pc.dA = dA;
+    pc.n = n;
+    pc.lda = lda;
+    pc.k = k;
+    pc.p = p;
+    pc.q = q;
+    pc.m = m;
+    pc.seed = seed;
+    pc.scaled = scaled;
+    pc.alpha_in = alpha_in;
+    pc.d_alpha_out = d_alpha_out;
+    pc.d_info = d_info;
+    pc.dP = dP;
+    pc.ldp = ldp;
+    pc.dW = dW;
+    pc.ldw = ldw;
+    pc.d_rank = d_rank;
+    pc.opts = opts;
+    pc.omega_ready = omega_ready;
+    PSD_TRY(proj_begin(ctx, pc));
     // the orthonormalisation after product t writes the side outputs of the
     // next pass: a power product (shifted) while t < 2q, else the core (Y = 0)
     {
-        const psd_bf16_side sd = side_for(q > 0 ? shift : nullptr);
-        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, fuse ? &sd : nullptr));
+        const psd_bf16_side sd = proj_side(ctx, q > 0 ? pc.shift : nullptr);
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, pc.fuse ? &sd : nullptr));
     }
     for (int t = 0; t < 2 * q; ++t) {
-        PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, shift, ws.Y, ws.ld, opts.prec, fuse));
-        const psd_bf16_side sd = side_for(t + 1 < 2 * q ? shift : nullptr);
-        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, fuse ? &sd : nullptr));
+        PSD_TRY(proj_power_pass(ctx, pc));
+        const psd_bf16_side sd = proj_side(ctx, t + 1 < 2 * q ? pc.shift : nullptr);
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, pc.fuse ? &sd : nullptr));
     }
-    // core C = Q^T A Q (Lemma 4: the unshifted A in both algorithms)
-    PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec, fuse));
-    {
-        stage_scope st(ctx, PSDPROJ_STAGE_CORE);
-        PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.Y, ws.ld, n, m, ws.gpart, ws.C, 2, nullptr, ctx->persist_sms), 2);
-    }
-    {
-        stage_scope st(ctx, PSDPROJ_STAGE_EIG);
-        PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, opts.eig,
-                          ws.ints + IN_EIGFAIL), psd_eig_launches(opts.eig));
-    }
-    int *rk = ws.ints + IN_RANK;
-    float *Wd = dW ? dW : ws.W;
-    const int64_t ldwd = dW ? ldw : ws.ld;
-    {
-        stage_scope st(ctx, PSDPROJ_STAGE_FACTOR);
-        PSD_KL(launch_factor_prep(s, ws.V, ws.d, m, ws.M, rk), 1);
-        PSD_KL(launch_tall_small(s, ws.Q, ws.ld, n, m, ws.M, m, nullptr, rk, Wd, ldwd, nullptr, ctx->persist_sms), 1);
-    }
-    if (opts.out_mode != PSDPROJ_OUT_FACTOR) {
-        stage_scope st(ctx, PSDPROJ_STAGE_SYRK);
-        const int upper = opts.out_mode == PSDPROJ_OUT_UPPER;
-        // the tensor-core SYRK takes up to 128 columns of W; wider factors
-        // are written by the FP32 kernel (at least as accurate)
-        if (opts.syrk_prec == PSDPROJ_PREC_FP32 || m > 128)
-            PSD_KL(launch_syrk_simt(s, Wd, ldwd, n, m, rk, dP, ldp, upper), 1);
-        else
-            PSD_KL(launch_syrk_tc(s, ctx->persist_sms, Wd, ldwd, n, m, rk, dP, ldp, upper, ws.Xhi,
-                                  ws.Xlo, ws.ld, ctx->d_status, ctx->wait_limit), 2);
-    }
-    if (d_rank) PSD_CK(cudaMemcpyAsync(d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, s));
-    return PSDPROJ_OK;
+    PSD_TRY(proj_core_pass(ctx, pc));
+    PSD_TRY(proj_core_small(ctx, pc));
+    return proj_finish(ctx, pc);
 }
 
 int ensure_stage(psdproj_ctx *ctx, float **buf, size_t *cap, size_t bytes, cudaStream_t s)
@@ -650,6 +770,9 @@ int psdproj_destroy(psdproj_ctx *ctx)
     if (ctx->dW_stage) cudaFree(ctx->dW_stage);
     if (ctx->det_part) cudaFree(ctx->det_part);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->g_exec) cudaGraphExecDestroy(ctx->g_exec);
+    if (ctx->g_slots) cudaFree(ctx->g_slots);
+    if (ctx->g_tabs) cudaFree(ctx->g_tabs);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->Ab) cudaFree(ctx->Ab);
     if (ctx->Ab_lo) cudaFree(ctx->Ab_lo);
@@ -834,7 +957,7 @@ size_t psdproj_workspace_bytes(const psdproj_ctx *ctx)
 {
     if (!ctx) return 0;
     size_t b = ctx->ws.bytes + ctx->Ab_bytes + ctx->Ab_lo_bytes + ctx->dA_stage_bytes + ctx->dP_stage_bytes +
-               ctx->dW_stage_bytes + ctx->det_part_bytes;
+               ctx->dW_stage_bytes + ctx->det_part_bytes + ctx->g_slots_bytes + ctx->g_tabs_bytes;
     for (int i = 0; i < PSD_MAX_LANES; ++i)
         if (ctx->lane[i]) b += psdproj_workspace_bytes(ctx->lane[i]);
     return b;
@@ -1065,6 +1188,441 @@ void batch_graph_free(psdproj_ctx *ctx)
     ctx->graph_launches = 0;
 }
 
+// ---- grouped batch (psdproj_batched_grouped) -------------------------------
+// Every problem gets a workspace and image(s) of its own (one allocation), so
+// that all of them are in flight together, and the batch runs phase by phase:
+// the streaming phases (image, alpha, the products with A, the SYRK) per
+// problem on the lanes, and each small step of the orthonormalisations and of
+// the core (Gram, Cholesky, tall x small product, eigensolver, factor) as one
+// grouped launch over all problems on the context's stream, where the
+// single-problem path runs one block (or a few) per launch.
+
+struct grouped_slot {
+    psd_workspace ws;
+    uint16_t *Ab = nullptr, *Ab_lo = nullptr;
+    size_t Ab_bytes = 0, Ab_lo_bytes = 0;
+};
+
+// a grouped launch in device memory: its table and block maps
+struct gl_gram {
+    const psd_g_gram *tab = nullptr;
+    const int2 *bm = nullptr, *bm_red = nullptr;
+    int nb = 0, nb_red = 0;
+};
+struct gl_tall {
+    const psd_g_tall *tab = nullptr;
+    const int2 *bm = nullptr;
+    int nb = 0;
+};
+struct gl_qr {                 // one CholeskyQR2 over the problems of a stage
+    int count = 0;
+    gl_gram g1, g2;
+    const psd_g_chol *c1 = nullptr, *c2 = nullptr;
+    gl_tall t1, t2;
+};
+struct gl_core {               // core, eigensolver, factor
+    int count = 0;
+    gl_gram g;
+    const psd_g_eig *eig = nullptr;
+    const int2 *bm_ns = nullptr, *bm_ray = nullptr;
+    int nb_ns = 0, nb_ray = 0;
+    const psd_g_factor *fac = nullptr;
+    gl_tall t;
+};
+
+struct grouped_plan {
+    batch_plan lanes;
+    std::vector<grouped_slot> slot;
+    std::vector<proj_call> pc;
+    int qmax = 0, m_max = 0, mp_max = 0;
+    std::vector<gl_qr> qr;     // stage s: the orthonormalisation after product s - 1 (s = 0: after Y = A Omega)
+    gl_core core;
+};
+
+// image bytes of one problem in form prec: (high or only part, low part)
+void slot_image_bytes(int64_t n, int prec, size_t &hi, size_t &lo)
+{
+    hi = lo = 0;
+    if (prec == PSDPROJ_PREC_TF32) hi = (size_t)psd_tile32_count(n) * (size_t)PSD_TILE_BYTES;
+    else if (prec == PSDPROJ_PREC_BF16) hi = (size_t)psd_tile_count(n) * (size_t)PSD_TILE_BYTES;
+    else if (prec == PSDPROJ_PREC_BF16X3) hi = lo = (size_t)psd_tile_count(n) * (size_t)PSD_TILE_BYTES;
+}
+
+size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+// Per-problem workspaces and images, carved from ctx->g_slots (grown when
+// too small; zeroed whenever the plan is made, as a workspace is when
+// allocated)
+int grouped_slots(psdproj_ctx *ctx, const psdproj_opts &opts, int count, const psdproj_problem *probs,
+                  std::vector<grouped_slot> &slot)
+{
+    slot.assign(count, grouped_slot());
+    std::vector<size_t> off(count);
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        psd_workspace lay;
+        const int lp = psd_lpad(probs[i].k + probs[i].p);
+        size_t hi, lo;
+        slot_image_bytes(probs[i].n, opts.prec, hi, lo);
+        off[i] = total;
+        total += align_up(carve_workspace(lay, nullptr, probs[i].n, lp), 1024) + align_up(hi, 1024) +
+                 align_up(lo, 1024);
+    }
+    if (ctx->g_slots_bytes < total) {
+        PSD_TRY(psd_budget_check(ctx, ctx->g_slots_bytes, total));
+        if (ctx->g_slots) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->g_slots);
+            ctx->g_slots = nullptr;
+            ctx->g_slots_bytes = 0;
+        }
+        PSD_CK(cudaMalloc(&ctx->g_slots, total));
+        ctx->g_slots_bytes = total;
+    }
+    char *base = static_cast<char *>(ctx->g_slots);
+    for (int i = 0; i < count; ++i) {
+        grouped_slot &sl = slot[i];
+        const int64_t n = probs[i].n;
+        const int lp = psd_lpad(probs[i].k + probs[i].p);
+        char *b = base + off[i];
+        const size_t wb = carve_workspace(sl.ws, b, n, lp);
+        sl.ws.base = nullptr;              // part of g_slots: never freed on its own
+        sl.ws.bytes = 0;
+        sl.ws.n = n;
+        sl.ws.lpad = lp;
+        sl.ws.ld = psd_ld(n);
+        size_t hi, lo;
+        slot_image_bytes(n, opts.prec, hi, lo);
+        char *img = b + align_up(wb, 1024);
+        if (hi) {
+            sl.Ab = reinterpret_cast<uint16_t *>(img);
+            sl.Ab_bytes = hi;
+        }
+        if (lo) {
+            sl.Ab_lo = reinterpret_cast<uint16_t *>(img + align_up(hi, 1024));
+            sl.Ab_lo_bytes = lo;
+        }
+    }
+    PSD_CK(cudaMemsetAsync(ctx->g_slots, 0, total, ctx->stream));
+    return PSDPROJ_OK;
+}
+
+// Host copies of the grouped tables, laid out for one upload
+struct table_blob {
+    std::vector<char> h;
+    template <class T>
+    size_t put(const std::vector<T> &v)
+    {
+        const size_t off = align_up(h.size(), 64);
+        h.resize(off + sizeof(T) * v.size());
+        if (!v.empty()) memcpy(h.data() + off, v.data(), sizeof(T) * v.size());
+        return off;
+    }
+};
+
+// table offsets of a grouped launch before the upload
+struct gram_off { size_t tab, bm, bm_red; int nb, nb_red; };
+struct tall_off { size_t tab, bm; int nb; };
+
+gram_off put_gram(table_blob &tb, const std::vector<psd_g_gram> &t)
+{
+    std::vector<int2> bm, bmr;
+    for (int e = 0; e < (int)t.size(); ++e) {
+        for (int b = 0; b < t[e].nblk; ++b) bm.push_back(make_int2(e, b));
+        const int nr = psd_gram_reduce_blocks(t[e].m);
+        for (int b = 0; b < nr; ++b) bmr.push_back(make_int2(e, b));
+    }
+    gram_off o;
+    o.tab = tb.put(t);
+    o.bm = tb.put(bm);
+    o.bm_red = tb.put(bmr);
+    o.nb = (int)bm.size();
+    o.nb_red = (int)bmr.size();
+    return o;
+}
+
+tall_off put_tall(table_blob &tb, const std::vector<psd_g_tall> &t)
+{
+    std::vector<int2> bm;
+    for (int e = 0; e < (int)t.size(); ++e)
+        for (int b = 0; b < t[e].nb; ++b) bm.push_back(make_int2(e, b));
+    tall_off o;
+    o.tab = tb.put(t);
+    o.bm = tb.put(bm);
+    o.nb = (int)bm.size();
+    return o;
+}
+
+psd_g_gram gram_entry(const psd_workspace &ws, const float *X, const float *Z, int64_t n, int m, double *G,
+                      float2 *Gdf, int sms)
+{
+    psd_g_gram g;
+    g.X = X;
+    g.Z = Z;
+    g.ldx = g.ldz = ws.ld;
+    g.n = n;
+    g.m = m;
+    g.mp = (int)psd_round_up(m, 8);
+    g.rows = (int)psd_gram_rows(n, sms);
+    g.nblk = psd_gram_blocks(n, sms);
+    g.gpart = ws.gpart;
+    g.G = G;
+    g.Gdf = Gdf;
+    return g;
+}
+
+psd_g_tall tall_entry(const float *Y, int64_t ldy, int64_t n, int m, const float *B, const int *colmask,
+                      const int *d_cols, float *Z, int64_t ldz, const psd_bf16_side *side)
+{
+    psd_g_tall t;
+    t.Y = Y;
+    t.ldy = ldy;
+    t.n = n;
+    t.m = m;
+    t.B = B;
+    t.c = m;
+    t.colmask = colmask;
+    t.d_cols = d_cols;
+    t.Z = Z;
+    t.ldz = ldz;
+    t.side = side ? *side : psd_bf16_side{nullptr, 0, nullptr, 0, nullptr};
+    t.ntiles = (int)((n + PSD_TALL_RT - 1) / PSD_TALL_RT);
+    // four tiles (128 rows) per block: the block's copy of B is read once per four
+    t.nb = (t.ntiles + 3) / 4;
+    return t;
+}
+
+// The tables of every grouped launch of the batch, uploaded to ctx->g_tabs
+int grouped_tables(psdproj_ctx *ctx, grouped_plan &gp)
+{
+    const int count = (int)gp.pc.size();
+    const int sms = ctx->persist_sms;
+    table_blob tb;
+    struct qr_off { int count; gram_off g1, g2; size_t c1, c2; tall_off t1, t2; };
+    std::vector<qr_off> qo;
+    for (int st = 0; st <= 2 * gp.qmax; ++st) {
+        std::vector<psd_g_gram> g1, g2;
+        std::vector<psd_g_chol> c1, c2;
+        std::vector<psd_g_tall> t1, t2;
+        for (int i = 0; i < count; ++i) {
+            const proj_call &pc = gp.pc[i];
+            if (st > 0 && st > 2 * pc.q) continue;      // product st - 1 is not one of this problem's
+            const psd_workspace &ws = gp.slot[i].ws;
+            const int64_t n = pc.n;
+            const int m = pc.m;
+            float2 *gdf = reinterpret_cast<float2 *>(ws.cholscr);
+            g1.push_back(gram_entry(ws, ws.Y, ws.Y, n, m, ws.G, gdf, sms));
+            g2.push_back(gram_entry(ws, ws.T, ws.T, n, m, ws.G, gdf, sms));
+            c1.push_back(psd_g_chol{gdf, m, ws.Rinv, ws.dead, nullptr});
+            c2.push_back(psd_g_chol{gdf, m, ws.Rinv, ws.dead, ws.ints + IN_QRANK});
+            t1.push_back(tall_entry(ws.Y, ws.ld, n, m, ws.Rinv, ws.dead, nullptr, ws.T, ws.ld, nullptr));
+            // the side outputs of the pass that reads Q next: a power product
+            // (shifted) while product st is one of the problem's, else the core
+            const psd_bf16_side sd{ws.Xhi, ws.ld, ws.Y, ws.ld, st < 2 * pc.q ? proj_shift(pc, ws) : nullptr};
+            t2.push_back(tall_entry(ws.T, ws.ld, n, m, ws.Rinv, ws.dead, nullptr, ws.Q, ws.ld,
+                                    proj_fuse(pc) ? &sd : nullptr));
+        }
+        qr_off o;
+        o.count = (int)c1.size();
+        o.g1 = put_gram(tb, g1);
+        o.g2 = put_gram(tb, g2);
+        o.c1 = tb.put(c1);
+        o.c2 = tb.put(c2);
+        o.t1 = put_tall(tb, t1);
+        o.t2 = put_tall(tb, t2);
+        qo.push_back(o);
+    }
+    std::vector<psd_g_gram> cg;
+    std::vector<psd_g_eig> ce;
+    std::vector<psd_g_factor> cf;
+    std::vector<psd_g_tall> ct;
+    std::vector<int2> bns, bray;
+    for (int i = 0; i < count; ++i) {
+        const proj_call &pc = gp.pc[i];
+        const psd_workspace &ws = gp.slot[i].ws;
+        const int m = pc.m;
+        cg.push_back(gram_entry(ws, ws.Q, ws.Y, pc.n, m, ws.C, nullptr, sms));
+        ce.push_back(psd_g_eig{ws.C, m, ws.V, ws.d, ws.eigscr, ws.ints + IN_EIGFAIL});
+        cf.push_back(psd_g_factor{ws.V, ws.d, m, ws.M, ws.ints + IN_RANK});
+        float *Wd = pc.dW ? pc.dW : ws.W;
+        const int64_t ldwd = pc.dW ? pc.ldw : ws.ld;
+        ct.push_back(tall_entry(ws.Q, ws.ld, pc.n, m, ws.M, nullptr, ws.ints + IN_RANK, Wd, ldwd, nullptr));
+        for (int b = 0; b < psd_eig_ns_blocks(m); ++b) bns.push_back(make_int2(i, b));
+        for (int b = 0; b < m; ++b) bray.push_back(make_int2(i, b));
+    }
+    const gram_off cgo = put_gram(tb, cg);
+    const size_t ceo = tb.put(ce), cfo = tb.put(cf), bnso = tb.put(bns), brayo = tb.put(bray);
+    const tall_off cto = put_tall(tb, ct);
+    const size_t bytes = align_up(tb.h.size(), 256);
+    if (ctx->g_tabs_bytes < bytes) {
+        PSD_TRY(psd_budget_check(ctx, ctx->g_tabs_bytes, bytes));
+        if (ctx->g_tabs) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->g_tabs);
+            ctx->g_tabs = nullptr;
+            ctx->g_tabs_bytes = 0;
+        }
+        PSD_CK(cudaMalloc(&ctx->g_tabs, bytes));
+        ctx->g_tabs_bytes = bytes;
+    }
+    // the previous plan's launches may still read the tables: upload in order
+    PSD_CK(cudaStreamSynchronize(ctx->stream));
+    PSD_CK(cudaMemcpy(ctx->g_tabs, tb.h.data(), tb.h.size(), cudaMemcpyHostToDevice));
+    const char *d = static_cast<const char *>(ctx->g_tabs);
+    auto gram_at = [&](const gram_off &o) {
+        gl_gram g;
+        g.tab = reinterpret_cast<const psd_g_gram *>(d + o.tab);
+        g.bm = reinterpret_cast<const int2 *>(d + o.bm);
+        g.bm_red = reinterpret_cast<const int2 *>(d + o.bm_red);
+        g.nb = o.nb;
+        g.nb_red = o.nb_red;
+        return g;
+    };
+    auto tall_at = [&](const tall_off &o) {
+        gl_tall t;
+        t.tab = reinterpret_cast<const psd_g_tall *>(d + o.tab);
+        t.bm = reinterpret_cast<const int2 *>(d + o.bm);
+        t.nb = o.nb;
+        return t;
+    };
+    gp.qr.clear();
+    for (const qr_off &o : qo) {
+        gl_qr q;
+        q.count = o.count;
+        q.g1 = gram_at(o.g1);
+        q.g2 = gram_at(o.g2);
+        q.c1 = reinterpret_cast<const psd_g_chol *>(d + o.c1);
+        q.c2 = reinterpret_cast<const psd_g_chol *>(d + o.c2);
+        q.t1 = tall_at(o.t1);
+        q.t2 = tall_at(o.t2);
+        gp.qr.push_back(q);
+    }
+    gp.core.count = count;
+    gp.core.g = gram_at(cgo);
+    gp.core.eig = reinterpret_cast<const psd_g_eig *>(d + ceo);
+    gp.core.fac = reinterpret_cast<const psd_g_factor *>(d + cfo);
+    gp.core.bm_ns = reinterpret_cast<const int2 *>(d + bnso);
+    gp.core.bm_ray = reinterpret_cast<const int2 *>(d + brayo);
+    gp.core.nb_ns = (int)bns.size();
+    gp.core.nb_ray = (int)bray.size();
+    gp.core.t = tall_at(cto);
+    return PSDPROJ_OK;
+}
+
+// A lane running one problem's phase: the lane's workspace and image are
+// those of the problem's slot until the binding ends
+struct slot_binding {
+    psdproj_ctx *c;
+    psd_workspace ws;
+    uint16_t *Ab, *Ab_lo;
+    size_t Ab_bytes, Ab_lo_bytes;
+    slot_binding(psdproj_ctx *lane, const grouped_slot &sl)
+        : c(lane), ws(lane->ws), Ab(lane->Ab), Ab_lo(lane->Ab_lo), Ab_bytes(lane->Ab_bytes),
+          Ab_lo_bytes(lane->Ab_lo_bytes)
+    {
+        lane->ws = sl.ws;
+        lane->Ab = sl.Ab;
+        lane->Ab_lo = sl.Ab_lo;
+        lane->Ab_bytes = sl.Ab_bytes;
+        lane->Ab_lo_bytes = sl.Ab_lo_bytes;
+    }
+    ~slot_binding()
+    {
+        c->ws = ws;
+        c->Ab = Ab;
+        c->Ab_lo = Ab_lo;
+        c->Ab_bytes = Ab_bytes;
+        c->Ab_lo_bytes = Ab_lo_bytes;
+    }
+};
+
+int grouped_qr(psdproj_ctx *ctx, const grouped_plan &gp, const gl_qr &q)
+{
+    cudaStream_t s = ctx->stream;
+    const double tau = 1e-10;     // the dependent-column threshold of cholqr2
+    PSD_KL(launch_gram_grouped(s, q.g1.tab, 0, q.g1.bm, q.g1.nb, q.g1.bm_red, q.g1.nb_red, gp.mp_max), 2);
+    PSD_KL(launch_cholesky_grouped(s, q.c1, q.count, gp.m_max, 1, tau, ctx->d_status), 1);
+    PSD_KL(launch_tall_small_grouped(s, q.t1.tab, q.t1.bm, q.t1.nb, gp.m_max), 1);
+    PSD_KL(launch_gram_grouped(s, q.g2.tab, 0, q.g2.bm, q.g2.nb, q.g2.bm_red, q.g2.nb_red, gp.mp_max), 2);
+    PSD_KL(launch_cholesky_grouped(s, q.c2, q.count, gp.m_max, 0, tau, ctx->d_status), 1);
+    PSD_KL(launch_tall_small_grouped(s, q.t2.tab, q.t2.bm, q.t2.nb, gp.m_max), 1);
+    return PSDPROJ_OK;
+}
+
+int grouped_core(psdproj_ctx *ctx, const grouped_plan &gp, const psdproj_opts &opts)
+{
+    cudaStream_t s = ctx->stream;
+    const gl_core &c = gp.core;
+    PSD_KL(launch_gram_grouped(s, c.g.tab, 1, c.g.bm, c.g.nb, c.g.bm_red, c.g.nb_red, gp.mp_max), 2);
+    PSD_KL(launch_eig_grouped(s, c.eig, c.count, c.bm_ns, c.nb_ns, c.bm_ray, c.nb_ray, gp.m_max, ctx->d_status,
+                              opts.eig),
+           psd_eig_launches(opts.eig));
+    PSD_KL(launch_factor_prep_grouped(s, c.fac, c.count), 1);
+    PSD_KL(launch_tall_small_grouped(s, c.t.tab, c.t.bm, c.t.nb, gp.m_max), 1);
+    return PSDPROJ_OK;
+}
+
+// Issue a planned grouped batch on the context's stream
+int grouped_issue(psdproj_ctx *ctx, grouped_plan &gp, const psdproj_opts &opts)
+{
+    const int S = gp.lanes.S;
+    // the lanes run with this call's settings
+    struct lane_settings {
+        psdproj_ctx *ctx;
+        int S;
+        ~lane_settings()
+        {
+            for (int j = 0; j < S; ++j) {
+                ctx->lane[j]->wait_limit = 0;
+                ctx->lane[j]->det = false;
+            }
+        }
+    } settings_scope{ctx, S};
+    for (int j = 0; j < S; ++j) {
+        ctx->lane[j]->wait_limit = (long long)opts.spin_limit;
+        ctx->lane[j]->det = false;
+    }
+    // one phase of every problem with `take(i)` on the lanes, forked from and
+    // joined back to the context's stream (also after an error)
+    auto on_lanes = [&](auto take, auto phase) -> int {
+        cudaEvent_t fork = ctx->lane_ev[PSD_MAX_LANES];
+        PSD_CK(cudaEventRecord(fork, ctx->stream));
+        for (int j = 0; j < S; ++j) PSD_CK(cudaStreamWaitEvent(ctx->lane[j]->stream, fork, 0));
+        int rc = PSDPROJ_OK;
+        for (int i : gp.lanes.order) {
+            if (!take(i)) continue;
+            psdproj_ctx *lane = ctx->lane[gp.lanes.lane_of[i]];
+            slot_binding bind(lane, gp.slot[i]);
+            rc = phase(lane, gp.pc[i]);
+            if (rc != PSDPROJ_OK) break;
+        }
+        for (int j = 0; j < S; ++j) {
+            cudaEventRecord(ctx->lane_ev[j], ctx->lane[j]->stream);
+            cudaStreamWaitEvent(ctx->stream, ctx->lane_ev[j], 0);
+        }
+        return rc;
+    };
+    auto all = [](int) { return true; };
+    PSD_TRY(on_lanes(all, [](psdproj_ctx *c, proj_call &pc) { return proj_begin(c, pc); }));
+    PSD_TRY(grouped_qr(ctx, gp, gp.qr[0]));
+    for (int t = 0; t < 2 * gp.qmax; ++t) {
+        PSD_TRY(on_lanes([&](int i) { return t < 2 * gp.pc[i].q; },
+                         [](psdproj_ctx *c, proj_call &pc) { return proj_power_pass(c, pc); }));
+        PSD_TRY(grouped_qr(ctx, gp, gp.qr[t + 1]));
+    }
+    PSD_TRY(on_lanes(all, [](psdproj_ctx *c, proj_call &pc) { return proj_core_pass(c, pc); }));
+    PSD_TRY(grouped_core(ctx, gp, opts));
+    return on_lanes(all, [](psdproj_ctx *c, proj_call &pc) { return proj_finish(c, pc); });
+}
+
+void grouped_graph_free(psdproj_ctx *ctx)
+{
+    if (ctx->g_exec) cudaGraphExecDestroy(ctx->g_exec);
+    ctx->g_exec = nullptr;
+    ctx->g_probs.clear();
+    ctx->g_launches = 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1160,6 +1718,106 @@ int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *pr
     }
     PSD_CK(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
     g_launches.fetch_add(ctx->graph_launches);
+    return PSDPROJ_OK;
+}
+
+int psdproj_batched_grouped(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
+                            const psdproj_opts *opts_in)
+{
+    if (!ctx || count < 0 || (count > 0 && !probs)) return PSDPROJ_EINVAL;
+    psdproj_opts opts;
+    if (opts_in) opts = *opts_in; else psdproj_default_opts(&opts);
+    PSD_TRY(check_opts(&opts));
+    int64_t nmax = 0;
+    int mmax = 0;
+    PSD_TRY(batch_validate(opts, count, probs, nmax, mmax));
+    // the grouped small steps are the shared-memory kernels (m <= 128); the
+    // fixed-order products of the deterministic form are not grouped
+    if (mmax > 128 || opts.deterministic) return PSDPROJ_ENOTSUP;
+    if (count == 0) return PSDPROJ_OK;
+    device_guard g(ctx->device);
+    const int lanes = batch_lanes(ctx, count, probs);
+    const bool same = ctx->g_exec && (int)ctx->g_probs.size() == count &&
+                      memcmp(ctx->g_probs.data(), probs, sizeof(psdproj_problem) * (size_t)count) == 0 &&
+                      memcmp(&ctx->g_opts, &opts, sizeof(opts)) == 0 && ctx->g_streams == lanes &&
+                      ctx->g_persist == ctx->persist_sms;
+    if (!same) {
+        grouped_graph_free(ctx);
+        grouped_plan gp;
+        gp.lanes = batch_make_plan(ctx, opts, count, probs, lanes);
+        if (gp.lanes.S < 1) gp.lanes.S = 1;
+        for (int j = 0; j < gp.lanes.S; ++j) PSD_TRY(ensure_lane(ctx, j));
+        gp.pc.resize(count);
+        for (int i = 0; i < count; ++i) {
+            const psdproj_problem &pb = probs[i];
+            proj_call &pc = gp.pc[i];
+            pc.dA = pb.dA;
+            pc.n = pb.n;
+            pc.lda = pb.lda;
+            pc.k = pb.k;
+            pc.p = pb.p;
+            pc.q = pb.q;
+            pc.m = pb.k + pb.p;
+            pc.seed = pb.seed;
+            pc.scaled = pb.algorithm == 2;
+            pc.alpha_in = pb.alpha_in;
+            pc.d_alpha_out = pb.d_alpha_out;
+            pc.d_info = pb.d_info;
+            pc.dP = pb.dP;
+            pc.ldp = pb.ldp;
+            pc.dW = pb.dW;
+            pc.ldw = pb.ldw;
+            pc.d_rank = pb.d_rank;
+            pc.opts = opts;
+            if (pb.q > gp.qmax) gp.qmax = pb.q;
+            if (pc.m > gp.m_max) gp.m_max = pc.m;
+        }
+        gp.mp_max = (int)psd_round_up(gp.m_max, 8);
+        PSD_TRY(grouped_slots(ctx, opts, count, probs, gp.slot));
+        PSD_TRY(grouped_tables(ctx, gp));
+        // record with the stage timers off (events inside a graph are not read back)
+        int timing_was = ctx->timing.on;
+        ctx->timing.on = 0;
+        int lane_timing[PSD_MAX_LANES] = {};
+        for (int j = 0; j < PSD_MAX_LANES; ++j)
+            if (ctx->lane[j]) {
+                lane_timing[j] = ctx->lane[j]->timing.on;
+                ctx->lane[j]->timing.on = 0;
+            }
+        if (!ctx->capture_stream)
+            PSD_CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        // the slots' zeroing (on the context's stream) ends before the recorded work
+        PSD_CK(cudaStreamSynchronize(ctx->stream));
+        cudaStream_t user = ctx->stream;
+        const uint64_t l0 = g_launches.load();
+        PSD_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed));
+        ctx->stream = ctx->capture_stream;
+        const int rc = grouped_issue(ctx, gp, opts);
+        ctx->stream = user;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        const uint64_t nk = g_launches.load() - l0;
+        g_launches.fetch_sub(nk);      // recorded, not launched: counted on each replay
+        ctx->timing.on = timing_was;
+        for (int j = 0; j < PSD_MAX_LANES; ++j)
+            if (ctx->lane[j]) ctx->lane[j]->timing.on = lane_timing[j];
+        if (rc != PSDPROJ_OK || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc != PSDPROJ_OK ? rc : cuda_status(ec, __LINE__);
+        }
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return cuda_status(ei, __LINE__);
+        ctx->g_exec = exec;
+        ctx->g_probs.assign(probs, probs + count);
+        ctx->g_opts = opts;
+        ctx->g_streams = lanes;
+        ctx->g_persist = ctx->persist_sms;
+        ctx->g_launches = nk;
+    }
+    PSD_CK(cudaGraphLaunch(ctx->g_exec, ctx->stream));
+    g_launches.fetch_add(ctx->g_launches);
     return PSDPROJ_OK;
 }
 

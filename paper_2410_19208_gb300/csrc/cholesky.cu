@@ -298,9 +298,9 @@ size_t blocked_smem(int m)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NTB, 1)
-cholesky_blocked_kernel(const float2 *__restrict__ Gd, int m, float *__restrict__ Rinv,
-                        int *__restrict__ dead, int *__restrict__ d_qrank, float tau, int *d_status)
+__device__ __forceinline__ void cholesky_blocked_body(const float2 *__restrict__ Gd, int m, float *__restrict__ Rinv,
+                                                      int *__restrict__ dead, int *__restrict__ d_qrank, float tau,
+                                                      int *d_status)
 {
     using N = num<T>;
     constexpr int NB = chol_nb<T>::value;
@@ -568,6 +568,23 @@ cholesky_blocked_kernel(const float2 *__restrict__ Gd, int m, float *__restrict_
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(NTB, 1)
+cholesky_blocked_kernel(const float2 *__restrict__ Gd, int m, float *__restrict__ Rinv,
+                        int *__restrict__ dead, int *__restrict__ d_qrank, float tau, int *d_status)
+{
+    cholesky_blocked_body<T>(Gd, m, Rinv, dead, d_qrank, tau, d_status);
+}
+
+// many problems in one launch: block b factors entry b
+template <typename T>
+__global__ void __launch_bounds__(NTB, 1)
+cholesky_blocked_grouped_kernel(const psd_g_chol *__restrict__ tab, float tau, int *d_status)
+{
+    const psd_g_chol a = tab[blockIdx.x];
+    cholesky_blocked_body<T>(a.Gd, a.m, a.Rinv, a.dead, a.d_qrank, tau, d_status);
+}
+
 // Z (n x c) = Y (n x m) * B (m x c, column-major ld m).  Block: 64 rows x 64
 // output columns; 256 threads with 4 x 4 micro-tiles.
 constexpr int TR = 64, TC = 64, KC = 64;
@@ -723,13 +740,14 @@ tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int 
 // 4 ty .. 4 ty + 3 (16 FMAs per two 16-byte shared loads per K step).  The
 // tile is staged K-major with batched, coalesced loads; stores are coalesced
 // over the rows.
-constexpr int RT = 32;              // rows per tile
+constexpr int RT = PSD_TALL_RT;     // rows per tile
 constexpr int LDB = 132, LDT = 36;  // shared row strides (floats) of B and of the Y tile
 
-__global__ void __launch_bounds__(256)
-tall_small_res_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m, const float *__restrict__ B,
-                      int c, const int *__restrict__ colmask, const int *__restrict__ d_cols, float *__restrict__ Z,
-                      int64_t ldz, psd_bf16_side side, int ntiles)
+__device__ __forceinline__ void tall_small_res_body(const float *__restrict__ Y, int64_t ldy, int64_t n, int m,
+                                                    const float *__restrict__ B, int c,
+                                                    const int *__restrict__ colmask, const int *__restrict__ d_cols,
+                                                    float *__restrict__ Z, int64_t ldz, psd_bf16_side side,
+                                                    int ntiles, int bid, int nb)
 {
     extern __shared__ __align__(16) float smt[];
     float *Bs = smt;                              // Bs[k * LDB + col] = B(k, col)
@@ -747,7 +765,7 @@ tall_small_res_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m
         const int gc = 4 * ty + j;
         zero[j] = gc >= ncols || (colmask && gc < c && colmask[gc]);
     }
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int tile = bid; tile < ntiles; tile += nb) {
         const int64_t row0 = (int64_t)tile * RT;
         __syncthreads();
         // stage Y(row0 .. row0 + 31, 0 .. m-1), 8 loads in flight per thread
@@ -798,6 +816,25 @@ tall_small_res_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256)
+tall_small_res_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int m, const float *__restrict__ B,
+                      int c, const int *__restrict__ colmask, const int *__restrict__ d_cols, float *__restrict__ Z,
+                      int64_t ldz, psd_bf16_side side, int ntiles)
+{
+    tall_small_res_body(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz, side, ntiles, blockIdx.x, gridDim.x);
+}
+
+// many problems in one launch: block b runs block bmap[b].y of entry
+// bmap[b].x, which strides over that entry's tiles by its nb
+__global__ void __launch_bounds__(256, 2)
+tall_small_res_grouped_kernel(const psd_g_tall *__restrict__ tab, const int2 *__restrict__ bmap)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_tall a = tab[b.x];
+    tall_small_res_body(a.Y, a.ldy, a.n, a.m, a.B, a.c, a.colmask, a.d_cols, a.Z, a.ldz, a.side, a.ntiles, b.y,
+                        a.nb);
 }
 
 }  // namespace
@@ -874,5 +911,37 @@ cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64
         tall_small_kernel<<<grid, 256, 0, s>>>(Y, ldy, n, m, B, c, colmask, d_cols, Z, ldz);
     }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cholesky_grouped(cudaStream_t s, const psd_g_chol *tab, int count, int m_max, int first_pass,
+                                    double tau, int *d_status)
+{
+    if (count < 1 || m_max < 1 || m_max > SMEM_M) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (first_pass) {
+        e = cudaFuncSetAttribute(cholesky_blocked_grouped_kernel<df>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)blocked_smem<df>(SMEM_M));
+        if (e != cudaSuccess) return e;
+        cholesky_blocked_grouped_kernel<df><<<(unsigned)count, NTB, blocked_smem<df>(m_max), s>>>(tab, (float)tau,
+                                                                                                  d_status);
+    } else {
+        e = cudaFuncSetAttribute(cholesky_blocked_grouped_kernel<float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blocked_smem<float>(SMEM_M));
+        if (e != cudaSuccess) return e;
+        cholesky_blocked_grouped_kernel<float><<<(unsigned)count, NTB, blocked_smem<float>(m_max), s>>>(
+            tab, (float)tau, d_status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tall_small_grouped(cudaStream_t s, const psd_g_tall *tab, const int2 *bmap, int nb, int m_max)
+{
+    if (nb < 1 || m_max < 1 || m_max > 128) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) * (size_t)m_max * (LDB + LDT);
+    cudaError_t e = cudaFuncSetAttribute(tall_small_res_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float) * 128 * (LDB + LDT)));
+    if (e != cudaSuccess) return e;
+    tall_small_res_grouped_kernel<<<(unsigned)nb, 256, smem, s>>>(tab, bmap);
     return cudaGetLastError();
 }

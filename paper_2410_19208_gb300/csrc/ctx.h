@@ -138,6 +138,16 @@ struct psdproj_ctx {
     int graph_streams = 0, graph_persist = 0;
     uint64_t graph_launches = 0;     // kernels in the graph (counted per replay)
     cudaStream_t capture_stream = nullptr;   // the stream a graph is recorded on
+    // psdproj_batched_grouped: a workspace and image(s) per problem (g_slots)
+    // and the grouped launches' tables (g_tabs); the recorded batch and what
+    // it was recorded for
+    void *g_slots = nullptr;  size_t g_slots_bytes = 0;
+    void *g_tabs = nullptr;   size_t g_tabs_bytes = 0;
+    cudaGraphExec_t g_exec = nullptr;
+    std::vector<psdproj_problem> g_probs;
+    psdproj_opts g_opts = {};
+    int g_streams = 0, g_persist = 0;
+    uint64_t g_launches = 0;
 };
 
 // PSDPROJ_OK when the budget of ctx's root allows replacing `old_bytes` of
@@ -243,6 +253,98 @@ cudaError_t launch_sym_pass_tc(cudaStream_t s, int sm_count, const uint16_t *Ab,
 cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float *Z,
                         int64_t ldz, int64_t n, int m, float *gpart, double *G,
                         int symmetrize, float *Gdf = nullptr, int sm_count = 0);
+
+// Rows per block of launch_gram's product kernel for the symmetric forms
+// with m <= 128 (about two blocks per SM, at least PSD_GRAM_CHUNK rows, so
+// that the partials fit a workspace sized for ceil(n / PSD_GRAM_CHUNK)
+// chunks), its block count, and the blocks of its reduction.
+inline int64_t psd_gram_rows(int64_t n, int sm_count)
+{
+    if (sm_count <= 0) sm_count = 148;
+    const int64_t rows = (n + 2 * sm_count - 1) / (2 * sm_count);
+    return psd_round_up(rows < PSD_GRAM_CHUNK ? PSD_GRAM_CHUNK : rows, 8);
+}
+inline int psd_gram_blocks(int64_t n, int sm_count)
+{
+    const int64_t rows = psd_gram_rows(n, sm_count);
+    return (int)((n + rows - 1) / rows);
+}
+inline int psd_gram_reduce_blocks(int m)
+{
+    const int nt8 = (int)psd_round_up(m, 8) / 8;
+    return (nt8 * (nt8 + 1) / 2 * 64 + 31) / 32;
+}
+
+// ---- grouped launches (psdproj_batched_grouped) --------------------------
+// One launch runs one small step for many problems.  Entry e of a table
+// holds the arguments problem e's own launch would take (all with m <= 128);
+// for the kernels with several blocks per problem, bmap[b] = (entry, block
+// of that entry) says what block b of the launch does; the one-block
+// kernels run entry b in block b.  Tables and maps live in device memory.
+struct psd_g_gram {          // launch_gram, symmetric forms, m <= 128
+    const float *X, *Z;      // Z: the two-sided form only
+    int64_t ldx, ldz, n;
+    int m, mp, rows, nblk;   // mp = round_up(m, 8); rows, nblk: psd_gram_rows / psd_gram_blocks
+    float *gpart;
+    double *G;
+    float2 *Gdf;             // may be NULL
+};
+// two: the two-sided form (S = (X^T Z + Z^T X)/2); nb / nb_red: the blocks
+// of the product and of the reduction (bmap: block < nblk of its entry;
+// bmap_red: block < psd_gram_reduce_blocks(m))
+cudaError_t launch_gram_grouped(cudaStream_t s, const psd_g_gram *tab, int two, const int2 *bmap, int nb,
+                                const int2 *bmap_red, int nb_red, int mp_max);
+
+struct psd_g_chol {          // launch_cholesky, m <= 128 (reads the double-float Gram)
+    const float2 *Gd;
+    int m;
+    float *Rinv;
+    int *dead;
+    int *d_qrank;            // may be NULL
+};
+cudaError_t launch_cholesky_grouped(cudaStream_t s, const psd_g_chol *tab, int count, int m_max, int first_pass,
+                                    double tau, int *d_status);
+
+constexpr int PSD_TALL_RT = 32;   // rows per tile of the tall x small product (m, c <= 128)
+struct psd_g_tall {          // launch_tall_small, m, c <= 128
+    const float *Y;
+    int64_t ldy, n;
+    int m;
+    const float *B;
+    int c;
+    const int *colmask, *d_cols;
+    float *Z;
+    int64_t ldz;
+    psd_bf16_side side;      // no side outputs: Xh = Y = NULL
+    int ntiles, nb;          // ntiles = ceil(n / PSD_TALL_RT); nb blocks stride over them
+};
+cudaError_t launch_tall_small_grouped(cudaStream_t s, const psd_g_tall *tab, const int2 *bmap, int nb, int m_max);
+
+struct psd_g_eig {           // launch_eig, m <= 128
+    const double *C;
+    int m;
+    float *V;
+    double *d;
+    float *scr;              // 3 (m+2)^2 floats
+    int *d_fail;             // the tridiagonal solver's failure flag
+};
+// blocks per problem of the Newton-Schulz kernels and of the Rayleigh quotients
+inline int psd_eig_ns_blocks(int m) { return ((m + 15) / 16) * ((m + 15) / 16); }
+// bmap_ns: block < psd_eig_ns_blocks(m) of its entry; bmap_ray: block < m
+cudaError_t launch_eig_grouped(cudaStream_t s, const psd_g_eig *tab, int count, const int2 *bmap_ns, int nb_ns,
+                               const int2 *bmap_ray, int nb_ray, int m_max, int *d_status, int method);
+cudaError_t launch_eig_tridiag_grouped(cudaStream_t s, const psd_g_eig *tab, int count, const int2 *bmap_ns,
+                                       int nb_ns, const int2 *bmap_ray, int nb_ray, int m_max,
+                                       int *d_status_on_fail);
+
+struct psd_g_factor {        // launch_factor_prep
+    const float *V;
+    const double *d;
+    int m;
+    float *M;
+    int *d_rank;
+};
+cudaError_t launch_factor_prep_grouped(cudaStream_t s, const psd_g_factor *tab, int count);
 
 // first_pass = 1: double-float factorization (FP64 when m > 128); 0: FP32.
 // Writes R^-1 (m x m column-major FP32), the dependent-column flags and

@@ -29,10 +29,9 @@ constexpr int NT = 512;
 constexpr int MAX_SWEEPS = 40;
 constexpr int MAXH = PSD_MAX_M / 2;
 
-__global__ void __launch_bounds__(NT, 1)
-eig_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
-           double *__restrict__ dout, float *gA, float *gV, int smem_A, int smem_V,
-           int *d_status, const int *only_if)
+__device__ __forceinline__ void eig_body(const double *__restrict__ C, int m, float *__restrict__ Vout,
+                                         double *__restrict__ dout, float *gA, float *gV, int smem_A, int smem_V,
+                                         int *d_status, const int *only_if)
 {
     // fallback use: run only when the tridiagonal solver flagged a failure
     if (only_if && *only_if == 0) return;
@@ -209,6 +208,24 @@ eig_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
     for (int i = tid; i < m; i += NT) dout[s_rank[i]] = (double)A[i * ld + i];
 }
 
+__global__ void __launch_bounds__(NT, 1)
+eig_kernel(const double *__restrict__ C, int m, float *__restrict__ Vout,
+           double *__restrict__ dout, float *gA, float *gV, int smem_A, int smem_V,
+           int *d_status, const int *only_if)
+{
+    eig_body(C, m, Vout, dout, gA, gV, smem_A, smem_V, d_status, only_if);
+}
+
+// many problems in one launch: block b solves entry b, with both matrices in
+// shared memory (m <= 128); fallback: only where the entry's tridiagonal
+// solver flagged a failure
+__global__ void __launch_bounds__(NT, 1)
+eig_grouped_kernel(const psd_g_eig *__restrict__ tab, int *d_status, int fallback)
+{
+    const psd_g_eig a = tab[blockIdx.x];
+    eig_body(a.C, a.m, a.V, a.d, a.scr, a.scr, 1, 1, d_status, fallback ? a.d_fail : nullptr);
+}
+
 }  // namespace
 
 cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double *d,
@@ -235,5 +252,24 @@ cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double 
                                          200 * 1024);
     if (e != cudaSuccess) return e;
     eig_kernel<<<1, NT, smem, s>>>(C, m, V, d, gA, gV, smem_A, smem_V, d_status, only_if);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eig_grouped(cudaStream_t s, const psd_g_eig *tab, int count, const int2 *bmap_ns, int nb_ns,
+                               const int2 *bmap_ray, int nb_ray, int m_max, int *d_status, int method)
+{
+    if (count < 1 || m_max < 1 || m_max > 128) return cudaErrorInvalidValue;
+    if (method != PSDPROJ_EIG_JACOBI) {
+        cudaError_t e = launch_eig_tridiag_grouped(s, tab, count, bmap_ns, nb_ns, bmap_ray, nb_ray, m_max,
+                                                   method == PSDPROJ_EIG_TRIDIAG ? d_status : nullptr);
+        if (e != cudaSuccess || method == PSDPROJ_EIG_TRIDIAG) return e;
+    }
+    const int mm = m_max + (m_max & 1);
+    const size_t matA = sizeof(float) * (((size_t)mm * (mm + 1) + 3) & ~(size_t)3);
+    const size_t matV = sizeof(float) * (size_t)mm * (mm + 4);
+    cudaError_t e = cudaFuncSetAttribute(eig_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         200 * 1024);
+    if (e != cudaSuccess) return e;
+    eig_grouped_kernel<<<(unsigned)count, NT, matA + matV, s>>>(tab, d_status, method == PSDPROJ_EIG_AUTO ? 1 : 0);
     return cudaGetLastError();
 }

@@ -183,10 +183,9 @@ __device__ void inverse_step(const float *d, const float *e, int m, float lambda
     for (int i = 0; i < m; ++i) x[i * ld] *= inv;
 }
 
-__global__ void __launch_bounds__(NT, 1)
-eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ Vout,
-                   double *__restrict__ dout, float *gscr, int *__restrict__ d_fail,
-                   int *d_status_on_fail)
+__device__ __forceinline__ void eig_tridiag_body(const double *__restrict__ C, int mfull, float *__restrict__ Vout,
+                                                 double *__restrict__ dout, float *gscr, int *__restrict__ d_fail,
+                                                 int *d_status_on_fail)
 {
     extern __shared__ float sm[];
     const bool in_smem = mfull <= SMEM_M;
@@ -735,6 +734,22 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     }
 }
 
+__global__ void __launch_bounds__(NT, 1)
+eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ Vout,
+                   double *__restrict__ dout, float *gscr, int *__restrict__ d_fail,
+                   int *d_status_on_fail)
+{
+    eig_tridiag_body(C, mfull, Vout, dout, gscr, d_fail, d_status_on_fail);
+}
+
+// many problems in one launch: block b solves entry b (m <= SMEM_M)
+__global__ void __launch_bounds__(NT, 1)
+eig_tridiag_grouped_kernel(const psd_g_eig *__restrict__ tab, int *d_status_on_fail)
+{
+    const psd_g_eig a = tab[blockIdx.x];
+    eig_tridiag_body(a.C, a.m, a.V, a.d, a.scr, a.d_fail, d_status_on_fail);
+}
+
 }  // namespace
 
 namespace {
@@ -744,13 +759,13 @@ namespace {
 // V^T V per 256 threads, columns staged 32 rows at a time.  V^T V further than
 // 1e-2 from I (or not finite) fails the solver: *d_fail = 1 and, when asked,
 // ENOCONV.
-__global__ void __launch_bounds__(256)
-ns_gram_kernel(const float *__restrict__ V, int m, float *__restrict__ S, float *__restrict__ Vc, int *d_fail,
-               int *d_status_on_fail)
+__device__ __forceinline__ void ns_gram_body(const float *__restrict__ V, int m, float *__restrict__ S,
+                                             float *__restrict__ Vc, int *d_fail, int *d_status_on_fail, int bx,
+                                             int by)
 {
     __shared__ float Va[32][17], Vb[32][17];
     __shared__ float s_dev[8];
-    const int a0 = blockIdx.x * 16, b0 = blockIdx.y * 16;
+    const int a0 = bx * 16, b0 = by * 16;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     float acc = 0.0f;
     for (int r0 = 0; r0 < m; r0 += 32) {
@@ -760,7 +775,7 @@ ns_gram_kernel(const float *__restrict__ V, int m, float *__restrict__ S, float 
             const float va = (okr && a0 + c < m) ? V[(int64_t)(a0 + c) * m + r0 + r] : 0.0f;
             Va[r][c] = va;
             Vb[r][c] = (okr && b0 + c < m) ? V[(int64_t)(b0 + c) * m + r0 + r] : 0.0f;
-            if (blockIdx.y == 0 && okr && a0 + c < m) Vc[(int64_t)(a0 + c) * m + r0 + r] = va;
+            if (by == 0 && okr && a0 + c < m) Vc[(int64_t)(a0 + c) * m + r0 + r] = va;
         }
         __syncthreads();
 #pragma unroll 8
@@ -788,12 +803,29 @@ ns_gram_kernel(const float *__restrict__ V, int m, float *__restrict__ S, float 
     }
 }
 
-// Vout = V S (m x m, column-major): a block of 16 x 16 entries per 256 threads
 __global__ void __launch_bounds__(256)
-ns_apply_kernel(const float *__restrict__ V, const float *__restrict__ S, int m, float *__restrict__ Vout)
+ns_gram_kernel(const float *__restrict__ V, int m, float *__restrict__ S, float *__restrict__ Vc, int *d_fail,
+               int *d_status_on_fail)
+{
+    ns_gram_body(V, m, S, Vc, d_fail, d_status_on_fail, blockIdx.x, blockIdx.y);
+}
+
+// the scratch of entry a: S, then the copy of V (as launch_eig_tridiag)
+__global__ void __launch_bounds__(256)
+ns_gram_grouped_kernel(const psd_g_eig *__restrict__ tab, const int2 *__restrict__ bmap, int *d_status_on_fail)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_eig a = tab[b.x];
+    const int g = (a.m + 15) / 16;
+    ns_gram_body(a.V, a.m, a.scr, a.scr + (size_t)a.m * a.m, a.d_fail, d_status_on_fail, b.y % g, b.y / g);
+}
+
+// Vout = V S (m x m, column-major): a block of 16 x 16 entries per 256 threads
+__device__ __forceinline__ void ns_apply_body(const float *__restrict__ V, const float *__restrict__ S, int m,
+                                              float *__restrict__ Vout, int bx, int by)
 {
     __shared__ float Vr[16][33], Sc[32][17];
-    const int r0 = blockIdx.x * 16, c0 = blockIdx.y * 16;
+    const int r0 = bx * 16, c0 = by * 16;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     float acc = 0.0f;
     for (int k0 = 0; k0 < m; k0 += 32) {
@@ -812,17 +844,31 @@ ns_apply_kernel(const float *__restrict__ V, const float *__restrict__ S, int m,
     if (r < m && c < m) Vout[(int64_t)c * m + r] = acc;
 }
 
+__global__ void __launch_bounds__(256)
+ns_apply_kernel(const float *__restrict__ V, const float *__restrict__ S, int m, float *__restrict__ Vout)
+{
+    ns_apply_body(V, S, m, Vout, blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(256)
+ns_apply_grouped_kernel(const psd_g_eig *__restrict__ tab, const int2 *__restrict__ bmap)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_eig a = tab[b.x];
+    const int g = (a.m + 15) / 16;
+    ns_apply_body(a.scr + (size_t)a.m * a.m, a.scr, a.m, a.V, b.y % g, b.y / g);
+}
+
 // d_i <- v_i^T C v_i / v_i^T v_i in FP64: the Rayleigh quotient of the computed
 // eigenvector against the FP64 core matrix, whose error is quadratic in the
 // vector's (FP32 vectors orthonormal to ~1e-7 give eigenvalues to ~1e-14
 // ||C||).  Where the quotient and the FP32 eigenvalue disagree in sign the
 // eigenvalue is indistinguishable from zero at FP32 accuracy: 0.  Exact
 // zeros (the removed zero rows) stay zero.  One block per eigenpair.
-__global__ void __launch_bounds__(256)
-eig_rayleigh_kernel(const double *__restrict__ C, const float *__restrict__ V, int m, double *__restrict__ d)
+__device__ __forceinline__ void eig_rayleigh_body(const double *__restrict__ C, const float *__restrict__ V, int m,
+                                                  double *__restrict__ d, int i)
 {
     __shared__ double s_red[2][8];
-    const int i = blockIdx.x;
     const float *v = V + (int64_t)i * m;
     double acc = 0.0, nn = 0.0;              // v^T C v and v^T v
     for (int r = threadIdx.x; r < m; r += 256) {
@@ -854,6 +900,20 @@ eig_rayleigh_kernel(const double *__restrict__ C, const float *__restrict__ V, i
     }
 }
 
+__global__ void __launch_bounds__(256)
+eig_rayleigh_kernel(const double *__restrict__ C, const float *__restrict__ V, int m, double *__restrict__ d)
+{
+    eig_rayleigh_body(C, V, m, d, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+eig_rayleigh_grouped_kernel(const psd_g_eig *__restrict__ tab, const int2 *__restrict__ bmap)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_eig a = tab[b.x];
+    eig_rayleigh_body(a.C, a.V, a.m, a.d, b.y);
+}
+
 }  // namespace
 
 cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V, double *d,
@@ -881,5 +941,28 @@ cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     eig_rayleigh_kernel<<<m, 256, 0, s>>>(C, V, m, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eig_tridiag_grouped(cudaStream_t s, const psd_g_eig *tab, int count, const int2 *bmap_ns,
+                                       int nb_ns, const int2 *bmap_ray, int nb_ray, int m_max,
+                                       int *d_status_on_fail)
+{
+    if (count < 1 || nb_ns < 1 || nb_ray < 1 || m_max < 1 || m_max > SMEM_M) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) * (3 * (size_t)m_max + 8) * (m_max + 1);
+    constexpr size_t smem_max = sizeof(float) * (3 * (size_t)SMEM_M + 8) * (SMEM_M + 1);
+    cudaError_t e = cudaFuncSetAttribute(eig_tridiag_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_max);
+    if (e != cudaSuccess) return e;
+    eig_tridiag_grouped_kernel<<<(unsigned)count, NT, smem, s>>>(tab, d_status_on_fail);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ns_gram_grouped_kernel<<<(unsigned)nb_ns, 256, 0, s>>>(tab, bmap_ns, d_status_on_fail);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ns_apply_grouped_kernel<<<(unsigned)nb_ns, 256, 0, s>>>(tab, bmap_ns);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    eig_rayleigh_grouped_kernel<<<(unsigned)nb_ray, 256, 0, s>>>(tab, bmap_ray);
     return cudaGetLastError();
 }

@@ -9,8 +9,8 @@ namespace {
 
 // M = V diag(sqrt(max(d, 0))) and the count of positive eigenvalues; one
 // root per column (FP64 roots are slow on this GPU), then the scaling
-__global__ void factor_prep_kernel(const float *__restrict__ V, const double *__restrict__ d,
-                                   int m, float *__restrict__ M, int *__restrict__ d_rank)
+__device__ __forceinline__ void factor_prep_body(const float *__restrict__ V, const double *__restrict__ d, int m,
+                                                 float *__restrict__ M, int *__restrict__ d_rank)
 {
     __shared__ int s_r;
     __shared__ float s_g[PSD_MAX_M];
@@ -24,6 +24,19 @@ __global__ void factor_prep_kernel(const float *__restrict__ V, const double *__
     __syncthreads();
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) M[e] = V[e] * s_g[e / m];
     if (threadIdx.x == 0 && d_rank) *d_rank = s_r;
+}
+
+__global__ void factor_prep_kernel(const float *__restrict__ V, const double *__restrict__ d,
+                                   int m, float *__restrict__ M, int *__restrict__ d_rank)
+{
+    factor_prep_body(V, d, m, M, d_rank);
+}
+
+// many problems in one launch: block b prepares entry b
+__global__ void factor_prep_grouped_kernel(const psd_g_factor *__restrict__ tab)
+{
+    const psd_g_factor a = tab[blockIdx.x];
+    factor_prep_body(a.V, a.d, a.m, a.M, a.d_rank);
 }
 
 // P tile (I, J), I <= J, 128 x 128, 256 threads, 8 x 8 micro-tiles.
@@ -115,6 +128,13 @@ cudaError_t launch_factor_prep(cudaStream_t s, const float *V, const double *d, 
                                int *d_rank)
 {
     factor_prep_kernel<<<1, 1024, 0, s>>>(V, d, m, M, d_rank);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factor_prep_grouped(cudaStream_t s, const psd_g_factor *tab, int count)
+{
+    if (count < 1) return cudaErrorInvalidValue;
+    factor_prep_grouped_kernel<<<(unsigned)count, 1024, 0, s>>>(tab);
     return cudaGetLastError();
 }
 

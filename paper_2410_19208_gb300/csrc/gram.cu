@@ -226,9 +226,9 @@ constexpr int SR = 64;            // rows staged at a time
 constexpr int NTU = 160;          // >= tiles of the upper triangle for m <= 128 (136)
 
 template <bool TWO>
-__global__ void __launch_bounds__(NTU)
-gram_upper_kernel(const float *__restrict__ X, int64_t ldx, const float *__restrict__ Z, int64_t ldz, int64_t n,
-                  int m, int mp, int rows, float *__restrict__ gpart)
+__device__ __forceinline__ void gram_upper_body(const float *__restrict__ X, int64_t ldx,
+                                                const float *__restrict__ Z, int64_t ldz, int64_t n, int m,
+                                                int mp, int rows, float *__restrict__ gpart, int bid)
 {
     extern __shared__ __align__(16) float sgu[];
     const int ld = mp + 4;
@@ -251,7 +251,7 @@ gram_upper_kernel(const float *__restrict__ X, int64_t ldx, const float *__restr
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[i][j] = 0.0f;
-    const int64_t rbeg = (int64_t)blockIdx.x * rows;
+    const int64_t rbeg = (int64_t)bid * rows;
     const int64_t rend = min(rbeg + rows, n);
     for (int64_t r0 = rbeg; r0 < rend; r0 += SR) {
         const int nr = (int)min((int64_t)SR, rend - r0);
@@ -308,7 +308,7 @@ gram_upper_kernel(const float *__restrict__ X, int64_t ldx, const float *__restr
         }
     }
     if (act) {
-        float *out = gpart + ((int64_t)blockIdx.x * ntiles + tid) * 64;
+        float *out = gpart + ((int64_t)bid * ntiles + tid) * 64;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             reinterpret_cast<float4 *>(out + 8 * i)[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
@@ -317,20 +317,38 @@ gram_upper_kernel(const float *__restrict__ X, int64_t ldx, const float *__restr
     }
 }
 
+template <bool TWO>
+__global__ void __launch_bounds__(NTU)
+gram_upper_kernel(const float *__restrict__ X, int64_t ldx, const float *__restrict__ Z, int64_t ldz, int64_t n,
+                  int m, int mp, int rows, float *__restrict__ gpart)
+{
+    gram_upper_body<TWO>(X, ldx, Z, ldz, n, m, mp, rows, gpart, blockIdx.x);
+}
+
+// many problems in one launch: block b runs block bmap[b].y of entry bmap[b].x
+template <bool TWO>
+__global__ void __launch_bounds__(NTU)
+gram_upper_grouped_kernel(const psd_g_gram *__restrict__ tab, const int2 *__restrict__ bmap)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_gram a = tab[b.x];
+    gram_upper_body<TWO>(a.X, a.ldx, TWO ? a.Z : a.X, TWO ? a.ldz : a.ldx, a.n, a.m, a.mp, a.rows, a.gpart, b.y);
+}
+
 // G from the per-block partials of gram_upper_kernel: a block takes 32
 // consecutive positions q of the tile-major partial (lane = position, so the
 // loads are coalesced) and its 8 warps split the block partials (warp g:
 // partials g, g + 8, ...), each summing in double-float; the 8 sums are
 // added in a fixed order (deterministic).  Both (a, b) and (b, a) are
 // written (scale: 1 for X^T X, 1/2 for the two-sided form).
-__global__ void __launch_bounds__(256)
-gram_upper_reduce_kernel(const float *__restrict__ gpart, int nblk, int m, int mp, float scale,
-                         double *__restrict__ G, float2 *__restrict__ Gdf)
+__device__ __forceinline__ void gram_upper_reduce_body(const float *__restrict__ gpart, int nblk, int m, int mp,
+                                                       float scale, double *__restrict__ G,
+                                                       float2 *__restrict__ Gdf, int bid)
 {
     __shared__ fsum part[8][32];
     const int nt8 = mp / 8, ntiles = nt8 * (nt8 + 1) / 2;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int q = blockIdx.x * 32 + lane;
+    const int q = bid * 32 + lane;
     const bool inr = q < ntiles * 64;
     fsum acc = {0.0f, 0.0f};
     if (inr) {
@@ -362,6 +380,21 @@ gram_upper_reduce_kernel(const float *__restrict__ gpart, int nblk, int m, int m
     }
 }
 
+__global__ void __launch_bounds__(256)
+gram_upper_reduce_kernel(const float *__restrict__ gpart, int nblk, int m, int mp, float scale,
+                         double *__restrict__ G, float2 *__restrict__ Gdf)
+{
+    gram_upper_reduce_body(gpart, nblk, m, mp, scale, G, Gdf, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256)
+gram_upper_reduce_grouped_kernel(const psd_g_gram *__restrict__ tab, const int2 *__restrict__ bmap, float scale)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_gram a = tab[b.x];
+    gram_upper_reduce_body(a.gpart, a.nblk, a.m, a.mp, scale, a.G, a.Gdf, b.y);
+}
+
 }  // namespace
 
 // symmetrize: 0 = G = X^T Z as is; 1 = X == Z (upper computed, mirrored);
@@ -376,10 +409,8 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
         // fit the workspace sized for ceil(n / PSD_GRAM_CHUNK) chunks of mp^2),
         // about two blocks per SM
         const int mp = (int)psd_round_up(m, 8);
-        if (sm_count <= 0) sm_count = 148;
-        int64_t rows = (n + 2 * sm_count - 1) / (2 * sm_count);
-        rows = psd_round_up(rows < PSD_GRAM_CHUNK ? PSD_GRAM_CHUNK : rows, 8);
-        const int nblk = (int)((n + rows - 1) / rows);
+        const int64_t rows = psd_gram_rows(n, sm_count);
+        const int nblk = psd_gram_blocks(n, sm_count);
         const bool two = symmetrize == 2;
         const size_t smem = sizeof(float) * (size_t)SR * (mp + 4) * (two ? 2 : 1);
         if (two) {
@@ -394,9 +425,7 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
             gram_upper_kernel<false><<<nblk, NTU, smem, s>>>(X, ldx, X, ldx, n, m, mp, (int)rows, gpart);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const int nt8 = mp / 8;
-        const int npos = nt8 * (nt8 + 1) / 2 * 64;
-        gram_upper_reduce_kernel<<<(unsigned)((npos + 31) / 32), 256, 0, s>>>(
+        gram_upper_reduce_kernel<<<(unsigned)psd_gram_reduce_blocks(m), 256, 0, s>>>(
             gpart, nblk, m, mp, two ? 0.5f : 1.0f, G, reinterpret_cast<float2 *>(Gdf));
         return cudaGetLastError();
     }
@@ -432,5 +461,27 @@ cudaError_t launch_gram(cudaStream_t s, const float *X, int64_t ldx, const float
     const int64_t threads = (int64_t)mp * mp * 8;
     gram_reduce_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(gpart, nchunk, m, mp, symmetrize, G,
                                                                           reinterpret_cast<float2 *>(Gdf));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_grouped(cudaStream_t s, const psd_g_gram *tab, int two, const int2 *bmap, int nb,
+                                const int2 *bmap_red, int nb_red, int mp_max)
+{
+    if (nb < 1 || nb_red < 1 || mp_max < 8 || mp_max > 128) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(float) * (size_t)SR * (mp_max + 4) * (two ? 2 : 1);
+    // process-wide attributes: the largest size (m = 128)
+    const int smax = (int)(sizeof(float) * SR * (128 + 4) * (two ? 2 : 1));
+    cudaError_t e = two ? cudaFuncSetAttribute(gram_upper_grouped_kernel<true>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smax)
+                        : cudaFuncSetAttribute(gram_upper_grouped_kernel<false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+    if (e != cudaSuccess) return e;
+    if (two)
+        gram_upper_grouped_kernel<true><<<(unsigned)nb, NTU, smem, s>>>(tab, bmap);
+    else
+        gram_upper_grouped_kernel<false><<<(unsigned)nb, NTU, smem, s>>>(tab, bmap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gram_upper_reduce_grouped_kernel<<<(unsigned)nb_red, 256, 0, s>>>(tab, bmap_red, two ? 0.5f : 1.0f);
     return cudaGetLastError();
 }

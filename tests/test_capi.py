@@ -74,6 +74,8 @@ def test_batched_descriptor_layout_and_rejection(lib):
     assert ps.Problem.seed.offset == 40 and ps.Problem.d_rank.offset == 104
     # no context: argument error before any device work
     assert lib.psdproj_batched(None, 1, None, None) == 1
+    assert lib.psdproj_batched_grouped(None, 1, None, None) == 1
+    assert lib.psdproj_batched_grouped(None, -1, None, None) == 1
 
 
 def test_struct_layouts_match_the_c_header(tmp_path):

@@ -963,6 +963,127 @@ def test_batched_graph_replays_the_batch(ctx, oracle_lib):
         c.close()
 
 
+# a ragged batch for the grouped path: sides from 64 to 2048 (odd ones and
+# several 256-row block rows), widths 2 .. 128 (the grouped kernels' limit),
+# q = 0, 1, 2 and both algorithms
+GROUPED_BATCH = [
+    (64, 8, 4, 0, 1), (97, 12, 8, 1, 2), (130, 16, 8, 2, 1), (255, 30, 8, 1, 2), (300, 120, 8, 1, 1),
+    (517, 64, 8, 0, 2), (1024, 64, 8, 2, 1), (1500, 100, 10, 1, 2), (77, 2, 0, 1, 1), (640, 40, 8, 1, 2),
+]
+
+
+def _grouped_problems(specs, seed0):
+    probs, mats = [], []
+    for i, (n, k, p, q, alg) in enumerate(specs):
+        Vr, lam = si.make_problem("batch", n, seed_u=seed0 + i, seed_lam=seed0 + 100 + i)
+        A32 = si.form_A_numpy(Vr, lam).astype(np.float32)
+        mats.append(A32)
+        d = dict(A=torch.from_numpy(A32).cuda(), k=k, p=p, q=q, seed=seed0 + 7 * i, algorithm=alg,
+                 P=torch.full((n, n), float("nan"), device="cuda"), W=ps.tall_empty(n, k + p),
+                 rank=torch.full((1,), -1, dtype=torch.int32, device="cuda"))
+        if alg == 2:
+            d["alpha_out"] = torch.zeros(1, dtype=torch.float64, device="cuda")
+            d["info"] = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        probs.append(d)
+    return probs, mats
+
+
+def test_batched_grouped_matches_the_oracle_on_a_ragged_batch(ctx, oracle_lib):
+    """psdproj_batched_grouped in the FP32 form: every problem of a ragged
+    batch (sides 64..1500, widths 2..128, q = 0..2, both algorithms) against
+    the oracle, on the first call (recorded) and on a replay."""
+    probs, mats = _grouped_problems(GROUPED_BATCH, 400)
+    refs = []
+    for d, A32 in zip(probs, mats):
+        A64 = A32.astype(np.float64)
+        if d["algorithm"] == 1:
+            r = oracle_lib.alg1(A64, d["k"], d["p"], d["q"], d["seed"])
+            refs.append((r["W"] @ r["W"].T, r["rplus"], None))
+        else:
+            r = oracle_lib.alg2(A64, d["k"], d["p"], d["q"], d["seed"], N=10)
+            _, s1, s2 = oracle_lib.min_eig(A64, 10, d["seed"])
+            refs.append((r["W_red"] @ r["W_red"].T, r["rplus"], (r["alpha"], s1 + s2)))
+    c = ps.Context(0)
+    c.set_batch_streams(4)
+    try:
+        for rep in range(2):                     # record, then replay
+            for d in probs:
+                d["P"].fill_(float("nan"))
+                d["rank"].fill_(-1)
+            c.batched(probs, grouped=True)
+            assert c.sync_status() == 0
+            for d, (Pref, rplus, al) in zip(probs, refs):
+                n = d["A"].shape[0]
+                P = d["P"].cpu().numpy().astype(np.float64)
+                W = d["W"].cpu().numpy().astype(np.float64)
+                assert np.all(np.isfinite(P)), n
+                assert _rel(P, Pref) <= TOL, (rep, n, _rel(P, Pref))
+                assert int(d["rank"].item()) == rplus, n
+                assert _rel(W @ W.T, P) <= 1e-5
+                if al is not None:
+                    assert int(d["info"].item()) == 0
+                    assert abs(d["alpha_out"].item() - al[0]) <= 1e-5 * al[1]
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("variant", ["bf16", "bf16_ritz", "tf32"])
+def test_batched_grouped_matches_single_calls(ctx, oracle_lib, variant):
+    """The grouped batch in the tensor-core forms (and the Ritz variant of
+    alpha, whose extra steps run per problem) against psdproj_alg1 /
+    psdproj_alg2 called one problem at a time with the same options: the
+    factors agree within the forms' run-to-run spread, P = W W^T, and the
+    batch with larger sides (up to 2048) replays."""
+    prec = ps.PREC_TF32 if variant == "tf32" else ps.PREC_BF16
+    kw = dict(alpha_mode=ps.ALPHA_RITZ) if variant == "bf16_ritz" else {}
+    opts = ps.make_opts(prec=prec, syrk_prec=ps.PREC_BF16X3, **kw)
+    specs = GROUPED_BATCH + [(2048, 64, 8, 1, 1), (1800, 96, 8, 1, 2)]
+    probs, _ = _grouped_problems(specs, 800)
+    c = ps.Context(0)
+    c.set_batch_streams(8)
+    try:
+        for _ in range(2):
+            for d in probs:
+                d["W"].fill_(float("nan"))
+            c.batched(probs, opts=opts, grouped=True)
+            assert c.sync_status() == 0
+        for d in probs:
+            n = d["A"].shape[0]
+            W1 = ps.tall_empty(n, d["k"] + d["p"])
+            rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+            fn = ctx.alg1 if d["algorithm"] == 1 else ctx.alg2
+            fn(d["A"], d["k"], d["p"], d["q"], d["seed"], W=W1, P=torch.empty(n, n, device="cuda"), rank=rank,
+               opts=opts)
+            assert ctx.sync_status() == 0
+            ref = W1.cpu().numpy().astype(np.float64)
+            got = d["W"].cpu().numpy().astype(np.float64)
+            rel = np.sqrt(max(oracle_lib.factor_dist2(got, ref), 0.0) / oracle_lib.factor_norm2(ref))
+            assert rel <= 2e-3, (n, rel)
+            assert int(d["rank"].item()) == int(rank.item())
+            Pg = d["P"].cpu().numpy().astype(np.float64)
+            assert np.abs(Pg - got @ got.T).max() <= 3e-5 * (np.abs(got) @ np.abs(got).T).max() + 1e-7
+    finally:
+        c.close()
+
+
+def test_batched_grouped_rejects_what_it_does_not_group(ctx):
+    """Widths above 128 and the deterministic form: ENOTSUP before anything
+    runs; bad problems: EINVAL, as psdproj_batched."""
+    n = 300
+    A = torch.zeros(n, n, device="cuda")
+    P = torch.full((n, n), 7.0, device="cuda")
+    good = dict(A=A, k=8, p=4, q=0, seed=1, algorithm=1, P=P)
+    wide = dict(A=A, k=125, p=4, q=0, seed=1, algorithm=1, P=P)
+    for probs, opts, code in (([good, wide], None, 7), ([good], ps.make_opts(deterministic=1), 7),
+                              ([good, dict(good, algorithm=3)], None, 1)):
+        with pytest.raises(ps.PsdprojError) as ei:
+            ctx.batched(probs, opts=opts, grouped=True)
+        assert ei.value.code == code
+    assert ctx.sync_status() == 0
+    assert torch.all(P == 7.0)
+    ctx.batched([], grouped=True)
+
+
 @pytest.mark.gpu
 def test_tune_batch_picks_a_lane_count_and_stores_it(ctx, oracle_lib, tmp_path, monkeypatch):
     """psdproj_tune_batch times the batch on 2, 4, 8 and 16 lanes, sets the
