@@ -11,6 +11,7 @@ that an oversized problem is rejected before anything runs, and that a host
 pointer is refused.  This file is named to be collected last.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -56,17 +57,24 @@ def test_noalloc_min_eig_matches_regular_entry_point(n, seed):
     for i in range(2):  # two calls in a row share the same scratch
         if i == 1:
             # nothing is allocated by the call: the device's free memory and
-            # torch's allocator are unchanged across it
+            # torch's allocator are unchanged across it (earlier tests'
+            # cyclic garbage collected first, the collector held off while
+            # measuring, so that no tensor is freed in between)
+            gc.collect()
+            gc.disable()
+        try:
             free0, _ = torch.cuda.mem_get_info()
-            alloc0 = torch.cuda.memory_allocated()
-            reserved0 = torch.cuda.memory_reserved()
-        code = _noalloc(A, 10, seed, stream, out)
-        assert code == 0, ps.STATUS.get(code)
-        torch.cuda.synchronize()
-        if i == 1:
+            alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+            code = _noalloc(A, 10, seed, stream, out)
+            torch.cuda.synchronize()
             free1, _ = torch.cuda.mem_get_info()
+            alloc1, reserved1 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+        finally:
+            gc.enable()
+        assert code == 0, ps.STATUS.get(code)
+        if i == 1:
             assert free1 == free0
-            assert torch.cuda.memory_allocated() == alloc0 and torch.cuda.memory_reserved() == reserved0
+            assert alloc1 == alloc0 and reserved1 == reserved0
         got = out.cpu().numpy()
         assert np.all(np.abs(got - ref) <= tol), (got, ref)
 
