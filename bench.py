@@ -336,7 +336,7 @@ def run_batched(args, emit=True):
                   "gpu_launches": launches, "clocks": clocks}
     # the same batch recorded once into a CUDA graph and replayed
     # (psdproj_batched_graph), with the stream counts that pay most
-    for S in (8, 16):
+    for S in (16, 32):
         ctx.set_batch_streams(S)
         for _ in range(max(args.warmup, 3)):
             ctx.batched(probs, opts=opts, graph=True)
@@ -359,7 +359,7 @@ def run_batched(args, emit=True):
     # the grouped batch (psdproj_batched_grouped): the small steps of all
     # problems as one launch per step, the streaming steps on the lanes, the
     # whole batch recorded once into a CUDA graph and replayed
-    for S in (8, 16):
+    for S in (16, 32, 64):
         ctx.set_batch_streams(S)
         for _ in range(max(args.warmup, 3)):
             ctx.batched(probs, opts=opts, grouped=True)

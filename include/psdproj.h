@@ -290,13 +290,13 @@ int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *pr
 int psdproj_batched_grouped(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
                             const psdproj_opts *opts);
 
-/* Number of helper streams psdproj_batched spreads a batch over (1..16,
+/* Number of helper streams psdproj_batched spreads a batch over (1..64,
  * default 8; 1 = the context's own stream only).  Each helper holds its own
  * workspace, sized for the largest problem it has run. */
 int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams);
 
 /* Batch autotuning.  psdproj_tune_batch runs `probs` (as psdproj_batched_graph
- * does) on 2, 4, 8 and 16 helper streams, one recording run and `reps` timed
+ * does) on 2, 4, 8, 16, 32 and 64 helper streams, one recording run and `reps` timed
  * replays each on the context's stream, keeps the fastest, sets it on the
  * context (as psdproj_set_batch_streams) and stores it in the tuning table
  * under the batch's bucket: (device name, SM count, floor(log2 of the median
@@ -305,7 +305,7 @@ int psdproj_set_batch_streams(psdproj_ctx *ctx, int streams);
  * (time per batch; either may be NULL) report the choice.
  *
  * psdproj_batched and psdproj_batched_graph use, in this order: the
- * environment variable PSDPROJ_BATCH_STREAMS (1..16); the context's own lane
+ * environment variable PSDPROJ_BATCH_STREAMS (1..64); the context's own lane
  * count if set; the tuning table's entry for the batch's bucket; the default
  * 8.  The table lives in the process and, when PSDPROJ_TUNE_CACHE names a
  * file, in that file (one "key<TAB>streams" line per entry; when the

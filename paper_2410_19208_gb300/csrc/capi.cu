@@ -373,6 +373,10 @@ struct proj_call {
     int *d_rank = nullptr;
     psdproj_opts opts = {};
     bool omega_ready = false;            // Omega already in the workspace (warm start of Alg. 6)
+    // set by the grouped batch for the phases it runs as grouped launches
+    bool omega_prepared = false;         // Omega and its BF16 side outputs already written
+    bool w_split = false;                // W's BF16 high and low parts written with W
+    bool rank_written = false;           // the factor step wrote *d_rank
     // set by proj_begin
     const double *shift = nullptr;       // device shift of the power products (NULL: none)
     bool fuse = false;                   // BF16 side outputs written by X's producers
@@ -394,6 +398,14 @@ const double *proj_shift(const proj_call &pc, const psd_workspace &ws)
     return pc.scaled ? ws.scal + SC_SHIFT : nullptr;
 }
 
+// The core C also as double-float pairs (m <= 128: the Gram reduction's own
+// sums, in the orthonormalisation's then unused scratch), for the
+// eigenvalues' Rayleigh quotients; NULL for wider sketches
+float *core_gdf(const psd_workspace &ws, int m)
+{
+    return m <= 128 ? reinterpret_cast<float *>(ws.cholscr) : nullptr;
+}
+
 // The BF16 pass's side outputs for the next pass over ctx's workspace
 psd_bf16_side proj_side(psdproj_ctx *ctx, const double *next_shift)
 {
@@ -401,25 +413,27 @@ psd_bf16_side proj_side(psdproj_ctx *ctx, const double *next_shift)
     return psd_bf16_side{ws.Xhi, ws.ld, ws.Y, ws.ld, next_shift};
 }
 
-// The image of A, alpha (Alg. 3), Omega (Alg. 1) and Y = (A + shift I) Omega
-int proj_begin(psdproj_ctx *ctx, proj_call &pc)
+// the tensor-core forms read A once here and their image(s) in every later pass
+int proj_pack(psdproj_ctx *ctx, const proj_call &pc)
 {
-    psdproj_opts &opts = pc.opts;
+    if (pc.opts.prec == PSDPROJ_PREC_FP32) return PSDPROJ_OK;
+    return pack_image(ctx, pc.dA, pc.n, pc.lda, pc.opts.prec);
+}
+
+// Alg. 3's alpha by Alg. 5 (two power iterations, Alg. 4) unless given or
+// taken from the Ritz values (proj_sketch), and the shift it sets
+int proj_alpha(psdproj_ctx *ctx, const proj_call &pc)
+{
+    if (!pc.scaled || proj_ritz(pc)) return PSDPROJ_OK;
+    const psdproj_opts &opts = pc.opts;
     psd_workspace &ws = ctx->ws;
     cudaStream_t s = ctx->stream;
     const float *dA = pc.dA;
     const int64_t n = pc.n, lda = pc.lda;
-    const int m = pc.m;
     const uint64_t seed = pc.seed;
     const double alpha_in = pc.alpha_in;
-    const double *shift = nullptr;
     const bool bf16 = opts.prec == PSDPROJ_PREC_BF16;
-    const bool tc = opts.prec != PSDPROJ_PREC_FP32;
-    // the tensor-core forms read A once here and their image(s) in every later pass
-    if (tc) PSD_TRY(pack_image(ctx, dA, n, lda, opts.prec));
-    // variant: alpha from the Ritz values of the unshifted sketch (below)
-    const bool ritz = proj_ritz(pc);
-    if (pc.scaled && !ritz) {
+    {
         double *sc = ws.scal;
         if (!(alpha_in > 0.0)) {
             stage_scope st(ctx, PSDPROJ_STAGE_GEMV);
@@ -448,16 +462,31 @@ int proj_begin(psdproj_ctx *ctx, proj_call &pc)
         PSD_KL(launch_alpha_finish(s, sc + SC_SIGMA1, sc + SC_SIGMA2, alpha_in,
                                    pc.d_alpha_out ? pc.d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
                                    pc.d_info ? pc.d_info : ws.ints + IN_INFO), 1);
-        shift = sc + SC_SHIFT;
     }
+    return PSDPROJ_OK;
+}
+
+// Omega (Alg. 1) and Y = (A + shift I) Omega, after proj_pack and proj_alpha
+// (the Ritz variant of alpha: its unshifted sketch first)
+int proj_sketch(psdproj_ctx *ctx, proj_call &pc)
+{
+    psdproj_opts &opts = pc.opts;
+    psd_workspace &ws = ctx->ws;
+    cudaStream_t s = ctx->stream;
+    const float *dA = pc.dA;
+    const int64_t n = pc.n, lda = pc.lda;
+    const int m = pc.m;
+    const uint64_t seed = pc.seed;
+    const bool ritz = proj_ritz(pc);
+    const double *shift = pc.scaled && !ritz ? ws.scal + SC_SHIFT : nullptr;
     const int lpad = psd_lpad(m);
     // BF16 form: every kernel that writes the next pass's X (Omega, the last
     // product of each CholeskyQR2) also writes that pass's BF16 image of X
     // and starts its Y, so the passes need no conversion sweep
     const bool fuse = proj_fuse(pc);
-    bool prepared = false;
+    bool prepared = pc.omega_prepared && fuse;
     // Omega (Alg. 1), then Y = (A + shift I) Omega
-    if (!pc.omega_ready) {
+    if (!pc.omega_ready && !pc.omega_prepared) {
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
         if (opts.sketch == PSDPROJ_SKETCH_SRHT) {
             PSD_KL(launch_srht(s, seed, n, m, lpad, ws.ld, ws.picks, ctx->d_status, ws.Om, ws.ld), 2);
@@ -476,14 +505,15 @@ int proj_begin(psdproj_ctx *ctx, proj_call &pc)
         PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Om, ws.ld, m, nullptr, ws.Y, ws.ld, opts.prec));
         PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK));
         PSD_TRY(sym_pass(ctx, dA, n, lda, ws.Q, ws.ld, m, nullptr, ws.W, ws.ld, opts.prec));
+        float *cdf = core_gdf(ws, m);
         {
             stage_scope st(ctx, PSDPROJ_STAGE_CORE);
-            PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.W, ws.ld, n, m, ws.gpart, ws.C, 2, nullptr, ctx->persist_sms), 2);
+            PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.W, ws.ld, n, m, ws.gpart, ws.C, 2, cdf, ctx->persist_sms), 2);
         }
         {
             stage_scope st(ctx, PSDPROJ_STAGE_EIG);
             PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, opts.eig,
-                              ws.ints + IN_EIGFAIL), psd_eig_launches(opts.eig));
+                              ws.ints + IN_EIGFAIL, cdf), psd_eig_launches(opts.eig));
         }
         stage_scope st(ctx, PSDPROJ_STAGE_OTHER);
         PSD_KL(launch_ritz_alpha(s, ws.d, m, pc.d_alpha_out ? pc.d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
@@ -496,6 +526,14 @@ int proj_begin(psdproj_ctx *ctx, proj_call &pc)
     pc.shift = shift;
     pc.fuse = fuse;
     return PSDPROJ_OK;
+}
+
+// The image of A, alpha (Alg. 3), Omega (Alg. 1) and Y = (A + shift I) Omega
+int proj_begin(psdproj_ctx *ctx, proj_call &pc)
+{
+    PSD_TRY(proj_pack(ctx, pc));
+    PSD_TRY(proj_alpha(ctx, pc));
+    return proj_sketch(ctx, pc);
 }
 
 // power product: Y = (A + shift I) Q
@@ -522,14 +560,15 @@ int proj_core_small(psdproj_ctx *ctx, const proj_call &pc)
     cudaStream_t s = ctx->stream;
     const int64_t n = pc.n;
     const int m = pc.m;
+    float *cdf = core_gdf(ws, m);
     {
         stage_scope st(ctx, PSDPROJ_STAGE_CORE);
-        PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.Y, ws.ld, n, m, ws.gpart, ws.C, 2, nullptr, ctx->persist_sms), 2);
+        PSD_KL(launch_gram(s, ws.Q, ws.ld, ws.Y, ws.ld, n, m, ws.gpart, ws.C, 2, cdf, ctx->persist_sms), 2);
     }
     {
         stage_scope st(ctx, PSDPROJ_STAGE_EIG);
         PSD_KL(launch_eig(s, ws.C, m, ws.V, ws.d, ws.eigscr, ctx->d_status, pc.opts.eig,
-                          ws.ints + IN_EIGFAIL), psd_eig_launches(pc.opts.eig));
+                          ws.ints + IN_EIGFAIL, cdf), psd_eig_launches(pc.opts.eig));
     }
     int *rk = ws.ints + IN_RANK;
     stage_scope st(ctx, PSDPROJ_STAGE_FACTOR);
@@ -557,9 +596,11 @@ int proj_finish(psdproj_ctx *ctx, const proj_call &pc)
             PSD_KL(launch_syrk_simt(s, Wd, ldwd, pc.n, m, rk, pc.dP, pc.ldp, upper), 1);
         else
             PSD_KL(launch_syrk_tc(s, ctx->persist_sms, Wd, ldwd, pc.n, m, rk, pc.dP, pc.ldp, upper, ws.Xhi,
-                                  ws.Xlo, ws.ld, ctx->d_status, ctx->wait_limit), 2);
+                                  ws.Xlo, ws.ld, ctx->d_status, ctx->wait_limit, pc.w_split ? 1 : 0),
+                   pc.w_split ? 1 : 2);
     }
-    if (pc.d_rank) PSD_CK(cudaMemcpyAsync(pc.d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    if (pc.d_rank && !pc.rank_written)
+        PSD_CK(cudaMemcpyAsync(pc.d_rank, rk, sizeof(int), cudaMemcpyDeviceToDevice, s));
     return PSDPROJ_OK;
 }
 
@@ -1237,7 +1278,29 @@ struct grouped_plan {
     int qmax = 0, m_max = 0, mp_max = 0;
     std::vector<gl_qr> qr;     // stage s: the orthonormalisation after product s - 1 (s = 0: after Y = A Omega)
     gl_core core;
+    // Alg. 3's alpha by grouped power iterations (BF16 form, alpha not given,
+    // not the Ritz variant): which problems, and the launches' tables
+    std::vector<char> galpha;
+    int n_galpha = 0, N = 0;
+    const psd_g_pi *pi1 = nullptr, *pi2 = nullptr;
+    const int2 *bm_pi = nullptr;
+    int nb_pi = 0;
+    const psd_g_alpha *al = nullptr;
+    // grouped images (BF16 forms) and test matrices (Gaussian sketch)
+    bool gpack = false, gpack_lo = false;
+    const psd_g_pack *pk = nullptr, *pk_lo = nullptr;
+    const int2 *bm_pk = nullptr;
+    int nb_pk = 0;
+    const psd_g_gauss *gs = nullptr;
+    const int2 *bm_gs = nullptr;
+    int nb_gs = 0;
 };
+
+// alpha of this problem comes from the grouped power iterations
+bool grouped_alpha(const proj_call &pc)
+{
+    return pc.scaled && !proj_ritz(pc) && !(pc.alpha_in > 0.0) && pc.opts.prec == PSDPROJ_PREC_BF16;
+}
 
 // image bytes of one problem in form prec: (high or only part, low part)
 void slot_image_bytes(int64_t n, int prec, size_t &hi, size_t &lo)
@@ -1441,18 +1504,106 @@ int grouped_tables(psdproj_ctx *ctx, grouped_plan &gp)
         const proj_call &pc = gp.pc[i];
         const psd_workspace &ws = gp.slot[i].ws;
         const int m = pc.m;
-        cg.push_back(gram_entry(ws, ws.Q, ws.Y, pc.n, m, ws.C, nullptr, sms));
-        ce.push_back(psd_g_eig{ws.C, m, ws.V, ws.d, ws.eigscr, ws.ints + IN_EIGFAIL});
-        cf.push_back(psd_g_factor{ws.V, ws.d, m, ws.M, ws.ints + IN_RANK});
+        float2 *cdf = reinterpret_cast<float2 *>(core_gdf(ws, m));
+        cg.push_back(gram_entry(ws, ws.Q, ws.Y, pc.n, m, ws.C, cdf, sms));
+        ce.push_back(psd_g_eig{ws.C, cdf, m, ws.V, ws.d, ws.eigscr, ws.ints + IN_EIGFAIL});
+        cf.push_back(psd_g_factor{ws.V, ws.d, m, ws.M, ws.ints + IN_RANK, pc.rank_written ? pc.d_rank : nullptr});
         float *Wd = pc.dW ? pc.dW : ws.W;
         const int64_t ldwd = pc.dW ? pc.ldw : ws.ld;
-        ct.push_back(tall_entry(ws.Q, ws.ld, pc.n, m, ws.M, nullptr, ws.ints + IN_RANK, Wd, ldwd, nullptr));
+        // the split-BF16 SYRK's operands written with W
+        psd_bf16_side wsd{ws.Xhi, ws.ld, nullptr, 0, nullptr, ws.Xlo};
+        ct.push_back(tall_entry(ws.Q, ws.ld, pc.n, m, ws.M, nullptr, ws.ints + IN_RANK, Wd, ldwd,
+                                pc.w_split ? &wsd : nullptr));
         for (int b = 0; b < psd_eig_ns_blocks(m); ++b) bns.push_back(make_int2(i, b));
-        for (int b = 0; b < m; ++b) bray.push_back(make_int2(i, b));
+        for (int b = 0; b < psd_eig_ray_blocks(m); ++b) bray.push_back(make_int2(i, b));
     }
     const gram_off cgo = put_gram(tb, cg);
     const size_t ceo = tb.put(ce), cfo = tb.put(cf), bnso = tb.put(bns), brayo = tb.put(bray);
     const tall_off cto = put_tall(tb, ct);
+    // the grouped power iterations: run 1 with A, run 2 with A - sigma_1 I
+    // (Alg. 5), then alpha = |sigma_1 - sigma_2| and the shift
+    std::vector<psd_g_pi> p1, p2;
+    std::vector<psd_g_alpha> al;
+    std::vector<int2> bpi;
+    for (int i = 0; i < count; ++i) {
+        if (!gp.galpha[i]) continue;
+        const proj_call &pc = gp.pc[i];
+        const grouped_slot &sl = gp.slot[i];
+        const psd_workspace &ws = sl.ws;
+        double *sc = ws.scal;
+        psd_g_pi e;
+        e.Ab = sl.Ab;
+        e.n = pc.n;
+        e.v0 = ws.pv0;
+        e.v1 = ws.pv1;
+        e.v2 = ws.pv2;
+        e.scal = sc;
+        e.shift_neg = nullptr;
+        e.sigma = sc + SC_SIGMA1;
+        e.seed = pc.seed;
+        // one CTA per 16 tiles: a small product is dominated by each CTA's
+        // fixed costs (its barriers, the norm of x), not by its tiles
+        const int64_t tiles = psd_tile_count(pc.n);
+        e.nb = (int)((tiles + 15) / 16);
+        for (int b = 0; b < e.nb; ++b) bpi.push_back(make_int2((int)p1.size(), b));
+        p1.push_back(e);
+        e.shift_neg = sc + SC_SIGMA1;
+        e.sigma = sc + SC_SIGMA2;
+        p2.push_back(e);
+        al.push_back(psd_g_alpha{sc + SC_SIGMA1, sc + SC_SIGMA2, pc.alpha_in,
+                                 pc.d_alpha_out ? pc.d_alpha_out : sc + SC_ALPHA, sc + SC_SHIFT,
+                                 pc.d_info ? pc.d_info : ws.ints + IN_INFO});
+    }
+    const size_t p1o = tb.put(p1), p2o = tb.put(p2), alo = tb.put(al), bpio = tb.put(bpi);
+    // images: the blocks of each upper block triangle
+    std::vector<psd_g_pack> pk, pkl;
+    std::vector<int2> bpk;
+    if (gp.gpack) {
+        for (int i = 0; i < count; ++i) {
+            const proj_call &pc = gp.pc[i];
+            const int nbr = (int)((pc.n + PSD_TILE_M - 1) / PSD_TILE_M);
+            psd_g_pack e;
+            e.A = pc.dA;
+            e.n = pc.n;
+            e.lda = pc.lda;
+            e.Ab = gp.slot[i].Ab;
+            e.nbc = nbr * PSD_TILE_R;
+            e.vec = (pc.lda % 4) == 0 && (reinterpret_cast<uintptr_t>(pc.dA) & 15) == 0;
+            const int64_t nblocks = (int64_t)e.nbc * nbr * (PSD_TILE_M / 64);
+            for (int64_t b = 0; b < nblocks; ++b) {
+                const int J = (int)(b % e.nbc);
+                const int I = (int)((b / e.nbc) * 64 / PSD_TILE_M);
+                if (J >= PSD_TILE_R * I) bpk.push_back(make_int2((int)pk.size(), (int)b));
+            }
+            pk.push_back(e);
+            e.Ab = gp.slot[i].Ab_lo;
+            pkl.push_back(e);
+        }
+    }
+    const size_t pko = tb.put(pk), pklo = tb.put(pkl), bpko = tb.put(bpk);
+    // test matrices (with the BF16 pass's side outputs where the form fuses them)
+    std::vector<psd_g_gauss> gs;
+    std::vector<int2> bgs;
+    for (int i = 0; i < count; ++i) {
+        const proj_call &pc = gp.pc[i];
+        if (!pc.omega_prepared) continue;
+        const psd_workspace &ws = gp.slot[i].ws;
+        psd_g_gauss e;
+        e.seed = pc.seed;
+        e.n = pc.n;
+        e.m = pc.m;
+        e.mpad = psd_lpad(pc.m);
+        e.rows_pad = ws.ld;
+        e.X = ws.Om;
+        e.ldx = ws.ld;
+        e.side = proj_fuse(pc) ? psd_bf16_side{ws.Xhi, ws.ld, ws.Y, ws.ld, proj_shift(pc, ws)}
+                               : psd_bf16_side{nullptr, 0, nullptr, 0, nullptr};
+        const int64_t vals = e.rows_pad * e.mpad;
+        e.nb = (int)((vals + 2047) / 2048);      // eight values per thread
+        for (int b = 0; b < e.nb; ++b) bgs.push_back(make_int2((int)gs.size(), b));
+        gs.push_back(e);
+    }
+    const size_t gso = tb.put(gs), bgso = tb.put(bgs);
     const size_t bytes = align_up(tb.h.size(), 256);
     if (ctx->g_tabs_bytes < bytes) {
         PSD_TRY(psd_budget_check(ctx, ctx->g_tabs_bytes, bytes));
@@ -1506,6 +1657,34 @@ int grouped_tables(psdproj_ctx *ctx, grouped_plan &gp)
     gp.core.nb_ns = (int)bns.size();
     gp.core.nb_ray = (int)bray.size();
     gp.core.t = tall_at(cto);
+    gp.pi1 = reinterpret_cast<const psd_g_pi *>(d + p1o);
+    gp.pi2 = reinterpret_cast<const psd_g_pi *>(d + p2o);
+    gp.al = reinterpret_cast<const psd_g_alpha *>(d + alo);
+    gp.bm_pi = reinterpret_cast<const int2 *>(d + bpio);
+    gp.nb_pi = (int)bpi.size();
+    gp.pk = reinterpret_cast<const psd_g_pack *>(d + pko);
+    gp.pk_lo = reinterpret_cast<const psd_g_pack *>(d + pklo);
+    gp.bm_pk = reinterpret_cast<const int2 *>(d + bpko);
+    gp.nb_pk = (int)bpk.size();
+    gp.gs = reinterpret_cast<const psd_g_gauss *>(d + gso);
+    gp.bm_gs = reinterpret_cast<const int2 *>(d + bgso);
+    gp.nb_gs = (int)bgs.size();
+    return PSDPROJ_OK;
+}
+
+// alpha of the grouped-alpha problems: the two power iterations (Alg. 4 in
+// Alg. 5) of all of them as grouped launches, then alpha and the shift
+int grouped_alpha_issue(psdproj_ctx *ctx, const grouped_plan &gp, const psdproj_opts &opts)
+{
+    cudaStream_t s = ctx->stream;
+    const long long wl = (long long)opts.spin_limit;
+    PSD_KL(launch_pi_start_grouped(s, gp.pi1, gp.bm_pi, gp.nb_pi, 3u), 1);
+    PSD_KL(launch_power_iteration_grouped(s, gp.pi1, gp.n_galpha, gp.bm_pi, gp.nb_pi, gp.N, ctx->d_status, wl),
+           gp.N + 2);
+    PSD_KL(launch_pi_start_grouped(s, gp.pi2, gp.bm_pi, gp.nb_pi, 4u), 1);
+    PSD_KL(launch_power_iteration_grouped(s, gp.pi2, gp.n_galpha, gp.bm_pi, gp.nb_pi, gp.N, ctx->d_status, wl),
+           gp.N + 2);
+    PSD_KL(launch_alpha_finish_grouped(s, gp.al, gp.n_galpha), 1);
     return PSDPROJ_OK;
 }
 
@@ -1593,7 +1772,7 @@ int grouped_issue(psdproj_ctx *ctx, grouped_plan &gp, const psdproj_opts &opts)
             if (!take(i)) continue;
             psdproj_ctx *lane = ctx->lane[gp.lanes.lane_of[i]];
             slot_binding bind(lane, gp.slot[i]);
-            rc = phase(lane, gp.pc[i]);
+            rc = phase(lane, gp.pc[i], i);
             if (rc != PSDPROJ_OK) break;
         }
         for (int j = 0; j < S; ++j) {
@@ -1603,16 +1782,37 @@ int grouped_issue(psdproj_ctx *ctx, grouped_plan &gp, const psdproj_opts &opts)
         return rc;
     };
     auto all = [](int) { return true; };
-    PSD_TRY(on_lanes(all, [](psdproj_ctx *c, proj_call &pc) { return proj_begin(c, pc); }));
+    // the images (grouped in the BF16 forms), alpha (grouped power
+    // iterations where they apply, else per problem), the test matrices
+    // (grouped for the Gaussian sketch), then the first products
+    if (gp.gpack) {
+        PSD_KL(launch_pack_grouped(ctx->stream, gp.pk, gp.bm_pk, gp.nb_pk, 0), 1);
+        if (gp.gpack_lo) PSD_KL(launch_pack_grouped(ctx->stream, gp.pk_lo, gp.bm_pk, gp.nb_pk, 1), 1);
+    }
+    auto lane_first = [&](int i) {
+        const proj_call &pc = gp.pc[i];
+        return (!gp.gpack && pc.opts.prec != PSDPROJ_PREC_FP32) ||
+               (!gp.galpha[i] && pc.scaled && !proj_ritz(pc));
+    };
+    bool any_first = false;
+    for (int i = 0; i < (int)gp.pc.size(); ++i) any_first = any_first || lane_first(i);
+    if (any_first)
+        PSD_TRY(on_lanes(lane_first, [&](psdproj_ctx *c, proj_call &pc, int i) {
+            if (!gp.gpack) PSD_TRY(proj_pack(c, pc));
+            return gp.galpha[i] ? PSDPROJ_OK : proj_alpha(c, pc);
+        }));
+    if (gp.n_galpha > 0) PSD_TRY(grouped_alpha_issue(ctx, gp, opts));
+    if (gp.nb_gs > 0) PSD_KL(launch_gaussian_grouped(ctx->stream, gp.gs, gp.bm_gs, gp.nb_gs, 0u), 1);
+    PSD_TRY(on_lanes(all, [](psdproj_ctx *c, proj_call &pc, int) { return proj_sketch(c, pc); }));
     PSD_TRY(grouped_qr(ctx, gp, gp.qr[0]));
     for (int t = 0; t < 2 * gp.qmax; ++t) {
         PSD_TRY(on_lanes([&](int i) { return t < 2 * gp.pc[i].q; },
-                         [](psdproj_ctx *c, proj_call &pc) { return proj_power_pass(c, pc); }));
+                         [](psdproj_ctx *c, proj_call &pc, int) { return proj_power_pass(c, pc); }));
         PSD_TRY(grouped_qr(ctx, gp, gp.qr[t + 1]));
     }
-    PSD_TRY(on_lanes(all, [](psdproj_ctx *c, proj_call &pc) { return proj_core_pass(c, pc); }));
+    PSD_TRY(on_lanes(all, [](psdproj_ctx *c, proj_call &pc, int) { return proj_core_pass(c, pc); }));
     PSD_TRY(grouped_core(ctx, gp, opts));
-    return on_lanes(all, [](psdproj_ctx *c, proj_call &pc) { return proj_finish(c, pc); });
+    return on_lanes(all, [](psdproj_ctx *c, proj_call &pc, int) { return proj_finish(c, pc); });
 }
 
 void grouped_graph_free(psdproj_ctx *ctx)
@@ -1773,6 +1973,22 @@ int psdproj_batched_grouped(psdproj_ctx *ctx, int count, const psdproj_problem *
             if (pc.m > gp.m_max) gp.m_max = pc.m;
         }
         gp.mp_max = (int)psd_round_up(gp.m_max, 8);
+        gp.N = opts.N;
+        gp.galpha.assign(count, 0);
+        for (int i = 0; i < count; ++i)
+            if (grouped_alpha(gp.pc[i])) {
+                gp.galpha[i] = 1;
+                ++gp.n_galpha;
+            }
+        gp.gpack = opts.prec == PSDPROJ_PREC_BF16 || opts.prec == PSDPROJ_PREC_BF16X3;
+        gp.gpack_lo = opts.prec == PSDPROJ_PREC_BF16X3;
+        for (int i = 0; i < count; ++i) {
+            proj_call &pc = gp.pc[i];
+            pc.omega_prepared = opts.sketch == PSDPROJ_SKETCH_GAUSS;
+            // the tensor-core SYRK (m <= 128 here) reads the split W
+            pc.w_split = opts.out_mode != PSDPROJ_OUT_FACTOR && opts.syrk_prec == PSDPROJ_PREC_BF16X3;
+            pc.rank_written = pc.d_rank != nullptr;
+        }
         PSD_TRY(grouped_slots(ctx, opts, count, probs, gp.slot));
         PSD_TRY(grouped_tables(ctx, gp));
         // record with the stage timers off (events inside a graph are not read back)
@@ -1826,7 +2042,7 @@ int psdproj_tune_batch(psdproj_ctx *ctx, int count, const psdproj_problem *probs
 {
     if (!ctx || count < 1 || !probs || reps < 1) return PSDPROJ_EINVAL;
     device_guard g(ctx->device);
-    static const int trial[] = {2, 4, 8, 16};
+    static const int trial[] = {2, 4, 8, 16, 32, 64};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PSD_CK(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {

@@ -578,7 +578,8 @@ cholesky_blocked_kernel(const float2 *__restrict__ Gd, int m, float *__restrict_
 
 // many problems in one launch: block b factors entry b
 template <typename T>
-__global__ void __launch_bounds__(NTB, 1)
+// (two blocks per SM: many problems in flight, 64 registers fit both passes)
+__global__ void __launch_bounds__(NTB, 2)
 cholesky_blocked_grouped_kernel(const psd_g_chol *__restrict__ tab, float tau, int *d_status)
 {
     const psd_g_chol a = tab[blockIdx.x];
@@ -741,7 +742,10 @@ tall_small_wide_kernel(const float *__restrict__ Y, int64_t ldy, int64_t n, int 
 // tile is staged K-major with batched, coalesced loads; stores are coalesced
 // over the rows.
 constexpr int RT = PSD_TALL_RT;     // rows per tile
-constexpr int LDB = 132, LDT = 36;  // shared row strides (floats) of B and of the Y tile
+// shared row strides (floats) of B, of the Y tile and of the output tile
+constexpr int LDB = 132, LDT = 36, LDO = 36;
+// shared memory of the product for m rows of B
+constexpr size_t tall_smem(int m) { return sizeof(float) * ((size_t)m * (LDB + LDT) + 128 * (size_t)LDO); }
 
 __device__ __forceinline__ void tall_small_res_body(const float *__restrict__ Y, int64_t ldy, int64_t n, int m,
                                                     const float *__restrict__ B, int c,
@@ -752,11 +756,26 @@ __device__ __forceinline__ void tall_small_res_body(const float *__restrict__ Y,
     extern __shared__ __align__(16) float smt[];
     float *Bs = smt;                              // Bs[k * LDB + col] = B(k, col)
     float *Ys = smt + (size_t)m * LDB;            // Ys[k * LDT + r] = Y(row0 + r, k)
+    float *Os = Ys + (size_t)m * LDT;             // Os[col * LDO + r] = Z(row0 + r, col)
     const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
     const int ncols = d_cols ? min(*d_cols, c) : c;
-    for (int e = tid; e < m * 128; e += 256) {
-        const int col = e / m, k = e - (e / m) * m;
-        Bs[k * LDB + col] = col < ncols ? B[(int64_t)col * m + k] : 0.0f;
+    // B, 8 loads in flight per thread before their stores
+    for (int base = 0; base < m * 128; base += 256 * 8) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = base + tid + 256 * u;
+            const int col = e / m, k = e - (e / m) * m;
+            v[u] = (e < m * 128 && col < ncols) ? B[(int64_t)col * m + k] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = base + tid + 256 * u;
+            if (e < m * 128) {
+                const int col = e / m, k = e - (e / m) * m;
+                Bs[k * LDB + col] = v[u];
+            }
+        }
     }
     const float shift = side.d_shift ? (float)*side.d_shift : 0.0f;
     bool zero[4];
@@ -789,8 +808,10 @@ __device__ __forceinline__ void tall_small_res_body(const float *__restrict__ Y,
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+        // warp w owns columns 16 w .. 16 w + 15; past the used columns B is
+        // zero and so is the product: those warps skip the loop (uniform)
 #pragma unroll 4
-        for (int k = 0; k < m; ++k) {
+        for (int k = 0; k < (16 * (tid >> 5) < ncols ? m : 0); ++k) {
             const float4 y4 = *reinterpret_cast<const float4 *>(Ys + k * LDT + 4 * tx);
             const float4 b4 = *reinterpret_cast<const float4 *>(Bs + k * LDB + 4 * ty);
             const float y[4] = {y4.x, y4.y, y4.z, y4.w};
@@ -800,20 +821,30 @@ __device__ __forceinline__ void tall_small_res_body(const float *__restrict__ Y,
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(y[i], bb[j], acc[i][j]);
         }
+        // the tile through shared memory (one 16-byte store per column and
+        // thread), then stored a column per warp instruction: lane = row
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int gc = 4 * ty + j;
-            if (gc >= c) continue;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int64_t gr = row0 + 4 * tx + i;
-                if (gr >= n) continue;
-                const float z = zero[j] ? 0.0f : acc[i][j];
-                Z[(int64_t)gc * ldz + gr] = z;
-                // side outputs for the BF16 pass that reads Z next
-                if (side.Xh) side.Xh[(int64_t)gc * side.ldh + gr] = __bfloat16_as_ushort(__float2bfloat16_rn(z));
-                if (side.Y) side.Y[(int64_t)gc * side.ldy + gr] = shift * z;
-            }
+            if (gc < c)
+                *reinterpret_cast<float4 *>(Os + gc * LDO + 4 * tx) =
+                    zero[j] ? make_float4(0.0f, 0.0f, 0.0f, 0.0f)
+                            : make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
+        }
+        __syncthreads();
+        for (int e = tid; e < c * RT; e += 256) {
+            const int gc = e / RT, r = e % RT;
+            const int64_t gr = row0 + r;
+            if (gr >= n) continue;
+            const float z = Os[gc * LDO + r];
+            Z[(int64_t)gc * ldz + gr] = z;
+            // side outputs for the BF16 pass that reads Z next (or the
+            // split-BF16 SYRK's operands)
+            const __nv_bfloat16 zh = __float2bfloat16_rn(z);
+            if (side.Xh) side.Xh[(int64_t)gc * side.ldh + gr] = __bfloat16_as_ushort(zh);
+            if (side.Xl)
+                side.Xl[(int64_t)gc * side.ldh + gr] = __bfloat16_as_ushort(__float2bfloat16_rn(z - __bfloat162float(zh)));
+            if (side.Y) side.Y[(int64_t)gc * side.ldy + gr] = shift * z;
         }
     }
 }
@@ -885,10 +916,10 @@ cudaError_t launch_tall_small(cudaStream_t s, const float *Y, int64_t ldy, int64
     const psd_bf16_side sd = side ? *side : psd_bf16_side{nullptr, 0, nullptr, 0, nullptr};
     if (side && c > 128) return cudaErrorNotSupported;
     if (m <= 128 && c <= 128 && n > 0) {
-        const size_t smem = sizeof(float) * (size_t)m * (LDB + LDT);
+        const size_t smem = tall_smem(m);
         // the attribute is process-wide: the largest size (m = 128)
         cudaError_t e = cudaFuncSetAttribute(tall_small_res_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(sizeof(float) * 128 * (LDB + LDT)));
+                                             (int)tall_smem(128));
         if (e != cudaSuccess) return e;
         const int ntiles = (int)((n + RT - 1) / RT);
         const int per_sm = smem <= 227 * 1024 / 3 ? 3 : 2;
@@ -938,9 +969,9 @@ cudaError_t launch_cholesky_grouped(cudaStream_t s, const psd_g_chol *tab, int c
 cudaError_t launch_tall_small_grouped(cudaStream_t s, const psd_g_tall *tab, const int2 *bmap, int nb, int m_max)
 {
     if (nb < 1 || m_max < 1 || m_max > 128) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(float) * (size_t)m_max * (LDB + LDT);
+    const size_t smem = tall_smem(m_max);
     cudaError_t e = cudaFuncSetAttribute(tall_small_res_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float) * 128 * (LDB + LDT)));
+                                         (int)tall_smem(128));
     if (e != cudaSuccess) return e;
     tall_small_res_grouped_kernel<<<(unsigned)nb, 256, smem, s>>>(tab, bmap);
     return cudaGetLastError();

@@ -92,7 +92,7 @@ struct psd_timing {
     int kind[PSD_MAX_TIMED];
 };
 
-constexpr int PSD_MAX_LANES = 16;     // most streams a batch is spread over
+constexpr int PSD_MAX_LANES = 64;     // most streams a batch is spread over
 
 struct psdproj_ctx {
     int device = 0;
@@ -174,6 +174,10 @@ struct psd_bf16_side {
     float *Y;
     int64_t ldy;
     const double *d_shift;
+    // the tall x small product only (may be NULL): also the low parts
+    // bf16(Z - bf16(Z)) at leading dimension ldh, the split-BF16 SYRK's
+    // second operand
+    uint16_t *Xl;
 };
 
 cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, uint32_t stream_id,
@@ -322,20 +326,76 @@ cudaError_t launch_tall_small_grouped(cudaStream_t s, const psd_g_tall *tab, con
 
 struct psd_g_eig {           // launch_eig, m <= 128
     const double *C;
+    const float2 *Cd;        // C as double-float pairs, may be NULL
     int m;
     float *V;
     double *d;
     float *scr;              // 3 (m+2)^2 floats
     int *d_fail;             // the tridiagonal solver's failure flag
 };
-// blocks per problem of the Newton-Schulz kernels and of the Rayleigh quotients
+// blocks per problem of the Newton-Schulz kernels and of the Rayleigh
+// quotients (m <= 128: PSD_RQ eigenpairs per block, C and the eigenvectors
+// in psd_rayleigh_smem(m) bytes of shared memory)
+constexpr int PSD_RQ = 8;
 inline int psd_eig_ns_blocks(int m) { return ((m + 15) / 16) * ((m + 15) / 16); }
-// bmap_ns: block < psd_eig_ns_blocks(m) of its entry; bmap_ray: block < m
+inline int psd_eig_ray_blocks(int m) { return (m + PSD_RQ - 1) / PSD_RQ; }
+inline size_t psd_rayleigh_smem(int m) { return sizeof(double) * (size_t)m * m + sizeof(float) * PSD_RQ * (size_t)m; }
+// bmap_ns: block < psd_eig_ns_blocks(m) of its entry; bmap_ray: block < psd_eig_ray_blocks(m)
 cudaError_t launch_eig_grouped(cudaStream_t s, const psd_g_eig *tab, int count, const int2 *bmap_ns, int nb_ns,
                                const int2 *bmap_ray, int nb_ray, int m_max, int *d_status, int method);
 cudaError_t launch_eig_tridiag_grouped(cudaStream_t s, const psd_g_eig *tab, int count, const int2 *bmap_ns,
                                        int nb_ns, const int2 *bmap_ray, int nb_ray, int m_max,
                                        int *d_status_on_fail);
+
+struct psd_g_pi {            // one power iteration on the BF16 image (launch_power_iteration_bf16)
+    const uint16_t *Ab;
+    int64_t n;
+    float *v0, *v1, *v2;     // 16-byte aligned, n floats each
+    double *scal;            // the iteration's scales (scal[0], scal[1])
+    const double *shift_neg; // may be NULL: as launch_power_iteration_bf16's d_shift_neg
+    double *sigma;           // ||y|| of the last product
+    uint64_t seed;
+    int nb;                  // CTAs per product, 1 <= nb <= psd_tile_count(n); also the start's blocks
+};
+// the start vector (Philox stream stream_id of seed) and scales; bmap: block
+// < nb of its entry
+cudaError_t launch_pi_start_grouped(cudaStream_t s, const psd_g_pi *tab, const int2 *bmap, int nb,
+                                   uint32_t stream_id);
+// N + 1 products, each normalising its input, then the norms
+cudaError_t launch_power_iteration_grouped(cudaStream_t s, const psd_g_pi *tab, int count, const int2 *bmap,
+                                          int nb, int N, int *d_status, long long wait_limit = 0);
+
+struct psd_g_alpha {         // launch_alpha_finish
+    const double *s1, *s2;
+    double alpha_in;
+    double *d_alpha;         // may be NULL
+    double *d_shift;
+    int *d_info;             // may be NULL
+};
+cudaError_t launch_alpha_finish_grouped(cudaStream_t s, const psd_g_alpha *tab, int count);
+
+struct psd_g_pack {          // launch_pack_bf16 (device A)
+    const float *A;
+    int64_t n, lda;
+    uint16_t *Ab;
+    int nbc, vec;            // tile columns; A rows 16-byte aligned
+};
+// part as launch_pack_bf16; bmap: (entry, block) over the blocks of the
+// upper block triangle (tile column J >= PSD_TILE_R * block row)
+cudaError_t launch_pack_grouped(cudaStream_t s, const psd_g_pack *tab, const int2 *bmap, int nb, int part);
+
+struct psd_g_gauss {         // launch_gaussian
+    uint64_t seed;
+    int64_t n;
+    int m, mpad;
+    int64_t rows_pad;
+    float *X;
+    int64_t ldx;
+    psd_bf16_side side;
+    int nb;                  // blocks striding over the entry's rows_pad x mpad values
+};
+cudaError_t launch_gaussian_grouped(cudaStream_t s, const psd_g_gauss *tab, const int2 *bmap, int nb,
+                                    uint32_t stream_id);
 
 struct psd_g_factor {        // launch_factor_prep
     const float *V;
@@ -343,6 +403,7 @@ struct psd_g_factor {        // launch_factor_prep
     int m;
     float *M;
     int *d_rank;
+    int *d_rank_out;         // may be NULL: a second copy of the rank (the caller's)
 };
 cudaError_t launch_factor_prep_grouped(cudaStream_t s, const psd_g_factor *tab, int count);
 
@@ -375,10 +436,12 @@ inline int psd_eig_launches(int method)
 {
     return method == PSDPROJ_EIG_JACOBI ? 1 : (method == PSDPROJ_EIG_AUTO ? 5 : 4);
 }
+// Cdf (may be NULL): C also as double-float pairs (hi, lo), m x m, from
+// which the eigenvalues' FP64 Rayleigh quotients take C v (else from C).
 cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double *d,
-                       float *scratch, int *d_status, int method, int *d_flag);
+                       float *scratch, int *d_status, int method, int *d_flag, const float *Cdf = nullptr);
 cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V, double *d,
-                               float *scratch, int *d_fail, int *d_status_on_fail);
+                               float *scratch, int *d_fail, int *d_status_on_fail, const float *Cdf = nullptr);
 
 cudaError_t launch_factor_prep(cudaStream_t s, const float *V, const double *d, int m,
                                float *M, int *d_rank);
@@ -386,10 +449,12 @@ cudaError_t launch_factor_prep(cudaStream_t s, const float *V, const double *d, 
 cudaError_t launch_syrk_simt(cudaStream_t s, const float *W, int64_t ldw, int64_t n, int m,
                              const int *d_rank, float *P, int64_t ldp, int upper_only);
 
+// prepared != 0: Whi / Wlo already hold W's BF16 high and low parts (the
+// producer of W wrote them), so the split is not launched
 cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t ldw,
                            int64_t n, int m, const int *d_rank, float *P, int64_t ldp,
                            int upper_only, uint16_t *Whi, uint16_t *Wlo, int64_t ldh,
-                           int *d_status, long long wait_limit = 0);
+                           int *d_status, long long wait_limit = 0, int prepared = 0);
 
 // Power iteration (Alg. 4) with optional shift taken from *d_shift_in
 // (negated sigma); writes sigma to *d_sigma.

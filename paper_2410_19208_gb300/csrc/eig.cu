@@ -229,12 +229,12 @@ eig_grouped_kernel(const psd_g_eig *__restrict__ tab, int *d_status, int fallbac
 }  // namespace
 
 cudaError_t launch_eig(cudaStream_t s, const double *C, int m, float *V, double *d,
-                       float *scratch, int *d_status, int method, int *d_flag)
+                       float *scratch, int *d_status, int method, int *d_flag, const float *Cdf)
 {
     const int *only_if = nullptr;
     if (method != PSDPROJ_EIG_JACOBI) {
         cudaError_t e = launch_eig_tridiag(s, C, m, V, d, scratch, d_flag,
-                                           method == PSDPROJ_EIG_TRIDIAG ? d_status : nullptr);
+                                           method == PSDPROJ_EIG_TRIDIAG ? d_status : nullptr, Cdf);
         if (e != cudaSuccess || method == PSDPROJ_EIG_TRIDIAG) return e;
         only_if = d_flag;
     }

@@ -742,8 +742,9 @@ eig_tridiag_kernel(const double *__restrict__ C, int mfull, float *__restrict__ 
     eig_tridiag_body(C, mfull, Vout, dout, gscr, d_fail, d_status_on_fail);
 }
 
-// many problems in one launch: block b solves entry b (m <= SMEM_M)
-__global__ void __launch_bounds__(NT, 1)
+// many problems in one launch: block b solves entry b (m <= SMEM_M), two
+// blocks per SM
+__global__ void __launch_bounds__(NT, 2)
 eig_tridiag_grouped_kernel(const psd_g_eig *__restrict__ tab, int *d_status_on_fail)
 {
     const psd_g_eig a = tab[blockIdx.x];
@@ -865,15 +866,50 @@ ns_apply_grouped_kernel(const psd_g_eig *__restrict__ tab, const int2 *__restric
 // ||C||).  Where the quotient and the FP32 eigenvalue disagree in sign the
 // eigenvalue is indistinguishable from zero at FP32 accuracy: 0.  Exact
 // zeros (the removed zero rows) stay zero.  One block per eigenpair.
-__device__ __forceinline__ void eig_rayleigh_body(const double *__restrict__ C, const float *__restrict__ V, int m,
-                                                  double *__restrict__ d, int i)
+// the quotient's use: the FP64 value where it agrees in sign with the
+// solver's eigenvalue l0 (exact zeros kept), else 0
+__device__ __forceinline__ double rayleigh_update(double num, double den, double l0)
+{
+    const double q = den > 0.0 ? num / den : 0.0;
+    return (l0 == 0.0 || !isfinite(q)) ? l0 : ((q > 0.0) == (l0 > 0.0) ? q : 0.0);
+}
+
+// (C v)_r = sum_c C(r, c) v_c with C as double-float pairs (hi, lo), the form
+// the core's Gram reduction sums in: a compensated dot product in FP32
+// arithmetic (Dot2 of Ogita, Rump and Oishi, "Accurate sum and dot
+// product", 2005: each high product split exactly by FMA, the errors summed
+// beside the sum), as accurate as FP64 here and without this GPU's slow FP64
+// pipe.  Cd(r, c) = cd[c * ldc + r]; v in shared or global memory.
+__device__ __forceinline__ double cv_dot2(const float2 *cd, int ldc, const float *v, int m, int r)
+{
+    float sh = 0.0f, sl = 0.0f;
+    for (int c = 0; c < m; ++c) {
+        const float2 cc = cd[c * ldc + r];
+        const float vc = v[c];
+        const float ph = cc.x * vc;
+        const float pe = fmaf(cc.x, vc, -ph) + cc.y * vc;
+        const float t = sh + ph;                     // two_sum(sh, ph)
+        const float bv = t - sh;
+        sl += ((sh - (t - bv)) + (ph - bv)) + pe;
+        sh = t;
+    }
+    return (double)sh + (double)sl;
+}
+
+// Cd (may be NULL): C also as double-float pairs, from which C v is formed
+// (cv_dot2); else from the FP64 C.  The quotient itself is FP64.
+__device__ __forceinline__ void eig_rayleigh_body(const double *__restrict__ C, const float2 *__restrict__ Cd,
+                                                  const float *__restrict__ V, int m, double *__restrict__ d, int i)
 {
     __shared__ double s_red[2][8];
     const float *v = V + (int64_t)i * m;
     double acc = 0.0, nn = 0.0;              // v^T C v and v^T v
     for (int r = threadIdx.x; r < m; r += 256) {
         double y = 0.0;
-        for (int c = 0; c < m; ++c) y = fma(C[(int64_t)c * m + r], (double)v[c], y);
+        if (Cd)
+            y = cv_dot2(Cd, m, v, m, r);
+        else
+            for (int c = 0; c < m; ++c) y = fma(C[(int64_t)c * m + r], (double)v[c], y);
         const double vr = (double)v[r];
         acc = fma(vr, y, acc);
         nn = fma(vr, vr, nn);
@@ -894,30 +930,95 @@ __device__ __forceinline__ void eig_rayleigh_body(const double *__restrict__ C, 
             num += s_red[0][w];
             den += s_red[1][w];
         }
-        const double q = den > 0.0 ? num / den : 0.0;
-        const double l0 = d[i];
-        d[i] = (l0 == 0.0 || !isfinite(q)) ? l0 : ((q > 0.0) == (l0 > 0.0) ? q : 0.0);
+        d[i] = rayleigh_update(num, den, d[i]);
+    }
+}
+
+// The same quotients for m <= 128, PSD_RQ eigenpairs per block (group g):
+// C (pairs, or FP64) and the group's eigenvectors staged in shared memory
+// once, then two eigenpairs at a time, thread r of each half of the block
+// forming (C v)_r.  Shared memory: psd_rayleigh_smem(m).
+__device__ __forceinline__ void eig_rayleigh_smem_body(const double *__restrict__ C, const float2 *__restrict__ Cd,
+                                                       const float *__restrict__ V, int m, double *__restrict__ d,
+                                                       int g)
+{
+    extern __shared__ __align__(16) unsigned char rq_sm[];
+    float2 *sCd = reinterpret_cast<float2 *>(rq_sm);
+    double *sC = reinterpret_cast<double *>(rq_sm);
+    float *sV = reinterpret_cast<float *>(rq_sm + sizeof(double) * (size_t)m * m);
+    __shared__ double s_red[8][2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = g * PSD_RQ, cnt = min(PSD_RQ, m - i0);
+    if (Cd)
+        for (int e = tid; e < m * m; e += 256) sCd[e] = Cd[e];
+    else
+        for (int e = tid; e < m * m; e += 256) sC[e] = C[e];
+    for (int e = tid; e < cnt * m; e += 256) sV[e] = V[(int64_t)i0 * m + e];
+    __syncthreads();
+    const int half = tid >> 7, r = tid & 127;
+    for (int j0 = 0; j0 < cnt; j0 += 2) {
+        const int j = j0 + half;
+        double acc = 0.0, nn = 0.0;
+        if (j < cnt && r < m) {
+            const float *v = sV + j * m;
+            double y = 0.0;
+            if (Cd)
+                y = cv_dot2(sCd, m, v, m, r);
+            else
+                for (int c = 0; c < m; ++c) y = fma(sC[c * m + r], (double)v[c], y);
+            const double vr = (double)v[r];
+            acc = vr * y;
+            nn = vr * vr;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        }
+        if (lane == 0) {
+            s_red[warp][0] = acc;
+            s_red[warp][1] = nn;
+        }
+        __syncthreads();
+        if (r == 0 && j < cnt) {
+            double num = 0.0, den = 0.0;
+            for (int w = 4 * half; w < 4 * half + 4; ++w) {
+                num += s_red[w][0];
+                den += s_red[w][1];
+            }
+            d[i0 + j] = rayleigh_update(num, den, d[i0 + j]);
+        }
+        __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(256)
-eig_rayleigh_kernel(const double *__restrict__ C, const float *__restrict__ V, int m, double *__restrict__ d)
+eig_rayleigh_kernel(const double *__restrict__ C, const float2 *__restrict__ Cd, const float *__restrict__ V, int m,
+                    double *__restrict__ d)
 {
-    eig_rayleigh_body(C, V, m, d, blockIdx.x);
+    eig_rayleigh_body(C, Cd, V, m, d, blockIdx.x);
 }
 
+__global__ void __launch_bounds__(256)
+eig_rayleigh_smem_kernel(const double *__restrict__ C, const float2 *__restrict__ Cd, const float *__restrict__ V,
+                         int m, double *__restrict__ d)
+{
+    eig_rayleigh_smem_body(C, Cd, V, m, d, blockIdx.x);
+}
+
+// many problems: block b, group bmap[b].y of entry bmap[b].x (m <= 128)
 __global__ void __launch_bounds__(256)
 eig_rayleigh_grouped_kernel(const psd_g_eig *__restrict__ tab, const int2 *__restrict__ bmap)
 {
     const int2 b = bmap[blockIdx.x];
     const psd_g_eig a = tab[b.x];
-    eig_rayleigh_body(a.C, a.V, a.m, a.d, b.y);
+    eig_rayleigh_smem_body(a.C, a.Cd, a.V, a.m, a.d, b.y);
 }
 
 }  // namespace
 
 cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V, double *d,
-                               float *scratch, int *d_fail, int *d_status_on_fail)
+                               float *scratch, int *d_fail, int *d_status_on_fail, const float *Cdf)
 {
     // three m x (m+1) buffers plus 8 slack rows read (never used) by the
     // edge tiles of the Newton-Schulz products
@@ -940,7 +1041,15 @@ cudaError_t launch_eig_tridiag(cudaStream_t s, const double *C, int m, float *V,
     ns_apply_kernel<<<g, 256, 0, s>>>(Vc, S, m, V);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    eig_rayleigh_kernel<<<m, 256, 0, s>>>(C, V, m, d);
+    const float2 *cd = reinterpret_cast<const float2 *>(Cdf);
+    if (m <= SMEM_M) {
+        e = cudaFuncSetAttribute(eig_rayleigh_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)psd_rayleigh_smem(SMEM_M));
+        if (e != cudaSuccess) return e;
+        eig_rayleigh_smem_kernel<<<psd_eig_ray_blocks(m), 256, psd_rayleigh_smem(m), s>>>(C, cd, V, m, d);
+    } else {
+        eig_rayleigh_kernel<<<m, 256, 0, s>>>(C, cd, V, m, d);
+    }
     return cudaGetLastError();
 }
 
@@ -963,6 +1072,9 @@ cudaError_t launch_eig_tridiag_grouped(cudaStream_t s, const psd_g_eig *tab, int
     ns_apply_grouped_kernel<<<(unsigned)nb_ns, 256, 0, s>>>(tab, bmap_ns);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    eig_rayleigh_grouped_kernel<<<(unsigned)nb_ray, 256, 0, s>>>(tab, bmap_ray);
+    e = cudaFuncSetAttribute(eig_rayleigh_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)psd_rayleigh_smem(SMEM_M));
+    if (e != cudaSuccess) return e;
+    eig_rayleigh_grouped_kernel<<<(unsigned)nb_ray, 256, psd_rayleigh_smem(m_max), s>>>(tab, bmap_ray);
     return cudaGetLastError();
 }

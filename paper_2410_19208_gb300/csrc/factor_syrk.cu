@@ -10,7 +10,8 @@ namespace {
 // M = V diag(sqrt(max(d, 0))) and the count of positive eigenvalues; one
 // root per column (FP64 roots are slow on this GPU), then the scaling
 __device__ __forceinline__ void factor_prep_body(const float *__restrict__ V, const double *__restrict__ d, int m,
-                                                 float *__restrict__ M, int *__restrict__ d_rank)
+                                                 float *__restrict__ M, int *__restrict__ d_rank,
+                                                 int *__restrict__ d_rank_out)
 {
     __shared__ int s_r;
     __shared__ float s_g[PSD_MAX_M];
@@ -24,19 +25,20 @@ __device__ __forceinline__ void factor_prep_body(const float *__restrict__ V, co
     __syncthreads();
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) M[e] = V[e] * s_g[e / m];
     if (threadIdx.x == 0 && d_rank) *d_rank = s_r;
+    if (threadIdx.x == 0 && d_rank_out) *d_rank_out = s_r;
 }
 
 __global__ void factor_prep_kernel(const float *__restrict__ V, const double *__restrict__ d,
                                    int m, float *__restrict__ M, int *__restrict__ d_rank)
 {
-    factor_prep_body(V, d, m, M, d_rank);
+    factor_prep_body(V, d, m, M, d_rank, nullptr);
 }
 
 // many problems in one launch: block b prepares entry b
 __global__ void factor_prep_grouped_kernel(const psd_g_factor *__restrict__ tab)
 {
     const psd_g_factor a = tab[blockIdx.x];
-    factor_prep_body(a.V, a.d, a.m, a.M, a.d_rank);
+    factor_prep_body(a.V, a.d, a.m, a.M, a.d_rank, a.d_rank_out);
 }
 
 // P tile (I, J), I <= J, 128 x 128, 256 threads, 8 x 8 micro-tiles.

@@ -53,16 +53,15 @@ __device__ __forceinline__ float box_muller(uint32_t w0, uint32_t w1)
     return sqrtf(m2lnu) * cospif(two_u2);
 }
 
-__global__ void gaussian_kernel(uint64_t seed, uint32_t stream_id, int64_t n, int m,
-                                int mpad, int64_t rows_pad, float *__restrict__ X,
-                                int64_t ldx, psd_bf16_side side)
+__device__ __forceinline__ void gaussian_body(uint64_t seed, uint32_t stream_id, int64_t n, int m, int mpad,
+                                              int64_t rows_pad, float *__restrict__ X, int64_t ldx,
+                                              psd_bf16_side side, int bid, int nb)
 {
     const float shift = side.d_shift ? (float)*side.d_shift : 0.0f;
     const uint32_t k0 = (uint32_t)(seed & 0xffffffffu);
     const uint32_t k1 = (uint32_t)(seed >> 32);
     const int64_t total = rows_pad * (int64_t)mpad;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t idx = bid * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)nb * blockDim.x) {
         const int c = (int)(idx / rows_pad);
         const int64_t i = idx - (int64_t)c * rows_pad;
         float v = 0.0f;
@@ -75,6 +74,41 @@ __global__ void gaussian_kernel(uint64_t seed, uint32_t stream_id, int64_t n, in
         }
         X[(int64_t)c * ldx + i] = v;
     }
+}
+
+__global__ void gaussian_kernel(uint64_t seed, uint32_t stream_id, int64_t n, int m,
+                                int mpad, int64_t rows_pad, float *__restrict__ X,
+                                int64_t ldx, psd_bf16_side side)
+{
+    gaussian_body(seed, stream_id, n, m, mpad, rows_pad, X, ldx, side, blockIdx.x, gridDim.x);
+}
+
+// many test matrices in one launch: block b runs block bmap[b].y of entry
+// bmap[b].x's nb (each entry as its own launch_gaussian)
+__global__ void __launch_bounds__(256)
+gaussian_grouped_kernel(const psd_g_gauss *__restrict__ tab, const int2 *__restrict__ bmap, uint32_t stream_id)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_gauss a = tab[b.x];
+    gaussian_body(a.seed, stream_id, a.n, a.m, a.mpad, a.rows_pad, a.X, a.ldx, a.side, b.y, a.nb);
+}
+
+// The starts of many power iterations (as launch_gaussian of the start
+// vector v0 with n rows and one column, then launch_pi_init): block b runs
+// block bmap[b].y of entry bmap[b].x's nb
+__global__ void __launch_bounds__(256)
+pi_start_grouped_kernel(const psd_g_pi *__restrict__ tab, const int2 *__restrict__ bmap, uint32_t stream_id)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_pi a = tab[b.x];
+    const psd_bf16_side none = {nullptr, 0, nullptr, 0, nullptr};
+    gaussian_body(a.seed, stream_id, a.n, 1, 1, a.n, a.v0, a.n, none, b.y, a.nb);
+    if (b.y == 0 && threadIdx.x == 0) {
+        a.scal[0] = 1.0;
+        a.scal[1] = 0.0;
+    }
+    for (int64_t i = b.y * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)a.nb * blockDim.x)
+        a.v1[i] = 0.0f;
 }
 
 // SRHT test matrix (the real counterpart of the subsampled randomized
@@ -155,6 +189,22 @@ cudaError_t launch_srht(cudaStream_t s, uint64_t seed, int64_t n, int m, int mpa
 
 // Writes rows [0, rows_pad) x columns [0, mpad); entries with i >= n or
 // c >= m are zero (padding of context-owned buffers).
+cudaError_t launch_gaussian_grouped(cudaStream_t s, const psd_g_gauss *tab, const int2 *bmap, int nb,
+                                    uint32_t stream_id)
+{
+    if (nb < 1) return cudaErrorInvalidValue;
+    gaussian_grouped_kernel<<<(unsigned)nb, 256, 0, s>>>(tab, bmap, stream_id);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pi_start_grouped(cudaStream_t s, const psd_g_pi *tab, const int2 *bmap, int nb,
+                                   uint32_t stream_id)
+{
+    if (nb < 1) return cudaErrorInvalidValue;
+    pi_start_grouped_kernel<<<(unsigned)nb, 256, 0, s>>>(tab, bmap, stream_id);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gaussian(cudaStream_t s, uint64_t seed, uint32_t stream_id, int64_t n,
                             int m, int mpad, int64_t rows_pad, float *X, int64_t ldx,
                             const psd_bf16_side *side)

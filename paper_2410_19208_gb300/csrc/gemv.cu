@@ -266,6 +266,9 @@ __device__ __forceinline__ dfl dfl_warp_sum(dfl acc)
     return acc;
 }
 
+// v_i of three vectors (i = 0, 1, 2) without an indexed local array
+__device__ __forceinline__ float *pick3(float *a, float *b, float *c, int i) { return i == 0 ? a : (i == 1 ? b : c); }
+
 __device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
 {
     a[0] = __uint_as_float(u.x << 16); a[1] = __uint_as_float(u.x & 0xFFFF0000u);
@@ -281,10 +284,11 @@ __device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&a)[8])
 // CTA in the same order (so every CTA uses the same scale); else by
 // scal[0].  clear (may be NULL): zeroed, each CTA its slice (the next
 // product's output, this product's input no longer being read).
-__global__ void __launch_bounds__(gt::NTG, gt::CTAS_PER_SM)
-sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64_t tiles,
-                      const float *__restrict__ x, float *__restrict__ y, const double *scal, int self_norm,
-                      float *__restrict__ clear, const double *d_shift_neg, int *d_status, long long wait_limit)
+__device__ __forceinline__ void sym_gemv_tiles_body(const uint16_t *__restrict__ Ab, int64_t n, int nbr,
+                                                    int64_t tiles, const float *__restrict__ x,
+                                                    float *__restrict__ y, const double *scal, int self_norm,
+                                                    float *__restrict__ clear, const double *d_shift_neg,
+                                                    int *d_status, long long wait_limit, int bid, int nb)
 {
     const long long WL = wait_limit > 0 ? wait_limit : gt::WAIT_LIMIT;
     using namespace tc;
@@ -296,8 +300,8 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
     __shared__ dfl s_red[8];
     __shared__ float s_sc;
     const int nbc = nbr * PSD_TILE_R;
-    const int64_t t0 = tiles * blockIdx.x / gridDim.x;
-    const int64_t t1 = tiles * (blockIdx.x + 1) / gridDim.x;
+    const int64_t t0 = tiles * bid / nb;
+    const int64_t t1 = tiles * (bid + 1) / nb;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < gt::STAGES; ++s) {
@@ -336,7 +340,7 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
     } else {
         griddep_wait();
         if (clear) {
-            const int64_t c0 = n * blockIdx.x / gridDim.x, c1 = n * (blockIdx.x + 1) / gridDim.x;
+            const int64_t c0 = n * bid / nb, c1 = n * (bid + 1) / nb;
             for (int64_t i = c0 + threadIdx.x; i < c1; i += gt::NCOMP) clear[i] = 0.0f;
         }
         if (t0 >= t1) return;      // no tile: the producer issues no copy either
@@ -485,6 +489,29 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
 
 }
 
+__global__ void __launch_bounds__(gt::NTG, gt::CTAS_PER_SM)
+sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64_t tiles,
+                      const float *__restrict__ x, float *__restrict__ y, const double *scal, int self_norm,
+                      float *__restrict__ clear, const double *d_shift_neg, int *d_status, long long wait_limit)
+{
+    sym_gemv_tiles_body(Ab, n, nbr, tiles, x, y, scal, self_norm, clear, d_shift_neg, d_status, wait_limit,
+                        blockIdx.x, gridDim.x);
+}
+
+// product `it` of many power iterations in one launch: block b runs CTA
+// bmap[b].y of entry bmap[b].x's product (its own rotation of v0, v1, v2)
+__global__ void __launch_bounds__(gt::NTG, gt::CTAS_PER_SM)
+sym_gemv_tiles_grouped_kernel(const psd_g_pi *__restrict__ tab, const int2 *__restrict__ bmap, int it,
+                              int *d_status, long long wait_limit)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_pi a = tab[b.x];
+    sym_gemv_tiles_body(a.Ab, a.n, (int)((a.n + PSD_TILE_M - 1) / PSD_TILE_M), psd_tile_count(a.n),
+                        pick3(a.v0, a.v1, a.v2, it % 3), pick3(a.v0, a.v1, a.v2, (it + 1) % 3), a.scal,
+                        it > 0 ? 1 : 0, pick3(a.v0, a.v1, a.v2, (it + 2) % 3), a.shift_neg, d_status, wait_limit,
+                        b.y, a.nb);
+}
+
 // ||y|| of a finished product and the clearing of the next product's output
 // (the previous input, no longer read), as a kernel of its own after the
 // product: one block of 1024 threads, each summing y_i^2 over a strided slice
@@ -496,9 +523,8 @@ sym_gemv_tiles_kernel(const uint16_t *__restrict__ Ab, int64_t n, int nbr, int64
 // handful of operations per SM and clock on this GPU, is kept out of the
 // sum; this replaced an eight-block FP64 kernel with an atomic ticket
 // (9.8 us -> a few us per product).
-__global__ void __launch_bounds__(1024)
-pi_norm_kernel(const float *__restrict__ y, float *__restrict__ other, int64_t n, double *scal,
-               double *d_sigma)
+__device__ __forceinline__ void pi_norm_body(const float *__restrict__ y, float *__restrict__ other, int64_t n,
+                                             double *scal, double *d_sigma)
 {
     __shared__ dfl red[32];
     dfl acc = dfl_warp_sum(dfl_sumsq(y, n, threadIdx.x, 1024, other));
@@ -514,6 +540,22 @@ pi_norm_kernel(const float *__restrict__ y, float *__restrict__ other, int64_t n
             if (d_sigma) *d_sigma = nrm;
         }
     }
+}
+
+__global__ void __launch_bounds__(1024)
+pi_norm_kernel(const float *__restrict__ y, float *__restrict__ other, int64_t n, double *scal,
+               double *d_sigma)
+{
+    pi_norm_body(y, other, n, scal, d_sigma);
+}
+
+// the norms closing many power iterations of N + 1 products: block b, entry b
+__global__ void __launch_bounds__(1024)
+pi_norm_grouped_kernel(const psd_g_pi *__restrict__ tab, int N)
+{
+    const psd_g_pi a = tab[blockIdx.x];
+    pi_norm_body(pick3(a.v0, a.v1, a.v2, (N + 1) % 3), pick3(a.v0, a.v1, a.v2, (N + 2) % 3), a.n, a.scal,
+                 a.sigma);
 }
 
 __global__ void pi_init_kernel(double *scal, float *v1, int64_t n)
@@ -542,6 +584,20 @@ __global__ void alpha_finish_kernel(const double *d_s1, const double *d_s2, doub
 // over the eigenvalues d of the core C = Q^T A Q of an unshifted sketch
 // (Ritz values lie in [lambda_min(A), lambda_max(A)], so this estimates
 // |lambda_min| from inside); outputs as alpha_finish_kernel.
+// alpha_finish for many problems: thread i, entry i
+__global__ void alpha_finish_grouped_kernel(const psd_g_alpha *__restrict__ tab, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const psd_g_alpha a = tab[i];
+    double al = a.alpha_in;
+    if (!(a.alpha_in > 0.0)) al = fabs(*a.s1 - *a.s2);
+    const bool ok = isfinite(al) && al > 1e-300;
+    if (a.d_alpha) *a.d_alpha = al;
+    *a.d_shift = ok ? al : 0.0;
+    if (a.d_info) *a.d_info = ok ? 0 : 1;
+}
+
 __global__ void ritz_alpha_kernel(const double *d, int m, double *d_alpha, double *d_shift, int *d_info)
 {
     double lo = 0.0;
@@ -658,6 +714,40 @@ cudaError_t launch_power_iteration_bf16(cudaStream_t s, int sm_count, const uint
     }
     // ||y|| of the last product (sigma)
     pi_norm_kernel<<<1, 1024, 0, s>>>(v[(N + 1) % 3], v[(N + 2) % 3], n, scal, d_sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_power_iteration_grouped(cudaStream_t s, const psd_g_pi *tab, int count, const int2 *bmap,
+                                          int nb, int N, int *d_status, long long wait_limit)
+{
+    if (count < 1 || nb < 1 || N < 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(sym_gemv_tiles_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gt::SMEM);
+    if (e != cudaSuccess) return e;
+    // the products chained by programmatic dependent launch, as in the
+    // single-problem iteration
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nb);
+    cfg.blockDim = dim3(gt::NTG);
+    cfg.dynamicSmemBytes = gt::SMEM;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    for (int it = 0; it <= N; ++it) {
+        e = cudaLaunchKernelEx(&cfg, sym_gemv_tiles_grouped_kernel, tab, bmap, it, d_status, wait_limit);
+        if (e != cudaSuccess) return e;
+    }
+    pi_norm_grouped_kernel<<<(unsigned)count, 1024, 0, s>>>(tab, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_alpha_finish_grouped(cudaStream_t s, const psd_g_alpha *tab, int count)
+{
+    if (count < 1) return cudaErrorInvalidValue;
+    alpha_finish_grouped_kernel<<<(unsigned)((count + 127) / 128), 128, 0, s>>>(tab, count);
     return cudaGetLastError();
 }
 

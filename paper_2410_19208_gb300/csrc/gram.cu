@@ -326,8 +326,9 @@ gram_upper_kernel(const float *__restrict__ X, int64_t ldx, const float *__restr
 }
 
 // many problems in one launch: block b runs block bmap[b].y of entry bmap[b].x
+// (two blocks per SM: each block's rows are few when the problems are small)
 template <bool TWO>
-__global__ void __launch_bounds__(NTU)
+__global__ void __launch_bounds__(NTU, 2)
 gram_upper_grouped_kernel(const psd_g_gram *__restrict__ tab, const int2 *__restrict__ bmap)
 {
     const int2 b = bmap[blockIdx.x];

@@ -492,19 +492,17 @@ __device__ __forceinline__ float lo_part(float v)
 // converts 4 consecutive entries (one float4 of A) in each of 4 rows 16
 // apart, its four loads issued together, into halves of 16-byte chunks of
 // the swizzled rows.  grid.x: 64-column tiles J, grid.y: 64-row chunks;
-// tiles left of the diagonal block exit at once.  part 1 writes the low
+// tiles left of the diagonal block exit at once (pack_block: block bid of
+// the (tile column, 64-row chunk) blocks of one image).  part 1 writes the low
 // parts bf16(a - bf16(a)) instead (the split-BF16 form's second image).
-__global__ void __launch_bounds__(256)
-pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
-                       uint16_t *__restrict__ Ab, int nbc, int vec, int part, int64_t nblocks)
+__device__ __forceinline__ void pack_block(const float *__restrict__ A, int64_t n, int64_t lda,
+                                           uint16_t *__restrict__ Ab, int nbc, int vec, int part, int64_t bid)
 {
     constexpr int RPT = 4;                            // rows per thread
-    // grid-strided over the (tile column J, 64-row chunk) blocks
-    for (int64_t bid = blockIdx.x; bid < nblocks; bid += gridDim.x) {
     const int J = (int)(bid % nbc);
     const int64_t chunk = bid / nbc;
     const int I = (int)((chunk * 64) / BM);
-    if (J < R * I) continue;                          // uniform across the block
+    if (J < R * I) return;                            // uniform across the block
     const int64_t rbase = chunk * 64 + (threadIdx.x >> 4);
     const int64_t c0 = (int64_t)J * BN + 4 * (threadIdx.x & 15);
     float v[RPT][4];
@@ -544,7 +542,23 @@ pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
         const int rt = (int)(r - (int64_t)I * BM);     // row within the tile
         *reinterpret_cast<uint2 *>(tile + rt * 128 + ((k ^ (rt & 7)) << 4) + 8 * (threadIdx.x & 1)) = o;
     }
-    }
+}
+
+__global__ void __launch_bounds__(256)
+pack_upper_bf16_kernel(const float *__restrict__ A, int64_t n, int64_t lda,
+                       uint16_t *__restrict__ Ab, int nbc, int vec, int part, int64_t nblocks)
+{
+    // grid-strided over the (tile column J, 64-row chunk) blocks
+    for (int64_t bid = blockIdx.x; bid < nblocks; bid += gridDim.x) pack_block(A, n, lda, Ab, nbc, vec, part, bid);
+}
+
+// many images in one launch: block b packs block bmap[b].y of entry bmap[b].x
+__global__ void __launch_bounds__(256)
+pack_upper_bf16_grouped_kernel(const psd_g_pack *__restrict__ tab, const int2 *__restrict__ bmap, int part)
+{
+    const int2 b = bmap[blockIdx.x];
+    const psd_g_pack a = tab[b.x];
+    pack_block(a.A, a.n, a.lda, a.Ab, a.nbc, a.vec, part, b.y);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() { return tensor_map_encoder(); }
@@ -568,6 +582,13 @@ cudaError_t launch_pack_bf16(cudaStream_t s, const float *A, int64_t n, int64_t 
     if (host && grid > 152 * 2) grid = 152 * 2;
     if (grid > 0x7fffffff) grid = 0x7fffffff;
     pack_upper_bf16_kernel<<<(unsigned)grid, 256, 0, s>>>(A, n, lda, Ab, nbc, vec, part, nblocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_grouped(cudaStream_t s, const psd_g_pack *tab, const int2 *bmap, int nb, int part)
+{
+    if (nb < 1) return cudaErrorInvalidValue;
+    pack_upper_bf16_grouped_kernel<<<(unsigned)nb, 256, 0, s>>>(tab, bmap, part);
     return cudaGetLastError();
 }
 

@@ -370,7 +370,8 @@ bool encode_w(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *map, void *bas
 
 cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t ldw, int64_t n,
                            int m, const int *d_rank, float *P, int64_t ldp, int upper_only,
-                           uint16_t *Whi, uint16_t *Wlo, int64_t ldh, int *d_status, long long wait_limit)
+                           uint16_t *Whi, uint16_t *Wlo, int64_t ldh, int *d_status, long long wait_limit,
+                           int prepared)
 {
     if (m < 1 || m > KMAX) return cudaErrorNotSupported;
     if ((ldh % 8) != 0 || ldh < n || (reinterpret_cast<uintptr_t>(Whi) & 15) ||
@@ -378,7 +379,7 @@ cudaError_t launch_syrk_tc(cudaStream_t s, int sm_count, const float *W, int64_t
         return cudaErrorNotSupported;
     auto enc = get_encode();
     if (!enc) return cudaErrorNotSupported;
-    {
+    if (!prepared) {
         const int64_t total = n * (int64_t)m;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4096) blocks = 4096;

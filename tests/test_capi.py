@@ -136,6 +136,6 @@ def test_tuning_table_and_its_cache_file(lib, tmp_path, monkeypatch):
     f2.write_text("Test_GPU:7:9:5\t16\nbad line\nTest_GPU:7:3:1\t99\n")
     monkeypatch.setenv("PSDPROJ_TUNE_CACHE", str(f2))
     assert ps.tune_lookup("Test GPU", 7, 1000, 40) == 16
-    assert ps.tune_lookup("Test GPU", 7, 8, 2) is None       # 99 is out of range (1..16): dropped
+    assert ps.tune_lookup("Test GPU", 7, 8, 2) is None       # 99 is out of range (1..64): dropped
     with pytest.raises(RuntimeError):
-        ps.tune_store("Test GPU", 7, 1000, 40, 17)
+        ps.tune_store("Test GPU", 7, 1000, 40, 65)

@@ -1086,7 +1086,7 @@ def test_batched_grouped_rejects_what_it_does_not_group(ctx):
 
 @pytest.mark.gpu
 def test_tune_batch_picks_a_lane_count_and_stores_it(ctx, oracle_lib, tmp_path, monkeypatch):
-    """psdproj_tune_batch times the batch on 2, 4, 8 and 16 lanes, sets the
+    """psdproj_tune_batch times the batch on 2, 4, ..., 64 lanes, sets the
     fastest on the context and stores it under the batch's bucket; a fresh
     context then finds it in the table (and in the cache file), and the last
     run's results are correct (each factor matches a single call's)."""
@@ -1102,7 +1102,7 @@ def test_tune_batch_picks_a_lane_count_and_stores_it(ctx, oracle_lib, tmp_path, 
                           P=torch.empty(n, n, device="cuda"), W=ps.tall_empty(n, k + 8)))
     c = ps.Context(0)
     best, ms = c.tune_batch(probs, opts=opts, reps=2)
-    assert best in (2, 4, 8, 16) and ms > 0.0
+    assert best in (2, 4, 8, 16, 32, 64) and ms > 0.0
     assert c.sync_status() == 0
     prop = torch.cuda.get_device_properties(0)
     med = sorted(sizes)[len(sizes) // 2]
