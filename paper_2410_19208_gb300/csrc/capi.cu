@@ -322,8 +322,13 @@ int sym_pass(psdproj_ctx *ctx, const float *A, int64_t n, int64_t lda, const flo
 
 // CholeskyQR2: Q = orth(Y); Y is read only in the first half.  side (may be
 // NULL): the final product also writes the BF16 pass's side outputs of Q.
+// passes = 1 (an orthonormalisation between two power products): the first
+// half only, Q = Y R^-1 with R from the double-float Cholesky, the same span
+// as Y and orthonormal to about eps32 kappa(Y)^2, i.e. well conditioned
+// wherever the second half could run at all; the products that follow only
+// need a well-conditioned basis of that span.
 int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, float *Q,
-            int64_t ldq, int *d_qrank, const psd_bf16_side *side = nullptr)
+            int64_t ldq, int *d_qrank, const psd_bf16_side *side = nullptr, int passes = 2)
 {
     psd_workspace &ws = ctx->ws;
     cudaStream_t s = ctx->stream;
@@ -332,8 +337,12 @@ int cholqr2(psdproj_ctx *ctx, const float *Y, int64_t ldy, int64_t n, int m, flo
     // m <= 128: the Gram also as double-float pairs, in the (then unused) large-m scratch
     float *gdf = m <= 128 ? reinterpret_cast<float *>(ws.cholscr) : nullptr;
     PSD_KL(launch_gram(s, Y, ldy, Y, ldy, n, m, ws.gpart, ws.G, 1, gdf, ctx->persist_sms), 2);
-    PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, nullptr, tau, ctx->d_status, 1,
-                           ws.cholscr), 1);
+    PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, passes == 1 ? d_qrank : nullptr, tau, ctx->d_status,
+                           1, ws.cholscr), 1);
+    if (passes == 1) {
+        PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, Q, ldq, side, ctx->persist_sms), 1);
+        return PSDPROJ_OK;
+    }
     PSD_KL(launch_tall_small(s, Y, ldy, n, m, ws.Rinv, m, ws.dead, nullptr, ws.T, ws.ld, nullptr, ctx->persist_sms), 1);
     PSD_KL(launch_gram(s, ws.T, ws.ld, ws.T, ws.ld, n, m, ws.gpart, ws.G, 1, gdf, ctx->persist_sms), 2);
     PSD_KL(launch_cholesky(s, ws.G, gdf, m, ws.Rinv, ws.dead, d_qrank, tau, ctx->d_status, 0,
@@ -657,14 +666,17 @@ int run_projection(psdproj_ctx *ctx, const float *dA, int64_t n, int64_t lda, in
     PSD_TRY(proj_begin(ctx, pc));
     // the orthonormalisation after product t writes the side outputs of the
     // next pass: a power product (shifted) while t < 2q, else the core (Y = 0)
+    // (one CholeskyQR pass where a power product follows, both before the core)
     {
         const psd_bf16_side sd = proj_side(ctx, q > 0 ? pc.shift : nullptr);
-        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, pc.fuse ? &sd : nullptr));
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, pc.fuse ? &sd : nullptr,
+                        q > 0 ? 1 : 2));
     }
     for (int t = 0; t < 2 * q; ++t) {
         PSD_TRY(proj_power_pass(ctx, pc));
         const psd_bf16_side sd = proj_side(ctx, t + 1 < 2 * q ? pc.shift : nullptr);
-        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, pc.fuse ? &sd : nullptr));
+        PSD_TRY(cholqr2(ctx, ws.Y, ws.ld, n, m, ws.Q, ws.ld, ws.ints + IN_QRANK, pc.fuse ? &sd : nullptr,
+                        t + 1 < 2 * q ? 1 : 2));
     }
     PSD_TRY(proj_core_pass(ctx, pc));
     PSD_TRY(proj_core_small(ctx, pc));
@@ -1256,7 +1268,7 @@ struct gl_tall {
     int nb = 0;
 };
 struct gl_qr {                 // one CholeskyQR2 over the problems of a stage
-    int count = 0;
+    int count = 0, count2 = 0;    // problems; those that take the second half
     gl_gram g1, g2;
     const psd_g_chol *c1 = nullptr, *c2 = nullptr;
     gl_tall t1, t2;
@@ -1461,7 +1473,7 @@ int grouped_tables(psdproj_ctx *ctx, grouped_plan &gp)
     const int count = (int)gp.pc.size();
     const int sms = ctx->persist_sms;
     table_blob tb;
-    struct qr_off { int count; gram_off g1, g2; size_t c1, c2; tall_off t1, t2; };
+    struct qr_off { int count, count2; gram_off g1, g2; size_t c1, c2; tall_off t1, t2; };
     std::vector<qr_off> qo;
     for (int st = 0; st <= 2 * gp.qmax; ++st) {
         std::vector<psd_g_gram> g1, g2;
@@ -1474,19 +1486,25 @@ int grouped_tables(psdproj_ctx *ctx, grouped_plan &gp)
             const int64_t n = pc.n;
             const int m = pc.m;
             float2 *gdf = reinterpret_cast<float2 *>(ws.cholscr);
-            g1.push_back(gram_entry(ws, ws.Y, ws.Y, n, m, ws.G, gdf, sms));
-            g2.push_back(gram_entry(ws, ws.T, ws.T, n, m, ws.G, gdf, sms));
-            c1.push_back(psd_g_chol{gdf, m, ws.Rinv, ws.dead, nullptr});
-            c2.push_back(psd_g_chol{gdf, m, ws.Rinv, ws.dead, ws.ints + IN_QRANK});
-            t1.push_back(tall_entry(ws.Y, ws.ld, n, m, ws.Rinv, ws.dead, nullptr, ws.T, ws.ld, nullptr));
             // the side outputs of the pass that reads Q next: a power product
-            // (shifted) while product st is one of the problem's, else the core
-            const psd_bf16_side sd{ws.Xhi, ws.ld, ws.Y, ws.ld, st < 2 * pc.q ? proj_shift(pc, ws) : nullptr};
-            t2.push_back(tall_entry(ws.T, ws.ld, n, m, ws.Rinv, ws.dead, nullptr, ws.Q, ws.ld,
-                                    proj_fuse(pc) ? &sd : nullptr));
+            // (shifted) while product st is one of the problem's, else the
+            // core; before a power product the first half alone (cholqr2's
+            // passes = 1) writes Q
+            const bool one = st < 2 * pc.q;
+            const psd_bf16_side sd{ws.Xhi, ws.ld, ws.Y, ws.ld, one ? proj_shift(pc, ws) : nullptr};
+            const psd_bf16_side *sdp = proj_fuse(pc) ? &sd : nullptr;
+            g1.push_back(gram_entry(ws, ws.Y, ws.Y, n, m, ws.G, gdf, sms));
+            c1.push_back(psd_g_chol{gdf, m, ws.Rinv, ws.dead, one ? ws.ints + IN_QRANK : nullptr});
+            t1.push_back(one ? tall_entry(ws.Y, ws.ld, n, m, ws.Rinv, ws.dead, nullptr, ws.Q, ws.ld, sdp)
+                             : tall_entry(ws.Y, ws.ld, n, m, ws.Rinv, ws.dead, nullptr, ws.T, ws.ld, nullptr));
+            if (one) continue;
+            g2.push_back(gram_entry(ws, ws.T, ws.T, n, m, ws.G, gdf, sms));
+            c2.push_back(psd_g_chol{gdf, m, ws.Rinv, ws.dead, ws.ints + IN_QRANK});
+            t2.push_back(tall_entry(ws.T, ws.ld, n, m, ws.Rinv, ws.dead, nullptr, ws.Q, ws.ld, sdp));
         }
         qr_off o;
         o.count = (int)c1.size();
+        o.count2 = (int)c2.size();
         o.g1 = put_gram(tb, g1);
         o.g2 = put_gram(tb, g2);
         o.c1 = tb.put(c1);
@@ -1640,6 +1658,7 @@ int grouped_tables(psdproj_ctx *ctx, grouped_plan &gp)
     for (const qr_off &o : qo) {
         gl_qr q;
         q.count = o.count;
+        q.count2 = o.count2;
         q.g1 = gram_at(o.g1);
         q.g2 = gram_at(o.g2);
         q.c1 = reinterpret_cast<const psd_g_chol *>(d + o.c1);
@@ -1722,8 +1741,9 @@ int grouped_qr(psdproj_ctx *ctx, const grouped_plan &gp, const gl_qr &q)
     PSD_KL(launch_gram_grouped(s, q.g1.tab, 0, q.g1.bm, q.g1.nb, q.g1.bm_red, q.g1.nb_red, gp.mp_max), 2);
     PSD_KL(launch_cholesky_grouped(s, q.c1, q.count, gp.m_max, 1, tau, ctx->d_status), 1);
     PSD_KL(launch_tall_small_grouped(s, q.t1.tab, q.t1.bm, q.t1.nb, gp.m_max), 1);
+    if (q.count2 == 0) return PSDPROJ_OK;
     PSD_KL(launch_gram_grouped(s, q.g2.tab, 0, q.g2.bm, q.g2.nb, q.g2.bm_red, q.g2.nb_red, gp.mp_max), 2);
-    PSD_KL(launch_cholesky_grouped(s, q.c2, q.count, gp.m_max, 0, tau, ctx->d_status), 1);
+    PSD_KL(launch_cholesky_grouped(s, q.c2, q.count2, gp.m_max, 0, tau, ctx->d_status), 1);
     PSD_KL(launch_tall_small_grouped(s, q.t2.tab, q.t2.bm, q.t2.nb, gp.m_max), 1);
     return PSDPROJ_OK;
 }
