@@ -85,7 +85,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true", help="skip the TF32 / split-BF16 comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched workload in the headline run")
     ap.add_argument("--no-serve", action="store_true", help="skip the served workload in the headline run")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batched", "serve", "profile"],
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "batched", "serve", "profile", "batched-profile"],
                     help="batched: 512 matrices, sides log-uniform in [64, 2048], through psdproj_batched; "
                          "serve: Poisson arrivals through psdproj_server; profile: the small case the ncu "
                          "summaries under profiles/ are captured on (three Alg. 2 projections, BF16 form, "
@@ -566,10 +567,39 @@ def run_profile_case(args):
     ctx.close()
 
 
+def run_batched_profile_case(args):
+    """A case for ncu: the 512-matrix batch recipe (BF16 form, split-BF16
+    SYRK) through psdproj_batched_grouped, recorded and run once, then
+    replayed once; no timing."""
+    import torch
+    import paper_2410_19208_gb300 as ps
+    import synth_inputs as si
+    dev = torch.device("cuda", 0)
+    sizes = [int(x) for x in si.log_uniform_sizes(args.batch_count, 64, 2048, seed=7)]
+    probs = []
+    for i, n in enumerate(sizes):
+        Vr, lam = si.make_problem("batch", n, seed_u=1000 + i, seed_lam=5000 + i)
+        probs.append(dict(A=si.form_A_torch(Vr, lam, dev), k=max(2, min(n // 8, 64)), p=8, q=1, seed=SEED + i,
+                          algorithm=1 + (i % 2), P=torch.empty(n, n, device=dev)))
+    opts = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3)
+    ctx = ps.Context(0, torch.cuda.current_stream(dev))
+    ctx.set_batch_streams(32)
+    for _ in range(2):
+        ctx.batched(probs, opts=opts, grouped=True)
+    st = ctx.sync_status()
+    if st != 0:
+        raise SystemExit(f"device status {ps.STATUS.get(st)}")
+    print(json.dumps({"workload": "batched-profile", "problems": len(probs), "status": "ok"}))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.workload == "profile":
         run_profile_case(args)
+        return
+    if args.workload == "batched-profile":
+        run_batched_profile_case(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -175,7 +175,9 @@ uint64_t psdproj_kernel_launches(void);
 
 /* Randomized PSD projection (Alg. 2 with the range finder of Alg. 1):
  *   Omega = randn(n, k+p) (Philox4x32-10 stream 0 of `seed`),
- *   Q = orth(A^(2q+1) Omega), orthonormalised after every product,
+ *   Q = orth(A^(2q+1) Omega), orthonormalised after every product (by
+ *   one CholeskyQR pass where another product follows, which keeps the
+ *   span and a well-conditioned basis; by CholeskyQR2 before the core),
  *   Q^T A Q = V D V^T,  W = Q V sqrt(max(D,0)),  P = W W^T.
  * Requires n >= 1, k >= 1, p >= 0, 1 <= k+p <= min(n, 512), 0 <= q <= 16,
  * lda >= n, ldp >= n (when P is written), ldw >= n (when dW != NULL).
@@ -273,13 +275,15 @@ int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *pr
 /* The same batch with its small steps grouped: every problem gets a
  * workspace and image of its own (one allocation held by the context, sized
  * to the sum of the problems' psdproj_projection_bytes), and the batch runs
- * phase by phase, each phase for all problems before the next: the image,
- * alpha (Alg. 3) and Y = (A + shift I) Omega per problem on the helper
- * streams; then each CholeskyQR2 of Alg. 1's orthonormalisations (Gram,
- * Cholesky, tall x small product, twice) as six grouped launches over the
- * problems whose product it follows; the power and core products per problem
- * on the helper streams; the core Q^T A Q, the l x l eigensolver (Alg. 2)
- * and the factor W = Q V sqrt(max(D, 0)) as grouped launches; P = W W^T per
+ * phase by phase, each phase for all problems before the next: the BF16
+ * images, alpha (Alg. 3: the power iterations of Alg. 5) and Omega as
+ * grouped launches (other forms and options per problem), Y = (A + shift I)
+ * Omega per problem on the helper streams; then each of Alg. 1's
+ * orthonormalisations (Gram, Cholesky, tall x small product; before the core
+ * a second such pass: CholeskyQR2) as grouped launches over the problems
+ * whose product it follows; the power and core products per problem on the
+ * helper streams; the core Q^T A Q, the l x l eigensolver (Alg. 2) and the
+ * factor W = Q V sqrt(max(D, 0)) as grouped launches; P = W W^T per
  * problem.  A grouped launch runs, for each problem, the blocks its own
  * launch would run, so results equal psdproj_batched's up to the order of
  * the passes' floating-point additions.  Recorded once into a CUDA graph and
