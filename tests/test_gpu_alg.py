@@ -1066,6 +1066,62 @@ def test_batched_grouped_matches_single_calls(ctx, oracle_lib, variant):
         c.close()
 
 
+@pytest.mark.parametrize("variant", ["srht_upper", "factor_jacobi_bf16x3", "alpha_given_tridiag_fp32syrk"])
+def test_batched_grouped_options_match_single_calls(ctx, oracle_lib, variant):
+    """The grouped batch's option-dependent phases against single calls with
+    the same options: the SRHT sketch (drawn per problem) with the upper
+    triangle of P only; the factor alone (no SYRK) with the Jacobi
+    eigensolver in the split-BF16 form; a given alpha for the Alg. 3
+    problems (alpha per problem, not by the grouped power iterations) with
+    the tridiagonal solver alone and the FP32 SYRK."""
+    kw = {"srht_upper": dict(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3, sketch=ps.SKETCH_SRHT,
+                             out_mode=ps.OUT_UPPER),
+          "factor_jacobi_bf16x3": dict(prec=ps.PREC_BF16X3, out_mode=ps.OUT_FACTOR, eig=ps.EIG_JACOBI),
+          "alpha_given_tridiag_fp32syrk": dict(prec=ps.PREC_BF16, syrk_prec=ps.PREC_FP32,
+                                               eig=ps.EIG_TRIDIAG)}[variant]
+    opts = ps.make_opts(**kw)
+    specs = [(64, 8, 4, 0, 1), (97, 12, 8, 1, 2), (300, 40, 8, 1, 1), (517, 64, 8, 2, 2), (1024, 64, 8, 1, 2)]
+    probs, mats = _grouped_problems(specs, 1200)
+    for d, A32 in zip(probs, mats):
+        if variant == "factor_jacobi_bf16x3":
+            d["P"] = None
+        if variant.startswith("alpha_given") and d["algorithm"] == 2:
+            d["alpha_in"] = float(np.abs(np.linalg.eigvalsh(A32.astype(np.float64))).max())
+    c = ps.Context(0)
+    c.set_batch_streams(4)
+    try:
+        c.batched(probs, opts=opts, grouped=True)
+        assert c.sync_status() == 0
+        for d in probs:
+            n = d["A"].shape[0]
+            W1 = ps.tall_empty(n, d["k"] + d["p"])
+            P1 = None if d["P"] is None else torch.empty(n, n, device="cuda")
+            rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+            if d["algorithm"] == 1:
+                ctx.alg1(d["A"], d["k"], d["p"], d["q"], d["seed"], W=W1, P=P1, rank=rank, opts=opts)
+            else:
+                ctx.alg2(d["A"], d["k"], d["p"], d["q"], d["seed"], alpha_in=d.get("alpha_in", 0.0), W=W1, P=P1,
+                         rank=rank, opts=opts)
+            assert ctx.sync_status() == 0
+            ref = W1.cpu().numpy().astype(np.float64)
+            got = d["W"].cpu().numpy().astype(np.float64)
+            rel = np.sqrt(max(oracle_lib.factor_dist2(got, ref), 0.0) / oracle_lib.factor_norm2(ref))
+            assert rel <= 2e-3, (variant, n, rel)
+            assert int(d["rank"].item()) == int(rank.item())
+            if d["P"] is not None:
+                Pg = d["P"].cpu().numpy().astype(np.float64)
+                WW = got @ got.T
+                iu = np.triu_indices(n)
+                tol = 3e-5 * (np.abs(got) @ np.abs(got).T).max() + 1e-7
+                assert np.abs(Pg[iu] - WW[iu]).max() <= tol
+            if d["algorithm"] == 2:
+                assert int(d["info"].item()) == 0
+                if "alpha_in" in d:
+                    assert d["alpha_out"].item() == d["alpha_in"]
+    finally:
+        c.close()
+
+
 def test_batched_grouped_rejects_what_it_does_not_group(ctx):
     """Widths above 128 and the deterministic form: ENOTSUP before anything
     runs; bad problems: EINVAL, as psdproj_batched."""
