@@ -290,7 +290,12 @@ int psdproj_batched_graph(psdproj_ctx *ctx, int count, const psdproj_problem *pr
  * replayed like psdproj_batched_graph (same rules for the table, settings
  * and buffers).  Requires k + p <= 128 in every problem (else
  * PSDPROJ_ENOTSUP) and opts.deterministic = 0 (else PSDPROJ_ENOTSUP).  The
- * first call of a table synchronises the context's stream. */
+ * first call of a table synchronises the context's stream.  A batch of 32
+ * problems or more is recorded as two halves (alternating in decreasing
+ * cost), each with half of the helper streams and its own chain of grouped
+ * launches on a stream of the context's, so that one half's grouped steps
+ * overlap the other half's per-problem products; the environment variable
+ * PSDPROJ_GROUPED_SPLIT=1, read when a batch is recorded, keeps it whole. */
 int psdproj_batched_grouped(psdproj_ctx *ctx, int count, const psdproj_problem *probs,
                             const psdproj_opts *opts);
 

@@ -824,8 +824,12 @@ int psdproj_destroy(psdproj_ctx *ctx)
     if (ctx->det_part) cudaFree(ctx->det_part);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->g_exec) cudaGraphExecDestroy(ctx->g_exec);
-    if (ctx->g_slots) cudaFree(ctx->g_slots);
-    if (ctx->g_tabs) cudaFree(ctx->g_tabs);
+    for (int w = 0; w < 2; ++w) {
+        if (ctx->g_slots[w]) cudaFree(ctx->g_slots[w]);
+        if (ctx->g_tabs[w]) cudaFree(ctx->g_tabs[w]);
+        if (ctx->g_ev[w]) cudaEventDestroy(ctx->g_ev[w]);
+    }
+    if (ctx->g_stream2) cudaStreamDestroy(ctx->g_stream2);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
     if (ctx->Ab) cudaFree(ctx->Ab);
     if (ctx->Ab_lo) cudaFree(ctx->Ab_lo);
@@ -1010,7 +1014,8 @@ size_t psdproj_workspace_bytes(const psdproj_ctx *ctx)
 {
     if (!ctx) return 0;
     size_t b = ctx->ws.bytes + ctx->Ab_bytes + ctx->Ab_lo_bytes + ctx->dA_stage_bytes + ctx->dP_stage_bytes +
-               ctx->dW_stage_bytes + ctx->det_part_bytes + ctx->g_slots_bytes + ctx->g_tabs_bytes;
+               ctx->dW_stage_bytes + ctx->det_part_bytes + ctx->g_slots_bytes[0] + ctx->g_slots_bytes[1] +
+               ctx->g_tabs_bytes[0] + ctx->g_tabs_bytes[1];
     for (int i = 0; i < PSD_MAX_LANES; ++i)
         if (ctx->lane[i]) b += psdproj_workspace_bytes(ctx->lane[i]);
     return b;
@@ -1284,7 +1289,8 @@ struct gl_core {               // core, eigensolver, factor
 };
 
 struct grouped_plan {
-    batch_plan lanes;
+    batch_plan lanes;          // lane_of: relative to lane0
+    int lane0 = 0;             // the plan's first lane (ctx->lane[lane0 + j])
     std::vector<grouped_slot> slot;
     std::vector<proj_call> pc;
     int qmax = 0, m_max = 0, mp_max = 0;
@@ -1325,10 +1331,10 @@ void slot_image_bytes(int64_t n, int prec, size_t &hi, size_t &lo)
 
 size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
 
-// Per-problem workspaces and images, carved from ctx->g_slots (grown when
+// Per-problem workspaces and images, carved from ctx->g_slots[w] (grown when
 // too small; zeroed whenever the plan is made, as a workspace is when
 // allocated)
-int grouped_slots(psdproj_ctx *ctx, const psdproj_opts &opts, int count, const psdproj_problem *probs,
+int grouped_slots(psdproj_ctx *ctx, int w, const psdproj_opts &opts, int count, const psdproj_problem *probs,
                   std::vector<grouped_slot> &slot)
 {
     slot.assign(count, grouped_slot());
@@ -1343,18 +1349,18 @@ int grouped_slots(psdproj_ctx *ctx, const psdproj_opts &opts, int count, const p
         total += align_up(carve_workspace(lay, nullptr, probs[i].n, lp), 1024) + align_up(hi, 1024) +
                  align_up(lo, 1024);
     }
-    if (ctx->g_slots_bytes < total) {
-        PSD_TRY(psd_budget_check(ctx, ctx->g_slots_bytes, total));
-        if (ctx->g_slots) {
+    if (ctx->g_slots_bytes[w] < total) {
+        PSD_TRY(psd_budget_check(ctx, ctx->g_slots_bytes[w], total));
+        if (ctx->g_slots[w]) {
             cudaStreamSynchronize(ctx->stream);
-            cudaFree(ctx->g_slots);
-            ctx->g_slots = nullptr;
-            ctx->g_slots_bytes = 0;
+            cudaFree(ctx->g_slots[w]);
+            ctx->g_slots[w] = nullptr;
+            ctx->g_slots_bytes[w] = 0;
         }
-        PSD_CK(cudaMalloc(&ctx->g_slots, total));
-        ctx->g_slots_bytes = total;
+        PSD_CK(cudaMalloc(&ctx->g_slots[w], total));
+        ctx->g_slots_bytes[w] = total;
     }
-    char *base = static_cast<char *>(ctx->g_slots);
+    char *base = static_cast<char *>(ctx->g_slots[w]);
     for (int i = 0; i < count; ++i) {
         grouped_slot &sl = slot[i];
         const int64_t n = probs[i].n;
@@ -1378,7 +1384,7 @@ int grouped_slots(psdproj_ctx *ctx, const psdproj_opts &opts, int count, const p
             sl.Ab_lo_bytes = lo;
         }
     }
-    PSD_CK(cudaMemsetAsync(ctx->g_slots, 0, total, ctx->stream));
+    PSD_CK(cudaMemsetAsync(ctx->g_slots[w], 0, total, ctx->stream));
     return PSDPROJ_OK;
 }
 
@@ -1467,8 +1473,8 @@ psd_g_tall tall_entry(const float *Y, int64_t ldy, int64_t n, int m, const float
     return t;
 }
 
-// The tables of every grouped launch of the batch, uploaded to ctx->g_tabs
-int grouped_tables(psdproj_ctx *ctx, grouped_plan &gp)
+// The tables of every grouped launch of the batch, uploaded to ctx->g_tabs[w]
+int grouped_tables(psdproj_ctx *ctx, int w, grouped_plan &gp)
 {
     const int count = (int)gp.pc.size();
     const int sms = ctx->persist_sms;
@@ -1623,21 +1629,21 @@ int grouped_tables(psdproj_ctx *ctx, grouped_plan &gp)
     }
     const size_t gso = tb.put(gs), bgso = tb.put(bgs);
     const size_t bytes = align_up(tb.h.size(), 256);
-    if (ctx->g_tabs_bytes < bytes) {
-        PSD_TRY(psd_budget_check(ctx, ctx->g_tabs_bytes, bytes));
-        if (ctx->g_tabs) {
+    if (ctx->g_tabs_bytes[w] < bytes) {
+        PSD_TRY(psd_budget_check(ctx, ctx->g_tabs_bytes[w], bytes));
+        if (ctx->g_tabs[w]) {
             cudaStreamSynchronize(ctx->stream);
-            cudaFree(ctx->g_tabs);
-            ctx->g_tabs = nullptr;
-            ctx->g_tabs_bytes = 0;
+            cudaFree(ctx->g_tabs[w]);
+            ctx->g_tabs[w] = nullptr;
+            ctx->g_tabs_bytes[w] = 0;
         }
-        PSD_CK(cudaMalloc(&ctx->g_tabs, bytes));
-        ctx->g_tabs_bytes = bytes;
+        PSD_CK(cudaMalloc(&ctx->g_tabs[w], bytes));
+        ctx->g_tabs_bytes[w] = bytes;
     }
     // the previous plan's launches may still read the tables: upload in order
     PSD_CK(cudaStreamSynchronize(ctx->stream));
-    PSD_CK(cudaMemcpy(ctx->g_tabs, tb.h.data(), tb.h.size(), cudaMemcpyHostToDevice));
-    const char *d = static_cast<const char *>(ctx->g_tabs);
+    PSD_CK(cudaMemcpy(ctx->g_tabs[w], tb.h.data(), tb.h.size(), cudaMemcpyHostToDevice));
+    const char *d = static_cast<const char *>(ctx->g_tabs[w]);
     auto gram_at = [&](const gram_off &o) {
         gl_gram g;
         g.tab = reinterpret_cast<const psd_g_gram *>(d + o.tab);
@@ -1765,39 +1771,40 @@ int grouped_core(psdproj_ctx *ctx, const grouped_plan &gp, const psdproj_opts &o
 int grouped_issue(psdproj_ctx *ctx, grouped_plan &gp, const psdproj_opts &opts)
 {
     const int S = gp.lanes.S;
+    psdproj_ctx **ln = ctx->lane + gp.lane0;
     // the lanes run with this call's settings
     struct lane_settings {
-        psdproj_ctx *ctx;
+        psdproj_ctx **ln;
         int S;
         ~lane_settings()
         {
             for (int j = 0; j < S; ++j) {
-                ctx->lane[j]->wait_limit = 0;
-                ctx->lane[j]->det = false;
+                ln[j]->wait_limit = 0;
+                ln[j]->det = false;
             }
         }
-    } settings_scope{ctx, S};
+    } settings_scope{ln, S};
     for (int j = 0; j < S; ++j) {
-        ctx->lane[j]->wait_limit = (long long)opts.spin_limit;
-        ctx->lane[j]->det = false;
+        ln[j]->wait_limit = (long long)opts.spin_limit;
+        ln[j]->det = false;
     }
     // one phase of every problem with `take(i)` on the lanes, forked from and
     // joined back to the context's stream (also after an error)
     auto on_lanes = [&](auto take, auto phase) -> int {
         cudaEvent_t fork = ctx->lane_ev[PSD_MAX_LANES];
         PSD_CK(cudaEventRecord(fork, ctx->stream));
-        for (int j = 0; j < S; ++j) PSD_CK(cudaStreamWaitEvent(ctx->lane[j]->stream, fork, 0));
+        for (int j = 0; j < S; ++j) PSD_CK(cudaStreamWaitEvent(ln[j]->stream, fork, 0));
         int rc = PSDPROJ_OK;
         for (int i : gp.lanes.order) {
             if (!take(i)) continue;
-            psdproj_ctx *lane = ctx->lane[gp.lanes.lane_of[i]];
+            psdproj_ctx *lane = ln[gp.lanes.lane_of[i]];
             slot_binding bind(lane, gp.slot[i]);
             rc = phase(lane, gp.pc[i], i);
             if (rc != PSDPROJ_OK) break;
         }
         for (int j = 0; j < S; ++j) {
-            cudaEventRecord(ctx->lane_ev[j], ctx->lane[j]->stream);
-            cudaStreamWaitEvent(ctx->stream, ctx->lane_ev[j], 0);
+            cudaEventRecord(ctx->lane_ev[gp.lane0 + j], ln[j]->stream);
+            cudaStreamWaitEvent(ctx->stream, ctx->lane_ev[gp.lane0 + j], 0);
         }
         return rc;
     };
@@ -1833,6 +1840,61 @@ int grouped_issue(psdproj_ctx *ctx, grouped_plan &gp, const psdproj_opts &opts)
     PSD_TRY(on_lanes(all, [](psdproj_ctx *c, proj_call &pc, int) { return proj_core_pass(c, pc); }));
     PSD_TRY(grouped_core(ctx, gp, opts));
     return on_lanes(all, [](psdproj_ctx *c, proj_call &pc, int) { return proj_finish(c, pc); });
+}
+
+// The plan of (part of) a grouped batch: its problems, lanes lane0 ..
+// lane0 + lanes - 1, slots and tables in ctx->g_slots[w] / g_tabs[w]
+int grouped_make(psdproj_ctx *ctx, const psdproj_opts &opts, int count, const psdproj_problem *probs, int lanes,
+                 int lane0, int w, grouped_plan &gp)
+{
+    gp.lanes = batch_make_plan(ctx, opts, count, probs, lanes);
+    if (gp.lanes.S < 1) gp.lanes.S = 1;
+    gp.lane0 = lane0;
+    for (int j = 0; j < gp.lanes.S; ++j) PSD_TRY(ensure_lane(ctx, lane0 + j));
+    gp.pc.resize(count);
+    for (int i = 0; i < count; ++i) {
+        const psdproj_problem &pb = probs[i];
+        proj_call &pc = gp.pc[i];
+        pc.dA = pb.dA;
+        pc.n = pb.n;
+        pc.lda = pb.lda;
+        pc.k = pb.k;
+        pc.p = pb.p;
+        pc.q = pb.q;
+        pc.m = pb.k + pb.p;
+        pc.seed = pb.seed;
+        pc.scaled = pb.algorithm == 2;
+        pc.alpha_in = pb.alpha_in;
+        pc.d_alpha_out = pb.d_alpha_out;
+        pc.d_info = pb.d_info;
+        pc.dP = pb.dP;
+        pc.ldp = pb.ldp;
+        pc.dW = pb.dW;
+        pc.ldw = pb.ldw;
+        pc.d_rank = pb.d_rank;
+        pc.opts = opts;
+        if (pb.q > gp.qmax) gp.qmax = pb.q;
+        if (pc.m > gp.m_max) gp.m_max = pc.m;
+    }
+    gp.mp_max = (int)psd_round_up(gp.m_max, 8);
+    gp.N = opts.N;
+    gp.galpha.assign(count, 0);
+    for (int i = 0; i < count; ++i)
+        if (grouped_alpha(gp.pc[i])) {
+            gp.galpha[i] = 1;
+            ++gp.n_galpha;
+        }
+    gp.gpack = opts.prec == PSDPROJ_PREC_BF16 || opts.prec == PSDPROJ_PREC_BF16X3;
+    gp.gpack_lo = opts.prec == PSDPROJ_PREC_BF16X3;
+    for (int i = 0; i < count; ++i) {
+        proj_call &pc = gp.pc[i];
+        pc.omega_prepared = opts.sketch == PSDPROJ_SKETCH_GAUSS;
+        // the tensor-core SYRK (m <= 128 here) reads the split W
+        pc.w_split = opts.out_mode != PSDPROJ_OUT_FACTOR && opts.syrk_prec == PSDPROJ_PREC_BF16X3;
+        pc.rank_written = pc.d_rank != nullptr;
+    }
+    PSD_TRY(grouped_slots(ctx, w, opts, count, probs, gp.slot));
+    return grouped_tables(ctx, w, gp);
 }
 
 void grouped_graph_free(psdproj_ctx *ctx)
@@ -1963,54 +2025,28 @@ int psdproj_batched_grouped(psdproj_ctx *ctx, int count, const psdproj_problem *
                       ctx->g_persist == ctx->persist_sms;
     if (!same) {
         grouped_graph_free(ctx);
-        grouped_plan gp;
-        gp.lanes = batch_make_plan(ctx, opts, count, probs, lanes);
-        if (gp.lanes.S < 1) gp.lanes.S = 1;
-        for (int j = 0; j < gp.lanes.S; ++j) PSD_TRY(ensure_lane(ctx, j));
-        gp.pc.resize(count);
-        for (int i = 0; i < count; ++i) {
-            const psdproj_problem &pb = probs[i];
-            proj_call &pc = gp.pc[i];
-            pc.dA = pb.dA;
-            pc.n = pb.n;
-            pc.lda = pb.lda;
-            pc.k = pb.k;
-            pc.p = pb.p;
-            pc.q = pb.q;
-            pc.m = pb.k + pb.p;
-            pc.seed = pb.seed;
-            pc.scaled = pb.algorithm == 2;
-            pc.alpha_in = pb.alpha_in;
-            pc.d_alpha_out = pb.d_alpha_out;
-            pc.d_info = pb.d_info;
-            pc.dP = pb.dP;
-            pc.ldp = pb.ldp;
-            pc.dW = pb.dW;
-            pc.ldw = pb.ldw;
-            pc.d_rank = pb.d_rank;
-            pc.opts = opts;
-            if (pb.q > gp.qmax) gp.qmax = pb.q;
-            if (pc.m > gp.m_max) gp.m_max = pc.m;
+        // a batch of 32 problems or more runs as two halves, each with half
+        // of the lanes and its own chain of grouped launches on a stream of
+        // its own (two branches of the graph): the latency-bound grouped
+        // steps of one half overlap the per-problem products of the other
+        const char *env = getenv("PSDPROJ_GROUPED_SPLIT");
+        const int G = (env && atoi(env) == 1) || count < 32 || lanes < 2 ? 1 : 2;
+        std::vector<psdproj_problem> half[2];
+        {
+            // alternate in decreasing cost, so that the halves weigh alike
+            const batch_plan byc = batch_make_plan(ctx, opts, count, probs, 1);
+            int r = 0;
+            for (int i : byc.order) half[r++ % G].push_back(probs[i]);
         }
-        gp.mp_max = (int)psd_round_up(gp.m_max, 8);
-        gp.N = opts.N;
-        gp.galpha.assign(count, 0);
-        for (int i = 0; i < count; ++i)
-            if (grouped_alpha(gp.pc[i])) {
-                gp.galpha[i] = 1;
-                ++gp.n_galpha;
-            }
-        gp.gpack = opts.prec == PSDPROJ_PREC_BF16 || opts.prec == PSDPROJ_PREC_BF16X3;
-        gp.gpack_lo = opts.prec == PSDPROJ_PREC_BF16X3;
-        for (int i = 0; i < count; ++i) {
-            proj_call &pc = gp.pc[i];
-            pc.omega_prepared = opts.sketch == PSDPROJ_SKETCH_GAUSS;
-            // the tensor-core SYRK (m <= 128 here) reads the split W
-            pc.w_split = opts.out_mode != PSDPROJ_OUT_FACTOR && opts.syrk_prec == PSDPROJ_PREC_BF16X3;
-            pc.rank_written = pc.d_rank != nullptr;
+        std::vector<grouped_plan> gps(G);
+        for (int w = 0; w < G; ++w)
+            PSD_TRY(grouped_make(ctx, opts, (int)half[w].size(), half[w].data(), lanes / G, w * (lanes / G), w,
+                                 gps[w]));
+        if (G == 2) {
+            if (!ctx->g_stream2) PSD_CK(cudaStreamCreateWithFlags(&ctx->g_stream2, cudaStreamNonBlocking));
+            for (int w = 0; w < 2; ++w)
+                if (!ctx->g_ev[w]) PSD_CK(cudaEventCreateWithFlags(&ctx->g_ev[w], cudaEventDisableTiming));
         }
-        PSD_TRY(grouped_slots(ctx, opts, count, probs, gp.slot));
-        PSD_TRY(grouped_tables(ctx, gp));
         // record with the stage timers off (events inside a graph are not read back)
         int timing_was = ctx->timing.on;
         ctx->timing.on = 0;
@@ -2028,7 +2064,23 @@ int psdproj_batched_grouped(psdproj_ctx *ctx, int count, const psdproj_problem *
         const uint64_t l0 = g_launches.load();
         PSD_CK(cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeRelaxed));
         ctx->stream = ctx->capture_stream;
-        const int rc = grouped_issue(ctx, gp, opts);
+        int rc = PSDPROJ_OK;
+        if (G == 1) {
+            rc = grouped_issue(ctx, gps[0], opts);
+        } else {
+            cudaStream_t s0 = ctx->stream;
+            cudaError_t ef = cudaEventRecord(ctx->g_ev[0], s0);
+            if (ef == cudaSuccess) ef = cudaStreamWaitEvent(ctx->g_stream2, ctx->g_ev[0], 0);
+            rc = ef != cudaSuccess ? cuda_status(ef, __LINE__) : grouped_issue(ctx, gps[0], opts);
+            if (rc == PSDPROJ_OK) {
+                ctx->stream = ctx->g_stream2;
+                rc = grouped_issue(ctx, gps[1], opts);
+                ctx->stream = s0;
+            }
+            // joined back also after an error, so that the capture ends
+            cudaEventRecord(ctx->g_ev[1], ctx->g_stream2);
+            cudaStreamWaitEvent(s0, ctx->g_ev[1], 0);
+        }
         ctx->stream = user;
         cudaGraph_t graph = nullptr;
         const cudaError_t ec = cudaStreamEndCapture(ctx->capture_stream, &graph);

@@ -141,8 +141,13 @@ struct psdproj_ctx {
     // psdproj_batched_grouped: a workspace and image(s) per problem (g_slots)
     // and the grouped launches' tables (g_tabs); the recorded batch and what
     // it was recorded for
-    void *g_slots = nullptr;  size_t g_slots_bytes = 0;
-    void *g_tabs = nullptr;   size_t g_tabs_bytes = 0;
+    // (the batch in up to two halves, each with its own slots and tables;
+    // the second half's grouped launches on g_stream2, forked from and
+    // joined back to the context's stream by g_ev)
+    void *g_slots[2] = {};    size_t g_slots_bytes[2] = {};
+    void *g_tabs[2] = {};     size_t g_tabs_bytes[2] = {};
+    cudaStream_t g_stream2 = nullptr;
+    cudaEvent_t g_ev[2] = {};
     cudaGraphExec_t g_exec = nullptr;
     std::vector<psdproj_problem> g_probs;
     psdproj_opts g_opts = {};

@@ -1106,7 +1106,12 @@ def test_batched_grouped_options_match_single_calls(ctx, oracle_lib, variant):
             ref = W1.cpu().numpy().astype(np.float64)
             got = d["W"].cpu().numpy().astype(np.float64)
             rel = np.sqrt(max(oracle_lib.factor_dist2(got, ref), 0.0) / oracle_lib.factor_norm2(ref))
-            assert rel <= 2e-3, (variant, n, rel)
+            # two runs of the BF16 forms differ in the order of the passes'
+            # FP32 additions, which the BF16 rounding of X can lift to 2^-8
+            # of an entry; with q = 2 and the SRHT's +-1 test matrix that
+            # spread reached 2.5e-3 between runs; a wrong phase (sketch,
+            # shift, a stale Omega) gives O(1)
+            assert rel <= 5e-3, (variant, n, rel)
             assert int(d["rank"].item()) == int(rank.item())
             if d["P"] is not None:
                 Pg = d["P"].cpu().numpy().astype(np.float64)
@@ -1118,6 +1123,45 @@ def test_batched_grouped_options_match_single_calls(ctx, oracle_lib, variant):
                 assert int(d["info"].item()) == 0
                 if "alpha_in" in d:
                     assert d["alpha_out"].item() == d["alpha_in"]
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("split", ["1", "2"])
+def test_batched_grouped_in_two_halves_matches_single_calls(ctx, oracle_lib, monkeypatch, split):
+    """A batch of 40 problems (sides 64..700, both algorithms, q = 0..2): from
+    32 problems on the grouped batch runs as two halves pipelined on two
+    streams (PSDPROJ_GROUPED_SPLIT=1 keeps it whole); either way each factor
+    matches a single call's within the BF16 form's spread, and the recorded
+    batch replays."""
+    monkeypatch.setenv("PSDPROJ_GROUPED_SPLIT", split)
+    sizes = [int(x) for x in si.log_uniform_sizes(40, 64, 700, seed=23)]
+    specs = [(n, max(2, min(n // 8, 48)), 8, i % 3, 1 + (i % 2)) for i, n in enumerate(sizes)]
+    probs, _ = _grouped_problems(specs, 1500)
+    opts = ps.make_opts(prec=ps.PREC_BF16, syrk_prec=ps.PREC_BF16X3)
+    c = ps.Context(0)
+    c.set_batch_streams(8)
+    try:
+        for _ in range(2):
+            for d in probs:
+                d["W"].fill_(float("nan"))
+            c.batched(probs, opts=opts, grouped=True)
+            assert c.sync_status() == 0
+        for d in probs:
+            n = d["A"].shape[0]
+            W1 = ps.tall_empty(n, d["k"] + d["p"])
+            rank = torch.zeros(1, dtype=torch.int32, device="cuda")
+            fn = ctx.alg1 if d["algorithm"] == 1 else ctx.alg2
+            fn(d["A"], d["k"], d["p"], d["q"], d["seed"], W=W1, P=torch.empty(n, n, device="cuda"), rank=rank,
+               opts=opts)
+            assert ctx.sync_status() == 0
+            ref = W1.cpu().numpy().astype(np.float64)
+            got = d["W"].cpu().numpy().astype(np.float64)
+            rel = np.sqrt(max(oracle_lib.factor_dist2(got, ref), 0.0) / oracle_lib.factor_norm2(ref))
+            assert rel <= 2e-3, (n, rel)
+            assert int(d["rank"].item()) == int(rank.item())
+            Pg = d["P"].cpu().numpy().astype(np.float64)
+            assert np.abs(Pg - got @ got.T).max() <= 3e-5 * (np.abs(got) @ np.abs(got).T).max() + 1e-7
     finally:
         c.close()
 
