@@ -98,7 +98,7 @@ __device__ __forceinline__ void eig_body(const double *__restrict__ C, int m, fl
         if (sweep == 0) abs_floor = 1e-10f * sqrtf(s_fro);
 
         for (int r = 0; r < mm - 1; ++r) {
-            // rotation of each pair of this round
+            // the rotation of each pair of round r of the circle ordering
             if (tid < half) {
                 int p, q;
                 if (tid == 0) { p = mm - 1; q = r; }
