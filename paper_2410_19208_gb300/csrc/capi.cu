@@ -1410,7 +1410,7 @@ gram_off put_gram(table_blob &tb, const std::vector<psd_g_gram> &t)
     std::vector<int2> bm, bmr;
     for (int e = 0; e < (int)t.size(); ++e) {
         for (int b = 0; b < t[e].nblk; ++b) bm.push_back(make_int2(e, b));
-        const int nr = psd_gram_reduce_blocks(t[e].m);
+        const int nr = psd_gram_reduce_grouped_blocks(t[e].m, t[e].nblk);
         for (int b = 0; b < nr; ++b) bmr.push_back(make_int2(e, b));
     }
     gram_off o;

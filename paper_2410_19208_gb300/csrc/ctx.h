@@ -283,6 +283,14 @@ inline int psd_gram_reduce_blocks(int m)
     const int nt8 = (int)psd_round_up(m, 8) / 8;
     return (nt8 * (nt8 + 1) / 2 * 64 + 31) / 32;
 }
+// In a grouped reduction an entry with at most PSD_GRAM_RED_SEQ partials
+// takes a thread per position (256 per block), others the form above
+constexpr int PSD_GRAM_RED_SEQ = 32;
+inline int psd_gram_reduce_grouped_blocks(int m, int nblk)
+{
+    const int nt8 = (int)psd_round_up(m, 8) / 8;
+    return nblk <= PSD_GRAM_RED_SEQ ? (nt8 * (nt8 + 1) / 2 * 64 + 255) / 256 : psd_gram_reduce_blocks(m);
+}
 
 // ---- grouped launches (psdproj_batched_grouped) --------------------------
 // One launch runs one small step for many problems.  Entry e of a table
@@ -300,7 +308,7 @@ struct psd_g_gram {          // launch_gram, symmetric forms, m <= 128
 };
 // two: the two-sided form (S = (X^T Z + Z^T X)/2); nb / nb_red: the blocks
 // of the product and of the reduction (bmap: block < nblk of its entry;
-// bmap_red: block < psd_gram_reduce_blocks(m))
+// bmap_red: block < psd_gram_reduce_grouped_blocks(m, nblk))
 cudaError_t launch_gram_grouped(cudaStream_t s, const psd_g_gram *tab, int two, const int2 *bmap, int nb,
                                 const int2 *bmap_red, int nb_red, int mp_max);
 

@@ -342,25 +342,11 @@ gram_upper_grouped_kernel(const psd_g_gram *__restrict__ tab, const int2 *__rest
 // partials g, g + 8, ...), each summing in double-float; the 8 sums are
 // added in a fixed order (deterministic).  Both (a, b) and (b, a) are
 // written (scale: 1 for X^T X, 1/2 for the two-sided form).
-__device__ __forceinline__ void gram_upper_reduce_body(const float *__restrict__ gpart, int nblk, int m, int mp,
-                                                       float scale, double *__restrict__ G,
-                                                       float2 *__restrict__ Gdf, int bid)
+// position q of the tile-major partials (tile q / 64, entry (i, j) of its
+// 8 x 8 block) stored as entries (a, b) and (b, a) of G (and Gdf), scaled
+__device__ __forceinline__ void gram_reduce_store(fsum acc, int q, int nt8, int m, float scale,
+                                                  double *__restrict__ G, float2 *__restrict__ Gdf)
 {
-    __shared__ fsum part[8][32];
-    const int nt8 = mp / 8, ntiles = nt8 * (nt8 + 1) / 2;
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int q = bid * 32 + lane;
-    const bool inr = q < ntiles * 64;
-    fsum acc = {0.0f, 0.0f};
-    if (inr) {
-#pragma unroll 4
-        for (int b = g; b < nblk; b += 8) acc = fsum_add(acc, {gpart[(int64_t)b * ntiles * 64 + q], 0.0f});
-    }
-    part[g][lane] = acc;
-    __syncthreads();
-    if (g != 0 || !inr) return;
-#pragma unroll
-    for (int w = 1; w < 8; ++w) acc = fsum_add(acc, part[w][lane]);
     const int t = q >> 6, ij = q & 63, i = ij >> 3, j = ij & 7;
     int bi = 0, tt = t;
     while (tt >= nt8 - bi) {
@@ -381,6 +367,45 @@ __device__ __forceinline__ void gram_upper_reduce_body(const float *__restrict__
     }
 }
 
+__device__ __forceinline__ void gram_upper_reduce_body(const float *__restrict__ gpart, int nblk, int m, int mp,
+                                                       float scale, double *__restrict__ G,
+                                                       float2 *__restrict__ Gdf, int bid)
+{
+    __shared__ fsum part[8][32];
+    const int nt8 = mp / 8, ntiles = nt8 * (nt8 + 1) / 2;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int q = bid * 32 + lane;
+    const bool inr = q < ntiles * 64;
+    fsum acc = {0.0f, 0.0f};
+    if (inr) {
+#pragma unroll 4
+        for (int b = g; b < nblk; b += 8) acc = fsum_add(acc, {gpart[(int64_t)b * ntiles * 64 + q], 0.0f});
+    }
+    part[g][lane] = acc;
+    __syncthreads();
+    if (g != 0 || !inr) return;
+#pragma unroll
+    for (int w = 1; w < 8; ++w) acc = fsum_add(acc, part[w][lane]);
+    gram_reduce_store(acc, q, nt8, m, scale, G, Gdf);
+}
+
+// The same sums with a thread per position (256 per block), each adding its
+// position's partials in order: a problem of a grouped batch with at most
+// PSD_GRAM_RED_SEQ partials would leave most warps of the form above idle
+// in its many blocks
+__device__ __forceinline__ void gram_upper_reduce_seq_body(const float *__restrict__ gpart, int nblk, int m, int mp,
+                                                           float scale, double *__restrict__ G,
+                                                           float2 *__restrict__ Gdf, int bid)
+{
+    const int nt8 = mp / 8, ntiles = nt8 * (nt8 + 1) / 2;
+    const int q = bid * 256 + threadIdx.x;
+    if (q >= ntiles * 64) return;
+    fsum acc = {0.0f, 0.0f};
+#pragma unroll 4
+    for (int b = 0; b < nblk; ++b) acc = fsum_add(acc, {gpart[(int64_t)b * ntiles * 64 + q], 0.0f});
+    gram_reduce_store(acc, q, nt8, m, scale, G, Gdf);
+}
+
 __global__ void __launch_bounds__(256)
 gram_upper_reduce_kernel(const float *__restrict__ gpart, int nblk, int m, int mp, float scale,
                          double *__restrict__ G, float2 *__restrict__ Gdf)
@@ -393,7 +418,10 @@ gram_upper_reduce_grouped_kernel(const psd_g_gram *__restrict__ tab, const int2 
 {
     const int2 b = bmap[blockIdx.x];
     const psd_g_gram a = tab[b.x];
-    gram_upper_reduce_body(a.gpart, a.nblk, a.m, a.mp, scale, a.G, a.Gdf, b.y);
+    if (a.nblk <= PSD_GRAM_RED_SEQ)          // uniform across the block
+        gram_upper_reduce_seq_body(a.gpart, a.nblk, a.m, a.mp, scale, a.G, a.Gdf, b.y);
+    else
+        gram_upper_reduce_body(a.gpart, a.nblk, a.m, a.mp, scale, a.G, a.Gdf, b.y);
 }
 
 }  // namespace
